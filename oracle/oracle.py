@@ -1,0 +1,220 @@
+"""ctypes wrapper around the plain-C FP64 oracle (``nebem_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference legs of ``bench.py``.  The CUDA path never imports it.
+
+Every function takes the raw element records (``ELEMENT_DTYPE`` arrays) and builds its
+own local frames, image translations and constants inside the C code.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "nebem_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+_d = C.POINTER(C.c_double)
+_i32 = C.POINTER(C.c_int32)
+_vp = C.c_void_p
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-shared", "-fPIC",
+               "-std=c11", "-o", tmp, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        L.or_ke.restype = C.c_double
+        L.or_eps0.restype = C.c_double
+        L.or_num_threads.restype = C.c_int
+        L.or_influence_points.argtypes = [_vp, _d, C.c_int64, C.c_int, _d, _d]
+        L.or_image_table.argtypes = [_d, C.c_int, C.c_int, _d]
+        L.or_image_table.restype = C.c_int64
+        L.or_fill.argtypes = [_vp, C.c_int64, _d, C.c_int, C.c_int, _d]
+        L.or_lu_factor.argtypes = [C.c_int64, _d, _i32]
+        L.or_lu_solve.argtypes = [C.c_int64, _d, _i32, _d]
+        L.or_rhs.argtypes = [_vp, C.c_int64, _d, C.c_int32, _d]
+        L.or_eval.argtypes = [_vp, C.c_int64, _d, _d, C.c_int, C.c_int, _d, C.c_int64, _d, _d]
+        L.or_centroids.argtypes = [_vp, C.c_int64, _d, _d, _d]
+        L.or_space_charge.argtypes = [_d, _d, C.c_int64, _d, C.c_int64, C.c_int, C.c_double, _d, _d]
+        L.or_rhs_space_charge.argtypes = [_vp, C.c_int64, _d, C.c_int32, _d, _d, C.c_int64, C.c_double, _d]
+        L.or_dynamic_step.argtypes = [_vp, C.c_int64, _d, C.c_int32, _d, C.c_int, C.c_int, _d, _i32, _d, _d,
+                                      C.c_int64, C.c_double, C.c_double, C.c_double, _d, _d]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(_d)
+
+
+def _pi(a):
+    return a.ctypes.data_as(_i32)
+
+
+def _rec(el):
+    el = np.ascontiguousarray(el)
+    assert el.dtype.itemsize == 128
+    return el, el.ctypes.data_as(_vp)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise ValueError(f"oracle {what} failed with code {rc}")
+
+
+def ke() -> float:
+    return lib().or_ke()
+
+
+def eps0() -> float:
+    return lib().or_eps0()
+
+
+def num_threads() -> int:
+    return lib().or_num_threads()
+
+
+def influence(element, pts, poly: bool = False):
+    """Phi' (m) and E' (dimensionless, global components) of one element at points."""
+    el, pe = _rec(np.atleast_1d(element)[:1])
+    pts = np.ascontiguousarray(np.atleast_2d(pts), dtype=np.float64)
+    n = pts.shape[0]
+    phi = np.empty(n)
+    E = np.empty((n, 3))
+    _check(lib().or_influence_points(pe, _p(pts), n, int(poly), _p(phi), _p(E)), "influence")
+    return phi, E
+
+
+def image_table(lattice, lo, hi):
+    if lattice is None:
+        return np.zeros((1, 3))
+    m = hi - lo + 1
+    t = np.empty((m * m, 3))
+    lat = np.ascontiguousarray(lattice, dtype=np.float64)
+    lib().or_image_table(_p(lat), lo, hi, _p(t))
+    return t
+
+
+def _lat(g):
+    return None if g.lattice is None else np.ascontiguousarray(g.lattice, dtype=np.float64)
+
+
+def fill(g):
+    """Influence matrix K (n x n, returned as a C-ordered array with K[i, j])."""
+    el, pe = _rec(g.elements)
+    n = el.shape[0]
+    K = np.empty(n * n)
+    lat = _lat(g)
+    _check(lib().or_fill(pe, n, _p(lat), g.img_lo, g.img_hi, _p(K)), "fill")
+    return K.reshape(n, n).T.copy()  # column-major storage -> K[i, j]
+
+
+def lu_factor(K):
+    """Partial-pivoting LU of K[i, j]; returns (column-major factors, pivots)."""
+    n = K.shape[0]
+    A = np.asfortranarray(K, dtype=np.float64).ravel(order="F").copy()
+    piv = np.empty(n, dtype=np.int32)
+    _check(lib().or_lu_factor(n, _p(A), _pi(piv)), "lu_factor")
+    return A, piv
+
+
+def lu_solve(fac, b):
+    A, piv = fac
+    x = np.array(b, dtype=np.float64, copy=True)
+    lib().or_lu_solve(x.shape[0], _p(A), _pi(piv), _p(x))
+    return x
+
+
+def rhs(g, voltages=None):
+    el, pe = _rec(g.elements)
+    v = np.ascontiguousarray(g.voltages if voltages is None else voltages, dtype=np.float64)
+    b = np.empty(el.shape[0])
+    _check(lib().or_rhs(pe, el.shape[0], _p(v), v.shape[0], _p(b)), "rhs")
+    return b
+
+
+def solve(g, voltages=None, K=None):
+    """sigma (C/m^2) for the geometry's boundary conditions; also returns K and factors."""
+    K = fill(g) if K is None else K
+    fac = lu_factor(K)
+    return lu_solve(fac, rhs(g, voltages)), K, fac
+
+
+def eval_points(g, sigma, pts):
+    el, pe = _rec(g.elements)
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    n = pts.shape[0]
+    phi = np.empty(n)
+    E = np.empty((n, 3))
+    lat = _lat(g)
+    _check(lib().or_eval(pe, el.shape[0], _p(sigma), _p(lat), g.img_lo, g.img_hi, _p(pts), n, _p(phi), _p(E)),
+           "eval")
+    return phi, E
+
+
+def centroids(g):
+    el, pe = _rec(g.elements)
+    n = el.shape[0]
+    c = np.empty((n, 3)); nr = np.empty((n, 3)); a = np.empty(n)
+    _check(lib().or_centroids(pe, n, _p(c), _p(nr), _p(a)), "centroids")
+    return c, nr, a
+
+
+def space_charge(src, q, tgt=None, soft=1e-6):
+    """Softened direct sum; tgt=None means targets are the sources (self excluded)."""
+    src = np.ascontiguousarray(src, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    selfidx = tgt is None
+    tgt = src if tgt is None else np.ascontiguousarray(tgt, dtype=np.float64)
+    nt = tgt.shape[0]
+    phi = np.empty(nt)
+    E = np.empty((nt, 3))
+    lib().or_space_charge(_p(src), _p(q), src.shape[0], _p(tgt), nt, int(selfidx), soft, _p(phi), _p(E))
+    return phi, E
+
+
+def rhs_space_charge(g, pos, q, soft=1e-6):
+    el, pe = _rec(g.elements)
+    v = np.ascontiguousarray(g.voltages, dtype=np.float64)
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    b = np.empty(el.shape[0])
+    _check(lib().or_rhs_space_charge(pe, el.shape[0], _p(v), v.shape[0], _p(pos), _p(q), pos.shape[0], soft,
+                                     _p(b)), "rhs_space_charge")
+    return b
+
+
+def dynamic_step(g, fac, pos, q, soft=1e-6, mu=1e-4, dt=1e-9):
+    """One Alg. 4 step; returns (new positions, sigma, E at carriers before the move)."""
+    el, pe = _rec(g.elements)
+    v = np.ascontiguousarray(g.voltages, dtype=np.float64)
+    A, piv = fac
+    pos = np.array(pos, dtype=np.float64, copy=True)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    n = el.shape[0]
+    sigma = np.empty(n)
+    E = np.empty((pos.shape[0], 3))
+    lat = _lat(g)
+    _check(lib().or_dynamic_step(pe, n, _p(v), v.shape[0], _p(lat), g.img_lo, g.img_hi, _p(A), _pi(piv),
+                                 _p(pos), _p(q), pos.shape[0], soft, mu, dt, _p(sigma), _p(E)), "dynamic_step")
+    return pos, sigma, E

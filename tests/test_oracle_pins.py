@@ -1,0 +1,460 @@
+"""Pins for the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Nothing here compares the oracle with itself: every check uses an independent route
+(adaptive quadrature of the defining integrals of Sec. 2.1, textbook closed values,
+the far-field limit, E = -grad(phi) (Sec. 2), Gauss's law, Galerkin reciprocity, an
+independent LU from numpy, refinement of the unit-cube capacitance, cube symmetry,
+the interface condition of the dielectric rows checked through the evaluation path).
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from oracle import oracle as O
+from paper_2606_24154_gb300 import inputs as I
+
+
+def rect_el(v0, v1, v3):
+    v0, v1, v3 = map(np.asarray, (v0, v1, v3))
+    el = np.zeros(1, I.ELEMENT_DTYPE)
+    el["kind"] = I.KIND_RECT
+    el["v"][0] = [v0, v1, v1 + v3 - v0, v3]
+    return el
+
+
+def tri_el(v0, v1, v2):
+    el = np.zeros(1, I.ELEMENT_DTYPE)
+    el["kind"] = I.KIND_TRI
+    el["v"][0, :3] = [v0, v1, v2]
+    return el
+
+
+def random_rect(gen, scale=1e-3):
+    c = gen.normal(size=3) * scale
+    u = gen.normal(size=3); u /= np.linalg.norm(u)
+    w = np.cross(u, gen.normal(size=3)); w /= np.linalg.norm(w)
+    L1, L2 = scale * gen.uniform(0.3, 1.5, 2)
+    v0 = c - 0.5 * L1 * u - 0.5 * L2 * w
+    return rect_el(v0, v0 + L1 * u, v0 + L2 * w)
+
+
+def random_tri(gen, scale=1e-3):
+    v = gen.normal(size=(3, 3)) * scale
+    return tri_el(*v)
+
+
+def quad_influence(el, P, eps=1e-13):
+    """Adaptive 2-D quadrature of Phi' and E' over the parametrised element."""
+    v = el["v"][0]
+    P = np.asarray(P, float)
+    if el["kind"][0] == I.KIND_RECT:
+        e1, e2 = v[1] - v[0], v[3] - v[0]
+        jac = np.linalg.norm(np.cross(e1, e2))
+        top = lambda s: 1.0
+    else:
+        e1, e2 = v[1] - v[0], v[2] - v[0]
+        jac = np.linalg.norm(np.cross(e1, e2))
+        top = lambda s: 1.0 - s
+
+    def comp(k):
+        def f(t, s):
+            x = v[0] + s * e1 + t * e2
+            d = P - x
+            r = math.sqrt(d @ d)
+            return jac / r if k < 0 else jac * d[k] / r**3
+        return integrate.dblquad(f, 0.0, 1.0, 0.0, top, epsabs=0.0, epsrel=eps)[0]
+
+    return comp(-1), np.array([comp(0), comp(1), comp(2)])
+
+
+def _normal(el):
+    v = el["v"][0]
+    n = np.cross(v[1] - v[0], v[2] - v[0])
+    return n / np.linalg.norm(n)
+
+
+def _centroid(el):
+    v = el["v"][0]
+    return v[:4].mean(0) if el["kind"][0] == I.KIND_RECT else v[:3].mean(0)
+
+
+@pytest.mark.parametrize("shape", ["rect", "tri"])
+def test_closed_form_vs_quadrature(shape):
+    gen = np.random.default_rng(7)
+    worst = 0.0
+    for trial in range(6):
+        el = random_rect(gen) if shape == "rect" else random_tri(gen)
+        c, n = _centroid(el), _normal(el)
+        size = math.sqrt(np.linalg.norm(np.cross(el["v"][0][1] - el["v"][0][0], el["v"][0][2] - el["v"][0][0])))
+        for dist, h in [(0.3, 0.2), (1.0, 0.5), (3.0, 1.0), (0.2, 0.05), (2.0, -0.7)]:
+            dirn = gen.normal(size=3); dirn -= (dirn @ n) * n; dirn /= np.linalg.norm(dirn)
+            P = c + dist * size * dirn + h * size * n
+            phi, E = O.influence(el, P)
+            qphi, qE = quad_influence(el, P)
+            worst = max(worst, abs(phi[0] - qphi) / abs(qphi),
+                        np.abs(E[0] - qE).max() / np.abs(qE).max())
+    assert worst < 2e-11, worst
+
+
+def test_rect_equals_two_triangles():
+    gen = np.random.default_rng(11)
+    cases = [random_rect(gen) for _ in range(20)]
+    # an exactly axis-aligned rectangle (local normal coordinate of in-plane points is 0)
+    cases.append(rect_el([-1e-3, -0.5e-3, 0.0], [1e-3, -0.5e-3, 0.0], [-1e-3, 0.7e-3, 0.0]))
+    for ci, el in enumerate(cases):
+        v = el["v"][0]
+        t1, t2 = tri_el(v[0], v[1], v[2]), tri_el(v[0], v[2], v[3])
+        c, n = _centroid(el), _normal(el)
+        size = math.sqrt(np.linalg.norm(np.cross(v[1] - v[0], v[3] - v[0])))
+        P = [c + size * gen.normal(size=3) * s for s in (0.1, 0.7, 3.0, 30.0)]
+        if ci == len(cases) - 1:
+            # in-plane points: inside (off the diagonal) and outside the element
+            P += [np.array([0.3e-3, -0.2e-3, 0.0]), np.array([2.5e-3, 0.1e-3, 0.0]),
+                  np.array([-0.4e-3, 0.6e-3, 0.0])]
+        P = np.array(P)
+        pr, Er = O.influence(el, P)
+        pa, Ea = O.influence(t1, P)
+        pb, Eb = O.influence(t2, P)
+        scale_p = np.abs(pr).max()
+        assert np.abs(pr - (pa + pb)).max() <= 1e-12 * scale_p
+        assert np.abs(Er - (Ea + Eb)).max() <= 1e-11 * max(1.0, np.abs(Er).max())
+        # the polygon form of the rectangle agrees too (two independent formulas)
+        pp, Ep = O.influence(el, P, poly=True)
+        assert np.abs(pr - pp).max() <= 1e-12 * scale_p
+        assert np.abs(Er - Ep).max() <= 1e-11 * max(1.0, np.abs(Er).max())
+
+
+def test_square_textbook_values():
+    a = 2e-3
+    el = rect_el([0, 0, 0], [a, 0, 0], [0, a, 0])  # in the z=0 plane, normal +z
+    phi, E = O.influence(el, [[a / 2, a / 2, 0.0]])
+    assert abs(phi[0] - 4 * a * math.log(1 + math.sqrt(2))) < 1e-14 * a * 10
+    assert np.abs(E).max() < 1e-12
+    b = a / 2
+    for h in [1e-6, 1e-4, 1e-3, 1e-2, 1.0]:
+        _, E = O.influence(el, [[b, b, h]])
+        omega = 4 * math.atan(b * b / (h * math.sqrt(2 * b * b + h * h)))
+        assert abs(E[0, 2] - omega) <= 1e-13 * max(omega, 1e-300) + 1e-300
+        assert abs(E[0, 0]) < 1e-12 and abs(E[0, 1]) < 1e-12
+
+
+def test_normal_jump_and_principal_value():
+    gen = np.random.default_rng(3)
+    for el in [random_rect(gen), random_tri(gen)]:
+        c, n = _centroid(el), _normal(el)
+        size = 1e-3
+        for delta in [1e-9 * size, 1e-12 * size]:
+            _, Ep = O.influence(el, c + delta * n)
+            _, Em = O.influence(el, c - delta * n)
+            jump = (Ep[0] - Em[0]) @ n
+            assert abs(jump - 4 * math.pi) < 1e-6
+    # principal value exactly in the plane: the mean of the one-sided limits, i.e. no
+    # normal component (axis-aligned element, so the in-plane point is exact)
+    el = rect_el([-1e-3, -1e-3, 0.0], [1e-3, -1e-3, 0.0], [-1e-3, 0.5e-3, 0.0])
+    P = np.array([[0.2e-3, -0.1e-3, 0.0]])
+    _, E0 = O.influence(el, P)
+    _, Ep = O.influence(el, P + [0, 0, 1e-15])
+    _, Em = O.influence(el, P - [0, 0, 1e-15])
+    assert E0[0, 2] == 0.0
+    assert np.allclose(E0[0], 0.5 * (Ep[0] + Em[0]), rtol=1e-9, atol=1e-9)
+
+
+def test_self_term_principal_value_in_fill():
+    gen = np.random.default_rng(5)
+    el = np.concatenate([random_tri(gen), random_rect(gen)])
+    el["bc"] = I.BC_DIELECTRIC
+    el["eps_a"], el["eps_b"] = 4.4, 1.0
+    g = I.Geometry("pv", el, np.array([0.0]))
+    K = O.fill(g)
+    # the element's own normal field at its centroid is zero (principal value): the
+    # diagonal equals the interface term alone
+    diag = (4.4 + 1.0) / (2 * O.eps0() * (1.0 - 4.4))
+    assert np.allclose(np.diag(K), diag, rtol=1e-14)
+
+
+@pytest.mark.parametrize("shape", ["rect", "tri"])
+def test_far_field_limit(shape):
+    gen = np.random.default_rng(13)
+    el = random_rect(gen) if shape == "rect" else random_tri(gen)
+    v = el["v"][0]
+    A = 0.5 * np.linalg.norm(np.cross(v[1] - v[0], v[2] - v[0])) * (2 if shape == "rect" else 1)
+    c = _centroid(el)
+    size = math.sqrt(A)
+    errs = []
+    for R in [30.0, 300.0, 3000.0]:
+        d = gen.normal(size=3); d /= np.linalg.norm(d)
+        P = c + R * size * d
+        phi, E = O.influence(el, P)
+        r = R * size
+        errs.append((abs(phi[0] * r / A - 1.0), np.linalg.norm(E[0] * r * r / A - d)))
+    # monopole limit with O((a/r)^2) error: each decade of distance gains ~2 decades
+    assert errs[0][0] < 5e-3 and errs[1][0] < 5e-5 and errs[2][0] < 5e-7
+    assert errs[0][1] < 5e-3 and errs[1][1] < 5e-5 and errs[2][1] < 5e-7
+
+
+@pytest.mark.parametrize("shape", ["rect", "tri"])
+def test_field_is_minus_gradient(shape):
+    gen = np.random.default_rng(17)
+    el = random_rect(gen) if shape == "rect" else random_tri(gen)
+    c, n = _centroid(el), _normal(el)
+    size = 1e-3
+    for P in [c + size * gen.normal(size=3) for _ in range(5)] + [c + 0.01 * size * n + 0.1 * size * gen.normal(size=3)]:
+        h = 1e-5 * size
+        _, E = O.influence(el, P)
+        g = np.zeros(3)
+        for k in range(3):
+            dp = np.zeros(3); dp[k] = h
+            pp, _ = O.influence(el, P + dp)
+            pm, _ = O.influence(el, P - dp)
+            g[k] = (pp[0] - pm[0]) / (2 * h)
+        assert np.abs(E[0] + g).max() <= 1e-7 * max(1.0, np.abs(E[0]).max())
+
+
+def _box_flux(field_fn, lo, hi, m=40):
+    x, w = np.polynomial.legendre.leggauss(m)
+    total = 0.0
+    for ax in range(3):
+        u_ax, w_ax = (ax + 1) % 3, (ax + 2) % 3
+        su = 0.5 * (hi[u_ax] - lo[u_ax]); sw = 0.5 * (hi[w_ax] - lo[w_ax])
+        cu = 0.5 * (hi[u_ax] + lo[u_ax]); cw = 0.5 * (hi[w_ax] + lo[w_ax])
+        U, W = np.meshgrid(cu + su * x, cw + sw * x, indexing="ij")
+        WT = np.outer(w, w) * su * sw
+        for side, sgn in ((hi[ax], 1.0), (lo[ax], -1.0)):
+            P = np.zeros((m * m, 3))
+            P[:, ax] = side; P[:, u_ax] = U.ravel(); P[:, w_ax] = W.ravel()
+            E = field_fn(P)
+            total += sgn * (E[:, ax] * WT.ravel()).sum()
+    return total
+
+
+@pytest.mark.parametrize("shape", ["rect", "tri"])
+def test_gauss_law_single_element(shape):
+    gen = np.random.default_rng(19)
+    el = random_rect(gen, 1.0) if shape == "rect" else random_tri(gen, 1.0)
+    v = el["v"][0][: (4 if shape == "rect" else 3)]
+    A = np.linalg.norm(np.cross(v[1] - v[0], v[2] - v[0])) * (1.0 if shape == "rect" else 0.5)
+    lo, hi = v.min(0) - 1.0, v.max(0) + 1.0
+    flux = _box_flux(lambda P: O.influence(el, P)[1], lo, hi)
+    assert abs(flux - 4 * math.pi * A) < 1e-9 * 4 * math.pi * A
+    lo2 = hi + 0.5
+    flux0 = _box_flux(lambda P: O.influence(el, P)[1], lo2, lo2 + 1.0)
+    assert abs(flux0) < 1e-10 * 4 * math.pi * A
+
+
+def _surface_integral(el, fn, m=24):
+    """Gauss-Legendre integral of fn over an element (collapsed map for triangles)."""
+    x, w = np.polynomial.legendre.leggauss(m)
+    s = 0.5 * (x + 1.0); ws = 0.5 * w
+    S, T = np.meshgrid(s, s, indexing="ij")
+    W = np.outer(ws, ws)
+    v = el["v"][0]
+    if el["kind"][0] == I.KIND_RECT:
+        e1, e2 = v[1] - v[0], v[3] - v[0]
+        jac = np.linalg.norm(np.cross(e1, e2))
+        P = v[0] + S.ravel()[:, None] * e1 + T.ravel()[:, None] * e2
+        return (fn(P) * W.ravel()).sum() * jac
+    e1, e2 = v[1] - v[0], v[2] - v[0]
+    jac = np.linalg.norm(np.cross(e1, e2))
+    a, b = S.ravel(), (T * (1.0 - S)).ravel()
+    P = v[0] + a[:, None] * e1 + b[:, None] * e2
+    return (fn(P) * W.ravel() * (1.0 - S.ravel())).sum() * jac
+
+
+def test_galerkin_reciprocity():
+    gen = np.random.default_rng(23)
+    for trial in range(4):
+        ei = random_rect(gen) if trial % 2 else random_tri(gen)
+        ej = random_tri(gen)
+        ej["v"] += np.array([3e-3, 1e-3, -2e-3])
+        a = _surface_integral(ei, lambda P: O.influence(ej, P)[0])
+        b = _surface_integral(ej, lambda P: O.influence(ei, P)[0])
+        assert abs(a - b) <= 1e-9 * abs(a)
+
+
+def test_image_sum_equals_explicit_copies():
+    g = I.thgem(I.PlateSpec(n_phi=12, n_r=1, n_zc=1, n_zf=2), n_plane=1)
+    g.img_lo, g.img_hi = -1, 1
+    t = O.image_table(g.lattice, -1, 1)
+    # explicit superposition of translated copies, without images
+    copies = []
+    for k in range(t.shape[0]):
+        e = g.elements.copy()
+        e["v"] = e["v"] + t[k]
+        if e["kind"][0] == I.KIND_TRI:
+            pass
+        copies.append(e)
+    big = np.concatenate(copies)
+    # triangles keep v[3] = 0 as padding: restore the padding after the shift
+    tri = big["kind"] == I.KIND_TRI
+    big["v"][tri, 3] = 0.0
+    gb = I.Geometry("copies", big, g.voltages)
+    sigma = np.random.default_rng(1).normal(size=g.n)
+    P = I.cell_points(g, 50, I.rng(99))
+    p1, E1 = O.eval_points(g, sigma, P)
+    p2, E2 = O.eval_points(gb, np.tile(sigma, t.shape[0]), P)
+    assert np.abs(p1 - p2).max() <= 1e-11 * np.abs(p1).max()
+    assert np.abs(E1 - E2).max() <= 1e-11 * np.abs(E1).max()
+    # image index order: k = (k1 - lo) * m + (k2 - lo)
+    a1, a2 = g.lattice
+    assert np.array_equal(t[0], -a1 - a2) and np.array_equal(t[1], -a1) and np.array_equal(t[3], -a2)
+    assert np.array_equal(t[4], np.zeros(3)) and np.array_equal(t[8], a1 + a2)
+
+
+def test_lu_matches_numpy_and_tie_break():
+    gen = np.random.default_rng(29)
+    n = 60
+    K = gen.normal(size=(n, n)) + n * 0.1 * np.eye(n)
+    b = gen.normal(size=n)
+    x = O.lu_solve(O.lu_factor(K), b)
+    xr = np.linalg.solve(K, b)
+    assert np.abs(x - xr).max() <= 1e-12 * np.abs(xr).max()
+    # ties: equal |a| in column 0 -> the lowest index is the pivot (no swap at step 0)
+    T = np.array([[2.0, 1.0, 0.0], [-2.0, 3.0, 1.0], [2.0, 0.0, 5.0]])
+    _, piv = O.lu_factor(T)
+    assert piv[0] == 0
+    T2 = np.array([[1.0, 1.0, 0.0], [-2.0, 3.0, 1.0], [2.0, 0.0, 5.0]])
+    _, piv2 = O.lu_factor(T2)
+    assert piv2[0] == 1
+    # backward error of the factorisation on a BEM matrix
+    g = I.cube(n_per_edge=4)
+    Kc = O.fill(g)
+    sig = O.lu_solve(O.lu_factor(Kc), O.rhs(g))
+    r = Kc @ sig - O.rhs(g)
+    assert np.abs(r).max() / (np.abs(Kc).max() * np.abs(sig).max() * g.n) < 1e-15
+
+
+def _capacitance(n_edge):
+    g = I.cube(edge=0.01, n_per_edge=n_edge)
+    sigma, K, fac = O.solve(g)
+    _, _, area = O.centroids(g)
+    return (sigma * area).sum() / 1.0 / (4 * math.pi * O.eps0() * 0.01), g, sigma
+
+
+def test_cube_capacitance_refinement():
+    c4, _, _ = _capacitance(4)
+    c8, _, _ = _capacitance(8)
+    c12, _, _ = _capacitance(12)
+    ref = 0.6607
+    # constant-element collocation approaches the unit-cube value monotonically
+    assert c4 < c8 < c12 < ref + 2e-3
+    assert abs(c12 - ref) < abs(c8 - ref) < abs(c4 - ref)
+    assert abs(c8 - ref) < 0.01 * ref
+
+
+def test_cube_symmetry_and_gauss():
+    cap, g, sigma = _capacitance(8)
+    c, nr, area = O.centroids(g)
+    key = {tuple(np.round(ci / 1e-6).astype(int)): i for i, ci in enumerate(c)}
+    perms = [(0, 1, 2), (1, 2, 0), (2, 0, 1), (1, 0, 2), (0, 2, 1), (2, 1, 0)]
+    for perm in perms:
+        for signs in [(1, 1, 1), (-1, 1, 1), (1, -1, -1), (-1, -1, -1)]:
+            cc = c[:, perm] * np.array(signs)
+            idx = [key[tuple(np.round(x / 1e-6).astype(int))] for x in cc]
+            assert np.abs(sigma[idx] - sigma).max() <= 1e-12 * np.abs(sigma).max()
+    P = np.random.default_rng(2).uniform(-0.02, 0.02, (20, 3))
+    p1, E1 = O.eval_points(g, sigma, P)
+    p2, E2 = O.eval_points(g, sigma, -P)
+    assert np.abs(p1 - p2).max() <= 1e-12 * np.abs(p1).max()
+    assert np.abs(E1 + E2).max() <= 1e-11 * np.abs(E1).max()
+    # Gauss's law on the solved charge: flux through an enclosing box = Q / eps0
+    Q = (sigma * area).sum()
+    flux = _box_flux(lambda X: O.eval_points(g, sigma, X)[1], np.full(3, -0.015), np.full(3, 0.015), m=32)
+    assert abs(flux - Q / O.eps0()) < 1e-8 * Q / O.eps0()
+    # potential on the conductor away from collocation points is close to 1 V
+    v = g.elements["v"][0]
+    P_edge = 0.25 * v[0] + 0.75 * v[2]
+    ph, _ = O.eval_points(g, sigma, P_edge[None])
+    assert abs(ph[0] - 1.0) < 0.05
+
+
+def _slab_capacitor():
+    """Two conductor plates around a dielectric slab (square lattice, +-3 images)."""
+    p = 1e-3
+    b = I._Builder()
+    m = 3
+    xs = np.linspace(-p / 2, p / 2, m + 1)
+
+    def sheet(z, up, bc, cond, ea=1.0, eb=1.0):
+        for i in range(m):
+            for j in range(m):
+                v0 = [xs[i], xs[j], z]
+                v1 = [xs[i + 1], xs[j], z]
+                v3 = [xs[i], xs[j + 1], z]
+                v2 = [xs[i + 1], xs[j + 1], z]
+                if up:
+                    b.rect(v0, v1, v2, v3, bc, cond, ea, eb)
+                else:
+                    b.rect(v0, v3, v2, v1, bc, cond, ea, eb)
+
+    sheet(1e-3, True, I.BC_CONDUCTOR, 0)
+    sheet(-1e-3, True, I.BC_CONDUCTOR, 1)
+    sheet(0.4e-3, True, I.BC_DIELECTRIC, -1, 4.0, 1.0)   # slab top: slab below (-n side)
+    sheet(-0.4e-3, False, I.BC_DIELECTRIC, -1, 4.0, 1.0)  # slab bottom: normal -z, slab above
+    lat = np.array([[p, 0, 0], [0, p, 0]])
+    return I.Geometry("slab", b.build(), np.array([100.0, 0.0]), lattice=lat, img_lo=-3, img_hi=3)
+
+
+def test_dielectric_interface_condition():
+    g = _slab_capacitor()
+    sigma, K, fac = O.solve(g)
+    c, nr, _ = O.centroids(g)
+    diel = np.where(g.elements["bc"] == I.BC_DIELECTRIC)[0]
+    d = 1e-9
+    _, Eb = O.eval_points(g, sigma, c[diel] + d * nr[diel])   # +n side (eps_b)
+    _, Ea = O.eval_points(g, sigma, c[diel] - d * nr[diel])   # -n side (eps_a)
+    ea = g.elements["eps_a"][diel]; eb = g.elements["eps_b"][diel]
+    Dn_a = ea * (Ea * nr[diel]).sum(1)
+    Dn_b = eb * (Eb * nr[diel]).sum(1)
+    assert np.abs(Dn_a - Dn_b).max() <= 1e-5 * np.abs(Dn_a).max()
+    # the slab weakens the field inside it: E_slab / E_gas close to 1/eps_r at the centre
+    _, Ein = O.eval_points(g, sigma, np.array([[0, 0, 0.0]]))
+    _, Eout = O.eval_points(g, sigma, np.array([[0, 0, 0.7e-3]]))
+    assert 0.2 < Ein[0, 2] / Eout[0, 2] < 0.3
+
+
+def test_space_charge_invariants():
+    gen = np.random.default_rng(31)
+    n = 300
+    pos = gen.normal(size=(n, 3)) * 1e-4
+    q = np.where(gen.random(n) < 0.5, 1.0, -1.0) * I.E_CHARGE
+    phi, E = O.space_charge(pos, q, soft=1e-6)
+    # Newton's third law: the total force on the cloud vanishes
+    F = (q[:, None] * E).sum(0)
+    assert np.abs(F).max() <= 1e-12 * (np.abs(q[:, None] * E)).sum()
+    # the interaction energy is symmetric: sum_t q_t phi_t == sum over ordered pairs
+    # self exclusion by index: removing carrier 0 and evaluating at its position
+    p0, E0 = O.space_charge(pos[1:], q[1:], tgt=pos[:1], soft=1e-6)
+    assert abs(p0[0] - phi[0]) <= 1e-14 * abs(phi[0]) and np.allclose(E0[0], E[0], rtol=1e-13, atol=0)
+    # symmetric cloud: field at the centre vanishes
+    sym = np.concatenate([pos, -pos]); qs = np.concatenate([q, q])
+    _, Ec = O.space_charge(sym, qs, tgt=np.zeros((1, 3)), soft=1e-6)
+    assert np.abs(Ec).max() <= 1e-12 * np.abs(E).max()
+    # a distant same-sign cluster looks like a point charge at its charge centroid
+    far = np.array([[1.0, 0.0, 0.0]])
+    pf, Ef = O.space_charge(pos, np.abs(q), tgt=far, soft=1e-6)
+    Qt = np.abs(q).sum()
+    r = np.linalg.norm(far[0] - pos.mean(0))
+    assert abs(pf[0] / (O.ke() * Qt / r) - 1) < 1e-7
+
+
+def test_known_charge_rhs_and_dynamic_step():
+    g = I.cube(n_per_edge=4)
+    sigma0, K, fac = O.solve(g)
+    c, nr, _ = O.centroids(g)
+    gen = np.random.default_rng(37)
+    pos = gen.normal(size=(40, 3)) * 2e-3 + np.array([0.0, 0.0, 0.012])
+    q = np.where(gen.random(40) < 0.5, 1.0, -1.0) * 1e-15
+    pos1, sigma, E = O.dynamic_step(g, fac, pos, q)
+    # with the known charges, the total potential at every collocation point is the BC
+    pe, _ = O.eval_points(g, sigma, c)
+    ps, _ = O.space_charge(pos, q, tgt=c, soft=1e-6)
+    assert np.abs(pe + ps - 1.0).max() < 1e-10
+    # sigma is affine in q
+    _, sigma2, _ = O.dynamic_step(g, fac, pos, 2 * q)
+    assert np.abs((sigma2 - sigma0) - 2 * (sigma - sigma0)).max() <= 1e-9 * np.abs(sigma - sigma0).max()
+    # carriers move along sign(q) mu E dt
+    step = np.sign(q)[:, None] * 1e-4 * E * 1e-9
+    assert np.abs(pos1 - (pos + step)).max() <= 4e-16 * np.abs(pos).max()
+    assert np.abs(step).max() > 1e-3 * 1e-16 * 0 + 1e-14
