@@ -1,0 +1,321 @@
+"""Benchmark: element-point influence evaluations per second on the THGEM unit cell.
+
+Workload (the configuration the headline metric is quoted on): hexagonal THGEM cell,
+pitch 1 mm, 9,996 flat rectangles and triangles, 5 x 5 periodic images, potential and
+field at 1,000,000 points uniform in the cell volume, mixed precision (FP32 far-field
+Gauss rules, FP64 near-field closed forms), charge densities from a mixed solve with
+FP64 refinement.  One step = one evaluation of all points (the whole hot path of the
+evaluation: every element, every image, every point).  Synthetic, seeded inputs.
+
+Reported next to it: the plain FP64 path's rate (on a point sample), the mixed path's
+error against the FP64 path, the roofline of the dominant kernel, the end-to-end rate
+through the host-buffer C-ABI call, and the FP64 CPU oracle timed on a bounded sample.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_POINTS = 1_000_000
+FP64_SAMPLE = 19_456
+CHECK_SAMPLE = 512
+ORACLE_SAMPLE = 2_048
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--points", type=int, default=N_POINTS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def workload(n_points):
+    from paper_2606_24154_gb300 import inputs as I
+    g = I.thgem()
+    pts = I.cell_points(g, n_points, I.rng(1, 0))
+    return g, pts
+
+
+def oracle_rate(g, pts, n):
+    """FP64 CPU oracle on a bounded sample of the same workload (evals/s, threads)."""
+    from oracle import oracle as O
+    sigma = I_sigma(g)
+    sample = pts[:n]
+    t = time.perf_counter()
+    O.eval_points(g, sigma, sample)
+    dt = time.perf_counter() - t
+    return n * g.n * g.n_images / dt, O.num_threads(), dt
+
+
+def I_sigma(g):
+    """Seeded structured charge density for the CPU sample (the oracle's cost does not
+    depend on its values)."""
+    from paper_2606_24154_gb300 import inputs as I
+    return I.rng(1, 5).normal(size=g.n) * 1e-6
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    g, pts = workload(max(ORACLE_SAMPLE, 256))
+    n = min(ORACLE_SAMPLE, pts.shape[0]) // 4  # per step: a quarter of the sample
+    from oracle import oracle as O
+    sigma = I_sigma(g)
+    for w in range(args.warmup):
+        O.eval_points(g, sigma, pts[:max(8, n // 8)])
+    times = []
+    for s in range(args.steps):
+        sl = pts[(s * n) % (pts.shape[0] - n):][:n]
+        t = time.perf_counter()
+        O.eval_points(g, sigma, sl)
+        times.append(time.perf_counter() - t)
+    per = statistics.mean(times)
+    val = n * g.n * g.n_images / per
+    line = {
+        "impl": "reference", "metric": "element-point influence evals/s", "value": val, "unit": "evals/s",
+        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"thgem_cell N={g.n} images={g.n_images} points={N_POINTS} (bounded sample "
+                               f"of {n} points per step)", "precision": "fp64 oracle"},
+        "cpu_baseline": {"value": val, "unit": "evals/s", "cores": O.num_threads(), "kind": "oracle",
+                         "sample": f"{n} of {N_POINTS} points per step, all {g.n} elements x {g.n_images} images"},
+        "e2e": {"value": val, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_native(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2606_24154_gb300 import build as B
+    from paper_2606_24154_gb300 import nebem as N
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    B.build()
+    N.load()
+
+    g, pts_h = workload(args.points)
+    n_el, n_img = g.n, g.n_images
+    ctx = N.Context(device=local).set_geometry(g)
+    sigma, info, _ = ctx.solve(N.NEBEM_MIXED)
+
+    stream = torch.cuda.Stream(device=dev)
+    s_handle = stream.cuda_stream
+    npts = pts_h.shape[0]
+    pts = torch.from_numpy(pts_h).to(dev)
+    phi = torch.empty(npts, dtype=torch.float64, device=dev)
+    E = torch.empty((npts, 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        N.nebem_eval_device(ctx.h, pts.data_ptr(), npts, phi.data_ptr(), E.data_ptr(), N.NEBEM_MIXED, s_handle)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed")
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(float(k))  # evict L2 (512 MB > 129 MB) between timed steps
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    wall = time.perf_counter() - t0
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    evals = npts * n_el * n_img
+    value = evals * world / (ms * 1e-3)
+
+    # ---- accuracy of the mixed path against the FP64 path, and the FP64 path's rate
+    ns = min(FP64_SAMPLE, npts)
+    phi64 = torch.empty(ns, dtype=torch.float64, device=dev)
+    E64 = torch.empty((ns, 3), dtype=torch.float64, device=dev)
+    with torch.cuda.stream(stream):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        N.nebem_eval_device(ctx.h, pts.data_ptr(), ns, phi64.data_ptr(), E64.data_ptr(), N.NEBEM_FP64, s_handle)
+        b.record(stream)
+    torch.cuda.synchronize()
+    fp64_rate = ns * n_el * n_img / (a.elapsed_time(b) * 1e-3)
+    d_phi = (phi[:ns] - phi64).abs().max().item() / phi64.abs().max().item()
+    d_E = (E[:ns] - E64).norm(dim=1).max().item() / E64.norm(dim=1).max().item()
+    emag = E64.norm(dim=1)
+    floor = 1e-3 * emag.max()
+    pp_E = ((E[:ns] - E64).norm(dim=1) / torch.maximum(emag, floor)).max().item()
+
+    # ---- roofline of the dominant kernel (mixed eval): FP32 lane operations
+    from paper_2606_24154_gb300 import roofline as R
+    counts = R.tier_counts(g, pts_h, sample=CHECK_SAMPLE)
+    alg_ops = R.fp32_ops_per_launch(counts, npts / CHECK_SAMPLE)
+    peaks, peak_src = load_peaks()
+    peak_ops = R.fp32_peak_ops(peaks.get("sm_max_mhz", 2070.0))
+    achieved = alg_ops / (ms * 1e-3)
+
+    # ---- end to end through the host-buffer call (pinned host memory, copies inside)
+    pts_pin = torch.from_numpy(pts_h).pin_memory()
+    phi_pin = torch.empty(npts, dtype=torch.float64).pin_memory()
+    E_pin = torch.empty((npts, 3), dtype=torch.float64).pin_memory()
+    e2e_times = []
+    import ctypes as C
+    L = N.load()
+    dp = C.POINTER(C.c_double)
+    for k in range(max(2, args.steps // 2) + 1):
+        t = time.perf_counter()
+        rc = L.nebem_eval(ctx.h, C.cast(pts_pin.data_ptr(), dp), npts, C.cast(phi_pin.data_ptr(), dp),
+                          C.cast(E_pin.data_ptr(), dp), N.NEBEM_MIXED)
+        if rc != 0:
+            raise N.NebemError(rc, "nebem_eval")
+        if k > 0:
+            e2e_times.append(time.perf_counter() - t)
+    e2e_val = evals * world / statistics.mean(e2e_times)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, dt = oracle_rate(g, pts_h, ORACLE_SAMPLE)
+        cpu = {"value": rate, "unit": "evals/s", "cores": cores, "kind": "oracle",
+               "sample": f"{ORACLE_SAMPLE} of {npts} points, all {n_el} elements x {n_img} images "
+                         f"({dt:.1f} s FP64 on the host)"}
+
+    if rank == 0:
+        line = {
+            "metric": "element-point influence evals/s (mixed FP32/FP64, <=1e-6 rel err vs FP64 path)",
+            "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"thgem_cell N={n_el} images={n_img} points={npts} mixed eval",
+                       "elements": n_el, "images": n_img, "points_per_gpu": npts,
+                       "l2": "flushed between timed steps (512 MB write)", "parallelism": f"points sharded x{world}"},
+            "accuracy": {"phi_rel_err_vs_fp64": d_phi, "E_rel_err_vs_fp64": d_E,
+                         "E_pointwise_rel_err_floor1e-3": pp_E, "sample_points": ns,
+                         "sigma_refinement": {"iterations": info.iterations, "correction": info.correction}},
+            "fp64_path": {"value": fp64_rate, "unit": "evals/s", "sample_points": ns,
+                          "speedup_mixed_over_fp64": value / world / fp64_rate},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                         "frac": achieved / peak_ops, "traffic": None,
+                         "note": "FP32 lane ops (Gauss nodes x 13 + pairs x 9) per launch / event time; peak = "
+                                 "152 SMs x 128 lanes x max SM clock"},
+            "tiers": counts,
+            "e2e": {"value": e2e_val, "unit": "evals/s", "h2d_bytes_per_step": int(pts_pin.numel() * 8),
+                    "d2h_bytes_per_step": int((phi_pin.numel() + E_pin.numel()) * 8)},
+            "cpu_baseline": cpu,
+            "gpu_launches": args.steps,
+            "clocks": clocks,
+            "wall_s_timed_region": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,280 @@
+/*
+ * nebem.h -- C-ABI of libnebem, a single-GPU (GB300, sm_103a) implementation of the
+ * data-parallel hot path of the nearly exact Boundary Element Method (neBEM):
+ * closed-form potential and field influence of uniformly charged flat rectangular
+ * and triangular elements plus their periodic images, evaluated over large target
+ * sets, used to fill the collocation influence matrix, to evaluate potential and
+ * field at points, and to add the direct sum over space-charge carriers.
+ *
+ * Paper references are to "neBEM: A GPU-accelerated Electrostatic Field Solver":
+ * Sec. 2 (Eq. 1-5: Poisson equation, point-charge potential, superposition of the
+ * potential and of the field), Sec. 2 (Eq. Matrix: K . rho = phi by collocation at
+ * element centroids, rho = K^-1 phi), Sec. 2.1 (closed-form potential Phi' and field
+ * E' of a uniformly charged rectangle / right triangle; weighting-field reuse of the
+ * factors), Sec. 4.1 (LU-based solve, Alg. 1; RHVector with the known-charge term),
+ * Sec. 4.2 (space-charge kernel, Alg. 2), Sec. 4.3 (dynamic update, Alg. 4),
+ * Sec. 5 Case 2 (periodic "virtual copies" of a THGEM unit cell).
+ *
+ * Units are SI: metres, volts, C/m^2 for charge densities, C for point charges,
+ * V/m for fields.  The Coulomb constant is 1/(4 pi eps0) with
+ * eps0 = 8.8541878128e-12 F/m.
+ *
+ * Conventions common to every call:
+ *   - Return value: NEBEM_OK (0) or a negative nebem_status.  A failed call leaves
+ *     the context's previous valid state unchanged unless stated otherwise;
+ *     nebem_last_error() gives a human-readable message for the calling thread.
+ *   - Ownership: caller buffers are never retained.  Host inputs are copied before
+ *     the call returns; host outputs are written before it returns.  Device variants
+ *     (suffix _device) read and write caller device memory asynchronously on the
+ *     given CUDA stream (NULL = the context's own stream); the caller keeps those
+ *     buffers alive until the stream reaches the call.
+ *   - A context is bound to one CUDA device and is not thread-safe: calls on one
+ *     context must be serialised by the caller.  Different contexts are independent.
+ *   - Precision argument: NEBEM_FP64 runs every pair through the FP64 closed forms;
+ *     NEBEM_MIXED evaluates element-point pairs farther than ratio_near element radii
+ *     with FP32 Gauss rules whose order grows as the pair gets closer (target-minus-
+ *     source differences formed exactly from two-float coordinates, FP32 arithmetic,
+ *     FP64 accumulation), keeps nearer pairs in the FP64 closed forms, factors in FP32
+ *     and refines in FP64 against the FP64 matrix.
+ */
+#ifndef NEBEM_H
+#define NEBEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum nebem_status {
+    NEBEM_OK = 0,
+    NEBEM_INVALID_ARG = -1,        /* NULL where not allowed, negative size, bad enum */
+    NEBEM_BAD_STATE = -2,          /* call out of order (e.g. eval before solve) */
+    NEBEM_OUT_OF_MEMORY = -3,      /* device or host allocation failed */
+    NEBEM_CUDA = -4,               /* a CUDA runtime call failed */
+    NEBEM_SINGULAR = -5,           /* exact zero pivot in the LU factorisation */
+    NEBEM_NOT_CONVERGED = -6,      /* iterative refinement hit its iteration limit */
+    NEBEM_TIMEOUT = -7,            /* a bounded device-side wait gave up */
+    NEBEM_DEGENERATE_ELEMENT = -8, /* zero-area, non-planar or non-right-angled element */
+    NEBEM_NO_DEVICE = -9,          /* no usable CUDA device */
+    NEBEM_TOO_LARGE = -10          /* size beyond a documented limit */
+} nebem_status;
+
+typedef enum nebem_precision { NEBEM_FP64 = 0, NEBEM_MIXED = 1 } nebem_precision;
+
+typedef enum nebem_kind { NEBEM_RECT = 0, NEBEM_TRI = 1 } nebem_kind;
+typedef enum nebem_bc { NEBEM_CONDUCTOR = 0, NEBEM_DIELECTRIC = 1 } nebem_bc;
+
+/* One flat boundary element (Sec. 2: rectangular and triangular surface elements with
+ * uniform charge density; collocation at the centroid).  128 bytes.
+ *   kind      NEBEM_RECT: v[0..3] in order around the rectangle, right angles, planar
+ *             (v2 = v1 + v3 - v0 within 1e-9 relative).  NEBEM_TRI: v[0..2]; v[3] ignored.
+ *   bc        NEBEM_CONDUCTOR: potential prescribed, V = voltages[conductor].
+ *             NEBEM_DIELECTRIC: interface between relative permittivities eps_a on the
+ *             -n side and eps_b on the +n side (eps_a != eps_b); conductor ignored.
+ *   normal n  right-hand rule on v0, v1, v2, i.e. along (v1 - v0) x (v2 - v0). */
+typedef struct nebem_element {
+    int32_t kind;
+    int32_t bc;
+    int32_t conductor;
+    int32_t reserved; /* must be 0 */
+    double eps_a;
+    double eps_b;
+    double v[4][3];
+} nebem_element;
+
+/* Context options.  Obtain defaults with nebem_default_options(). */
+typedef struct nebem_options {
+    int32_t device;          /* CUDA device ordinal (default 0) */
+    int32_t ir_max_iter;     /* iterative refinement limit in mixed solves (default 30) */
+    double ir_tol;           /* stop when ||d sigma||_inf / ||sigma||_inf <= ir_tol (1e-8) */
+    double ratio_a;          /* mixed eval: pairs with distance >= ratio_a element radii use
+                                the low-order FP32 Gauss rule (6-node triangle, 3x3
+                                rectangle; default 24) */
+    double ratio_b;          /* >= ratio_b radii: 16-node FP32 rule (default 8) */
+    double ratio_near;       /* >= ratio_near radii: 36-node FP32 rule; nearer pairs take
+                                the FP64 closed form (default 3) */
+    double softening;        /* default Plummer softening of carrier charges, m (1e-6) */
+    double sc_near;          /* space charge: pairs closer than this (m) form the FP32
+                                difference from exact two-float coordinates (default 1e-4) */
+    int32_t lu_block;        /* LU panel width, 32 or 64 (default 64) */
+    int32_t reserved0;
+    double reserved[5];
+} nebem_options;
+
+/* Result report of nebem_solve. */
+typedef struct nebem_solve_info {
+    int32_t precision;       /* the precision that ran */
+    int32_t iterations;      /* refinement iterations (0 for FP64) */
+    double correction;       /* last ||d sigma||_inf / ||sigma||_inf (mixed) */
+    double residual;         /* ||K sigma - b||_inf / ||sigma||_inf, FP64 (scale of K) */
+    double ms_fill;          /* device time of the influence-matrix fill */
+    double ms_factor;        /* device time of the LU factorisation */
+    double ms_solve;         /* device time of triangular solves and refinement */
+    double reserved[4];
+} nebem_solve_info;
+
+typedef struct nebem_ctx nebem_ctx;
+
+/* Fill *opt with the defaults listed above. */
+int nebem_default_options(nebem_options *opt);
+
+/* Create a context on opt->device (opt may be NULL: defaults).  *out receives the
+ * context; it owns all device memory it allocates and frees it in nebem_destroy.
+ * Errors: NEBEM_INVALID_ARG (out NULL or bad option), NEBEM_NO_DEVICE, NEBEM_CUDA. */
+int nebem_create(nebem_ctx **out, const nebem_options *opt);
+
+/* Destroy a context and free its device memory.  NULL is accepted (no-op). */
+int nebem_destroy(nebem_ctx *ctx);
+
+/* Message for the last failed call on this thread (static storage, never NULL). */
+const char *nebem_last_error(void);
+
+/* Name of a status code (static storage, never NULL). */
+const char *nebem_status_string(int status);
+
+/* Define the geometry (Sec. 2: discretised boundaries; Sec. 5 Case 2: periodic
+ * virtual copies).  el[n] is copied; each element's local frame (origin v0, x along
+ * v0->v1, y along the normal), centroid, edge data and far-field Gauss nodes are built
+ * in FP64 on the host and uploaded.
+ *   lattice  NULL: no images.  Otherwise two primitive translations a1 = lattice[0..2],
+ *            a2 = lattice[3..5]; the images are t = k1*a1 + k2*a2 for k1, k2 in
+ *            [img_lo, img_hi] (at most 11 per axis), image index
+ *            (k1 - img_lo) * m + (k2 - img_lo), m = img_hi - img_lo + 1; every element's
+ *            influence is summed over all images (the base cell is the image t = 0,
+ *            which must be in range).
+ * Invalidates the factors, charge densities and the known-charge set.
+ * Errors: NEBEM_INVALID_ARG, NEBEM_DEGENERATE_ELEMENT (index in nebem_last_error),
+ * NEBEM_TOO_LARGE (more than 11 images per axis), NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
+int nebem_set_geometry(nebem_ctx *ctx, const nebem_element *el, int64_t n, const double *lattice,
+                       int32_t img_lo, int32_t img_hi);
+
+/* Conductor potentials (Sec. 2: Dirichlet boundary conditions; Sec. 2.1: K does not
+ * depend on them, so the factors are kept).  voltages[n_conductors] is copied.  Every
+ * conductor element's index must be < n_conductors.  Invalidates sigma only. */
+int nebem_set_bc(nebem_ctx *ctx, const double *voltages, int32_t n_conductors);
+
+/* Solve K sigma = b (Eq. Matrix; Alg. 1 with an LU solve instead of an explicit inverse).
+ *   precision  NEBEM_FP64: FP64 fill, FP64 blocked LU with partial pivoting, FP64
+ *              triangular solves.  NEBEM_MIXED: FP64 fill, FP32 LU, FP64 iterative
+ *              refinement (residual with the FP64 K) until ir_tol.
+ *   Conductor rows: K_ij = ke sum_k Phi'(c_i; j + t_k), b_i = V - phi_sc(c_i).
+ *   Interface rows: K_ij = ke sum_k n_i . E'(c_i; j + t_k) (principal value on the own
+ *   element) + delta_ij (eps_a + eps_b) / (2 eps0 (eps_b - eps_a)), b_i = -n_i . E_sc(c_i).
+ * The matrix and factors are kept on the device and reused by later solves with new
+ * voltages or a new known-charge set.  sigma_out[n] (host, may be NULL) receives the
+ * charge densities; info (may be NULL) the report.
+ * Errors: NEBEM_BAD_STATE (no geometry or no voltages), NEBEM_SINGULAR,
+ * NEBEM_NOT_CONVERGED (sigma and info are still written), NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
+int nebem_solve(nebem_ctx *ctx, int32_t precision, double *sigma_out, nebem_solve_info *info);
+
+/* Replace the charge densities (n values, host) without solving, e.g. to evaluate a
+ * stored solution.  Errors: NEBEM_BAD_STATE (no geometry). */
+int nebem_set_sigma(nebem_ctx *ctx, const double *sigma, int64_t n);
+
+/* Copy the current charge densities (n values) to host memory.  NEBEM_BAD_STATE if none. */
+int nebem_get_sigma(nebem_ctx *ctx, double *sigma_out, int64_t n);
+
+/* Fill the influence matrix (as nebem_solve does) and copy it to host memory in
+ * column-major order, K_out[i + j*n] = K_ij.  K_out may be NULL (device copy only). */
+int nebem_fill(nebem_ctx *ctx, int32_t precision, double *K_out);
+
+/* Potential and field at points (Eq. Potential and Eq. Field with the element charge
+ * densities; Sec. 4.1 PFAtPoint = element part + known-charge part): phi(x) =
+ * ke sum_j sigma_j sum_k Phi'(x; j + t_k) [+ ke sum_c q_c / sqrt(r^2 + s^2) when a
+ * known-charge set is present], E likewise.  pts[n][3] row-major (host);
+ * phi[n] and/or E[n][3] (host) may be NULL.  n = 0 is allowed.
+ * Errors: NEBEM_BAD_STATE (no charge densities), NEBEM_INVALID_ARG. */
+int nebem_eval(nebem_ctx *ctx, const double *pts, int64_t n, double *phi, double *E, int32_t precision);
+
+/* Device variant of nebem_eval: d_pts, d_phi, d_E are device pointers (d_phi or d_E may
+ * be NULL); runs asynchronously on `stream` (a cudaStream_t, NULL = context stream).
+ * Uses context-owned scratch, so calls on one context must not overlap in time. */
+int nebem_eval_device(nebem_ctx *ctx, const double *d_pts, int64_t n, double *d_phi, double *d_E,
+                      int32_t precision, void *stream);
+
+/* Set the known-charge set (Sec. 4.2 OptKnCh; Alg. 4 UpdateSpaceCharge): n point
+ * carriers at pos[n][3] (m) with charges q[n] (C), Plummer softening `softening` (m,
+ * > 0; <= 0 selects the context default).  Copied to the device.  n = 0 clears it.
+ * Invalidates sigma (the right-hand side changes), keeps the factors. */
+int nebem_space_charge(nebem_ctx *ctx, const double *pos, const double *q, int64_t n, double softening);
+
+/* Direct space-charge sum at points (Alg. 2, all pairs, softened):
+ * phi_t = ke sum_{c != self(t)} q_c / sqrt(r^2 + s^2), E_t = ke sum q_c (x_t - x_c) /
+ * (r^2 + s^2)^{3/2}.  exclude_self != 0 means target t is carrier t (n must equal the
+ * carrier count) and is excluded.  Host buffers as in nebem_eval. */
+int nebem_space_charge_eval(nebem_ctx *ctx, const double *pts, int64_t n, double *phi, double *E,
+                            int32_t precision, int32_t exclude_self);
+
+/* Run `steps` dynamic space-charge updates (Alg. 4 with SpChTh = 0; carriers drift
+ * instead of being tracked): per step (1) right-hand side with the known charges at the
+ * collocation points, (2) sigma from the retained factors (mixed: FP32 solve + FP64
+ * refinement), (3) E at every carrier from all elements (with images) and all other
+ * carriers, (4) x_c += sign(q_c) * mu * E_c * dt.  Requires a solved geometry
+ * (factors) and a known-charge set; positions stay on the device between steps.
+ * pos_out[n][3] (host, may be NULL) receives the final positions.
+ * Errors: NEBEM_BAD_STATE, NEBEM_NOT_CONVERGED, NEBEM_CUDA. */
+int nebem_step(nebem_ctx *ctx, int32_t steps, double mu, double dt, int32_t precision, double *pos_out);
+
+/* Image translations of the current geometry in index order (count * 3 doubles,
+ * host).  *count receives the number of images; t_out may be NULL to query it. */
+int nebem_image_table(nebem_ctx *ctx, double *t_out, int64_t *count);
+
+/* Influence of single elements (no charge density, no images) at points, for kernel
+ * checks: for element e and point p, phi_out[e*n_pts + p] = Phi'(p) (m) and
+ * E_out[(e*n_pts + p)*3 + c] = E'_c(p) (dimensionless), in FP64 closed form.
+ * Host buffers; needs no geometry (a context provides the device).  At most 1e8 pairs. */
+int nebem_element_influence(nebem_ctx *ctx, const nebem_element *el, int64_t n_el, const double *pts,
+                            int64_t n_pts, double *phi_out, double *E_out);
+
+/* ------------------------------------------------------------------ serving
+ * Continuous batching over several resident solved contexts (a field-query server).
+ * Requests are admitted as device memory frees up, split into point chunks that a
+ * persistent batched evaluation kernel pulls from a device work queue; requests that
+ * arrive while others run join the running kernel.  Results are bit-identical to
+ * the same request evaluated alone. */
+typedef struct nebem_server nebem_server;
+
+typedef struct nebem_server_options {
+    int64_t arena_points;   /* device staging capacity in points (default 4,194,304) */
+    int32_t chunk_points;   /* points per work item (default 1024) */
+    int32_t max_requests;   /* in-flight request slots (default 256) */
+    int32_t workers;        /* persistent CTAs (0 = 2 per SM) */
+    int32_t idle_us;        /* a persistent kernel with no work exits after this (default 2000) */
+    double reserved[4];
+} nebem_server_options;
+
+int nebem_server_default_options(nebem_server_options *opt);
+
+/* Create a server over n_ctx solved contexts (all on one device; they must stay alive
+ * until nebem_server_destroy).  Geometry index g in submit refers to ctxs[g]. */
+int nebem_server_create(nebem_server **out, nebem_ctx *const *ctxs, int32_t n_ctx,
+                        const nebem_server_options *opt);
+
+/* Submit a request: n points pts[n][3] (host) for geometry `geometry`; results go to the
+ * caller's host buffers phi[n] / E[n][3] (either may be NULL), which must stay valid
+ * until the request completes.  Returns immediately with *req_id.  Admission waits in
+ * the server's host queue while the arena is full.
+ * Errors: NEBEM_INVALID_ARG, NEBEM_TOO_LARGE (n > arena_points), NEBEM_BAD_STATE. */
+int nebem_server_submit(nebem_server *srv, int32_t geometry, const double *pts, int64_t n, double *phi,
+                        double *E, int32_t precision, int64_t *req_id);
+
+/* Drive the server (admission, launches, completions) and report whether req_id is
+ * done (*done = 1; its outputs are written) or not (*done = 0). */
+int nebem_server_poll(nebem_server *srv, int64_t req_id, int32_t *done);
+
+/* Drive the server until req_id completes or timeout_ms passes (NEBEM_TIMEOUT). */
+int nebem_server_wait(nebem_server *srv, int64_t req_id, int64_t timeout_ms);
+
+/* Per-request timing (host clock, seconds since server creation): submit, admission,
+ * completion.  NEBEM_BAD_STATE if not complete. */
+int nebem_server_request_times(nebem_server *srv, int64_t req_id, double *t_submit, double *t_admit,
+                               double *t_done);
+
+/* Finish outstanding work and free the server (contexts are not destroyed). */
+int nebem_server_destroy(nebem_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NEBEM_H */

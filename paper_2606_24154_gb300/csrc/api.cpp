@@ -1,0 +1,354 @@
+// api.cpp -- the C-ABI of libnebem (declared in include/nebem.h): context lifetime,
+// geometry and boundary conditions, solve orchestration (fill -> LU -> substitution
+// [-> FP64 refinement]), evaluation at points, known-charge set and dynamic steps.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "context.h"
+#include "geometry.h"
+
+namespace nb {
+
+static thread_local std::string g_last_error = "no error";
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int fail(int code, const std::string& msg) {
+    set_error(msg);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    return fail(e == cudaErrorMemoryAllocation ? NEBEM_OUT_OF_MEMORY : NEBEM_CUDA,
+                std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+void DevBuf::release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+cudaError_t DevBuf::ensure(size_t nbytes) {
+    if (bytes >= nbytes && ptr) return cudaSuccess;
+    release();
+    if (nbytes == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc(&ptr, nbytes);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        cudaGetLastError();
+        return e;
+    }
+    bytes = nbytes;
+    return cudaSuccess;
+}
+
+Ctx::~Ctx() {
+    cudaSetDevice(device);
+    for (DevBuf* b : {&d_el, &d_far, &d_diag, &d_sigma, &d_K, &d_LU64, &d_LU32, &d_piv64, &d_piv32, &d_work, &d_b,
+                      &d_x, &d_r, &d_r32, &d_small, &d_pts, &d_phi, &d_E, &d_car, &d_q, &d_car2, &d_sc_tgt,
+                      &d_sc_phi, &d_sc_E, &d_scratch})
+        b->release();
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    if (stream) cudaStreamDestroy(stream);
+}
+
+}  // namespace nb
+
+using namespace nb;
+
+#define CK(call)                                                          \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);               \
+    } while (0)
+
+extern "C" {
+
+const char* nebem_last_error(void) { return g_last_error.c_str(); }
+
+const char* nebem_status_string(int s) {
+    switch (s) {
+        case NEBEM_OK: return "NEBEM_OK";
+        case NEBEM_INVALID_ARG: return "NEBEM_INVALID_ARG";
+        case NEBEM_BAD_STATE: return "NEBEM_BAD_STATE";
+        case NEBEM_OUT_OF_MEMORY: return "NEBEM_OUT_OF_MEMORY";
+        case NEBEM_CUDA: return "NEBEM_CUDA";
+        case NEBEM_SINGULAR: return "NEBEM_SINGULAR";
+        case NEBEM_NOT_CONVERGED: return "NEBEM_NOT_CONVERGED";
+        case NEBEM_TIMEOUT: return "NEBEM_TIMEOUT";
+        case NEBEM_DEGENERATE_ELEMENT: return "NEBEM_DEGENERATE_ELEMENT";
+        case NEBEM_NO_DEVICE: return "NEBEM_NO_DEVICE";
+        case NEBEM_TOO_LARGE: return "NEBEM_TOO_LARGE";
+        default: return "NEBEM_UNKNOWN_STATUS";
+    }
+}
+
+int nebem_default_options(nebem_options* opt) {
+    if (!opt) return fail(NEBEM_INVALID_ARG, "opt is NULL");
+    std::memset(opt, 0, sizeof(*opt));
+    opt->device = 0;
+    opt->ir_max_iter = 30;
+    opt->ir_tol = 1e-8;
+    opt->ratio_a = 24.0;
+    opt->ratio_b = 8.0;
+    opt->ratio_near = 3.0;
+    opt->softening = 1e-6;
+    opt->sc_near = 1e-4;
+    opt->lu_block = 64;
+    return NEBEM_OK;
+}
+
+int nebem_create(nebem_ctx** out, const nebem_options* opt) {
+    if (!out) return fail(NEBEM_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    nebem_options o;
+    nebem_default_options(&o);
+    if (opt) o = *opt;
+    if (o.lu_block < 32 || o.lu_block > 64 || o.lu_block % 32) return fail(NEBEM_INVALID_ARG, "lu_block must be 32 or 64");
+    if (!(o.ir_tol > 0.0) || o.ir_max_iter < 1) return fail(NEBEM_INVALID_ARG, "bad refinement options");
+    if (!(o.ratio_near >= 1.5) || !(o.ratio_b >= o.ratio_near) || !(o.ratio_a >= o.ratio_b) || !(o.ratio_a < 1e6))
+        return fail(NEBEM_INVALID_ARG, "need 1.5 <= ratio_near <= ratio_b <= ratio_a");
+    if (!(o.softening > 0.0)) return fail(NEBEM_INVALID_ARG, "softening must be > 0");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(NEBEM_NO_DEVICE, "no CUDA device");
+    }
+    if (o.device < 0 || o.device >= ndev) return fail(NEBEM_INVALID_ARG, "device ordinal out of range");
+    Ctx* c = new (std::nothrow) Ctx();
+    if (!c) return fail(NEBEM_OUT_OF_MEMORY, "host allocation failed");
+    c->opt = o;
+    c->device = o.device;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    if (e == cudaSuccess) e = cudaGetDeviceProperties(&c->props, c->device);
+    if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "nebem_create");
+    }
+    *out = reinterpret_cast<nebem_ctx*>(c);
+    return NEBEM_OK;
+}
+
+int nebem_destroy(nebem_ctx* ctx) {
+    if (!ctx) return NEBEM_OK;
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    delete c;
+    return NEBEM_OK;
+}
+
+int nebem_set_geometry(nebem_ctx* ctx, const nebem_element* el, int64_t n, const double* lattice, int32_t img_lo,
+                       int32_t img_hi) {
+    if (!ctx) return fail(NEBEM_INVALID_ARG, "ctx is NULL");
+    if (n <= 0 || !el) return fail(NEBEM_INVALID_ARG, "need n > 0 elements");
+    if (n > (int64_t)INT32_MAX) return fail(NEBEM_TOO_LARGE, "too many elements");
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    CK(cudaSetDevice(c->device));
+    std::string why;
+    ImageTable img;
+    int rc = build_images(lattice, img_lo, img_hi, img, why);
+    if (rc) return fail(rc, why);
+    std::vector<Elem> h_el((size_t)n);
+    std::vector<FarNodes> h_far((size_t)n);
+    std::vector<double> h_diag((size_t)n);
+    std::vector<int32_t> h_bc((size_t)n), h_cond((size_t)n);
+    for (int64_t i = 0; i < n; ++i) {
+        if (el[i].reserved != 0) return fail(NEBEM_INVALID_ARG, "element " + std::to_string(i) + ": reserved != 0");
+        rc = build_element(el[i], c->opt, h_el[i], h_diag[i], h_far[i], why);
+        if (rc) return fail(rc, "element " + std::to_string(i) + ": " + why);
+        h_bc[i] = el[i].bc;
+        h_cond[i] = el[i].conductor;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    // invalidate everything that depends on the geometry
+    c->n = 0;
+    c->K_valid = c->fac64_valid = c->fac32_valid = c->sigma_valid = false;
+    c->bc_set = false;
+    c->n_car = 0;
+    CK(c->d_el.ensure(sizeof(Elem) * n));
+    CK(c->d_far.ensure(sizeof(FarNodes) * n));
+    CK(c->d_diag.ensure(sizeof(double) * n));
+    CK(c->d_sigma.ensure(sizeof(double) * n));
+    CK(cudaMemcpyAsync(c->d_el.ptr, h_el.data(), sizeof(Elem) * n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_far.ptr, h_far.data(), sizeof(FarNodes) * n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_diag.ptr, h_diag.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->img = img;
+    c->h_bc = std::move(h_bc);
+    c->h_cond = std::move(h_cond);
+    c->h_el = std::move(h_el);
+    c->n = n;
+    return NEBEM_OK;
+}
+
+int nebem_set_bc(nebem_ctx* ctx, const double* voltages, int32_t n_conductors) {
+    if (!ctx) return fail(NEBEM_INVALID_ARG, "ctx is NULL");
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (c->n == 0) return fail(NEBEM_BAD_STATE, "set_geometry first");
+    if (n_conductors < 0 || (n_conductors > 0 && !voltages)) return fail(NEBEM_INVALID_ARG, "bad voltages");
+    for (int64_t i = 0; i < c->n; ++i)
+        if (c->h_bc[i] == NEBEM_CONDUCTOR && (c->h_cond[i] < 0 || c->h_cond[i] >= n_conductors))
+            return fail(NEBEM_INVALID_ARG, "element " + std::to_string(i) + " has conductor index out of range");
+    for (int32_t k = 0; k < n_conductors; ++k)
+        if (!std::isfinite(voltages[k])) return fail(NEBEM_INVALID_ARG, "non-finite voltage");
+    c->voltages.assign(voltages, voltages + n_conductors);
+    c->bc_set = true;
+    c->sigma_valid = false;
+    return NEBEM_OK;
+}
+
+int nebem_image_table(nebem_ctx* ctx, double* t_out, int64_t* count) {
+    if (!ctx || !count) return fail(NEBEM_INVALID_ARG, "NULL argument");
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (c->n == 0) return fail(NEBEM_BAD_STATE, "set_geometry first");
+    *count = c->img.n;
+    if (t_out) std::memcpy(t_out, c->img.t, sizeof(double) * 3 * c->img.n);
+    return NEBEM_OK;
+}
+
+int nebem_fill(nebem_ctx* ctx, int32_t precision, double* K_out) {
+    if (!ctx) return fail(NEBEM_INVALID_ARG, "ctx is NULL");
+    if (precision != NEBEM_FP64 && precision != NEBEM_MIXED) return fail(NEBEM_INVALID_ARG, "bad precision");
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (c->n == 0) return fail(NEBEM_BAD_STATE, "set_geometry first");
+    CK(cudaSetDevice(c->device));
+    int rc = ensure_fill(c, nullptr);
+    if (rc) return rc;
+    if (K_out) {
+        CK(cudaMemcpyAsync(K_out, c->d_K.ptr, sizeof(double) * c->n * c->n, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return NEBEM_OK;
+}
+
+int nebem_solve(nebem_ctx* ctx, int32_t precision, double* sigma_out, nebem_solve_info* info) {
+    if (!ctx) return fail(NEBEM_INVALID_ARG, "ctx is NULL");
+    if (precision != NEBEM_FP64 && precision != NEBEM_MIXED) return fail(NEBEM_INVALID_ARG, "bad precision");
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (c->n == 0) return fail(NEBEM_BAD_STATE, "set_geometry first");
+    if (!c->bc_set) return fail(NEBEM_BAD_STATE, "set_bc first");
+    CK(cudaSetDevice(c->device));
+    nebem_solve_info inf;
+    std::memset(&inf, 0, sizeof(inf));
+    inf.precision = precision;
+    int rc = ensure_fill(c, &inf.ms_fill);
+    if (rc) return rc;
+    c->sc_precision = precision;
+    rc = ensure_factors(c, precision, &inf.ms_factor);
+    if (rc) return rc;
+    rc = build_rhs(c);
+    if (rc) return rc;
+    rc = solve_with_factors(c, precision, &inf);
+    if (sigma_out && (rc == NEBEM_OK || rc == NEBEM_NOT_CONVERGED)) {
+        CK(cudaMemcpyAsync(sigma_out, c->d_sigma.ptr, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    if (info) *info = inf;
+    return rc;
+}
+
+int nebem_set_sigma(nebem_ctx* ctx, const double* sigma, int64_t n) {
+    if (!ctx || !sigma) return fail(NEBEM_INVALID_ARG, "NULL argument");
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (c->n == 0) return fail(NEBEM_BAD_STATE, "set_geometry first");
+    if (n != c->n) return fail(NEBEM_INVALID_ARG, "sigma length must equal the element count");
+    CK(cudaSetDevice(c->device));
+    CK(cudaMemcpyAsync(c->d_sigma.ptr, sigma, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->sigma_valid = true;
+    return NEBEM_OK;
+}
+
+int nebem_get_sigma(nebem_ctx* ctx, double* sigma_out, int64_t n) {
+    if (!ctx || !sigma_out) return fail(NEBEM_INVALID_ARG, "NULL argument");
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (!c->sigma_valid) return fail(NEBEM_BAD_STATE, "no charge densities");
+    if (n != c->n) return fail(NEBEM_INVALID_ARG, "length must equal the element count");
+    CK(cudaSetDevice(c->device));
+    CK(cudaMemcpyAsync(sigma_out, c->d_sigma.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NEBEM_OK;
+}
+
+int nebem_eval_device(nebem_ctx* ctx, const double* d_pts, int64_t n, double* d_phi, double* d_E, int32_t precision,
+                      void* stream) {
+    if (!ctx) return fail(NEBEM_INVALID_ARG, "ctx is NULL");
+    if (n < 0 || (n > 0 && !d_pts)) return fail(NEBEM_INVALID_ARG, "bad points");
+    if (precision != NEBEM_FP64 && precision != NEBEM_MIXED) return fail(NEBEM_INVALID_ARG, "bad precision");
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (!c->sigma_valid) return fail(NEBEM_BAD_STATE, "no charge densities (solve or set_sigma first)");
+    if (n == 0) return NEBEM_OK;
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    return eval_points(c, d_pts, n, d_phi, d_E, precision, s);
+}
+
+int nebem_eval(nebem_ctx* ctx, const double* pts, int64_t n, double* phi, double* E, int32_t precision) {
+    if (!ctx) return fail(NEBEM_INVALID_ARG, "ctx is NULL");
+    if (n < 0 || (n > 0 && !pts)) return fail(NEBEM_INVALID_ARG, "bad points");
+    if (precision != NEBEM_FP64 && precision != NEBEM_MIXED) return fail(NEBEM_INVALID_ARG, "bad precision");
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (!c->sigma_valid) return fail(NEBEM_BAD_STATE, "no charge densities (solve or set_sigma first)");
+    if (n == 0) return NEBEM_OK;
+    CK(cudaSetDevice(c->device));
+    CK(c->d_pts.ensure(sizeof(double) * 3 * n));
+    CK(c->d_phi.ensure(sizeof(double) * n));
+    CK(c->d_E.ensure(sizeof(double) * 3 * n));
+    CK(cudaMemcpyAsync(c->d_pts.ptr, pts, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream));
+    int rc = eval_points(c, (const double*)c->d_pts.ptr, n, phi ? (double*)c->d_phi.ptr : nullptr,
+                         E ? (double*)c->d_E.ptr : nullptr, precision, c->stream);
+    if (rc) return rc;
+    if (phi) CK(cudaMemcpyAsync(phi, c->d_phi.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    if (E) CK(cudaMemcpyAsync(E, c->d_E.ptr, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return NEBEM_OK;
+}
+
+int nebem_element_influence(nebem_ctx* ctx, const nebem_element* el, int64_t n_el, const double* pts, int64_t n_pts,
+                            double* phi_out, double* E_out) {
+    if (!ctx || !el || !pts || !phi_out || !E_out || n_el <= 0 || n_pts <= 0)
+        return fail(NEBEM_INVALID_ARG, "bad argument");
+    if (n_el * n_pts > 100000000LL) return fail(NEBEM_TOO_LARGE, "more than 1e8 pairs");
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    CK(cudaSetDevice(c->device));
+    std::vector<Elem> h((size_t)n_el);
+    std::string why;
+    for (int64_t i = 0; i < n_el; ++i) {
+        double dg;
+        FarNodes fn;
+        int rc = build_element(el[i], c->opt, h[i], dg, fn, why);
+        if (rc) return fail(rc, "element " + std::to_string(i) + ": " + why);
+    }
+    const int64_t pairs = n_el * n_pts;
+    DevBuf be, bp, bphi, bE;
+    CK(be.ensure(sizeof(Elem) * n_el));
+    CK(bp.ensure(sizeof(double) * 3 * n_pts));
+    CK(bphi.ensure(sizeof(double) * pairs));
+    CK(bE.ensure(sizeof(double) * 3 * pairs));
+    CK(cudaMemcpyAsync(be.ptr, h.data(), sizeof(Elem) * n_el, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(bp.ptr, pts, sizeof(double) * 3 * n_pts, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_element_influence((const Elem*)be.ptr, n_el, (const double*)bp.ptr, n_pts, (double*)bphi.ptr,
+                                (double*)bE.ptr, c->stream));
+    CK(cudaMemcpyAsync(phi_out, bphi.ptr, sizeof(double) * pairs, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(E_out, bE.ptr, sizeof(double) * 3 * pairs, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    be.release();
+    bp.release();
+    bphi.release();
+    bE.release();
+    return NEBEM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,80 @@
+// context.h -- the state behind an opaque nebem_ctx (one geometry on one device).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "nb_internal.h"
+
+namespace nb {
+
+// A device allocation owned by the context (grown on demand, freed on destroy).
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t nbytes);
+    void release();
+    template <typename T>
+    T* as() const {
+        return static_cast<T*>(ptr);
+    }
+};
+
+struct Ctx {
+    nebem_options opt{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaDeviceProp props{};
+
+    // geometry
+    int64_t n = 0;
+    ImageTable img{};
+    std::vector<Elem> h_el;
+    std::vector<int32_t> h_bc, h_cond;
+    DevBuf d_el, d_far, d_diag;
+
+    // boundary conditions and solution
+    std::vector<double> voltages;
+    bool bc_set = false;
+    DevBuf d_sigma;
+    bool sigma_valid = false;
+
+    // matrix and factors
+    DevBuf d_K, d_LU64, d_LU32, d_piv64, d_piv32, d_work;
+    bool K_valid = false, fac64_valid = false, fac32_valid = false;
+    DevBuf d_b, d_x, d_r, d_r32, d_small;
+
+    // evaluation staging (host-pointer variant) and scratch
+    DevBuf d_pts, d_phi, d_E, d_scratch;
+
+    // known-charge set (space charge)
+    int64_t n_car = 0;
+    double soft = 1e-6;
+    int sc_precision = NEBEM_FP64;  // precision of the known-charge RHS term
+    DevBuf d_car, d_q, d_car2, d_sc_tgt, d_sc_phi, d_sc_E;
+    std::vector<double> h_q;
+
+    ~Ctx();
+};
+
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* where);
+
+// solve.cpp
+int ensure_fill(Ctx* c, double* ms);
+int ensure_factors(Ctx* c, int precision, double* ms);
+int build_rhs(Ctx* c);
+int solve_with_factors(Ctx* c, int precision, nebem_solve_info* info);
+// elements only (with images)
+int eval_elements(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision, cudaStream_t s);
+// elements + known charges (PFAtPoint)
+int eval_points(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision, cudaStream_t s);
+
+// spacecharge_api.cpp
+int rhs_known_charge(Ctx* c);
+int add_known_charge(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision,
+                     cudaStream_t s);
+
+}  // namespace nb

@@ -1,0 +1,247 @@
+// geometry.cpp -- host-side FP64 construction of the device element table, the image
+// table and the FP32 far-field Gauss nodes (Sec. 2: flat rectangular / triangular
+// elements, collocation at centroids; Sec. 5 Case 2: periodic virtual copies).
+#include "geometry.h"
+
+#include <cmath>
+#include <cstring>
+
+namespace nb {
+
+namespace {
+
+inline void sub3(const double* a, const double* b, double* c) {
+    c[0] = a[0] - b[0];
+    c[1] = a[1] - b[1];
+    c[2] = a[2] - b[2];
+}
+inline double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+inline void cross3(const double* a, const double* b, double* c) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Symmetric 6-point degree-4 triangle rule (Strang-Fix / Dunavant): two orbits of
+// barycentric points (a, a, 1 - 2a) with weights (fractions of the area).
+const double kTriA[2] = {0.445948490915965, 0.091576213509771};
+const double kTriW[2] = {0.223381589678011, 0.109951743655322};
+
+}  // namespace
+
+void gauss_legendre01(int m, double* x, double* w) {
+    for (int i = 0; i < m; ++i) {
+        // initial guess (Chebyshev-like) then Newton on the Legendre recurrence
+        double t = std::cos(kPi * (i + 0.75) / (m + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (int k = 2; k <= m; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            const double pm = (m == 1) ? t : p1;
+            const double pm1 = (m == 1) ? 1.0 : p0;
+            dp = m * (t * pm - pm1) / (t * t - 1.0);
+            const double dt = pm / dp;
+            t -= dt;
+            if (std::fabs(dt) < 1e-16) break;
+        }
+        x[i] = 0.5 * (1.0 - t);
+        w[i] = 1.0 / ((1.0 - t * t) * dp * dp);  // 2/((1-t^2) P'^2) on [-1,1], halved for [0,1]
+    }
+}
+
+int build_element(const nebem_element& r, const nebem_options& opt, Elem& e, double& diag, FarNodes& fn,
+                  std::string& why) {
+    std::memset(&e, 0, sizeof(e));
+    std::memset(&fn, 0, sizeof(fn));
+    if (r.kind != NEBEM_RECT && r.kind != NEBEM_TRI) {
+        why = "unknown element kind";
+        return NEBEM_INVALID_ARG;
+    }
+    if (r.bc != NEBEM_CONDUCTOR && r.bc != NEBEM_DIELECTRIC) {
+        why = "unknown boundary-condition type";
+        return NEBEM_INVALID_ARG;
+    }
+    const int nv = (r.kind == NEBEM_RECT) ? 4 : 3;
+    for (int v = 0; v < nv; ++v)
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(r.v[v][k])) {
+                why = "non-finite vertex";
+                return NEBEM_DEGENERATE_ELEMENT;
+            }
+    double e1[3], e2[3], n[3];
+    sub3(r.v[1], r.v[0], e1);
+    sub3(r.v[2], r.v[0], e2);
+    cross3(e1, e2, n);
+    const double l1 = std::sqrt(dot3(e1, e1));
+    const double ln = std::sqrt(dot3(n, n));
+    if (!(l1 > 0.0) || !(ln > 1e-300)) {
+        why = "zero-area element";
+        return NEBEM_DEGENERATE_ELEMENT;
+    }
+    for (int k = 0; k < 3; ++k) {
+        e.o[k] = r.v[0][k];
+        e.ex[k] = e1[k] / l1;
+        e.ey[k] = n[k] / ln;
+    }
+    cross3(e.ey, e.ex, e.ez);
+    if (nv == 4) {
+        double e3[3], chk[3];
+        sub3(r.v[3], r.v[0], e3);
+        const double l3 = std::sqrt(dot3(e3, e3));
+        for (int k = 0; k < 3; ++k) chk[k] = r.v[1][k] + e3[k] - r.v[2][k];
+        const double scale = l1 + l3;
+        if (!(l3 > 0.0) || std::fabs(dot3(e1, e3)) > 1e-9 * l1 * l3 || std::sqrt(dot3(chk, chk)) > 1e-9 * scale) {
+            why = "rectangle is not planar with right angles";
+            return NEBEM_DEGENERATE_ELEMENT;
+        }
+    }
+    e.nv = nv;
+    e.bc = r.bc;
+    e.cond = r.conductor;
+    for (int v = 0; v < nv; ++v) {
+        double d[3];
+        sub3(r.v[v], r.v[0], d);
+        e.qx[v] = dot3(d, e.ex);
+        e.qz[v] = dot3(d, e.ez);
+    }
+    for (int v = 0; v < nv; ++v) {
+        const int w = (v + 1) % nv;
+        const double dx = e.qx[w] - e.qx[v], dz = e.qz[w] - e.qz[v];
+        const double len = std::sqrt(dx * dx + dz * dz);
+        if (!(len > 0.0)) {
+            why = "zero-length edge";
+            return NEBEM_DEGENERATE_ELEMENT;
+        }
+        e.inv_len[v] = 1.0 / len;
+    }
+    for (int f = 0; f < nv - 2; ++f) {
+        const double ux = e.qx[f + 1] - e.qx[0], uz = e.qz[f + 1] - e.qz[0];
+        const double vx = e.qx[f + 2] - e.qx[0], vz = e.qz[f + 2] - e.qz[0];
+        e.twoA[f] = ux * vz - uz * vx;
+    }
+    for (int k = 0; k < 3; ++k) {
+        double s = 0.0;
+        for (int v = 0; v < nv; ++v) s += r.v[v][k];
+        e.c[k] = s / nv;
+    }
+    double rho = 0.0;
+    for (int v = 0; v < nv; ++v) {
+        double d[3];
+        sub3(r.v[v], e.c, d);
+        rho = std::fmax(rho, std::sqrt(dot3(d, d)));
+    }
+    e.rho = rho;
+    diag = 0.0;
+    if (r.bc == NEBEM_DIELECTRIC) {
+        if (!(r.eps_a > 0.0) || !(r.eps_b > 0.0) || r.eps_a == r.eps_b) {
+            why = "dielectric interface needs eps_a != eps_b, both > 0";
+            return NEBEM_INVALID_ARG;
+        }
+        diag = (r.eps_a + r.eps_b) / (2.0 * kEps0 * (r.eps_b - r.eps_a));
+    }
+    // FP32 far-field Gauss nodes as offsets from the centroid, weights x area.
+    const double area = (nv == 4) ? e.twoA[0] : 0.5 * e.twoA[0];
+    auto put = [&](float4& dst, const double* g, double wt) {
+        double d[3];
+        sub3(g, e.c, d);
+        dst.x = (float)d[0];
+        dst.y = (float)d[1];
+        dst.z = (float)d[2];
+        dst.w = (float)(wt * area);
+    };
+    int n_a = 0;
+    if (nv == 4) {
+        double e3[3];
+        sub3(r.v[3], r.v[0], e3);
+        auto tensor = [&](int m, float4* dst) {
+            double x[16], w[16];
+            gauss_legendre01(m, x, w);
+            int cnt = 0;
+            for (int a = 0; a < m; ++a)
+                for (int b = 0; b < m; ++b) {
+                    double g[3];
+                    for (int k = 0; k < 3; ++k) g[k] = r.v[0][k] + x[a] * e1[k] + x[b] * e3[k];
+                    put(dst[cnt++], g, w[a] * w[b]);
+                }
+            return cnt;
+        };
+        n_a = tensor(3, fn.a);
+        tensor(4, fn.b);
+        tensor(6, fn.c);
+    } else {
+        // degree-4 six-point rule
+        for (int g2 = 0; g2 < 2; ++g2)
+            for (int rr = 0; rr < 3; ++rr) {
+                double bc[3] = {kTriA[g2], kTriA[g2], kTriA[g2]};
+                bc[rr] = 1.0 - 2.0 * kTriA[g2];
+                double g[3];
+                for (int k = 0; k < 3; ++k) g[k] = bc[0] * r.v[0][k] + bc[1] * r.v[1][k] + bc[2] * r.v[2][k];
+                put(fn.a[n_a++], g, kTriW[g2]);
+            }
+        // collapsed (Duffy) product rules: x = v0 + s e1 + t (1 - s) e2, weight 2 ws wt (1 - s)
+        auto collapsed = [&](int m, float4* dst) {
+            double x[16], w[16];
+            gauss_legendre01(m, x, w);
+            int cnt = 0;
+            for (int a = 0; a < m; ++a)
+                for (int b = 0; b < m; ++b) {
+                    const double sa = x[a], tb = x[b] * (1.0 - x[a]);
+                    double g[3];
+                    for (int k = 0; k < 3; ++k) g[k] = r.v[0][k] + sa * e1[k] + tb * e2[k];
+                    put(dst[cnt++], g, 2.0 * w[a] * w[b] * (1.0 - x[a]));
+                }
+            return cnt;
+        };
+        collapsed(4, fn.b);
+        collapsed(6, fn.c);
+    }
+    const double ra = opt.ratio_a * rho, rb = opt.ratio_b * rho, rn = opt.ratio_near * rho;
+    fn.hdr.x = (float)(ra * ra);
+    fn.hdr.y = (float)(rb * rb);
+    fn.hdr.z = (float)(rn * rn);
+    fn.hdr.w = (float)n_a;
+    return NEBEM_OK;
+}
+
+int build_images(const double* lattice, int lo, int hi, ImageTable& img, std::string& why) {
+    std::memset(&img, 0, sizeof(img));
+    if (!lattice) {
+        img.n = 1;
+        img.k0 = 0;
+        return NEBEM_OK;
+    }
+    if (hi < lo || lo > 0 || hi < 0) {
+        why = "image range must contain 0";
+        return NEBEM_INVALID_ARG;
+    }
+    const int m = hi - lo + 1;
+    if (m > kMaxImgAxis) {
+        why = "more than 11 images per axis";
+        return NEBEM_TOO_LARGE;
+    }
+    for (int k = 0; k < 6; ++k)
+        if (!std::isfinite(lattice[k])) {
+            why = "non-finite lattice vector";
+            return NEBEM_INVALID_ARG;
+        }
+    img.n = m * m;
+    img.k0 = (0 - lo) * m + (0 - lo);
+    for (int k1 = lo; k1 <= hi; ++k1)
+        for (int k2 = lo; k2 <= hi; ++k2) {
+            const int k = (k1 - lo) * m + (k2 - lo);
+            for (int c = 0; c < 3; ++c) {
+                // one rounded product per term and one rounded sum (no contraction: this
+                // file is compiled with -ffp-contract=off)
+                const double p1 = (double)k1 * lattice[c];
+                const double p2 = (double)k2 * lattice[3 + c];
+                img.t[k][c] = p1 + p2;
+            }
+        }
+    return NEBEM_OK;
+}
+
+}  // namespace nb

@@ -1,0 +1,457 @@
+// lu.cu -- dense LU with partial pivoting, triangular solves, residual and refinement
+// helpers (Sec. 4.1, Alg. 1: the paper inverts K with an LU factorisation; here the
+// factors are kept and applied by forward/back substitution instead of forming K^-1).
+//
+// Right-looking blocked LU, column-major, lda = n, panel width nb:
+//   for each panel [k0, k0+nb):
+//     per column j: pivot search (max |a|, lowest row index on ties) -> row swap
+//                   inside the panel -> scale the column -> rank-1 update of the panel;
+//     apply the panel's swaps to the other columns;
+//     U12 = L11^-1 A12  (explicit inverse of the unit-lower nb x nb block, then a GEMM);
+//     A22 -= L21 U12    (GEMM).
+// Templated on the element type: double (FP64 solves) and float (mixed solves, the
+// FP64 iterative refinement lives in the caller).
+#include <algorithm>
+#include <vector>
+
+#include "nb_internal.h"
+
+namespace nb {
+
+namespace {
+
+constexpr int kPivBlocks = 256;
+constexpr int kPivThreads = 256;
+
+template <typename T>
+__global__ void k_pivot_partial(const T* __restrict__ A, int64_t n, int64_t j, double* __restrict__ pval,
+                                int64_t* __restrict__ pidx) {
+    double best = -1.0;
+    int64_t bidx = INT64_MAX;
+    for (int64_t i = j + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = fabs((double)A[i + j * n]);
+        if (v > best || (v == best && i < bidx)) {
+            best = v;
+            bidx = i;
+        }
+    }
+    __shared__ double sv[kPivThreads];
+    __shared__ int64_t si[kPivThreads];
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bidx;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            const double v = sv[threadIdx.x + s];
+            const int64_t ix = si[threadIdx.x + s];
+            if (v > sv[threadIdx.x] || (v == sv[threadIdx.x] && ix < si[threadIdx.x])) {
+                sv[threadIdx.x] = v;
+                si[threadIdx.x] = ix;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        pval[blockIdx.x] = sv[0];
+        pidx[blockIdx.x] = si[0];
+    }
+}
+
+// Final pivot reduction + row swap inside the panel columns [k0, k1).
+template <typename T>
+__global__ void k_pivot_swap(T* __restrict__ A, int64_t n, int64_t j, int64_t k0, int64_t k1,
+                             const double* __restrict__ pval, const int64_t* __restrict__ pidx, int nparts,
+                             int32_t* __restrict__ piv, int* __restrict__ info) {
+    __shared__ double sv[kPivThreads];
+    __shared__ int64_t si[kPivThreads];
+    double best = -1.0;
+    int64_t bidx = INT64_MAX;
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) {
+        const double v = pval[b];
+        const int64_t ix = pidx[b];
+        if (v > best || (v == best && ix < bidx)) {
+            best = v;
+            bidx = ix;
+        }
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bidx;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            const double v = sv[threadIdx.x + s];
+            const int64_t ix = si[threadIdx.x + s];
+            if (v > sv[threadIdx.x] || (v == sv[threadIdx.x] && ix < si[threadIdx.x])) {
+                sv[threadIdx.x] = v;
+                si[threadIdx.x] = ix;
+            }
+        }
+        __syncthreads();
+    }
+    // a column without a valid maximum (all NaN) keeps its own row: the factorisation is
+    // then reported singular through info and no out-of-range row is ever swapped
+    const int64_t p = (si[0] >= j && si[0] < n) ? si[0] : j;
+    if (threadIdx.x == 0) {
+        piv[j] = (int32_t)p;
+        if (!(sv[0] > 0.0) && *info == 0) *info = (int)(j + 1);
+    }
+    if (p != j) {
+        for (int64_t c = k0 + threadIdx.x; c < k1; c += blockDim.x) {
+            const T a = A[j + c * n];
+            A[j + c * n] = A[p + c * n];
+            A[p + c * n] = a;
+        }
+    }
+}
+
+// Scale column j below the diagonal and apply the rank-1 update to panel columns (j, k1).
+template <typename T>
+__global__ void k_scale_update(T* __restrict__ A, int64_t n, int64_t j, int64_t k1) {
+    extern __shared__ unsigned char smem_raw[];
+    T* urow = reinterpret_cast<T*>(smem_raw);
+    const int w = (int)(k1 - j - 1);
+    for (int c = threadIdx.x; c < w; c += blockDim.x) urow[c] = A[j + (j + 1 + c) * n];
+    __syncthreads();
+    const T d = A[j + j * n];
+    if (d == (T)0) return;
+    const T inv = (T)1 / d;
+    for (int64_t i = j + 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const T l = A[i + j * n] * inv;
+        A[i + j * n] = l;
+        for (int c = 0; c < w; ++c) A[i + (j + 1 + c) * n] -= l * urow[c];
+    }
+}
+
+// Apply the row swaps of panel rows [k0, k1) to columns outside the panel.
+template <typename T>
+__global__ void k_laswp(T* __restrict__ A, int64_t n, int64_t k0, int64_t k1, const int32_t* __restrict__ piv) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n || (c >= k0 && c < k1)) return;
+    for (int64_t r = k0; r < k1; ++r) {
+        const int64_t p = piv[r];
+        if (p != r) {
+            const T a = A[r + c * n];
+            A[r + c * n] = A[p + c * n];
+            A[p + c * n] = a;
+        }
+    }
+}
+
+// Inverse of the unit-lower nb x nb diagonal block at (k0, k0) into W (nb x nb, ld nb).
+template <typename T>
+__global__ void k_trtri_unit_lower(const T* __restrict__ A, int64_t n, int64_t k0, int nb, T* __restrict__ W) {
+    extern __shared__ unsigned char smem_raw[];
+    T* L = reinterpret_cast<T*>(smem_raw);  // nb x (nb+1)
+    const int ld = nb + 1;
+    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+        const int r = idx % nb, c = idx / nb;
+        L[r + c * ld] = A[(k0 + r) + (k0 + c) * n];
+    }
+    __syncthreads();
+    // thread c computes column c of X = L^-1: x_c = 1, x_r = -sum_{c<=s<r} L[r][s] x_s
+    for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+        T* x = W + (int64_t)c * nb;
+        for (int r = 0; r < c; ++r) x[r] = (T)0;
+        x[c] = (T)1;
+        for (int r = c + 1; r < nb; ++r) {
+            T s = (T)0;
+            for (int q = c; q < r; ++q) s += L[r + q * ld] * x[q];
+            x[r] = -s;
+        }
+    }
+}
+
+// C = alpha * A * B + beta * C; column-major, M x N x K; 64 x 64 tiles, 256 threads, 4x4
+// register tile per thread.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemm(int64_t M, int64_t N, int64_t K, T alpha, const T* __restrict__ A,
+                                              int64_t lda, const T* __restrict__ B, int64_t ldb, T beta,
+                                              T* __restrict__ C, int64_t ldc) {
+    constexpr int BM = 64, BN = 64, BK = 16;
+    __shared__ T As[BK][BM + 1];
+    __shared__ T Bs[BK][BN + 1];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+    T acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = (T)0;
+    for (int64_t k0 = 0; k0 < K; k0 += BK) {
+        for (int idx = threadIdx.x; idx < BM * BK; idx += 256) {
+            const int r = idx % BM, kk = idx / BM;
+            const int64_t gr = m0 + r, gk = k0 + kk;
+            As[kk][r] = (gr < M && gk < K) ? A[gr + gk * lda] : (T)0;
+        }
+        for (int idx = threadIdx.x; idx < BN * BK; idx += 256) {
+            const int kk = idx % BK, c = idx / BK;
+            const int64_t gk = k0 + kk, gc = n0 + c;
+            Bs[kk][c] = (gk < K && gc < N) ? B[gk + gc * ldb] : (T)0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                a[q] = As[kk][tx + 16 * q];
+                b[q] = Bs[kk][ty + 16 * q];
+            }
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int64_t gr = m0 + tx + 16 * p, gc = n0 + ty + 16 * q;
+            if (gr < M && gc < N) {
+                T* c = C + gr + gc * ldc;
+                *c = (beta == (T)0) ? alpha * acc[p][q] : fma(alpha, acc[p][q], beta * *c);
+            }
+        }
+}
+
+template <typename T>
+__global__ void k_copy_block(const T* __restrict__ W, int64_t ldw, T* __restrict__ A, int64_t lda, int64_t rows,
+                             int64_t cols) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rows * cols) return;
+    const int64_t r = t % rows, c = t / rows;
+    A[r + c * lda] = W[r + c * ldw];
+}
+
+template <typename T>
+cudaError_t gemm(int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t lda, const T* B, int64_t ldb, T beta,
+                 T* C, int64_t ldc, cudaStream_t s) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + 63) / 64));
+    k_gemm<T><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    return cudaGetLastError();
+}
+
+#define NB_TRY(x)                              \
+    do {                                       \
+        cudaError_t e_ = (x);                  \
+        if (e_ != cudaSuccess) return e_;      \
+    } while (0)
+
+// work layout: [0, nb*nb) L11 inverse; [nb*nb, nb*nb + nb*n) U12 staging;
+// then kPivBlocks doubles + kPivBlocks int64 for the pivot search.
+template <typename T>
+cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_info, cudaStream_t s) {
+    NB_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
+    T* Linv = work;
+    T* W = work + (size_t)nb * nb;
+    char* tail = reinterpret_cast<char*>(W + (size_t)nb * n);
+    size_t off = ((uintptr_t)tail + 15) & ~(uintptr_t)15;
+    double* pval = reinterpret_cast<double*>(off);
+    int64_t* pidx = reinterpret_cast<int64_t*>(pval + kPivBlocks);
+    for (int64_t k0 = 0; k0 < n; k0 += nb) {
+        const int64_t k1 = std::min<int64_t>(n, k0 + nb);
+        const int w = (int)(k1 - k0);
+        for (int64_t j = k0; j < k1; ++j) {
+            const int64_t rows = n - j;
+            const int pb = (int)std::min<int64_t>(kPivBlocks, (rows + kPivThreads - 1) / kPivThreads);
+            k_pivot_partial<T><<<pb, kPivThreads, 0, s>>>(A, n, j, pval, pidx);
+            k_pivot_swap<T><<<1, kPivThreads, 0, s>>>(A, n, j, k0, k1, pval, pidx, pb, piv, d_info);
+            if (j + 1 < n) {
+                const int64_t r2 = n - j - 1;
+                const int ub = (int)std::min<int64_t>(1024, (r2 + 127) / 128);
+                k_scale_update<T><<<ub, 128, sizeof(T) * nb, s>>>(A, n, j, k1);
+            }
+        }
+        NB_TRY(cudaGetLastError());
+        k_laswp<T><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(A, n, k0, k1, piv);
+        if (k1 < n) {
+            const int64_t m = n - k1;
+            k_trtri_unit_lower<T><<<1, 128, sizeof(T) * w * (w + 1), s>>>(A, n, k0, w, Linv);
+            // W = Linv * A12  (w x m), then A12 = W
+            NB_TRY(gemm<T>(w, m, w, (T)1, Linv, w, A + k0 + k1 * n, n, (T)0, W, w, s));
+            k_copy_block<T><<<(unsigned)((w * m + 255) / 256), 256, 0, s>>>(W, w, A + k0 + k1 * n, n, w, m);
+            // A22 -= L21 * U12
+            NB_TRY(gemm<T>(m, m, w, (T)-1, A + k1 + k0 * n, n, A + k0 + k1 * n, n, (T)1, A + k1 + k1 * n, n, s));
+        }
+        NB_TRY(cudaGetLastError());
+    }
+    return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- triangular solves
+constexpr int kTB = 64;  // solve block
+
+// b[perm] gather is done by applying swaps sequentially (single thread; n swaps).
+__global__ void k_apply_piv_f64(double* b, int64_t n, const int32_t* piv) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t p = piv[k];
+        if (p != k) {
+            const double t = b[k];
+            b[k] = b[p];
+            b[p] = t;
+        }
+    }
+}
+__global__ void k_apply_piv_f32(float* b, int64_t n, const int32_t* piv) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int64_t k = 0; k < n; ++k) {
+        const int64_t p = piv[k];
+        if (p != k) {
+            const float t = b[k];
+            b[k] = b[p];
+            b[p] = t;
+        }
+    }
+}
+
+// Solve the diagonal block [r0, r1) of L (unit lower, lower=1) or U (upper, lower=0) in place.
+template <typename T>
+__global__ void k_trsv_diag(const T* __restrict__ LU, int64_t n, int64_t r0, int64_t r1, T* __restrict__ b,
+                            int lower) {
+    __shared__ T x[kTB];
+    const int w = (int)(r1 - r0);
+    if (threadIdx.x < w) x[threadIdx.x] = b[r0 + threadIdx.x];
+    __syncthreads();
+    if (lower) {
+        for (int c = 0; c < w; ++c) {
+            const T xc = x[c];
+            if (threadIdx.x > c && threadIdx.x < w) x[threadIdx.x] -= LU[(r0 + threadIdx.x) + (r0 + c) * n] * xc;
+            __syncthreads();
+        }
+    } else {
+        for (int c = w - 1; c >= 0; --c) {
+            if (threadIdx.x == c) x[c] = x[c] / LU[(r0 + c) + (r0 + c) * n];
+            __syncthreads();
+            const T xc = x[c];
+            if (threadIdx.x < c) x[threadIdx.x] -= LU[(r0 + threadIdx.x) + (r0 + c) * n] * xc;
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x < w) b[r0 + threadIdx.x] = x[threadIdx.x];
+}
+
+// b[rows] -= LU[rows, c0:c1] * b[c0:c1] for rows in [q0, q1).
+template <typename T>
+__global__ void k_trsv_update(const T* __restrict__ LU, int64_t n, int64_t c0, int64_t c1, int64_t q0, int64_t q1,
+                              T* __restrict__ b) {
+    __shared__ T xs[kTB];
+    const int w = (int)(c1 - c0);
+    if (threadIdx.x < w) xs[threadIdx.x] = b[c0 + threadIdx.x];
+    __syncthreads();
+    const int64_t r = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= q1) return;
+    T s = (T)0;
+    for (int c = 0; c < w; ++c) s = fma(LU[r + (c0 + c) * n], xs[c], s);
+    b[r] -= s;
+}
+
+template <typename T>
+cudaError_t lu_solve(const T* LU, int64_t n, const int32_t* piv, T* b, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    if constexpr (sizeof(T) == 8)
+        k_apply_piv_f64<<<1, 1, 0, s>>>(reinterpret_cast<double*>(b), n, piv);
+    else
+        k_apply_piv_f32<<<1, 1, 0, s>>>(reinterpret_cast<float*>(b), n, piv);
+    for (int64_t r0 = 0; r0 < n; r0 += kTB) {
+        const int64_t r1 = std::min<int64_t>(n, r0 + kTB);
+        k_trsv_diag<T><<<1, kTB, 0, s>>>(LU, n, r0, r1, b, 1);
+        if (r1 < n) k_trsv_update<T><<<(unsigned)((n - r1 + 127) / 128), 128, 0, s>>>(LU, n, r0, r1, r1, n, b);
+    }
+    const int64_t last = ((n - 1) / kTB) * kTB;
+    for (int64_t r0 = last; r0 >= 0; r0 -= kTB) {
+        const int64_t r1 = std::min<int64_t>(n, r0 + kTB);
+        k_trsv_diag<T><<<1, kTB, 0, s>>>(LU, n, r0, r1, b, 0);
+        if (r0 > 0) k_trsv_update<T><<<(unsigned)((r0 + 127) / 128), 128, 0, s>>>(LU, n, r0, r1, 0, r0, b);
+    }
+    return cudaGetLastError();
+}
+
+__global__ void k_residual(const double* __restrict__ K, int64_t n, const double* __restrict__ x,
+                           const double* __restrict__ b, double* __restrict__ r) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int64_t j = 0; j < n; ++j) s = fma(K[i + j * n], x[j], s);
+    r[i] = b[i] - s;
+}
+
+__global__ void k_f64_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+// x += d; norms[0] = max|d|, norms[1] = max|x| (atomicMax on the bit patterns of
+// non-negative doubles, which order like the values).
+__global__ void k_ir_update(double* __restrict__ x, const float* __restrict__ d, int64_t n, double* norms) {
+    double md = 0.0, mx = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double di = (double)d[i];
+        const double xi = x[i] + di;
+        x[i] = xi;
+        md = fmax(md, fabs(di));
+        mx = fmax(mx, fabs(xi));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(reinterpret_cast<unsigned long long*>(norms), __double_as_longlong(md));
+        atomicMax(reinterpret_cast<unsigned long long*>(norms + 1), __double_as_longlong(mx));
+    }
+}
+
+__global__ void k_absmax(const double* __restrict__ a, int64_t n, double* out) {
+    double m = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(a[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned long long*>(out), __double_as_longlong(m));
+}
+
+}  // namespace
+
+size_t lu_work_elems(int64_t n, int nb) {
+    // L11^-1 + U12 staging + pivot partials (in bytes / 4 rounded up, covers both types)
+    return (size_t)nb * nb + (size_t)nb * (size_t)n + 16 + (size_t)kPivBlocks * 4;
+}
+
+cudaError_t lu_factor_f64(double* A, int64_t n, int32_t* piv, int nb, double* work, int* d_info, cudaStream_t s) {
+    return lu_factor<double>(A, n, piv, nb, work, d_info, s);
+}
+cudaError_t lu_factor_f32(float* A, int64_t n, int32_t* piv, int nb, float* work, int* d_info, cudaStream_t s) {
+    return lu_factor<float>(A, n, piv, nb, work, d_info, s);
+}
+cudaError_t lu_solve_f64(const double* LU, int64_t n, const int32_t* piv, double* b, cudaStream_t s) {
+    return lu_solve<double>(LU, n, piv, b, s);
+}
+cudaError_t lu_solve_f32(const float* LU, int64_t n, const int32_t* piv, float* b, cudaStream_t s) {
+    return lu_solve<float>(LU, n, piv, b, s);
+}
+cudaError_t gemv_residual(const double* K, int64_t n, const double* x, const double* b, double* r, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_residual<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(K, n, x, b, r);
+    return cudaGetLastError();
+}
+cudaError_t copy_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_f64_to_f32<<<(unsigned)std::min<int64_t>(65535, (n + 255) / 256), 256, 0, s>>>(a, b, n);
+    return cudaGetLastError();
+}
+cudaError_t ir_update(double* x, const float* d, int64_t n, double* d_norms, cudaStream_t s) {
+    NB_TRY(cudaMemsetAsync(d_norms, 0, 2 * sizeof(double), s));
+    k_ir_update<<<(unsigned)std::min<int64_t>(1024, (n + 255) / 256), 256, 0, s>>>(x, d, n, d_norms);
+    return cudaGetLastError();
+}
+cudaError_t vec_absmax(const double* a, int64_t n, double* out, cudaStream_t s) {
+    NB_TRY(cudaMemsetAsync(out, 0, sizeof(double), s));
+    k_absmax<<<(unsigned)std::min<int64_t>(1024, (n + 255) / 256), 256, 0, s>>>(a, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace nb

@@ -1,0 +1,102 @@
+// nb_internal.h -- library-internal types of libnebem (device element table, image
+// table, kernel launch wrappers).  Not part of the public C-ABI (include/nebem.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/nebem.h"
+
+namespace nb {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kEps0 = 8.8541878128e-12;  // F/m, CODATA 2018
+constexpr int kMaxImgAxis = 11;
+constexpr int kMaxImg = kMaxImgAxis * kMaxImgAxis;
+
+// Device element record (256 bytes), built on the host in FP64.  The element lies in
+// the plane y = 0 of its local frame (origin o = v0, ex along v0->v1, ey = unit normal,
+// ez = ey x ex) with counter-clockwise local (x, z) vertices (qx, qz).
+struct __align__(16) Elem {
+    double o[3], ex[3], ey[3], ez[3];  // frame
+    double qx[4], qz[4];                // local vertices (nv = 3 or 4)
+    double inv_len[4];                  // 1 / edge length, edge i = vertex i -> i+1
+    double twoA[2];                     // doubled areas of the fan triangles (0,1,2), (0,2,3)
+    double c[3];                        // centroid (global)
+    double rho;                         // circumradius about the centroid
+    int32_t nv, bc, cond, flags;
+};
+static_assert(sizeof(Elem) == 256, "Elem must be 256 bytes");
+
+// FP32 far-field shadow of one element for the mixed evaluation: Gauss nodes as offsets
+// from the centroid (x, y, z) with weight x area (w), for three distance tiers, and a
+// header (squared tier distances a^2, b^2, near^2 in m^2, node count of tier a).
+//   tier a (d >= ratio_a rho): triangle 6-point degree-4 rule, rectangle 3x3 Gauss-Legendre
+//   tier b (d >= ratio_b rho): triangle collapsed 4x4, rectangle 4x4
+//   tier c (d >= ratio_near rho): triangle collapsed 6x6, rectangle 6x6
+constexpr int kNodesA = 9;
+constexpr int kNodesB = 16;
+constexpr int kNodesC = 36;
+struct __align__(16) FarNodes {
+    float4 a[kNodesA];
+    float4 b[kNodesB];
+    float4 c[kNodesC];
+    float4 hdr;
+};
+
+struct ImageTable {
+    int32_t n;
+    int32_t k0;  // index of the zero translation
+    double t[kMaxImg][3];
+};
+
+// Per-element charge-weighted data used by the eval kernels.
+struct EvalTables {
+    const Elem* el;
+    const FarNodes* far;
+    const double* sigma;
+    int64_t n;
+};
+
+// ------------------------------------------------------------------ launchers (.cu)
+// Each returns cudaSuccess or the launch error.
+cudaError_t launch_eval_f64(const Elem* el, const double* sigma, int64_t n_el, const ImageTable& img,
+                            const double* pts, int64_t npts, double* phi, double* E, cudaStream_t s);
+cudaError_t launch_eval_mixed(const Elem* el, const FarNodes* far, const double* sigma, int64_t n_el,
+                              const ImageTable& img, const double* pts, int64_t npts, double* phi, double* E,
+                              cudaStream_t s);
+cudaError_t launch_fill_f64(const Elem* el, const double* diag, int64_t n, const ImageTable& img, double* K,
+                            cudaStream_t s);
+cudaError_t launch_element_influence(const Elem* el, int64_t n_el, const double* pts, int64_t npts,
+                                     double* phi, double* E, cudaStream_t s);
+
+// Dense LU (column-major, lda = n).  Scratch: pivots int32[n], work as documented in lu.cu.
+cudaError_t lu_factor_f64(double* A, int64_t n, int32_t* piv, int nb, double* work, int* d_info,
+                          cudaStream_t s);
+cudaError_t lu_factor_f32(float* A, int64_t n, int32_t* piv, int nb, float* work, int* d_info,
+                          cudaStream_t s);
+size_t lu_work_elems(int64_t n, int nb);
+cudaError_t lu_solve_f64(const double* LU, int64_t n, const int32_t* piv, double* b, cudaStream_t s);
+cudaError_t lu_solve_f32(const float* LU, int64_t n, const int32_t* piv, float* b, cudaStream_t s);
+cudaError_t convert_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
+cudaError_t gemv_residual(const double* K, int64_t n, const double* x, const double* b, double* r,
+                          cudaStream_t s);  // r = b - K x
+cudaError_t ir_update(double* x, const float* d, int64_t n, double* d_norms, cudaStream_t s);
+cudaError_t copy_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
+cudaError_t vec_absmax(const double* a, int64_t n, double* out, cudaStream_t s);
+
+// space charge (spacecharge.cu)
+cudaError_t launch_sc_split(const double* pos, const double* q, int64_t n, float4* hq, float4* lo, cudaStream_t s);
+cudaError_t launch_sc_eval(int precision, const double* src, const double* q, const float4* hq, const float4* lo,
+                           int64_t nsrc, const double* tgt, int64_t ntgt, int exclude_self, double soft,
+                           int accumulate, double* phi, double* E, cudaStream_t s);
+cudaError_t launch_rhs_sc(const Elem* el, int64_t n, const double* phi, const double* E, double* b, cudaStream_t s);
+cudaError_t launch_centroids(const Elem* el, int64_t n, double* c, cudaStream_t s);
+cudaError_t launch_drift(double* pos, const double* q, const double* E, int64_t n, double mu_dt, cudaStream_t s);
+
+// thread-local last error message
+void set_error(const std::string& msg);
+
+}  // namespace nb

@@ -1,0 +1,173 @@
+// solve.cpp -- solve orchestration on the context stream: influence-matrix fill,
+// LU factorisation (FP64, or FP32 for mixed solves), right-hand side, substitution and
+// FP64 iterative refinement; evaluation dispatch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "context.h"
+
+namespace nb {
+
+#define CK(call)                                                          \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);               \
+    } while (0)
+
+static int elapsed_ms(Ctx* c, double* ms) {
+    CK(cudaEventRecord(c->ev1, c->stream));
+    CK(cudaEventSynchronize(c->ev1));
+    float f = 0.f;
+    CK(cudaEventElapsedTime(&f, c->ev0, c->ev1));
+    if (ms) *ms = f;
+    return 0;
+}
+
+int ensure_fill(Ctx* c, double* ms) {
+    if (c->K_valid) return 0;
+    const int64_t n = c->n;
+    CK(c->d_K.ensure(sizeof(double) * n * n));
+    CK(cudaEventRecord(c->ev0, c->stream));
+    CK(launch_fill_f64(c->d_el.as<Elem>(), c->d_diag.as<double>(), n, c->img, c->d_K.as<double>(), c->stream));
+    int rc = elapsed_ms(c, ms);
+    if (rc) return rc;
+    c->K_valid = true;
+    c->fac64_valid = c->fac32_valid = false;
+    return 0;
+}
+
+int ensure_factors(Ctx* c, int precision, double* ms) {
+    const int64_t n = c->n;
+    const int nb = c->opt.lu_block;
+    int h_info = 0;
+    if (precision == NEBEM_FP64) {
+        if (c->fac64_valid) return 0;
+        CK(c->d_LU64.ensure(sizeof(double) * n * n));
+        CK(c->d_piv64.ensure(sizeof(int32_t) * n));
+        CK(c->d_work.ensure(sizeof(double) * lu_work_elems(n, nb)));
+        CK(c->d_small.ensure(256));
+        CK(cudaEventRecord(c->ev0, c->stream));
+        CK(cudaMemcpyAsync(c->d_LU64.ptr, c->d_K.ptr, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, c->stream));
+        CK(lu_factor_f64(c->d_LU64.as<double>(), n, c->d_piv64.as<int32_t>(), nb, c->d_work.as<double>(),
+                         c->d_small.as<int>(), c->stream));
+        int rc = elapsed_ms(c, ms);
+        if (rc) return rc;
+        CK(cudaMemcpy(&h_info, c->d_small.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+        if (h_info) return fail(NEBEM_SINGULAR, "zero pivot at column " + std::to_string(h_info - 1));
+        c->fac64_valid = true;
+    } else {
+        if (c->fac32_valid) return 0;
+        CK(c->d_LU32.ensure(sizeof(float) * n * n));
+        CK(c->d_piv32.ensure(sizeof(int32_t) * n));
+        CK(c->d_work.ensure(sizeof(double) * lu_work_elems(n, nb)));
+        CK(c->d_small.ensure(256));
+        CK(cudaEventRecord(c->ev0, c->stream));
+        CK(copy_f64_to_f32(c->d_K.as<double>(), c->d_LU32.as<float>(), n * n, c->stream));
+        CK(lu_factor_f32(c->d_LU32.as<float>(), n, c->d_piv32.as<int32_t>(), nb, c->d_work.as<float>(),
+                         c->d_small.as<int>(), c->stream));
+        int rc = elapsed_ms(c, ms);
+        if (rc) return rc;
+        CK(cudaMemcpy(&h_info, c->d_small.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+        if (h_info) return fail(NEBEM_SINGULAR, "zero pivot at column " + std::to_string(h_info - 1));
+        c->fac32_valid = true;
+    }
+    return 0;
+}
+
+// b_i = V(conductor_i) on conductor rows, 0 on interface rows; minus the known-charge
+// potential / normal field at the collocation points when a charge set is present.
+int build_rhs(Ctx* c) {
+    const int64_t n = c->n;
+    std::vector<double> b((size_t)n);
+    for (int64_t i = 0; i < n; ++i) b[i] = (c->h_bc[i] == NEBEM_CONDUCTOR) ? c->voltages[c->h_cond[i]] : 0.0;
+    CK(c->d_b.ensure(sizeof(double) * n));
+    CK(cudaMemcpyAsync(c->d_b.ptr, b.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    if (c->n_car > 0) {
+        int rc = rhs_known_charge(c);
+        if (rc) return rc;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return 0;
+}
+
+int solve_with_factors(Ctx* c, int precision, nebem_solve_info* info) {
+    const int64_t n = c->n;
+    CK(c->d_x.ensure(sizeof(double) * n));
+    CK(c->d_r.ensure(sizeof(double) * n));
+    CK(c->d_small.ensure(256));
+    double* x = c->d_sigma.as<double>();
+    double* b = c->d_b.as<double>();
+    double* r = c->d_r.as<double>();
+    double* norms = reinterpret_cast<double*>(c->d_small.as<char>() + 64);
+    CK(cudaEventRecord(c->ev0, c->stream));
+    int status = 0;
+    if (precision == NEBEM_FP64) {
+        CK(cudaMemcpyAsync(x, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+        CK(lu_solve_f64(c->d_LU64.as<double>(), n, c->d_piv64.as<int32_t>(), x, c->stream));
+    } else {
+        CK(c->d_r32.ensure(sizeof(float) * n));
+        float* d32 = c->d_r32.as<float>();
+        CK(cudaMemsetAsync(x, 0, sizeof(double) * n, c->stream));
+        CK(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+        double corr = 1.0;
+        int it = 0;
+        status = NEBEM_NOT_CONVERGED;
+        for (it = 1; it <= c->opt.ir_max_iter; ++it) {
+            CK(copy_f64_to_f32(r, d32, n, c->stream));
+            CK(lu_solve_f32(c->d_LU32.as<float>(), n, c->d_piv32.as<int32_t>(), d32, c->stream));
+            CK(ir_update(x, d32, n, norms, c->stream));
+            double h[2];
+            CK(cudaMemcpyAsync(h, norms, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            corr = (h[1] > 0.0) ? h[0] / h[1] : 0.0;
+            if (!std::isfinite(corr)) break;
+            CK(gemv_residual(c->d_K.as<double>(), n, x, b, r, c->stream));
+            if (corr <= c->opt.ir_tol) {
+                status = 0;
+                break;
+            }
+        }
+        if (info) {
+            info->iterations = std::min(it, c->opt.ir_max_iter);
+            info->correction = corr;
+        }
+    }
+    double ms = 0.0;
+    int rc = elapsed_ms(c, &ms);
+    if (rc) return rc;
+    if (info) info->ms_solve = ms;
+    // residual diagnostic ||K x - b||_inf / (||K||_inf-ish ||x||_inf)
+    CK(gemv_residual(c->d_K.as<double>(), n, x, b, r, c->stream));
+    CK(vec_absmax(r, n, norms, c->stream));
+    CK(vec_absmax(x, n, norms + 1, c->stream));
+    double h[2];
+    CK(cudaMemcpyAsync(h, norms, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (info) info->residual = (h[1] > 0.0) ? h[0] / h[1] : 0.0;
+    c->sigma_valid = true;
+    if (status) return fail(status, "iterative refinement did not reach the tolerance");
+    return 0;
+}
+
+int eval_elements(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision, cudaStream_t s) {
+    if (precision == NEBEM_MIXED)
+        CK(launch_eval_mixed(c->d_el.as<Elem>(), c->d_far.as<FarNodes>(), c->d_sigma.as<double>(), c->n, c->img,
+                             d_pts, n, d_phi, d_E, s));
+    else
+        CK(launch_eval_f64(c->d_el.as<Elem>(), c->d_sigma.as<double>(), c->n, c->img, d_pts, n, d_phi, d_E, s));
+    return 0;
+}
+
+int eval_points(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision, cudaStream_t s) {
+    int rc = eval_elements(c, d_pts, n, d_phi, d_E, precision, s);
+    if (rc) return rc;
+    return add_known_charge(c, d_pts, n, d_phi, d_E, precision, s);
+}
+
+
+}  // namespace nb

@@ -1,0 +1,78 @@
+"""Roofline bookkeeping for the mixed evaluation kernel (measurement only).
+
+Algorithmic work of one mixed evaluation launch, counted per (point, element, image)
+pair by its distance tier (distance to the image centroid in element circumradii):
+  tier a (>= ratio_a):   6 Gauss nodes (triangle) or 9 (rectangle)
+  tier b (>= ratio_b):   16 nodes
+  tier c (>= ratio_near): 36 nodes
+  near:                  one FP64 closed form
+Per Gauss node the FP32 arithmetic is 13 lane operations (3 differences, 3 for r^2,
+2 for w r^-1 and w r^-3 after one rsqrt, 1 for phi, 3 for E, 1 product) plus one MUFU
+rsqrt; per pair 9 (two-float difference: 6, squared distance: 3).  The counts are
+taken on a sample of points with the same thresholds as the kernel and scaled to the
+launch.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+OPS_PER_NODE = 13
+OPS_PER_PAIR = 9
+N_SM = 152
+FP32_LANES_PER_SM = 128
+MUFU_PER_SM = 16
+
+
+def _element_table(g):
+    kinds = g.elements["kind"]
+    v = g.elements["v"]
+    nv = np.where(kinds == 0, 4, 3)
+    c = np.where(nv[:, None] == 4, v[:, :4].mean(1), v[:, :3].mean(1))
+    d = np.linalg.norm(v - c[:, None, :], axis=2)
+    d[nv == 3, 3] = 0.0
+    rho = d.max(1)
+    return c, rho, nv
+
+
+def _images(g):
+    if g.lattice is None:
+        return np.zeros((1, 3))
+    ks = np.arange(g.img_lo, g.img_hi + 1)
+    return np.array([k1 * g.lattice[0] + k2 * g.lattice[1] for k1 in ks for k2 in ks])
+
+
+def tier_counts(g, pts, sample=4096, ratio_a=24.0, ratio_b=8.0, ratio_near=3.0, chunk=32):
+    c, rho, nv = _element_table(g)
+    t = _images(g)
+    C = (c[:, None, :] + t[None]).reshape(-1, 3)          # (el*img, 3)
+    R = np.repeat(rho, t.shape[0])
+    NV = np.repeat(nv, t.shape[0])
+    na = np.where(NV == 4, 9, 6)
+    counts = {"pairs": 0, "a": 0, "b": 0, "c": 0, "near": 0, "nodes": 0, "sample_points": 0}
+    P = pts[:sample]
+    for s in range(0, P.shape[0], chunk):
+        d = np.linalg.norm(P[s:s + chunk, None, :] - C[None], axis=2) / R[None]
+        ta = d >= ratio_a
+        tb = (~ta) & (d >= ratio_b)
+        tc = (~ta) & (~tb) & (d >= ratio_near)
+        tn = d < ratio_near
+        counts["pairs"] += d.size
+        counts["a"] += int(ta.sum())
+        counts["b"] += int(tb.sum())
+        counts["c"] += int(tc.sum())
+        counts["near"] += int(tn.sum())
+        counts["nodes"] += int((ta * na[None]).sum() + 16 * tb.sum() + 36 * tc.sum())
+    counts["sample_points"] = int(P.shape[0])
+    return counts
+
+
+def fp32_ops_per_launch(counts, scale):
+    return (OPS_PER_NODE * counts["nodes"] + OPS_PER_PAIR * counts["pairs"]) * scale
+
+
+def fp32_peak_ops(sm_mhz):
+    return N_SM * FP32_LANES_PER_SM * sm_mhz * 1e6
+
+
+def mufu_peak(sm_mhz):
+    return N_SM * MUFU_PER_SM * sm_mhz * 1e6

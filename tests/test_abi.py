@@ -1,0 +1,55 @@
+"""The C-ABI library loads and exports every symbol that include/nebem.h declares.
+
+CPU-only: no compute call is made (there is no GPU here); creating a context must fail
+with NEBEM_NO_DEVICE rather than fall back to anything.
+"""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "nebem.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nebem_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2606_24154_gb300 import build, nebem
+    build.build()
+    return nebem.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2606_24154_gb300 import nebem
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in nebem.SIGNATURES, f"binding lacks {name}"
+    out = subprocess.run(["nm", "-D", "--defined-only", nebem.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (nebem_\w+)", out))
+    assert set(names) <= exported, set(names) - exported
+
+
+def test_no_device_is_an_error_not_a_fallback(lib):
+    import torch
+    from paper_2606_24154_gb300 import nebem
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(nebem.NebemError) as ei:
+        nebem.nebem_create()
+    assert ei.value.code == nebem.NEBEM_NO_DEVICE
+
+
+def test_status_strings_and_defaults(lib):
+    from paper_2606_24154_gb300 import nebem
+    assert lib.nebem_status_string(nebem.NEBEM_SINGULAR) == b"NEBEM_SINGULAR"
+    o = nebem.nebem_default_options()
+    assert o.ir_tol == 1e-8 and o.lu_block == 64 and o.softening == 1e-6

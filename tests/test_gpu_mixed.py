@@ -1,0 +1,113 @@
+"""Mixed-precision evaluation (FP32 far-field Gauss rules + FP64 near closed forms)
+against the FP64 oracle: <= 1e-6 relative (normwise per quantity), and bit-identical
+per point whatever the batch it is evaluated in."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2606_24154_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL_MIXED = 1e-6
+
+
+@pytest.fixture(scope="module")
+def N():
+    from paper_2606_24154_gb300 import build, nebem
+    build.build()
+    nebem.load()
+    return nebem
+
+
+def rel_norm(a, ref):
+    return float(np.abs(a - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def rel_vec(a, ref):
+    return float(np.linalg.norm(a - ref, axis=1).max() / np.linalg.norm(ref, axis=1).max())
+
+
+def structured_sigma(g):
+    """A smooth, physically shaped charge density: conductor elements carry
+    eps0 * V / 1 mm with a smooth modulation, interface elements a tenth of the scale."""
+    c, _, _ = O.centroids(g)
+    v = g.voltages
+    sig = np.zeros(g.n)
+    cond = g.elements["bc"] == I.BC_CONDUCTOR
+    mod = 1.0 + 0.3 * np.sin(2 * np.pi * c[:, 0] / 1e-3) * np.cos(2 * np.pi * c[:, 1] / 1e-3)
+    sig[cond] = 8.854e-12 * v[g.elements["conductor"][cond]] / 1e-3 * mod[cond]
+    sig[~cond] = 0.1 * 8.854e-12 * 500.0 / 1e-3 * np.sin(2 * np.pi * c[~cond, 2] / 0.5e-3)
+    return sig
+
+
+def test_mixed_eval_cube_grid(N):
+    g = I.cube(n_per_edge=8)
+    sig_r, _, _ = O.solve(g)
+    pts = I.cube_grid_points()
+    ctx = N.Context().set_geometry(g)
+    ctx.set_sigma(sig_r)
+    phi, E = ctx.eval(pts, N.NEBEM_MIXED)
+    rphi, rE = O.eval_points(g, sig_r, pts)
+    assert rel_norm(phi, rphi) <= TOL_MIXED
+    assert rel_vec(E, rE) <= TOL_MIXED
+
+
+def test_mixed_eval_thgem_full_geometry_sampled(N):
+    g = I.thgem()
+    sigma = structured_sigma(g)
+    pts = I.cell_points(g, 64, I.rng(1, 11))
+    ctx = N.Context().set_geometry(g)
+    ctx.set_sigma(sigma)
+    phi, E = ctx.eval(pts, N.NEBEM_MIXED)
+    rphi, rE = O.eval_points(g, sigma, pts)
+    assert rel_norm(phi, rphi) <= TOL_MIXED, rel_norm(phi, rphi)
+    assert rel_vec(E, rE) <= TOL_MIXED, rel_vec(E, rE)
+
+
+def test_mixed_matches_fp64_path_on_many_points(N):
+    g = I.thgem()
+    sigma = structured_sigma(g)
+    pts = I.cell_points(g, 20000, I.rng(1, 12))
+    # points close to surfaces: the FP64 near-field branch and the high-order tiers
+    near = pts.copy()
+    near[:, 2] = np.where(pts[:, 2] > 0, 0.285e-3 + 1e-6 * (1 + np.abs(pts[:, 0]) * 1e3),
+                          -0.285e-3 - 1e-6 * (1 + np.abs(pts[:, 1]) * 1e3))
+    pts = np.concatenate([pts, near[:4000]])
+    ctx = N.Context().set_geometry(g)
+    ctx.set_sigma(sigma)
+    phi, E = ctx.eval(pts, N.NEBEM_MIXED)
+    phi64, E64 = ctx.eval(pts, N.NEBEM_FP64)
+    assert rel_norm(phi, phi64) <= TOL_MIXED
+    assert rel_vec(E, E64) <= TOL_MIXED
+
+
+def test_mixed_result_independent_of_batch(N):
+    g = I.thgem(I.PlateSpec(n_phi=24, n_r=3, n_zc=1, n_zf=4), n_plane=3)
+    sigma = structured_sigma(g)
+    ctx = N.Context().set_geometry(g)
+    ctx.set_sigma(sigma)
+    mine = I.cell_points(g, 300, I.rng(0, 21))
+    others = I.cell_points(g, 5000, I.rng(0, 22))
+    alone_phi, alone_E = ctx.eval(mine, N.NEBEM_MIXED)
+    batch = np.concatenate([others[:1777], mine, others[1777:]])
+    perm = I.rng(0, 23).permutation(batch.shape[0])
+    bphi, bE = ctx.eval(batch[perm], N.NEBEM_MIXED)
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(perm.size)
+    sel = inv[1777:1777 + 300]
+    assert np.array_equal(bphi[sel], alone_phi)
+    assert np.array_equal(bE[sel], alone_E)
+
+
+def test_mixed_ragged_and_empty(N):
+    g = I.cube(n_per_edge=4)
+    sig_r, _, _ = O.solve(g)
+    ctx = N.Context().set_geometry(g)
+    ctx.set_sigma(sig_r)
+    for n in [0, 1, 127, 128, 129, 1000]:
+        pts = I.cell_points(g, max(n, 1), I.rng(0, 100 + n))[:n]
+        phi, E = ctx.eval(pts, N.NEBEM_MIXED)
+        if n:
+            rphi, rE = O.eval_points(g, sig_r, pts)
+            assert rel_norm(phi, rphi) <= TOL_MIXED and rel_vec(E, rE) <= TOL_MIXED

@@ -1,0 +1,251 @@
+"""GPU parity: the CUDA path (through the C-ABI) against the FP64 oracle.
+
+Tolerances: FP64 mode <= 1e-10 relative (per quantity, normwise, plus a per-point
+form with a floor of 1e-6 of the largest magnitude); image indexing bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2606_24154_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def N():
+    from paper_2606_24154_gb300 import build, nebem
+    build.build()
+    nebem.load()
+    return nebem
+
+
+def rel_norm(a, ref):
+    return float(np.abs(a - ref).max() / max(np.abs(ref).max(), 1e-300))
+
+
+def rel_point(a, ref, floor=1e-6):
+    """max_i |a_i - ref_i| / max(|ref_i|, floor * max|ref|), vectors per row."""
+    a = np.asarray(a).reshape(len(a), -1)
+    ref = np.asarray(ref).reshape(len(ref), -1)
+    d = np.linalg.norm(a - ref, axis=1)
+    m = np.linalg.norm(ref, axis=1)
+    return float((d / np.maximum(m, floor * m.max())).max())
+
+
+def small_thgem():
+    return I.thgem(I.PlateSpec(n_phi=24, n_r=3, n_zc=1, n_zf=4), n_plane=3)
+
+
+def random_elements(gen, n):
+    el = np.zeros(n, I.ELEMENT_DTYPE)
+    for i in range(n):
+        if i % 2 == 0:
+            c = gen.normal(size=3) * 1e-3
+            u = gen.normal(size=3); u /= np.linalg.norm(u)
+            w = np.cross(u, gen.normal(size=3)); w /= np.linalg.norm(w)
+            L1, L2 = 1e-3 * gen.uniform(0.2, 1.5, 2)
+            v0 = c - 0.5 * L1 * u - 0.5 * L2 * w
+            el[i]["kind"] = I.KIND_RECT
+            el[i]["v"] = [v0, v0 + L1 * u, v0 + L1 * u + L2 * w, v0 + L2 * w]
+        else:
+            el[i]["kind"] = I.KIND_TRI
+            el[i]["v"][:3] = gen.normal(size=(3, 3)) * 1e-3
+    return el
+
+
+def test_element_influence_closed_form(N):
+    gen = np.random.default_rng(101)
+    el = random_elements(gen, 12)
+    # axis-aligned rectangle and triangle for exact in-plane points
+    ax = np.zeros(2, I.ELEMENT_DTYPE)
+    ax[0]["kind"] = I.KIND_RECT
+    ax[0]["v"] = [[-1e-3, -1e-3, 0], [1e-3, -1e-3, 0], [1e-3, 0.5e-3, 0], [-1e-3, 0.5e-3, 0]]
+    ax[1]["kind"] = I.KIND_TRI
+    ax[1]["v"][:3] = [[0, 0, 0], [2e-3, 0, 0], [0.5e-3, 1.5e-3, 0]]
+    el = np.concatenate([el, ax])
+    pts = np.concatenate([gen.normal(size=(40, 3)) * 2e-3, gen.normal(size=(10, 3)) * 0.3e-3,
+                          gen.normal(size=(5, 3)) * 0.2,  # far
+                          [[0.2e-3, -0.3e-3, 0.0], [3e-3, 0.1e-3, 0.0], [0.4e-3, 0.2e-3, 0.0],
+                           [0.2e-3, -0.3e-3, 1e-14], [0.2e-3, -0.3e-3, -1e-14]]])
+    ctx = N.Context()
+    phi, E = N.nebem_element_influence(ctx.h, el, pts)
+    worst = 0.0
+    for e in range(el.shape[0]):
+        rp, rE = O.influence(el[e:e + 1], pts)
+        v = el[e]["v"][: (4 if el[e]["kind"] == I.KIND_RECT else 3)]
+        c = v.mean(0)
+        a = math.sqrt(np.linalg.norm(np.cross(v[1] - v[0], v[2] - v[0])))
+        # both closed forms cancel in the far field: allowed error ~ eps (d/a)^2 (a 40-digit
+        # reference shows each side within that bound at d/a ~ 600)
+        d = np.linalg.norm(pts - c, axis=1)
+        tol = 1e-12 + 2e-15 * (d / a) ** 2
+        ep = np.abs(phi[e] - rp) / np.abs(rp)
+        eE = np.linalg.norm(E[e] - rE, axis=1) / np.maximum(np.linalg.norm(rE, axis=1), 1e-300)
+        inplane = np.abs(pts[:, 2]) == 0.0
+        eE[inplane & (np.linalg.norm(rE, axis=1) < 1e-12)] = 0.0
+        worst = max(worst, float((ep / tol).max()), float((eE / tol).max()))
+    assert worst <= 1.0, worst
+
+
+def test_image_table_bit_exact(N):
+    g = I.thgem(I.PlateSpec(n_phi=12, n_r=1, n_zc=1, n_zf=2), n_plane=1)
+    for lo, hi in [(-2, 2), (-5, 5), (0, 0), (-1, 3)]:
+        ctx = N.Context()
+        N.nebem_set_geometry(ctx.h, g.elements, g.lattice, lo, hi)
+        t_gpu = N.nebem_image_table(ctx.h)
+        t_or = O.image_table(g.lattice, lo, hi)
+        assert t_gpu.shape == t_or.shape
+        assert np.array_equal(t_gpu.view(np.uint64), t_or.view(np.uint64))
+
+
+def test_fill_parity_cube(N):
+    g = I.cube(n_per_edge=8)
+    ctx = N.Context().set_geometry(g)
+    K = ctx.fill()
+    Kr = O.fill(g)
+    assert rel_norm(K, Kr) <= 1e-13
+    assert np.abs(K - Kr).max(axis=1).max() <= TOL64 * np.abs(Kr).max()
+
+
+def test_fill_parity_thgem_images_and_dielectric(N):
+    g = small_thgem()
+    assert (g.elements["bc"] == I.BC_DIELECTRIC).any() and (g.elements["kind"] == I.KIND_RECT).any()
+    ctx = N.Context().set_geometry(g)
+    K = ctx.fill()
+    Kr = O.fill(g)
+    # per row: conductor rows (potential) and interface rows (normal field) differ in scale
+    rowmax = np.abs(Kr).max(axis=1, keepdims=True)
+    assert (np.abs(K - Kr) / rowmax).max() <= TOL64
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_solve_parity_cube(N, prec):
+    g = I.cube(n_per_edge=8)
+    sig_r, K, fac = O.solve(g)
+    ctx = N.Context().set_geometry(g)
+    p = N.NEBEM_FP64 if prec == "fp64" else N.NEBEM_MIXED
+    sig, info, rc = ctx.solve(p)
+    tol = TOL64 if prec == "fp64" else 1e-8
+    assert rel_norm(sig, sig_r) <= tol
+    _, _, area = O.centroids(g)
+    cap = (sig * area).sum() / (4 * math.pi * O.eps0() * 0.01)
+    assert abs(cap - 0.6563946187799465) < 1e-9
+    if prec == "mixed":
+        assert 1 <= info.iterations <= 30 and info.correction <= 1e-8
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_solve_parity_thgem_small(N, prec):
+    g = small_thgem()
+    sig_r, K, fac = O.solve(g)
+    ctx = N.Context().set_geometry(g)
+    p = N.NEBEM_FP64 if prec == "fp64" else N.NEBEM_MIXED
+    sig, info, rc = ctx.solve(p)
+    tol = TOL64 if prec == "fp64" else 1e-8
+    assert rel_norm(sig, sig_r) <= tol, rel_norm(sig, sig_r)
+
+
+def test_eval_parity_cube_grid(N):
+    g = I.cube(n_per_edge=8)
+    sig_r, K, fac = O.solve(g)
+    pts = I.cube_grid_points()
+    ctx = N.Context().set_geometry(g)
+    ctx.set_sigma(sig_r)
+    phi, E = ctx.eval(pts, N.NEBEM_FP64)
+    rphi, rE = O.eval_points(g, sig_r, pts)
+    # points on the cube faces are the principal-value test (in-plane normal field)
+    assert rel_norm(phi, rphi) <= TOL64
+    assert rel_norm(E, rE) <= TOL64
+    assert rel_point(phi, rphi) <= 1e-9
+    assert rel_point(E, rE) <= 1e-9
+
+
+def test_eval_parity_thgem_full_geometry_sampled(N):
+    """Full-size THGEM cell (about 10,000 elements, 25 images) with a seeded charge
+    density; sampled points checked one by one against the oracle."""
+    g = I.thgem()
+    gen = I.rng(1, 7)
+    sigma = gen.normal(size=g.n) * 1e-6
+    pts = I.cell_points(g, 200, I.rng(1, 8))[:64]
+    ctx = N.Context().set_geometry(g)
+    ctx.set_sigma(sigma)
+    phi, E = ctx.eval(pts, N.NEBEM_FP64)
+    rphi, rE = O.eval_points(g, sigma, pts)
+    assert rel_norm(phi, rphi) <= TOL64
+    assert rel_norm(E, rE) <= TOL64
+
+
+def test_eval_ragged_and_empty(N):
+    g = small_thgem()
+    sigma = I.rng(0, 3).normal(size=g.n)
+    ctx = N.Context().set_geometry(g)
+    ctx.set_sigma(sigma)
+    for n in [0, 1, 127, 129, 300]:
+        pts = I.cell_points(g, max(n, 1), I.rng(0, n))[:n]
+        phi, E = ctx.eval(pts, N.NEBEM_FP64)
+        if n:
+            rphi, rE = O.eval_points(g, sigma, pts)
+            assert rel_norm(phi, rphi) <= TOL64 and rel_norm(E, rE) <= TOL64
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_space_charge_parity(N, prec):
+    g = I.thgem()
+    pos, q = I.carrier_cloud(g, 3000, I.rng(3, 1))
+    ctx = N.Context().set_geometry(g)
+    N.nebem_space_charge(ctx.h, pos, q, 1e-6)
+    p = N.NEBEM_FP64 if prec == "fp64" else N.NEBEM_MIXED
+    phi, E = N.nebem_space_charge_eval(ctx.h, pos, p, exclude_self=True)
+    rphi, rE = O.space_charge(pos, q, soft=1e-6)
+    tol = TOL64 if prec == "fp64" else 1e-6
+    assert rel_norm(phi, rphi) <= tol, rel_norm(phi, rphi)
+    assert rel_norm(E, rE) <= tol, rel_norm(E, rE)
+    tgt = I.cell_points(g, 100, I.rng(3, 2))
+    phi, E = N.nebem_space_charge_eval(ctx.h, tgt, p)
+    rphi, rE = O.space_charge(pos, q, tgt=tgt, soft=1e-6)
+    assert rel_norm(phi, rphi) <= tol and rel_norm(E, rE) <= tol
+
+
+def test_dynamic_step_parity(N):
+    g = I.cube(n_per_edge=4)
+    gen = np.random.default_rng(37)
+    pos = gen.normal(size=(300, 3)) * 2e-3 + np.array([0.0, 0.0, 0.012])
+    q = np.where(gen.random(300) < 0.5, 1.0, -1.0) * 1e-15
+    sig0, K, fac = O.solve(g)
+    ref = pos.copy()
+    for _ in range(3):
+        ref, sig_ref, _ = O.dynamic_step(g, fac, ref, q)
+    ctx = N.Context().set_geometry(g)
+    ctx.solve(N.NEBEM_FP64)
+    N.nebem_space_charge(ctx.h, pos, q, 1e-6)
+    out = N.nebem_step(ctx.h, 3, 1e-4, 1e-9, N.NEBEM_FP64, pos.shape[0])
+    disp_ref = ref - pos
+    assert np.abs((out - pos) - disp_ref).max() <= 1e-9 * np.abs(disp_ref).max()
+
+
+def test_error_paths(N):
+    ctx = N.Context()
+    with pytest.raises(N.NebemError) as e:
+        ctx.eval(np.zeros((3, 3)))
+    assert e.value.code == N.NEBEM_BAD_STATE
+    bad = np.zeros(1, I.ELEMENT_DTYPE)
+    bad["kind"] = I.KIND_TRI  # all vertices at the origin: zero area
+    with pytest.raises(N.NebemError) as e:
+        N.nebem_set_geometry(ctx.h, bad)
+    assert e.value.code == N.NEBEM_DEGENERATE_ELEMENT
+    g = I.cube(n_per_edge=2)
+    N.nebem_set_geometry(ctx.h, g.elements)
+    with pytest.raises(N.NebemError) as e:
+        N.nebem_solve(ctx.h, N.NEBEM_FP64, g.n)
+    assert e.value.code == N.NEBEM_BAD_STATE  # no voltages yet
+    with pytest.raises(N.NebemError) as e:
+        N.nebem_set_bc(ctx.h, [])
+    assert e.value.code == N.NEBEM_INVALID_ARG  # conductor 0 out of range
+    with pytest.raises(N.NebemError) as e:
+        N.nebem_set_geometry(ctx.h, g.elements, np.eye(2, 3), -6, 6)
+    assert e.value.code == N.NEBEM_TOO_LARGE
