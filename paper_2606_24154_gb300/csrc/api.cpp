@@ -53,7 +53,7 @@ Ctx::~Ctx() {
     cudaSetDevice(device);
     for (DevBuf* b : {&d_el, &d_far, &d_diag, &d_sigma, &d_K, &d_LU64, &d_LU32, &d_piv64, &d_piv32, &d_work, &d_b,
                       &d_x, &d_r, &d_r32, &d_small, &d_pts, &d_phi, &d_E, &d_car, &d_q, &d_car2, &d_sc_tgt,
-                      &d_sc_phi, &d_sc_E, &d_scratch})
+                      &d_sc_phi, &d_sc_E, &d_scratch, &d_cjk, &d_cell_start, &d_cell_items})
         b->release();
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
@@ -171,6 +171,10 @@ int nebem_set_geometry(nebem_ctx* ctx, const nebem_element* el, int64_t n, const
         h_bc[i] = el[i].bc;
         h_cond[i] = el[i].conductor;
     }
+    NearGrid grid;
+    std::vector<int32_t> cell_start, cell_items;
+    rc = build_near_grid(h_el, img, c->opt.ratio_near, grid, cell_start, cell_items, why);
+    if (rc) return fail(rc, why);
     CK(cudaStreamSynchronize(c->stream));
     // invalidate everything that depends on the geometry
     c->n = 0;
@@ -184,7 +188,16 @@ int nebem_set_geometry(nebem_ctx* ctx, const nebem_element* el, int64_t n, const
     CK(cudaMemcpyAsync(c->d_el.ptr, h_el.data(), sizeof(Elem) * n, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_far.ptr, h_far.data(), sizeof(FarNodes) * n, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_diag.ptr, h_diag.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    CK(c->d_cjk.ensure(sizeof(float4) * 2 * n * img.n));
+    CK(launch_image_centroids(c->d_el.as<Elem>(), n, img, c->d_cjk.as<float4>(), c->stream));
+    CK(c->d_cell_start.ensure(sizeof(int32_t) * cell_start.size()));
+    CK(c->d_cell_items.ensure(sizeof(int32_t) * cell_items.size()));
+    CK(cudaMemcpyAsync(c->d_cell_start.ptr, cell_start.data(), sizeof(int32_t) * cell_start.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_cell_items.ptr, cell_items.data(), sizeof(int32_t) * cell_items.size(),
+                       cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    c->grid = grid;
     c->img = img;
     c->h_bc = std::move(h_bc);
     c->h_cond = std::move(h_cond);

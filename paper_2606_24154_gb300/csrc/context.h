@@ -34,6 +34,8 @@ struct Ctx {
     std::vector<Elem> h_el;
     std::vector<int32_t> h_bc, h_cond;
     DevBuf d_el, d_far, d_diag;
+    DevBuf d_cjk, d_cell_start, d_cell_items;  // mixed eval: two-float image centroids, near cell list
+    NearGrid grid{};
 
     // boundary conditions and solution
     std::vector<double> voltages;

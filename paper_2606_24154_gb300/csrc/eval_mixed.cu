@@ -9,16 +9,24 @@
 //   nearer                FP64 closed form (influence.cuh), where ln/atan cancel
 // Quadrature per node: Phi += w / r, E += w (P - x_n) / r^3 with one rsqrt.
 //
-// The FP32 difference P - x_n must keep its relative accuracy even when P and the
-// node are millimetres from the origin but only micrometres apart, so both sides are
-// held as two floats (hi + lo): (P_hi - C_hi) + (P_lo - C_lo), where C = c_j + t_k is the
-// image centroid formed in FP64 once per block tile and split.  Node offsets from the
-// centroid are small, so the remaining FP32 operations carry ~1e-7 relative error.
+// Two kernels: k_eval_far runs every FP32 tier over all (element, image) pairs and skips
+// near pairs; k_eval_near visits only the image centroids in the 27 grid cells around
+// each point (a cell list built per geometry, cell edge >= the largest near radius) and
+// adds the near pairs' FP64 closed forms.  Keeping the FP64 code out of the far kernel
+// keeps its register count (and so its occupancy) at the FP32 kernel's level.  Both
+// kernels decide "near" with the same rounded FP32 operations (pair_d2) on the same
+// inputs, so every pair is counted exactly once.
+//
+// The FP32 difference P - x_n keeps its relative accuracy even when P and the node are
+// millimetres from the origin but micrometres apart: both sides are held as two floats
+// (hi + lo) and (P_hi - C_hi) + (P_lo - C_lo) is formed first, C = c_j + t_k being the
+// image centroid (FP64 sum split once per geometry).  Node offsets from the centroid are
+// small, so the remaining FP32 operations carry ~1e-7 relative error.
 //
 // Accumulation: per element over its images in FP32, weighted by sigma_j, summed in FP32
-// over groups of kGroup elements and flushed to FP64 accumulators.  The choice of
-// arithmetic depends only on the pair itself, so a point's result does not depend on
-// which other points share its launch (bit-identical alone or batched).
+// over groups of kGroup elements and flushed to FP64.  Every decision depends only on the
+// pair, and each point's sums run in a fixed order, so a point's result is bit-identical
+// whatever other points share its launch.
 #include "influence.cuh"
 
 namespace nb {
@@ -26,9 +34,24 @@ namespace nb {
 namespace {
 
 constexpr int kMT = 128;        // threads per block (one target each)
-constexpr int kTileMax = 32;    // elements per shared-memory tile
-constexpr int kCjkMax = 1024;   // (element, image) centres per tile
-constexpr int kGroup = 4;       // elements per FP32 partial sum
+constexpr int kTileMax = 16;    // elements per shared-memory tile
+constexpr int kCjkMax = 512;    // (element, image) centres per tile
+constexpr int kGroup = 8;       // elements per FP32 partial sum
+
+// Squared FP32 distance between a point (two floats per coordinate) and an image centroid;
+// the operation sequence is pinned (no contraction) so both kernels agree bit for bit.
+__device__ __forceinline__ float pair_d2(float phx, float phy, float phz, float plx, float ply, float plz,
+                                         const float4& ch, const float4& cl, float& dx, float& dy, float& dz) {
+    dx = __fadd_rn(__fsub_rn(phx, ch.x), __fsub_rn(plx, cl.x));
+    dy = __fadd_rn(__fsub_rn(phy, ch.y), __fsub_rn(ply, cl.y));
+    dz = __fadd_rn(__fsub_rn(phz, ch.z), __fsub_rn(plz, cl.z));
+    return __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+}
+
+__device__ __forceinline__ void split2f(double x, float& hi, float& lo) {
+    hi = __double2float_rn(x);
+    lo = __double2float_rn(x - (double)hi);
+}
 
 __device__ __forceinline__ void nodes_f32(const float4* __restrict__ nd, int m, float dx, float dy, float dz,
                                           float& ph, float& ex, float& ey, float& ez) {
@@ -47,16 +70,14 @@ __device__ __forceinline__ void nodes_f32(const float4* __restrict__ nd, int m, 
     }
 }
 
-__global__ void __launch_bounds__(kMT) k_eval_mixed(const Elem* __restrict__ el, const FarNodes* __restrict__ far,
-                                                    const double* __restrict__ sigma, int64_t n_el,
-                                                    const ImageTable img, int tile_el,
-                                                    const double* __restrict__ pts, int64_t npts,
-                                                    double* __restrict__ phi, double* __restrict__ E) {
-    __shared__ Elem s_el[kTileMax];
+__global__ void __launch_bounds__(kMT, 8) k_eval_far(const FarNodes* __restrict__ far, const float4* __restrict__ cjk,
+                                                  const double* __restrict__ sigma, int64_t n_el, int nimg,
+                                                  int tile_el, const double* __restrict__ pts, int64_t npts,
+                                                  double* __restrict__ phi, double* __restrict__ E) {
     __shared__ float4 s_a[kTileMax][kNodesA];
     __shared__ float4 s_hdr[kTileMax];
     __shared__ float s_sig[kTileMax];
-    __shared__ float s_c[kCjkMax][6];  // image centroids: hi.xyz, lo.xyz
+    __shared__ float4 s_c[kCjkMax][2];  // image centroids: hi, lo
 
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = p < npts;
@@ -66,83 +87,47 @@ __global__ void __launch_bounds__(kMT) k_eval_mixed(const Elem* __restrict__ el,
         Py = pts[3 * p + 1];
         Pz = pts[3 * p + 2];
     }
-    const float phx = (float)Px, phy = (float)Py, phz = (float)Pz;
-    const float plx = (float)(Px - (double)phx), ply = (float)(Py - (double)phy), plz = (float)(Pz - (double)phz);
-    const int nimg = img.n;
+    float phx, phy, phz, plx, ply, plz;
+    split2f(Px, phx, plx);
+    split2f(Py, phy, ply);
+    split2f(Pz, phz, plz);
 
     double aphi = 0.0, aEx = 0.0, aEy = 0.0, aEz = 0.0;
     for (int64_t base = 0; base < n_el; base += tile_el) {
         const int cnt = (int)min((int64_t)tile_el, n_el - base);
         __syncthreads();
-        {
-            const double2* src = reinterpret_cast<const double2*>(el + base);
-            double2* dst = reinterpret_cast<double2*>(s_el);
-            for (int i = threadIdx.x; i < cnt * 16; i += blockDim.x) dst[i] = src[i];
-            for (int i = threadIdx.x; i < cnt * kNodesA; i += blockDim.x)
-                s_a[i / kNodesA][i % kNodesA] = far[base + i / kNodesA].a[i % kNodesA];
-            for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-                s_hdr[i] = far[base + i].hdr;
-                s_sig[i] = (float)sigma[base + i];
-            }
-            for (int i = threadIdx.x; i < cnt * nimg; i += blockDim.x) {
-                const int jj = i / nimg, k = i % nimg;
-                const Elem& e = el[base + jj];
-                const double cx = e.c[0] + img.t[k][0];
-                const double cy = e.c[1] + img.t[k][1];
-                const double cz = e.c[2] + img.t[k][2];
-                const float hx = (float)cx, hy = (float)cy, hz = (float)cz;
-                s_c[i][0] = hx;
-                s_c[i][1] = hy;
-                s_c[i][2] = hz;
-                s_c[i][3] = (float)(cx - (double)hx);
-                s_c[i][4] = (float)(cy - (double)hy);
-                s_c[i][5] = (float)(cz - (double)hz);
-            }
+        for (int i = threadIdx.x; i < cnt * kNodesA; i += blockDim.x)
+            s_a[i / kNodesA][i % kNodesA] = far[base + i / kNodesA].a[i % kNodesA];
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            s_hdr[i] = far[base + i].hdr;
+            s_sig[i] = (float)sigma[base + i];
         }
+        const float4* src = cjk + 2 * base * nimg;
+        for (int i = threadIdx.x; i < 2 * cnt * nimg; i += blockDim.x) s_c[i >> 1][i & 1] = src[i];
         __syncthreads();
         float gphi = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
         for (int jj = 0; jj < cnt; ++jj) {
             const float4 hdr = s_hdr[jj];
             const int n_a = (int)hdr.w;
+            const FarNodes* fj = far + base + jj;
             float lphi = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
-            double nphi = 0.0, nlx = 0.0, nly = 0.0, nlz = 0.0;  // FP64 near pairs, local frame
-            bool any_near = false;
             for (int k = 0; k < nimg; ++k) {
-                const float* C = s_c[jj * nimg + k];
-                const float dx = (phx - C[0]) + (plx - C[3]);
-                const float dy = (phy - C[1]) + (ply - C[4]);
-                const float dz = (phz - C[2]) + (plz - C[5]);
-                const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (d2 >= hdr.x) {
+                float dx, dy, dz;
+                const float d2 = pair_d2(phx, phy, phz, plx, ply, plz, s_c[jj * nimg + k][0], s_c[jj * nimg + k][1],
+                                         dx, dy, dz);
+                if (d2 >= hdr.x)
                     nodes_f32(s_a[jj], n_a, dx, dy, dz, lphi, lx, ly, lz);
-                } else if (d2 >= hdr.y) {
-                    nodes_f32(far[base + jj].b, kNodesB, dx, dy, dz, lphi, lx, ly, lz);
-                } else if (d2 >= hdr.z) {
-                    nodes_f32(far[base + jj].c, kNodesC, dx, dy, dz, lphi, lx, ly, lz);
-                } else {
-                    double f, ux, uy, uz;
-                    elem_local_f64(s_el[jj], Px - img.t[k][0], Py - img.t[k][1], Pz - img.t[k][2], false, f, ux, uy,
-                                   uz);
-                    nphi += f;
-                    nlx += ux;
-                    nly += uy;
-                    nlz += uz;
-                    any_near = true;
-                }
+                else if (d2 >= hdr.y)
+                    nodes_f32(fj->b, kNodesB, dx, dy, dz, lphi, lx, ly, lz);
+                else if (d2 >= hdr.z)
+                    nodes_f32(fj->c, kNodesC, dx, dy, dz, lphi, lx, ly, lz);
+                // nearer pairs: k_eval_near
             }
             const float s = s_sig[jj];
             gphi = fmaf(s, lphi, gphi);
             gx = fmaf(s, lx, gx);
             gy = fmaf(s, ly, gy);
             gz = fmaf(s, lz, gz);
-            if (any_near) {
-                const Elem& e = s_el[jj];
-                const double sd = sigma[base + jj];
-                aphi = fma(sd, nphi, aphi);
-                aEx = fma(sd, fma(nlx, e.ex[0], fma(nly, e.ey[0], nlz * e.ez[0])), aEx);
-                aEy = fma(sd, fma(nlx, e.ex[1], fma(nly, e.ey[1], nlz * e.ez[1])), aEy);
-                aEz = fma(sd, fma(nlx, e.ex[2], fma(nly, e.ey[2], nlz * e.ez[2])), aEz);
-            }
             if ((jj % kGroup) == kGroup - 1 || jj == cnt - 1) {
                 aphi += (double)gphi;
                 aEx += (double)gx;
@@ -163,15 +148,98 @@ __global__ void __launch_bounds__(kMT) k_eval_mixed(const Elem* __restrict__ el,
     }
 }
 
+__global__ void __launch_bounds__(kMT) k_eval_near(const Elem* __restrict__ el, const FarNodes* __restrict__ far,
+                                                   const float4* __restrict__ cjk, const double* __restrict__ sigma,
+                                                   int nimg, const ImageTable img, const NearGrid grid,
+                                                   const int32_t* __restrict__ cell_start,
+                                                   const int32_t* __restrict__ cell_items,
+                                                   const double* __restrict__ pts, int64_t npts,
+                                                   double* __restrict__ phi, double* __restrict__ E) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npts) return;
+    const double Px = pts[3 * p], Py = pts[3 * p + 1], Pz = pts[3 * p + 2];
+    float phx, phy, phz, plx, ply, plz;
+    split2f(Px, phx, plx);
+    split2f(Py, phy, ply);
+    split2f(Pz, phz, plz);
+    // cell of the point, clamped (a point more than one cell outside has no near pair)
+    int cc[3];
+    const double P[3] = {Px, Py, Pz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double f = floor((P[a] - grid.origin[a]) * grid.inv_h);
+        f = fmin(fmax(f, -2.0), (double)grid.dims[a] + 1.0);
+        cc[a] = (int)f;
+    }
+    double aphi = 0.0, aEx = 0.0, aEy = 0.0, aEz = 0.0;
+    bool any = false;
+    for (int z = max(cc[2] - 1, 0); z <= min(cc[2] + 1, grid.dims[2] - 1); ++z)
+        for (int y = max(cc[1] - 1, 0); y <= min(cc[1] + 1, grid.dims[1] - 1); ++y)
+            for (int x = max(cc[0] - 1, 0); x <= min(cc[0] + 1, grid.dims[0] - 1); ++x) {
+                const int64_t cell = ((int64_t)z * grid.dims[1] + y) * grid.dims[0] + x;
+                for (int32_t it = cell_start[cell]; it < cell_start[cell + 1]; ++it) {
+                    const int32_t jk = cell_items[it];
+                    const int32_t j = jk / nimg, k = jk - j * nimg;
+                    float dx, dy, dz;
+                    const float d2 = pair_d2(phx, phy, phz, plx, ply, plz, cjk[2 * (int64_t)jk], cjk[2 * (int64_t)jk + 1],
+                                             dx, dy, dz);
+                    if (!(d2 < far[j].hdr.z)) continue;
+                    const Elem& e = el[j];
+                    double f, ux, uy, uz;
+                    elem_local_f64(e, Px - img.t[k][0], Py - img.t[k][1], Pz - img.t[k][2], false, f, ux, uy, uz);
+                    const double s = sigma[j];
+                    aphi = fma(s, f, aphi);
+                    aEx = fma(s, fma(ux, e.ex[0], fma(uy, e.ey[0], uz * e.ez[0])), aEx);
+                    aEy = fma(s, fma(ux, e.ex[1], fma(uy, e.ey[1], uz * e.ez[1])), aEy);
+                    aEz = fma(s, fma(ux, e.ex[2], fma(uy, e.ey[2], uz * e.ez[2])), aEz);
+                    any = true;
+                }
+            }
+    if (!any) return;
+    const double ke = 1.0 / (4.0 * kPi * kEps0);
+    if (phi) phi[p] += ke * aphi;
+    if (E) {
+        E[3 * p] += ke * aEx;
+        E[3 * p + 1] += ke * aEy;
+        E[3 * p + 2] += ke * aEz;
+    }
+}
+
+// Two-float image centroids, entry (j, k) at 2 * (j * nimg + k): hi then lo.
+__global__ void k_image_centroids(const Elem* __restrict__ el, int64_t n, const ImageTable img,
+                                  float4* __restrict__ cjk) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * img.n) return;
+    const int64_t j = i / img.n;
+    const int k = (int)(i - j * img.n);
+    float h[3], l[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) split2f(el[j].c[a] + img.t[k][a], h[a], l[a]);
+    cjk[2 * i] = make_float4(h[0], h[1], h[2], 0.f);
+    cjk[2 * i + 1] = make_float4(l[0], l[1], l[2], 0.f);
+}
+
 }  // namespace
 
-cudaError_t launch_eval_mixed(const Elem* el, const FarNodes* far, const double* sigma, int64_t n_el,
-                              const ImageTable& img, const double* pts, int64_t npts, double* phi, double* E,
+cudaError_t launch_image_centroids(const Elem* el, int64_t n, const ImageTable& img, float4* cjk, cudaStream_t s) {
+    const int64_t total = n * img.n;
+    if (total == 0) return cudaSuccess;
+    k_image_centroids<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(el, n, img, cjk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval_mixed(const Elem* el, const FarNodes* far, const float4* cjk, const double* sigma,
+                              int64_t n_el, const ImageTable& img, const NearGrid& grid, const int32_t* cell_start,
+                              const int32_t* cell_items, const double* pts, int64_t npts, double* phi, double* E,
                               cudaStream_t s) {
     if (npts == 0) return cudaSuccess;
     const int tile_el = max(1, min(kTileMax, kCjkMax / img.n));
-    const int64_t blocks = (npts + kMT - 1) / kMT;
-    k_eval_mixed<<<(unsigned)blocks, kMT, 0, s>>>(el, far, sigma, n_el, img, tile_el, pts, npts, phi, E);
+    const unsigned blocks = (unsigned)((npts + kMT - 1) / kMT);
+    k_eval_far<<<blocks, kMT, 0, s>>>(far, cjk, sigma, n_el, img.n, tile_el, pts, npts, phi, E);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_eval_near<<<blocks, kMT, 0, s>>>(el, far, cjk, sigma, img.n, img, grid, cell_start, cell_items, pts, npts, phi,
+                                       E);
     return cudaGetLastError();
 }
 

@@ -207,6 +207,60 @@ int build_element(const nebem_element& r, const nebem_options& opt, Elem& e, dou
     return NEBEM_OK;
 }
 
+int build_near_grid(const std::vector<Elem>& el, const ImageTable& img, double ratio_near, NearGrid& grid,
+                    std::vector<int32_t>& cell_start, std::vector<int32_t>& cell_items, std::string& why) {
+    const int64_t n = (int64_t)el.size(), m = img.n, total = n * m;
+    if (total > (int64_t)INT32_MAX) {
+        why = "too many element images for the near-pair grid";
+        return NEBEM_TOO_LARGE;
+    }
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, rmax = 0.0;
+    std::vector<double> C((size_t)total * 3);
+    for (int64_t j = 0; j < n; ++j) {
+        rmax = std::fmax(rmax, ratio_near * el[j].rho);
+        for (int64_t k = 0; k < m; ++k)
+            for (int a = 0; a < 3; ++a) {
+                const double v = el[j].c[a] + img.t[k][a];
+                C[(j * m + k) * 3 + a] = v;
+                lo[a] = std::fmin(lo[a], v);
+                hi[a] = std::fmax(hi[a], v);
+            }
+    }
+    double h = 1.01 * rmax;
+    if (!(h > 0.0)) h = 1.0;
+    // bound the cell count (16M); larger cells only cost more candidates per query
+    for (;;) {
+        double cells = 1.0;
+        for (int a = 0; a < 3; ++a) cells *= std::floor((hi[a] - lo[a]) / h) + 3.0;
+        if (cells <= 16.0e6) break;
+        h *= 1.5;
+    }
+    grid.inv_h = 1.0 / h;
+    for (int a = 0; a < 3; ++a) {
+        grid.origin[a] = lo[a] - h;
+        grid.dims[a] = (int32_t)std::floor((hi[a] - grid.origin[a]) * grid.inv_h) + 2;
+    }
+    grid.pad = 0;
+    const int64_t ncell = (int64_t)grid.dims[0] * grid.dims[1] * grid.dims[2];
+    std::vector<int32_t> cell_of((size_t)total);
+    cell_start.assign((size_t)ncell + 1, 0);
+    for (int64_t i = 0; i < total; ++i) {
+        int64_t cc[3];
+        for (int a = 0; a < 3; ++a) {
+            const double f = std::floor((C[i * 3 + a] - grid.origin[a]) * grid.inv_h);
+            cc[a] = (int64_t)std::fmin(std::fmax(f, 0.0), (double)grid.dims[a] - 1.0);
+        }
+        const int64_t cell = (cc[2] * grid.dims[1] + cc[1]) * grid.dims[0] + cc[0];
+        cell_of[i] = (int32_t)cell;
+        cell_start[cell + 1]++;
+    }
+    for (int64_t c = 0; c < ncell; ++c) cell_start[c + 1] += cell_start[c];
+    cell_items.assign((size_t)total, 0);
+    std::vector<int32_t> fillp(cell_start.begin(), cell_start.end() - 1);
+    for (int64_t i = 0; i < total; ++i) cell_items[fillp[cell_of[i]]++] = (int32_t)i;  // stable: ascending j*m+k
+    return NEBEM_OK;
+}
+
 int build_images(const double* lattice, int lo, int hi, ImageTable& img, std::string& why) {
     std::memset(&img, 0, sizeof(img));
     if (!lattice) {

@@ -1,6 +1,7 @@
 // geometry.h -- host-side element-table construction (see geometry.cpp).
 #pragma once
 #include <string>
+#include <vector>
 
 #include "nb_internal.h"
 
@@ -14,6 +15,11 @@ int build_element(const nebem_element& r, const nebem_options& opt, Elem& e, dou
 
 // Gauss-Legendre nodes and weights on [0, 1] (m <= 16), by Newton iteration on P_m.
 void gauss_legendre01(int m, double* x, double* w);
+
+// Cell list of the image centroids c_j + t_k (entry j * nimg + k) for the near-pair search;
+// near radius of element j = ratio_near * rho_j.  Cells in x-fastest order, CSR form.
+int build_near_grid(const std::vector<Elem>& el, const ImageTable& img, double ratio_near, NearGrid& grid,
+                    std::vector<int32_t>& cell_start, std::vector<int32_t>& cell_items, std::string& why);
 
 // Image translations t = k1 a1 + k2 a2, index (k1-lo)*m + (k2-lo); lattice NULL -> one
 // zero translation.

@@ -52,21 +52,25 @@ struct ImageTable {
     double t[kMaxImg][3];
 };
 
-// Per-element charge-weighted data used by the eval kernels.
-struct EvalTables {
-    const Elem* el;
-    const FarNodes* far;
-    const double* sigma;
-    int64_t n;
+// Uniform grid over the image centroids for the near-pair search of the mixed
+// evaluation: cell (x, y, z) = floor((c - origin) * inv_h), edge h >= 1.01 x the largest
+// near radius, so every near pair of a point lies in its cell or the 26 neighbours.
+struct NearGrid {
+    double origin[3];
+    double inv_h;
+    int32_t dims[3];
+    int32_t pad;
 };
 
 // ------------------------------------------------------------------ launchers (.cu)
 // Each returns cudaSuccess or the launch error.
 cudaError_t launch_eval_f64(const Elem* el, const double* sigma, int64_t n_el, const ImageTable& img,
                             const double* pts, int64_t npts, double* phi, double* E, cudaStream_t s);
-cudaError_t launch_eval_mixed(const Elem* el, const FarNodes* far, const double* sigma, int64_t n_el,
-                              const ImageTable& img, const double* pts, int64_t npts, double* phi, double* E,
+cudaError_t launch_eval_mixed(const Elem* el, const FarNodes* far, const float4* cjk, const double* sigma,
+                              int64_t n_el, const ImageTable& img, const NearGrid& grid, const int32_t* cell_start,
+                              const int32_t* cell_items, const double* pts, int64_t npts, double* phi, double* E,
                               cudaStream_t s);
+cudaError_t launch_image_centroids(const Elem* el, int64_t n, const ImageTable& img, float4* cjk, cudaStream_t s);
 cudaError_t launch_fill_f64(const Elem* el, const double* diag, int64_t n, const ImageTable& img, double* K,
                             cudaStream_t s);
 cudaError_t launch_element_influence(const Elem* el, int64_t n_el, const double* pts, int64_t npts,

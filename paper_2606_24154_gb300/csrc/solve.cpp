@@ -156,8 +156,9 @@ int solve_with_factors(Ctx* c, int precision, nebem_solve_info* info) {
 
 int eval_elements(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision, cudaStream_t s) {
     if (precision == NEBEM_MIXED)
-        CK(launch_eval_mixed(c->d_el.as<Elem>(), c->d_far.as<FarNodes>(), c->d_sigma.as<double>(), c->n, c->img,
-                             d_pts, n, d_phi, d_E, s));
+        CK(launch_eval_mixed(c->d_el.as<Elem>(), c->d_far.as<FarNodes>(), c->d_cjk.as<float4>(),
+                             c->d_sigma.as<double>(), c->n, c->img, c->grid, c->d_cell_start.as<int32_t>(),
+                             c->d_cell_items.as<int32_t>(), d_pts, n, d_phi, d_E, s));
     else
         CK(launch_eval_f64(c->d_el.as<Elem>(), c->d_sigma.as<double>(), c->n, c->img, d_pts, n, d_phi, d_E, s));
     return 0;
