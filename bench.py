@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--points", type=int, default=N_POINTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=40)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--workload", default="thgem_eval",
+                    choices=["thgem_eval", "double_thgem_solve", "space_charge"])
     return ap.parse_args()
 
 
@@ -163,6 +167,41 @@ def run_reference(args):
     return 0
 
 
+def serving_run(N, ctxs, geoms, n_req, scale, precision, seed):
+    """Replay a seeded Poisson trace (2000 requests/s, sizes log-uniform in [1e2, 1e6]
+    times `scale`, geometry uniform over the resident contexts) through the server;
+    returns p50/p99 latency (submit -> outputs in host memory) and points/s."""
+    from paper_2606_24154_gb300 import inputs as I
+    t_arr, sizes, geo = I.serving_trace(n_req, I.rng(4, seed), n_geometries=len(ctxs))
+    sizes = np.maximum(1, (sizes * scale).astype(np.int64))
+    reqs = []
+    for k in range(n_req):
+        g = geoms[geo[k]]
+        pts = np.ascontiguousarray(I.cell_points(g, int(sizes[k]), I.rng(4, 1000 + k)))
+        reqs.append((pts, np.empty(pts.shape[0]), np.empty((pts.shape[0], 3))))
+    srv = N.nebem_server_create([c.h for c in ctxs])
+    ids = [None] * n_req
+    done = [False] * n_req
+    t0 = time.perf_counter()
+    i = 0
+    while i < n_req or not all(done):
+        now = time.perf_counter() - t0
+        while i < n_req and t_arr[i] <= now:
+            ids[i] = N.nebem_server_submit(srv, int(geo[i]), reqs[i][0], reqs[i][1], reqs[i][2], precision)
+            i += 1
+        for k in range(i):
+            if not done[k]:
+                done[k] = N.nebem_server_poll(srv, ids[k])
+        time.sleep(50e-6)
+    times = np.array([N.nebem_server_request_times(srv, r) for r in ids])
+    N.nebem_server_destroy(srv)
+    lat = (times[:, 2] - times[:, 0]) * 1e3
+    span = times[:, 2].max() - times[:, 0].min()
+    return {"requests": n_req, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "points_per_s": float(sizes.sum() / span), "points": int(sizes.sum()), "makespan_s": float(span),
+            "size_scale": scale}
+
+
 def run_native(args):
     import torch
     import torch.distributed as dist
@@ -269,6 +308,36 @@ def run_native(args):
             e2e_times.append(time.perf_counter() - t)
     e2e_val = evals * world / statistics.mean(e2e_times)
 
+    # ---- solve of the same geometry: mixed (FP32 LU + FP64 refinement) vs plain FP64
+    solve = {}
+    for name, prec in (("mixed", N.NEBEM_MIXED), ("fp64", N.NEBEM_FP64)):
+        c2 = N.Context(device=local).set_geometry(g)
+        _, inf, _ = c2.solve(prec)
+        solve[name] = {"ms_fill": inf.ms_fill, "ms_factor": inf.ms_factor, "ms_solve": inf.ms_solve,
+                       "refinement_iterations": inf.iterations}
+        c2.close()
+
+    # ---- serving: configs 0-2 resident (cube, THGEM cell, double THGEM), continuous batching
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        from paper_2606_24154_gb300 import inputs as I
+        geoms = [I.cube(), g, I.double_thgem()]
+        sctx = [N.Context(device=local).set_geometry(geoms[0]), ctx, N.Context(device=local).set_geometry(geoms[2])]
+        t = time.perf_counter()
+        sctx[0].solve(N.NEBEM_MIXED)
+        _, inf2, _ = sctx[2].solve(N.NEBEM_MIXED)
+        setup = time.perf_counter() - t
+        serving = {"trace": "Poisson 2000/s, sizes log-uniform 1e2..1e6, geometry uniform over 3 resident",
+                   "mixed": serving_run(N, sctx, geoms, args.serving_requests, 1.0, N.NEBEM_MIXED, 0),
+                   "mixed_small": serving_run(N, sctx, geoms, 20, 0.01, N.NEBEM_MIXED, 1),
+                   "fp64_small": serving_run(N, sctx, geoms, 20, 0.01, N.NEBEM_FP64, 1),
+                   "double_thgem_solve": {"elements": geoms[2].n, "ms_fill": inf2.ms_fill,
+                                          "ms_factor_fp32": inf2.ms_factor, "ms_refine": inf2.ms_solve,
+                                          "iterations": inf2.iterations, "correction": inf2.correction},
+                   "setup_s": setup}
+        sctx[0].close()
+        sctx[2].close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, dt = oracle_rate(g, pts_h, ORACLE_SAMPLE)
@@ -295,6 +364,8 @@ def run_native(args):
                          "note": "FP32 lane ops (Gauss nodes x 13 + pairs x 9) per launch / event time; peak = "
                                  "152 SMs x 128 lanes x max SM clock"},
             "tiers": counts,
+            "solve_thgem": solve,
+            "serving": serving,
             "e2e": {"value": e2e_val, "unit": "evals/s", "h2d_bytes_per_step": int(pts_pin.numel() * 8),
                     "d2h_bytes_per_step": int((phi_pin.numel() + E_pin.numel()) * 8)},
             "cpu_baseline": cpu,
@@ -310,10 +381,85 @@ def run_native(args):
     return 0
 
 
+def run_double_thgem_solve(args):
+    """Double THGEM (40,368 elements, 25 images): FP64 fill, then the mixed solve (FP32
+    LU + FP64 refinement to 1e-8) against the plain FP64 LU; one step = one full solve."""
+    import torch
+
+    from paper_2606_24154_gb300 import build as B
+    from paper_2606_24154_gb300 import inputs as I
+    from paper_2606_24154_gb300 import nebem as N
+    B.build()
+    g = I.double_thgem()
+    res = {"mixed": [], "fp64": None}
+    sig_m = None
+    for step in range(max(1, args.steps)):
+        c = N.Context().set_geometry(g)
+        t = time.perf_counter()
+        sig_m, inf, _ = c.solve(N.NEBEM_MIXED)
+        res["mixed"].append({"wall_s": time.perf_counter() - t, "ms_fill": inf.ms_fill, "ms_factor": inf.ms_factor,
+                             "ms_refine": inf.ms_solve, "iterations": inf.iterations,
+                             "correction": inf.correction})
+        c.close()
+    c = N.Context().set_geometry(g)
+    t = time.perf_counter()
+    sig_d, inf, _ = c.solve(N.NEBEM_FP64)
+    res["fp64"] = {"wall_s": time.perf_counter() - t, "ms_fill": inf.ms_fill, "ms_factor": inf.ms_factor,
+                   "ms_solve": inf.ms_solve}
+    c.close()
+    err = float(np.abs(sig_m - sig_d).max() / np.abs(sig_d).max())
+    n = g.n
+    best = min(r["ms_factor"] for r in res["mixed"])
+    line = {"metric": "double THGEM solve: FP32 LU + FP64 refinement vs FP64 LU", "workload":
+            f"double_thgem N={n} images={g.n_images}", "value": (2.0 / 3.0) * n ** 3 / (best * 1e-3) / 1e12,
+            "unit": "TFLOP/s (FP32 LU, 2/3 N^3)", "sigma_rel_err_mixed_vs_fp64": err,
+            "fp64_lu_tflops": (2.0 / 3.0) * n ** 3 / (res["fp64"]["ms_factor"] * 1e-3) / 1e12, "runs": res,
+            "fill_evals_per_s": n * n * g.n_images / (res["fp64"]["ms_fill"] * 1e-3)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_space_charge(args):
+    """Dynamic space charge on the THGEM cell: 1e6 point carriers (Gaussian cloud, sigma
+    0.1 mm, half ions), per step: known-charge RHS at the collocation points, solve with
+    the retained factors, E at every carrier from all elements (images) and all other
+    carriers, drift x += sign(q) mu E dt (mu = 1e-4 m^2/Vs, dt = 1 ns)."""
+    from paper_2606_24154_gb300 import build as B
+    from paper_2606_24154_gb300 import inputs as I
+    from paper_2606_24154_gb300 import nebem as N
+    B.build()
+    g = I.thgem()
+    n_car = args.points
+    pos, q = I.carrier_cloud(g, n_car, I.rng(3, 0))
+    out = {}
+    for name, prec in (("mixed", N.NEBEM_MIXED),):
+        c = N.Context().set_geometry(g)
+        c.solve(prec)
+        N.nebem_space_charge(c.h, pos, q, 1e-6)
+        N.nebem_step(c.h, max(1, args.warmup), 1e-4, 1e-9, prec, n_car)
+        N.nebem_space_charge(c.h, pos, q, 1e-6)
+        t = time.perf_counter()
+        N.nebem_step(c.h, args.steps, 1e-4, 1e-9, prec, n_car)
+        dt = (time.perf_counter() - t) / args.steps
+        pairs = n_car * (n_car - 1) + g.n * n_car
+        out[name] = {"s_per_step": dt, "carrier_pairs_per_s": pairs / dt,
+                     "element_evals_per_s": n_car * g.n * g.n_images / dt}
+        c.close()
+    line = {"metric": "dynamic space-charge step time", "workload": f"thgem_cell N={g.n} carriers={n_car}",
+            "value": out["mixed"]["s_per_step"], "unit": "s/step", "higher_is_better": False, "steps": args.steps,
+            "detail": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "double_thgem_solve":
+        return run_double_thgem_solve(args)
+    if args.workload == "space_charge":
+        return run_space_charge(args)
     return run_native(args)
 
 

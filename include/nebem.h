@@ -179,6 +179,12 @@ int nebem_get_sigma(nebem_ctx *ctx, double *sigma_out, int64_t n);
  * column-major order, K_out[i + j*n] = K_ij.  K_out may be NULL (device copy only). */
 int nebem_fill(nebem_ctx *ctx, int32_t precision, double *K_out);
 
+/* Gather entries of the current influence matrix (filled on demand as nebem_fill does):
+ * out[e] = K[rows[e], cols[e]] for e < count (host arrays; indices 0 <= r, c < n).  For
+ * checks of matrices too large to copy whole.  Errors: NEBEM_BAD_STATE (no geometry),
+ * NEBEM_INVALID_ARG (index out of range). */
+int nebem_matrix_entries(nebem_ctx *ctx, const int64_t *rows, const int64_t *cols, int64_t count, double *out);
+
 /* Potential and field at points (Eq. Potential and Eq. Field with the element charge
  * densities; Sec. 4.1 PFAtPoint = element part + known-charge part): phi(x) =
  * ke sum_j sigma_j sum_k Phi'(x; j + t_k) [+ ke sum_c q_c / sqrt(r^2 + s^2) when a

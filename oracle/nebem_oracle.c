@@ -315,6 +315,41 @@ int or_fill(const or_input *in, int64_t n, const double *lattice, int lo, int hi
     return 0;
 }
 
+/* Selected entries K[rows[e], cols[e]] of the influence matrix (same definition as
+ * or_fill), for checks of full-size matrices one entry at a time. */
+int or_fill_entries(const or_input *in, int64_t n, const double *lattice, int lo, int hi, const int64_t *rows,
+                    const int64_t *cols, int64_t count, double *out) {
+    or_elem *el = (or_elem *)malloc(sizeof(or_elem) * (size_t)(n ? n : 1));
+    int rc = or_build(in, n, el);
+    if (rc) {
+        free(el);
+        return rc;
+    }
+    int64_t nimg = image_count(lattice, lo, hi);
+    double *tt = (double *)malloc(sizeof(double) * 3 * (size_t)nimg);
+    or_image_table(lattice, lo, hi, tt);
+    int64_t kzero = lattice ? (int64_t)(0 - lo) * (hi - lo + 1) + (0 - lo) : 0;
+    double ke = or_ke();
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t e = 0; e < count; ++e) {
+        int64_t i = rows[e], j = cols[e];
+        const or_elem *ei = &el[i];
+        double acc = 0.0;
+        for (int64_t k = 0; k < nimg; ++k) {
+            double P[3] = {ei->c[0] - tt[3 * k], ei->c[1] - tt[3 * k + 1], ei->c[2] - tt[3 * k + 2]};
+            double phi, E[3];
+            or_influence(&el[j], P, (i == j && k == kzero), &phi, E);
+            acc += (ei->bc == 0) ? phi : dot3(ei->ey, E);
+        }
+        double v = ke * acc;
+        if (i == j && ei->bc == 1) v += (ei->eps_a + ei->eps_b) / (2.0 * OR_EPS0 * (ei->eps_b - ei->eps_a));
+        out[e] = v;
+    }
+    free(tt);
+    free(el);
+    return 0;
+}
+
 /* In-place LU with partial pivoting (row of max |a|, lowest index on ties), column-major.
  * piv[k] = row swapped with row k at step k.  Returns 0 or -(1+k) for a zero pivot. */
 int or_lu_factor(int64_t n, double *A, int32_t *piv) {

@@ -49,6 +49,8 @@ def lib():
         L.or_image_table.argtypes = [_d, C.c_int, C.c_int, _d]
         L.or_image_table.restype = C.c_int64
         L.or_fill.argtypes = [_vp, C.c_int64, _d, C.c_int, C.c_int, _d]
+        L.or_fill_entries.argtypes = [_vp, C.c_int64, _d, C.c_int, C.c_int, C.POINTER(C.c_int64),
+                                      C.POINTER(C.c_int64), C.c_int64, _d]
         L.or_lu_factor.argtypes = [C.c_int64, _d, _i32]
         L.or_lu_solve.argtypes = [C.c_int64, _d, _i32, _d]
         L.or_rhs.argtypes = [_vp, C.c_int64, _d, C.c_int32, _d]
@@ -126,6 +128,19 @@ def fill(g):
     lat = _lat(g)
     _check(lib().or_fill(pe, n, _p(lat), g.img_lo, g.img_hi, _p(K)), "fill")
     return K.reshape(n, n).T.copy()  # column-major storage -> K[i, j]
+
+
+def fill_entries(g, rows, cols):
+    """K[rows[e], cols[e]] computed entry by entry (full-size checks)."""
+    el, pe = _rec(g.elements)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    cols = np.ascontiguousarray(cols, dtype=np.int64)
+    out = np.empty(rows.shape[0])
+    lat = _lat(g)
+    i64 = C.POINTER(C.c_int64)
+    _check(lib().or_fill_entries(pe, el.shape[0], _p(lat), g.img_lo, g.img_hi, rows.ctypes.data_as(i64),
+                                 cols.ctypes.data_as(i64), rows.shape[0], _p(out)), "fill_entries")
+    return out
 
 
 def lu_factor(K):

@@ -246,6 +246,31 @@ int nebem_fill(nebem_ctx* ctx, int32_t precision, double* K_out) {
     return NEBEM_OK;
 }
 
+int nebem_matrix_entries(nebem_ctx* ctx, const int64_t* rows, const int64_t* cols, int64_t count, double* out) {
+    if (!ctx || count < 0 || (count > 0 && (!rows || !cols || !out))) return fail(NEBEM_INVALID_ARG, "bad argument");
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (c->n == 0) return fail(NEBEM_BAD_STATE, "set_geometry first");
+    for (int64_t e = 0; e < count; ++e)
+        if (rows[e] < 0 || rows[e] >= c->n || cols[e] < 0 || cols[e] >= c->n)
+            return fail(NEBEM_INVALID_ARG, "entry index out of range");
+    if (count == 0) return NEBEM_OK;
+    CK(cudaSetDevice(c->device));
+    int rc = ensure_fill(c, nullptr);
+    if (rc) return rc;
+    DevBuf idx, val;
+    CK(idx.ensure(sizeof(int64_t) * count));
+    CK(val.ensure(sizeof(double) * count));
+    std::vector<int64_t> lin((size_t)count);
+    for (int64_t e = 0; e < count; ++e) lin[e] = rows[e] + cols[e] * c->n;
+    CK(cudaMemcpyAsync(idx.ptr, lin.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_gather(c->d_K.as<double>(), idx.as<int64_t>(), count, val.as<double>(), c->stream));
+    CK(cudaMemcpyAsync(out, val.ptr, sizeof(double) * count, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    idx.release();
+    val.release();
+    return NEBEM_OK;
+}
+
 int nebem_solve(nebem_ctx* ctx, int32_t precision, double* sigma_out, nebem_solve_info* info) {
     if (!ctx) return fail(NEBEM_INVALID_ARG, "ctx is NULL");
     if (precision != NEBEM_FP64 && precision != NEBEM_MIXED) return fail(NEBEM_INVALID_ARG, "bad precision");

@@ -1,0 +1,276 @@
+// eval_blocks.cuh -- per-block evaluation bodies shared by the standalone evaluation
+// kernels (eval_f64.cu, eval_mixed.cu) and the serving kernel (server.cu): one thread per
+// target, `count` <= blockDim.x targets starting at `pts`.  Using the same functions in
+// both places makes a point's result identical whichever launch evaluates it.
+//
+// Mixed precision.
+//
+// Same sums as the FP64 kernel (Eq. Potential / Eq. Field over elements and periodic
+// images), but each (point, element, image) pair picks its arithmetic by its distance d
+// to the image centroid, in units of the element's circumradius rho:
+//   d >= ratio_a rho      FP32 Gauss rule, tier a (6 nodes triangle / 9 rectangle)
+//   d >= ratio_b rho      FP32 Gauss rule, tier b (16 nodes)
+//   d >= ratio_near rho   FP32 Gauss rule, tier c (36 nodes)
+//   nearer                FP64 closed form (influence.cuh), where ln/atan cancel
+// Quadrature per node: Phi += w / r, E += w (P - x_n) / r^3 with one rsqrt.
+//
+// Two kernels: k_eval_far runs every FP32 tier over all (element, image) pairs and skips
+// near pairs; k_eval_near visits only the image centroids in the 27 grid cells around
+// each point (a cell list built per geometry, cell edge >= the largest near radius) and
+// adds the near pairs' FP64 closed forms.  Keeping the FP64 code out of the far kernel
+// keeps its register count (and so its occupancy) at the FP32 kernel's level.  Both
+// kernels decide "near" with the same rounded FP32 operations (pair_d2) on the same
+// inputs, so every pair is counted exactly once.
+//
+// The FP32 difference P - x_n keeps its relative accuracy even when P and the node are
+// millimetres from the origin but micrometres apart: both sides are held as two floats
+// (hi + lo) and (P_hi - C_hi) + (P_lo - C_lo) is formed first, C = c_j + t_k being the
+// image centroid (FP64 sum split once per geometry).  Node offsets from the centroid are
+// small, so the remaining FP32 operations carry ~1e-7 relative error.
+//
+// Accumulation: per element over its images in FP32, weighted by sigma_j, summed in FP32
+// over groups of kGroup elements and flushed to FP64.  Every decision depends only on the
+// pair, and each point's sums run in a fixed order, so a point's result is bit-identical
+// whatever other points share its launch.
+#pragma once
+#include "influence.cuh"
+
+namespace nb {
+
+constexpr int kEvalThreads = 128;  // threads per block (one target each)
+constexpr int kTileMax = 16;       // elements per shared-memory tile (mixed)
+constexpr int kCjkMax = 512;       // (element, image) centres per tile (mixed)
+constexpr int kGroup = 8;          // elements per FP32 partial sum (mixed)
+constexpr int kTile64 = 32;        // elements per shared-memory tile (FP64)
+
+// Squared FP32 distance between a point (two floats per coordinate) and an image centroid;
+// the operation sequence is pinned (no contraction) so both kernels agree bit for bit.
+__device__ __forceinline__ float pair_d2(float phx, float phy, float phz, float plx, float ply, float plz,
+                                         const float4& ch, const float4& cl, float& dx, float& dy, float& dz) {
+    dx = __fadd_rn(__fsub_rn(phx, ch.x), __fsub_rn(plx, cl.x));
+    dy = __fadd_rn(__fsub_rn(phy, ch.y), __fsub_rn(ply, cl.y));
+    dz = __fadd_rn(__fsub_rn(phz, ch.z), __fsub_rn(plz, cl.z));
+    return __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+}
+
+__device__ __forceinline__ void split2f(double x, float& hi, float& lo) {
+    hi = __double2float_rn(x);
+    lo = __double2float_rn(x - (double)hi);
+}
+
+__device__ __forceinline__ void nodes_f32(const float4* __restrict__ nd, int m, float dx, float dy, float dz,
+                                          float& ph, float& ex, float& ey, float& ez) {
+#pragma unroll 3
+    for (int i = 0; i < m; ++i) {
+        const float4 q = nd[i];
+        const float rx = dx - q.x, ry = dy - q.y, rz = dz - q.z;
+        const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+        const float ri = rsqrtf(r2);
+        const float wr = q.w * ri;
+        const float wr3 = wr * ri * ri;
+        ph += wr;
+        ex = fmaf(wr3, rx, ex);
+        ey = fmaf(wr3, ry, ey);
+        ez = fmaf(wr3, rz, ez);
+    }
+}
+
+// Far part (FP32 tiers) of `count` targets; writes ke * sum (overwrites phi / E).
+__device__ __forceinline__ void far_block(const GeomView& g, const double* __restrict__ pts, int count,
+                                          double* __restrict__ phi, double* __restrict__ E) {
+    const FarNodes* __restrict__ far = g.far;
+    const float4* __restrict__ cjk = g.cjk;
+    const double* __restrict__ sigma = g.sigma;
+    const int64_t n_el = g.n_el;
+    const int nimg = g.nimg;
+    const int tile_el = g.tile_el;
+    __shared__ float4 s_a[kTileMax][kNodesA];
+    __shared__ float4 s_hdr[kTileMax];
+    __shared__ float s_sig[kTileMax];
+    __shared__ float4 s_c[kCjkMax][2];  // image centroids: hi, lo
+
+    const int p = threadIdx.x;
+    const bool active = p < count;
+    double Px = 0.0, Py = 0.0, Pz = 0.0;
+    if (active) {
+        Px = pts[3 * p];
+        Py = pts[3 * p + 1];
+        Pz = pts[3 * p + 2];
+    }
+    float phx, phy, phz, plx, ply, plz;
+    split2f(Px, phx, plx);
+    split2f(Py, phy, ply);
+    split2f(Pz, phz, plz);
+
+    double aphi = 0.0, aEx = 0.0, aEy = 0.0, aEz = 0.0;
+    for (int64_t base = 0; base < n_el; base += tile_el) {
+        const int cnt = (int)min((int64_t)tile_el, n_el - base);
+        __syncthreads();
+        for (int i = threadIdx.x; i < cnt * kNodesA; i += blockDim.x)
+            s_a[i / kNodesA][i % kNodesA] = far[base + i / kNodesA].a[i % kNodesA];
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+            s_hdr[i] = far[base + i].hdr;
+            s_sig[i] = (float)sigma[base + i];
+        }
+        const float4* src = cjk + 2 * base * nimg;
+        for (int i = threadIdx.x; i < 2 * cnt * nimg; i += blockDim.x) s_c[i >> 1][i & 1] = src[i];
+        __syncthreads();
+        float gphi = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+        for (int jj = 0; jj < cnt; ++jj) {
+            const float4 hdr = s_hdr[jj];
+            const int n_a = (int)hdr.w;
+            const FarNodes* fj = far + base + jj;
+            float lphi = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+            for (int k = 0; k < nimg; ++k) {
+                float dx, dy, dz;
+                const float d2 = pair_d2(phx, phy, phz, plx, ply, plz, s_c[jj * nimg + k][0], s_c[jj * nimg + k][1],
+                                         dx, dy, dz);
+                if (d2 >= hdr.x)
+                    nodes_f32(s_a[jj], n_a, dx, dy, dz, lphi, lx, ly, lz);
+                else if (d2 >= hdr.y)
+                    nodes_f32(fj->b, kNodesB, dx, dy, dz, lphi, lx, ly, lz);
+                else if (d2 >= hdr.z)
+                    nodes_f32(fj->c, kNodesC, dx, dy, dz, lphi, lx, ly, lz);
+                // nearer pairs: k_eval_near
+            }
+            const float s = s_sig[jj];
+            gphi = fmaf(s, lphi, gphi);
+            gx = fmaf(s, lx, gx);
+            gy = fmaf(s, ly, gy);
+            gz = fmaf(s, lz, gz);
+            if ((jj % kGroup) == kGroup - 1 || jj == cnt - 1) {
+                aphi += (double)gphi;
+                aEx += (double)gx;
+                aEy += (double)gy;
+                aEz += (double)gz;
+                gphi = gx = gy = gz = 0.f;
+            }
+        }
+    }
+    if (active) {
+        const double ke = 1.0 / (4.0 * kPi * kEps0);
+        if (phi) phi[p] = ke * aphi;
+        if (E) {
+            E[3 * p] = ke * aEx;
+            E[3 * p + 1] = ke * aEy;
+            E[3 * p + 2] = ke * aEz;
+        }
+    }
+}
+
+// Near part (FP64 closed forms) of one target; adds ke * sum to phi[p] / E[p].
+__device__ __forceinline__ void near_point(const GeomView& g, const ImageTable& img, const double* __restrict__ pts,
+                                           int64_t p, double* __restrict__ phi, double* __restrict__ E) {
+    const Elem* __restrict__ el = g.el;
+    const FarNodes* __restrict__ far = g.far;
+    const float4* __restrict__ cjk = g.cjk;
+    const double* __restrict__ sigma = g.sigma;
+    const int32_t* __restrict__ cell_start = g.cell_start;
+    const int32_t* __restrict__ cell_items = g.cell_items;
+    const int nimg = g.nimg;
+    const NearGrid& grid = g.grid;
+    const double Px = pts[3 * p], Py = pts[3 * p + 1], Pz = pts[3 * p + 2];
+    float phx, phy, phz, plx, ply, plz;
+    split2f(Px, phx, plx);
+    split2f(Py, phy, ply);
+    split2f(Pz, phz, plz);
+    // cell of the point, clamped (a point more than one cell outside has no near pair)
+    int cc[3];
+    const double P[3] = {Px, Py, Pz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double f = floor((P[a] - grid.origin[a]) * grid.inv_h);
+        f = fmin(fmax(f, -2.0), (double)grid.dims[a] + 1.0);
+        cc[a] = (int)f;
+    }
+    double aphi = 0.0, aEx = 0.0, aEy = 0.0, aEz = 0.0;
+    bool any = false;
+    for (int z = max(cc[2] - 1, 0); z <= min(cc[2] + 1, grid.dims[2] - 1); ++z)
+        for (int y = max(cc[1] - 1, 0); y <= min(cc[1] + 1, grid.dims[1] - 1); ++y)
+            for (int x = max(cc[0] - 1, 0); x <= min(cc[0] + 1, grid.dims[0] - 1); ++x) {
+                const int64_t cell = ((int64_t)z * grid.dims[1] + y) * grid.dims[0] + x;
+                for (int32_t it = cell_start[cell]; it < cell_start[cell + 1]; ++it) {
+                    const int32_t jk = cell_items[it];
+                    const int32_t j = jk / nimg, k = jk - j * nimg;
+                    float dx, dy, dz;
+                    const float d2 = pair_d2(phx, phy, phz, plx, ply, plz, cjk[2 * (int64_t)jk], cjk[2 * (int64_t)jk + 1],
+                                             dx, dy, dz);
+                    if (!(d2 < far[j].hdr.z)) continue;
+                    const Elem& e = el[j];
+                    double f, ux, uy, uz;
+                    elem_local_f64(e, Px - img.t[k][0], Py - img.t[k][1], Pz - img.t[k][2], false, f, ux, uy, uz);
+                    const double s = sigma[j];
+                    aphi = fma(s, f, aphi);
+                    aEx = fma(s, fma(ux, e.ex[0], fma(uy, e.ey[0], uz * e.ez[0])), aEx);
+                    aEy = fma(s, fma(ux, e.ex[1], fma(uy, e.ey[1], uz * e.ez[1])), aEy);
+                    aEz = fma(s, fma(ux, e.ex[2], fma(uy, e.ey[2], uz * e.ez[2])), aEz);
+                    any = true;
+                }
+            }
+    if (!any) return;
+    const double ke = 1.0 / (4.0 * kPi * kEps0);
+    if (phi) phi[p] += ke * aphi;
+    if (E) {
+        E[3 * p] += ke * aEx;
+        E[3 * p + 1] += ke * aEy;
+        E[3 * p + 2] += ke * aEz;
+    }
+}
+
+__device__ __forceinline__ void load_elem_tile(Elem* s_el, const Elem* __restrict__ el, int64_t base, int cnt) {
+    const double2* src = reinterpret_cast<const double2*>(el + base);
+    double2* dst = reinterpret_cast<double2*>(s_el);
+    for (int i = threadIdx.x; i < cnt * 16; i += blockDim.x) dst[i] = src[i];
+}
+
+// FP64 closed forms for every pair of `count` targets (overwrites phi / E).
+__device__ __forceinline__ void f64_block(const Elem* __restrict__ el, const double* __restrict__ sigma, int64_t n_el,
+                                          const ImageTable& img, const double* __restrict__ pts, int count,
+                                          double* __restrict__ phi, double* __restrict__ E) {
+    __shared__ Elem s_el[kTile64];
+    __shared__ double s_sig[kTile64];
+    const int p = threadIdx.x;
+    const bool active = p < count;
+    double Px = 0.0, Py = 0.0, Pz = 0.0;
+    if (active) {
+        Px = pts[3 * p];
+        Py = pts[3 * p + 1];
+        Pz = pts[3 * p + 2];
+    }
+    double aphi = 0.0, aEx = 0.0, aEy = 0.0, aEz = 0.0;
+    for (int64_t base = 0; base < n_el; base += kTile64) {
+        const int cnt = (int)min((int64_t)kTile64, n_el - base);
+        __syncthreads();
+        load_elem_tile(s_el, el, base, cnt);
+        if (threadIdx.x < cnt) s_sig[threadIdx.x] = sigma[base + threadIdx.x];
+        __syncthreads();
+        for (int jj = 0; jj < cnt; ++jj) {
+            const Elem& e = s_el[jj];
+            double lphi = 0.0, lx = 0.0, ly = 0.0, lz = 0.0;
+            for (int k = 0; k < img.n; ++k) {
+                double f, gx, gy, gz;
+                elem_local_f64(e, Px - img.t[k][0], Py - img.t[k][1], Pz - img.t[k][2], false, f, gx, gy, gz);
+                lphi += f;
+                lx += gx;
+                ly += gy;
+                lz += gz;
+            }
+            const double s = s_sig[jj];
+            aphi = fma(s, lphi, aphi);
+            aEx = fma(s, fma(lx, e.ex[0], fma(ly, e.ey[0], lz * e.ez[0])), aEx);
+            aEy = fma(s, fma(lx, e.ex[1], fma(ly, e.ey[1], lz * e.ez[1])), aEy);
+            aEz = fma(s, fma(lx, e.ex[2], fma(ly, e.ey[2], lz * e.ez[2])), aEz);
+        }
+    }
+    if (active) {
+        const double ke = 1.0 / (4.0 * kPi * kEps0);
+        if (phi) phi[p] = ke * aphi;
+        if (E) {
+            E[3 * p] = ke * aEx;
+            E[3 * p + 1] = ke * aEy;
+            E[3 * p + 2] = ke * aEz;
+        }
+    }
+}
+
+}  // namespace nb

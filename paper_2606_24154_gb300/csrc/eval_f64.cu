@@ -2,14 +2,15 @@
 //
 // Evaluation (Eq. Potential / Eq. Field with element charge densities):
 //   phi(x) = ke sum_j sigma_j sum_k Phi'(x - t_k; j),  E(x) likewise with E'.
-// One thread per target; element tiles are staged in shared memory (broadcast reads);
-// the image sum of one element is accumulated in its local frame and rotated once.
+// One thread per target (body f64_block in eval_blocks.cuh); element tiles are staged in
+// shared memory (broadcast reads); the image sum of one element is accumulated in its
+// local frame and rotated once.
 //
 // Fill (Eq. Matrix, collocation at centroids):
 //   conductor row i:  K_ij = ke sum_k Phi'(c_i - t_k; j)
 //   interface row i:  K_ij = ke sum_k n_i . E'(c_i - t_k; j) + delta_ij diag_i
 // Thread per row i (coalesced column-major stores K[i + j n]), grid.y over column chunks.
-#include "influence.cuh"
+#include "eval_blocks.cuh"
 
 namespace nb {
 
@@ -29,50 +30,9 @@ __global__ void __launch_bounds__(kThreads) k_eval_f64(const Elem* __restrict__ 
                                                        int64_t n_el, const ImageTable img,
                                                        const double* __restrict__ pts, int64_t npts,
                                                        double* __restrict__ phi, double* __restrict__ E) {
-    __shared__ Elem s_el[kTile];
-    __shared__ double s_sig[kTile];
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = p < npts;
-    double Px = 0.0, Py = 0.0, Pz = 0.0;
-    if (active) {
-        Px = pts[3 * p];
-        Py = pts[3 * p + 1];
-        Pz = pts[3 * p + 2];
-    }
-    double aphi = 0.0, aEx = 0.0, aEy = 0.0, aEz = 0.0;
-    for (int64_t base = 0; base < n_el; base += kTile) {
-        const int cnt = (int)min((int64_t)kTile, n_el - base);
-        __syncthreads();
-        load_tile(s_el, el, base, cnt);
-        if (threadIdx.x < cnt) s_sig[threadIdx.x] = sigma[base + threadIdx.x];
-        __syncthreads();
-        for (int jj = 0; jj < cnt; ++jj) {
-            const Elem& e = s_el[jj];
-            double lphi = 0.0, lx = 0.0, ly = 0.0, lz = 0.0;
-            for (int k = 0; k < img.n; ++k) {
-                double f, gx, gy, gz;
-                elem_local_f64(e, Px - img.t[k][0], Py - img.t[k][1], Pz - img.t[k][2], false, f, gx, gy, gz);
-                lphi += f;
-                lx += gx;
-                ly += gy;
-                lz += gz;
-            }
-            const double s = s_sig[jj];
-            aphi = fma(s, lphi, aphi);
-            aEx = fma(s, fma(lx, e.ex[0], fma(ly, e.ey[0], lz * e.ez[0])), aEx);
-            aEy = fma(s, fma(lx, e.ex[1], fma(ly, e.ey[1], lz * e.ez[1])), aEy);
-            aEz = fma(s, fma(lx, e.ex[2], fma(ly, e.ey[2], lz * e.ez[2])), aEz);
-        }
-    }
-    if (active) {
-        const double ke = 1.0 / (4.0 * kPi * kEps0);
-        if (phi) phi[p] = ke * aphi;
-        if (E) {
-            E[3 * p] = ke * aEx;
-            E[3 * p + 1] = ke * aEy;
-            E[3 * p + 2] = ke * aEz;
-        }
-    }
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x;
+    const int count = (int)min((int64_t)blockDim.x, npts - base);
+    f64_block(el, sigma, n_el, img, pts + 3 * base, count, phi ? phi + base : nullptr, E ? E + 3 * base : nullptr);
 }
 
 __global__ void __launch_bounds__(kThreads) k_fill_f64(const Elem* __restrict__ el, const double* __restrict__ diag_in,

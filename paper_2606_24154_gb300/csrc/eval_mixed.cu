@@ -1,208 +1,26 @@
-// eval_mixed.cu -- mixed-precision evaluation of potential and field at points.
-//
-// Same sums as the FP64 kernel (Eq. Potential / Eq. Field over elements and periodic
-// images), but each (point, element, image) pair picks its arithmetic by its distance d
-// to the image centroid, in units of the element's circumradius rho:
-//   d >= ratio_a rho      FP32 Gauss rule, tier a (6 nodes triangle / 9 rectangle)
-//   d >= ratio_b rho      FP32 Gauss rule, tier b (16 nodes)
-//   d >= ratio_near rho   FP32 Gauss rule, tier c (36 nodes)
-//   nearer                FP64 closed form (influence.cuh), where ln/atan cancel
-// Quadrature per node: Phi += w / r, E += w (P - x_n) / r^3 with one rsqrt.
-//
-// Two kernels: k_eval_far runs every FP32 tier over all (element, image) pairs and skips
-// near pairs; k_eval_near visits only the image centroids in the 27 grid cells around
-// each point (a cell list built per geometry, cell edge >= the largest near radius) and
-// adds the near pairs' FP64 closed forms.  Keeping the FP64 code out of the far kernel
-// keeps its register count (and so its occupancy) at the FP32 kernel's level.  Both
-// kernels decide "near" with the same rounded FP32 operations (pair_d2) on the same
-// inputs, so every pair is counted exactly once.
-//
-// The FP32 difference P - x_n keeps its relative accuracy even when P and the node are
-// millimetres from the origin but micrometres apart: both sides are held as two floats
-// (hi + lo) and (P_hi - C_hi) + (P_lo - C_lo) is formed first, C = c_j + t_k being the
-// image centroid (FP64 sum split once per geometry).  Node offsets from the centroid are
-// small, so the remaining FP32 operations carry ~1e-7 relative error.
-//
-// Accumulation: per element over its images in FP32, weighted by sigma_j, summed in FP32
-// over groups of kGroup elements and flushed to FP64.  Every decision depends only on the
-// pair, and each point's sums run in a fixed order, so a point's result is bit-identical
-// whatever other points share its launch.
-#include "influence.cuh"
+// eval_mixed.cu -- mixed-precision evaluation kernels (bodies in eval_blocks.cuh): the FP32
+// far-field kernel over all (element, image) pairs, the FP64 near-pair kernel over the
+// cell list, and the per-geometry two-float image-centroid table.
+#include "eval_blocks.cuh"
 
 namespace nb {
 
 namespace {
 
-constexpr int kMT = 128;        // threads per block (one target each)
-constexpr int kTileMax = 16;    // elements per shared-memory tile
-constexpr int kCjkMax = 512;    // (element, image) centres per tile
-constexpr int kGroup = 8;       // elements per FP32 partial sum
-
-// Squared FP32 distance between a point (two floats per coordinate) and an image centroid;
-// the operation sequence is pinned (no contraction) so both kernels agree bit for bit.
-__device__ __forceinline__ float pair_d2(float phx, float phy, float phz, float plx, float ply, float plz,
-                                         const float4& ch, const float4& cl, float& dx, float& dy, float& dz) {
-    dx = __fadd_rn(__fsub_rn(phx, ch.x), __fsub_rn(plx, cl.x));
-    dy = __fadd_rn(__fsub_rn(phy, ch.y), __fsub_rn(ply, cl.y));
-    dz = __fadd_rn(__fsub_rn(phz, ch.z), __fsub_rn(plz, cl.z));
-    return __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+__global__ void __launch_bounds__(kEvalThreads, 8) k_eval_far(const GeomView g, const double* __restrict__ pts,
+                                                            int64_t npts, double* __restrict__ phi,
+                                                            double* __restrict__ E) {
+    const int64_t base = (int64_t)blockIdx.x * blockDim.x;
+    const int count = (int)min((int64_t)blockDim.x, npts - base);
+    far_block(g, pts + 3 * base, count, phi ? phi + base : nullptr, E ? E + 3 * base : nullptr);
 }
 
-__device__ __forceinline__ void split2f(double x, float& hi, float& lo) {
-    hi = __double2float_rn(x);
-    lo = __double2float_rn(x - (double)hi);
-}
-
-__device__ __forceinline__ void nodes_f32(const float4* __restrict__ nd, int m, float dx, float dy, float dz,
-                                          float& ph, float& ex, float& ey, float& ez) {
-#pragma unroll 3
-    for (int i = 0; i < m; ++i) {
-        const float4 q = nd[i];
-        const float rx = dx - q.x, ry = dy - q.y, rz = dz - q.z;
-        const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-        const float ri = rsqrtf(r2);
-        const float wr = q.w * ri;
-        const float wr3 = wr * ri * ri;
-        ph += wr;
-        ex = fmaf(wr3, rx, ex);
-        ey = fmaf(wr3, ry, ey);
-        ez = fmaf(wr3, rz, ez);
-    }
-}
-
-__global__ void __launch_bounds__(kMT, 8) k_eval_far(const FarNodes* __restrict__ far, const float4* __restrict__ cjk,
-                                                  const double* __restrict__ sigma, int64_t n_el, int nimg,
-                                                  int tile_el, const double* __restrict__ pts, int64_t npts,
-                                                  double* __restrict__ phi, double* __restrict__ E) {
-    __shared__ float4 s_a[kTileMax][kNodesA];
-    __shared__ float4 s_hdr[kTileMax];
-    __shared__ float s_sig[kTileMax];
-    __shared__ float4 s_c[kCjkMax][2];  // image centroids: hi, lo
-
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = p < npts;
-    double Px = 0.0, Py = 0.0, Pz = 0.0;
-    if (active) {
-        Px = pts[3 * p];
-        Py = pts[3 * p + 1];
-        Pz = pts[3 * p + 2];
-    }
-    float phx, phy, phz, plx, ply, plz;
-    split2f(Px, phx, plx);
-    split2f(Py, phy, ply);
-    split2f(Pz, phz, plz);
-
-    double aphi = 0.0, aEx = 0.0, aEy = 0.0, aEz = 0.0;
-    for (int64_t base = 0; base < n_el; base += tile_el) {
-        const int cnt = (int)min((int64_t)tile_el, n_el - base);
-        __syncthreads();
-        for (int i = threadIdx.x; i < cnt * kNodesA; i += blockDim.x)
-            s_a[i / kNodesA][i % kNodesA] = far[base + i / kNodesA].a[i % kNodesA];
-        for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-            s_hdr[i] = far[base + i].hdr;
-            s_sig[i] = (float)sigma[base + i];
-        }
-        const float4* src = cjk + 2 * base * nimg;
-        for (int i = threadIdx.x; i < 2 * cnt * nimg; i += blockDim.x) s_c[i >> 1][i & 1] = src[i];
-        __syncthreads();
-        float gphi = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-        for (int jj = 0; jj < cnt; ++jj) {
-            const float4 hdr = s_hdr[jj];
-            const int n_a = (int)hdr.w;
-            const FarNodes* fj = far + base + jj;
-            float lphi = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
-            for (int k = 0; k < nimg; ++k) {
-                float dx, dy, dz;
-                const float d2 = pair_d2(phx, phy, phz, plx, ply, plz, s_c[jj * nimg + k][0], s_c[jj * nimg + k][1],
-                                         dx, dy, dz);
-                if (d2 >= hdr.x)
-                    nodes_f32(s_a[jj], n_a, dx, dy, dz, lphi, lx, ly, lz);
-                else if (d2 >= hdr.y)
-                    nodes_f32(fj->b, kNodesB, dx, dy, dz, lphi, lx, ly, lz);
-                else if (d2 >= hdr.z)
-                    nodes_f32(fj->c, kNodesC, dx, dy, dz, lphi, lx, ly, lz);
-                // nearer pairs: k_eval_near
-            }
-            const float s = s_sig[jj];
-            gphi = fmaf(s, lphi, gphi);
-            gx = fmaf(s, lx, gx);
-            gy = fmaf(s, ly, gy);
-            gz = fmaf(s, lz, gz);
-            if ((jj % kGroup) == kGroup - 1 || jj == cnt - 1) {
-                aphi += (double)gphi;
-                aEx += (double)gx;
-                aEy += (double)gy;
-                aEz += (double)gz;
-                gphi = gx = gy = gz = 0.f;
-            }
-        }
-    }
-    if (active) {
-        const double ke = 1.0 / (4.0 * kPi * kEps0);
-        if (phi) phi[p] = ke * aphi;
-        if (E) {
-            E[3 * p] = ke * aEx;
-            E[3 * p + 1] = ke * aEy;
-            E[3 * p + 2] = ke * aEz;
-        }
-    }
-}
-
-__global__ void __launch_bounds__(kMT) k_eval_near(const Elem* __restrict__ el, const FarNodes* __restrict__ far,
-                                                   const float4* __restrict__ cjk, const double* __restrict__ sigma,
-                                                   int nimg, const ImageTable img, const NearGrid grid,
-                                                   const int32_t* __restrict__ cell_start,
-                                                   const int32_t* __restrict__ cell_items,
-                                                   const double* __restrict__ pts, int64_t npts,
-                                                   double* __restrict__ phi, double* __restrict__ E) {
+__global__ void __launch_bounds__(kEvalThreads) k_eval_near(const GeomView g, const ImageTable img,
+                                                          const double* __restrict__ pts, int64_t npts,
+                                                          double* __restrict__ phi, double* __restrict__ E) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npts) return;
-    const double Px = pts[3 * p], Py = pts[3 * p + 1], Pz = pts[3 * p + 2];
-    float phx, phy, phz, plx, ply, plz;
-    split2f(Px, phx, plx);
-    split2f(Py, phy, ply);
-    split2f(Pz, phz, plz);
-    // cell of the point, clamped (a point more than one cell outside has no near pair)
-    int cc[3];
-    const double P[3] = {Px, Py, Pz};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        double f = floor((P[a] - grid.origin[a]) * grid.inv_h);
-        f = fmin(fmax(f, -2.0), (double)grid.dims[a] + 1.0);
-        cc[a] = (int)f;
-    }
-    double aphi = 0.0, aEx = 0.0, aEy = 0.0, aEz = 0.0;
-    bool any = false;
-    for (int z = max(cc[2] - 1, 0); z <= min(cc[2] + 1, grid.dims[2] - 1); ++z)
-        for (int y = max(cc[1] - 1, 0); y <= min(cc[1] + 1, grid.dims[1] - 1); ++y)
-            for (int x = max(cc[0] - 1, 0); x <= min(cc[0] + 1, grid.dims[0] - 1); ++x) {
-                const int64_t cell = ((int64_t)z * grid.dims[1] + y) * grid.dims[0] + x;
-                for (int32_t it = cell_start[cell]; it < cell_start[cell + 1]; ++it) {
-                    const int32_t jk = cell_items[it];
-                    const int32_t j = jk / nimg, k = jk - j * nimg;
-                    float dx, dy, dz;
-                    const float d2 = pair_d2(phx, phy, phz, plx, ply, plz, cjk[2 * (int64_t)jk], cjk[2 * (int64_t)jk + 1],
-                                             dx, dy, dz);
-                    if (!(d2 < far[j].hdr.z)) continue;
-                    const Elem& e = el[j];
-                    double f, ux, uy, uz;
-                    elem_local_f64(e, Px - img.t[k][0], Py - img.t[k][1], Pz - img.t[k][2], false, f, ux, uy, uz);
-                    const double s = sigma[j];
-                    aphi = fma(s, f, aphi);
-                    aEx = fma(s, fma(ux, e.ex[0], fma(uy, e.ey[0], uz * e.ez[0])), aEx);
-                    aEy = fma(s, fma(ux, e.ex[1], fma(uy, e.ey[1], uz * e.ez[1])), aEy);
-                    aEz = fma(s, fma(ux, e.ex[2], fma(uy, e.ey[2], uz * e.ez[2])), aEz);
-                    any = true;
-                }
-            }
-    if (!any) return;
-    const double ke = 1.0 / (4.0 * kPi * kEps0);
-    if (phi) phi[p] += ke * aphi;
-    if (E) {
-        E[3 * p] += ke * aEx;
-        E[3 * p + 1] += ke * aEy;
-        E[3 * p + 2] += ke * aEz;
-    }
+    near_point(g, img, pts, p, phi, E);
 }
 
 // Two-float image centroids, entry (j, k) at 2 * (j * nimg + k): hi then lo.
@@ -228,18 +46,33 @@ cudaError_t launch_image_centroids(const Elem* el, int64_t n, const ImageTable& 
     return cudaGetLastError();
 }
 
+GeomView make_view(const Elem* el, const FarNodes* far, const float4* cjk, const double* sigma, int64_t n_el,
+                   const ImageTable& img, const NearGrid& grid, const int32_t* cell_start, const int32_t* cell_items) {
+    GeomView g;
+    g.el = el;
+    g.far = far;
+    g.cjk = cjk;
+    g.sigma = sigma;
+    g.cell_start = cell_start;
+    g.cell_items = cell_items;
+    g.n_el = n_el;
+    g.nimg = img.n;
+    g.tile_el = max(1, min(kTileMax, kCjkMax / img.n));
+    g.grid = grid;
+    return g;
+}
+
 cudaError_t launch_eval_mixed(const Elem* el, const FarNodes* far, const float4* cjk, const double* sigma,
                               int64_t n_el, const ImageTable& img, const NearGrid& grid, const int32_t* cell_start,
                               const int32_t* cell_items, const double* pts, int64_t npts, double* phi, double* E,
                               cudaStream_t s) {
     if (npts == 0) return cudaSuccess;
-    const int tile_el = max(1, min(kTileMax, kCjkMax / img.n));
-    const unsigned blocks = (unsigned)((npts + kMT - 1) / kMT);
-    k_eval_far<<<blocks, kMT, 0, s>>>(far, cjk, sigma, n_el, img.n, tile_el, pts, npts, phi, E);
+    const GeomView g = make_view(el, far, cjk, sigma, n_el, img, grid, cell_start, cell_items);
+    const unsigned blocks = (unsigned)((npts + kEvalThreads - 1) / kEvalThreads);
+    k_eval_far<<<blocks, kEvalThreads, 0, s>>>(g, pts, npts, phi, E);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_eval_near<<<blocks, kMT, 0, s>>>(el, far, cjk, sigma, img.n, img, grid, cell_start, cell_items, pts, npts, phi,
-                                       E);
+    k_eval_near<<<blocks, kEvalThreads, 0, s>>>(g, img, pts, npts, phi, E);
     return cudaGetLastError();
 }
 

@@ -414,7 +414,19 @@ __global__ void k_absmax(const double* __restrict__ a, int64_t n, double* out) {
     if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned long long*>(out), __double_as_longlong(m));
 }
 
+__global__ void k_gather(const double* __restrict__ a, const int64_t* __restrict__ idx, int64_t n,
+                         double* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a[idx[i]];
+}
+
 }  // namespace
+
+cudaError_t launch_gather(const double* a, const int64_t* idx, int64_t n, double* out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, idx, n, out);
+    return cudaGetLastError();
+}
 
 size_t lu_work_elems(int64_t n, int nb) {
     // L11^-1 + U12 staging + pivot partials (in bytes / 4 rounded up, covers both types)

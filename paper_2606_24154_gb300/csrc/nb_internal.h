@@ -62,6 +62,23 @@ struct NearGrid {
     int32_t pad;
 };
 
+// Device-side view of one geometry for the evaluation bodies.
+struct GeomView {
+    const Elem* el;
+    const FarNodes* far;
+    const float4* cjk;
+    const double* sigma;
+    const int32_t* cell_start;
+    const int32_t* cell_items;
+    int64_t n_el;
+    int32_t nimg;
+    int32_t tile_el;
+    NearGrid grid;
+};
+
+GeomView make_view(const Elem* el, const FarNodes* far, const float4* cjk, const double* sigma, int64_t n_el,
+                   const ImageTable& img, const NearGrid& grid, const int32_t* cell_start, const int32_t* cell_items);
+
 // ------------------------------------------------------------------ launchers (.cu)
 // Each returns cudaSuccess or the launch error.
 cudaError_t launch_eval_f64(const Elem* el, const double* sigma, int64_t n_el, const ImageTable& img,
@@ -89,6 +106,7 @@ cudaError_t gemv_residual(const double* K, int64_t n, const double* x, const dou
                           cudaStream_t s);  // r = b - K x
 cudaError_t ir_update(double* x, const float* d, int64_t n, double* d_norms, cudaStream_t s);
 cudaError_t copy_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
+cudaError_t launch_gather(const double* a, const int64_t* idx, int64_t n, double* out, cudaStream_t s);
 cudaError_t vec_absmax(const double* a, int64_t n, double* out, cudaStream_t s);
 
 // space charge (spacecharge.cu)

@@ -1,7 +1,220 @@
-// server.cpp -- continuous-batching field-query server (declared in include/nebem.h).
+// server.cpp -- continuous-batching field-query server over several resident solved
+// contexts (C-ABI in include/nebem.h; persistent kernel in server.cu).
+//
+// Requests enter a host FIFO.  A request is admitted when a slot is free, the device
+// point arena has room for its points and the work ring has room for its items: its
+// points are copied into the arena, its remaining-item counter is set, and its items
+// (128 points each) are appended to the ring in host-mapped memory before `tail` is
+// advanced.  A persistent kernel (relaunched whenever admitted work exists and no
+// instance is running) claims items as they appear, so requests admitted while others
+// run join the running launch.  On completion the outputs are copied to the caller's
+// buffers and the arena range, slot and ring items are released.
+//
+// The server is driven from the caller's thread: submit, poll and wait each run one
+// round of completion -> admission -> launch.  Calls on one server must be serialised.
+#include <atomic>
+#include <chrono>
 #include <cstring>
+#include <deque>
+#include <thread>
+#include <unordered_map>
+#include <vector>
 
 #include "context.h"
+#include "server_internal.h"
+
+namespace nb {
+
+namespace {
+
+#define CK(call)                                                          \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);               \
+    } while (0)
+
+constexpr int kItemPoints = 128;
+
+struct Interval {
+    int64_t start, len;
+};
+
+// First-fit allocator over [0, cap) points.
+struct Arena {
+    int64_t cap = 0;
+    std::vector<Interval> free_list;
+    void reset(int64_t c) {
+        cap = c;
+        free_list.assign(1, Interval{0, c});
+    }
+    int64_t alloc(int64_t n) {
+        for (size_t i = 0; i < free_list.size(); ++i)
+            if (free_list[i].len >= n) {
+                const int64_t s = free_list[i].start;
+                free_list[i].start += n;
+                free_list[i].len -= n;
+                if (free_list[i].len == 0) free_list.erase(free_list.begin() + (long)i);
+                return s;
+            }
+        return -1;
+    }
+    void release(int64_t s, int64_t n) {
+        size_t i = 0;
+        while (i < free_list.size() && free_list[i].start < s) ++i;
+        free_list.insert(free_list.begin() + (long)i, Interval{s, n});
+        if (i + 1 < free_list.size() && free_list[i].start + free_list[i].len == free_list[i + 1].start) {
+            free_list[i].len += free_list[i + 1].len;
+            free_list.erase(free_list.begin() + (long)i + 1);
+        }
+        if (i > 0 && free_list[i - 1].start + free_list[i - 1].len == free_list[i].start) {
+            free_list[i - 1].len += free_list[i].len;
+            free_list.erase(free_list.begin() + (long)i);
+        }
+    }
+};
+
+struct Request {
+    int64_t id = 0;
+    int32_t geom = 0, precision = 0;
+    const double* pts = nullptr;
+    int64_t n = 0;
+    double* phi = nullptr;
+    double* E = nullptr;
+    double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+    int32_t slot = -1;
+    int64_t offset = -1, items = 0, gen = 0;
+    int state = 0;  // 0 queued, 1 admitted, 2 done
+};
+
+}  // namespace
+
+struct Server {
+    int device = 0;
+    nebem_server_options opt{};
+    std::vector<Ctx*> ctxs;
+    cudaStream_t compute = nullptr, copy = nullptr;
+    cudaEvent_t kernel_done = nullptr;
+    bool kernel_launched = false;
+    DevBuf d_geoms, d_pts, d_phi, d_E, d_head, d_remaining;
+    WorkItem* h_ring = nullptr;
+    int64_t* h_tail = nullptr;
+    int64_t* h_done = nullptr;
+    int64_t ring_cap = 0, published = 0, in_flight_items = 0;
+    Arena arena;
+    std::vector<int32_t> free_slots;
+    std::vector<int64_t> slot_gen;
+    std::deque<Request*> queue;
+    std::vector<Request*> admitted;
+    std::unordered_map<int64_t, Request*> reqs;
+    int64_t next_id = 1;
+    std::chrono::steady_clock::time_point t0;
+
+    double now() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+
+    ~Server() {
+        cudaSetDevice(device);
+        if (compute) cudaStreamSynchronize(compute);
+        for (DevBuf* b : {&d_geoms, &d_pts, &d_phi, &d_E, &d_head, &d_remaining}) b->release();
+        if (h_ring) cudaFreeHost(h_ring);
+        if (h_tail) cudaFreeHost(h_tail);
+        if (h_done) cudaFreeHost(h_done);
+        if (kernel_done) cudaEventDestroy(kernel_done);
+        if (compute) cudaStreamDestroy(compute);
+        if (copy) cudaStreamDestroy(copy);
+        for (auto& kv : reqs) delete kv.second;
+    }
+
+    int complete() {
+        for (size_t i = 0; i < admitted.size();) {
+            Request* r = admitted[i];
+            const int64_t done = __atomic_load_n(&h_done[r->slot], __ATOMIC_ACQUIRE);
+            if (done != r->gen) {
+                ++i;
+                continue;
+            }
+            if (r->phi)
+                CK(cudaMemcpyAsync(r->phi, d_phi.as<double>() + r->offset,
+                                   sizeof(double) * r->n, cudaMemcpyDeviceToHost, copy));
+            if (r->E)
+                CK(cudaMemcpyAsync(r->E, d_E.as<double>() + 3 * r->offset, sizeof(double) * 3 * r->n,
+                                   cudaMemcpyDeviceToHost, copy));
+            CK(cudaStreamSynchronize(copy));
+            arena.release(r->offset, r->n);
+            free_slots.push_back(r->slot);
+            in_flight_items -= r->items;
+            r->state = 2;
+            r->t_done = now();
+            admitted.erase(admitted.begin() + (long)i);
+        }
+        return 0;
+    }
+
+    int admit() {
+        while (!queue.empty()) {
+            Request* r = queue.front();
+            const int64_t items = (r->n + kItemPoints - 1) / kItemPoints;
+            if (free_slots.empty() || in_flight_items + items > ring_cap) break;
+            const int64_t off = arena.alloc(r->n);
+            if (off < 0) break;
+            queue.pop_front();
+            const int32_t slot = free_slots.back();
+            free_slots.pop_back();
+            r->slot = slot;
+            r->offset = off;
+            r->items = items;
+            r->gen = ++slot_gen[slot];
+            const int cnt = (int)items;
+            CK(cudaMemcpyAsync(d_pts.as<double>() + 3 * off, r->pts, sizeof(double) * 3 * r->n,
+                               cudaMemcpyHostToDevice, copy));
+            CK(cudaMemcpyAsync(d_remaining.as<int>() + slot, &cnt, sizeof(int), cudaMemcpyHostToDevice, copy));
+            CK(cudaStreamSynchronize(copy));
+            for (int64_t k = 0; k < items; ++k) {
+                WorkItem& w = h_ring[(published + k) % ring_cap];
+                w.slot = slot;
+                w.geom = r->geom;
+                w.precision = r->precision;
+                w.count = (int32_t)std::min<int64_t>(kItemPoints, r->n - k * kItemPoints);
+                w.offset = off + k * kItemPoints;
+                w.gen = r->gen;
+            }
+            published += items;
+            __atomic_store_n(h_tail, published, __ATOMIC_RELEASE);
+            in_flight_items += items;
+            r->state = 1;
+            r->t_admit = now();
+            admitted.push_back(r);
+        }
+        return 0;
+    }
+
+    int launch_if_needed() {
+        if (admitted.empty()) return 0;
+        if (kernel_launched) {
+            const cudaError_t q = cudaEventQuery(kernel_done);
+            if (q == cudaErrorNotReady) return 0;
+            if (q != cudaSuccess) return cuda_fail(q, "serving kernel");
+        }
+        CK(launch_serve(d_geoms.as<ServeGeom>(), h_ring, ring_cap, h_tail, d_head.as<unsigned long long>(),
+                        d_pts.as<double>(), d_phi.as<double>(), d_E.as<double>(), d_remaining.as<int>(), h_done,
+                        (uint64_t)opt.idle_us * 1000ull, opt.workers, compute));
+        CK(cudaEventRecord(kernel_done, compute));
+        kernel_launched = true;
+        return 0;
+    }
+
+    int drive() {
+        CK(cudaSetDevice(device));
+        int rc = complete();
+        if (rc) return rc;
+        rc = admit();
+        if (rc) return rc;
+        return launch_if_needed();
+    }
+};
+
+}  // namespace nb
 
 using namespace nb;
 
@@ -11,7 +224,7 @@ int nebem_server_default_options(nebem_server_options* opt) {
     if (!opt) return fail(NEBEM_INVALID_ARG, "opt is NULL");
     std::memset(opt, 0, sizeof(*opt));
     opt->arena_points = 4194304;
-    opt->chunk_points = 1024;
+    opt->chunk_points = kItemPoints;
     opt->max_requests = 256;
     opt->workers = 0;
     opt->idle_us = 2000;
@@ -19,17 +232,146 @@ int nebem_server_default_options(nebem_server_options* opt) {
 }
 
 int nebem_server_create(nebem_server** out, nebem_ctx* const* ctxs, int32_t n_ctx, const nebem_server_options* opt) {
-    (void)out; (void)ctxs; (void)n_ctx; (void)opt;
-    return fail(NEBEM_BAD_STATE, "server not built yet");
+    if (!out || !ctxs || n_ctx <= 0) return fail(NEBEM_INVALID_ARG, "need contexts");
+    *out = nullptr;
+    nebem_server_options o;
+    nebem_server_default_options(&o);
+    if (opt) o = *opt;
+    if (o.arena_points <= 0 || o.max_requests <= 0 || o.idle_us <= 0 || o.workers < 0)
+        return fail(NEBEM_INVALID_ARG, "bad server options");
+    if (o.chunk_points != kItemPoints) return fail(NEBEM_INVALID_ARG, "chunk_points must be 128");
+    std::vector<Ctx*> cs;
+    for (int32_t i = 0; i < n_ctx; ++i) {
+        Ctx* c = reinterpret_cast<Ctx*>(ctxs[i]);
+        if (!c) return fail(NEBEM_INVALID_ARG, "NULL context");
+        if (!c->sigma_valid) return fail(NEBEM_BAD_STATE, "context " + std::to_string(i) + " has no charge densities");
+        if (c->device != reinterpret_cast<Ctx*>(ctxs[0])->device)
+            return fail(NEBEM_INVALID_ARG, "all contexts must share one device");
+        cs.push_back(c);
+    }
+    Server* s = new (std::nothrow) Server();
+    if (!s) return fail(NEBEM_OUT_OF_MEMORY, "host allocation failed");
+    s->opt = o;
+    s->device = cs[0]->device;
+    s->ctxs = cs;
+    s->t0 = std::chrono::steady_clock::now();
+    auto bail = [&](int rc) {
+        delete s;
+        return rc;
+    };
+    cudaError_t e = cudaSetDevice(s->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->kernel_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "nebem_server_create"));
+    if (s->opt.workers == 0) s->opt.workers = 2 * cs[0]->props.multiProcessorCount;
+    const int64_t cap = o.arena_points;
+    std::vector<ServeGeom> geoms;
+    for (Ctx* c : cs)
+        geoms.push_back(make_serve_geom(c->d_el.as<Elem>(), c->d_far.as<FarNodes>(), c->d_cjk.as<float4>(),
+                                        c->d_sigma.as<double>(), c->n, c->img, c->grid,
+                                        c->d_cell_start.as<int32_t>(), c->d_cell_items.as<int32_t>()));
+    s->ring_cap = std::max<int64_t>(4096, 2 * (cap + kItemPoints - 1) / kItemPoints);
+    if ((e = s->d_geoms.ensure(sizeof(ServeGeom) * geoms.size())) != cudaSuccess ||
+        (e = s->d_pts.ensure(sizeof(double) * 3 * cap)) != cudaSuccess ||
+        (e = s->d_phi.ensure(sizeof(double) * cap)) != cudaSuccess ||
+        (e = s->d_E.ensure(sizeof(double) * 3 * cap)) != cudaSuccess ||
+        (e = s->d_head.ensure(sizeof(unsigned long long))) != cudaSuccess ||
+        (e = s->d_remaining.ensure(sizeof(int) * o.max_requests)) != cudaSuccess)
+        return bail(cuda_fail(e, "server device buffers"));
+    if ((e = cudaHostAlloc(&s->h_ring, sizeof(WorkItem) * s->ring_cap, cudaHostAllocMapped)) != cudaSuccess ||
+        (e = cudaHostAlloc(&s->h_tail, 64, cudaHostAllocMapped)) != cudaSuccess ||
+        (e = cudaHostAlloc(&s->h_done, sizeof(int64_t) * o.max_requests, cudaHostAllocMapped)) != cudaSuccess)
+        return bail(cuda_fail(e, "server mapped buffers"));
+    std::memset(s->h_ring, 0, sizeof(WorkItem) * s->ring_cap);
+    std::memset(s->h_tail, 0, 64);
+    std::memset(s->h_done, 0, sizeof(int64_t) * o.max_requests);
+    if ((e = cudaMemcpy(s->d_geoms.ptr, geoms.data(), sizeof(ServeGeom) * geoms.size(), cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaMemset(s->d_head.ptr, 0, sizeof(unsigned long long))) != cudaSuccess)
+        return bail(cuda_fail(e, "server setup copies"));
+    s->arena.reset(cap);
+    s->slot_gen.assign((size_t)o.max_requests, 0);
+    for (int32_t i = o.max_requests - 1; i >= 0; --i) s->free_slots.push_back(i);
+    *out = reinterpret_cast<nebem_server*>(s);
+    return NEBEM_OK;
 }
-int nebem_server_submit(nebem_server*, int32_t, const double*, int64_t, double*, double*, int32_t, int64_t*) {
-    return fail(NEBEM_BAD_STATE, "server not built yet");
+
+int nebem_server_submit(nebem_server* srv, int32_t geometry, const double* pts, int64_t n, double* phi, double* E,
+                        int32_t precision, int64_t* req_id) {
+    if (!srv || !req_id) return fail(NEBEM_INVALID_ARG, "NULL argument");
+    Server* s = reinterpret_cast<Server*>(srv);
+    if (geometry < 0 || geometry >= (int32_t)s->ctxs.size()) return fail(NEBEM_INVALID_ARG, "bad geometry index");
+    if (n <= 0 || !pts) return fail(NEBEM_INVALID_ARG, "need n > 0 points");
+    if (precision != NEBEM_FP64 && precision != NEBEM_MIXED) return fail(NEBEM_INVALID_ARG, "bad precision");
+    if (n > s->opt.arena_points) return fail(NEBEM_TOO_LARGE, "request larger than the point arena");
+    Request* r = new (std::nothrow) Request();
+    if (!r) return fail(NEBEM_OUT_OF_MEMORY, "host allocation failed");
+    r->id = s->next_id++;
+    r->geom = geometry;
+    r->precision = precision;
+    r->pts = pts;
+    r->n = n;
+    r->phi = phi;
+    r->E = E;
+    r->t_submit = s->now();
+    s->reqs[r->id] = r;
+    s->queue.push_back(r);
+    *req_id = r->id;
+    return s->drive();
 }
-int nebem_server_poll(nebem_server*, int64_t, int32_t*) { return fail(NEBEM_BAD_STATE, "server not built yet"); }
-int nebem_server_wait(nebem_server*, int64_t, int64_t) { return fail(NEBEM_BAD_STATE, "server not built yet"); }
-int nebem_server_request_times(nebem_server*, int64_t, double*, double*, double*) {
-    return fail(NEBEM_BAD_STATE, "server not built yet");
+
+int nebem_server_poll(nebem_server* srv, int64_t req_id, int32_t* done) {
+    if (!srv || !done) return fail(NEBEM_INVALID_ARG, "NULL argument");
+    Server* s = reinterpret_cast<Server*>(srv);
+    auto it = s->reqs.find(req_id);
+    if (it == s->reqs.end()) return fail(NEBEM_INVALID_ARG, "unknown request");
+    int rc = s->drive();
+    if (rc) return rc;
+    *done = it->second->state == 2 ? 1 : 0;
+    return NEBEM_OK;
 }
-int nebem_server_destroy(nebem_server*) { return NEBEM_OK; }
+
+int nebem_server_wait(nebem_server* srv, int64_t req_id, int64_t timeout_ms) {
+    if (!srv) return fail(NEBEM_INVALID_ARG, "NULL argument");
+    Server* s = reinterpret_cast<Server*>(srv);
+    auto it = s->reqs.find(req_id);
+    if (it == s->reqs.end()) return fail(NEBEM_INVALID_ARG, "unknown request");
+    const double deadline = s->now() + 1e-3 * (double)timeout_ms;
+    for (;;) {
+        int rc = s->drive();
+        if (rc) return rc;
+        if (it->second->state == 2) return NEBEM_OK;
+        if (s->now() > deadline) return fail(NEBEM_TIMEOUT, "request not complete within the timeout");
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+int nebem_server_request_times(nebem_server* srv, int64_t req_id, double* t_submit, double* t_admit, double* t_done) {
+    if (!srv) return fail(NEBEM_INVALID_ARG, "NULL argument");
+    Server* s = reinterpret_cast<Server*>(srv);
+    auto it = s->reqs.find(req_id);
+    if (it == s->reqs.end()) return fail(NEBEM_INVALID_ARG, "unknown request");
+    const Request* r = it->second;
+    if (r->state != 2) return fail(NEBEM_BAD_STATE, "request not complete");
+    if (t_submit) *t_submit = r->t_submit;
+    if (t_admit) *t_admit = r->t_admit;
+    if (t_done) *t_done = r->t_done;
+    return NEBEM_OK;
+}
+
+int nebem_server_destroy(nebem_server* srv) {
+    if (!srv) return NEBEM_OK;
+    Server* s = reinterpret_cast<Server*>(srv);
+    // finish admitted work (the kernel idles out once the ring is drained); queued
+    // requests that were never admitted are dropped
+    s->queue.clear();
+    for (int guard = 0; guard < 600000 && !s->admitted.empty(); ++guard) {
+        if (s->drive()) break;
+        std::this_thread::sleep_for(std::chrono::microseconds(100));
+    }
+    delete s;
+    return NEBEM_OK;
+}
 
 }  // extern "C"

@@ -1,0 +1,35 @@
+// server_internal.h -- types shared by the serving kernel (server.cu) and its host side
+// (server.cpp).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nb_internal.h"
+
+namespace nb {
+
+// One work item: up to 128 points of one request, at `offset` in the point arena.
+struct WorkItem {
+    int32_t slot;       // request slot (remaining-item counter, completion word)
+    int32_t geom;       // geometry index
+    int32_t precision;  // NEBEM_FP64 / NEBEM_MIXED
+    int32_t count;      // points in this item
+    int64_t offset;     // first point in the arena
+    int64_t gen;        // generation number the completion word receives
+};
+
+// Device-side geometry record of the server (one per context).
+struct ServeGeom {
+    GeomView view;
+    ImageTable img;
+};
+
+ServeGeom make_serve_geom(const Elem* el, const FarNodes* far, const float4* cjk, const double* sigma, int64_t n_el,
+                          const ImageTable& img, const NearGrid& grid, const int32_t* cell_start,
+                          const int32_t* cell_items);
+
+cudaError_t launch_serve(const ServeGeom* geoms, const WorkItem* ring, int64_t ring_cap, int64_t* tail_mapped,
+                         unsigned long long* head, const double* arena_pts, double* arena_phi, double* arena_E,
+                         int* remaining, int64_t* done_mapped, uint64_t idle_ns, int workers, cudaStream_t s);
+
+}  // namespace nb

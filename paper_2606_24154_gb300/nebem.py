@@ -90,6 +90,7 @@ SIGNATURES = {
     "nebem_set_sigma": (C.c_int, [_vp, _d, C.c_int64]),
     "nebem_get_sigma": (C.c_int, [_vp, _d, C.c_int64]),
     "nebem_fill": (C.c_int, [_vp, C.c_int32, _d]),
+    "nebem_matrix_entries": (C.c_int, [_vp, _i64p, _i64p, C.c_int64, _d]),
     "nebem_eval": (C.c_int, [_vp, _d, C.c_int64, _d, _d, C.c_int32]),
     "nebem_eval_device": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, C.c_int32, _vp]),
     "nebem_space_charge": (C.c_int, [_vp, _d, _d, C.c_int64, C.c_double]),
@@ -205,6 +206,15 @@ def nebem_fill(ctx, precision: int, n: int):
     K = np.empty(n * n)
     _check(load().nebem_fill(ctx, precision, _dp(K)), "nebem_fill")
     return K.reshape(n, n).T  # column-major -> K[i, j]
+
+
+def nebem_matrix_entries(ctx, rows, cols):
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    c = np.ascontiguousarray(cols, dtype=np.int64)
+    out = np.empty(r.shape[0])
+    _check(load().nebem_matrix_entries(ctx, r.ctypes.data_as(_i64p), c.ctypes.data_as(_i64p), r.shape[0], _dp(out)),
+           "nebem_matrix_entries")
+    return out
 
 
 def nebem_eval(ctx, pts, precision: int, want_phi=True, want_E=True):
