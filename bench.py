@@ -186,6 +186,9 @@ def serving_run(N, ctxs, geoms, n_req, scale, precision, seed):
     i = 0
     while i < n_req or not all(done):
         now = time.perf_counter() - t0
+        if now > 900.0:
+            N.nebem_server_destroy(srv)
+            raise RuntimeError("serving trace did not complete within 900 s")
         while i < n_req and t_arr[i] <= now:
             ids[i] = N.nebem_server_submit(srv, int(geo[i]), reqs[i][0], reqs[i][1], reqs[i][2], precision)
             i += 1
