@@ -220,7 +220,11 @@ def run_native(args):
     B.build()
     N.load()
 
-    g, pts_h = workload(args.points)
+    from paper_2606_24154_gb300 import inputs as I
+    from paper_2606_24154_gb300 import sharding as S
+    g = I.thgem()
+    # weak scaling: every rank evaluates its own points (seed stream = rank)
+    pts_h = I.cell_points(g, args.points, I.rng(1, S.shard_seed_stream(rank)))
     n_el, n_img = g.n, g.n_images
     ctx = N.Context(device=local).set_geometry(g)
     sigma, info, _ = ctx.solve(N.NEBEM_MIXED)
@@ -261,12 +265,9 @@ def run_native(args):
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     evals = npts * n_el * n_img
-    value = evals * world / (ms * 1e-3)
+    ms, total_evals = S.reduce_step_time(ms, evals, dev)
+    value = total_evals / (ms * 1e-3)
 
     # ---- accuracy of the mixed path against the FP64 path, and the FP64 path's rate
     ns = min(FP64_SAMPLE, npts)
@@ -309,11 +310,12 @@ def run_native(args):
             raise N.NebemError(rc, "nebem_eval")
         if k > 0:
             e2e_times.append(time.perf_counter() - t)
-    e2e_val = evals * world / statistics.mean(e2e_times)
+    e2e_ms, _ = S.reduce_step_time(statistics.mean(e2e_times) * 1e3, evals, dev)
+    e2e_val = total_evals / (e2e_ms * 1e-3)
 
     # ---- solve of the same geometry: mixed (FP32 LU + FP64 refinement) vs plain FP64
     solve = {}
-    for name, prec in (("mixed", N.NEBEM_MIXED), ("fp64", N.NEBEM_FP64)):
+    for name, prec in ((("mixed", N.NEBEM_MIXED), ("fp64", N.NEBEM_FP64)) if world == 1 else ()):
         c2 = N.Context(device=local).set_geometry(g)
         _, inf, _ = c2.solve(prec)
         solve[name] = {"ms_fill": inf.ms_fill, "ms_factor": inf.ms_factor, "ms_solve": inf.ms_solve,

@@ -88,9 +88,10 @@ typedef struct nebem_options {
     int32_t device;          /* CUDA device ordinal (default 0) */
     int32_t ir_max_iter;     /* iterative refinement limit in mixed solves (default 30) */
     double ir_tol;           /* stop when ||d sigma||_inf / ||sigma||_inf <= ir_tol (1e-8) */
-    double ratio_a;          /* mixed eval: pairs with distance >= ratio_a element radii use
-                                the low-order FP32 Gauss rule (6-node triangle, 3x3
-                                rectangle; default 24) */
+    double ratio_0;          /* mixed eval: pairs with distance >= ratio_0 element radii use
+                                the 4-node FP32 Gauss rule (default 64) */
+    double ratio_a;          /* >= ratio_a radii: 6-node triangle / 3x3 rectangle rule
+                                (default 24) */
     double ratio_b;          /* >= ratio_b radii: 16-node FP32 rule (default 8) */
     double ratio_near;       /* >= ratio_near radii: 36-node FP32 rule; nearer pairs take
                                 the FP64 closed form (default 3) */
@@ -99,7 +100,7 @@ typedef struct nebem_options {
                                 difference from exact two-float coordinates (default 1e-4) */
     int32_t lu_block;        /* LU panel width, 32 or 64 (default 64) */
     int32_t reserved0;
-    double reserved[5];
+    double reserved[4];
 } nebem_options;
 
 /* Result report of nebem_solve. */
@@ -221,6 +222,23 @@ int nebem_space_charge_eval(nebem_ctx *ctx, const double *pts, int64_t n, double
  * pos_out[n][3] (host, may be NULL) receives the final positions.
  * Errors: NEBEM_BAD_STATE, NEBEM_NOT_CONVERGED, NEBEM_CUDA. */
 int nebem_step(nebem_ctx *ctx, int32_t steps, double mu, double dt, int32_t precision, double *pos_out);
+
+/* Dense LU factorisation of a caller's matrix on the device (Sec. 4.1, Alg. 1, with the
+ * factors kept instead of forming the inverse): right-looking blocked LU with partial
+ * pivoting (largest |a|, lowest row index on ties), FP64, in place.
+ *   d_A    device, n x n column-major (lda = n); overwritten by L (unit lower, below the
+ *          diagonal) and U.
+ *   d_piv  device int32[n]; row k was swapped with row d_piv[k] at step k.
+ * Runs on `stream` (NULL = the context stream) and synchronises it before returning.
+ * Allocates its work buffer (about (lu_block + 1) * n doubles) on the context's device
+ * for the duration of the call.  Errors: NEBEM_SINGULAR (zero pivot; the factors are
+ * incomplete), NEBEM_INVALID_ARG, NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
+int nebem_lu_factor_device(nebem_ctx *ctx, double *d_A, int64_t n, int32_t *d_piv, void *stream);
+
+/* Solve A x = b in place with factors from nebem_lu_factor_device: d_b (device, n) is
+ * overwritten by x.  Asynchronous on `stream` (NULL = the context stream). */
+int nebem_lu_solve_device(nebem_ctx *ctx, const double *d_LU, int64_t n, const int32_t *d_piv, double *d_b,
+                          void *stream);
 
 /* Image translations of the current geometry in index order (count * 3 doubles,
  * host).  *count receives the number of images; t_out may be NULL to query it. */

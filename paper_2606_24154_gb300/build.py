@@ -21,6 +21,12 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
           "-I", os.path.join(HERE, "..", "include")]
 
 
+# Per-file flags: the FP32 evaluation bodies (standalone mixed kernels and the serving
+# kernel, which must agree bit for bit) flush denormals: their distances, weights and
+# field terms are all many orders of magnitude above the FP32 denormal range.
+FILE_FLAGS = {"eval_mixed.cu": ["-ftz=true"], "server.cu": ["-ftz=true"]}
+
+
 def _nvcc() -> str:
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     if not os.path.exists(nvcc):
@@ -53,7 +59,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
     def compile_one(src):
         obj = os.path.join(BUILD_DIR, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *COMMON, *extra, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *COMMON, *FILE_FLAGS.get(os.path.basename(src), []), *extra, "-c", src, "-o", obj]
         if src.endswith(".cu"):
             cmd += ["-Xptxas", "-warn-spills"]
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -97,6 +97,7 @@ int nebem_default_options(nebem_options* opt) {
     opt->device = 0;
     opt->ir_max_iter = 30;
     opt->ir_tol = 1e-8;
+    opt->ratio_0 = 64.0;
     opt->ratio_a = 24.0;
     opt->ratio_b = 8.0;
     opt->ratio_near = 3.0;
@@ -114,8 +115,9 @@ int nebem_create(nebem_ctx** out, const nebem_options* opt) {
     if (opt) o = *opt;
     if (o.lu_block < 32 || o.lu_block > 64 || o.lu_block % 32) return fail(NEBEM_INVALID_ARG, "lu_block must be 32 or 64");
     if (!(o.ir_tol > 0.0) || o.ir_max_iter < 1) return fail(NEBEM_INVALID_ARG, "bad refinement options");
-    if (!(o.ratio_near >= 1.5) || !(o.ratio_b >= o.ratio_near) || !(o.ratio_a >= o.ratio_b) || !(o.ratio_a < 1e6))
-        return fail(NEBEM_INVALID_ARG, "need 1.5 <= ratio_near <= ratio_b <= ratio_a");
+    if (!(o.ratio_near >= 1.5) || !(o.ratio_b >= o.ratio_near) || !(o.ratio_a >= o.ratio_b) ||
+        !(o.ratio_0 >= o.ratio_a) || !(o.ratio_0 < 1e6))
+        return fail(NEBEM_INVALID_ARG, "need 1.5 <= ratio_near <= ratio_b <= ratio_a <= ratio_0");
     if (!(o.softening > 0.0)) return fail(NEBEM_INVALID_ARG, "softening must be > 0");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -351,6 +353,35 @@ int nebem_eval(nebem_ctx* ctx, const double* pts, int64_t n, double* phi, double
     if (phi) CK(cudaMemcpyAsync(phi, c->d_phi.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
     if (E) CK(cudaMemcpyAsync(E, c->d_E.ptr, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return NEBEM_OK;
+}
+
+int nebem_lu_factor_device(nebem_ctx* ctx, double* d_A, int64_t n, int32_t* d_piv, void* stream) {
+    if (!ctx || n <= 0 || !d_A || !d_piv) return fail(NEBEM_INVALID_ARG, "bad argument");
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    const int nb = c->opt.lu_block;
+    DevBuf work, info;
+    CK(work.ensure(sizeof(double) * lu_work_elems(n, nb)));
+    CK(info.ensure(sizeof(int)));
+    CK(lu_factor_f64(d_A, n, d_piv, nb, work.as<double>(), info.as<int>(), s));
+    int h_info = 0;
+    CK(cudaMemcpyAsync(&h_info, info.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    work.release();
+    info.release();
+    if (h_info) return fail(NEBEM_SINGULAR, "zero pivot at column " + std::to_string(h_info - 1));
+    return NEBEM_OK;
+}
+
+int nebem_lu_solve_device(nebem_ctx* ctx, const double* d_LU, int64_t n, const int32_t* d_piv, double* d_b,
+                          void* stream) {
+    if (!ctx || n <= 0 || !d_LU || !d_piv || !d_b) return fail(NEBEM_INVALID_ARG, "bad argument");
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    CK(lu_solve_f64(d_LU, n, d_piv, d_b, s));
     return NEBEM_OK;
 }
 

@@ -8,6 +8,7 @@
 // Same sums as the FP64 kernel (Eq. Potential / Eq. Field over elements and periodic
 // images), but each (point, element, image) pair picks its arithmetic by its distance d
 // to the image centroid, in units of the element's circumradius rho:
+//   d >= ratio_0 rho      FP32 Gauss rule, tier 0 (4 nodes)
 //   d >= ratio_a rho      FP32 Gauss rule, tier a (6 nodes triangle / 9 rectangle)
 //   d >= ratio_b rho      FP32 Gauss rule, tier b (16 nodes)
 //   d >= ratio_near rho   FP32 Gauss rule, tier c (36 nodes)
@@ -58,10 +59,11 @@ __device__ __forceinline__ void split2f(double x, float& hi, float& lo) {
     lo = __double2float_rn(x - (double)hi);
 }
 
-__device__ __forceinline__ void nodes_f32(const float4* __restrict__ nd, int m, float dx, float dy, float dz,
-                                          float& ph, float& ex, float& ey, float& ez) {
-#pragma unroll 3
-    for (int i = 0; i < m; ++i) {
+template <int M>
+__device__ __forceinline__ void nodes_f32(const float4* __restrict__ nd, float dx, float dy, float dz, float& ph,
+                                          float& ex, float& ey, float& ez) {
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
         const float4 q = nd[i];
         const float rx = dx - q.x, ry = dy - q.y, rz = dz - q.z;
         const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
@@ -84,7 +86,9 @@ __device__ __forceinline__ void far_block(const GeomView& g, const double* __res
     const int64_t n_el = g.n_el;
     const int nimg = g.nimg;
     const int tile_el = g.tile_el;
+    __shared__ float4 s_f[kTileMax][kNodes0];
     __shared__ float4 s_a[kTileMax][kNodesA];
+    __shared__ int s_na[kTileMax];
     __shared__ float4 s_hdr[kTileMax];
     __shared__ float s_sig[kTileMax];
     __shared__ float4 s_c[kCjkMax][2];  // image centroids: hi, lo
@@ -108,8 +112,11 @@ __device__ __forceinline__ void far_block(const GeomView& g, const double* __res
         __syncthreads();
         for (int i = threadIdx.x; i < cnt * kNodesA; i += blockDim.x)
             s_a[i / kNodesA][i % kNodesA] = far[base + i / kNodesA].a[i % kNodesA];
+        for (int i = threadIdx.x; i < cnt * kNodes0; i += blockDim.x)
+            s_f[i / kNodes0][i % kNodes0] = far[base + i / kNodes0].f[i % kNodes0];
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
             s_hdr[i] = far[base + i].hdr;
+            s_na[i] = far[base + i].n_a;
             s_sig[i] = (float)sigma[base + i];
         }
         const float4* src = cjk + 2 * base * nimg;
@@ -118,19 +125,25 @@ __device__ __forceinline__ void far_block(const GeomView& g, const double* __res
         float gphi = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
         for (int jj = 0; jj < cnt; ++jj) {
             const float4 hdr = s_hdr[jj];
-            const int n_a = (int)hdr.w;
+            const bool rect = s_na[jj] == kNodesA;
             const FarNodes* fj = far + base + jj;
             float lphi = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
             for (int k = 0; k < nimg; ++k) {
                 float dx, dy, dz;
                 const float d2 = pair_d2(phx, phy, phz, plx, ply, plz, s_c[jj * nimg + k][0], s_c[jj * nimg + k][1],
                                          dx, dy, dz);
-                if (d2 >= hdr.x)
-                    nodes_f32(s_a[jj], n_a, dx, dy, dz, lphi, lx, ly, lz);
-                else if (d2 >= hdr.y)
-                    nodes_f32(fj->b, kNodesB, dx, dy, dz, lphi, lx, ly, lz);
-                else if (d2 >= hdr.z)
-                    nodes_f32(fj->c, kNodesC, dx, dy, dz, lphi, lx, ly, lz);
+                if (d2 >= hdr.x) {
+                    nodes_f32<kNodes0>(s_f[jj], dx, dy, dz, lphi, lx, ly, lz);
+                } else if (d2 >= hdr.y) {
+                    if (rect)
+                        nodes_f32<kNodesA>(s_a[jj], dx, dy, dz, lphi, lx, ly, lz);
+                    else
+                        nodes_f32<6>(s_a[jj], dx, dy, dz, lphi, lx, ly, lz);
+                } else if (d2 >= hdr.z) {
+                    nodes_f32<kNodesB>(fj->b, dx, dy, dz, lphi, lx, ly, lz);
+                } else if (d2 >= hdr.w) {
+                    nodes_f32<kNodesC>(fj->c, dx, dy, dz, lphi, lx, ly, lz);
+                }
                 // nearer pairs: k_eval_near
             }
             const float s = s_sig[jj];
@@ -195,7 +208,7 @@ __device__ __forceinline__ void near_point(const GeomView& g, const ImageTable& 
                     float dx, dy, dz;
                     const float d2 = pair_d2(phx, phy, phz, plx, ply, plz, cjk[2 * (int64_t)jk], cjk[2 * (int64_t)jk + 1],
                                              dx, dy, dz);
-                    if (!(d2 < far[j].hdr.z)) continue;
+                    if (!(d2 < far[j].hdr.w)) continue;
                     const Elem& e = el[j];
                     double f, ux, uy, uz;
                     elem_local_f64(e, Px - img.t[k][0], Py - img.t[k][1], Pz - img.t[k][2], false, f, ux, uy, uz);

@@ -27,6 +27,11 @@ inline void cross3(const double* a, const double* b, double* c) {
 const double kTriA[2] = {0.445948490915965, 0.091576213509771};
 const double kTriW[2] = {0.223381589678011, 0.109951743655322};
 
+// Strang-Fix 4-point degree-3 triangle rule: centroid with weight -27/48 and the three
+// points (3/5, 1/5, 1/5) with weight 25/48.
+const double kTri3B[4][3] = {{1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0}, {0.6, 0.2, 0.2}, {0.2, 0.6, 0.2}, {0.2, 0.2, 0.6}};
+const double kTri3W[4] = {-27.0 / 48.0, 25.0 / 48.0, 25.0 / 48.0, 25.0 / 48.0};
+
 }  // namespace
 
 void gauss_legendre01(int m, double* x, double* w) {
@@ -169,10 +174,18 @@ int build_element(const nebem_element& r, const nebem_options& opt, Elem& e, dou
                 }
             return cnt;
         };
+        tensor(2, fn.f);
         n_a = tensor(3, fn.a);
         tensor(4, fn.b);
         tensor(6, fn.c);
     } else {
+        // degree-3 four-point rule
+        for (int q = 0; q < 4; ++q) {
+            double g[3];
+            for (int k = 0; k < 3; ++k)
+                g[k] = kTri3B[q][0] * r.v[0][k] + kTri3B[q][1] * r.v[1][k] + kTri3B[q][2] * r.v[2][k];
+            put(fn.f[q], g, kTri3W[q]);
+        }
         // degree-4 six-point rule
         for (int g2 = 0; g2 < 2; ++g2)
             for (int rr = 0; rr < 3; ++rr) {
@@ -199,11 +212,13 @@ int build_element(const nebem_element& r, const nebem_options& opt, Elem& e, dou
         collapsed(4, fn.b);
         collapsed(6, fn.c);
     }
-    const double ra = opt.ratio_a * rho, rb = opt.ratio_b * rho, rn = opt.ratio_near * rho;
-    fn.hdr.x = (float)(ra * ra);
-    fn.hdr.y = (float)(rb * rb);
-    fn.hdr.z = (float)(rn * rn);
-    fn.hdr.w = (float)n_a;
+    const double r0 = opt.ratio_0 * rho, ra = opt.ratio_a * rho, rb = opt.ratio_b * rho,
+                 rn = opt.ratio_near * rho;
+    fn.hdr.x = (float)(r0 * r0);
+    fn.hdr.y = (float)(ra * ra);
+    fn.hdr.z = (float)(rb * rb);
+    fn.hdr.w = (float)(rn * rn);
+    fn.n_a = n_a;
     return NEBEM_OK;
 }
 

@@ -37,6 +37,7 @@ class nebem_options(C.Structure):
         ("device", C.c_int32),
         ("ir_max_iter", C.c_int32),
         ("ir_tol", C.c_double),
+        ("ratio_0", C.c_double),
         ("ratio_a", C.c_double),
         ("ratio_b", C.c_double),
         ("ratio_near", C.c_double),
@@ -44,7 +45,7 @@ class nebem_options(C.Structure):
         ("sc_near", C.c_double),
         ("lu_block", C.c_int32),
         ("reserved0", C.c_int32),
-        ("reserved", C.c_double * 5),
+        ("reserved", C.c_double * 4),
     ]
 
 
@@ -96,6 +97,8 @@ SIGNATURES = {
     "nebem_space_charge": (C.c_int, [_vp, _d, _d, C.c_int64, C.c_double]),
     "nebem_space_charge_eval": (C.c_int, [_vp, _d, C.c_int64, _d, _d, C.c_int32, C.c_int32]),
     "nebem_step": (C.c_int, [_vp, C.c_int32, C.c_double, C.c_double, C.c_int32, _d]),
+    "nebem_lu_factor_device": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp]),
+    "nebem_lu_solve_device": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp]),
     "nebem_image_table": (C.c_int, [_vp, _d, _i64p]),
     "nebem_element_influence": (C.c_int, [_vp, _vp, C.c_int64, _d, C.c_int64, _d, _d]),
     "nebem_server_default_options": (C.c_int, [C.POINTER(nebem_server_options)]),
@@ -251,6 +254,14 @@ def nebem_step(ctx, steps: int, mu: float, dt: float, precision: int, n_carriers
     pos = np.empty((n_carriers, 3))
     _check(load().nebem_step(ctx, steps, mu, dt, precision, _dp(pos)), "nebem_step")
     return pos
+
+
+def nebem_lu_factor_device(ctx, d_A: int, n: int, d_piv: int, stream: int | None = None):
+    _check(load().nebem_lu_factor_device(ctx, d_A, n, d_piv, stream), "nebem_lu_factor_device")
+
+
+def nebem_lu_solve_device(ctx, d_LU: int, n: int, d_piv: int, d_b: int, stream: int | None = None):
+    _check(load().nebem_lu_solve_device(ctx, d_LU, n, d_piv, d_b, stream), "nebem_lu_solve_device")
 
 
 def nebem_image_table(ctx):

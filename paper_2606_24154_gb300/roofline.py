@@ -2,6 +2,7 @@
 
 Algorithmic work of one mixed evaluation launch, counted per (point, element, image)
 pair by its distance tier (distance to the image centroid in element circumradii):
+  tier 0 (>= ratio_0):   4 Gauss nodes
   tier a (>= ratio_a):   6 Gauss nodes (triangle) or 9 (rectangle)
   tier b (>= ratio_b):   16 nodes
   tier c (>= ratio_near): 36 nodes
@@ -41,27 +42,29 @@ def _images(g):
     return np.array([k1 * g.lattice[0] + k2 * g.lattice[1] for k1 in ks for k2 in ks])
 
 
-def tier_counts(g, pts, sample=4096, ratio_a=24.0, ratio_b=8.0, ratio_near=3.0, chunk=32):
+def tier_counts(g, pts, sample=4096, ratio_0=64.0, ratio_a=24.0, ratio_b=8.0, ratio_near=3.0, chunk=32):
     c, rho, nv = _element_table(g)
     t = _images(g)
     C = (c[:, None, :] + t[None]).reshape(-1, 3)          # (el*img, 3)
     R = np.repeat(rho, t.shape[0])
     NV = np.repeat(nv, t.shape[0])
     na = np.where(NV == 4, 9, 6)
-    counts = {"pairs": 0, "a": 0, "b": 0, "c": 0, "near": 0, "nodes": 0, "sample_points": 0}
+    counts = {"pairs": 0, "t0": 0, "a": 0, "b": 0, "c": 0, "near": 0, "nodes": 0, "sample_points": 0}
     P = pts[:sample]
     for s in range(0, P.shape[0], chunk):
         d = np.linalg.norm(P[s:s + chunk, None, :] - C[None], axis=2) / R[None]
-        ta = d >= ratio_a
-        tb = (~ta) & (d >= ratio_b)
-        tc = (~ta) & (~tb) & (d >= ratio_near)
+        t0 = d >= ratio_0
+        ta = (~t0) & (d >= ratio_a)
+        tb = (d < ratio_a) & (d >= ratio_b)
+        tc = (d < ratio_b) & (d >= ratio_near)
         tn = d < ratio_near
         counts["pairs"] += d.size
+        counts["t0"] += int(t0.sum())
         counts["a"] += int(ta.sum())
         counts["b"] += int(tb.sum())
         counts["c"] += int(tc.sum())
         counts["near"] += int(tn.sum())
-        counts["nodes"] += int((ta * na[None]).sum() + 16 * tb.sum() + 36 * tc.sum())
+        counts["nodes"] += int(4 * t0.sum() + (ta * na[None]).sum() + 16 * tb.sum() + 36 * tc.sum())
     counts["sample_points"] = int(P.shape[0])
     return counts
 

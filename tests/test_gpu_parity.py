@@ -274,3 +274,26 @@ def test_fill_parity_double_thgem_full_size_sampled(N):
     ref = O.fill_entries(g, rows, cols)
     diag = O.fill_entries(g, rows, rows)
     assert (np.abs(got - ref) / np.abs(diag)).max() <= TOL64
+
+
+def test_dense_lu_device_matches_oracle(N):
+    """nebem_lu_factor_device / nebem_lu_solve_device on a BEM matrix (oracle-filled) and
+    on a ragged size, against the oracle's LU: same pivots, factors and solution."""
+    import torch
+    ctx = N.Context()
+    for g in (I.cube(n_per_edge=8), I.thgem(I.PlateSpec(n_phi=12, n_r=2, n_zc=1, n_zf=3), n_plane=2)):
+        K = O.fill(g)
+        n = K.shape[0]
+        A_ref, piv_ref = O.lu_factor(K)
+        dA = torch.tensor(np.asfortranarray(K).ravel(order="F"), device="cuda")
+        dpiv = torch.empty(n, dtype=torch.int32, device="cuda")
+        N.nebem_lu_factor_device(ctx.h, dA.data_ptr(), n, dpiv.data_ptr())
+        assert np.array_equal(dpiv.cpu().numpy(), piv_ref)
+        LU = dA.cpu().numpy()
+        assert np.abs(LU - A_ref).max() <= TOL64 * np.abs(A_ref).max()
+        b = O.rhs(g)
+        db = torch.tensor(b, device="cuda")
+        N.nebem_lu_solve_device(ctx.h, dA.data_ptr(), n, dpiv.data_ptr(), db.data_ptr())
+        torch.cuda.synchronize()
+        x_ref = O.lu_solve((A_ref, piv_ref), b)
+        assert np.abs(db.cpu().numpy() - x_ref).max() <= TOL64 * np.abs(x_ref).max()
