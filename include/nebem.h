@@ -240,6 +240,24 @@ int nebem_lu_factor_device(nebem_ctx *ctx, double *d_A, int64_t n, int32_t *d_pi
 int nebem_lu_solve_device(nebem_ctx *ctx, const double *d_LU, int64_t n, const int32_t *d_piv, double *d_b,
                           void *stream);
 
+/* The same factorisation as nebem_lu_factor_device for callers that cannot allocate
+ * device memory while they run: codes that reserve the device's memory up front for
+ * their own pool (where a cudaMalloc would fail or fragment it), or loops that must not
+ * allocate after start-up (cudaMalloc / cudaFree can synchronise the device).  There is
+ * no counterpart in the paper; this is a property of the library, not of the method.
+ *   d_A, d_piv  as in nebem_lu_factor_device (device memory owned by the caller).
+ *   n           1 <= n <= 4096; larger n returns NEBEM_TOO_LARGE before any GPU work.
+ *   stream      cudaStream_t the work runs on (NULL = the legacy default stream); the
+ *               call synchronises it before returning.
+ * Needs no context: it runs on the calling thread's current device.  Its work space is a
+ * fixed static device array of the library (about 2.1 MB, held on every GPU that loads
+ * the library until the process exits); the first call on a device looks up that array's
+ * device address and caches it.  All calls on a device share the array, so calls whose
+ * GPU work overlaps in time race on it: serialise them.  No memory is allocated by the
+ * call (it issues only kernel launches, a memset and one small device-to-host copy).
+ * Errors: NEBEM_INVALID_ARG, NEBEM_TOO_LARGE, NEBEM_SINGULAR, NEBEM_CUDA. */
+int nebem_lu_factor_device_noalloc(double *d_A, int64_t n, int32_t *d_piv, void *stream);
+
 /* Image translations of the current geometry in index order (count * 3 doubles,
  * host).  *count receives the number of images; t_out may be NULL to query it. */
 int nebem_image_table(nebem_ctx *ctx, double *t_out, int64_t *count);

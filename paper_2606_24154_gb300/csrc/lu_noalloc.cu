@@ -1,0 +1,77 @@
+// lu_noalloc.cu -- dense LU factorisation entry point that allocates no memory.
+//
+// Some callers cannot call cudaMalloc while they run: codes that reserve the device's
+// memory up front for their own pool (a cudaMalloc would fail, or fragment the pool),
+// and latency-critical loops that must not allocate after start-up (cudaMalloc and
+// cudaFree can synchronise the device).  nebem_lu_factor_device_noalloc gives them the
+// same factorisation as nebem_lu_factor_device with its work space (the inverse of the
+// diagonal block, the row-panel staging buffer, the pivot-search partials and the
+// singularity flag) in one file-scope device array instead of a per-call allocation.
+//
+// The array is a static __device__ object of this library: every GPU that loads the
+// library holds it (about 2.1 MB) until the process exits, and all calls on a device
+// share it, so calls whose GPU work overlaps in time race on it.  In host code its name
+// is only a host-side stand-in; the device address is obtained once per device with
+// cudaGetSymbolAddress (on the first call made with that device current) and cached.
+#include <mutex>
+
+#include "context.h"
+
+namespace nb {
+
+namespace {
+
+constexpr int64_t kNoAllocMaxN = 4096;
+constexpr int kNoAllocBlock = 64;
+// lu_work_elems(kNoAllocMaxN, kNoAllocBlock) doubles of work space, then the flag
+constexpr size_t kWorkDoubles = (size_t)kNoAllocBlock * kNoAllocBlock + (size_t)kNoAllocBlock * kNoAllocMaxN + 16 +
+                                (size_t)256 * 4;
+constexpr size_t kScratchDoubles = kWorkDoubles + 32;
+
+static __device__ __align__(256) double g_lu_scratch[kScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+double* g_addr[kMaxDevices] = {nullptr};
+
+int scratch_address(int dev, double** out) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_lu_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_lu_scratch)");
+        g_addr[dev] = static_cast<double*>(p);
+    }
+    *out = g_addr[dev];
+    return NEBEM_OK;
+}
+
+}  // namespace
+
+}  // namespace nb
+
+using namespace nb;
+
+extern "C" int nebem_lu_factor_device_noalloc(double* d_A, int64_t n, int32_t* d_piv, void* stream) {
+    if (!d_A || !d_piv || n <= 0) return fail(NEBEM_INVALID_ARG, "bad argument");
+    if (n > kNoAllocMaxN)
+        return fail(NEBEM_TOO_LARGE, "nebem_lu_factor_device_noalloc handles n <= 4096 (static work space)");
+    static_assert(kWorkDoubles >= 64 * 64 + 64 * 4096 + 16 + 256 * 4, "work space too small");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(NEBEM_INVALID_ARG, "device ordinal beyond 63");
+    double* scratch = nullptr;
+    int rc = scratch_address(dev, &scratch);
+    if (rc) return rc;
+    int* info = reinterpret_cast<int*>(scratch + kWorkDoubles);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    e = lu_factor_f64(d_A, n, d_piv, kNoAllocBlock, scratch, info, s);  // clears the flag first
+    if (e != cudaSuccess) return cuda_fail(e, "lu_factor_f64");
+    int h_info = 0;
+    e = cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "nebem_lu_factor_device_noalloc");
+    if (h_info) return fail(NEBEM_SINGULAR, "zero pivot at column " + std::to_string(h_info - 1));
+    return NEBEM_OK;
+}

@@ -99,6 +99,7 @@ SIGNATURES = {
     "nebem_step": (C.c_int, [_vp, C.c_int32, C.c_double, C.c_double, C.c_int32, _d]),
     "nebem_lu_factor_device": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp]),
     "nebem_lu_solve_device": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp]),
+    "nebem_lu_factor_device_noalloc": (C.c_int, [_vp, C.c_int64, _vp, _vp]),
     "nebem_image_table": (C.c_int, [_vp, _d, _i64p]),
     "nebem_element_influence": (C.c_int, [_vp, _vp, C.c_int64, _d, C.c_int64, _d, _d]),
     "nebem_server_default_options": (C.c_int, [C.POINTER(nebem_server_options)]),
@@ -262,6 +263,11 @@ def nebem_lu_factor_device(ctx, d_A: int, n: int, d_piv: int, stream: int | None
 
 def nebem_lu_solve_device(ctx, d_LU: int, n: int, d_piv: int, d_b: int, stream: int | None = None):
     _check(load().nebem_lu_solve_device(ctx, d_LU, n, d_piv, d_b, stream), "nebem_lu_solve_device")
+
+
+def nebem_lu_factor_device_noalloc(d_A: int, n: int, d_piv: int, stream: int | None = None):
+    """Dense LU with the library's static work space (n <= 4096); allocates nothing."""
+    _check(load().nebem_lu_factor_device_noalloc(d_A, n, d_piv, stream), "nebem_lu_factor_device_noalloc")
 
 
 def nebem_image_table(ctx):
