@@ -374,7 +374,7 @@ def run_native(args):
             "e2e": {"value": e2e_val, "unit": "evals/s", "h2d_bytes_per_step": int(pts_pin.numel() * 8),
                     "d2h_bytes_per_step": int((phi_pin.numel() + E_pin.numel()) * 8)},
             "cpu_baseline": cpu,
-            "gpu_launches": 2 * args.steps,  # k_eval_far + k_eval_near per step
+            "gpu_launches": 5 * args.steps,  # k_bin_keys, k_bin_scan, k_bin_scatter, k_eval_far, k_eval_near per step
             "clocks": clocks,
             "wall_s_timed_region": wall,
         }

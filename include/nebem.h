@@ -235,6 +235,13 @@ int nebem_step(nebem_ctx *ctx, int32_t steps, double mu, double dt, int32_t prec
  * incomplete), NEBEM_INVALID_ARG, NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
 int nebem_lu_factor_device(nebem_ctx *ctx, double *d_A, int64_t n, int32_t *d_piv, void *stream);
 
+/* FP32 variant (the factorisation inside mixed solves): d_A is float, n x n column-major.
+ * The rank-64 trailing updates run on the tensor cores (tcgen05, TF32 with a hi/lo split
+ * of both operands, FP32 accumulation); panels, swaps and the unit-lower block inverse
+ * run in FP32 on the CUDA cores.  Errors as nebem_lu_factor_device, plus NEBEM_TIMEOUT if
+ * a tensor-core update's bounded wait gave up. */
+int nebem_lu_factor_device_f32(nebem_ctx *ctx, float *d_A, int64_t n, int32_t *d_piv, void *stream);
+
 /* Solve A x = b in place with factors from nebem_lu_factor_device: d_b (device, n) is
  * overwritten by x.  Asynchronous on `stream` (NULL = the context stream). */
 int nebem_lu_solve_device(nebem_ctx *ctx, const double *d_LU, int64_t n, const int32_t *d_piv, double *d_b,

@@ -364,7 +364,7 @@ int nebem_lu_factor_device(nebem_ctx* ctx, double* d_A, int64_t n, int32_t* d_pi
     const int nb = c->opt.lu_block;
     DevBuf work, info;
     CK(work.ensure(sizeof(double) * lu_work_elems(n, nb)));
-    CK(info.ensure(sizeof(int)));
+    CK(info.ensure(2 * sizeof(int)));
     CK(lu_factor_f64(d_A, n, d_piv, nb, work.as<double>(), info.as<int>(), s));
     int h_info = 0;
     CK(cudaMemcpyAsync(&h_info, info.ptr, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -372,6 +372,26 @@ int nebem_lu_factor_device(nebem_ctx* ctx, double* d_A, int64_t n, int32_t* d_pi
     work.release();
     info.release();
     if (h_info) return fail(NEBEM_SINGULAR, "zero pivot at column " + std::to_string(h_info - 1));
+    return NEBEM_OK;
+}
+
+int nebem_lu_factor_device_f32(nebem_ctx* ctx, float* d_A, int64_t n, int32_t* d_piv, void* stream) {
+    if (!ctx || n <= 0 || !d_A || !d_piv) return fail(NEBEM_INVALID_ARG, "bad argument");
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    const int nb = c->opt.lu_block;
+    DevBuf work, info;
+    CK(work.ensure(sizeof(double) * lu_work_elems(n, nb)));
+    CK(info.ensure(2 * sizeof(int)));
+    CK(lu_factor_f32(d_A, n, d_piv, nb, work.as<float>(), info.as<int>(), s));
+    int h2[2] = {0, 0};
+    CK(cudaMemcpyAsync(h2, info.ptr, sizeof(h2), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    work.release();
+    info.release();
+    if (h2[1]) return fail(NEBEM_TIMEOUT, "tensor-core trailing update: bounded wait gave up");
+    if (h2[0]) return fail(NEBEM_SINGULAR, "zero pivot at column " + std::to_string(h2[0] - 1));
     return NEBEM_OK;
 }
 

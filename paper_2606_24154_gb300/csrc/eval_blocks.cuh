@@ -77,8 +77,10 @@ __device__ __forceinline__ void nodes_f32(const float4* __restrict__ nd, float d
     }
 }
 
-// Far part (FP32 tiers) of `count` targets; writes ke * sum (overwrites phi / E).
-__device__ __forceinline__ void far_block(const GeomView& g, const double* __restrict__ pts, int count,
+// Far part (FP32 tiers) of `count` targets; writes ke * sum (overwrites phi / E).  Thread
+// t takes point idx[base + t] (or base + t when idx is null) of pts / phi / E.
+__device__ __forceinline__ void far_block(const GeomView& g, const double* __restrict__ pts,
+                                          const int32_t* __restrict__ idx, int64_t base, int count,
                                           double* __restrict__ phi, double* __restrict__ E) {
     const FarNodes* __restrict__ far = g.far;
     const float4* __restrict__ cjk = g.cjk;
@@ -93,10 +95,11 @@ __device__ __forceinline__ void far_block(const GeomView& g, const double* __res
     __shared__ float s_sig[kTileMax];
     __shared__ float4 s_c[kCjkMax][2];  // image centroids: hi, lo
 
-    const int p = threadIdx.x;
-    const bool active = p < count;
+    const bool active = (int)threadIdx.x < count;
+    int64_t p = 0;
     double Px = 0.0, Py = 0.0, Pz = 0.0;
     if (active) {
+        p = idx ? (int64_t)idx[base + threadIdx.x] : base + threadIdx.x;
         Px = pts[3 * p];
         Py = pts[3 * p + 1];
         Pz = pts[3 * p + 2];

@@ -1,6 +1,7 @@
-// eval_mixed.cu -- mixed-precision evaluation kernels (bodies in eval_blocks.cuh): the FP32
-// far-field kernel over all (element, image) pairs, the FP64 near-pair kernel over the
-// cell list, and the per-geometry two-float image-centroid table.
+// eval_mixed.cu -- mixed-precision evaluation kernels (bodies in eval_blocks.cuh): spatial
+// binning of the targets, the FP32 far-field kernel over all (element, image) pairs, the
+// FP64 near-pair kernel over the cell list, and the per-geometry two-float image-centroid
+// table.
 #include "eval_blocks.cuh"
 
 namespace nb {
@@ -8,19 +9,84 @@ namespace nb {
 namespace {
 
 __global__ void __launch_bounds__(kEvalThreads, 8) k_eval_far(const GeomView g, const double* __restrict__ pts,
-                                                            int64_t npts, double* __restrict__ phi,
-                                                            double* __restrict__ E) {
+                                                            const int32_t* __restrict__ order, int64_t npts,
+                                                            double* __restrict__ phi, double* __restrict__ E) {
     const int64_t base = (int64_t)blockIdx.x * blockDim.x;
     const int count = (int)min((int64_t)blockDim.x, npts - base);
-    far_block(g, pts + 3 * base, count, phi ? phi + base : nullptr, E ? E + 3 * base : nullptr);
+    far_block(g, pts, order, base, count, phi, E);
 }
 
 __global__ void __launch_bounds__(kEvalThreads) k_eval_near(const GeomView g, const ImageTable img,
-                                                          const double* __restrict__ pts, int64_t npts,
+                                                          const double* __restrict__ pts,
+                                                          const int32_t* __restrict__ order, int64_t npts,
                                                           double* __restrict__ phi, double* __restrict__ E) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= npts) return;
-    near_point(g, img, pts, p, phi, E);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npts) return;
+    near_point(g, img, pts, order ? (int64_t)order[i] : i, phi, E);
+}
+
+// ---- spatial binning of the targets: counting sort by the Morton index of a 64^3 grid
+// over the near-pair grid's box (points outside are clamped to the border cells).  Warps
+// then hold nearby points, whose (element, image) pairs mostly fall in the same distance
+// tier, so the tier branches stay converged.  The order only changes which lane evaluates
+// a point, never the point's arithmetic; positions within a cell come from atomics and
+// may differ between runs without changing any result.
+constexpr int kBinBits = 6;
+constexpr int kBins = 1 << (3 * kBinBits);
+
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {  // 6 bits -> every third bit
+    uint32_t r = 0;
+#pragma unroll
+    for (int b = 0; b < kBinBits; ++b) r |= ((v >> b) & 1u) << (3 * b);
+    return r;
+}
+
+__global__ void k_bin_keys(const double* __restrict__ pts, int64_t n, const NearGrid grid,
+                           int32_t* __restrict__ key, int32_t* __restrict__ count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const double span = (double)grid.dims[a] / grid.inv_h;
+        double f = floor((pts[3 * i + a] - grid.origin[a]) / span * (double)(1 << kBinBits));
+        f = fmin(fmax(f, 0.0), (double)((1 << kBinBits) - 1));
+        c[a] = (uint32_t)f;
+    }
+    const int32_t k = (int32_t)(spread3(c[0]) | (spread3(c[1]) << 1) | (spread3(c[2]) << 2));
+    key[i] = k;
+    atomicAdd(&count[k], 1);
+}
+
+// Exclusive scan of kBins counts by one block of 1024 threads (kBins / 1024 per thread):
+// per-thread sums, a block scan of those, then each thread rewrites its range in place.
+__global__ void __launch_bounds__(1024) k_bin_scan(int32_t* __restrict__ count) {
+    constexpr int per = kBins / 1024;
+    __shared__ int32_t part[1024];
+    int32_t* mine = count + threadIdx.x * per;
+    int32_t s = 0;
+    for (int j = 0; j < per; ++j) s += mine[j];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int32_t v = (threadIdx.x >= (unsigned)off) ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int32_t run = part[threadIdx.x] - s;  // exclusive prefix of this thread's range
+    for (int j = 0; j < per; ++j) {
+        const int32_t c = mine[j];
+        mine[j] = run;
+        run += c;
+    }
+}
+
+__global__ void k_bin_scatter(const int32_t* __restrict__ key, int64_t n, int32_t* __restrict__ next,
+                              int32_t* __restrict__ order) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    order[atomicAdd(&next[key[i]], 1)] = (int32_t)i;
 }
 
 // Two-float image centroids, entry (j, k) at 2 * (j * nimg + k): hi then lo.
@@ -62,17 +128,31 @@ GeomView make_view(const Elem* el, const FarNodes* far, const float4* cjk, const
     return g;
 }
 
+size_t eval_mixed_scratch_bytes(int64_t npts) {
+    return sizeof(int32_t) * ((size_t)kBins + 2 * (size_t)npts);
+}
+
 cudaError_t launch_eval_mixed(const Elem* el, const FarNodes* far, const float4* cjk, const double* sigma,
                               int64_t n_el, const ImageTable& img, const NearGrid& grid, const int32_t* cell_start,
                               const int32_t* cell_items, const double* pts, int64_t npts, double* phi, double* E,
-                              cudaStream_t s) {
+                              void* scratch, cudaStream_t s) {
     if (npts == 0) return cudaSuccess;
+    if (npts > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
     const GeomView g = make_view(el, far, cjk, sigma, n_el, img, grid, cell_start, cell_items);
-    const unsigned blocks = (unsigned)((npts + kEvalThreads - 1) / kEvalThreads);
-    k_eval_far<<<blocks, kEvalThreads, 0, s>>>(g, pts, npts, phi, E);
-    cudaError_t e = cudaGetLastError();
+    int32_t* count = static_cast<int32_t*>(scratch);
+    int32_t* key = count + kBins;
+    int32_t* order = key + npts;
+    const unsigned pblocks = (unsigned)((npts + 255) / 256);
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int32_t) * kBins, s);
     if (e != cudaSuccess) return e;
-    k_eval_near<<<blocks, kEvalThreads, 0, s>>>(g, img, pts, npts, phi, E);
+    k_bin_keys<<<pblocks, 256, 0, s>>>(pts, npts, grid, key, count);
+    k_bin_scan<<<1, 1024, 0, s>>>(count);
+    k_bin_scatter<<<pblocks, 256, 0, s>>>(key, npts, count, order);
+    const unsigned blocks = (unsigned)((npts + kEvalThreads - 1) / kEvalThreads);
+    k_eval_far<<<blocks, kEvalThreads, 0, s>>>(g, pts, order, npts, phi, E);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_eval_near<<<blocks, kEvalThreads, 0, s>>>(g, img, pts, order, npts, phi, E);
     return cudaGetLastError();
 }
 

@@ -245,7 +245,8 @@ cudaError_t gemm(int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t l
 // then kPivBlocks doubles + kPivBlocks int64 for the pivot search.
 template <typename T>
 cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_info, cudaStream_t s) {
-    NB_TRY(cudaMemsetAsync(d_info, 0, sizeof(int), s));
+    // d_info[0]: first zero pivot (1-based) or 0; d_info[1]: tensor-core update gave up
+    NB_TRY(cudaMemsetAsync(d_info, 0, 2 * sizeof(int), s));
     T* Linv = work;
     T* W = work + (size_t)nb * nb;
     char* tail = reinterpret_cast<char*>(W + (size_t)nb * n);
@@ -274,7 +275,16 @@ cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_inf
             // W = Linv * A12  (w x m), then A12 = W
             NB_TRY(gemm<T>(w, m, w, (T)1, Linv, w, A + k0 + k1 * n, n, (T)0, W, w, s));
             k_copy_block<T><<<(unsigned)((w * m + 255) / 256), 256, 0, s>>>(W, w, A + k0 + k1 * n, n, w, m);
-            // A22 -= L21 * U12
+            // A22 -= L21 * U12: tensor cores (TF32 x3) for the FP32 factorisation's 64-wide
+            // panels, FP64 FMA for the FP64 factorisation
+            if constexpr (sizeof(T) == 4) {
+                if (w == 64) {
+                    NB_TRY(tc_update_f32(m, m, reinterpret_cast<const float*>(A + k1 + k0 * n), n,
+                                         reinterpret_cast<const float*>(A + k0 + k1 * n), n,
+                                         reinterpret_cast<float*>(A + k1 + k1 * n), n, d_info + 1, s));
+                    continue;
+                }
+            }
             NB_TRY(gemm<T>(m, m, w, (T)-1, A + k1 + k0 * n, n, A + k0 + k1 * n, n, (T)1, A + k1 + k1 * n, n, s));
         }
         NB_TRY(cudaGetLastError());

@@ -26,7 +26,7 @@ constexpr int kNoAllocBlock = 64;
 // lu_work_elems(kNoAllocMaxN, kNoAllocBlock) doubles of work space, then the flag
 constexpr size_t kWorkDoubles = (size_t)kNoAllocBlock * kNoAllocBlock + (size_t)kNoAllocBlock * kNoAllocMaxN + 16 +
                                 (size_t)256 * 4;
-constexpr size_t kScratchDoubles = kWorkDoubles + 32;
+constexpr size_t kScratchDoubles = kWorkDoubles + 32;  // + flags (two ints)
 
 static __device__ __align__(256) double g_lu_scratch[kScratchDoubles];
 

@@ -1,0 +1,195 @@
+// lu_tc.cu -- trailing-matrix update of the mixed (FP32) LU on the 5th-generation tensor
+// cores: C[M x N] -= A[M x 64] * B[64 x N] (column-major FP32), the rank-64 update that
+// follows each panel of the blocked factorisation (Sec. 4.1 / Alg. 1: LU; the trailing
+// update carries almost all of its 2/3 N^3 flops).
+//
+// Each CTA (128 threads) owns a 128 x 128 tile of C.  The A and B tiles are split into
+// TF32 pairs (hi = x rounded to TF32, lo = x - hi) and staged in shared memory in the
+// canonical K-major, non-swizzled UMMA layout (8-row x 16-byte core matrices; core
+// matrices adjacent along K are LBO = 128 B apart, 8-row groups SBO = 2048 B apart).
+// One elected thread issues tcgen05.mma kind::tf32 (M = 128, N = 128, K = 8 per
+// instruction) for lo*hi, hi*lo and hi*hi -- 24 instructions accumulating in FP32 in
+// tensor memory (128 lanes x 128 columns) -- then commits to an mbarrier.  The product is
+// read back with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = rows of C) and
+// subtracted from C in global memory.  The three-term split keeps the product within a
+// few FP32 units of roundoff, which the FP64 iterative refinement of the solve expects.
+//
+// The mbarrier wait is bounded: after kSpinLimit polls the CTA records an error flag,
+// skips the epilogue, still frees its tensor memory and returns.
+#include "nb_internal.h"
+
+namespace nb {
+
+namespace {
+
+constexpr int kTM = 128, kTN = 128, kTK = 64;
+constexpr uint32_t kCoreBytes = 128;                 // 8 rows x 16 bytes
+constexpr uint32_t kLBO = kCoreBytes;                // next core matrix along K
+constexpr uint32_t kSBO = (kTK / 4) * kCoreBytes;    // next 8-row group: 2048 B
+constexpr uint32_t kOperandBytes = kTM * kTK * 4;    // 32 KB per operand tile
+constexpr uint32_t kSmemBytes = 4 * kOperandBytes + 64;
+constexpr long long kSpinLimit = 1ll << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// byte offset of element (row r, k) in a K-major non-swizzled operand tile
+__device__ __forceinline__ uint32_t kmajor_off(int r, int k) {
+    return (uint32_t)(r >> 3) * kSBO + (uint32_t)(k >> 2) * kLBO + (uint32_t)(r & 7) * 16u + (uint32_t)(k & 3) * 4u;
+}
+
+// shared-memory matrix descriptor: start >> 4 (bits 0-13), LBO >> 4 (16-29), SBO >> 4
+// (32-45), fixed 0b001 at bits 46-48, base offset 0, no swizzle (bits 61-63 = 0)
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(kLBO >> 4) << 16;
+    d |= (uint64_t)(kSBO >> 4) << 32;
+    d |= 1ull << 46;
+    return d;
+}
+
+// instruction descriptor, kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32 (bits 7-9,
+// 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22, M >> 4 at bits 24-28
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTN >> 3) << 17) |
+                            ((uint32_t)(kTM >> 4) << 24);
+
+__device__ __forceinline__ float tf32_hi(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__global__ void __launch_bounds__(128, 1) k_tc_update(int64_t M, int64_t N, const float* __restrict__ A, int64_t lda,
+                                                       const float* __restrict__ B, int64_t ldb, float* __restrict__ C,
+                                                       int64_t ldc, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* a_hi = smem;
+    unsigned char* a_lo = smem + kOperandBytes;
+    unsigned char* b_hi = smem + 2 * kOperandBytes;
+    unsigned char* b_lo = smem + 3 * kOperandBytes;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 4 * kOperandBytes);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 4 * kOperandBytes + 16);
+
+    const int64_t m0 = (int64_t)blockIdx.x * kTM, n0 = (int64_t)blockIdx.y * kTN;
+    const int tid = threadIdx.x, warp = tid >> 5;
+
+    // ---- stage A (rows m0.., K = 64; column-major source: m fastest) and B (K x N,
+    //      column-major source: k fastest) as TF32 hi/lo pairs
+    for (int idx = tid; idx < kTM * kTK; idx += 128) {
+        const int r = idx % kTM, k = idx / kTM;
+        const int64_t gm = m0 + r;
+        const float x = (gm < M) ? A[gm + (int64_t)k * lda] : 0.f;
+        const float h = tf32_hi(x);
+        const uint32_t o = kmajor_off(r, k);
+        *reinterpret_cast<float*>(a_hi + o) = h;
+        *reinterpret_cast<float*>(a_lo + o) = x - h;
+    }
+    for (int idx = tid; idx < kTN * kTK; idx += 128) {
+        const int k = idx % kTK, c = idx / kTK;
+        const int64_t gn = n0 + c;
+        const float x = (gn < N) ? B[k + gn * ldb] : 0.f;
+        const float h = tf32_hi(x);
+        const uint32_t o = kmajor_off(c, k);
+        *reinterpret_cast<float*>(b_hi + o) = h;
+        *reinterpret_cast<float*>(b_lo + o) = x - h;
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    // make the generic-proxy smem writes visible to the tensor core (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;");
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+
+    // ---- issue the 24 MMAs from one thread: lo*hi, hi*lo, hi*hi over 8 K-steps of 8
+    if (tid == 0) {
+        const unsigned char* As[3] = {a_lo, a_hi, a_hi};
+        const unsigned char* Bs[3] = {b_hi, b_lo, b_hi};
+        uint32_t first = 1;
+        for (int t = 0; t < 3; ++t) {
+            for (int ks = 0; ks < kTK / 8; ++ks) {
+                // one K-step of 8 TF32 = two core matrices along K = 2 * LBO bytes
+                const uint64_t ad = make_desc(smem_u32(As[t]) + (uint32_t)ks * 2u * kLBO);
+                const uint64_t bd = make_desc(smem_u32(Bs[t]) + (uint32_t)ks * 2u * kLBO);
+                const uint32_t acc = first ? 0u : 1u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+                first = 0;
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(mbar)));
+    }
+
+    // ---- bounded wait for the MMAs (phase 0)
+    uint32_t done = 0;
+    for (long long it = 0; it < kSpinLimit && !done; ++it) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_u32(mbar)));
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int ok = __syncthreads_and((int)done);
+    if (!ok) {
+        if (tid == 0) atomicExch(err, 1);
+    } else {
+        // ---- epilogue: warp w reads TMEM lanes 32w + (0..31) = rows of the tile, 32 columns
+        //      at a time, and subtracts from C (consecutive rows per column: coalesced)
+        const int64_t row = m0 + warp * 32 + (tid & 31);
+        for (int cb = 0; cb < kTN; cb += 32) {
+            uint32_t v[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (row < M) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int64_t col = n0 + cb + j;
+                    if (col < N) C[row + col * ldc] -= __uint_as_float(v[j]);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTN));
+}
+
+}  // namespace
+
+cudaError_t tc_update_f32(int64_t M, int64_t N, const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
+                          int64_t ldc, int* err, cudaStream_t s) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid((unsigned)((M + kTM - 1) / kTM), (unsigned)((N + kTN - 1) / kTN));
+    k_tc_update<<<grid, 128, kSmemBytes, s>>>(M, N, A, lda, B, ldb, C, ldc, err);
+    return cudaGetLastError();
+}
+
+}  // namespace nb

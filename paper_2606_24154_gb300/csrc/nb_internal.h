@@ -92,14 +92,21 @@ cudaError_t launch_eval_f64(const Elem* el, const double* sigma, int64_t n_el, c
 cudaError_t launch_eval_mixed(const Elem* el, const FarNodes* far, const float4* cjk, const double* sigma,
                               int64_t n_el, const ImageTable& img, const NearGrid& grid, const int32_t* cell_start,
                               const int32_t* cell_items, const double* pts, int64_t npts, double* phi, double* E,
-                              cudaStream_t s);
+                              void* scratch, cudaStream_t s);
+// scratch bytes launch_eval_mixed needs for npts points (target binning)
+size_t eval_mixed_scratch_bytes(int64_t npts);
 cudaError_t launch_image_centroids(const Elem* el, int64_t n, const ImageTable& img, float4* cjk, cudaStream_t s);
 cudaError_t launch_fill_f64(const Elem* el, const double* diag, int64_t n, const ImageTable& img, double* K,
                             cudaStream_t s);
 cudaError_t launch_element_influence(const Elem* el, int64_t n_el, const double* pts, int64_t npts,
                                      double* phi, double* E, cudaStream_t s);
 
-// Dense LU (column-major, lda = n).  Scratch: pivots int32[n], work as documented in lu.cu.
+// C[M x N] -= A[M x 64] * B[64 x N] on tcgen05 tensor cores (TF32 x3 split, FP32
+// accumulation); *err is set if the bounded wait for the MMAs gave up.
+cudaError_t tc_update_f32(int64_t M, int64_t N, const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
+                          int64_t ldc, int* err, cudaStream_t s);
+
+// Dense LU (column-major, lda = n).  d_info: two ints (first zero pivot, tensor-core timeout).  Scratch: pivots int32[n], work as documented in lu.cu.
 cudaError_t lu_factor_f64(double* A, int64_t n, int32_t* piv, int nb, double* work, int* d_info,
                           cudaStream_t s);
 cudaError_t lu_factor_f32(float* A, int64_t n, int32_t* piv, int nb, float* work, int* d_info,

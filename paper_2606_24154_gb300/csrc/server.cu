@@ -60,8 +60,8 @@ __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restr
         double* phi = arena_phi + it.offset;
         double* E = arena_E + 3 * it.offset;
         if (it.precision == NEBEM_MIXED) {
-            far_block(G.view, pts, it.count, phi, E);
-            if ((int)threadIdx.x < it.count) near_point(G.view, G.img, pts, threadIdx.x, phi, E);
+            far_block(G.view, arena_pts, nullptr, it.offset, it.count, arena_phi, arena_E);
+            if ((int)threadIdx.x < it.count) near_point(G.view, G.img, arena_pts, it.offset + threadIdx.x, arena_phi, arena_E);
         } else {
             f64_block(G.view.el, G.view.sigma, G.view.n_el, G.img, pts, it.count, phi, E);
         }

@@ -72,7 +72,10 @@ int ensure_factors(Ctx* c, int precision, double* ms) {
                          c->d_small.as<int>(), c->stream));
         int rc = elapsed_ms(c, ms);
         if (rc) return rc;
-        CK(cudaMemcpy(&h_info, c->d_small.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+        int h2[2] = {0, 0};
+        CK(cudaMemcpy(h2, c->d_small.ptr, sizeof(h2), cudaMemcpyDeviceToHost));
+        h_info = h2[0];
+        if (h2[1]) return fail(NEBEM_TIMEOUT, "tensor-core trailing update: bounded wait gave up");
         if (h_info) return fail(NEBEM_SINGULAR, "zero pivot at column " + std::to_string(h_info - 1));
         c->fac32_valid = true;
     }
@@ -155,12 +158,15 @@ int solve_with_factors(Ctx* c, int precision, nebem_solve_info* info) {
 }
 
 int eval_elements(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision, cudaStream_t s) {
-    if (precision == NEBEM_MIXED)
+    if (precision == NEBEM_MIXED) {
+        CK(c->d_scratch.ensure(eval_mixed_scratch_bytes(n)));
         CK(launch_eval_mixed(c->d_el.as<Elem>(), c->d_far.as<FarNodes>(), c->d_cjk.as<float4>(),
                              c->d_sigma.as<double>(), c->n, c->img, c->grid, c->d_cell_start.as<int32_t>(),
-                             c->d_cell_items.as<int32_t>(), d_pts, n, d_phi, d_E, s));
-    else
+                             c->d_cell_items.as<int32_t>(), d_pts, n, d_phi, d_E, c->d_scratch.ptr, s));
+    }
+    else {
         CK(launch_eval_f64(c->d_el.as<Elem>(), c->d_sigma.as<double>(), c->n, c->img, d_pts, n, d_phi, d_E, s));
+    }
     return 0;
 }
 

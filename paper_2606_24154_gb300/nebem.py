@@ -98,6 +98,7 @@ SIGNATURES = {
     "nebem_space_charge_eval": (C.c_int, [_vp, _d, C.c_int64, _d, _d, C.c_int32, C.c_int32]),
     "nebem_step": (C.c_int, [_vp, C.c_int32, C.c_double, C.c_double, C.c_int32, _d]),
     "nebem_lu_factor_device": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp]),
+    "nebem_lu_factor_device_f32": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp]),
     "nebem_lu_solve_device": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp]),
     "nebem_lu_factor_device_noalloc": (C.c_int, [_vp, C.c_int64, _vp, _vp]),
     "nebem_image_table": (C.c_int, [_vp, _d, _i64p]),
@@ -259,6 +260,10 @@ def nebem_step(ctx, steps: int, mu: float, dt: float, precision: int, n_carriers
 
 def nebem_lu_factor_device(ctx, d_A: int, n: int, d_piv: int, stream: int | None = None):
     _check(load().nebem_lu_factor_device(ctx, d_A, n, d_piv, stream), "nebem_lu_factor_device")
+
+
+def nebem_lu_factor_device_f32(ctx, d_A: int, n: int, d_piv: int, stream: int | None = None):
+    _check(load().nebem_lu_factor_device_f32(ctx, d_A, n, d_piv, stream), "nebem_lu_factor_device_f32")
 
 
 def nebem_lu_solve_device(ctx, d_LU: int, n: int, d_piv: int, d_b: int, stream: int | None = None):
