@@ -269,6 +269,13 @@ int nebem_lu_factor_device_noalloc(double *d_A, int64_t n, int32_t *d_piv, void 
  * host).  *count receives the number of images; t_out may be NULL to query it. */
 int nebem_image_table(nebem_ctx *ctx, double *t_out, int64_t *count);
 
+/* Distance tier that the mixed evaluation assigns to every (point, element, image) pair,
+ * for checks: codes[(p * n_el + j) * n_images + k] = 0 (FP32 4-node rule), 1 (6/9-node),
+ * 2 (16-node), 3 (36-node) or 4 (FP64 closed form), decided in FP32 from two-float
+ * coordinates against (ratio * element radius)^2 (the options' ratio_0, ratio_a, ratio_b,
+ * ratio_near).  pts[n][3] and codes are host arrays; at most 2e8 pairs. */
+int nebem_pair_tiers(nebem_ctx *ctx, const double *pts, int64_t n, uint8_t *codes);
+
 /* Influence of single elements (no charge density, no images) at points, for kernel
  * checks: for element e and point p, phi_out[e*n_pts + p] = Phi'(p) (m) and
  * E_out[(e*n_pts + p)*3 + c] = E'_c(p) (dimensionless), in FP64 closed form.

@@ -350,6 +350,66 @@ int or_fill_entries(const or_input *in, int64_t n, const double *lattice, int lo
     return 0;
 }
 
+/* Distance tier of every (point, element, image) pair for the mixed-precision evaluation
+ * (a pair classification written out for checks; codes[(p * n + j) * nimg + k]):
+ *   0: d >= r0 rho_j,  1: >= ra rho_j,  2: >= rb rho_j,  3: >= rn rho_j,  4: nearer,
+ * with rho_j the element's circumradius about its centroid c_j and d the distance from
+ * the point to c_j + t_k.  The decision is taken in FP32, as the evaluation takes it: both
+ * positions split into two floats (hi = fl(x), lo = fl(x - hi)), each difference
+ * (P_hi - C_hi) + (P_lo - C_lo) and d^2 = fma(dx, dx, fma(dy, dy, dz * dz)) rounded in
+ * float (this file is compiled without contraction), thresholds fl((r rho)^2). */
+int or_pair_tiers(const or_input *in, int64_t n, const double *lattice, int lo, int hi, const double *pts,
+                  int64_t npts, const double *ratios, uint8_t *codes) {
+    or_elem *el = (or_elem *)malloc(sizeof(or_elem) * (size_t)(n ? n : 1));
+    int rc = or_build(in, n, el);
+    if (rc) {
+        free(el);
+        return rc;
+    }
+    int64_t nimg = image_count(lattice, lo, hi);
+    double *tt = (double *)malloc(sizeof(double) * 3 * (size_t)nimg);
+    or_image_table(lattice, lo, hi, tt);
+    float *thr = (float *)malloc(sizeof(float) * 4 * (size_t)(n ? n : 1));
+    for (int64_t j = 0; j < n; ++j) {
+        double rho = 0.0;
+        for (int v = 0; v < el[j].nv; ++v) {
+            double d[3] = {in[j].v[v][0] - el[j].c[0], in[j].v[v][1] - el[j].c[1], in[j].v[v][2] - el[j].c[2]};
+            rho = fmax(rho, sqrt(dot3(d, d)));
+        }
+        for (int t = 0; t < 4; ++t) {
+            double r = ratios[t] * rho;
+            thr[4 * j + t] = (float)(r * r);
+        }
+    }
+    for (int64_t p = 0; p < npts; ++p) {
+        float ph[3], pl[3];
+        for (int a = 0; a < 3; ++a) {
+            ph[a] = (float)pts[3 * p + a];
+            pl[a] = (float)(pts[3 * p + a] - (double)ph[a]);
+        }
+        for (int64_t j = 0; j < n; ++j)
+            for (int64_t k = 0; k < nimg; ++k) {
+                float ch[3], cl[3], dd[3];
+                for (int a = 0; a < 3; ++a) {
+                    double C = el[j].c[a] + tt[3 * k + a];
+                    ch[a] = (float)C;
+                    cl[a] = (float)(C - (double)ch[a]);
+                    float u = ph[a] - ch[a];
+                    float w = pl[a] - cl[a];
+                    dd[a] = u + w;
+                }
+                float d2 = fmaf(dd[0], dd[0], fmaf(dd[1], dd[1], dd[2] * dd[2]));
+                const float *th = thr + 4 * j;
+                uint8_t code = (d2 >= th[0]) ? 0 : (d2 >= th[1]) ? 1 : (d2 >= th[2]) ? 2 : (d2 >= th[3]) ? 3 : 4;
+                codes[(p * n + j) * nimg + k] = code;
+            }
+    }
+    free(thr);
+    free(tt);
+    free(el);
+    return 0;
+}
+
 /* In-place LU with partial pivoting (row of max |a|, lowest index on ties), column-major.
  * piv[k] = row swapped with row k at step k.  Returns 0 or -(1+k) for a zero pivot. */
 int or_lu_factor(int64_t n, double *A, int32_t *piv) {

@@ -51,6 +51,8 @@ def lib():
         L.or_fill.argtypes = [_vp, C.c_int64, _d, C.c_int, C.c_int, _d]
         L.or_fill_entries.argtypes = [_vp, C.c_int64, _d, C.c_int, C.c_int, C.POINTER(C.c_int64),
                                       C.POINTER(C.c_int64), C.c_int64, _d]
+        L.or_pair_tiers.argtypes = [_vp, C.c_int64, _d, C.c_int, C.c_int, _d, C.c_int64, _d,
+                                    C.POINTER(C.c_uint8)]
         L.or_lu_factor.argtypes = [C.c_int64, _d, _i32]
         L.or_lu_solve.argtypes = [C.c_int64, _d, _i32, _d]
         L.or_rhs.argtypes = [_vp, C.c_int64, _d, C.c_int32, _d]
@@ -141,6 +143,18 @@ def fill_entries(g, rows, cols):
     _check(lib().or_fill_entries(pe, el.shape[0], _p(lat), g.img_lo, g.img_hi, rows.ctypes.data_as(i64),
                                  cols.ctypes.data_as(i64), rows.shape[0], _p(out)), "fill_entries")
     return out
+
+
+def pair_tiers(g, pts, ratios=(64.0, 24.0, 8.0, 3.0)):
+    """Distance-tier code (0..4) of every (point, element, image) pair, FP32 decision."""
+    el, pe = _rec(g.elements)
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    r = np.ascontiguousarray(ratios, dtype=np.float64)
+    nimg = 1 if g.lattice is None else (g.img_hi - g.img_lo + 1) ** 2
+    codes = np.empty(pts.shape[0] * el.shape[0] * nimg, dtype=np.uint8)
+    _check(lib().or_pair_tiers(pe, el.shape[0], _p(_lat(g)), g.img_lo, g.img_hi, _p(pts), pts.shape[0], _p(r),
+                               codes.ctypes.data_as(C.POINTER(C.c_uint8))), "pair_tiers")
+    return codes.reshape(pts.shape[0], el.shape[0], nimg)
 
 
 def lu_factor(K):

@@ -405,6 +405,27 @@ int nebem_lu_solve_device(nebem_ctx* ctx, const double* d_LU, int64_t n, const i
     return NEBEM_OK;
 }
 
+int nebem_pair_tiers(nebem_ctx* ctx, const double* pts, int64_t n, uint8_t* codes) {
+    if (!ctx || n < 0 || (n > 0 && (!pts || !codes))) return fail(NEBEM_INVALID_ARG, "bad argument");
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (c->n == 0) return fail(NEBEM_BAD_STATE, "set_geometry first");
+    const int64_t total = n * c->n * c->img.n;
+    if (total > 200000000LL) return fail(NEBEM_TOO_LARGE, "more than 2e8 pairs");
+    if (total == 0) return NEBEM_OK;
+    CK(cudaSetDevice(c->device));
+    DevBuf bp, bc;
+    CK(bp.ensure(sizeof(double) * 3 * n));
+    CK(bc.ensure((size_t)total));
+    CK(cudaMemcpyAsync(bp.ptr, pts, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_pair_tiers(c->d_far.as<FarNodes>(), c->d_cjk.as<float4>(), c->n, c->img.n, bp.as<double>(), n,
+                         bc.as<uint8_t>(), c->stream));
+    CK(cudaMemcpyAsync(codes, bc.ptr, (size_t)total, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    bp.release();
+    bc.release();
+    return NEBEM_OK;
+}
+
 int nebem_element_influence(nebem_ctx* ctx, const nebem_element* el, int64_t n_el, const double* pts, int64_t n_pts,
                             double* phi_out, double* E_out) {
     if (!ctx || !el || !pts || !phi_out || !E_out || n_el <= 0 || n_pts <= 0)

@@ -43,6 +43,7 @@ constexpr int kTileMax = 16;       // elements per shared-memory tile (mixed)
 constexpr int kCjkMax = 512;       // (element, image) centres per tile (mixed)
 constexpr int kGroup = 8;          // elements per FP32 partial sum (mixed)
 constexpr int kTile64 = 32;        // elements per shared-memory tile (FP64)
+constexpr int kChunkEl = 1024;     // elements per chunk of the far sums (multiple of every tile width)
 
 // Squared FP32 distance between a point (two floats per coordinate) and an image centroid;
 // the operation sequence is pinned (no contraction) so both kernels agree bit for bit.
@@ -57,6 +58,24 @@ __device__ __forceinline__ float pair_d2(float phx, float phy, float phz, float 
 __device__ __forceinline__ void split2f(double x, float& hi, float& lo) {
     hi = __double2float_rn(x);
     lo = __double2float_rn(x - (double)hi);
+}
+
+// Tier-0 rule with its four nodes held in registers (loaded once per element).
+__device__ __forceinline__ void nodes4_reg(const float4& q0, const float4& q1, const float4& q2, const float4& q3,
+                                           float dx, float dy, float dz, float& ph, float& ex, float& ey, float& ez) {
+    const float4 q[4] = {q0, q1, q2, q3};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float rx = dx - q[i].x, ry = dy - q[i].y, rz = dz - q[i].z;
+        const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+        const float ri = rsqrtf(r2);
+        const float wr = q[i].w * ri;
+        const float wr3 = wr * ri * ri;
+        ph += wr;
+        ex = fmaf(wr3, rx, ex);
+        ey = fmaf(wr3, ry, ey);
+        ez = fmaf(wr3, rz, ez);
+    }
 }
 
 template <int M>
@@ -77,15 +96,18 @@ __device__ __forceinline__ void nodes_f32(const float4* __restrict__ nd, float d
     }
 }
 
-// Far part (FP32 tiers) of `count` targets; writes ke * sum (overwrites phi / E).  Thread
-// t takes point idx[base + t] (or base + t when idx is null) of pts / phi / E.
-__device__ __forceinline__ void far_block(const GeomView& g, const double* __restrict__ pts,
-                                          const int32_t* __restrict__ idx, int64_t base, int count,
-                                          double* __restrict__ phi, double* __restrict__ E) {
+// Raw FP64 sums (phi, E; before the factor ke) of the far pairs of one point over the
+// elements [e0, e1).  Called by every thread of the block (shared-memory tiles); the
+// inactive threads' sums are unused.
+struct Sum4 {
+    double phi, x, y, z;
+};
+
+__device__ __forceinline__ Sum4 far_range(const GeomView& g, float phx, float phy, float phz, float plx, float ply,
+                                          float plz, int64_t e0, int64_t e1) {
     const FarNodes* __restrict__ far = g.far;
     const float4* __restrict__ cjk = g.cjk;
     const double* __restrict__ sigma = g.sigma;
-    const int64_t n_el = g.n_el;
     const int nimg = g.nimg;
     const int tile_el = g.tile_el;
     __shared__ float4 s_f[kTileMax][kNodes0];
@@ -95,23 +117,9 @@ __device__ __forceinline__ void far_block(const GeomView& g, const double* __res
     __shared__ float s_sig[kTileMax];
     __shared__ float4 s_c[kCjkMax][2];  // image centroids: hi, lo
 
-    const bool active = (int)threadIdx.x < count;
-    int64_t p = 0;
-    double Px = 0.0, Py = 0.0, Pz = 0.0;
-    if (active) {
-        p = idx ? (int64_t)idx[base + threadIdx.x] : base + threadIdx.x;
-        Px = pts[3 * p];
-        Py = pts[3 * p + 1];
-        Pz = pts[3 * p + 2];
-    }
-    float phx, phy, phz, plx, ply, plz;
-    split2f(Px, phx, plx);
-    split2f(Py, phy, ply);
-    split2f(Pz, phz, plz);
-
     double aphi = 0.0, aEx = 0.0, aEy = 0.0, aEz = 0.0;
-    for (int64_t base = 0; base < n_el; base += tile_el) {
-        const int cnt = (int)min((int64_t)tile_el, n_el - base);
+    for (int64_t base = e0; base < e1; base += tile_el) {
+        const int cnt = (int)min((int64_t)tile_el, e1 - base);
         __syncthreads();
         for (int i = threadIdx.x; i < cnt * kNodesA; i += blockDim.x)
             s_a[i / kNodesA][i % kNodesA] = far[base + i / kNodesA].a[i % kNodesA];
@@ -130,13 +138,14 @@ __device__ __forceinline__ void far_block(const GeomView& g, const double* __res
             const float4 hdr = s_hdr[jj];
             const bool rect = s_na[jj] == kNodesA;
             const FarNodes* fj = far + base + jj;
+            const float4 q0 = s_f[jj][0], q1 = s_f[jj][1], q2 = s_f[jj][2], q3 = s_f[jj][3];
             float lphi = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
             for (int k = 0; k < nimg; ++k) {
                 float dx, dy, dz;
                 const float d2 = pair_d2(phx, phy, phz, plx, ply, plz, s_c[jj * nimg + k][0], s_c[jj * nimg + k][1],
                                          dx, dy, dz);
                 if (d2 >= hdr.x) {
-                    nodes_f32<kNodes0>(s_f[jj], dx, dy, dz, lphi, lx, ly, lz);
+                    nodes4_reg(q0, q1, q2, q3, dx, dy, dz, lphi, lx, ly, lz);
                 } else if (d2 >= hdr.y) {
                     if (rect)
                         nodes_f32<kNodesA>(s_a[jj], dx, dy, dz, lphi, lx, ly, lz);
@@ -163,15 +172,52 @@ __device__ __forceinline__ void far_block(const GeomView& g, const double* __res
             }
         }
     }
+    return Sum4{aphi, aEx, aEy, aEz};
+}
+
+__device__ __forceinline__ void load_point_2f(const double* __restrict__ pts, int64_t p, bool active, float& phx,
+                                              float& phy, float& phz, float& plx, float& ply, float& plz) {
+    double Px = 0.0, Py = 0.0, Pz = 0.0;
     if (active) {
-        const double ke = 1.0 / (4.0 * kPi * kEps0);
-        if (phi) phi[p] = ke * aphi;
-        if (E) {
-            E[3 * p] = ke * aEx;
-            E[3 * p + 1] = ke * aEy;
-            E[3 * p + 2] = ke * aEz;
-        }
+        Px = pts[3 * p];
+        Py = pts[3 * p + 1];
+        Pz = pts[3 * p + 2];
     }
+    split2f(Px, phx, plx);
+    split2f(Py, phy, ply);
+    split2f(Pz, phz, plz);
+}
+
+__device__ __forceinline__ void store_far(double* __restrict__ phi, double* __restrict__ E, int64_t p, const Sum4& s) {
+    const double ke = 1.0 / (4.0 * kPi * kEps0);
+    if (phi) phi[p] = ke * s.phi;
+    if (E) {
+        E[3 * p] = ke * s.x;
+        E[3 * p + 1] = ke * s.y;
+        E[3 * p + 2] = ke * s.z;
+    }
+}
+
+// Far part (FP32 tiers) of `count` targets; writes ke * sum (overwrites phi / E).  Thread
+// t takes point idx[base + t] (or base + t when idx is null) of pts / phi / E.  The
+// elements are summed in chunks of kChunkEl whose FP64 sums are added in order, so that
+// a launch split over element chunks (the server's small requests) gives the same bits.
+__device__ __forceinline__ void far_block(const GeomView& g, const double* __restrict__ pts,
+                                          const int32_t* __restrict__ idx, int64_t base, int count,
+                                          double* __restrict__ phi, double* __restrict__ E) {
+    const bool active = (int)threadIdx.x < count;
+    const int64_t p = active ? (idx ? (int64_t)idx[base + threadIdx.x] : base + threadIdx.x) : 0;
+    float phx, phy, phz, plx, ply, plz;
+    load_point_2f(pts, p, active, phx, phy, phz, plx, ply, plz);
+    Sum4 tot{0.0, 0.0, 0.0, 0.0};
+    for (int64_t e0 = 0; e0 < g.n_el; e0 += kChunkEl) {
+        const Sum4 c = far_range(g, phx, phy, phz, plx, ply, plz, e0, min(e0 + (int64_t)kChunkEl, g.n_el));
+        tot.phi += c.phi;
+        tot.x += c.x;
+        tot.y += c.y;
+        tot.z += c.z;
+    }
+    if (active) store_far(phi, E, p, tot);
 }
 
 // Near part (FP64 closed forms) of one target; adds ke * sum to phi[p] / E[p].

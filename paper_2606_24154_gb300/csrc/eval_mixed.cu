@@ -8,7 +8,7 @@ namespace nb {
 
 namespace {
 
-__global__ void __launch_bounds__(kEvalThreads, 8) k_eval_far(const GeomView g, const double* __restrict__ pts,
+__global__ void __launch_bounds__(kEvalThreads, 6) k_eval_far(const GeomView g, const double* __restrict__ pts,
                                                             const int32_t* __restrict__ order, int64_t npts,
                                                             double* __restrict__ phi, double* __restrict__ E) {
     const int64_t base = (int64_t)blockIdx.x * blockDim.x;
@@ -103,7 +103,34 @@ __global__ void k_image_centroids(const Elem* __restrict__ el, int64_t n, const 
     cjk[2 * i + 1] = make_float4(l[0], l[1], l[2], 0.f);
 }
 
+// Distance-tier code of every (point, element, image) pair, as the evaluation decides it:
+// 0 tier 0, 1 tier a, 2 tier b, 3 tier c, 4 FP64 near pair.
+__global__ void k_pair_tiers(const FarNodes* __restrict__ far, const float4* __restrict__ cjk, int64_t n_el, int nimg,
+                             const double* __restrict__ pts, int64_t npts, uint8_t* __restrict__ codes) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= npts * n_el * nimg) return;
+    const int64_t p = t / (n_el * nimg);
+    const int64_t jk = t - p * (n_el * nimg);
+    const int64_t j = jk / nimg;
+    float phx, phy, phz, plx, ply, plz;
+    split2f(pts[3 * p], phx, plx);
+    split2f(pts[3 * p + 1], phy, ply);
+    split2f(pts[3 * p + 2], phz, plz);
+    float dx, dy, dz;
+    const float d2 = pair_d2(phx, phy, phz, plx, ply, plz, cjk[2 * jk], cjk[2 * jk + 1], dx, dy, dz);
+    const float4 h = far[j].hdr;
+    codes[t] = (d2 >= h.x) ? 0 : (d2 >= h.y) ? 1 : (d2 >= h.z) ? 2 : (d2 >= h.w) ? 3 : 4;
+}
+
 }  // namespace
+
+cudaError_t launch_pair_tiers(const FarNodes* far, const float4* cjk, int64_t n_el, int nimg, const double* pts,
+                              int64_t npts, uint8_t* codes, cudaStream_t s) {
+    const int64_t total = npts * n_el * nimg;
+    if (total == 0) return cudaSuccess;
+    k_pair_tiers<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(far, cjk, n_el, nimg, pts, npts, codes);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_image_centroids(const Elem* el, int64_t n, const ImageTable& img, float4* cjk, cudaStream_t s) {
     const int64_t total = n * img.n;
@@ -123,7 +150,10 @@ GeomView make_view(const Elem* el, const FarNodes* far, const float4* cjk, const
     g.cell_items = cell_items;
     g.n_el = n_el;
     g.nimg = img.n;
-    g.tile_el = max(1, min(kTileMax, kCjkMax / img.n));
+    // largest power of two <= min(kTileMax, kCjkMax / images): divides the chunk width
+    int t = 1;
+    while (t * 2 <= kTileMax && t * 2 <= kCjkMax / img.n) t *= 2;
+    g.tile_el = t;
     g.grid = grid;
     return g;
 }

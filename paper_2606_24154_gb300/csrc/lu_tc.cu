@@ -3,14 +3,17 @@
 // follows each panel of the blocked factorisation (Sec. 4.1 / Alg. 1: LU; the trailing
 // update carries almost all of its 2/3 N^3 flops).
 //
-// Each CTA (128 threads) owns a 128 x 128 tile of C.  The A and B tiles are split into
-// TF32 pairs (hi = x rounded to TF32, lo = x - hi) and staged in shared memory in the
+// Each CTA (128 threads) owns a 128 x 64 tile of C (two CTAs fit per SM).  The A and B
+// tiles are split into TF32 pairs (hi = x rounded to TF32, lo = x - hi) and staged in
+// shared memory in the
 // canonical K-major, non-swizzled UMMA layout (8-row x 16-byte core matrices; core
 // matrices adjacent along K are LBO = 128 B apart, 8-row groups SBO = 2048 B apart).
-// One elected thread issues tcgen05.mma kind::tf32 (M = 128, N = 128, K = 8 per
+// One elected thread issues tcgen05.mma kind::tf32 (M = 128, N = 64, K = 8 per
 // instruction) for lo*hi, hi*lo and hi*hi -- 24 instructions accumulating in FP32 in
-// tensor memory (128 lanes x 128 columns) -- then commits to an mbarrier.  The product is
-// read back with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = rows of C) and
+// tensor memory (128 lanes x 64 columns) -- then commits to an mbarrier.  Operand tiles
+// are loaded with 16 float4 loads in flight per thread when the leading dimension and
+// pointers allow it, and the C tile is fetched into registers while the MMAs run.  The
+// product is read back with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = rows of C) and
 // subtracted from C in global memory.  The three-term split keeps the product within a
 // few FP32 units of roundoff, which the FP64 iterative refinement of the solve expects.
 //
@@ -22,12 +25,13 @@ namespace nb {
 
 namespace {
 
-constexpr int kTM = 128, kTN = 128, kTK = 64;
+constexpr int kTM = 128, kTN = 64, kTK = 64;
 constexpr uint32_t kCoreBytes = 128;                 // 8 rows x 16 bytes
 constexpr uint32_t kLBO = kCoreBytes;                // next core matrix along K
 constexpr uint32_t kSBO = (kTK / 4) * kCoreBytes;    // next 8-row group: 2048 B
-constexpr uint32_t kOperandBytes = kTM * kTK * 4;    // 32 KB per operand tile
-constexpr uint32_t kSmemBytes = 4 * kOperandBytes + 64;
+constexpr uint32_t kABytes = kTM * kTK * 4;          // 32 KB per A operand tile
+constexpr uint32_t kBBytes = kTN * kTK * 4;          // 16 KB per B operand tile
+constexpr uint32_t kSmemBytes = 2 * kABytes + 2 * kBBytes + 64;
 constexpr long long kSpinLimit = 1ll << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -61,39 +65,70 @@ __device__ __forceinline__ float tf32_hi(float x) {
     return __uint_as_float(r);
 }
 
-__global__ void __launch_bounds__(128, 1) k_tc_update(int64_t M, int64_t N, const float* __restrict__ A, int64_t lda,
+__device__ __forceinline__ void put_pair(unsigned char* hi, unsigned char* lo, uint32_t o, float x) {
+    const float h = tf32_hi(x);
+    *reinterpret_cast<float*>(hi + o) = h;
+    *reinterpret_cast<float*>(lo + o) = x - h;
+}
+
+__global__ void __launch_bounds__(128, 2) k_tc_update(int64_t M, int64_t N, const float* __restrict__ A, int64_t lda,
                                                        const float* __restrict__ B, int64_t ldb, float* __restrict__ C,
-                                                       int64_t ldc, int* __restrict__ err) {
+                                                       int64_t ldc, int vec, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* a_hi = smem;
-    unsigned char* a_lo = smem + kOperandBytes;
-    unsigned char* b_hi = smem + 2 * kOperandBytes;
-    unsigned char* b_lo = smem + 3 * kOperandBytes;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 4 * kOperandBytes);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 4 * kOperandBytes + 16);
+    unsigned char* a_lo = smem + kABytes;
+    unsigned char* b_hi = smem + 2 * kABytes;
+    unsigned char* b_lo = smem + 2 * kABytes + kBBytes;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * kABytes + 2 * kBBytes);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 2 * kABytes + 2 * kBBytes + 16);
 
     const int64_t m0 = (int64_t)blockIdx.x * kTM, n0 = (int64_t)blockIdx.y * kTN;
     const int tid = threadIdx.x, warp = tid >> 5;
+    const bool full = (m0 + kTM <= M) && (n0 + kTN <= N);
 
-    // ---- stage A (rows m0.., K = 64; column-major source: m fastest) and B (K x N,
-    //      column-major source: k fastest) as TF32 hi/lo pairs
-    for (int idx = tid; idx < kTM * kTK; idx += 128) {
-        const int r = idx % kTM, k = idx / kTM;
-        const int64_t gm = m0 + r;
-        const float x = (gm < M) ? A[gm + (int64_t)k * lda] : 0.f;
-        const float h = tf32_hi(x);
-        const uint32_t o = kmajor_off(r, k);
-        *reinterpret_cast<float*>(a_hi + o) = h;
-        *reinterpret_cast<float*>(a_lo + o) = x - h;
-    }
-    for (int idx = tid; idx < kTN * kTK; idx += 128) {
-        const int k = idx % kTK, c = idx / kTK;
-        const int64_t gn = n0 + c;
-        const float x = (gn < N) ? B[k + gn * ldb] : 0.f;
-        const float h = tf32_hi(x);
-        const uint32_t o = kmajor_off(c, k);
-        *reinterpret_cast<float*>(b_hi + o) = h;
-        *reinterpret_cast<float*>(b_lo + o) = x - h;
+    // ---- stage A (128 rows x 64 k, column-major source) and B (64 k x 64 columns)
+    if (vec && full) {
+        // A: thread t takes rows 4 (t % 32) .. +3 of columns t / 32 + 4 j, j < 16
+        float4 va[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int k = tid / 32 + 4 * j;
+            va[j] = *reinterpret_cast<const float4*>(A + m0 + 4 * (tid % 32) + (int64_t)k * lda);
+        }
+        // B: thread t takes k = 4 (t % 16) .. +3 of columns t / 16 + 8 j, j < 8
+        float4 vb[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int c = tid / 16 + 8 * j;
+            vb[j] = *reinterpret_cast<const float4*>(B + 4 * (tid % 16) + (n0 + c) * ldb);
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int k = tid / 32 + 4 * j, r = 4 * (tid % 32);
+            put_pair(a_hi, a_lo, kmajor_off(r, k), va[j].x);
+            put_pair(a_hi, a_lo, kmajor_off(r + 1, k), va[j].y);
+            put_pair(a_hi, a_lo, kmajor_off(r + 2, k), va[j].z);
+            put_pair(a_hi, a_lo, kmajor_off(r + 3, k), va[j].w);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int c = tid / 16 + 8 * j, k = 4 * (tid % 16);
+            put_pair(b_hi, b_lo, kmajor_off(c, k), vb[j].x);
+            put_pair(b_hi, b_lo, kmajor_off(c, k + 1), vb[j].y);
+            put_pair(b_hi, b_lo, kmajor_off(c, k + 2), vb[j].z);
+            put_pair(b_hi, b_lo, kmajor_off(c, k + 3), vb[j].w);
+        }
+    } else {
+        for (int idx = tid; idx < kTM * kTK; idx += 128) {
+            const int r = idx % kTM, k = idx / kTM;
+            const int64_t gm = m0 + r;
+            put_pair(a_hi, a_lo, kmajor_off(r, k), (gm < M) ? A[gm + (int64_t)k * lda] : 0.f);
+        }
+        for (int idx = tid; idx < kTN * kTK; idx += 128) {
+            const int k = idx % kTK, c = idx / kTK;
+            const int64_t gn = n0 + c;
+            put_pair(b_hi, b_lo, kmajor_off(c, k), (gn < N) ? B[k + gn * ldb] : 0.f);
+        }
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
@@ -113,7 +148,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_update(int64_t M, int64_t N, cons
 
     // ---- issue the 24 MMAs from one thread: lo*hi, hi*lo, hi*hi over 8 K-steps of 8
     if (tid == 0) {
-        const unsigned char* As[3] = {a_lo, a_hi, a_hi};
+        const unsigned char* As[3] = {a_lo, a_hi, a_hi};  // lo*hi, hi*lo, hi*hi
         const unsigned char* Bs[3] = {b_hi, b_lo, b_hi};
         uint32_t first = 1;
         for (int t = 0; t < 3; ++t) {
@@ -133,6 +168,15 @@ __global__ void __launch_bounds__(128, 1) k_tc_update(int64_t M, int64_t N, cons
             smem_u32(mbar)));
     }
 
+    // ---- fetch this thread's row of the C tile while the MMAs run
+    const int64_t row = m0 + warp * 32 + (tid & 31);
+    float cv[kTN];
+#pragma unroll
+    for (int j = 0; j < kTN; ++j) {
+        const int64_t col = n0 + j;
+        cv[j] = (row < M && col < N) ? C[row + col * ldc] : 0.f;
+    }
+
     // ---- bounded wait for the MMAs (phase 0)
     uint32_t done = 0;
     for (long long it = 0; it < kSpinLimit && !done; ++it) {
@@ -147,8 +191,8 @@ __global__ void __launch_bounds__(128, 1) k_tc_update(int64_t M, int64_t N, cons
         if (tid == 0) atomicExch(err, 1);
     } else {
         // ---- epilogue: warp w reads TMEM lanes 32w + (0..31) = rows of the tile, 32 columns
-        //      at a time, and subtracts from C (consecutive rows per column: coalesced)
-        const int64_t row = m0 + warp * 32 + (tid & 31);
+        //      at a time, and stores C - product (consecutive rows per column: coalesced)
+#pragma unroll
         for (int cb = 0; cb < kTN; cb += 32) {
             uint32_t v[32];
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
@@ -166,7 +210,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_update(int64_t M, int64_t N, cons
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int64_t col = n0 + cb + j;
-                    if (col < N) C[row + col * ldc] -= __uint_as_float(v[j]);
+                    if (col < N) C[row + col * ldc] = cv[cb + j] - __uint_as_float(v[j]);
                 }
             }
         }
@@ -187,8 +231,10 @@ cudaError_t tc_update_f32(int64_t M, int64_t N, const float* A, int64_t lda, con
         if (e != cudaSuccess) return e;
         attr = true;
     }
+    // vector loads need 16-byte aligned columns
+    const int vec = (lda % 4 == 0) && (ldb % 4 == 0) && (((uintptr_t)A & 15) == 0) && (((uintptr_t)B & 15) == 0);
     dim3 grid((unsigned)((M + kTM - 1) / kTM), (unsigned)((N + kTN - 1) / kTN));
-    k_tc_update<<<grid, 128, kSmemBytes, s>>>(M, N, A, lda, B, ldb, C, ldc, err);
+    k_tc_update<<<grid, 128, kSmemBytes, s>>>(M, N, A, lda, B, ldb, C, ldc, vec, err);
     return cudaGetLastError();
 }
 

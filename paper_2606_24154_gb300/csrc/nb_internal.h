@@ -93,6 +93,8 @@ cudaError_t launch_eval_mixed(const Elem* el, const FarNodes* far, const float4*
                               int64_t n_el, const ImageTable& img, const NearGrid& grid, const int32_t* cell_start,
                               const int32_t* cell_items, const double* pts, int64_t npts, double* phi, double* E,
                               void* scratch, cudaStream_t s);
+cudaError_t launch_pair_tiers(const FarNodes* far, const float4* cjk, int64_t n_el, int nimg, const double* pts,
+                              int64_t npts, uint8_t* codes, cudaStream_t s);
 // scratch bytes launch_eval_mixed needs for npts points (target binning)
 size_t eval_mixed_scratch_bytes(int64_t npts);
 cudaError_t launch_image_centroids(const Elem* el, int64_t n, const ImageTable& img, float4* cjk, cudaStream_t s);

@@ -3,9 +3,11 @@
 //
 // Requests enter a host FIFO.  A request is admitted when a slot is free, the device
 // point arena has room for its points and the work ring has room for its items: its
-// points are copied into the arena, its remaining-item counter is set, and its items
-// (128 points each) are appended to the ring in host-mapped memory before `tail` is
-// advanced.  A persistent kernel (relaunched whenever admitted work exists and no
+// points are copied into the arena, its remaining point-block counter is set, and its
+// items are appended to the ring in host-mapped memory before `tail` is advanced.  An
+// item is 128 points over all elements; a small mixed request (<= 1024 points) instead
+// gets one item per (point block, chunk of 1024 elements), so that its few points still
+// spread over many CTAs (its latency would otherwise be one CTA's pass over all elements).  A persistent kernel (relaunched whenever admitted work exists and no
 // instance is running) claims items as they appear, so requests admitted while others
 // run join the running launch.  On completion the outputs are copied to the caller's
 // buffers and the arena range, slot and ring items are released.
@@ -34,6 +36,8 @@ namespace {
     } while (0)
 
 constexpr int kItemPoints = 128;
+constexpr int64_t kSmallPoints = 1024;  // mixed requests up to this size are split by element chunks
+constexpr int kPartialBlocks = 512;     // point blocks with chunk partial sums in flight
 
 struct Interval {
     int64_t start, len;
@@ -83,6 +87,7 @@ struct Request {
     double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
     int32_t slot = -1;
     int64_t offset = -1, items = 0, gen = 0;
+    std::vector<int32_t> pblocks;  // partial-sum blocks of a chunked request
     int state = 0;  // 0 queued, 1 admitted, 2 done
 };
 
@@ -95,7 +100,10 @@ struct Server {
     cudaStream_t compute = nullptr, copy = nullptr;
     cudaEvent_t kernel_done = nullptr;
     bool kernel_launched = false;
-    DevBuf d_geoms, d_pts, d_phi, d_E, d_head, d_remaining;
+    DevBuf d_geoms, d_pts, d_phi, d_E, d_head, d_remaining, d_partials, d_pcount;
+    std::vector<int32_t> nchunks;  // element chunks per geometry
+    int32_t max_chunks = 1;
+    std::vector<int32_t> free_pblocks;
     WorkItem* h_ring = nullptr;
     int64_t* h_tail = nullptr;
     int64_t* h_done = nullptr;
@@ -116,7 +124,8 @@ struct Server {
     ~Server() {
         cudaSetDevice(device);
         if (compute) cudaStreamSynchronize(compute);
-        for (DevBuf* b : {&d_geoms, &d_pts, &d_phi, &d_E, &d_head, &d_remaining}) b->release();
+        for (DevBuf* b : {&d_geoms, &d_pts, &d_phi, &d_E, &d_head, &d_remaining, &d_partials, &d_pcount})
+            b->release();
         if (h_ring) cudaFreeHost(h_ring);
         if (h_tail) cudaFreeHost(h_tail);
         if (h_done) cudaFreeHost(h_done);
@@ -142,6 +151,8 @@ struct Server {
                                    cudaMemcpyDeviceToHost, copy));
             CK(cudaStreamSynchronize(copy));
             arena.release(r->offset, r->n);
+            for (int32_t pb : r->pblocks) free_pblocks.push_back(pb);
+            r->pblocks.clear();
             free_slots.push_back(r->slot);
             in_flight_items -= r->items;
             r->state = 2;
@@ -154,7 +165,11 @@ struct Server {
     int admit() {
         while (!queue.empty()) {
             Request* r = queue.front();
-            const int64_t items = (r->n + kItemPoints - 1) / kItemPoints;
+            const int64_t blocks = (r->n + kItemPoints - 1) / kItemPoints;
+            const int32_t nch = nchunks[r->geom];
+            const bool chunked = r->precision == NEBEM_MIXED && r->n <= kSmallPoints && nch > 1 &&
+                                 (int64_t)free_pblocks.size() >= blocks;
+            const int64_t items = chunked ? blocks * nch : blocks;
             if (free_slots.empty() || in_flight_items + items > ring_cap) break;
             const int64_t off = arena.alloc(r->n);
             if (off < 0) break;
@@ -165,20 +180,31 @@ struct Server {
             r->offset = off;
             r->items = items;
             r->gen = ++slot_gen[slot];
-            const int cnt = (int)items;
+            if (chunked)
+                for (int64_t b = 0; b < blocks; ++b) {
+                    r->pblocks.push_back(free_pblocks.back());
+                    free_pblocks.pop_back();
+                }
+            const int cnt = (int)blocks;  // the kernel counts finished point blocks
             CK(cudaMemcpyAsync(d_pts.as<double>() + 3 * off, r->pts, sizeof(double) * 3 * r->n,
                                cudaMemcpyHostToDevice, copy));
             CK(cudaMemcpyAsync(d_remaining.as<int>() + slot, &cnt, sizeof(int), cudaMemcpyHostToDevice, copy));
             CK(cudaStreamSynchronize(copy));
-            for (int64_t k = 0; k < items; ++k) {
-                WorkItem& w = h_ring[(published + k) % ring_cap];
-                w.slot = slot;
-                w.geom = r->geom;
-                w.precision = r->precision;
-                w.count = (int32_t)std::min<int64_t>(kItemPoints, r->n - k * kItemPoints);
-                w.offset = off + k * kItemPoints;
-                w.gen = r->gen;
-            }
+            int64_t k = 0;
+            for (int64_t b = 0; b < blocks; ++b)
+                for (int32_t c = 0; c < (chunked ? nch : 1); ++c, ++k) {
+                    WorkItem& w = h_ring[(published + k) % ring_cap];
+                    w.slot = slot;
+                    w.geom = r->geom;
+                    w.precision = r->precision;
+                    w.count = (int32_t)std::min<int64_t>(kItemPoints, r->n - b * kItemPoints);
+                    w.offset = off + b * kItemPoints;
+                    w.gen = r->gen;
+                    w.chunk = chunked ? c : -1;
+                    w.nchunks = nch;
+                    w.pblock = chunked ? r->pblocks[b] : -1;
+                    w.pad = 0;
+                }
             published += items;
             __atomic_store_n(h_tail, published, __ATOMIC_RELEASE);
             in_flight_items += items;
@@ -198,7 +224,8 @@ struct Server {
         }
         CK(launch_serve(d_geoms.as<ServeGeom>(), h_ring, ring_cap, h_tail, d_head.as<unsigned long long>(),
                         d_pts.as<double>(), d_phi.as<double>(), d_E.as<double>(), d_remaining.as<int>(), h_done,
-                        (uint64_t)opt.idle_us * 1000ull, opt.workers, compute));
+                        d_partials.as<double>(), d_pcount.as<int>(), max_chunks, (uint64_t)opt.idle_us * 1000ull,
+                        opt.workers, compute));
         CK(cudaEventRecord(kernel_done, compute));
         kernel_launched = true;
         return 0;
@@ -271,13 +298,22 @@ int nebem_server_create(nebem_server** out, nebem_ctx* const* ctxs, int32_t n_ct
         geoms.push_back(make_serve_geom(c->d_el.as<Elem>(), c->d_far.as<FarNodes>(), c->d_cjk.as<float4>(),
                                         c->d_sigma.as<double>(), c->n, c->img, c->grid,
                                         c->d_cell_start.as<int32_t>(), c->d_cell_items.as<int32_t>()));
-    s->ring_cap = std::max<int64_t>(4096, 2 * (cap + kItemPoints - 1) / kItemPoints);
+    for (Ctx* c : cs) {
+        const int32_t nc = (int32_t)((c->n + kChunkElements - 1) / kChunkElements);
+        s->nchunks.push_back(nc);
+        s->max_chunks = std::max(s->max_chunks, nc);
+    }
+    s->ring_cap = std::max<int64_t>(4096 + (int64_t)kPartialBlocks * s->max_chunks,
+                                    2 * (cap + kItemPoints - 1) / kItemPoints);
     if ((e = s->d_geoms.ensure(sizeof(ServeGeom) * geoms.size())) != cudaSuccess ||
         (e = s->d_pts.ensure(sizeof(double) * 3 * cap)) != cudaSuccess ||
         (e = s->d_phi.ensure(sizeof(double) * cap)) != cudaSuccess ||
         (e = s->d_E.ensure(sizeof(double) * 3 * cap)) != cudaSuccess ||
         (e = s->d_head.ensure(sizeof(unsigned long long))) != cudaSuccess ||
-        (e = s->d_remaining.ensure(sizeof(int) * o.max_requests)) != cudaSuccess)
+        (e = s->d_remaining.ensure(sizeof(int) * o.max_requests)) != cudaSuccess ||
+        (e = s->d_partials.ensure(sizeof(double) * 4 * kItemPoints * (size_t)kPartialBlocks * s->max_chunks)) !=
+            cudaSuccess ||
+        (e = s->d_pcount.ensure(sizeof(int) * kPartialBlocks)) != cudaSuccess)
         return bail(cuda_fail(e, "server device buffers"));
     if ((e = cudaHostAlloc(&s->h_ring, sizeof(WorkItem) * s->ring_cap, cudaHostAllocMapped)) != cudaSuccess ||
         (e = cudaHostAlloc(&s->h_tail, 64, cudaHostAllocMapped)) != cudaSuccess ||
@@ -288,8 +324,10 @@ int nebem_server_create(nebem_server** out, nebem_ctx* const* ctxs, int32_t n_ct
     std::memset(s->h_done, 0, sizeof(int64_t) * o.max_requests);
     if ((e = cudaMemcpy(s->d_geoms.ptr, geoms.data(), sizeof(ServeGeom) * geoms.size(), cudaMemcpyHostToDevice)) !=
             cudaSuccess ||
-        (e = cudaMemset(s->d_head.ptr, 0, sizeof(unsigned long long))) != cudaSuccess)
+        (e = cudaMemset(s->d_head.ptr, 0, sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMemset(s->d_pcount.ptr, 0, sizeof(int) * kPartialBlocks)) != cudaSuccess)
         return bail(cuda_fail(e, "server setup copies"));
+    for (int32_t i = kPartialBlocks - 1; i >= 0; --i) s->free_pblocks.push_back(i);
     s->arena.reset(cap);
     s->slot_gen.assign((size_t)o.max_requests, 0);
     for (int32_t i = o.max_requests - 1; i >= 0; --i) s->free_slots.push_back(i);

@@ -26,13 +26,17 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
+static_assert(kChunkElements == kChunkEl, "server chunk width must match the evaluation bodies");
+
 __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restrict__ geoms, const WorkItem* ring,
                                                         int64_t ring_cap, int64_t* tail_mapped,
                                                         unsigned long long* head, const double* __restrict__ arena_pts,
                                                         double* __restrict__ arena_phi, double* __restrict__ arena_E,
-                                                        int* remaining, int64_t* done_mapped, uint64_t idle_ns) {
+                                                        int* remaining, int64_t* done_mapped, double* partials,
+                                                        int* pblock_count, int max_chunks, uint64_t idle_ns) {
     __shared__ WorkItem it;
     __shared__ int have;
+    __shared__ int last;
     for (;;) {
         if (threadIdx.x == 0) {
             have = 0;
@@ -56,17 +60,55 @@ __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restr
         __syncthreads();
         if (!have) return;
         const ServeGeom& G = geoms[it.geom];
-        const double* pts = arena_pts + 3 * it.offset;
-        double* phi = arena_phi + it.offset;
-        double* E = arena_E + 3 * it.offset;
-        if (it.precision == NEBEM_MIXED) {
+        bool block_done = true;
+        if (it.precision != NEBEM_MIXED) {
+            f64_block(G.view.el, G.view.sigma, G.view.n_el, G.img, arena_pts + 3 * it.offset, it.count,
+                      arena_phi + it.offset, arena_E + 3 * it.offset);
+        } else if (it.chunk < 0) {
             far_block(G.view, arena_pts, nullptr, it.offset, it.count, arena_phi, arena_E);
-            if ((int)threadIdx.x < it.count) near_point(G.view, G.img, arena_pts, it.offset + threadIdx.x, arena_phi, arena_E);
+            if ((int)threadIdx.x < it.count)
+                near_point(G.view, G.img, arena_pts, it.offset + threadIdx.x, arena_phi, arena_E);
         } else {
-            f64_block(G.view.el, G.view.sigma, G.view.n_el, G.img, pts, it.count, phi, E);
+            // one element chunk of a point block: raw sums to the partial area; the CTA that
+            // finishes the block's last chunk adds the chunks in order (as far_block does),
+            // stores ke * sum and adds the near pairs
+            const bool active = (int)threadIdx.x < it.count;
+            const int64_t p = it.offset + threadIdx.x;
+            float phx, phy, phz, plx, ply, plz;
+            load_point_2f(arena_pts, p, active, phx, phy, phz, plx, ply, plz);
+            const int64_t e0 = (int64_t)it.chunk * kChunkEl;
+            const Sum4 c = far_range(G.view, phx, phy, phz, plx, ply, plz, e0,
+                                     min(e0 + (int64_t)kChunkEl, G.view.n_el));
+            double* part = partials + ((int64_t)it.pblock * max_chunks + it.chunk) * (4 * kEvalThreads);
+            part[4 * threadIdx.x] = c.phi;
+            part[4 * threadIdx.x + 1] = c.x;
+            part[4 * threadIdx.x + 2] = c.y;
+            part[4 * threadIdx.x + 3] = c.z;
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) last = (atomicAdd(&pblock_count[it.pblock], 1) == it.nchunks - 1);
+            __syncthreads();
+            block_done = last;
+            if (last) {
+                __threadfence();
+                Sum4 tot{0.0, 0.0, 0.0, 0.0};
+                for (int k = 0; k < it.nchunks; ++k) {
+                    const double* q = partials + ((int64_t)it.pblock * max_chunks + k) * (4 * kEvalThreads) +
+                                      4 * threadIdx.x;
+                    tot.phi += __ldcg(q);
+                    tot.x += __ldcg(q + 1);
+                    tot.y += __ldcg(q + 2);
+                    tot.z += __ldcg(q + 3);
+                }
+                if (active) {
+                    store_far(arena_phi, arena_E, p, tot);
+                    near_point(G.view, G.img, arena_pts, p, arena_phi, arena_E);
+                }
+                if (threadIdx.x == 0) pblock_count[it.pblock] = 0;
+            }
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && block_done) {
             __threadfence();
             if (atomicSub(&remaining[it.slot], 1) == 1) {
                 __threadfence_system();
@@ -82,9 +124,10 @@ __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restr
 
 cudaError_t launch_serve(const ServeGeom* geoms, const WorkItem* ring, int64_t ring_cap, int64_t* tail_mapped,
                          unsigned long long* head, const double* arena_pts, double* arena_phi, double* arena_E,
-                         int* remaining, int64_t* done_mapped, uint64_t idle_ns, int workers, cudaStream_t s) {
+                         int* remaining, int64_t* done_mapped, double* partials, int* pblock_count, int max_chunks,
+                         uint64_t idle_ns, int workers, cudaStream_t s) {
     k_serve<<<workers, kEvalThreads, 0, s>>>(geoms, ring, ring_cap, tail_mapped, head, arena_pts, arena_phi, arena_E,
-                                             remaining, done_mapped, idle_ns);
+                                             remaining, done_mapped, partials, pblock_count, max_chunks, idle_ns);
     return cudaGetLastError();
 }
 

@@ -102,6 +102,7 @@ SIGNATURES = {
     "nebem_lu_solve_device": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp]),
     "nebem_lu_factor_device_noalloc": (C.c_int, [_vp, C.c_int64, _vp, _vp]),
     "nebem_image_table": (C.c_int, [_vp, _d, _i64p]),
+    "nebem_pair_tiers": (C.c_int, [_vp, _d, C.c_int64, C.POINTER(C.c_uint8)]),
     "nebem_element_influence": (C.c_int, [_vp, _vp, C.c_int64, _d, C.c_int64, _d, _d]),
     "nebem_server_default_options": (C.c_int, [C.POINTER(nebem_server_options)]),
     "nebem_server_create": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int32, C.POINTER(nebem_server_options)]),
@@ -281,6 +282,14 @@ def nebem_image_table(ctx):
     t = np.empty((cnt.value, 3))
     _check(load().nebem_image_table(ctx, _dp(t), C.byref(cnt)), "nebem_image_table")
     return t
+
+
+def nebem_pair_tiers(ctx, pts, n_el: int, n_img: int):
+    p = _f64(pts, (-1, 3))
+    codes = np.empty(p.shape[0] * n_el * n_img, dtype=np.uint8)
+    _check(load().nebem_pair_tiers(ctx, _dp(p), p.shape[0], codes.ctypes.data_as(C.POINTER(C.c_uint8))),
+           "nebem_pair_tiers")
+    return codes.reshape(p.shape[0], n_el, n_img)
 
 
 def nebem_element_influence(ctx, elements, pts):

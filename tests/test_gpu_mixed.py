@@ -111,3 +111,18 @@ def test_mixed_ragged_and_empty(N):
         if n:
             rphi, rE = O.eval_points(g, sig_r, pts)
             assert rel_norm(phi, rphi) <= TOL_MIXED and rel_vec(E, rE) <= TOL_MIXED
+
+
+def test_pair_tiers_bit_exact_with_oracle(N):
+    """The mixed evaluation's per-pair tier decision (FP32 on two-float coordinates)
+    equals the oracle's written-out classification for every (point, element, image)."""
+    g = I.thgem(I.PlateSpec(n_phi=24, n_r=3, n_zc=1, n_zf=4), n_plane=3)
+    pts = I.cell_points(g, 120, I.rng(1, 31))
+    near = pts[:40].copy()
+    near[:, 2] = 0.285e-3 + 1e-7 * np.arange(40)  # just above the top Cu face
+    pts = np.concatenate([pts, near, [[0.0, 0.0, 0.0], [0.25e-3, 0.0, 0.1e-3]]])
+    ctx = N.Context().set_geometry(g)
+    got = N.nebem_pair_tiers(ctx.h, pts, g.n, g.n_images)
+    ref = O.pair_tiers(g, pts)
+    assert np.array_equal(got, ref)
+    assert set(np.unique(ref)) == {0, 1, 2, 3, 4}

@@ -297,3 +297,25 @@ def test_dense_lu_device_matches_oracle(N):
         torch.cuda.synchronize()
         x_ref = O.lu_solve((A_ref, piv_ref), b)
         assert np.abs(db.cpu().numpy() - x_ref).max() <= TOL64 * np.abs(x_ref).max()
+
+
+def test_weighting_fields_reuse_the_factors(N):
+    """K does not depend on the voltages, so the factors are reused (Sec. 2.1): the
+    solution for any voltage set equals the sum of per-conductor unit ("weighting
+    field") solutions, and each unit solution matches the oracle."""
+    g = small_thgem()
+    ctx = N.Context().set_geometry(g)
+    K = O.fill(g)
+    fac = O.lu_factor(K)
+    units = []
+    for c in range(len(g.voltages)):
+        v = np.zeros(len(g.voltages)); v[c] = 1.0
+        N.nebem_set_bc(ctx.h, v)
+        sig, info, _ = ctx.solve(N.NEBEM_FP64)
+        ref = O.lu_solve(fac, O.rhs(g, v))
+        assert rel_norm(sig, ref) <= TOL64
+        units.append(sig)
+    N.nebem_set_bc(ctx.h, g.voltages)
+    sig_all, _, _ = ctx.solve(N.NEBEM_FP64)
+    combo = sum(V * u for V, u in zip(g.voltages, units))
+    assert rel_norm(combo, sig_all) <= 1e-12

@@ -120,3 +120,24 @@ def test_server_argument_errors(N, ctxs):
         assert e.value.code == N.NEBEM_INVALID_ARG
     finally:
         N.nebem_server_destroy(srv)
+
+
+def test_server_small_requests_split_by_element_chunks(N):
+    """Small mixed requests on the full THGEM cell (10 element chunks) run as one item per
+    (point block, chunk); their results equal the standalone evaluation bit for bit."""
+    g = I.thgem()
+    c = N.Context().set_geometry(g)
+    c.solve(N.NEBEM_MIXED)
+    srv = N.nebem_server_create([c.h])
+    try:
+        reqs = []
+        for k, n in enumerate([1, 50, 129, 300, 1024, 1025]):
+            pts = _request_points(g, n, 500 + k)
+            phi, E = np.empty(n), np.empty((n, 3))
+            reqs.append((N.nebem_server_submit(srv, 0, pts, phi, E, N.NEBEM_MIXED), pts, phi, E))
+        for rid, pts, phi, E in reqs:
+            N.nebem_server_wait(srv, rid, 120000)
+            rphi, rE = c.eval(pts, N.NEBEM_MIXED)
+            assert np.array_equal(phi, rphi) and np.array_equal(E, rE)
+    finally:
+        N.nebem_server_destroy(srv)
