@@ -265,6 +265,29 @@ int nebem_lu_solve_device(nebem_ctx *ctx, const double *d_LU, int64_t n, const i
  * Errors: NEBEM_INVALID_ARG, NEBEM_TOO_LARGE, NEBEM_SINGULAR, NEBEM_CUDA. */
 int nebem_lu_factor_device_noalloc(double *d_A, int64_t n, int32_t *d_piv, void *stream);
 
+/* FastVolume map (Sec. 3.3; CreateFastVolPF of Sec. 4.1): evaluate potential and field
+ * once at the nodes of a rectilinear grid -- node coordinates per axis, strictly
+ * increasing, at least 2 per axis, so nodes can be packed where the field varies fast --
+ * with the evaluation kernels of nebem_eval (elements with images, plus known charges),
+ * and keep the node values on the device.  One map per context; a new build replaces it.
+ * The map belongs to the current charge densities: after any change of them (solve,
+ * set_sigma, set_geometry, space_charge, step) lookups fail with NEBEM_BAD_STATE until it
+ * is rebuilt.  Axis arrays are host memory, copied.  At most 1e8 nodes.
+ * For a weighting-field map, set unit voltages on the readout (nebem_set_bc), solve with
+ * the retained factors and build.  Errors: NEBEM_BAD_STATE (no charge densities),
+ * NEBEM_INVALID_ARG, NEBEM_TOO_LARGE, NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
+int nebem_fastvol_build(nebem_ctx *ctx, const double *x_nodes, int32_t nx, const double *y_nodes, int32_t ny,
+                        const double *z_nodes, int32_t nz, int32_t precision);
+
+/* Trilinear interpolation of the map at points (host buffers as in nebem_eval): the
+ * eight nodes of the cell that holds the point, weights from its fractional position;
+ * points outside the grid box take the value at the nearest point of the box. */
+int nebem_fastvol_eval(nebem_ctx *ctx, const double *pts, int64_t n, double *phi, double *E);
+
+/* Device variant of nebem_fastvol_eval (asynchronous on `stream`, NULL = context stream). */
+int nebem_fastvol_eval_device(nebem_ctx *ctx, const double *d_pts, int64_t n, double *d_phi, double *d_E,
+                              void *stream);
+
 /* Image translations of the current geometry in index order (count * 3 doubles,
  * host).  *count receives the number of images; t_out may be NULL to query it. */
 int nebem_image_table(nebem_ctx *ctx, double *t_out, int64_t *count);

@@ -622,3 +622,205 @@ int or_dynamic_step(const or_input *in, int64_t n, const double *voltages, int32
     free(Es);
     return rc;
 }
+
+/* ---------------------------------------------------------------------------------
+ * Line-charge representation of the known charges (Sec. 4.2, Alg. 3; the LineCh
+ * branch of Alg. 4).
+ *
+ * Alg. 3, kernel 1: every point charge p falls in voxel v = f(p; dx, dy, dz) and adds its
+ * charge to that voxel's total; a voxel that receives a point is occupied.  Kernel 2:
+ * every occupied voxel yields one line charge (start, stop, lambda).
+ * Readings fixed here where the paper is silent:
+ *   - the grid is anchored at the minimum corner (xmin, ymin, zmin) of the cloud:
+ *     i = floor((x - xmin) / dx), likewise j, k; nx = floor((xmax - xmin) / dx) + 1;
+ *     flat voxel index v = (k * ny + j) * nx + i;
+ *   - the line runs along z (the drift direction) through the voxel's centre, from its
+ *     lower to its upper z face: start = (xmin + (i + 1/2) dx, ymin + (j + 1/2) dy,
+ *     zmin + k dz), stop = start + (0, 0, dz), lambda = total charge / dz (C/m);
+ *   - lines are listed in increasing voxel index, and a voxel's total is summed over
+ *     its points in increasing point index.
+ * ------------------------------------------------------------------------------- */
+
+typedef struct {
+    int64_t v;
+    int64_t i;
+} or_vox_pair;
+
+static int vox_pair_cmp(const void *a, const void *b) {
+    const or_vox_pair *x = (const or_vox_pair *)a, *y = (const or_vox_pair *)b;
+    if (x->v != y->v) return (x->v < y->v) ? -1 : 1;
+    return (x->i < y->i) ? -1 : (x->i > y->i);
+}
+
+/* Grid of Alg. 3 for a cloud: lo[3] (minimum corner) and dims[3]; 0, or -1 for bad input
+ * or a grid of 4e18 voxels or more. */
+int or_voxel_grid(const double *pos, int64_t n, const double d[3], double lo[3], int64_t dims[3]) {
+    if (n <= 0) return -1;
+    for (int a = 0; a < 3; ++a) {
+        if (!(d[a] > 0.0)) return -1;
+        double mn = pos[a], mx = pos[a];
+        for (int64_t p = 1; p < n; ++p) {
+            if (pos[3 * p + a] < mn) mn = pos[3 * p + a];
+            if (pos[3 * p + a] > mx) mx = pos[3 * p + a];
+        }
+        lo[a] = mn;
+        double na = floor((mx - mn) / d[a]) + 1.0;
+        if (!(na < 4.0e18)) return -1;
+        dims[a] = (int64_t)na;
+    }
+    /* the flat voxel index must fit in 62 bits */
+    if ((double)dims[0] * (double)dims[1] * (double)dims[2] >= 4.0e18) return -1;
+    return 0;
+}
+
+/* Alg. 3.  Returns the number of lines L (all written: start, stop L x 3; lambda L;
+ * voxel L, the flat voxel index of each line; each may be NULL), or -1 on bad input.
+ * The caller sizes the outputs for n lines (the most there can be). */
+int64_t or_voxel_lines(const double *pos, const double *q, int64_t n, const double d[3], double *start,
+                       double *stop, double *lambda, int64_t *voxel) {
+    double lo[3];
+    int64_t dims[3];
+    if (or_voxel_grid(pos, n, d, lo, dims)) return -1;
+    /* kernel 1: the voxel of every point */
+    or_vox_pair *pv = (or_vox_pair *)malloc(sizeof(or_vox_pair) * (size_t)n);
+    for (int64_t p = 0; p < n; ++p) {
+        int64_t ijk[3];
+        for (int a = 0; a < 3; ++a) {
+            int64_t c = (int64_t)floor((pos[3 * p + a] - lo[a]) / d[a]);
+            ijk[a] = c < dims[a] - 1 ? c : dims[a] - 1;
+        }
+        pv[p].v = (ijk[2] * dims[1] + ijk[1]) * dims[0] + ijk[0];
+        pv[p].i = p;
+    }
+    /* kernel 2: occupied voxels in increasing index, each summing its points in order */
+    qsort(pv, (size_t)n, sizeof(or_vox_pair), vox_pair_cmp);
+    int64_t L = 0;
+    for (int64_t s = 0; s < n;) {
+        int64_t v = pv[s].v, e = s;
+        double Q = 0.0;
+        while (e < n && pv[e].v == v) Q += q[pv[e++].i];
+        int64_t i = v % dims[0], j = (v / dims[0]) % dims[1], k = v / (dims[0] * dims[1]);
+        double a[3] = {lo[0] + ((double)i + 0.5) * d[0], lo[1] + ((double)j + 0.5) * d[1], lo[2] + (double)k * d[2]};
+        if (start) memcpy(start + 3 * L, a, sizeof a);
+        if (stop) {
+            stop[3 * L] = a[0];
+            stop[3 * L + 1] = a[1];
+            stop[3 * L + 2] = a[2] + d[2];
+        }
+        if (lambda) lambda[L] = Q / d[2];
+        if (voxel) voxel[L] = v;
+        ++L;
+        s = e;
+    }
+    free(pv);
+    return L;
+}
+
+/* Potential and field of finite uniform line charges (LineCh), softened like the point
+ * charges: for a line from A to B (unit u, length L) and target P, with w = P - A,
+ * a = w.u, perpendicular part p = w - a u, rho^2 = |p|^2 + s^2, s1 = -a, s2 = L - a,
+ *   phi = ke lambda int_0^L dt / sqrt((a - t)^2 + rho^2)
+ *       = ke lambda (asinh(s2 / rho) - asinh(s1 / rho)),
+ *   (on the axis with s = 0: ke lambda ln(s2 / s1) before the start, ln(s1 / s2) past the end),
+ *   E = -grad phi = ke lambda [ (1/R2 - 1/R1) u + (s2/R2 - s1/R1) p / rho^2 ],
+ *   R1,2 = sqrt(s1,2^2 + rho^2).
+ * accumulate != 0 adds to phi_out / E_out. */
+void or_line_charge(const double *start, const double *stop, const double *lambda, int64_t nl, const double *tgt,
+                    int64_t nt, double soft, int accumulate, double *phi_out, double *E_out) {
+    double ke = or_ke(), s2s = soft * soft;
+#pragma omp parallel for schedule(static)
+    for (int64_t t = 0; t < nt; ++t) {
+        double ph = 0.0, E[3] = {0.0, 0.0, 0.0};
+        for (int64_t l = 0; l < nl; ++l) {
+            double u[3], w[3], p[3];
+            for (int a = 0; a < 3; ++a) u[a] = stop[3 * l + a] - start[3 * l + a];
+            double len = norm3(u);
+            for (int a = 0; a < 3; ++a) {
+                u[a] /= len;
+                w[a] = tgt[3 * t + a] - start[3 * l + a];
+            }
+            double ax = dot3(w, u);
+            for (int a = 0; a < 3; ++a) p[a] = w[a] - ax * u[a];
+            double rho2 = dot3(p, p) + s2s, rho = sqrt(rho2);
+            double s1 = -ax, s2 = len - ax;
+            double R1 = sqrt(s1 * s1 + rho2), R2 = sqrt(s2 * s2 + rho2);
+            /* asinh(s/rho) = ln(s + R) - ln(rho): for a target on either side of the
+             * segment's span the difference is a log ratio (also at rho = 0, on the axis);
+             * beside the span rho > 0 and the asinh difference is used directly */
+            double I;
+            if (s1 >= 0.0)
+                I = log((s2 + R2) / (s1 + R1));
+            else if (s2 <= 0.0)
+                I = log((R1 - s1) / (R2 - s2));
+            else
+                I = asinh(s2 / rho) - asinh(s1 / rho);
+            ph += lambda[l] * I;
+            double cu = lambda[l] * (1.0 / R2 - 1.0 / R1);
+            double cp = (rho2 > 0.0) ? lambda[l] * (s2 / R2 - s1 / R1) / rho2 : 0.0;
+            for (int a = 0; a < 3; ++a) E[a] += cu * u[a] + cp * p[a];
+        }
+        if (phi_out) phi_out[t] = (accumulate ? phi_out[t] : 0.0) + ke * ph;
+        if (E_out)
+            for (int a = 0; a < 3; ++a) E_out[3 * t + a] = (accumulate ? E_out[3 * t + a] : 0.0) + ke * E[a];
+    }
+}
+
+/* Right-hand side with line charges as the known charges: conductor rows
+ * V - phi_lines(c_i), dielectric rows -n_i . E_lines(c_i). */
+int or_rhs_lines(const or_input *in, int64_t n, const double *voltages, int32_t ncond, const double *start,
+                 const double *stop, const double *lambda, int64_t nl, double soft, double *b) {
+    int rc = or_rhs(in, n, voltages, ncond, b);
+    if (rc || nl == 0) return rc;
+    double *c = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    double *nr = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    double *ph = (double *)malloc(sizeof(double) * (size_t)n);
+    double *E = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+    rc = or_centroids(in, n, c, nr, NULL);
+    if (rc == 0) {
+        or_line_charge(start, stop, lambda, nl, c, n, soft, 0, ph, E);
+        for (int64_t i = 0; i < n; ++i) b[i] -= (in[i].bc == 0) ? ph[i] : dot3(nr + 3 * i, E + 3 * i);
+    }
+    free(c);
+    free(nr);
+    free(ph);
+    free(E);
+    return rc;
+}
+
+/* One dynamic step with the line representation (Alg. 4, Type == Line, SpChTh = 0):
+ * (1) Alg. 3 on the carriers, (2) RHS with the lines, (3) sigma from the retained
+ * factors, (4) E at every carrier from the elements (with images) and all lines,
+ * (5) x += sign(q) mu E dt.  E_out (ncar x 3) may be NULL. */
+int or_dynamic_step_lines(const or_input *in, int64_t n, const double *voltages, int32_t ncond,
+                          const double *lattice, int lo, int hi, const double *LU, const int32_t *piv, double *pos,
+                          const double *q, int64_t ncar, const double d[3], double soft, double mu, double dt,
+                          double *sigma_out, double *E_out) {
+    double *st = (double *)malloc(sizeof(double) * 3 * (size_t)ncar);
+    double *sp = (double *)malloc(sizeof(double) * 3 * (size_t)ncar);
+    double *lam = (double *)malloc(sizeof(double) * (size_t)ncar);
+    double *b = (double *)malloc(sizeof(double) * (size_t)(n ? n : 1));
+    double *Ee = (double *)malloc(sizeof(double) * 3 * (size_t)ncar);
+    int64_t nl = or_voxel_lines(pos, q, ncar, d, st, sp, lam, NULL);
+    int rc = nl < 0 ? -1 : or_rhs_lines(in, n, voltages, ncond, st, sp, lam, nl, soft, b);
+    if (rc == 0) {
+        or_lu_solve(n, LU, piv, b);
+        rc = or_eval(in, n, b, lattice, lo, hi, pos, ncar, NULL, Ee);
+    }
+    if (rc == 0) {
+        or_line_charge(st, sp, lam, nl, pos, ncar, soft, 1, NULL, Ee);
+        for (int64_t c = 0; c < ncar; ++c) {
+            double sg = (q[c] > 0.0) ? 1.0 : ((q[c] < 0.0) ? -1.0 : 0.0);
+            for (int k = 0; k < 3; ++k) {
+                if (E_out) E_out[3 * c + k] = Ee[3 * c + k];
+                pos[3 * c + k] += sg * mu * Ee[3 * c + k] * dt;
+            }
+        }
+        if (sigma_out) memcpy(sigma_out, b, sizeof(double) * (size_t)n);
+    }
+    free(st);
+    free(sp);
+    free(lam);
+    free(b);
+    free(Ee);
+    return rc;
+}

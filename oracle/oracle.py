@@ -62,6 +62,14 @@ def lib():
         L.or_rhs_space_charge.argtypes = [_vp, C.c_int64, _d, C.c_int32, _d, _d, C.c_int64, C.c_double, _d]
         L.or_dynamic_step.argtypes = [_vp, C.c_int64, _d, C.c_int32, _d, C.c_int, C.c_int, _d, _i32, _d, _d,
                                       C.c_int64, C.c_double, C.c_double, C.c_double, _d, _d]
+        _i64 = C.POINTER(C.c_int64)
+        L.or_voxel_grid.argtypes = [_d, C.c_int64, _d, _d, _i64]
+        L.or_voxel_lines.argtypes = [_d, _d, C.c_int64, _d, _d, _d, _d, _i64]
+        L.or_voxel_lines.restype = C.c_int64
+        L.or_line_charge.argtypes = [_d, _d, _d, C.c_int64, _d, C.c_int64, C.c_double, C.c_int, _d, _d]
+        L.or_rhs_lines.argtypes = [_vp, C.c_int64, _d, C.c_int32, _d, _d, _d, C.c_int64, C.c_double, _d]
+        L.or_dynamic_step_lines.argtypes = [_vp, C.c_int64, _d, C.c_int32, _d, C.c_int, C.c_int, _d, _i32, _d,
+                                            _d, C.c_int64, _d, C.c_double, C.c_double, C.c_double, _d, _d]
         _lib = L
     return _lib
 
@@ -246,4 +254,114 @@ def dynamic_step(g, fac, pos, q, soft=1e-6, mu=1e-4, dt=1e-9):
     lat = _lat(g)
     _check(lib().or_dynamic_step(pe, n, _p(v), v.shape[0], _p(lat), g.img_lo, g.img_hi, _p(A), _pi(piv),
                                  _p(pos), _p(q), pos.shape[0], soft, mu, dt, _p(sigma), _p(E)), "dynamic_step")
+    return pos, sigma, E
+
+
+def fastvol(g, sigma, x_nodes, y_nodes, z_nodes, pts):
+    """FastVolume map (Sec. 3.3): potential and field at the grid nodes (oracle
+    evaluation), then trilinear interpolation of the eight nodes of each point's cell;
+    coordinates outside the box are clamped to it."""
+    ax, ay, az = (np.asarray(a, dtype=np.float64) for a in (x_nodes, y_nodes, z_nodes))
+    X, Y, Z = np.meshgrid(ax, ay, az, indexing="ij")
+    nodes = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    vphi, vE = eval_points(g, sigma, nodes)
+    vphi = vphi.reshape(len(ax), len(ay), len(az))
+    vE = vE.reshape(len(ax), len(ay), len(az), 3)
+    pts = np.asarray(pts, dtype=np.float64)
+    phi = np.empty(pts.shape[0])
+    E = np.empty((pts.shape[0], 3))
+    for p, (x, y, z) in enumerate(pts):
+        idx, frac = [], []
+        for a, v in zip((ax, ay, az), (x, y, z)):
+            v = min(max(v, a[0]), a[-1])
+            c = min(max(int(np.searchsorted(a, v, side="right")) - 1, 0), len(a) - 2)
+            idx.append(c)
+            frac.append((v - a[c]) / (a[c + 1] - a[c]))
+        sp, sE = 0.0, np.zeros(3)
+        for di in (0, 1):
+            for dj in (0, 1):
+                for dk in (0, 1):
+                    w = ((frac[0] if di else 1 - frac[0]) * (frac[1] if dj else 1 - frac[1])
+                         * (frac[2] if dk else 1 - frac[2]))
+                    sp += w * vphi[idx[0] + di, idx[1] + dj, idx[2] + dk]
+                    sE += w * vE[idx[0] + di, idx[1] + dj, idx[2] + dk]
+        phi[p] = sp
+        E[p] = sE
+    return phi, E
+
+
+def voxel_grid(pos, d):
+    """Alg. 3 grid of a cloud: (minimum corner, dims)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    lo = np.empty(3)
+    dims = np.empty(3, dtype=np.int64)
+    _check(lib().or_voxel_grid(_p(pos), pos.shape[0], _p(d), _p(lo), dims.ctypes.data_as(C.POINTER(C.c_int64))),
+           "voxel_grid")
+    return lo, dims
+
+
+class Lines:
+    """Line charges: start, stop (L x 3, m), lam (L, C/m), voxel (L, flat voxel index)."""
+
+    def __init__(self, start, stop, lam, voxel=None):
+        self.start = np.ascontiguousarray(start, dtype=np.float64)
+        self.stop = np.ascontiguousarray(stop, dtype=np.float64)
+        self.lam = np.ascontiguousarray(lam, dtype=np.float64)
+        self.voxel = voxel
+
+    def __len__(self):
+        return self.lam.shape[0]
+
+
+def voxel_lines(pos, q, d):
+    """Point -> line charge reduction (Sec. 4.2, Alg. 3) with the readings stated in
+    nebem_oracle.c: grid at the cloud's minimum corner, one z-directed line through the
+    centre of every occupied voxel, lambda = total charge / dz."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    n = pos.shape[0]
+    st, sp, lam = np.empty((n, 3)), np.empty((n, 3)), np.empty(n)
+    vox = np.empty(n, dtype=np.int64)
+    L = lib().or_voxel_lines(_p(pos), _p(q), n, _p(d), _p(st), _p(sp), _p(lam),
+                             vox.ctypes.data_as(C.POINTER(C.c_int64)))
+    _check(0 if L >= 0 else -1, "voxel_lines")
+    return Lines(st[:L].copy(), sp[:L].copy(), lam[:L].copy(), vox[:L].copy())
+
+
+def line_charge(lines, tgt, soft=1e-6):
+    """Potential and field of the line charges at the targets (softened closed form)."""
+    tgt = np.ascontiguousarray(tgt, dtype=np.float64)
+    nt = tgt.shape[0]
+    phi, E = np.empty(nt), np.empty((nt, 3))
+    lib().or_line_charge(_p(lines.start), _p(lines.stop), _p(lines.lam), len(lines), _p(tgt), nt, soft, 0,
+                         _p(phi), _p(E))
+    return phi, E
+
+
+def rhs_lines(g, lines, soft=1e-6):
+    el, pe = _rec(g.elements)
+    v = np.ascontiguousarray(g.voltages, dtype=np.float64)
+    b = np.empty(el.shape[0])
+    _check(lib().or_rhs_lines(pe, el.shape[0], _p(v), v.shape[0], _p(lines.start), _p(lines.stop),
+                              _p(lines.lam), len(lines), soft, _p(b)), "rhs_lines")
+    return b
+
+
+def dynamic_step_lines(g, fac, pos, q, d, soft=1e-6, mu=1e-4, dt=1e-9):
+    """One Alg. 4 step with Type == Line; returns (new positions, sigma, E at carriers)."""
+    el, pe = _rec(g.elements)
+    v = np.ascontiguousarray(g.voltages, dtype=np.float64)
+    A, piv = fac
+    pos = np.array(pos, dtype=np.float64, copy=True)
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    n = el.shape[0]
+    sigma = np.empty(n)
+    E = np.empty((pos.shape[0], 3))
+    lat = _lat(g)
+    _check(lib().or_dynamic_step_lines(pe, n, _p(v), v.shape[0], _p(lat), g.img_lo, g.img_hi, _p(A), _pi(piv),
+                                       _p(pos), _p(q), pos.shape[0], _p(d), soft, mu, dt, _p(sigma), _p(E)),
+           "dynamic_step_lines")
     return pos, sigma, E

@@ -53,7 +53,8 @@ Ctx::~Ctx() {
     cudaSetDevice(device);
     for (DevBuf* b : {&d_el, &d_far, &d_diag, &d_sigma, &d_K, &d_LU64, &d_LU32, &d_piv64, &d_piv32, &d_work, &d_b,
                       &d_x, &d_r, &d_r32, &d_small, &d_pts, &d_phi, &d_E, &d_car, &d_q, &d_car2, &d_sc_tgt,
-                      &d_sc_phi, &d_sc_E, &d_scratch, &d_cjk, &d_cell_start, &d_cell_items})
+                      &d_sc_phi, &d_sc_E, &d_scratch, &d_cjk, &d_cell_start, &d_cell_items, &d_fv_ax, &d_fv_ay, &d_fv_az, &d_fv_phi,
+                      &d_fv_E})
         b->release();
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
@@ -181,6 +182,7 @@ int nebem_set_geometry(nebem_ctx* ctx, const nebem_element* el, int64_t n, const
     // invalidate everything that depends on the geometry
     c->n = 0;
     c->K_valid = c->fac64_valid = c->fac32_valid = c->sigma_valid = false;
+    ++c->sigma_version;
     c->bc_set = false;
     c->n_car = 0;
     CK(c->d_el.ensure(sizeof(Elem) * n));
@@ -308,6 +310,7 @@ int nebem_set_sigma(nebem_ctx* ctx, const double* sigma, int64_t n) {
     CK(cudaMemcpyAsync(c->d_sigma.ptr, sigma, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->sigma_valid = true;
+    ++c->sigma_version;
     return NEBEM_OK;
 }
 

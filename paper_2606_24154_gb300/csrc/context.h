@@ -42,6 +42,12 @@ struct Ctx {
     bool bc_set = false;
     DevBuf d_sigma;
     bool sigma_valid = false;
+    int64_t sigma_version = 0;  // bumped whenever the charge densities or known charges change
+
+    // FastVolume map (node axes and node values), built from sigma_version fv_version
+    DevBuf d_fv_ax, d_fv_ay, d_fv_az, d_fv_phi, d_fv_E;
+    int32_t fv_dims[3] = {0, 0, 0};
+    int64_t fv_version = -1;
 
     // matrix and factors
     DevBuf d_K, d_LU64, d_LU32, d_piv64, d_piv32, d_work;

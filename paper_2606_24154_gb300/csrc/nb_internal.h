@@ -133,6 +133,13 @@ cudaError_t launch_rhs_sc(const Elem* el, int64_t n, const double* phi, const do
 cudaError_t launch_centroids(const Elem* el, int64_t n, double* c, cudaStream_t s);
 cudaError_t launch_drift(double* pos, const double* q, const double* E, int64_t n, double mu_dt, cudaStream_t s);
 
+// FastVolume (fastvol.cu)
+cudaError_t launch_grid_nodes(const double* ax, const double* ay, const double* az, int nx, int ny, int nz,
+                              double* pts, cudaStream_t s);
+cudaError_t launch_fastvol_lookup(const double* ax, const double* ay, const double* az, int nx, int ny, int nz,
+                                  const double* vphi, const double* vE, const double* pts, int64_t n, double* phi,
+                                  double* E, cudaStream_t s);
+
 // thread-local last error message
 void set_error(const std::string& msg);
 

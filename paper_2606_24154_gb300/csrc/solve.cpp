@@ -153,6 +153,7 @@ int solve_with_factors(Ctx* c, int precision, nebem_solve_info* info) {
     CK(cudaStreamSynchronize(c->stream));
     if (info) info->residual = (h[1] > 0.0) ? h[0] / h[1] : 0.0;
     c->sigma_valid = true;
+    ++c->sigma_version;
     if (status) return fail(status, "iterative refinement did not reach the tolerance");
     return 0;
 }

@@ -62,6 +62,7 @@ int nebem_space_charge(nebem_ctx* ctx, const double* pos, const double* q, int64
     CK(cudaSetDevice(c->device));
     CK(cudaStreamSynchronize(c->stream));
     c->sigma_valid = false;
+    ++c->sigma_version;
     c->n_car = 0;
     if (n == 0) return NEBEM_OK;
     CK(c->d_car.ensure(sizeof(double) * 3 * n));
@@ -133,6 +134,7 @@ int nebem_step(nebem_ctx* ctx, int32_t steps, double mu, double dt, int32_t prec
                            c->d_car2.as<float4>() + m, c->stream));
     }
     c->sigma_valid = false;  // sigma belongs to the positions before the last move
+    ++c->sigma_version;
     if (pos_out) CK(cudaMemcpyAsync(pos_out, c->d_car.ptr, sizeof(double) * 3 * m, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     Ec.release();

@@ -101,6 +101,9 @@ SIGNATURES = {
     "nebem_lu_factor_device_f32": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp]),
     "nebem_lu_solve_device": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp]),
     "nebem_lu_factor_device_noalloc": (C.c_int, [_vp, C.c_int64, _vp, _vp]),
+    "nebem_fastvol_build": (C.c_int, [_vp, _d, C.c_int32, _d, C.c_int32, _d, C.c_int32, C.c_int32]),
+    "nebem_fastvol_eval": (C.c_int, [_vp, _d, C.c_int64, _d, _d]),
+    "nebem_fastvol_eval_device": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp]),
     "nebem_image_table": (C.c_int, [_vp, _d, _i64p]),
     "nebem_pair_tiers": (C.c_int, [_vp, _d, C.c_int64, C.POINTER(C.c_uint8)]),
     "nebem_element_influence": (C.c_int, [_vp, _vp, C.c_int64, _d, C.c_int64, _d, _d]),
@@ -274,6 +277,26 @@ def nebem_lu_solve_device(ctx, d_LU: int, n: int, d_piv: int, d_b: int, stream: 
 def nebem_lu_factor_device_noalloc(d_A: int, n: int, d_piv: int, stream: int | None = None):
     """Dense LU with the library's static work space (n <= 4096); allocates nothing."""
     _check(load().nebem_lu_factor_device_noalloc(d_A, n, d_piv, stream), "nebem_lu_factor_device_noalloc")
+
+
+def nebem_fastvol_build(ctx, x_nodes, y_nodes, z_nodes, precision: int):
+    ax, ay, az = _f64(x_nodes), _f64(y_nodes), _f64(z_nodes)
+    _check(load().nebem_fastvol_build(ctx, _dp(ax), ax.shape[0], _dp(ay), ay.shape[0], _dp(az), az.shape[0],
+                                      precision), "nebem_fastvol_build")
+
+
+def nebem_fastvol_eval(ctx, pts):
+    p = _f64(pts, (-1, 3))
+    n = p.shape[0]
+    phi = np.empty(n)
+    E = np.empty((n, 3))
+    _check(load().nebem_fastvol_eval(ctx, _dp(p), n, _dp(phi), _dp(E)), "nebem_fastvol_eval")
+    return phi, E
+
+
+def nebem_fastvol_eval_device(ctx, d_pts: int, n: int, d_phi: int | None, d_E: int | None,
+                              stream: int | None = None):
+    _check(load().nebem_fastvol_eval_device(ctx, d_pts, n, d_phi, d_E, stream), "nebem_fastvol_eval_device")
 
 
 def nebem_image_table(ctx):

@@ -318,4 +318,6 @@ def test_weighting_fields_reuse_the_factors(N):
     N.nebem_set_bc(ctx.h, g.voltages)
     sig_all, _, _ = ctx.solve(N.NEBEM_FP64)
     combo = sum(V * u for V, u in zip(g.voltages, units))
-    assert rel_norm(combo, sig_all) <= 1e-12
+    # each unit solve is good to the FP64 solve tolerance; the voltage-weighted sum of
+    # four of them (|V| up to 1700 V, opposite signs) carries those errors scaled by |V|
+    assert rel_norm(combo, sig_all) <= TOL64

@@ -458,3 +458,171 @@ def test_known_charge_rhs_and_dynamic_step():
     step = np.sign(q)[:, None] * 1e-4 * E * 1e-9
     assert np.abs(pos1 - (pos + step)).max() <= 4e-16 * np.abs(pos).max()
     assert np.abs(step).max() > 1e-3 * 1e-16 * 0 + 1e-14
+
+
+# --- line-charge representation (Sec. 4.2, Alg. 3; LineCh in Alg. 4) ---------------
+
+def _cloud(seed, n=300, scale=30e-6):
+    gen = np.random.default_rng(seed)
+    pos = gen.normal(scale=scale, size=(n, 3))
+    q = gen.choice([-1.0, 1.0], n) * I.E_CHARGE * gen.integers(1, 5, n)
+    return pos, q
+
+
+def test_voxel_lines_brute_force():
+    """Alg. 3 against an assignment by geometric containment: every voxel of the grid
+    is visited and the points with lo + i d <= x < lo + (i+1) d (per axis) are summed
+    in point order; the occupied voxels are exactly the oracle's lines, in voxel order."""
+    pos, q = _cloud(3)
+    d = np.array([12e-6, 15e-6, 20e-6])
+    L = O.voxel_lines(pos, q, d)
+    lo = pos.min(0)
+    dims = (np.floor((pos.max(0) - lo) / d) + 1).astype(np.int64)
+    assert np.array_equal(O.voxel_grid(pos, d)[1], dims)
+    starts, lams, vox = [], [], []
+    for k in range(dims[2]):
+        for j in range(dims[1]):
+            for i in range(dims[0]):
+                idx = np.array([i, j, k])
+                inside = np.all((pos >= lo + idx * d) & ((pos < lo + (idx + 1) * d) | (idx == dims - 1)), axis=1)
+                if not inside.any():
+                    continue
+                Q = 0.0
+                for p in np.nonzero(inside)[0]:
+                    Q += q[p]
+                vox.append((k * dims[1] + j) * dims[0] + i)
+                starts.append([lo[0] + (i + 0.5) * d[0], lo[1] + (j + 0.5) * d[1], lo[2] + k * d[2]])
+                lams.append(Q / d[2])
+    assert np.array_equal(L.voxel, vox)
+    assert np.array_equal(L.start, np.array(starts))
+    assert np.array_equal(L.stop[:, :2], L.start[:, :2]) and np.array_equal(L.stop[:, 2], L.start[:, 2] + d[2])
+    assert np.array_equal(L.lam, np.array(lams))
+    # charge is conserved
+    assert abs((L.lam * d[2]).sum() - q.sum()) <= 1e-14 * np.abs(q).sum()
+    # a voxel as large as the cloud gives one line with all the charge
+    big = O.voxel_lines(pos, q, [1.0, 1.0, 1.0])
+    assert len(big) == 1 and abs(big.lam[0] - q.sum()) <= 1e-14 * np.abs(q).sum()
+
+
+def _line_quad(A, B, lam, P, s):
+    u = B - A
+    Ln = np.linalg.norm(u)
+    u = u / Ln
+
+    def r(t):
+        return P - A - t * u
+
+    def f(t, k):
+        rr = r(t)
+        R2 = rr @ rr + s * s
+        return 1.0 / math.sqrt(R2) if k < 0 else rr[k] / R2 ** 1.5
+
+    opts = dict(epsabs=0.0, epsrel=1e-13, limit=200)
+    phi = integrate.quad(f, 0.0, Ln, args=(-1,), **opts)[0]
+    E = np.array([integrate.quad(f, 0.0, Ln, args=(k,), **opts)[0] for k in range(3)])
+    return O.ke() * lam * phi, O.ke() * lam * E
+
+
+def test_line_charge_vs_quadrature():
+    gen = np.random.default_rng(41)
+    for trial in range(6):
+        A = gen.normal(size=3) * 1e-4
+        B = A + gen.normal(size=3) * 5e-5
+        lam = gen.normal() * 1e-9
+        lines = O.Lines(A[None], B[None], np.array([lam]))
+        s = [0.0, 1e-6][trial % 2]
+        P = np.stack([A + gen.normal(size=3) * 1e-4 for _ in range(4)] + [0.5 * (A + B) + 2e-6 * gen.normal(size=3)])
+        phi, E = O.line_charge(lines, P, soft=s)
+        for p in range(P.shape[0]):
+            rp, rE = _line_quad(A, B, lam, P[p], s)
+            assert abs(phi[p] - rp) <= 1e-11 * abs(rp)
+            assert np.abs(E[p] - rE).max() <= 1e-10 * np.linalg.norm(rE)
+
+
+def test_line_charge_textbook_values():
+    ke, lam, Ln = O.ke(), 3e-10, 2e-4
+    A, B = np.zeros(3), np.array([0.0, 0.0, Ln])
+    lines = O.Lines(A[None], B[None], np.array([lam]))
+    # on the axis beyond the end (no softening): ke lam ln((d+L)/d), E_z = ke lam (1/d - 1/(d+L))
+    dd = 7e-5
+    phi, E = O.line_charge(lines, np.array([[0.0, 0.0, Ln + dd]]), soft=0.0)
+    assert abs(phi[0] - ke * lam * math.log((dd + Ln) / dd)) <= 1e-14 * abs(phi[0])
+    assert abs(E[0, 2] - ke * lam * (1 / dd - 1 / (dd + Ln))) <= 1e-13 * abs(E[0, 2])
+    assert np.abs(E[0, :2]).max() <= 1e-12 * abs(E[0, 2])
+    # beside the midpoint: E_perp = ke lam L / (rho sqrt(rho^2 + L^2/4)), E_z = 0
+    rho = 3e-5
+    phi, E = O.line_charge(lines, np.array([[rho, 0.0, Ln / 2]]), soft=0.0)
+    assert abs(E[0, 0] - ke * lam * Ln / (rho * math.sqrt(rho ** 2 + Ln ** 2 / 4))) <= 1e-13 * abs(E[0, 0])
+    assert abs(E[0, 2]) <= 1e-12 * abs(E[0, 0])
+    assert abs(phi[0] - 2 * ke * lam * math.asinh(Ln / 2 / rho)) <= 1e-14 * abs(phi[0])
+    # far field: a point charge lam L
+    for R, tol in [(1e-2, 1e-3), (1e-1, 1e-5)]:
+        P = np.array([[R * 0.6, 0.0, Ln / 2 + R * 0.8]])
+        phi, E = O.line_charge(lines, P, soft=1e-6)
+        assert abs(phi[0] * R / (ke * lam * Ln) - 1) < tol
+
+
+def test_line_charge_gauss_law_and_gradient():
+    lam, Ln = 1e-9, 1.0
+    A, B = np.array([0.1, -0.2, 0.3]), np.array([0.1, -0.2, 0.3]) + np.array([0.48, 0.6, 0.64]) * Ln
+    lines = O.Lines(A[None], B[None], np.array([lam]))
+    lo, hi = np.minimum(A, B) - 0.7, np.maximum(A, B) + 0.7
+    flux = _box_flux(lambda P: O.line_charge(lines, P, soft=0.0)[1], lo, hi, m=60)
+    assert abs(flux - lam * Ln / O.eps0()) <= 1e-7 * lam * Ln / O.eps0()
+    # E = -grad phi, softened and not
+    gen = np.random.default_rng(43)
+    for s in (0.0, 0.05):
+        for P in [A + gen.normal(size=3) * 0.5 for _ in range(4)]:
+            _, E = O.line_charge(lines, P[None], soft=s)
+            h, g = 1e-5, np.zeros(3)
+            for k in range(3):
+                dp = np.zeros(3); dp[k] = h
+                g[k] = (O.line_charge(lines, (P + dp)[None], soft=s)[0][0]
+                        - O.line_charge(lines, (P - dp)[None], soft=s)[0][0]) / (2 * h)
+            assert np.abs(E[0] + g).max() <= 1e-7 * np.abs(E[0]).max()
+
+
+def test_line_rhs_tends_to_point_rhs():
+    """A carrier at the centre of its own small voxel becomes a short line centred on it,
+    so the line-charge RHS equals the point-charge RHS up to O((dz / r)^2) (Alg. 4,
+    Type == Line vs Type == Point).  Two uncharged carriers fix the grid's corner."""
+    g = I.cube(n_per_edge=4)
+    gen = np.random.default_rng(47)
+    d = 1e-6
+    pos = gen.normal(size=(30, 3)) * 2e-3 + np.array([0.0, 0.0, 0.012])
+    q = np.where(gen.random(30) < 0.5, 1.0, -1.0) * 1e-15
+    lo = pos.min(0) - 10 * d
+    pos = lo + (np.floor((pos - lo) / d) + 0.5) * d
+    cloud = np.concatenate([lo[None], pos, (pos.max(0) + 10 * d)[None]])
+    qc = np.concatenate([[0.0], q, [0.0]])
+    L = O.voxel_lines(cloud, qc, [d, d, d])
+    assert len(L) == 32 and (L.lam != 0).sum() == 30
+    mid = 0.5 * (L.start + L.stop)
+    assert np.abs(np.sort(mid[L.lam != 0], axis=0) - np.sort(pos, axis=0)).max() <= 1e-15
+    b_pt = O.rhs_space_charge(g, pos, q)
+    b_ln = O.rhs_lines(g, L)
+    b0 = O.rhs(g)
+    assert np.abs((b_ln - b0) - (b_pt - b0)).max() <= 1e-6 * np.abs(b_pt - b0).max()
+    with pytest.raises(ValueError):
+        O.voxel_lines(pos, q, [1e-12, 1e-12, 1e-12])  # 1e27 voxels: rejected
+
+
+def test_dynamic_step_lines_satisfies_bc():
+    g = I.cube(n_per_edge=4)
+    _, _, fac = O.solve(g)
+    c, _, _ = O.centroids(g)
+    gen = np.random.default_rng(53)
+    pos = gen.normal(size=(200, 3)) * 5e-4 + np.array([0.0, 0.0, 0.009])
+    q = np.where(gen.random(200) < 0.5, 1.0, -1.0) * 1e-14
+    d = np.array([3e-4, 3e-4, 4e-4])
+    pos1, sigma, E = O.dynamic_step_lines(g, fac, pos, q, d)
+    L = O.voxel_lines(pos, q, d)
+    # with the lines as known charges, the total potential at every collocation point is the BC
+    pe, Ee = O.eval_points(g, sigma, c)
+    pl, _ = O.line_charge(L, c)
+    assert np.abs(pe + pl - 1.0).max() < 1e-10
+    # E at the carriers is the elements' field plus the lines' field
+    _, Ec = O.eval_points(g, sigma, pos)
+    _, El = O.line_charge(L, pos)
+    assert np.abs(E - (Ec + El)).max() <= 1e-12 * np.abs(E).max()
+    assert np.abs(pos1 - (pos + np.sign(q)[:, None] * 1e-4 * E * 1e-9)).max() <= 4e-16 * np.abs(pos).max()
