@@ -206,10 +206,41 @@ int nebem_eval_device(nebem_ctx *ctx, const double *d_pts, int64_t n, double *d_
  * Invalidates sigma (the right-hand side changes), keeps the factors. */
 int nebem_space_charge(nebem_ctx *ctx, const double *pos, const double *q, int64_t n, double softening);
 
+/* Point -> line charge reduction (Sec. 4.2, Alg. 3) of the current point-charge set, which
+ * then stands for the known charges (the LineCh branch of Alg. 4) until the next
+ * nebem_space_charge call.
+ *   voxel[3]  voxel edges (dx, dy, dz) in m, each > 0.
+ * The grid is anchored at the minimum corner (xmin, ymin, zmin) of the cloud: a point
+ * falls in voxel (i, j, k) = floor((x - xmin) / dx), ... (IEEE FP64), with flat index
+ * (k * ny + j) * nx + i and ny, nx = floor((max - min) / d) + 1.  Every occupied voxel
+ * gives one line charge along +z through the voxel centre (xmin + (i + 1/2) dx,
+ * ymin + (j + 1/2) dy), from zmin + k dz to zmin + (k + 1) dz, with density
+ * lambda = (sum of the voxel's charges, in point order) / dz in C/m.  Lines are listed in
+ * increasing voxel index; the reduction is deterministic.  The line charges carry the
+ * point charges' softening: phi = ke lambda int dt / sqrt(r(t)^2 + s^2).
+ * While lines are in use, the right-hand side, nebem_eval's known-charge part,
+ * nebem_space_charge_eval (exclude_self must be 0) and nebem_step use them, and
+ * nebem_step repeats the reduction after every move.  The point charges are kept.
+ *   n_lines  (may be NULL) receives the number of lines.
+ * Invalidates sigma, keeps the factors.
+ * Errors: NEBEM_BAD_STATE (no point charges), NEBEM_TOO_LARGE (more than 2^26 points, or
+ * voxels * points >= 4e18), NEBEM_INVALID_ARG. */
+int nebem_space_charge_lines(nebem_ctx *ctx, const double *voxel, int64_t *n_lines);
+
+/* Copy the current line charges to the host: start[L][3], stop[L][3] (m), lambda[L] (C/m),
+ * each may be NULL.  *n_lines (may be NULL) receives L.  capacity = 0 only queries L;
+ * 0 < capacity < L returns NEBEM_TOO_LARGE and writes nothing.
+ * Errors: NEBEM_BAD_STATE when the known charges are point charges. */
+int nebem_get_lines(nebem_ctx *ctx, double *start, double *stop, double *lambda, int64_t capacity,
+                    int64_t *n_lines);
+
 /* Direct space-charge sum at points (Alg. 2, all pairs, softened):
  * phi_t = ke sum_{c != self(t)} q_c / sqrt(r^2 + s^2), E_t = ke sum q_c (x_t - x_c) /
  * (r^2 + s^2)^{3/2}.  exclude_self != 0 means target t is carrier t (n must equal the
- * carrier count) and is excluded.  Host buffers as in nebem_eval. */
+ * carrier count) and is excluded.  With line charges in use (nebem_space_charge_lines) the
+ * sum runs over the lines instead, exclude_self must be 0, and mixed precision evaluates
+ * lines farther than 3 half-lengths with FP32 Gauss-Legendre nodes along the line (2 to
+ * 6 by distance), nearer ones in FP64.  Host buffers as in nebem_eval. */
 int nebem_space_charge_eval(nebem_ctx *ctx, const double *pts, int64_t n, double *phi, double *E,
                             int32_t precision, int32_t exclude_self);
 
@@ -217,10 +248,13 @@ int nebem_space_charge_eval(nebem_ctx *ctx, const double *pts, int64_t n, double
  * instead of being tracked): per step (1) right-hand side with the known charges at the
  * collocation points, (2) sigma from the retained factors (mixed: FP32 solve + FP64
  * refinement), (3) E at every carrier from all elements (with images) and all other
- * carriers, (4) x_c += sign(q_c) * mu * E_c * dt.  Requires a solved geometry
+ * carriers, (4) x_c += sign(q_c) * mu * E_c * dt.  With line charges in use, every step
+ * starts with the reduction of Alg. 3 on the current positions, and (1) and (3) sum over
+ * the lines (a carrier's own charge is part of its voxel's line).  Requires a solved geometry
  * (factors) and a known-charge set; positions stay on the device between steps.
  * pos_out[n][3] (host, may be NULL) receives the final positions.
- * Errors: NEBEM_BAD_STATE, NEBEM_NOT_CONVERGED, NEBEM_CUDA. */
+ * Errors: NEBEM_BAD_STATE, NEBEM_NOT_CONVERGED, NEBEM_CUDA, NEBEM_TOO_LARGE (a step's voxel
+ * grid too large; the positions are still advanced). */
 int nebem_step(nebem_ctx *ctx, int32_t steps, double mu, double dt, int32_t precision, double *pos_out);
 
 /* Dense LU factorisation of a caller's matrix on the device (Sec. 4.1, Alg. 1, with the

@@ -24,7 +24,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
 # Per-file flags: the FP32 evaluation bodies (standalone mixed kernels and the serving
 # kernel, which must agree bit for bit) flush denormals: their distances, weights and
 # field terms are all many orders of magnitude above the FP32 denormal range.
-FILE_FLAGS = {"eval_mixed.cu": ["-ftz=true"], "server.cu": ["-ftz=true"]}
+FILE_FLAGS = {"eval_mixed.cu": ["-ftz=true"], "server.cu": ["-ftz=true"], "lines.cu": ["-ftz=true"]}
 
 
 def _nvcc() -> str:

@@ -63,6 +63,10 @@ struct Ctx {
     int sc_precision = NEBEM_FP64;  // precision of the known-charge RHS term
     DevBuf d_car, d_q, d_car2, d_sc_tgt, d_sc_phi, d_sc_E;
     std::vector<double> h_q;
+    // line-charge representation of the known charges (Alg. 3): on when sc_lines
+    bool sc_lines = false;
+    double voxel[3] = {0.0, 0.0, 0.0};
+    DevBuf d_vkeys, d_vflags, d_vbsum, d_vpartial, d_vgrid, d_lines, d_linesf;
 
     ~Ctx();
 };
@@ -84,5 +88,6 @@ int eval_points(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d
 int rhs_known_charge(Ctx* c);
 int add_known_charge(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision,
                      cudaStream_t s);
+VoxWork vox_work(Ctx* c);
 
 }  // namespace nb

@@ -133,6 +133,49 @@ cudaError_t launch_rhs_sc(const Elem* el, int64_t n, const double* phi, const do
 cudaError_t launch_centroids(const Elem* el, int64_t n, double* c, cudaStream_t s);
 cudaError_t launch_drift(double* pos, const double* q, const double* E, int64_t n, double mu_dt, cudaStream_t s);
 
+// line charges (lines.cu): point -> line reduction (Sec. 4.2, Alg. 3) and line-charge sums
+// Grid of the reduction and the resulting line count, kept on the device so that a
+// dynamic step needs no host round trip.  err != 0: the grid had too many voxels;
+// sticky keeps that flag over a sequence of reductions until the host clears it.
+struct VoxGrid {
+    double lo[3], d[3];
+    long long dims[3];
+    long long nvox;
+    long long nl;
+    int err;
+    int sticky;
+};
+// One line charge: start a, unit direction u, length len, density lam (C/m).
+struct __align__(16) LineRec {
+    double a[3], lam;
+    double u[3], len;
+};
+// FP32 shadow for the mixed sum: midpoint as two floats (mh.xyz + ml.xyz), half length
+// (mh.w), density (ml.w), direction (u.xyz).
+struct __align__(16) LineF {
+    float4 mh, ml, u;
+};
+// Device work space of one reduction of n points.
+struct VoxWork {
+    long long* keys;   // pad_len(n) sort keys (voxel * n + point)
+    int* flags;        // n segment heads, scanned in place to line indices
+    int* bsum;         // scan block sums, scan_blocks(n)
+    double* partial;   // 6 per min/max block
+    VoxGrid* grid;     // one
+    LineRec* lines;    // n (at most one line per point)
+    LineF* linesf;     // n
+};
+int64_t vox_pad_len(int64_t n);     // sort length: power of two >= max(n, 2048)
+int64_t vox_scan_blocks(int64_t n);
+constexpr int64_t kVoxMaxPoints = (int64_t)1 << 26;
+cudaError_t launch_voxelize(const double* pos, const double* q, int64_t n, const double d[3], const VoxWork& w,
+                            cudaStream_t s);
+// phi/E at targets from the lines of w.grid->nl (device count); perm (may be NULL) lists
+// the targets in the order the threads take them, as perm[t] % perm_div.
+cudaError_t launch_line_eval(int precision, const VoxWork& w, const double* tgt, const long long* perm,
+                             int64_t perm_div, int64_t nt, double soft, int accumulate, double* phi, double* E,
+                             cudaStream_t s);
+
 // FastVolume (fastvol.cu)
 cudaError_t launch_grid_nodes(const double* ax, const double* ay, const double* az, int nx, int ny, int nz,
                               double* pts, cudaStream_t s);

@@ -96,6 +96,8 @@ SIGNATURES = {
     "nebem_eval_device": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, C.c_int32, _vp]),
     "nebem_space_charge": (C.c_int, [_vp, _d, _d, C.c_int64, C.c_double]),
     "nebem_space_charge_eval": (C.c_int, [_vp, _d, C.c_int64, _d, _d, C.c_int32, C.c_int32]),
+    "nebem_space_charge_lines": (C.c_int, [_vp, _d, _i64p]),
+    "nebem_get_lines": (C.c_int, [_vp, _d, _d, _d, C.c_int64, _i64p]),
     "nebem_step": (C.c_int, [_vp, C.c_int32, C.c_double, C.c_double, C.c_int32, _d]),
     "nebem_lu_factor_device": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp]),
     "nebem_lu_factor_device_f32": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp]),
@@ -244,6 +246,23 @@ def nebem_space_charge(ctx, pos, q, softening=0.0):
     p = _f64(pos, (-1, 3))
     qq = _f64(q)
     _check(load().nebem_space_charge(ctx, _dp(p), _dp(qq), p.shape[0], softening), "nebem_space_charge")
+
+
+def nebem_space_charge_lines(ctx, voxel) -> int:
+    v = _f64(voxel)
+    nl = C.c_int64(0)
+    _check(load().nebem_space_charge_lines(ctx, _dp(v), C.byref(nl)), "nebem_space_charge_lines")
+    return nl.value
+
+
+def nebem_get_lines(ctx):
+    """(start, stop, lambda) of the current line charges."""
+    nl = C.c_int64(0)
+    _check(load().nebem_get_lines(ctx, None, None, None, 0, C.byref(nl)), "nebem_get_lines")
+    L = nl.value
+    start, stop, lam = np.empty((L, 3)), np.empty((L, 3)), np.empty(L)
+    _check(load().nebem_get_lines(ctx, _dp(start), _dp(stop), _dp(lam), L, C.byref(nl)), "nebem_get_lines")
+    return start, stop, lam
 
 
 def nebem_space_charge_eval(ctx, pts, precision: int, exclude_self=False):
