@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--serving-requests", type=int, default=40)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--workload", default="thgem_eval",
-                    choices=["thgem_eval", "double_thgem_solve", "space_charge"])
+                    choices=["thgem_eval", "double_thgem_solve", "space_charge", "lu"])
     return ap.parse_args()
 
 
@@ -450,9 +450,70 @@ def run_space_charge(args):
         out[name] = {"s_per_step": dt, "carrier_pairs_per_s": pairs / dt,
                      "element_evals_per_s": n_car * g.n * g.n_images / dt}
         c.close()
+    # the same steps with the carriers reduced to line charges (Alg. 3) before every step
+    voxel = [20e-6, 20e-6, 40e-6]
+    c = N.Context().set_geometry(g)
+    c.solve(N.NEBEM_MIXED)
+    N.nebem_space_charge(c.h, pos, q, 1e-6)
+    nl = N.nebem_space_charge_lines(c.h, voxel)
+    N.nebem_step(c.h, max(1, args.warmup), 1e-4, 1e-9, N.NEBEM_MIXED, n_car)
+    N.nebem_space_charge(c.h, pos, q, 1e-6)
+    N.nebem_space_charge_lines(c.h, voxel)
+    t = time.perf_counter()
+    N.nebem_step(c.h, args.steps, 1e-4, 1e-9, N.NEBEM_MIXED, n_car)
+    dt = (time.perf_counter() - t) / args.steps
+    t = time.perf_counter()
+    N.nebem_space_charge_eval(c.h, pos, N.NEBEM_MIXED)
+    t_sum = time.perf_counter() - t
+    out["mixed_lines"] = {"s_per_step": dt, "voxel_m": voxel, "lines": nl,
+                          "line_pairs_per_step": n_car * nl,
+                          "line_sum_at_carriers_s_host_api": t_sum,
+                          "element_evals_per_s": n_car * g.n * g.n_images / dt}
+    c.close()
     line = {"metric": "dynamic space-charge step time", "workload": f"thgem_cell N={g.n} carriers={n_car}",
             "value": out["mixed"]["s_per_step"], "unit": "s/step", "higher_is_better": False, "steps": args.steps,
             "detail": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_lu(args):
+    """Dense LU of an n x n matrix (n = --points) on the device, FP32 (tcgen05 trailing
+    updates) and FP64; one step = one factorisation of a fresh copy.  The matrix is a
+    seeded random matrix plus n on the diagonal (well conditioned, pivoting still active)."""
+    import torch
+
+    from paper_2606_24154_gb300 import build as B
+    from paper_2606_24154_gb300 import nebem as N
+    B.build()
+    n = args.points
+    gen = torch.Generator(device="cuda").manual_seed(20261203)
+    A0 = torch.rand((n, n), generator=gen, device="cuda", dtype=torch.float64) - 0.5
+    A0 += torch.eye(n, device="cuda", dtype=torch.float64) * 0.1 * n ** 0.5
+    piv = torch.empty(n, dtype=torch.int32, device="cuda")
+    c = N.Context()
+    out = {}
+    for name, dt, fn in (("fp32_tc", torch.float32, N.nebem_lu_factor_device_f32),
+                         ("fp64", torch.float64, N.nebem_lu_factor_device)):
+        A = torch.empty((n, n), dtype=dt, device="cuda")
+        times = []
+        for step in range(args.warmup + args.steps):
+            A.copy_(A0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn(c.h, A.data_ptr(), n, piv.data_ptr(), torch.cuda.current_stream().cuda_stream)
+            e1.record()
+            torch.cuda.synchronize()
+            if step >= args.warmup:
+                times.append(e0.elapsed_time(e1) * 1e-3)
+        t = min(times)
+        out[name] = {"s": t, "tflops": (2.0 / 3.0) * n ** 3 / t / 1e12}
+        del A
+    c.close()
+    line = {"metric": "dense LU factorisation", "workload": f"random n={n} (+diagonal), column-major",
+            "value": out["fp32_tc"]["tflops"], "unit": "TFLOP/s (2/3 n^3)", "higher_is_better": True,
+            "steps": args.steps, "detail": out}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -465,6 +526,8 @@ def main():
         return run_double_thgem_solve(args)
     if args.workload == "space_charge":
         return run_space_charge(args)
+    if args.workload == "lu":
+        return run_lu(args)
     return run_native(args)
 
 
