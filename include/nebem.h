@@ -55,20 +55,25 @@ typedef enum nebem_status {
     NEBEM_SINGULAR = -5,           /* exact zero pivot in the LU factorisation */
     NEBEM_NOT_CONVERGED = -6,      /* iterative refinement hit its iteration limit */
     NEBEM_TIMEOUT = -7,            /* a bounded device-side wait gave up */
-    NEBEM_DEGENERATE_ELEMENT = -8, /* zero-area, non-planar or non-right-angled element */
+    NEBEM_DEGENERATE_ELEMENT = -8, /* zero-area, non-planar, non-convex or non-right-angled element */
     NEBEM_NO_DEVICE = -9,          /* no usable CUDA device */
     NEBEM_TOO_LARGE = -10          /* size beyond a documented limit */
 } nebem_status;
 
 typedef enum nebem_precision { NEBEM_FP64 = 0, NEBEM_MIXED = 1 } nebem_precision;
 
-typedef enum nebem_kind { NEBEM_RECT = 0, NEBEM_TRI = 1 } nebem_kind;
+typedef enum nebem_kind { NEBEM_RECT = 0, NEBEM_TRI = 1, NEBEM_QUAD = 2 } nebem_kind;
 typedef enum nebem_bc { NEBEM_CONDUCTOR = 0, NEBEM_DIELECTRIC = 1 } nebem_bc;
 
 /* One flat boundary element (Sec. 2: rectangular and triangular surface elements with
  * uniform charge density; collocation at the centroid).  128 bytes.
  *   kind      NEBEM_RECT: v[0..3] in order around the rectangle, right angles, planar
  *             (v2 = v1 + v3 - v0 within 1e-9 relative).  NEBEM_TRI: v[0..2]; v[3] ignored.
+ *             NEBEM_QUAD: v[0..3] in order around a planar convex quadrilateral (v3 within
+ *             1e-9 of the size from the plane of v0, v1, v2; every corner convex); its
+ *             centroid is the area centroid.  Quadrilaterals are the flat pieces of graded
+ *             polar meshes and the primitives of Adaptive Modelling (nebem_set_primitives);
+ *             they use the same edge formula as the other kinds.
  *   bc        NEBEM_CONDUCTOR: potential prescribed, V = voltages[conductor].
  *             NEBEM_DIELECTRIC: interface between relative permittivities eps_a on the
  *             -n side and eps_b on the +n side (eps_a != eps_b); conductor ignored.

@@ -11,8 +11,9 @@
  *     (Sec. 2.1: rectangle with corners (X1,0,Z1),(X2,0,Z2); right/general triangle;
  *     field integral of r-hat / r^2), evaluated in closed form:
  *       * rectangles by the corner antiderivative in the paper's own parametrisation;
- *       * triangles by the boundary (edge) decomposition of the surface integral,
- *         with the solid angle written as a sum of per-edge arctangent differences;
+ *       * triangles and planar convex quadrilaterals by the boundary (edge)
+ *         decomposition of the surface integral, with the solid angle written as a sum
+ *         of per-edge arctangent differences;
  *   - periodic images ("virtual copies", Sec. 5 Case 2) of every element,
  *     t = k1*a1 + k2*a2 for k1, k2 in [lo, hi], image index (k1-lo)*m + (k2-lo);
  *   - the collocation influence matrix K (Eq. Matrix) with conductor rows
@@ -98,7 +99,7 @@ int or_build(const or_input *in, int64_t n, or_elem *out) {
         e->cond = r->conductor;
         e->eps_a = r->eps_a;
         e->eps_b = r->eps_b;
-        e->nv = (r->kind == 0) ? 4 : 3;
+        e->nv = (r->kind == 0 || r->kind == 2) ? 4 : 3;
         double e1[3], e2[3], nn[3];
         for (int k = 0; k < 3; ++k) {
             e->o[k] = r->v[0][k];
@@ -125,7 +126,31 @@ int or_build(const or_input *in, int64_t n, or_elem *out) {
             for (int vtx = 0; vtx < e->nv; ++vtx) s += r->v[vtx][k];
             e->c[k] = s / e->nv;
         }
-        if (e->kind == 0) {
+        if (e->kind == 2) {
+            /* planar convex quadrilateral: v3 in the plane of v0, v1, v2, every corner
+             * turning counter-clockwise in the local (x, z) frame; the centroid is the
+             * area centroid (triangles (v0, v1, v2) and (v0, v2, v3) weighted by area) */
+            double d3[3], size = 0.0;
+            for (int k = 0; k < 3; ++k) d3[k] = r->v[3][k] - r->v[0][k];
+            for (int vtx = 1; vtx < 4; ++vtx) {
+                double dv[3] = {r->v[vtx][0] - r->v[0][0], r->v[vtx][1] - r->v[0][1], r->v[vtx][2] - r->v[0][2]};
+                if (norm3(dv) > size) size = norm3(dv);
+            }
+            if (fabs(dot3(d3, e->ey)) > 1e-9 * size) return -(int)(1 + i);
+            for (int vtx = 0; vtx < 4; ++vtx) {
+                const double *a = e->q[vtx], *b = e->q[(vtx + 1) % 4], *c = e->q[(vtx + 2) % 4];
+                double turn = (b[0] - a[0]) * (c[1] - b[1]) - (b[1] - a[1]) * (c[0] - b[0]);
+                if (!(turn > 0.0)) return -(int)(1 + i);
+            }
+            double A1 = 0.5 * ((e->q[1][0] - e->q[0][0]) * (e->q[2][1] - e->q[0][1]) -
+                               (e->q[1][1] - e->q[0][1]) * (e->q[2][0] - e->q[0][0]));
+            double A2 = 0.5 * ((e->q[2][0] - e->q[0][0]) * (e->q[3][1] - e->q[0][1]) -
+                               (e->q[2][1] - e->q[0][1]) * (e->q[3][0] - e->q[0][0]));
+            for (int k = 0; k < 3; ++k)
+                e->c[k] = (A1 * (r->v[0][k] + r->v[1][k] + r->v[2][k]) / 3.0 +
+                           A2 * (r->v[0][k] + r->v[2][k] + r->v[3][k]) / 3.0) / (A1 + A2);
+            e->area = A1 + A2;
+        } else if (e->kind == 0) {
             /* rectangle: v3 - v0 must be perpendicular to v1 - v0 and v2 = v1 + v3 - v0 */
             double e3[3];
             for (int k = 0; k < 3; ++k) e3[k] = r->v[3][k] - r->v[0][k];
@@ -822,5 +847,82 @@ int or_dynamic_step_lines(const or_input *in, int64_t n, const double *voltages,
     free(lam);
     free(b);
     free(Ee);
+    return rc;
+}
+
+/* ---------------------------------------------------------------------------------
+ * Adaptive Modelling (Sec. 3.3; PrimAfter in Sec. 5.3.1): far copies of the periodic
+ * structure are represented by whole primitives carrying their average charge density.
+ * Readings fixed here where the paper is silent:
+ *   - a primitive is a flat polygon (rectangle, triangle or convex quadrilateral) that
+ *     the elements assigned to it tile; prim_of[j] is the primitive of element j, or -1
+ *     when element j belongs to none (it then stands for itself in every copy);
+ *   - the average charge density of primitive p is its total charge over its area,
+ *     sigma_p = sum_{j in p} sigma_j A_j / A_p;
+ *   - copy k = (k1, k2) of the lattice is distant when its ring index max(|k1|, |k2|)
+ *     exceeds prim_after; prim_after < 0 means no copy is distant (plain evaluation);
+ *   - the point's potential and field are the element sums over the near copies plus
+ *     the primitive sums over the distant copies.
+ * ------------------------------------------------------------------------------- */
+int or_eval_am(const or_input *in, int64_t n, const double *sigma, const double *lattice, int lo, int hi,
+               const or_input *prim, int64_t np, const int32_t *prim_of, int prim_after, const double *pts,
+               int64_t npts, double *phi_out, double *E_out) {
+    or_elem *el = (or_elem *)malloc(sizeof(or_elem) * (size_t)(n ? n : 1));
+    or_elem *pe = (or_elem *)malloc(sizeof(or_elem) * (size_t)(np ? np : 1));
+    double *psig = (double *)calloc((size_t)(np ? np : 1), sizeof(double));
+    double *parea = (double *)calloc((size_t)(np ? np : 1), sizeof(double));
+    int rc = or_build(in, n, el);
+    if (rc == 0 && np > 0) rc = or_build(prim, np, pe) ? -1 : 0;
+    for (int64_t j = 0; rc == 0 && j < n; ++j) {
+        if (prim_of[j] < -1 || prim_of[j] >= np) rc = -2;
+        else if (prim_of[j] >= 0) {
+            psig[prim_of[j]] += sigma[j] * el[j].area;
+            parea[prim_of[j]] += el[j].area;
+        }
+    }
+    for (int64_t p = 0; rc == 0 && p < np; ++p) {
+        if (fabs(parea[p] - pe[p].area) > 1e-9 * pe[p].area) rc = -3; /* elements do not tile it */
+        psig[p] /= pe[p].area;
+    }
+    int64_t nimg = image_count(lattice, lo, hi);
+    int m = hi - lo + 1;
+    double *tt = (double *)malloc(sizeof(double) * 3 * (size_t)nimg);
+    int *far = (int *)malloc(sizeof(int) * (size_t)nimg);
+    or_image_table(lattice, lo, hi, tt);
+    for (int64_t k = 0; k < nimg; ++k) {
+        int k1 = lattice ? (int)(k / m) + lo : 0, k2 = lattice ? (int)(k % m) + lo : 0;
+        int ring = abs(k1) > abs(k2) ? abs(k1) : abs(k2);
+        far[k] = (prim_after >= 0 && ring > prim_after);
+    }
+    double ke = or_ke();
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t p = 0; p < (rc == 0 ? npts : 0); ++p) {
+        double sphi = 0.0, sE[3] = {0.0, 0.0, 0.0};
+        for (int64_t k = 0; k < nimg; ++k) {
+            double P[3] = {pts[3 * p] - tt[3 * k], pts[3 * p + 1] - tt[3 * k + 1], pts[3 * p + 2] - tt[3 * k + 2]};
+            double f, E[3];
+            for (int64_t j = 0; j < n; ++j) {
+                if (far[k] && prim_of[j] >= 0) continue;
+                or_influence(&el[j], P, 0, &f, E);
+                sphi += sigma[j] * f;
+                for (int c = 0; c < 3; ++c) sE[c] += sigma[j] * E[c];
+            }
+            if (!far[k]) continue;
+            for (int64_t q = 0; q < np; ++q) {
+                or_influence(&pe[q], P, 0, &f, E);
+                sphi += psig[q] * f;
+                for (int c = 0; c < 3; ++c) sE[c] += psig[q] * E[c];
+            }
+        }
+        if (phi_out) phi_out[p] = ke * sphi;
+        if (E_out)
+            for (int c = 0; c < 3; ++c) E_out[3 * p + c] = ke * sE[c];
+    }
+    free(el);
+    free(pe);
+    free(psig);
+    free(parea);
+    free(tt);
+    free(far);
     return rc;
 }

@@ -70,6 +70,8 @@ def lib():
         L.or_rhs_lines.argtypes = [_vp, C.c_int64, _d, C.c_int32, _d, _d, _d, C.c_int64, C.c_double, _d]
         L.or_dynamic_step_lines.argtypes = [_vp, C.c_int64, _d, C.c_int32, _d, C.c_int, C.c_int, _d, _i32, _d,
                                             _d, C.c_int64, _d, C.c_double, C.c_double, C.c_double, _d, _d]
+        L.or_eval_am.argtypes = [_vp, C.c_int64, _d, _d, C.c_int, C.c_int, _vp, C.c_int64, C.POINTER(C.c_int32),
+                                 C.c_int, _d, C.c_int64, _d, _d]
         _lib = L
     return _lib
 
@@ -365,3 +367,20 @@ def dynamic_step_lines(g, fac, pos, q, d, soft=1e-6, mu=1e-4, dt=1e-9):
                                        _p(pos), _p(q), pos.shape[0], _p(d), soft, mu, dt, _p(sigma), _p(E)),
            "dynamic_step_lines")
     return pos, sigma, E
+
+
+def eval_am(g, sigma, prims, prim_of, prim_after, pts):
+    """Adaptive Modelling (Sec. 3.3): element sums over the copies with ring index
+    max(|k1|, |k2|) <= prim_after, primitive sums with the primitives' average charge
+    densities over the others (readings stated in nebem_oracle.c)."""
+    el, pe = _rec(g.elements)
+    pr, pp = _rec(np.atleast_1d(prims)) if len(prims) else (None, None)
+    po = np.ascontiguousarray(prim_of, dtype=np.int32)
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    phi, E = np.empty(pts.shape[0]), np.empty((pts.shape[0], 3))
+    lat = _lat(g)
+    _check(lib().or_eval_am(pe, el.shape[0], _p(sigma), _p(lat), g.img_lo, g.img_hi, pp, len(prims),
+                            po.ctypes.data_as(C.POINTER(C.c_int32)), prim_after, _p(pts), pts.shape[0], _p(phi),
+                            _p(E)), "eval_am")
+    return phi, E

@@ -62,7 +62,7 @@ int build_element(const nebem_element& r, const nebem_options& opt, Elem& e, dou
                   std::string& why) {
     std::memset(&e, 0, sizeof(e));
     std::memset(&fn, 0, sizeof(fn));
-    if (r.kind != NEBEM_RECT && r.kind != NEBEM_TRI) {
+    if (r.kind != NEBEM_RECT && r.kind != NEBEM_TRI && r.kind != NEBEM_QUAD) {
         why = "unknown element kind";
         return NEBEM_INVALID_ARG;
     }
@@ -70,7 +70,7 @@ int build_element(const nebem_element& r, const nebem_options& opt, Elem& e, dou
         why = "unknown boundary-condition type";
         return NEBEM_INVALID_ARG;
     }
-    const int nv = (r.kind == NEBEM_RECT) ? 4 : 3;
+    const int nv = (r.kind == NEBEM_TRI) ? 3 : 4;
     for (int v = 0; v < nv; ++v)
         for (int k = 0; k < 3; ++k)
             if (!std::isfinite(r.v[v][k])) {
@@ -93,7 +93,19 @@ int build_element(const nebem_element& r, const nebem_options& opt, Elem& e, dou
         e.ey[k] = n[k] / ln;
     }
     cross3(e.ey, e.ex, e.ez);
-    if (nv == 4) {
+    if (r.kind == NEBEM_QUAD) {
+        double e3[3], size = 0.0;
+        sub3(r.v[3], r.v[0], e3);
+        for (int v = 1; v < 4; ++v) {
+            double d[3];
+            sub3(r.v[v], r.v[0], d);
+            size = std::fmax(size, std::sqrt(dot3(d, d)));
+        }
+        if (std::fabs(dot3(e3, e.ey)) > 1e-9 * size) {
+            why = "quadrilateral is not planar";
+            return NEBEM_DEGENERATE_ELEMENT;
+        }
+    } else if (nv == 4) {
         double e3[3], chk[3];
         sub3(r.v[3], r.v[0], e3);
         const double l3 = std::sqrt(dot3(e3, e3));
@@ -128,10 +140,27 @@ int build_element(const nebem_element& r, const nebem_options& opt, Elem& e, dou
         const double vx = e.qx[f + 2] - e.qx[0], vz = e.qz[f + 2] - e.qz[0];
         e.twoA[f] = ux * vz - uz * vx;
     }
-    for (int k = 0; k < 3; ++k) {
-        double s = 0.0;
-        for (int v = 0; v < nv; ++v) s += r.v[v][k];
-        e.c[k] = s / nv;
+    if (r.kind == NEBEM_QUAD) {
+        // every corner turns counter-clockwise in the local (x, z) frame
+        for (int v = 0; v < 4; ++v) {
+            const int a = v, b = (v + 1) % 4, c = (v + 2) % 4;
+            const double turn = (e.qx[b] - e.qx[a]) * (e.qz[c] - e.qz[b]) - (e.qz[b] - e.qz[a]) * (e.qx[c] - e.qx[b]);
+            if (!(turn > 0.0)) {
+                why = "quadrilateral is not convex";
+                return NEBEM_DEGENERATE_ELEMENT;
+            }
+        }
+        // area centroid of the fan triangles (v0, v1, v2) and (v0, v2, v3)
+        const double A1 = 0.5 * e.twoA[0], A2 = 0.5 * e.twoA[1];
+        for (int k = 0; k < 3; ++k)
+            e.c[k] = (A1 * (r.v[0][k] + r.v[1][k] + r.v[2][k]) / 3.0 + A2 * (r.v[0][k] + r.v[2][k] + r.v[3][k]) / 3.0) /
+                     (A1 + A2);
+    } else {
+        for (int k = 0; k < 3; ++k) {
+            double s = 0.0;
+            for (int v = 0; v < nv; ++v) s += r.v[v][k];
+            e.c[k] = s / nv;
+        }
     }
     double rho = 0.0;
     for (int v = 0; v < nv; ++v) {
@@ -149,7 +178,9 @@ int build_element(const nebem_element& r, const nebem_options& opt, Elem& e, dou
         diag = (r.eps_a + r.eps_b) / (2.0 * kEps0 * (r.eps_b - r.eps_a));
     }
     // FP32 far-field Gauss nodes as offsets from the centroid, weights x area.
-    const double area = (nv == 4) ? e.twoA[0] : 0.5 * e.twoA[0];
+    const double area = (r.kind == NEBEM_RECT) ? e.twoA[0]
+                        : (r.kind == NEBEM_QUAD) ? 0.5 * (e.twoA[0] + e.twoA[1])
+                                                 : 0.5 * e.twoA[0];
     auto put = [&](float4& dst, const double* g, double wt) {
         double d[3];
         sub3(g, e.c, d);
@@ -160,17 +191,26 @@ int build_element(const nebem_element& r, const nebem_options& opt, Elem& e, dou
     };
     int n_a = 0;
     if (nv == 4) {
-        double e3[3];
+        double e3[3], tw[3];
         sub3(r.v[3], r.v[0], e3);
+        for (int k = 0; k < 3; ++k) tw[k] = (r.kind == NEBEM_RECT) ? 0.0 : r.v[2][k] - r.v[1][k] - e3[k];
+        // tensor Gauss-Legendre on the bilinear map x(s, t) = v0 + s e1 + t e3 + s t tw,
+        // weight w_s w_t |x_s x x_t| (the area for a rectangle)
         auto tensor = [&](int m, float4* dst) {
             double x[16], w[16];
             gauss_legendre01(m, x, w);
             int cnt = 0;
             for (int a = 0; a < m; ++a)
                 for (int b = 0; b < m; ++b) {
-                    double g[3];
-                    for (int k = 0; k < 3; ++k) g[k] = r.v[0][k] + x[a] * e1[k] + x[b] * e3[k];
-                    put(dst[cnt++], g, w[a] * w[b]);
+                    double g[3], xs[3], xt[3], jn[3];
+                    for (int k = 0; k < 3; ++k) {
+                        g[k] = r.v[0][k] + x[a] * e1[k] + x[b] * e3[k] + x[a] * x[b] * tw[k];
+                        xs[k] = e1[k] + x[b] * tw[k];
+                        xt[k] = e3[k] + x[a] * tw[k];
+                    }
+                    cross3(xs, xt, jn);
+                    const double jac = (r.kind == NEBEM_RECT) ? area : std::sqrt(dot3(jn, jn));
+                    put(dst[cnt++], g, w[a] * w[b] * jac / area);
                 }
             return cnt;
         };

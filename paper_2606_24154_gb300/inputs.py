@@ -44,7 +44,7 @@ ELEMENT_DTYPE = np.dtype(
 )
 assert ELEMENT_DTYPE.itemsize == 128
 
-KIND_RECT, KIND_TRI = 0, 1
+KIND_RECT, KIND_TRI, KIND_QUAD = 0, 1, 2
 BC_CONDUCTOR, BC_DIELECTRIC = 0, 1
 
 E_CHARGE = 1.602176634e-19  # C (exact, SI 2019)
@@ -67,6 +67,10 @@ class Geometry:
     box: tuple[tuple[float, float], ...] | None = None
     xy_offset: tuple[float, float] = (0.0, 0.0)
     solids: list = field(default_factory=list)  # (kind, params) for the carrier resampler
+    # Primitives (flat polygons the elements tile, for Adaptive Modelling): records of
+    # ELEMENT_DTYPE and the primitive of every element (-1: none).
+    primitives: np.ndarray | None = None
+    prim_of: np.ndarray | None = None
 
     @property
     def n(self) -> int:
@@ -99,21 +103,42 @@ def _put(rec, kind, verts, bc, cond, eps_a=1.0, eps_b=1.0):
 class _Builder:
     def __init__(self):
         self.rows = []
+        self.prims = []   # (kind, verts) of every primitive
+        self.prim_of = []
+        self.cur = -1
+
+    def _add(self, row):
+        self.rows.append(row)
+        self.prim_of.append(self.cur)
 
     def rect(self, v0, v1, v2, v3, bc=BC_CONDUCTOR, cond=0, eps_a=1.0, eps_b=1.0):
-        self.rows.append((KIND_RECT, np.array([v0, v1, v2, v3], float), bc, cond, eps_a, eps_b))
+        self._add((KIND_RECT, np.array([v0, v1, v2, v3], float), bc, cond, eps_a, eps_b))
 
     def tri(self, v0, v1, v2, bc=BC_CONDUCTOR, cond=0, eps_a=1.0, eps_b=1.0):
-        self.rows.append((KIND_TRI, np.array([v0, v1, v2], float), bc, cond, eps_a, eps_b))
+        self._add((KIND_TRI, np.array([v0, v1, v2], float), bc, cond, eps_a, eps_b))
 
-    def extend(self, other: "_Builder"):
-        self.rows.extend(other.rows)
+    def quad(self, v0, v1, v2, v3, bc=BC_CONDUCTOR, cond=0, eps_a=1.0, eps_b=1.0):
+        self._add((KIND_QUAD, np.array([v0, v1, v2, v3], float), bc, cond, eps_a, eps_b))
+
+    def primitive(self, kind, verts):
+        """Elements added from now until end_primitive() tile this flat polygon."""
+        self.prims.append((kind, np.array(verts, float)))
+        self.cur = len(self.prims) - 1
+
+    def end_primitive(self):
+        self.cur = -1
 
     def build(self) -> np.ndarray:
         out = _records(len(self.rows))
         for i, (kind, verts, bc, cond, ea, eb) in enumerate(self.rows):
             _put(out[i], kind, verts, bc, cond, ea, eb)
         return out
+
+    def build_primitives(self):
+        out = _records(len(self.prims))
+        for i, (kind, verts) in enumerate(self.prims):
+            _put(out[i], kind, verts, BC_CONDUCTOR, 0)
+        return out, np.array(self.prim_of, dtype=np.int32)
 
 
 # --------------------------------------------------------------------------- cube
@@ -130,19 +155,23 @@ def cube(edge: float = 0.01, n_per_edge: int = 8, voltage: float = 1.0) -> Geome
     for a in range(3):
         u_ax, w_ax = (a + 1) % 3, (a + 2) % 3
         for sgn in (+1.0, -1.0):
+            def P(ui, wj):
+                p = [0.0, 0.0, 0.0]
+                p[a] = sgn * h
+                p[u_ax] = s[ui]
+                p[w_ax] = s[wj]
+                return p
+
+            m = n_per_edge
+            b.primitive(KIND_RECT, [P(0, 0), P(m, 0), P(m, m), P(0, m)] if sgn > 0
+                        else [P(0, 0), P(0, m), P(m, m), P(m, 0)])
             for i in range(n_per_edge):
                 for j in range(n_per_edge):
-                    def P(ui, wj):
-                        p = [0.0, 0.0, 0.0]
-                        p[a] = sgn * h
-                        p[u_ax] = s[ui]
-                        p[w_ax] = s[wj]
-                        return p
-
                     if sgn > 0:
                         b.rect(P(i, j), P(i + 1, j), P(i + 1, j + 1), P(i, j + 1))
                     else:
                         b.rect(P(i, j), P(i, j + 1), P(i + 1, j + 1), P(i + 1, j))
+            b.end_primitive()
     g = Geometry(
         name=f"cube_a{edge:g}_n{n_per_edge}",
         elements=b.build(),
@@ -150,6 +179,7 @@ def cube(edge: float = 0.01, n_per_edge: int = 8, voltage: float = 1.0) -> Geome
         box=((-2 * edge, 2 * edge),) * 3,
     )
     g.solids = [("box", (-h, h, -h, h, -h, h))]
+    g.primitives, g.prim_of = b.build_primitives()
     return g
 
 
@@ -187,11 +217,15 @@ def _annulus_to_hex(b: _Builder, z, r_in, pitch, n_phi, n_r, grade, up, bc, cond
         s = (grade ** np.arange(n_r + 1) - 1.0) / (grade ** n_r - 1.0)
     cx, cy = center
     for j in range(n_phi):
-        for i in range(n_r):
-            def P(ii, jj):
-                r = r_in + (R[jj] - r_in) * s[ii]
-                return [cx + r * math.cos(phis[jj]), cy + r * math.sin(phis[jj]), z]
+        def P(ii, jj):
+            r = r_in + (R[jj] - r_in) * s[ii]
+            return [cx + r * math.cos(phis[jj]), cy + r * math.sin(phis[jj]), z]
 
+        # the sector between two rays is a flat convex quadrilateral (hexagon corners lie
+        # on rays), tiled by its 2 n_r triangles
+        q = [P(0, j), P(n_r, j), P(n_r, j + 1), P(0, j + 1)]
+        b.primitive(KIND_QUAD, q if up else [q[0], q[3], q[2], q[1]])
+        for i in range(n_r):
             a, bb, c, d = P(i, j), P(i + 1, j), P(i + 1, j + 1), P(i, j + 1)
             if up:  # counter-clockwise seen from +z
                 b.tri(a, bb, c, bc, cond, eps_a, eps_b)
@@ -199,6 +233,7 @@ def _annulus_to_hex(b: _Builder, z, r_in, pitch, n_phi, n_r, grade, up, bc, cond
             else:
                 b.tri(a, c, bb, bc, cond, eps_a, eps_b)
                 b.tri(a, d, c, bc, cond, eps_a, eps_b)
+        b.end_primitive()
 
 
 def _annulus(b: _Builder, z, r_in, r_out, n_phi, n_rad, up, bc, cond, eps_a=1.0, eps_b=1.0,
@@ -208,10 +243,12 @@ def _annulus(b: _Builder, z, r_in, r_out, n_phi, n_rad, up, bc, cond, eps_a=1.0,
     rs = np.linspace(r_in, r_out, n_rad + 1)
     cx, cy = center
     for j in range(n_phi):
-        for i in range(n_rad):
-            def P(ii, jj):
-                return [cx + rs[ii] * math.cos(phis[jj]), cy + rs[ii] * math.sin(phis[jj]), z]
+        def P(ii, jj):
+            return [cx + rs[ii] * math.cos(phis[jj]), cy + rs[ii] * math.sin(phis[jj]), z]
 
+        q = [P(0, j), P(n_rad, j), P(n_rad, j + 1), P(0, j + 1)]
+        b.primitive(KIND_QUAD, q if up else [q[0], q[3], q[2], q[1]])
+        for i in range(n_rad):
             a, bb, c, d = P(i, j), P(i + 1, j), P(i + 1, j + 1), P(i, j + 1)
             if up:
                 b.tri(a, bb, c, bc, cond, eps_a, eps_b)
@@ -219,6 +256,7 @@ def _annulus(b: _Builder, z, r_in, r_out, n_phi, n_rad, up, bc, cond, eps_a=1.0,
             else:
                 b.tri(a, c, bb, bc, cond, eps_a, eps_b)
                 b.tri(a, d, c, bc, cond, eps_a, eps_b)
+        b.end_primitive()
 
 
 def _hole_wall(b: _Builder, r, z0, z1, n_phi, n_z, bc, cond, eps_a=1.0, eps_b=1.0,
@@ -228,12 +266,14 @@ def _hole_wall(b: _Builder, r, z0, z1, n_phi, n_z, bc, cond, eps_a=1.0, eps_b=1.
     zs = np.linspace(z0, z1, n_z + 1)
     cx, cy = center
     for j in range(n_phi):
+        p0 = [cx + r * math.cos(phis[j]), cy + r * math.sin(phis[j])]
+        p1 = [cx + r * math.cos(phis[j + 1]), cy + r * math.sin(phis[j + 1])]
+        b.primitive(KIND_RECT, [[*p0, zs[0]], [*p1, zs[0]], [*p1, zs[-1]], [*p0, zs[-1]]])
         for k in range(n_z):
-            p0 = [cx + r * math.cos(phis[j]), cy + r * math.sin(phis[j])]
-            p1 = [cx + r * math.cos(phis[j + 1]), cy + r * math.sin(phis[j + 1])]
             # v0 -> v1 along the facet chord, v1 -> v2 along +z: (v1-v0) x (v2-v0) points inwards.
             b.rect([*p0, zs[k]], [*p1, zs[k]], [*p1, zs[k + 1]], [*p0, zs[k + 1]], bc, cond,
                    eps_a, eps_b)
+        b.end_primitive()
 
 
 def _hex_plane(b: _Builder, z, pitch, n_sub, up, cond, center=(0.0, 0.0)):
@@ -244,6 +284,8 @@ def _hex_plane(b: _Builder, z, pitch, n_sub, up, cond, center=(0.0, 0.0)):
               cy + rv * math.sin(math.pi / 6 + k * math.pi / 3)) for k in range(7)]
     for k in range(6):
         A = np.array([cx, cy]); B = np.array(verts[k]); C = np.array(verts[k + 1])
+        pa, pb, pc = [A[0], A[1], z], [B[0], B[1], z], [C[0], C[1], z]
+        b.primitive(KIND_TRI, [pa, pb, pc] if up else [pa, pc, pb])
         # barycentric sub-triangulation
         def node(i, j):
             p = A + (B - A) * (i / n_sub) + (C - A) * (j / n_sub)
@@ -261,6 +303,7 @@ def _hex_plane(b: _Builder, z, pitch, n_sub, up, cond, center=(0.0, 0.0)):
                         b.tri(*t2, BC_CONDUCTOR, cond)
                     else:
                         b.tri(t2[0], t2[2], t2[1], BC_CONDUCTOR, cond)
+        b.end_primitive()
 
 
 @dataclass
@@ -335,6 +378,7 @@ def thgem(spec: PlateSpec | None = None, gap: float = 3.0e-3, n_plane: int = 9,
         z_range=(-(zt + gap), zt + gap),
     )
     g.solids = solids
+    g.primitives, g.prim_of = b.build_primitives()
     return g
 
 
@@ -365,6 +409,7 @@ def double_thgem(spec: PlateSpec | None = None, transfer: float = 2.0e-3, gap: f
         z_range=(-ztop, ztop),
     )
     g.solids = solids
+    g.primitives, g.prim_of = b.build_primitives()
     return g
 
 

@@ -45,10 +45,55 @@ def random_tri(gen, scale=1e-3):
     return tri_el(*v)
 
 
+def quad_el(v0, v1, v2, v3):
+    el = np.zeros(1, I.ELEMENT_DTYPE)
+    el["kind"] = I.KIND_QUAD
+    el["v"][0] = [v0, v1, v2, v3]
+    return el
+
+
+def random_quad(gen, scale=1e-3):
+    """A planar convex quadrilateral (corners at jittered quarter angles around a centre)."""
+    c = gen.normal(size=3) * scale
+    u = gen.normal(size=3); u /= np.linalg.norm(u)
+    w = np.cross(u, gen.normal(size=3)); w /= np.linalg.norm(w)
+    while True:
+        ang = np.arange(4) * 0.5 * math.pi + gen.uniform(-0.35, 0.35, 4)
+        rad = scale * gen.uniform(0.6, 1.4, 4)
+        q = np.stack([rad * np.cos(ang), rad * np.sin(ang)], 1)
+        turns = []
+        for k in range(4):
+            a, b = q[(k + 1) % 4] - q[k], q[(k + 2) % 4] - q[(k + 1) % 4]
+            turns.append(a[0] * b[1] - a[1] * b[0])
+        if min(turns) > 0.05 * scale * scale:
+            break
+    return quad_el(*[c + a * u + b * w for a, b in q])
+
+
+def _tri_area(a, b, c):
+    return 0.5 * np.linalg.norm(np.cross(b - a, c - a))
+
+
+def _area(el):
+    v = el["v"][0]
+    k = el["kind"][0]
+    if k == I.KIND_TRI:
+        return _tri_area(*v[:3])
+    return _tri_area(v[0], v[1], v[2]) + _tri_area(v[0], v[2], v[3])
+
+
+def random_shape(gen, shape, scale=1e-3):
+    return {"rect": random_rect, "tri": random_tri, "quad": random_quad}[shape](gen, scale)
+
+
 def quad_influence(el, P, eps=1e-13):
     """Adaptive 2-D quadrature of Phi' and E' over the parametrised element."""
     v = el["v"][0]
     P = np.asarray(P, float)
+    if el["kind"][0] == I.KIND_QUAD:  # the two triangles of the quadrilateral
+        p1, E1 = quad_influence(tri_el(v[0], v[1], v[2]), P, eps)
+        p2, E2 = quad_influence(tri_el(v[0], v[2], v[3]), P, eps)
+        return p1 + p2, E1 + E2
     if el["kind"][0] == I.KIND_RECT:
         e1, e2 = v[1] - v[0], v[3] - v[0]
         jac = np.linalg.norm(np.cross(e1, e2))
@@ -77,17 +122,20 @@ def _normal(el):
 
 def _centroid(el):
     v = el["v"][0]
+    if el["kind"][0] == I.KIND_QUAD:
+        a1, a2 = _tri_area(v[0], v[1], v[2]), _tri_area(v[0], v[2], v[3])
+        return (a1 * v[:3].mean(0) + a2 * v[[0, 2, 3]].mean(0)) / (a1 + a2)
     return v[:4].mean(0) if el["kind"][0] == I.KIND_RECT else v[:3].mean(0)
 
 
-@pytest.mark.parametrize("shape", ["rect", "tri"])
+@pytest.mark.parametrize("shape", ["rect", "tri", "quad"])
 def test_closed_form_vs_quadrature(shape):
     gen = np.random.default_rng(7)
     worst = 0.0
     for trial in range(6):
-        el = random_rect(gen) if shape == "rect" else random_tri(gen)
+        el = random_shape(gen, shape)
         c, n = _centroid(el), _normal(el)
-        size = math.sqrt(np.linalg.norm(np.cross(el["v"][0][1] - el["v"][0][0], el["v"][0][2] - el["v"][0][0])))
+        size = math.sqrt(_area(el))
         for dist, h in [(0.3, 0.2), (1.0, 0.5), (3.0, 1.0), (0.2, 0.05), (2.0, -0.7)]:
             dirn = gen.normal(size=3); dirn -= (dirn @ n) * n; dirn /= np.linalg.norm(dirn)
             P = c + dist * size * dirn + h * size * n
@@ -124,6 +172,38 @@ def test_rect_equals_two_triangles():
         pp, Ep = O.influence(el, P, poly=True)
         assert np.abs(pr - pp).max() <= 1e-12 * scale_p
         assert np.abs(Er - Ep).max() <= 1e-11 * max(1.0, np.abs(Er).max())
+
+
+def test_quad_equals_two_triangles_and_rect():
+    """A quadrilateral's edge formula equals the sum of its two triangles, and a
+    rectangle given as a quadrilateral equals the rectangle's corner antiderivative."""
+    gen = np.random.default_rng(23)
+    for _ in range(4):
+        q = random_quad(gen)
+        v = q["v"][0]
+        size = math.sqrt(_area(q))
+        P = _centroid(q) + size * gen.normal(size=(6, 3))
+        phi, E = O.influence(q, P)
+        p1, E1 = O.influence(tri_el(v[0], v[1], v[2]), P)
+        p2, E2 = O.influence(tri_el(v[0], v[2], v[3]), P)
+        assert np.abs(phi - (p1 + p2)).max() <= 1e-13 * np.abs(phi).max()
+        assert np.abs(E - (E1 + E2)).max() <= 1e-12 * np.abs(E).max()
+    r = random_rect(gen)
+    rq = quad_el(*r["v"][0])
+    P = _centroid(r) + 1e-3 * gen.normal(size=(6, 3))
+    pr, Er = O.influence(r, P)
+    pq, Eq = O.influence(rq, P)
+    assert np.abs(pr - pq).max() <= 1e-13 * np.abs(pr).max() and np.abs(Er - Eq).max() <= 1e-12 * np.abs(Er).max()
+    # the oracle's collocation point of a quadrilateral is its area centroid
+    c, _, area = O.centroids(I.Geometry(name="q", elements=q, voltages=np.array([1.0])))
+    assert np.allclose(c[0], _centroid(q), rtol=0, atol=1e-15) and abs(area[0] - _area(q)) <= 1e-15 * _area(q)
+    # non-planar and non-convex quadrilaterals are rejected
+    bent = q.copy(); bent["v"][0][3] += 1e-4 * _normal(q)
+    with pytest.raises(ValueError):
+        O.influence(bent, P)
+    dart = quad_el(v[0], v[1], v[0] + 0.1 * (v[2] - v[0]), v[3])
+    with pytest.raises(ValueError):
+        O.influence(dart, P)
 
 
 def test_square_textbook_values():
@@ -174,12 +254,11 @@ def test_self_term_principal_value_in_fill():
     assert np.allclose(np.diag(K), diag, rtol=1e-14)
 
 
-@pytest.mark.parametrize("shape", ["rect", "tri"])
+@pytest.mark.parametrize("shape", ["rect", "tri", "quad"])
 def test_far_field_limit(shape):
     gen = np.random.default_rng(13)
-    el = random_rect(gen) if shape == "rect" else random_tri(gen)
-    v = el["v"][0]
-    A = 0.5 * np.linalg.norm(np.cross(v[1] - v[0], v[2] - v[0])) * (2 if shape == "rect" else 1)
+    el = random_shape(gen, shape)
+    A = _area(el)
     c = _centroid(el)
     size = math.sqrt(A)
     errs = []
@@ -194,10 +273,10 @@ def test_far_field_limit(shape):
     assert errs[0][1] < 5e-3 and errs[1][1] < 5e-5 and errs[2][1] < 5e-7
 
 
-@pytest.mark.parametrize("shape", ["rect", "tri"])
+@pytest.mark.parametrize("shape", ["rect", "tri", "quad"])
 def test_field_is_minus_gradient(shape):
     gen = np.random.default_rng(17)
-    el = random_rect(gen) if shape == "rect" else random_tri(gen)
+    el = random_shape(gen, shape)
     c, n = _centroid(el), _normal(el)
     size = 1e-3
     for P in [c + size * gen.normal(size=3) for _ in range(5)] + [c + 0.01 * size * n + 0.1 * size * gen.normal(size=3)]:
@@ -229,12 +308,12 @@ def _box_flux(field_fn, lo, hi, m=40):
     return total
 
 
-@pytest.mark.parametrize("shape", ["rect", "tri"])
+@pytest.mark.parametrize("shape", ["rect", "tri", "quad"])
 def test_gauss_law_single_element(shape):
     gen = np.random.default_rng(19)
-    el = random_rect(gen, 1.0) if shape == "rect" else random_tri(gen, 1.0)
-    v = el["v"][0][: (4 if shape == "rect" else 3)]
-    A = np.linalg.norm(np.cross(v[1] - v[0], v[2] - v[0])) * (1.0 if shape == "rect" else 0.5)
+    el = random_shape(gen, shape, 1.0)
+    v = el["v"][0][: (3 if shape == "tri" else 4)]
+    A = _area(el)
     lo, hi = v.min(0) - 1.0, v.max(0) + 1.0
     flux = _box_flux(lambda P: O.influence(el, P)[1], lo, hi)
     assert abs(flux - 4 * math.pi * A) < 1e-9 * 4 * math.pi * A
@@ -626,3 +705,79 @@ def test_dynamic_step_lines_satisfies_bc():
     _, El = O.line_charge(L, pos)
     assert np.abs(E - (Ec + El)).max() <= 1e-12 * np.abs(E).max()
     assert np.abs(pos1 - (pos + np.sign(q)[:, None] * 1e-4 * E * 1e-9)).max() <= 4e-16 * np.abs(pos).max()
+
+
+# --- Adaptive Modelling (Sec. 3.3; PrimAfter) ----------------------------------------
+
+def _am_geometry(lo=-3, hi=3):
+    g = I.thgem(I.PlateSpec(n_phi=24, n_r=3, n_zc=1, n_zf=4), n_plane=3)
+    g.img_lo, g.img_hi = lo, hi
+    return g
+
+
+def _smooth_sigma(g):
+    c, _, _ = O.centroids(g)
+    return 1e-9 * (1.0 + 0.5 * np.sin(7e3 * c[:, 0]) * np.cos(5e3 * c[:, 1]) + 3e2 * c[:, 2])
+
+
+def test_am_exact_for_uniform_primitive_charge():
+    """With the charge density uniform over every primitive, a primitive's influence is
+    the sum of its elements' (additivity of the surface integral), so the adaptive
+    evaluation equals the full one for any PrimAfter."""
+    g = _am_geometry()
+    rough = _smooth_sigma(g)
+    _, _, area = O.centroids(g)
+    # per-primitive uniform density (the primitive average of the rough one)
+    pa = np.bincount(g.prim_of, weights=area)
+    sbar = np.bincount(g.prim_of, weights=rough * area) / pa
+    sigma = sbar[g.prim_of]
+    pts = I.cell_points(g, 40, I.rng(0, 60))
+    full_phi, full_E = O.eval_points(g, sigma, pts)
+    for pa_ in (0, 1, 2):
+        phi, E = O.eval_am(g, sigma, g.primitives, g.prim_of, pa_, pts)
+        assert np.abs(phi - full_phi).max() <= 1e-12 * np.abs(full_phi).max()
+        assert np.abs(E - full_E).max() <= 1e-11 * np.abs(full_E).max()
+
+
+def test_am_limits_and_trend():
+    """PrimAfter < 0 or beyond the last ring is the plain evaluation; for a density that
+    varies inside the primitives the error falls as PrimAfter grows (the trend of the
+    paper's PrimAfter table)."""
+    g = _am_geometry()
+    sigma = _smooth_sigma(g)
+    pts = I.cell_points(g, 40, I.rng(0, 61))
+    full_phi, full_E = O.eval_points(g, sigma, pts)
+    for pa_ in (-1, 3, 7):
+        phi, E = O.eval_am(g, sigma, g.primitives, g.prim_of, pa_, pts)
+        assert np.abs(phi - full_phi).max() <= 1e-13 * np.abs(full_phi).max()
+        assert np.abs(E - full_E).max() <= 1e-12 * np.abs(full_E).max()
+    errs = []
+    for pa_ in (0, 1, 2):
+        phi, E = O.eval_am(g, sigma, g.primitives, g.prim_of, pa_, pts)
+        errs.append(max(np.abs(phi - full_phi).max() / np.abs(full_phi).max(),
+                        np.abs(E - full_E).max() / np.abs(full_E).max()))
+    assert errs[0] > errs[1] > errs[2] > 0.0
+    assert errs[2] < 1e-3
+
+
+def test_am_unassigned_elements_and_bad_tiling():
+    g = _am_geometry(-2, 2)
+    sigma = _smooth_sigma(g)
+    pts = I.cell_points(g, 10, I.rng(0, 62))
+    # an element without a primitive stands for itself in every copy: dropping the
+    # primitives of a set of elements moves the result towards the full evaluation
+    po = g.prim_of.copy()
+    po[po < 40] = -1
+    keep = np.unique(po[po >= 0])
+    remap = -np.ones(len(g.primitives), dtype=np.int32)
+    remap[keep] = np.arange(len(keep))
+    po2 = np.where(po >= 0, remap[np.maximum(po, 0)], -1).astype(np.int32)
+    full_phi, _ = O.eval_points(g, sigma, pts)
+    a_phi, _ = O.eval_am(g, sigma, g.primitives, g.prim_of, 0, pts)
+    b_phi, _ = O.eval_am(g, sigma, g.primitives[keep], po2, 0, pts)
+    assert np.abs(b_phi - full_phi).max() < np.abs(a_phi - full_phi).max()
+    # elements that do not tile their primitive are rejected
+    bad = g.prim_of.copy()
+    bad[0] = bad[1] if bad[1] != bad[0] else bad[0] + 1
+    with pytest.raises(ValueError):
+        O.eval_am(g, sigma, g.primitives, bad, 0, pts)
