@@ -239,6 +239,27 @@ int nebem_space_charge_lines(nebem_ctx *ctx, const double *voxel, int64_t *n_lin
 int nebem_get_lines(nebem_ctx *ctx, double *start, double *stop, double *lambda, int64_t capacity,
                     int64_t *n_lines);
 
+/* Adaptive Modelling (Sec. 3.3; the PrimAfter parameter of the timing table in Sec. 5.3.1):
+ * evaluate distant periodic copies with whole primitives carrying the average charge
+ * density of their elements instead of the elements themselves.
+ *   prims[n_prim]   flat polygons (kind NEBEM_RECT, NEBEM_TRI or NEBEM_QUAD; bc, conductor
+ *                   and eps are ignored, reserved must be 0) that the elements tile.
+ *   prim_of[n]      primitive of every element of the geometry, or -1 for an element that
+ *                   belongs to none (it stands for itself in every copy).  The elements of
+ *                   a primitive must lie in its plane (1e-9 of its radius) and their areas
+ *                   must add up to its area (1e-9 relative).
+ *   prim_after      copy k = (k1, k2) is distant when max(|k1|, |k2|) > prim_after;
+ *                   prim_after < 0 switches Adaptive Modelling off.
+ * Primitive p carries sigma_p = sum_{j in p} sigma_j A_j / A_p (its total charge over its
+ * area), recomputed on the device whenever sigma changes.  Applies to every evaluation at
+ * points (nebem_eval, nebem_eval_device, FastVolume nodes, the carriers of nebem_step);
+ * not to the matrix fill nor to the server (nebem_server_*), which evaluate all copies
+ * element by element.  Copied at the call; set_geometry clears it.
+ * Errors: NEBEM_BAD_STATE (no geometry), NEBEM_INVALID_ARG (bad ids, tiling, planes),
+ * NEBEM_DEGENERATE_ELEMENT (a degenerate primitive). */
+int nebem_set_primitives(nebem_ctx *ctx, const nebem_element *prims, int32_t n_prim, const int32_t *prim_of,
+                         int32_t prim_after);
+
 /* Direct space-charge sum at points (Alg. 2, all pairs, softened):
  * phi_t = ke sum_{c != self(t)} q_c / sqrt(r^2 + s^2), E_t = ke sum q_c (x_t - x_c) /
  * (r^2 + s^2)^{3/2}.  exclude_self != 0 means target t is carrier t (n must equal the

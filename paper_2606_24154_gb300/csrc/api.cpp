@@ -54,8 +54,11 @@ Ctx::~Ctx() {
     for (DevBuf* b : {&d_el, &d_far, &d_diag, &d_sigma, &d_K, &d_LU64, &d_LU32, &d_piv64, &d_piv32, &d_work, &d_b,
                       &d_x, &d_r, &d_r32, &d_small, &d_pts, &d_phi, &d_E, &d_car, &d_q, &d_car2, &d_sc_tgt,
                       &d_sc_phi, &d_sc_E, &d_scratch, &d_cjk, &d_cell_start, &d_cell_items, &d_fv_ax, &d_fv_ay, &d_fv_az, &d_fv_phi,
-                      &d_fv_E, &d_vkeys, &d_vflags, &d_vbsum, &d_vpartial, &d_vgrid, &d_lines, &d_linesf})
+                      &d_fv_E, &d_vkeys, &d_vflags, &d_vbsum, &d_vpartial, &d_vgrid, &d_lines, &d_linesf,
+                      &d_am_start, &d_am_items, &d_am_elarea, &d_am_parea, &d_am_tmp})
         b->release();
+    am_near.release_all();
+    am_far.release_all();
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     if (stream) cudaStreamDestroy(stream);
@@ -186,6 +189,10 @@ int nebem_set_geometry(nebem_ctx* ctx, const nebem_element* el, int64_t n, const
     c->bc_set = false;
     c->n_car = 0;
     c->sc_lines = false;
+    c->am_on = false;
+    c->am_prim_after = -1;
+    c->am_near.release_all();
+    c->am_far.release_all();
     CK(c->d_el.ensure(sizeof(Elem) * n));
     CK(c->d_far.ensure(sizeof(FarNodes) * n));
     CK(c->d_diag.ensure(sizeof(double) * n));
@@ -204,6 +211,8 @@ int nebem_set_geometry(nebem_ctx* ctx, const nebem_element* el, int64_t n, const
     CK(cudaStreamSynchronize(c->stream));
     c->grid = grid;
     c->img = img;
+    c->img_lo = lattice ? img_lo : 0;
+    c->img_hi = lattice ? img_hi : 0;
     c->h_bc = std::move(h_bc);
     c->h_cond = std::move(h_cond);
     c->h_el = std::move(h_el);

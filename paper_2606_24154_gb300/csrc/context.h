@@ -21,6 +21,19 @@ struct DevBuf {
     }
 };
 
+// An element table with an image set, in the form the evaluation kernels take.  The
+// pointers are views (the context's own tables, or the own_* buffers).
+struct EvalSet {
+    int64_t n = 0;
+    ImageTable img{};
+    NearGrid grid{};
+    const Elem* el = nullptr;
+    const FarNodes* far = nullptr;
+    const double* sigma = nullptr;
+    DevBuf own_el, own_far, own_sigma, cjk, cell_start, cell_items;
+    void release_all();
+};
+
 struct Ctx {
     nebem_options opt{};
     int device = 0;
@@ -31,6 +44,7 @@ struct Ctx {
     // geometry
     int64_t n = 0;
     ImageTable img{};
+    int32_t img_lo = 0, img_hi = 0;  // image index range per lattice axis
     std::vector<Elem> h_el;
     std::vector<int32_t> h_bc, h_cond;
     DevBuf d_el, d_far, d_diag;
@@ -48,6 +62,16 @@ struct Ctx {
     DevBuf d_fv_ax, d_fv_ay, d_fv_az, d_fv_phi, d_fv_E;
     int32_t fv_dims[3] = {0, 0, 0};
     int64_t fv_version = -1;
+
+    // Adaptive Modelling: element sums over the near copies (am_near), primitive sums with
+    // average densities over the distant ones (am_far); CSR lists of the elements (with
+    // their areas) whose charge each far entry carries
+    bool am_on = false;
+    int32_t am_prim_after = -1;
+    int64_t am_n_prim = 0;
+    EvalSet am_near, am_far;
+    DevBuf d_am_start, d_am_items, d_am_elarea, d_am_parea, d_am_tmp;
+    int64_t am_sigma_version = -1;
 
     // matrix and factors
     DevBuf d_K, d_LU64, d_LU32, d_piv64, d_piv32, d_work;
@@ -81,6 +105,11 @@ int build_rhs(Ctx* c);
 int solve_with_factors(Ctx* c, int precision, nebem_solve_info* info);
 // elements only (with images)
 int eval_elements(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision, cudaStream_t s);
+// one evaluation set (elements or primitives with their images)
+int eval_set(Ctx* c, const EvalSet& es, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision,
+             cudaStream_t s);
+// am_api.cpp: the adaptive evaluation (near copies by elements, distant ones by primitives)
+int eval_adaptive(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision, cudaStream_t s);
 // elements + known charges (PFAtPoint)
 int eval_points(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision, cudaStream_t s);
 

@@ -176,6 +176,14 @@ cudaError_t launch_line_eval(int precision, const VoxWork& w, const double* tgt,
                              int64_t perm_div, int64_t nt, double soft, int accumulate, double* phi, double* E,
                              cudaStream_t s);
 
+// Adaptive Modelling (am.cu): average density of every far entry f,
+// sbar[f] = sum_{t in [start[f], start[f+1])} sigma[items[t]] * elarea[items[t]] / parea[f],
+// summed in list order; and phi += phi2, E += E2 (either may be NULL).
+cudaError_t launch_prim_sigma(const int32_t* start, const int32_t* items, const double* elarea, const double* parea,
+                              const double* sigma, int64_t nf, double* sbar, cudaStream_t s);
+cudaError_t launch_add_fields(double* phi, double* E, const double* phi2, const double* E2, int64_t n,
+                              cudaStream_t s);
+
 // FastVolume (fastvol.cu)
 cudaError_t launch_grid_nodes(const double* ax, const double* ay, const double* az, int nx, int ny, int nz,
                               double* pts, cudaStream_t s);

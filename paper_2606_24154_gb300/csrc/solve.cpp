@@ -158,14 +158,27 @@ int solve_with_factors(Ctx* c, int precision, nebem_solve_info* info) {
     return 0;
 }
 
+int eval_set(Ctx* c, const EvalSet& es, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision,
+             cudaStream_t s) {
+    if (precision == NEBEM_MIXED) {
+        CK(c->d_scratch.ensure(eval_mixed_scratch_bytes(n)));
+        CK(launch_eval_mixed(es.el, es.far, es.cjk.as<float4>(), es.sigma, es.n, es.img, es.grid,
+                             es.cell_start.as<int32_t>(), es.cell_items.as<int32_t>(), d_pts, n, d_phi, d_E,
+                             c->d_scratch.ptr, s));
+    } else {
+        CK(launch_eval_f64(es.el, es.sigma, es.n, es.img, d_pts, n, d_phi, d_E, s));
+    }
+    return 0;
+}
+
 int eval_elements(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision, cudaStream_t s) {
+    if (c->am_on) return eval_adaptive(c, d_pts, n, d_phi, d_E, precision, s);
     if (precision == NEBEM_MIXED) {
         CK(c->d_scratch.ensure(eval_mixed_scratch_bytes(n)));
         CK(launch_eval_mixed(c->d_el.as<Elem>(), c->d_far.as<FarNodes>(), c->d_cjk.as<float4>(),
                              c->d_sigma.as<double>(), c->n, c->img, c->grid, c->d_cell_start.as<int32_t>(),
                              c->d_cell_items.as<int32_t>(), d_pts, n, d_phi, d_E, c->d_scratch.ptr, s));
-    }
-    else {
+    } else {
         CK(launch_eval_f64(c->d_el.as<Elem>(), c->d_sigma.as<double>(), c->n, c->img, d_pts, n, d_phi, d_E, s));
     }
     return 0;

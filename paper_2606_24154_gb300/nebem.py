@@ -97,6 +97,7 @@ SIGNATURES = {
     "nebem_space_charge": (C.c_int, [_vp, _d, _d, C.c_int64, C.c_double]),
     "nebem_space_charge_eval": (C.c_int, [_vp, _d, C.c_int64, _d, _d, C.c_int32, C.c_int32]),
     "nebem_space_charge_lines": (C.c_int, [_vp, _d, _i64p]),
+    "nebem_set_primitives": (C.c_int, [_vp, _vp, C.c_int32, C.POINTER(C.c_int32), C.c_int32]),
     "nebem_get_lines": (C.c_int, [_vp, _d, _d, _d, C.c_int64, _i64p]),
     "nebem_step": (C.c_int, [_vp, C.c_int32, C.c_double, C.c_double, C.c_int32, _d]),
     "nebem_lu_factor_device": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp]),
@@ -246,6 +247,13 @@ def nebem_space_charge(ctx, pos, q, softening=0.0):
     p = _f64(pos, (-1, 3))
     qq = _f64(q)
     _check(load().nebem_space_charge(ctx, _dp(p), _dp(qq), p.shape[0], softening), "nebem_space_charge")
+
+
+def nebem_set_primitives(ctx, prims, prim_of, prim_after: int):
+    pr = np.ascontiguousarray(prims)
+    po = np.ascontiguousarray(prim_of, dtype=np.int32)
+    _check(load().nebem_set_primitives(ctx, pr.ctypes.data_as(_vp) if len(pr) else None, len(pr),
+                                       po.ctypes.data_as(C.POINTER(C.c_int32)), prim_after), "nebem_set_primitives")
 
 
 def nebem_space_charge_lines(ctx, voxel) -> int:
