@@ -13,7 +13,8 @@
 //   d >= ratio_b rho      FP32 Gauss rule, tier b (16 nodes)
 //   d >= ratio_near rho   FP32 Gauss rule, tier c (36 nodes)
 //   nearer                FP64 closed form (influence.cuh), where ln/atan cancel
-// Quadrature per node: Phi += w / r, E += w (P - x_n) / r^3 with one rsqrt.
+// Quadrature per node: Phi += w / r, E += w (P - x_n) / r^3 with one rsqrt; two nodes at
+// a time in the packed FP32x2 instructions (half the issue slots of scalar FP32).
 //
 // Two kernels: k_eval_far runs every FP32 tier over all (element, image) pairs and skips
 // near pairs; k_eval_near visits only the image centroids in the 27 grid cells around
@@ -60,40 +61,33 @@ __device__ __forceinline__ void split2f(double x, float& hi, float& lo) {
     lo = __double2float_rn(x - (double)hi);
 }
 
-// Tier-0 rule with its four nodes held in registers (loaded once per element).
-__device__ __forceinline__ void nodes4_reg(const float4& q0, const float4& q1, const float4& q2, const float4& q3,
-                                           float dx, float dy, float dz, float& ph, float& ex, float& ey, float& ez) {
-    const float4 q[4] = {q0, q1, q2, q3};
+// NP node pairs of one tier (layout in nb_internal.h: s = centroid - node, so the
+// node-to-point vector is d + s) with the packed FP32x2 instructions: each instruction
+// advances two nodes, lane x the first of a pair and lane y the second.
+template <int NP>
+__device__ __forceinline__ void node_pairs(const float4* __restrict__ nd, float2 dx, float2 dy, float2 dz,
+                                           float2& ph, float2& ex, float2& ey, float2& ez) {
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float rx = dx - q[i].x, ry = dy - q[i].y, rz = dz - q[i].z;
-        const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-        const float ri = rsqrtf(r2);
-        const float wr = q[i].w * ri;
-        const float wr3 = wr * ri * ri;
-        ph += wr;
-        ex = fmaf(wr3, rx, ex);
-        ey = fmaf(wr3, ry, ey);
-        ez = fmaf(wr3, rz, ez);
+    for (int i = 0; i < NP; ++i) {
+        const float4 u = nd[2 * i], v = nd[2 * i + 1];
+        const float2 rx = __fadd2_rn(dx, make_float2(u.x, u.y));
+        const float2 ry = __fadd2_rn(dy, make_float2(u.z, u.w));
+        const float2 rz = __fadd2_rn(dz, make_float2(v.x, v.y));
+        const float2 r2 = __ffma2_rn(rx, rx, __ffma2_rn(ry, ry, __fmul2_rn(rz, rz)));
+        const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+        const float2 wr = __fmul2_rn(make_float2(v.z, v.w), ri);
+        const float2 wr3 = __fmul2_rn(wr, __fmul2_rn(ri, ri));
+        ph = __fadd2_rn(ph, wr);
+        ex = __ffma2_rn(wr3, rx, ex);
+        ey = __ffma2_rn(wr3, ry, ey);
+        ez = __ffma2_rn(wr3, rz, ez);
     }
 }
 
-template <int M>
-__device__ __forceinline__ void nodes_f32(const float4* __restrict__ nd, float dx, float dy, float dz, float& ph,
-                                          float& ex, float& ey, float& ez) {
-#pragma unroll
-    for (int i = 0; i < M; ++i) {
-        const float4 q = nd[i];
-        const float rx = dx - q.x, ry = dy - q.y, rz = dz - q.z;
-        const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-        const float ri = rsqrtf(r2);
-        const float wr = q.w * ri;
-        const float wr3 = wr * ri * ri;
-        ph += wr;
-        ex = fmaf(wr3, rx, ex);
-        ey = fmaf(wr3, ry, ey);
-        ez = fmaf(wr3, rz, ez);
-    }
+// Tier 0 with its two node pairs held in registers (loaded once per element).
+__device__ __forceinline__ void pairs0_reg(const float4 (&q)[2 * kPairs0], float2 dx, float2 dy, float2 dz,
+                                           float2& ph, float2& ex, float2& ey, float2& ez) {
+    node_pairs<kPairs0>(q, dx, dy, dz, ph, ex, ey, ez);
 }
 
 // Raw FP64 sums (phi, E; before the factor ke) of the far pairs of one point over the
@@ -110,8 +104,8 @@ __device__ __forceinline__ Sum4 far_range(const GeomView& g, float phx, float ph
     const double* __restrict__ sigma = g.sigma;
     const int nimg = g.nimg;
     const int tile_el = g.tile_el;
-    __shared__ float4 s_f[kTileMax][kNodes0];
-    __shared__ float4 s_a[kTileMax][kNodesA];
+    __shared__ float4 s_f[kTileMax][2 * kPairs0];
+    __shared__ float4 s_a[kTileMax][2 * kPairsA];
     __shared__ int s_na[kTileMax];
     __shared__ float4 s_hdr[kTileMax];
     __shared__ float s_sig[kTileMax];
@@ -121,10 +115,9 @@ __device__ __forceinline__ Sum4 far_range(const GeomView& g, float phx, float ph
     for (int64_t base = e0; base < e1; base += tile_el) {
         const int cnt = (int)min((int64_t)tile_el, e1 - base);
         __syncthreads();
-        for (int i = threadIdx.x; i < cnt * kNodesA; i += blockDim.x)
-            s_a[i / kNodesA][i % kNodesA] = far[base + i / kNodesA].a[i % kNodesA];
-        for (int i = threadIdx.x; i < cnt * kNodes0; i += blockDim.x)
-            s_f[i / kNodes0][i % kNodes0] = far[base + i / kNodes0].f[i % kNodes0];
+        constexpr int kA = 2 * kPairsA, kF = 2 * kPairs0;
+        for (int i = threadIdx.x; i < cnt * kA; i += blockDim.x) s_a[i / kA][i % kA] = far[base + i / kA].a[i % kA];
+        for (int i = threadIdx.x; i < cnt * kF; i += blockDim.x) s_f[i / kF][i % kF] = far[base + i / kF].f[i % kF];
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
             s_hdr[i] = far[base + i].hdr;
             s_na[i] = far[base + i].n_a;
@@ -136,33 +129,36 @@ __device__ __forceinline__ Sum4 far_range(const GeomView& g, float phx, float ph
         float gphi = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
         for (int jj = 0; jj < cnt; ++jj) {
             const float4 hdr = s_hdr[jj];
-            const bool rect = s_na[jj] == kNodesA;
+            const bool rect = s_na[jj] == kPairsA;
             const FarNodes* fj = far + base + jj;
-            const float4 q0 = s_f[jj][0], q1 = s_f[jj][1], q2 = s_f[jj][2], q3 = s_f[jj][3];
-            float lphi = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+            float4 q[2 * kPairs0];
+#pragma unroll
+            for (int i = 0; i < 2 * kPairs0; ++i) q[i] = s_f[jj][i];
+            float2 lphi = make_float2(0.f, 0.f), lx = lphi, ly = lphi, lz = lphi;
             for (int k = 0; k < nimg; ++k) {
                 float dx, dy, dz;
                 const float d2 = pair_d2(phx, phy, phz, plx, ply, plz, s_c[jj * nimg + k][0], s_c[jj * nimg + k][1],
                                          dx, dy, dz);
+                const float2 DX = make_float2(dx, dx), DY = make_float2(dy, dy), DZ = make_float2(dz, dz);
                 if (d2 >= hdr.x) {
-                    nodes4_reg(q0, q1, q2, q3, dx, dy, dz, lphi, lx, ly, lz);
+                    pairs0_reg(q, DX, DY, DZ, lphi, lx, ly, lz);
                 } else if (d2 >= hdr.y) {
                     if (rect)
-                        nodes_f32<kNodesA>(s_a[jj], dx, dy, dz, lphi, lx, ly, lz);
+                        node_pairs<kPairsA>(s_a[jj], DX, DY, DZ, lphi, lx, ly, lz);
                     else
-                        nodes_f32<6>(s_a[jj], dx, dy, dz, lphi, lx, ly, lz);
+                        node_pairs<3>(s_a[jj], DX, DY, DZ, lphi, lx, ly, lz);
                 } else if (d2 >= hdr.z) {
-                    nodes_f32<kNodesB>(fj->b, dx, dy, dz, lphi, lx, ly, lz);
+                    node_pairs<kPairsB>(fj->b, DX, DY, DZ, lphi, lx, ly, lz);
                 } else if (d2 >= hdr.w) {
-                    nodes_f32<kNodesC>(fj->c, dx, dy, dz, lphi, lx, ly, lz);
+                    node_pairs<kPairsC>(fj->c, DX, DY, DZ, lphi, lx, ly, lz);
                 }
                 // nearer pairs: k_eval_near
             }
             const float s = s_sig[jj];
-            gphi = fmaf(s, lphi, gphi);
-            gx = fmaf(s, lx, gx);
-            gy = fmaf(s, ly, gy);
-            gz = fmaf(s, lz, gz);
+            gphi = fmaf(s, lphi.x + lphi.y, gphi);
+            gx = fmaf(s, lx.x + lx.y, gx);
+            gy = fmaf(s, ly.x + ly.y, gy);
+            gz = fmaf(s, lz.x + lz.y, gz);
             if ((jj % kGroup) == kGroup - 1 || jj == cnt - 1) {
                 aphi += (double)gphi;
                 aEx += (double)gx;

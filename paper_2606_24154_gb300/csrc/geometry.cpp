@@ -177,17 +177,30 @@ int build_element(const nebem_element& r, const nebem_options& opt, Elem& e, dou
         }
         diag = (r.eps_a + r.eps_b) / (2.0 * kEps0 * (r.eps_b - r.eps_a));
     }
-    // FP32 far-field Gauss nodes as offsets from the centroid, weights x area.
+    // FP32 far-field Gauss nodes: centroid - node, weight x area, packed in pairs.
     const double area = (r.kind == NEBEM_RECT) ? e.twoA[0]
                         : (r.kind == NEBEM_QUAD) ? 0.5 * (e.twoA[0] + e.twoA[1])
                                                  : 0.5 * e.twoA[0];
+    float4 node[kNodesC];  // one tier's nodes (x, y, z = centroid - node, w = weight x area)
     auto put = [&](float4& dst, const double* g, double wt) {
         double d[3];
-        sub3(g, e.c, d);
+        sub3(e.c, g, d);
         dst.x = (float)d[0];
         dst.y = (float)d[1];
         dst.z = (float)d[2];
         dst.w = (float)(wt * area);
+    };
+    // pack cnt nodes of `node` into pairs at dst; returns the pair count
+    auto pack = [&](int cnt, float4* dst) {
+        const int np = (cnt + 1) / 2;
+        for (int i = 0; i < np; ++i) {
+            const float4 a = node[2 * i];
+            float4 b = (2 * i + 1 < cnt) ? node[2 * i + 1] : node[2 * i];
+            if (2 * i + 1 >= cnt) b.w = 0.f;
+            dst[2 * i] = make_float4(a.x, b.x, a.y, b.y);
+            dst[2 * i + 1] = make_float4(a.z, b.z, a.w, b.w);
+        }
+        return np;
     };
     int n_a = 0;
     if (nv == 4) {
@@ -200,6 +213,8 @@ int build_element(const nebem_element& r, const nebem_options& opt, Elem& e, dou
             double x[16], w[16];
             gauss_legendre01(m, x, w);
             int cnt = 0;
+            float4* out = dst;
+            dst = node;
             for (int a = 0; a < m; ++a)
                 for (int b = 0; b < m; ++b) {
                     double g[3], xs[3], xt[3], jn[3];
@@ -212,7 +227,7 @@ int build_element(const nebem_element& r, const nebem_options& opt, Elem& e, dou
                     const double jac = (r.kind == NEBEM_RECT) ? area : std::sqrt(dot3(jn, jn));
                     put(dst[cnt++], g, w[a] * w[b] * jac / area);
                 }
-            return cnt;
+            return pack(cnt, out);
         };
         tensor(2, fn.f);
         n_a = tensor(3, fn.a);
@@ -224,17 +239,20 @@ int build_element(const nebem_element& r, const nebem_options& opt, Elem& e, dou
             double g[3];
             for (int k = 0; k < 3; ++k)
                 g[k] = kTri3B[q][0] * r.v[0][k] + kTri3B[q][1] * r.v[1][k] + kTri3B[q][2] * r.v[2][k];
-            put(fn.f[q], g, kTri3W[q]);
+            put(node[q], g, kTri3W[q]);
         }
+        pack(4, fn.f);
         // degree-4 six-point rule
+        int six = 0;
         for (int g2 = 0; g2 < 2; ++g2)
             for (int rr = 0; rr < 3; ++rr) {
                 double bc[3] = {kTriA[g2], kTriA[g2], kTriA[g2]};
                 bc[rr] = 1.0 - 2.0 * kTriA[g2];
                 double g[3];
                 for (int k = 0; k < 3; ++k) g[k] = bc[0] * r.v[0][k] + bc[1] * r.v[1][k] + bc[2] * r.v[2][k];
-                put(fn.a[n_a++], g, kTriW[g2]);
+                put(node[six++], g, kTriW[g2]);
             }
+        n_a = pack(six, fn.a);
         // collapsed (Duffy) product rules: x = v0 + s e1 + t (1 - s) e2, weight 2 ws wt (1 - s)
         auto collapsed = [&](int m, float4* dst) {
             double x[16], w[16];
@@ -245,9 +263,9 @@ int build_element(const nebem_element& r, const nebem_options& opt, Elem& e, dou
                     const double sa = x[a], tb = x[b] * (1.0 - x[a]);
                     double g[3];
                     for (int k = 0; k < 3; ++k) g[k] = r.v[0][k] + sa * e1[k] + tb * e2[k];
-                    put(dst[cnt++], g, 2.0 * w[a] * w[b] * (1.0 - x[a]));
+                    put(node[cnt++], g, 2.0 * w[a] * w[b] * (1.0 - x[a]));
                 }
-            return cnt;
+            return pack(cnt, dst);
         };
         collapsed(4, fn.b);
         collapsed(6, fn.c);

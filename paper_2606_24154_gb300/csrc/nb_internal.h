@@ -30,23 +30,32 @@ struct __align__(16) Elem {
 };
 static_assert(sizeof(Elem) == 256, "Elem must be 256 bytes");
 
-// FP32 far-field shadow of one element for the mixed evaluation: Gauss nodes as offsets
-// from the centroid (x, y, z) with weight x area (w), for four distance tiers, and
-// headers.  Tiers by distance d to the image centroid in element circumradii rho:
+// FP32 far-field shadow of one element for the mixed evaluation: Gauss nodes for four
+// distance tiers, and headers.  Tiers by distance d to the image centroid in element
+// circumradii rho:
 //   tier 0 (d >= ratio_0 rho):    triangle 4-point degree-3 rule, rectangle 2x2 Gauss-Legendre
 //   tier a (d >= ratio_a rho):    triangle 6-point degree-4 rule, rectangle 3x3
 //   tier b (d >= ratio_b rho):    triangle collapsed 4x4, rectangle 4x4
 //   tier c (d >= ratio_near rho): triangle collapsed 6x6, rectangle 6x6
-// hdr = squared tier distances (tier 0, a, b, near) in m^2; n_a = node count of tier a.
+// (quadrilaterals: the rectangle rules on their bilinear map).  Nodes are stored in pairs
+// for the packed FP32x2 arithmetic: pair i of a tier is the two float4
+//   (sa.x, sb.x, sa.y, sb.y), (sa.z, sb.z, wa, wb)
+// with s = centroid - node and w = weight x area; an odd count is padded with a node of
+// weight 0 at the position of the last node.  hdr = squared tier distances (tier 0, a, b,
+// near) in m^2; n_a = node pairs of tier a (5 rectangle / quadrilateral, 3 triangle).
 constexpr int kNodes0 = 4;
 constexpr int kNodesA = 9;
 constexpr int kNodesB = 16;
 constexpr int kNodesC = 36;
+constexpr int kPairs0 = 2;
+constexpr int kPairsA = 5;
+constexpr int kPairsB = 8;
+constexpr int kPairsC = 18;
 struct __align__(16) FarNodes {
-    float4 f[kNodes0];
-    float4 a[kNodesA];
-    float4 b[kNodesB];
-    float4 c[kNodesC];
+    float4 f[2 * kPairs0];
+    float4 a[2 * kPairsA];
+    float4 b[2 * kPairsB];
+    float4 c[2 * kPairsC];
     float4 hdr;
     int32_t n_a;
     int32_t pad[3];
