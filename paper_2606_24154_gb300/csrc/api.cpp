@@ -54,7 +54,7 @@ Ctx::~Ctx() {
     for (DevBuf* b : {&d_el, &d_far, &d_diag, &d_sigma, &d_K, &d_LU64, &d_LU32, &d_piv64, &d_piv32, &d_work, &d_b,
                       &d_x, &d_r, &d_r32, &d_small, &d_pts, &d_phi, &d_E, &d_car, &d_q, &d_car2, &d_sc_tgt,
                       &d_sc_phi, &d_sc_E, &d_scratch, &d_cjk, &d_cell_start, &d_cell_items, &d_fv_ax, &d_fv_ay, &d_fv_az, &d_fv_phi,
-                      &d_fv_E, &d_vkeys, &d_vflags, &d_vbsum, &d_vpartial, &d_vgrid, &d_lines, &d_linesf,
+                      &d_fv_E, &d_vkeys, &d_vflags, &d_vbsum, &d_vpartial, &d_vgrid, &d_lines, &d_linesf, &d_line_vox,
                       &d_am_start, &d_am_items, &d_am_elarea, &d_am_parea, &d_am_tmp})
         b->release();
     am_near.release_all();

@@ -90,7 +90,7 @@ struct Ctx {
     // line-charge representation of the known charges (Alg. 3): on when sc_lines
     bool sc_lines = false;
     double voxel[3] = {0.0, 0.0, 0.0};
-    DevBuf d_vkeys, d_vflags, d_vbsum, d_vpartial, d_vgrid, d_lines, d_linesf;
+    DevBuf d_vkeys, d_vflags, d_vbsum, d_vpartial, d_vgrid, d_lines, d_linesf, d_line_vox;
 
     ~Ctx();
 };

@@ -27,8 +27,10 @@
 // FP64 mode evaluates every pair so.  Mixed mode evaluates far lines by Gauss-Legendre
 // nodes along the line in FP32 on the two-float target-minus-midpoint difference, with a
 // node count by the distance d in half lengths h (>= 96 h: 2 nodes, >= 16 h: 3, >= 8 h: 4,
-// >= 3 h: 6; worst per-pair error about 1e-8), and nearer lines in the FP64 closed form;
-// FP32 partial sums over 32 lines are flushed to FP64.
+// >= 3 h: 6; worst per-pair error about 1e-8), FP32 partial sums over 32 lines flushed to
+// FP64 (k_line_far); lines nearer than 3 h take the FP64 closed form in a second kernel
+// that visits only the voxel rows around the target (k_line_near).  Both kernels decide
+// "near" with the same rounded FP32 operations, so every pair is counted once.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -296,7 +298,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_add(int* __restrict__ dat
 
 __global__ void k_make_lines(const long long* __restrict__ keys, int64_t n, const double* __restrict__ q,
                              const int* __restrict__ line_of, const VoxGrid* __restrict__ g,
-                             LineRec* __restrict__ lines, LineF* __restrict__ linesf) {
+                             LineRec* __restrict__ lines, LineF* __restrict__ linesf, long long* __restrict__ line_vox) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const long long v = keys[j] / n;
@@ -320,6 +322,7 @@ __global__ void k_make_lines(const long long* __restrict__ keys, int64_t n, cons
     r.u[2] = 1.0;
     r.len = dz;
     lines[L] = r;
+    line_vox[L] = v;
     const double mz = __dadd_rn(az, __dmul_rn(0.5, dz));
     const float hx = (float)ax, hy = (float)ay, hz = (float)mz;
     LineF f;
@@ -430,12 +433,35 @@ __device__ __forceinline__ void line_nodes(const float* __restrict__ x, const fl
     }
 }
 
-__global__ void __launch_bounds__(kLT) k_line_mixed(const LineF* __restrict__ linesf,
-                                                    const LineRec* __restrict__ lines,
-                                                    const VoxGrid* __restrict__ g, const double* __restrict__ tgt,
-                                                    const long long* __restrict__ perm, int64_t perm_div, int64_t nt,
-                                                    double s2, double ke, int accumulate, LineRules rules,
-                                                    double* __restrict__ phi, double* __restrict__ E) {
+// FP32 squared distance between a target (two floats per coordinate) and a line's
+// midpoint, and the near threshold (3 half lengths)^2: pinned operation sequences, so the
+// far and near kernels take the same decision for every pair.
+__device__ __forceinline__ float line_d2(float thx, float thy, float thz, float tlx, float tly, float tlz,
+                                         const LineF& L, float& dx, float& dy, float& dz) {
+    dx = __fadd_rn(__fsub_rn(thx, L.mh.x), __fsub_rn(tlx, L.ml.x));
+    dy = __fadd_rn(__fsub_rn(thy, L.mh.y), __fsub_rn(tly, L.ml.y));
+    dz = __fadd_rn(__fsub_rn(thz, L.mh.z), __fsub_rn(tlz, L.ml.z));
+    return __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+}
+
+__device__ __forceinline__ float line_near2(const LineF& L) { return __fmul_rn(9.f, __fmul_rn(L.mh.w, L.mh.w)); }
+
+__device__ __forceinline__ void split_target(double px, double py, double pz, float& thx, float& thy, float& thz,
+                                             float& tlx, float& tly, float& tlz) {
+    thx = (float)px;
+    thy = (float)py;
+    thz = (float)pz;
+    tlx = (float)(px - thx);
+    tly = (float)(py - thy);
+    tlz = (float)(pz - thz);
+}
+
+// Far pairs (d >= 3 h): FP32 Gauss-Legendre nodes along the line.  Near pairs are left to
+// k_line_near.
+__global__ void __launch_bounds__(kLT) k_line_far(const LineF* __restrict__ linesf, const VoxGrid* __restrict__ g,
+                                                  const double* __restrict__ tgt, const long long* __restrict__ perm,
+                                                  int64_t perm_div, int64_t nt, float s2f, double ke, int accumulate,
+                                                  LineRules rules, double* __restrict__ phi, double* __restrict__ E) {
     __shared__ LineF sf[kLT];
     __shared__ float rx[4][6], rw[4][6];
     if (threadIdx.x < 24) {
@@ -453,9 +479,8 @@ __global__ void __launch_bounds__(kLT) k_line_mixed(const LineF* __restrict__ li
         py = tgt[3 * p + 1];
         pz = tgt[3 * p + 2];
     }
-    const float thx = (float)px, thy = (float)py, thz = (float)pz;
-    const float tlx = (float)(px - thx), tly = (float)(py - thy), tlz = (float)(pz - thz);
-    const float s2f = (float)s2;
+    float thx, thy, thz, tlx, tly, tlz;
+    split_target(px, py, pz, thx, thy, thz, tlx, tly, tlz);
     double ph = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
     for (int64_t base = 0; base < nl; base += kLT) {
         __syncthreads();
@@ -467,21 +492,18 @@ __global__ void __launch_bounds__(kLT) k_line_mixed(const LineF* __restrict__ li
             float fph = 0.f, fex = 0.f, fey = 0.f, fez = 0.f;
             for (int k = sub; k < sub + m; ++k) {
                 const LineF L = sf[k];
-                const float dx = (thx - L.mh.x) + (tlx - L.ml.x);
-                const float dy = (thy - L.mh.y) + (tly - L.ml.y);
-                const float dz = (thz - L.mh.z) + (tlz - L.ml.z);
-                const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                float dx, dy, dz;
+                const float d2 = line_d2(thx, thy, thz, tlx, tly, tlz, L, dx, dy, dz);
                 const float h2 = L.mh.w * L.mh.w;
+                if (!(d2 >= line_near2(L))) continue;  // k_line_near
                 if (d2 >= 9216.f * h2)
                     line_nodes<2>(rx[0], rw[0], dx, dy, dz, L, s2f, fph, fex, fey, fez);
                 else if (d2 >= 256.f * h2)
                     line_nodes<3>(rx[1], rw[1], dx, dy, dz, L, s2f, fph, fex, fey, fez);
                 else if (d2 >= 64.f * h2)
                     line_nodes<4>(rx[2], rw[2], dx, dy, dz, L, s2f, fph, fex, fey, fez);
-                else if (d2 >= 9.f * h2)
-                    line_nodes<6>(rx[3], rw[3], dx, dy, dz, L, s2f, fph, fex, fey, fez);
                 else
-                    line_pair_f64(lines[base + k], px, py, pz, s2, ph, ex, ey, ez);
+                    line_nodes<6>(rx[3], rw[3], dx, dy, dz, L, s2f, fph, fex, fey, fez);
             }
             ph += fph;
             ex += fex;
@@ -490,6 +512,73 @@ __global__ void __launch_bounds__(kLT) k_line_mixed(const LineF* __restrict__ li
         }
     }
     if (active) store_result(p, accumulate, ke, ph, ex, ey, ez, phi, E);
+}
+
+// First index in line_vox[lo, hi) (ascending) with line_vox >= v.
+__device__ __forceinline__ int64_t lower_bound_vox(const long long* __restrict__ lv, int64_t lo, int64_t hi,
+                                                   long long v) {
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (lv[mid] < v)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Near pairs (d < 3 h) in FP64: the candidate lines of a target lie in the voxels whose
+// centre is within 3 h (padded by 1e-3 relative and one voxel) of it; every candidate row
+// (fixed j, k) is a contiguous range of voxel indices, found by binary search in the sorted
+// line_vox.  The decision d < 3 h is the far kernel's FP32 test.  Adds to phi / E.
+__global__ void __launch_bounds__(kLT) k_line_near(const LineF* __restrict__ linesf,
+                                                   const LineRec* __restrict__ lines,
+                                                   const long long* __restrict__ line_vox,
+                                                   const VoxGrid* __restrict__ g, const double* __restrict__ tgt,
+                                                   const long long* __restrict__ perm, int64_t perm_div, int64_t nt,
+                                                   double s2, double ke, double* __restrict__ phi,
+                                                   double* __restrict__ E) {
+    const int64_t t = (int64_t)blockIdx.x * kLT + threadIdx.x;
+    if (t >= nt) return;
+    const int64_t nl = g->nl;
+    if (nl == 0) return;
+    const int64_t p = target_index(perm, perm_div, t);
+    const double px = tgt[3 * p], py = tgt[3 * p + 1], pz = tgt[3 * p + 2];
+    float thx, thy, thz, tlx, tly, tlz;
+    split_target(px, py, pz, thx, thy, thz, tlx, tly, tlz);
+    const double reach = 1.5 * g->d[2] * (1.0 + 1e-3);  // 3 half lengths, padded
+    const double P[3] = {px, py, pz};
+    long long lo3[3], hi3[3];
+    for (int a = 0; a < 3; ++a) {
+        // voxel centres: lo + (i + 1/2) d per axis (x, y); midpoints lo + (k + 1/2) dz in z
+        const double c0 = (P[a] - reach - g->lo[a]) / g->d[a] - 0.5;
+        const double c1 = (P[a] + reach - g->lo[a]) / g->d[a] - 0.5;
+        double f0 = floor(c0), f1 = ceil(c1);
+        f0 = fmax(f0, 0.0);
+        f1 = fmin(f1, (double)(g->dims[a] - 1));
+        lo3[a] = (long long)f0;
+        hi3[a] = (long long)f1;
+        if (f1 < f0) return;
+    }
+    double ph = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
+    for (long long k = lo3[2]; k <= hi3[2]; ++k)
+        for (long long j = lo3[1]; j <= hi3[1]; ++j) {
+            const long long row = (k * g->dims[1] + j) * g->dims[0];
+            int64_t l = lower_bound_vox(line_vox, 0, nl, row + lo3[0]);
+            for (; l < nl && line_vox[l] <= row + hi3[0]; ++l) {
+                const LineF L = linesf[l];
+                float dx, dy, dz;
+                const float d2 = line_d2(thx, thy, thz, tlx, tly, tlz, L, dx, dy, dz);
+                if (d2 >= line_near2(L)) continue;  // k_line_far
+                line_pair_f64(lines[l], px, py, pz, s2, ph, ex, ey, ez);
+            }
+        }
+    if (phi) phi[p] += ke * ph;
+    if (E) {
+        E[3 * p] += ke * ex;
+        E[3 * p + 1] += ke * ey;
+        E[3 * p + 2] += ke * ez;
+    }
 }
 
 LineRules make_rules() {
@@ -536,7 +625,7 @@ cudaError_t launch_voxelize(const double* pos, const double* q, int64_t n, const
     k_scan_block<<<(unsigned)nb, kScanThreads, 0, s>>>(w.flags, n, w.bsum);
     k_scan_top<<<1, kScanThreads, 0, s>>>(w.bsum, nb, w.grid);
     k_scan_add<<<(unsigned)nb, kScanThreads, 0, s>>>(w.flags, n, w.bsum);
-    k_make_lines<<<nb256, 256, 0, s>>>(w.keys, n, q, w.flags, w.grid, w.lines, w.linesf);
+    k_make_lines<<<nb256, 256, 0, s>>>(w.keys, n, q, w.flags, w.grid, w.lines, w.linesf, w.line_vox);
     return cudaGetLastError();
 }
 
@@ -551,8 +640,10 @@ cudaError_t launch_line_eval(int precision, const VoxWork& w, const double* tgt,
                                           E);
     } else {
         static const LineRules rules = make_rules();
-        k_line_mixed<<<blocks, kLT, 0, s>>>(w.linesf, w.lines, w.grid, tgt, perm, perm_div, nt, soft * soft, ke,
-                                            accumulate, rules, phi, E);
+        k_line_far<<<blocks, kLT, 0, s>>>(w.linesf, w.grid, tgt, perm, perm_div, nt, (float)(soft * soft), ke,
+                                          accumulate, rules, phi, E);
+        k_line_near<<<blocks, kLT, 0, s>>>(w.linesf, w.lines, w.line_vox, w.grid, tgt, perm, perm_div, nt,
+                                           soft * soft, ke, phi, E);
     }
     return cudaGetLastError();
 }

@@ -173,6 +173,7 @@ struct VoxWork {
     VoxGrid* grid;     // one
     LineRec* lines;    // n (at most one line per point)
     LineF* linesf;     // n
+    long long* line_vox;  // n: flat voxel index of every line (ascending)
 };
 int64_t vox_pad_len(int64_t n);     // sort length: power of two >= max(n, 2048)
 int64_t vox_scan_blocks(int64_t n);

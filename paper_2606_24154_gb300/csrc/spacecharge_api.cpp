@@ -28,6 +28,7 @@ VoxWork vox_work(Ctx* c) {
     w.grid = c->d_vgrid.as<VoxGrid>();
     w.lines = c->d_lines.as<LineRec>();
     w.linesf = c->d_linesf.as<LineF>();
+    w.line_vox = c->d_line_vox.as<long long>();
     return w;
 }
 
@@ -44,6 +45,7 @@ int ensure_vox(Ctx* c, int64_t n) {
     }
     CK(c->d_lines.ensure(sizeof(LineRec) * n));
     CK(c->d_linesf.ensure(sizeof(LineF) * n));
+    CK(c->d_line_vox.ensure(sizeof(long long) * n));
     return 0;
 }
 
