@@ -281,23 +281,15 @@ __device__ __forceinline__ void load_elem_tile(Elem* s_el, const Elem* __restric
     for (int i = threadIdx.x; i < cnt * 16; i += blockDim.x) dst[i] = src[i];
 }
 
-// FP64 closed forms for every pair of `count` targets (overwrites phi / E).
-__device__ __forceinline__ void f64_block(const Elem* __restrict__ el, const double* __restrict__ sigma, int64_t n_el,
-                                          const ImageTable& img, const double* __restrict__ pts, int count,
-                                          double* __restrict__ phi, double* __restrict__ E) {
+// Raw FP64 sums (before the factor ke) of the closed forms of one point over the elements
+// [e0, e1) and all images.  Called by every thread of the block (shared-memory tiles).
+__device__ __forceinline__ Sum4 f64_range(const Elem* __restrict__ el, const double* __restrict__ sigma, int64_t e0,
+                                          int64_t e1, const ImageTable& img, double Px, double Py, double Pz) {
     __shared__ Elem s_el[kTile64];
     __shared__ double s_sig[kTile64];
-    const int p = threadIdx.x;
-    const bool active = p < count;
-    double Px = 0.0, Py = 0.0, Pz = 0.0;
-    if (active) {
-        Px = pts[3 * p];
-        Py = pts[3 * p + 1];
-        Pz = pts[3 * p + 2];
-    }
     double aphi = 0.0, aEx = 0.0, aEy = 0.0, aEz = 0.0;
-    for (int64_t base = 0; base < n_el; base += kTile64) {
-        const int cnt = (int)min((int64_t)kTile64, n_el - base);
+    for (int64_t base = e0; base < e1; base += kTile64) {
+        const int cnt = (int)min((int64_t)kTile64, e1 - base);
         __syncthreads();
         load_elem_tile(s_el, el, base, cnt);
         if (threadIdx.x < cnt) s_sig[threadIdx.x] = sigma[base + threadIdx.x];
@@ -320,15 +312,32 @@ __device__ __forceinline__ void f64_block(const Elem* __restrict__ el, const dou
             aEz = fma(s, fma(lx, e.ex[2], fma(ly, e.ey[2], lz * e.ez[2])), aEz);
         }
     }
+    return Sum4{aphi, aEx, aEy, aEz};
+}
+
+// FP64 closed forms for every pair of `count` targets (overwrites phi / E).  Sums over
+// kChunkEl-element chunks are added in order, so that a launch split over element chunks
+// (the server's small requests) gives the same bits.
+__device__ __forceinline__ void f64_block(const Elem* __restrict__ el, const double* __restrict__ sigma, int64_t n_el,
+                                          const ImageTable& img, const double* __restrict__ pts, int count,
+                                          double* __restrict__ phi, double* __restrict__ E) {
+    const int p = threadIdx.x;
+    const bool active = p < count;
+    double Px = 0.0, Py = 0.0, Pz = 0.0;
     if (active) {
-        const double ke = 1.0 / (4.0 * kPi * kEps0);
-        if (phi) phi[p] = ke * aphi;
-        if (E) {
-            E[3 * p] = ke * aEx;
-            E[3 * p + 1] = ke * aEy;
-            E[3 * p + 2] = ke * aEz;
-        }
+        Px = pts[3 * p];
+        Py = pts[3 * p + 1];
+        Pz = pts[3 * p + 2];
     }
+    Sum4 tot{0.0, 0.0, 0.0, 0.0};
+    for (int64_t e0 = 0; e0 < n_el; e0 += kChunkEl) {
+        const Sum4 c = f64_range(el, sigma, e0, min(e0 + (int64_t)kChunkEl, n_el), img, Px, Py, Pz);
+        tot.phi += c.phi;
+        tot.x += c.x;
+        tot.y += c.y;
+        tot.z += c.z;
+    }
+    if (active) store_far(phi, E, p, tot);
 }
 
 }  // namespace nb

@@ -36,7 +36,9 @@ namespace {
     } while (0)
 
 constexpr int kItemPoints = 128;
-constexpr int64_t kSmallPoints = 1024;  // mixed requests up to this size are split by element chunks
+constexpr int64_t kSmallPoints = 1024;      // mixed requests up to this size are split by element chunks
+constexpr int64_t kSmallPointsF64 = 16384;  // FP64 requests up to this size too (one block per SM already
+                                            // keeps the FP64 pipe busy, so larger ones need no split)
 constexpr int kPartialBlocks = 512;     // point blocks with chunk partial sums in flight
 
 struct Interval {
@@ -167,8 +169,8 @@ struct Server {
             Request* r = queue.front();
             const int64_t blocks = (r->n + kItemPoints - 1) / kItemPoints;
             const int32_t nch = nchunks[r->geom];
-            const bool chunked = r->precision == NEBEM_MIXED && r->n <= kSmallPoints && nch > 1 &&
-                                 (int64_t)free_pblocks.size() >= blocks;
+            const int64_t small = (r->precision == NEBEM_MIXED) ? kSmallPoints : kSmallPointsF64;
+            const bool chunked = r->n <= small && nch > 1 && (int64_t)free_pblocks.size() >= blocks;
             const int64_t items = chunked ? blocks * nch : blocks;
             if (free_slots.empty() || in_flight_items + items > ring_cap) break;
             const int64_t off = arena.alloc(r->n);

@@ -61,7 +61,8 @@ __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restr
         if (!have) return;
         const ServeGeom& G = geoms[it.geom];
         bool block_done = true;
-        if (it.precision != NEBEM_MIXED) {
+        const bool mixed = it.precision == NEBEM_MIXED;
+        if (it.chunk < 0 && !mixed) {
             f64_block(G.view.el, G.view.sigma, G.view.n_el, G.img, arena_pts + 3 * it.offset, it.count,
                       arena_phi + it.offset, arena_E + 3 * it.offset);
         } else if (it.chunk < 0) {
@@ -70,15 +71,22 @@ __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restr
                 near_point(G.view, G.img, arena_pts, it.offset + threadIdx.x, arena_phi, arena_E);
         } else {
             // one element chunk of a point block: raw sums to the partial area; the CTA that
-            // finishes the block's last chunk adds the chunks in order (as far_block does),
-            // stores ke * sum and adds the near pairs
+            // finishes the block's last chunk adds the chunks in order (as far_block and
+            // f64_block do), stores ke * sum and (mixed) adds the near pairs
             const bool active = (int)threadIdx.x < it.count;
             const int64_t p = it.offset + threadIdx.x;
-            float phx, phy, phz, plx, ply, plz;
-            load_point_2f(arena_pts, p, active, phx, phy, phz, plx, ply, plz);
             const int64_t e0 = (int64_t)it.chunk * kChunkEl;
-            const Sum4 c = far_range(G.view, phx, phy, phz, plx, ply, plz, e0,
-                                     min(e0 + (int64_t)kChunkEl, G.view.n_el));
+            const int64_t e1 = min(e0 + (int64_t)kChunkEl, G.view.n_el);
+            Sum4 c;
+            if (mixed) {
+                float phx, phy, phz, plx, ply, plz;
+                load_point_2f(arena_pts, p, active, phx, phy, phz, plx, ply, plz);
+                c = far_range(G.view, phx, phy, phz, plx, ply, plz, e0, e1);
+            } else {
+                const double Px = active ? arena_pts[3 * p] : 0.0, Py = active ? arena_pts[3 * p + 1] : 0.0,
+                             Pz = active ? arena_pts[3 * p + 2] : 0.0;
+                c = f64_range(G.view.el, G.view.sigma, e0, e1, G.img, Px, Py, Pz);
+            }
             double* part = partials + ((int64_t)it.pblock * max_chunks + it.chunk) * (4 * kEvalThreads);
             part[4 * threadIdx.x] = c.phi;
             part[4 * threadIdx.x + 1] = c.x;
@@ -102,7 +110,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restr
                 }
                 if (active) {
                     store_far(arena_phi, arena_E, p, tot);
-                    near_point(G.view, G.img, arena_pts, p, arena_phi, arena_E);
+                    if (mixed) near_point(G.view, G.img, arena_pts, p, arena_phi, arena_E);
                 }
                 if (threadIdx.x == 0) pblock_count[it.pblock] = 0;
             }

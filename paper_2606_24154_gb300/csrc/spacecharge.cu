@@ -13,7 +13,9 @@
 // lo = fl(x - hi)).  x_t - x_c = (hi_t - hi_c) + (lo_t - lo_c): for nearby carriers
 // hi_t - hi_c is exact (Sterbenz), so the difference keeps FP64 accuracy where it
 // matters (near pairs) while every operation is FP32; the rest of the pair term is
-// FP32 with rsqrt.  Runs of 32 sources are summed in FP32 and added to FP64 accumulators.
+// FP32 with rsqrt.  Runs of 32 sources are summed in FP32 and added to two-float
+// (hi + lo) running totals with an error-free two-sum; each thread takes two targets in
+// the lanes of the packed FP32x2 instructions.
 #include "nb_internal.h"
 
 namespace nb {
@@ -91,78 +93,81 @@ __global__ void k_split2f(const double* __restrict__ pos, const double* __restri
     lo[i] = make_float4((float)(x - hx), (float)(y - hy), (float)(z - hz), 0.f);
 }
 
+// Mixed sum: each thread takes two targets, t and t + kSC2Threads of its block, held in
+// the two lanes of the packed FP32x2 instructions; a source tile is staged in shared
+// memory with every value negated and duplicated into both lanes, so that a pair
+// (target, source) costs the same rounded operations as the scalar form
+//   d = (t_hi - s_hi) + (t_lo - s_lo),  r^2 = d.d + s^2,  q / r,  q d / r^3
+// at half the issue slots.  Partial sums over kFlush sources are added to running totals
+// kept as two floats (hi + lo, error-free two-sum), so no FP64 instruction runs per
+// source; the totals are converted to FP64 once per target.
+constexpr int kSC2Threads = 128;
+constexpr int kSC2Tile = 2 * kSC2Threads;  // targets per block = sources per tile
+
+struct F2Acc {  // two-float running total per lane: value = hi + lo
+    float2 hi, lo;
+};
+
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
+__device__ __forceinline__ void acc_add(F2Acc& a, float2 x) {
+    two_sum_add(a.hi.x, a.lo.x, x.x);
+    two_sum_add(a.hi.y, a.lo.y, x.y);
+}
+
 template <bool SELF>
-__device__ __forceinline__ void sc_tile_f32(const float4* __restrict__ sh, const float4* __restrict__ sl, int cnt,
-                                            float thx, float thy, float thz, float tlx, float tly, float tlz,
-                                            float s2, int self_k, float& ph, float& ex, float& ey, float& ez) {
+__device__ __forceinline__ void sc_tile_f32x2(const float4* __restrict__ A, const float4* __restrict__ B,
+                                              const float4* __restrict__ C, const float2* __restrict__ D, int k0,
+                                              int k1, float2 thx, float2 thy, float2 thz, float2 tlx, float2 tly,
+                                              float2 tlz, float2 s2, int self0, int self1, float2& ph, float2& ex,
+                                              float2& ey, float2& ez) {
 #pragma unroll 4
-    for (int k = 0; k < cnt; ++k) {
-        const float4 h = sh[k];
-        const float4 l = sl[k];
-        const float dx = (thx - h.x) + (tlx - l.x);
-        const float dy = (thy - h.y) + (tly - l.y);
-        const float dz = (thz - h.z) + (tlz - l.z);
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, s2)));
-        const float ri = rsqrtf(r2);
-        float qq = h.w;
-        if (SELF && k == self_k) qq = 0.f;
-        const float qr = qq * ri;
-        const float qr3 = qr * ri * ri;
-        ph += qr;
-        ex = fmaf(qr3, dx, ex);
-        ey = fmaf(qr3, dy, ey);
-        ez = fmaf(qr3, dz, ez);
+    for (int k = k0; k < k1; ++k) {
+        const float4 a = A[k], b = B[k], c = C[k];
+        const float2 d = D[k];
+        const float2 dx = __fadd2_rn(__fadd2_rn(thx, make_float2(a.x, a.y)), __fadd2_rn(tlx, make_float2(c.x, c.y)));
+        const float2 dy = __fadd2_rn(__fadd2_rn(thy, make_float2(a.z, a.w)), __fadd2_rn(tly, make_float2(c.z, c.w)));
+        const float2 dz = __fadd2_rn(__fadd2_rn(thz, make_float2(b.x, b.y)), __fadd2_rn(tlz, d));
+        const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, s2)));
+        const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+        float2 qq = make_float2(b.z, b.w);
+        if (SELF) {
+            if (k == self0) qq.x = 0.f;
+            if (k == self1) qq.y = 0.f;
+        }
+        const float2 qr = __fmul2_rn(qq, ri);
+        const float2 qr3 = __fmul2_rn(qr, __fmul2_rn(ri, ri));
+        ph = __fadd2_rn(ph, qr);
+        ex = __ffma2_rn(qr3, dx, ex);
+        ey = __ffma2_rn(qr3, dy, ey);
+        ez = __ffma2_rn(qr3, dz, ez);
     }
 }
 
-// Targets given as FP64 (split in-kernel); sources as two-float tiles.
-__global__ void __launch_bounds__(kSCThreads) k_sc_mixed(const float4* __restrict__ shq, const float4* __restrict__ slo,
-                                                         int64_t nsrc, const double* __restrict__ tgt, int64_t ntgt,
-                                                         int exclude_self, float s2, double ke, int accumulate,
-                                                         double* __restrict__ phi, double* __restrict__ E) {
-    __shared__ float4 sh[kSCThreads];
-    __shared__ float4 sl[kSCThreads];
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = t < ntgt;
+__device__ __forceinline__ void load_target_2f(const double* __restrict__ tgt, int64_t t, bool active, float& hx,
+                                               float& hy, float& hz, float& lx, float& ly, float& lz) {
     double x = 0, y = 0, z = 0;
     if (active) {
         x = tgt[3 * t];
         y = tgt[3 * t + 1];
         z = tgt[3 * t + 2];
     }
-    const float thx = (float)x, thy = (float)y, thz = (float)z;
-    const float tlx = (float)(x - thx), tly = (float)(y - thy), tlz = (float)(z - thz);
-    double ph = 0.0, ex = 0.0, ey = 0.0, ez = 0.0;
-    for (int64_t base = 0; base < nsrc; base += kSCThreads) {
-        __syncthreads();
-        const int64_t c = base + threadIdx.x;
-        if (c < nsrc) {
-            sh[threadIdx.x] = shq[c];
-            sl[threadIdx.x] = slo[c];
-        }
-        __syncthreads();
-        const int cnt = (int)min((int64_t)kSCThreads, nsrc - base);
-        // the tile that holds this thread's own carrier (block-uniform when targets are the
-        // sources in order: the tile index equals the block index)
-        const bool self_tile = exclude_self && (base == (int64_t)blockIdx.x * blockDim.x);
-        const int self_k = self_tile ? (int)(t - base) : -1;
-        // FP32 partial sums over 32 sources at a time, flushed to FP64: the +/- charges
-        // cancel, so longer FP32 runs would lose the result in the partial sums' rounding
-        for (int sub = 0; sub < cnt; sub += kFlush) {
-            const int m = min(kFlush, cnt - sub);
-            float fph = 0.f, fex = 0.f, fey = 0.f, fez = 0.f;
-            if (self_k >= sub && self_k < sub + m)
-                sc_tile_f32<true>(sh + sub, sl + sub, m, thx, thy, thz, tlx, tly, tlz, s2, self_k - sub, fph, fex,
-                                  fey, fez);
-            else
-                sc_tile_f32<false>(sh + sub, sl + sub, m, thx, thy, thz, tlx, tly, tlz, s2, -1, fph, fex, fey, fez);
-            ph += fph;
-            ex += fex;
-            ey += fey;
-            ez += fez;
-        }
-    }
-    if (!active) return;
+    hx = (float)x;
+    hy = (float)y;
+    hz = (float)z;
+    lx = (float)(x - hx);
+    ly = (float)(y - hy);
+    lz = (float)(z - hz);
+}
+
+__device__ __forceinline__ void store_target(int64_t t, int accumulate, double ke, double ph, double ex, double ey,
+                                             double ez, double* __restrict__ phi, double* __restrict__ E) {
     if (accumulate) {
         if (phi) phi[t] += ke * ph;
         if (E) {
@@ -178,6 +183,67 @@ __global__ void __launch_bounds__(kSCThreads) k_sc_mixed(const float4* __restric
             E[3 * t + 2] = ke * ez;
         }
     }
+}
+
+// Targets given as FP64 (split in-kernel); sources as two-float (hi, lo) arrays.
+__global__ void __launch_bounds__(kSC2Threads) k_sc_mixed(const float4* __restrict__ shq,
+                                                          const float4* __restrict__ slo, int64_t nsrc,
+                                                          const double* __restrict__ tgt, int64_t ntgt,
+                                                          int exclude_self, float s2, double ke, int accumulate,
+                                                          double* __restrict__ phi, double* __restrict__ E) {
+    __shared__ float4 sA[kSC2Tile], sB[kSC2Tile], sC[kSC2Tile];
+    __shared__ float2 sD[kSC2Tile];
+    const int64_t t0 = (int64_t)blockIdx.x * kSC2Tile + threadIdx.x;
+    const int64_t t1 = t0 + kSC2Threads;
+    float h0x, h0y, h0z, l0x, l0y, l0z, h1x, h1y, h1z, l1x, l1y, l1z;
+    load_target_2f(tgt, t0, t0 < ntgt, h0x, h0y, h0z, l0x, l0y, l0z);
+    load_target_2f(tgt, t1, t1 < ntgt, h1x, h1y, h1z, l1x, l1y, l1z);
+    const float2 thx = make_float2(h0x, h1x), thy = make_float2(h0y, h1y), thz = make_float2(h0z, h1z);
+    const float2 tlx = make_float2(l0x, l1x), tly = make_float2(l0y, l1y), tlz = make_float2(l0z, l1z);
+    const float2 s22 = make_float2(s2, s2);
+    const float2 zero = make_float2(0.f, 0.f);
+    F2Acc aph{zero, zero}, aex{zero, zero}, aey{zero, zero}, aez{zero, zero};
+    for (int64_t base = 0; base < nsrc; base += kSC2Tile) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < kSC2Tile; i += kSC2Threads) {
+            const int64_t c = base + i;
+            if (c < nsrc) {
+                const float4 h = shq[c], l = slo[c];
+                sA[i] = make_float4(-h.x, -h.x, -h.y, -h.y);
+                sB[i] = make_float4(-h.z, -h.z, h.w, h.w);
+                sC[i] = make_float4(-l.x, -l.x, -l.y, -l.y);
+                sD[i] = make_float2(-l.z, -l.z);
+            }
+        }
+        __syncthreads();
+        const int cnt = (int)min((int64_t)kSC2Tile, nsrc - base);
+        // the tile that holds this block's own carriers (targets are the sources in order)
+        const bool self_tile = exclude_self && (base == (int64_t)blockIdx.x * kSC2Tile);
+        const int self0 = self_tile ? (int)threadIdx.x : -1;
+        const int self1 = self_tile ? (int)threadIdx.x + kSC2Threads : -1;
+        // FP32 partial sums over kFlush sources: the +/- charges cancel, so longer FP32
+        // runs would lose the result in the partial sums' rounding
+        for (int sub = 0; sub < cnt; sub += kFlush) {
+            const int m = min(kFlush, cnt - sub);
+            float2 fph = zero, fex = zero, fey = zero, fez = zero;
+            if (self_tile && ((self0 >= sub && self0 < sub + m) || (self1 >= sub && self1 < sub + m)))
+                sc_tile_f32x2<true>(sA, sB, sC, sD, sub, sub + m, thx, thy, thz, tlx, tly, tlz, s22, self0, self1, fph,
+                                    fex, fey, fez);
+            else
+                sc_tile_f32x2<false>(sA, sB, sC, sD, sub, sub + m, thx, thy, thz, tlx, tly, tlz, s22, -1, -1, fph,
+                                     fex, fey, fez);
+            acc_add(aph, fph);
+            acc_add(aex, fex);
+            acc_add(aey, fey);
+            acc_add(aez, fez);
+        }
+    }
+    if (t0 < ntgt)
+        store_target(t0, accumulate, ke, (double)aph.hi.x + (double)aph.lo.x, (double)aex.hi.x + (double)aex.lo.x,
+                     (double)aey.hi.x + (double)aey.lo.x, (double)aez.hi.x + (double)aez.lo.x, phi, E);
+    if (t1 < ntgt)
+        store_target(t1, accumulate, ke, (double)aph.hi.y + (double)aph.lo.y, (double)aex.hi.y + (double)aex.lo.y,
+                     (double)aey.hi.y + (double)aey.lo.y, (double)aez.hi.y + (double)aez.lo.y, phi, E);
 }
 
 // b_i -= phi_sc(c_i) on conductor rows, b_i -= n_i . E_sc(c_i) on interface rows.
@@ -230,8 +296,8 @@ cudaError_t launch_sc_eval(int precision, const double* src, const double* q, co
         k_sc_f64<<<blocks, kSCThreads, 0, s>>>(src, q, nsrc, tgt, ntgt, exclude_self, soft * soft, ke, accumulate, phi,
                                                E);
     else
-        k_sc_mixed<<<blocks, kSCThreads, 0, s>>>(hq, lo, nsrc, tgt, ntgt, exclude_self, (float)(soft * soft), ke,
-                                                 accumulate, phi, E);
+        k_sc_mixed<<<(unsigned)((ntgt + kSC2Tile - 1) / kSC2Tile), kSC2Threads, 0, s>>>(
+            hq, lo, nsrc, tgt, ntgt, exclude_self, (float)(soft * soft), ke, accumulate, phi, E);
     return cudaGetLastError();
 }
 

@@ -122,22 +122,26 @@ def test_server_argument_errors(N, ctxs):
         N.nebem_server_destroy(srv)
 
 
-def test_server_small_requests_split_by_element_chunks(N):
-    """Small mixed requests on the full THGEM cell (10 element chunks) run as one item per
-    (point block, chunk); their results equal the standalone evaluation bit for bit."""
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_server_small_requests_split_by_element_chunks(N, prec):
+    """Small requests on the full THGEM cell (10 element chunks) run as one item per
+    (point block, chunk); their results equal the standalone evaluation bit for bit.
+    Mixed requests up to 1024 points and FP64 requests up to 16384 points are split."""
     g = I.thgem()
     c = N.Context().set_geometry(g)
     c.solve(N.NEBEM_MIXED)
+    p = N.NEBEM_MIXED if prec == "mixed" else N.NEBEM_FP64
+    sizes = [1, 50, 129, 300, 1024, 1025] if prec == "mixed" else [1, 129, 700, 2000]
     srv = N.nebem_server_create([c.h])
     try:
         reqs = []
-        for k, n in enumerate([1, 50, 129, 300, 1024, 1025]):
+        for k, n in enumerate(sizes):
             pts = _request_points(g, n, 500 + k)
             phi, E = np.empty(n), np.empty((n, 3))
-            reqs.append((N.nebem_server_submit(srv, 0, pts, phi, E, N.NEBEM_MIXED), pts, phi, E))
+            reqs.append((N.nebem_server_submit(srv, 0, pts, phi, E, p), pts, phi, E))
         for rid, pts, phi, E in reqs:
             N.nebem_server_wait(srv, rid, 120000)
-            rphi, rE = c.eval(pts, N.NEBEM_MIXED)
+            rphi, rE = c.eval(pts, p)
             assert np.array_equal(phi, rphi) and np.array_equal(E, rE)
     finally:
         N.nebem_server_destroy(srv)
