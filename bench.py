@@ -34,6 +34,10 @@ FP64_SAMPLE = 19_456
 CHECK_SAMPLE = 512
 ORACLE_SAMPLE = 2_048
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) of one k_eval_far launch on the default workload (1e6 points),
+# from ncu dram__bytes_read.sum + dram__bytes_write.sum (profiles/eval_mixed_thgem.md);
+# reported only for that workload and for the kernel version it was taken on.
+FAR_TRAFFIC_BYTES_1E6 = 73.45e6 + 24.29e6
 
 
 def parse():
@@ -43,6 +47,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--points", type=int, default=N_POINTS)
+    ap.add_argument("--fp64-points", type=int, default=FP64_SAMPLE,
+                    help="sample size of the FP64-path comparison (accuracy and FP64 rate)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=40)
     ap.add_argument("--no-serving", action="store_true")
@@ -270,7 +276,7 @@ def run_native(args):
     value = total_evals / (ms * 1e-3)
 
     # ---- accuracy of the mixed path against the FP64 path, and the FP64 path's rate
-    ns = min(FP64_SAMPLE, npts)
+    ns = min(args.fp64_points, npts)
     phi64 = torch.empty(ns, dtype=torch.float64, device=dev)
     E64 = torch.empty((ns, 3), dtype=torch.float64, device=dev)
     with torch.cuda.stream(stream):
@@ -365,9 +371,11 @@ def run_native(args):
             "fp64_path": {"value": fp64_rate, "unit": "evals/s", "sample_points": ns,
                           "speedup_mixed_over_fp64": value / world / fp64_rate},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                         "frac": achieved / peak_ops, "traffic": None,
-                         "note": "FP32 lane ops (Gauss nodes x 13 + pairs x 9) per launch / event time; peak = "
-                                 "152 SMs x 128 lanes x max SM clock"},
+                         "frac": achieved / peak_ops,
+                         "traffic": FAR_TRAFFIC_BYTES_1E6 if npts == N_POINTS else None,
+                         "note": "FP32 lane ops (Gauss nodes x 13 + pairs x 12) per launch / event time; peak = "
+                                 "152 SMs x 128 lanes x max SM clock; traffic = DRAM bytes per far-kernel launch "
+                                 "(ncu, 1e6 points)"},
             "tiers": counts,
             "solve_thgem": solve,
             "serving": serving,

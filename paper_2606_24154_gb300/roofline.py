@@ -9,7 +9,7 @@ pair by its distance tier (distance to the image centroid in element circumradii
   near:                  one FP64 closed form
 Per Gauss node the FP32 arithmetic is 13 lane operations (3 differences, 3 for r^2,
 2 for w r^-1 and w r^-3 after one rsqrt, 1 for phi, 3 for E, 1 product) plus one MUFU
-rsqrt; per pair 9 (two-float difference: 6, squared distance: 3).  The counts are
+rsqrt; per pair 12 (two-float difference: 3 per axis, squared distance: 3).  The counts are
 taken on a sample of points with the same thresholds as the kernel and scaled to the
 launch.
 """
@@ -18,7 +18,7 @@ from __future__ import annotations
 import numpy as np
 
 OPS_PER_NODE = 13
-OPS_PER_PAIR = 9
+OPS_PER_PAIR = 12
 N_SM = 152
 FP32_LANES_PER_SM = 128
 MUFU_PER_SM = 16
