@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--serving-requests", type=int, default=40)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--workload", default="thgem_eval",
-                    choices=["thgem_eval", "double_thgem_solve", "space_charge", "lu", "am"])
+                    choices=["thgem_eval", "double_thgem_solve", "space_charge", "lu", "am", "fastvol"])
     return ap.parse_args()
 
 
@@ -422,12 +422,22 @@ def run_double_thgem_solve(args):
     c.close()
     err = float(np.abs(sig_m - sig_d).max() / np.abs(sig_d).max())
     n = g.n
+    oracle = None
+    if not args.no_cpu_baseline:
+        from oracle import oracle as O
+        rows = np.repeat(np.arange(4), n)
+        cols = np.tile(np.arange(n), 4)
+        frate, cores = _oracle_rate(lambda: O.fill_entries(g, rows, cols), 4 * n * g.n_images)
+        A = np.random.default_rng(0).random((2048, 2048)) + 2048 * np.eye(2048)
+        lrate, _ = _oracle_rate(lambda: O.lu_factor(A), (2.0 / 3.0) * 2048 ** 3)
+        oracle = {"fill_pairs_per_s": frate, "fill_cores": cores, "lu_flops_per_s_n2048": lrate, "lu_cores": 1,
+                  "sample": "4 full rows of the 40k matrix (all images); LU of a 2048 x 2048 matrix (one thread)"}
     best = min(r["ms_factor"] for r in res["mixed"])
     line = {"metric": "double THGEM solve: FP32 LU + FP64 refinement vs FP64 LU", "workload":
             f"double_thgem N={n} images={g.n_images}", "value": (2.0 / 3.0) * n ** 3 / (best * 1e-3) / 1e12,
             "unit": "TFLOP/s (FP32 LU, 2/3 N^3)", "sigma_rel_err_mixed_vs_fp64": err,
             "fp64_lu_tflops": (2.0 / 3.0) * n ** 3 / (res["fp64"]["ms_factor"] * 1e-3) / 1e12, "runs": res,
-            "fill_evals_per_s": n * n * g.n_images / (res["fp64"]["ms_fill"] * 1e-3)}
+            "fill_evals_per_s": n * n * g.n_images / (res["fp64"]["ms_fill"] * 1e-3), "oracle_fp64": oracle}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -476,11 +486,99 @@ def run_space_charge(args):
     out["mixed_lines"] = {"s_per_step": dt, "voxel_m": voxel, "lines": nl,
                           "line_pairs_per_step": n_car * nl,
                           "line_sum_at_carriers_s_host_api": t_sum,
+                          "line_pairs_per_s_host_api": n_car * nl / t_sum,
                           "element_evals_per_s": n_car * g.n * g.n_images / dt}
     c.close()
+    if not args.no_cpu_baseline:
+        from oracle import oracle as O
+        nt = 256
+        rate, cores = _oracle_rate(lambda: O.space_charge(pos, q, tgt=pos[:nt], soft=1e-6), nt * n_car)
+        lines = O.voxel_lines(pos, q, voxel)
+        lrate, _ = _oracle_rate(lambda: O.line_charge(lines, pos[:2048]), 2048 * len(lines))
+        out["oracle_fp64"] = {"carrier_pairs_per_s": rate, "line_pairs_per_s": lrate, "cores": cores,
+                              "sample": f"{nt} carriers x all {n_car} sources; 2048 carriers x all lines"}
     line = {"metric": "dynamic space-charge step time", "workload": f"thgem_cell N={g.n} carriers={n_car}",
             "value": out["mixed"]["s_per_step"], "unit": "s/step", "higher_is_better": False, "steps": args.steps,
             "detail": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _oracle_rate(fn, units):
+    """The FP64 oracle timed on the host cores for `units` units of work: (units/s, threads)."""
+    from oracle import oracle as O
+    O.build()
+    t = time.perf_counter()
+    fn()
+    return units / (time.perf_counter() - t), O.num_threads()
+
+
+def run_fastvol(args):
+    """FastVolume (Sec. 3.3) on the THGEM cell: a map on a rectilinear grid graded through
+    the foil (node values from the mixed evaluation), then trilinear lookups at --points
+    points in the cell; build time, lookup rate and interpolation error in the drift region
+    against the direct evaluation."""
+    import torch
+
+    from paper_2606_24154_gb300 import build as B
+    from paper_2606_24154_gb300 import inputs as I
+    from paper_2606_24154_gb300 import nebem as N
+    B.build()
+    g = I.thgem()
+    c = N.Context().set_geometry(g)
+    c.solve(N.NEBEM_MIXED)
+    p = g.pitch
+    # nodes kept off element edges and vertices (where the in-plane field diverges) by
+    # small offsets, and strictly between the electrode planes
+    ax = np.linspace(-0.5 * p, 0.5 * p, 41) + 1.3e-6
+    ay = np.linspace(-p / np.sqrt(3), p / np.sqrt(3), 47) + 0.7e-6
+    az = np.concatenate([np.linspace(g.z_range[0] + 2e-6, -0.6e-3, 30), np.linspace(-0.59e-3, 0.59e-3, 60) + 1.1e-6,
+                         np.linspace(0.6e-3, g.z_range[1] - 2e-6, 30)])
+    nodes = len(ax) * len(ay) * len(az)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    N.nebem_fastvol_build(c.h, ax, ay, az, N.NEBEM_MIXED)
+    t_build = time.perf_counter() - t
+    pts = I.cell_points(g, args.points, I.rng(1, 0))
+    d_pts = torch.from_numpy(pts).cuda()
+    d_phi = torch.empty(args.points, dtype=torch.float64, device="cuda")
+    d_E = torch.empty((args.points, 3), dtype=torch.float64, device="cuda")
+    st = torch.cuda.Stream()
+    times = []
+    for step in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        N.nebem_fastvol_eval_device(c.h, d_pts.data_ptr(), args.points, d_phi.data_ptr(), d_E.data_ptr(),
+                                    st.cuda_stream)
+        e1.record(st)
+        torch.cuda.synchronize()
+        if step >= args.warmup:
+            times.append(e0.elapsed_time(e1) * 1e-3)
+    t_look = min(times)
+    # direct evaluation of the same points (mixed) for the error and the speed-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    d_phi2 = torch.empty_like(d_phi)
+    d_E2 = torch.empty_like(d_E)
+    N.nebem_eval_device(c.h, d_pts.data_ptr(), args.points, d_phi2.data_ptr(), d_E2.data_ptr(), N.NEBEM_MIXED,
+                        st.cuda_stream)
+    e1.record(st)
+    torch.cuda.synchronize()
+    t_direct = e0.elapsed_time(e1) * 1e-3
+    phi, E, phi2, E2 = (x.cpu().numpy() for x in (d_phi, d_E, d_phi2, d_E2))
+    drift = (pts[:, 2] > 1.2e-3) & (pts[:, 2] < 3.0e-3)
+    relE = np.linalg.norm(E - E2, axis=1) / np.linalg.norm(E2, axis=1)
+    c.close()
+    line = {"metric": "FastVolume lookups", "workload": f"thgem_cell N={g.n} grid={len(ax)}x{len(ay)}x{len(az)} "
+            f"points={args.points}", "value": args.points / t_look, "unit": "points/s", "higher_is_better": True,
+            "steps": args.steps, "detail": {
+                "nodes": nodes, "build_s": t_build, "lookup_s": t_look, "direct_mixed_eval_s": t_direct,
+                "speedup_lookup_vs_direct": t_direct / t_look,
+                "drift_region_E_rel_err_median": float(np.median(relE[drift])),
+                "drift_region_E_rel_err_p99": float(np.quantile(relE[drift], 0.99)),
+                "all_points_E_rel_err_median": float(np.median(relE)),
+                "non_finite_lookups": int((~np.isfinite(E)).any(axis=1).sum())}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -525,13 +623,22 @@ def run_am(args):
         rows.append({"prim_after": pa, "s_per_map": min(times),
                      "phi_max_rel_err": float(np.abs(phi - ref[0]).max() / np.abs(ref[0]).max()),
                      "E_max_rel_err": float(np.abs(E - ref[1]).max() / np.abs(ref[1]).max())})
+    sig = c.sigma()
     c.close()
+    oracle = None
+    if not args.no_cpu_baseline:
+        from oracle import oracle as O
+        sample = pts[:32]
+        r_full, cores = _oracle_rate(lambda: O.eval_points(g, sig, sample), 32)
+        r_am, _ = _oracle_rate(lambda: O.eval_am(g, sig, g.primitives, g.prim_of, 1, sample), 32)
+        oracle = {"points_per_s_full": r_full, "points_per_s_prim_after_1": r_am, "cores": cores,
+                  "sample": "32 of the map's points"}
     full = rows[0]["s_per_map"]
     line = {"metric": "Adaptive Modelling map time", "workload":
             f"thgem_cell N={g.n} primitives={len(g.primitives)} images=121 points={args.points} mixed",
             "value": min(r["s_per_map"] for r in rows if r["prim_after"] == 1), "unit": "s/map (PrimAfter=1)",
             "higher_is_better": False, "steps": args.steps, "speedup_prim_after_1": full / rows[4]["s_per_map"],
-            "detail": rows}
+            "detail": rows, "oracle_fp64": oracle}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -571,6 +678,11 @@ def run_lu(args):
         out[name] = {"s": t, "tflops": (2.0 / 3.0) * n ** 3 / t / 1e12}
         del A
     c.close()
+    if not args.no_cpu_baseline:
+        from oracle import oracle as O
+        A = np.random.default_rng(0).random((2048, 2048)) + 2048 * np.eye(2048)
+        lrate, cores = _oracle_rate(lambda: O.lu_factor(A), (2.0 / 3.0) * 2048 ** 3)
+        out["oracle_fp64"] = {"flops_per_s": lrate, "cores": 1, "sample": "n = 2048 (the oracle's LU is one thread)"}
     line = {"metric": "dense LU factorisation", "workload": f"random n={n} (+diagonal), column-major",
             "value": out["fp32_tc"]["tflops"], "unit": "TFLOP/s (2/3 n^3)", "higher_is_better": True,
             "steps": args.steps, "detail": out}
@@ -590,6 +702,8 @@ def main():
         return run_lu(args)
     if args.workload == "am":
         return run_am(args)
+    if args.workload == "fastvol":
+        return run_fastvol(args)
     return run_native(args)
 
 

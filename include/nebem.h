@@ -332,7 +332,10 @@ int nebem_lu_factor_device_noalloc(double *d_A, int64_t n, int32_t *d_piv, void 
  * and keep the node values on the device.  One map per context; a new build replaces it.
  * The map belongs to the current charge densities: after any change of them (solve,
  * set_sigma, set_geometry, space_charge, step) lookups fail with NEBEM_BAD_STATE until it
- * is rebuilt.  Axis arrays are host memory, copied.  At most 1e8 nodes.
+ * is rebuilt.  Axis arrays are host memory, copied.  At most 1e8 nodes.  A node placed
+ * exactly on an element's edge or vertex takes the field there, which diverges
+ * logarithmically (non-finite values that reach the cells around that node): keep nodes
+ * off element boundaries, e.g. by offsetting regular grids by a small fraction.
  * For a weighting-field map, set unit voltages on the readout (nebem_set_bc), solve with
  * the retained factors and build.  Errors: NEBEM_BAD_STATE (no charge densities),
  * NEBEM_INVALID_ARG, NEBEM_TOO_LARGE, NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
