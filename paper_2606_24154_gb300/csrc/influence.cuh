@@ -15,7 +15,8 @@
 // Omega is summed over the fan triangles (0,1,2) and (0,2,3) with the Van Oosterom -
 // Strackee form tan(Omega/2) = N / D, N = 2A Y, D = R0 R1 R2 + (r0.r1) R2 + (r0.r2) R1
 // + (r1.r2) R0 -- the numerator is exact (doubled area times height), so the far field
-// of the normal component suffers no cancellation.  Within 1e-4 element radii of the
+// of the normal component suffers no cancellation.  The two half-angles of a four-sided
+// element are added as the argument of the product (D1 + i N1)(D2 + i N2) (one atan2).  Within 1e-4 element radii of the
 // plane the solid angle is instead summed over the triangles (projection, q_i, q_i+1),
 // which stays well-conditioned where the projection meets the fan diagonal.  Exactly in
 // the element's plane (Y == 0) the normal field is the principal value 0.
@@ -65,6 +66,11 @@ __device__ __forceinline__ void poly_f64(const Elem& e, double X, double Y, doub
     double om = 0.0;
     if (Y != 0.0) {
         if (fabs(Y) >= 1e-4 * e.rho) {
+            // half-angles of the fan triangles as arguments of D + i N; their sum is the
+            // argument of the product, which stays inside (-pi, pi) here (the element
+            // subtends less than a hemisphere by a margin of order 1e-4), so one atan2
+            // of the product replaces one per triangle
+            double re = 1.0, im = 0.0;
 #pragma unroll
             for (int f = 0; f < NV - 2; ++f) {
                 const int i1 = f + 1, i2 = f + 2;
@@ -72,8 +78,17 @@ __device__ __forceinline__ void poly_f64(const Elem& e, double X, double Y, doub
                 const double d02 = fma(ax[0], ax[i2], fma(az[0], az[i2], Y2));
                 const double d12 = fma(ax[i1], ax[i2], fma(az[i1], az[i2], Y2));
                 const double D = fma(R[0] * R[i1], R[i2], fma(d01, R[i2], fma(d02, R[i1], d12 * R[0])));
-                om += 2.0 * atan2(e.twoA[f] * Y, D);
+                const double Nf = e.twoA[f] * Y;
+                if (f == 0) {
+                    re = D;
+                    im = Nf;
+                } else {
+                    const double r2 = fma(re, D, -im * Nf);
+                    im = fma(re, Nf, im * D);
+                    re = r2;
+                }
             }
+            om = 2.0 * atan2(im, re);
         } else {
             // Close to the plane the fan split is ill-conditioned where the projection
             // meets the shared diagonal; split at the projection instead: triangle
