@@ -123,6 +123,116 @@ __global__ void k_scale_update(T* __restrict__ A, int64_t n, int64_t j, int64_t 
     }
 }
 
+// One launch per panel column j, fusing what would otherwise be three launches:
+//   (a) for j > k0: scale column j-1 below its diagonal and apply its rank-1 update to
+//       the panel columns (j-1, k1), each thread for its own rows i >= j;
+//   (b) the partial pivot search of column j over the same rows (so a thread reads only
+//       values it has just updated itself);
+//   (c) the last block to finish (an atomic ticket, no waiting) reduces the partial maxima,
+//       records the pivot and swaps rows j and p inside the panel columns.
+// With do_pivot = 0 only (a) runs (the launch after the panel's last column).  The
+// per-element arithmetic is that of the three separate steps, in the same order.
+template <typename T>
+__global__ void __launch_bounds__(kPivThreads) k_panel_col(T* __restrict__ A, int64_t n, int64_t j, int64_t k0,
+                                                            int64_t k1, int do_pivot, double* __restrict__ pval,
+                                                            int64_t* __restrict__ pidx, int* __restrict__ ticket,
+                                                            int32_t* __restrict__ piv, int* __restrict__ info) {
+    __shared__ T urow[64];
+    __shared__ double sv[kPivThreads];
+    __shared__ int64_t si[kPivThreads];
+    __shared__ bool last;
+    const bool update = j > k0;
+    const int64_t jm = j - 1;
+    const int w = update ? (int)(k1 - j) : 0;  // columns (j-1, k1)
+    T inv = (T)0;
+    bool ok = true;
+    if (update) {
+        for (int c = threadIdx.x; c < w; c += blockDim.x) urow[c] = A[jm + (j + c) * n];
+        const T d = A[jm + jm * n];
+        ok = d != (T)0;
+        inv = ok ? (T)1 / d : (T)0;
+    }
+    __syncthreads();
+    double best = -1.0;
+    int64_t bidx = INT64_MAX;
+    for (int64_t i = j + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (update && ok) {
+            const T l = A[i + jm * n] * inv;
+            A[i + jm * n] = l;
+            for (int c = 0; c < w; ++c) A[i + (j + c) * n] -= l * urow[c];
+        }
+        if (do_pivot) {
+            const double v = fabs((double)A[i + j * n]);
+            if (v > best || (v == best && i < bidx)) {
+                best = v;
+                bidx = i;
+            }
+        }
+    }
+    if (!do_pivot) return;
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bidx;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) {
+            const double v = sv[threadIdx.x + st];
+            const int64_t ix = si[threadIdx.x + st];
+            if (v > sv[threadIdx.x] || (v == sv[threadIdx.x] && ix < si[threadIdx.x])) {
+                sv[threadIdx.x] = v;
+                si[threadIdx.x] = ix;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        pval[blockIdx.x] = sv[0];
+        pidx[blockIdx.x] = si[0];
+        __threadfence();
+        last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    // final reduction over the blocks' partial maxima (lowest row index on ties)
+    best = -1.0;
+    bidx = INT64_MAX;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+        const double v = __ldcg(pval + b);
+        const int64_t ix = __ldcg(pidx + b);
+        if (v > best || (v == best && ix < bidx)) {
+            best = v;
+            bidx = ix;
+        }
+    }
+    sv[threadIdx.x] = best;
+    si[threadIdx.x] = bidx;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) {
+            const double v = sv[threadIdx.x + st];
+            const int64_t ix = si[threadIdx.x + st];
+            if (v > sv[threadIdx.x] || (v == sv[threadIdx.x] && ix < si[threadIdx.x])) {
+                sv[threadIdx.x] = v;
+                si[threadIdx.x] = ix;
+            }
+        }
+        __syncthreads();
+    }
+    const int64_t p = (si[0] >= j && si[0] < n) ? si[0] : j;
+    if (threadIdx.x == 0) {
+        piv[j] = (int32_t)p;
+        if (!(sv[0] > 0.0) && *info == 0) *info = (int)(j + 1);
+        *ticket = 0;
+    }
+    if (p != j) {
+        for (int64_t c = k0 + threadIdx.x; c < k1; c += blockDim.x) {
+            const T a = __ldcg(A + j + c * n);
+            A[j + c * n] = __ldcg(A + p + c * n);
+            A[p + c * n] = a;
+        }
+    }
+}
+
 // Apply the row swaps of panel rows [k0, k1) to columns outside the panel.
 template <typename T>
 __global__ void k_laswp(T* __restrict__ A, int64_t n, int64_t k0, int64_t k1, const int32_t* __restrict__ piv) {
@@ -242,7 +352,7 @@ cudaError_t gemm(int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t l
     } while (0)
 
 // work layout: [0, nb*nb) L11 inverse; [nb*nb, nb*nb + nb*n) U12 staging;
-// then kPivBlocks doubles + kPivBlocks int64 for the pivot search.
+// then kPivBlocks doubles + kPivBlocks int64 for the pivot search and one int ticket.
 template <typename T>
 cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_info, cudaStream_t s) {
     // d_info[0]: first zero pivot (1-based) or 0; d_info[1]: tensor-core update gave up
@@ -253,19 +363,20 @@ cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_inf
     size_t off = ((uintptr_t)tail + 15) & ~(uintptr_t)15;
     double* pval = reinterpret_cast<double*>(off);
     int64_t* pidx = reinterpret_cast<int64_t*>(pval + kPivBlocks);
+    int* ticket = reinterpret_cast<int*>(pidx + kPivBlocks);
+    NB_TRY(cudaMemsetAsync(ticket, 0, sizeof(int), s));
+    if (nb > 64) return cudaErrorInvalidValue;  // k_panel_col stages at most 64 row values
     for (int64_t k0 = 0; k0 < n; k0 += nb) {
         const int64_t k1 = std::min<int64_t>(n, k0 + nb);
         const int w = (int)(k1 - k0);
-        for (int64_t j = k0; j < k1; ++j) {
+        // columns k0..k1-1: update by the previous column + pivot of this one; then the
+        // last column's scaling of the rows below the panel
+        for (int64_t j = k0; j <= k1; ++j) {
+            if (j == n) break;
             const int64_t rows = n - j;
             const int pb = (int)std::min<int64_t>(kPivBlocks, (rows + kPivThreads - 1) / kPivThreads);
-            k_pivot_partial<T><<<pb, kPivThreads, 0, s>>>(A, n, j, pval, pidx);
-            k_pivot_swap<T><<<1, kPivThreads, 0, s>>>(A, n, j, k0, k1, pval, pidx, pb, piv, d_info);
-            if (j + 1 < n) {
-                const int64_t r2 = n - j - 1;
-                const int ub = (int)std::min<int64_t>(1024, (r2 + 127) / 128);
-                k_scale_update<T><<<ub, 128, sizeof(T) * nb, s>>>(A, n, j, k1);
-            }
+            k_panel_col<T><<<pb, kPivThreads, 0, s>>>(A, n, j, k0, k1, j < k1 ? 1 : 0, pval, pidx, ticket, piv,
+                                                      d_info);
         }
         NB_TRY(cudaGetLastError());
         k_laswp<T><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(A, n, k0, k1, piv);
@@ -439,8 +550,8 @@ cudaError_t launch_gather(const double* a, const int64_t* idx, int64_t n, double
 }
 
 size_t lu_work_elems(int64_t n, int nb) {
-    // L11^-1 + U12 staging + pivot partials (in bytes / 4 rounded up, covers both types)
-    return (size_t)nb * nb + (size_t)nb * (size_t)n + 16 + (size_t)kPivBlocks * 4;
+    // L11^-1 + U12 staging + pivot partials and the ticket (in bytes / 4 rounded up, covers both types)
+    return (size_t)nb * nb + (size_t)nb * (size_t)n + 16 + (size_t)kPivBlocks * 4 + 16;
 }
 
 cudaError_t lu_factor_f64(double* A, int64_t n, int32_t* piv, int nb, double* work, int* d_info, cudaStream_t s) {
