@@ -30,6 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_POINTS = 1_000_000
+HEADLINE_METRIC = "element-point influence evals/s (mixed FP32/FP64, <=1e-6 rel err vs FP64 path)"
 FP64_SAMPLE = 19_456
 CHECK_SAMPLE = 512
 ORACLE_SAMPLE = 2_048
@@ -160,11 +161,12 @@ def run_reference(args):
     per = statistics.mean(times)
     val = n * g.n * g.n_images / per
     line = {
-        "impl": "reference", "metric": "element-point influence evals/s", "value": val, "unit": "evals/s",
-        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
+        "impl": "reference", "metric": HEADLINE_METRIC, "value": val, "unit": "evals/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"thgem_cell N={g.n} images={g.n_images} points={N_POINTS} (bounded sample "
-                               f"of {n} points per step)", "precision": "fp64 oracle"},
+        "config": {"workload": f"thgem_cell N={g.n} images={g.n_images} points={N_POINTS} mixed eval",
+                   "elements": g.n, "images": g.n_images, "points_per_gpu": N_POINTS,
+                   "reference_sample": f"{n} of the points per step, FP64 oracle on the host cores"},
         "cpu_baseline": {"value": val, "unit": "evals/s", "cores": O.num_threads(), "kind": "oracle",
                          "sample": f"{n} of {N_POINTS} points per step, all {g.n} elements x {g.n_images} images"},
         "e2e": {"value": val, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -358,7 +360,7 @@ def run_native(args):
 
     if rank == 0:
         line = {
-            "metric": "element-point influence evals/s (mixed FP32/FP64, <=1e-6 rel err vs FP64 path)",
+            "metric": HEADLINE_METRIC,
             "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
