@@ -126,3 +126,38 @@ def test_pair_tiers_bit_exact_with_oracle(N):
     ref = O.pair_tiers(g, pts)
     assert np.array_equal(got, ref)
     assert set(np.unique(ref)) == {0, 1, 2, 3, 4}
+
+
+def test_mixed_eval_121_images(N):
+    """Eleven copies per lattice axis (the largest image range): mixed against the oracle."""
+    g = I.thgem(I.PlateSpec(n_phi=24, n_r=3, n_zc=1, n_zf=4), n_plane=3)
+    g.img_lo, g.img_hi = -5, 5
+    sigma = structured_sigma(g)
+    ctx = N.Context().set_geometry(g)
+    ctx.set_sigma(sigma)
+    pts = I.cell_points(g, 200, I.rng(1, 33))
+    phi, E = ctx.eval(pts, N.NEBEM_MIXED)
+    rphi, rE = O.eval_points(g, sigma, pts)
+    assert rel_norm(phi, rphi) <= TOL_MIXED and rel_vec(E, rE) <= TOL_MIXED
+    assert N.nebem_image_table(ctx.h).shape[0] == 121
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_eval_device_on_caller_stream(N, prec):
+    """nebem_eval_device on a caller's CUDA stream gives the same bits as nebem_eval."""
+    import torch
+    g = I.thgem(I.PlateSpec(n_phi=24, n_r=3, n_zc=1, n_zf=4), n_plane=3)
+    sigma = structured_sigma(g)
+    ctx = N.Context().set_geometry(g)
+    ctx.set_sigma(sigma)
+    p = N.NEBEM_FP64 if prec == "fp64" else N.NEBEM_MIXED
+    pts = I.cell_points(g, 3000, I.rng(1, 34))
+    hphi, hE = ctx.eval(pts, p)
+    st = torch.cuda.Stream()
+    d_pts = torch.from_numpy(pts).cuda()
+    d_phi = torch.full((pts.shape[0],), float("nan"), dtype=torch.float64, device="cuda")
+    d_E = torch.full((pts.shape[0], 3), float("nan"), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    N.nebem_eval_device(ctx.h, d_pts.data_ptr(), pts.shape[0], d_phi.data_ptr(), d_E.data_ptr(), p, st.cuda_stream)
+    st.synchronize()
+    assert np.array_equal(d_phi.cpu().numpy(), hphi) and np.array_equal(d_E.cpu().numpy(), hE)

@@ -321,3 +321,26 @@ def test_weighting_fields_reuse_the_factors(N):
     # each unit solve is good to the FP64 solve tolerance; the voltage-weighted sum of
     # four of them (|V| up to 1700 V, opposite signs) carries those errors scaled by |V|
     assert rel_norm(combo, sig_all) <= TOL64
+
+
+def test_quadrilateral_elements_fill_solve_eval(N):
+    """A geometry of rectangles, triangles and planar convex quadrilaterals (the THGEM's
+    primitives taken as elements, one conductor, 5 x 5 copies): FP64 fill, solve and
+    evaluation against the oracle, and the mixed evaluation within its bound."""
+    g0 = I.thgem(I.PlateSpec(n_phi=24, n_r=3, n_zc=1, n_zf=4), n_plane=3)
+    g = I.Geometry(name="thgem_primitives", elements=g0.primitives.copy(), voltages=np.array([1.0]),
+                   lattice=g0.lattice, img_lo=-2, img_hi=2, pitch=g0.pitch, z_range=g0.z_range)
+    assert (g.elements["kind"] == I.KIND_QUAD).sum() > 0
+    ctx = N.Context().set_geometry(g)
+    K = ctx.fill(N.NEBEM_FP64)
+    Kr = O.fill(g)
+    assert rel_norm(K, Kr) <= TOL64
+    sig, _, _ = ctx.solve(N.NEBEM_FP64)
+    ref, _, _ = O.solve(g)
+    assert rel_norm(sig, ref) <= TOL64
+    pts = I.cell_points(g, 200, I.rng(2, 60))
+    phi, E = ctx.eval(pts, N.NEBEM_FP64)
+    rphi, rE = O.eval_points(g, ref, pts)
+    assert rel_norm(phi, rphi) <= TOL64 and rel_norm(E, rE) <= TOL64
+    phi, E = ctx.eval(pts, N.NEBEM_MIXED)
+    assert rel_norm(phi, rphi) <= 1e-6 and rel_norm(E, rE) <= 1e-6
