@@ -3,18 +3,18 @@
 // follows each panel of the blocked factorisation (Sec. 4.1 / Alg. 1: LU; the trailing
 // update carries almost all of its 2/3 N^3 flops).
 //
-// Each CTA (128 threads) owns a 128 x 64 tile of C (two CTAs fit per SM).  The A and B
-// tiles are split into TF32 pairs (hi = x rounded to TF32, lo = x - hi) and staged in
-// shared memory in the
+// Each CTA (128 threads) owns a 128-row strip of C and walks four 64-column tiles of it
+// (two CTAs fit per SM); its A tile is staged once.  A and B are split into TF32 pairs
+// (hi = x rounded to TF32, lo = x - hi) and staged in shared memory in the
 // canonical K-major, non-swizzled UMMA layout (8-row x 16-byte core matrices; core
 // matrices adjacent along K are LBO = 128 B apart, 8-row groups SBO = 2048 B apart).
 // One elected thread issues tcgen05.mma kind::tf32 (M = 128, N = 64, K = 8 per
 // instruction) for lo*hi, hi*lo and hi*hi -- 24 instructions accumulating in FP32 in
-// tensor memory (128 lanes x 64 columns) -- then commits to an mbarrier.  Operand tiles
-// are loaded with 16 float4 loads in flight per thread when the leading dimension and
-// pointers allow it, and the C tile is fetched into registers while the MMAs run.  The
-// product is read back with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = rows of C) and
-// subtracted from C in global memory.  The three-term split keeps the product within a
+// tensor memory -- then commits to an mbarrier.  Two accumulators (128 lanes x 64 columns
+// each) alternate between the tiles, so the write-back of tile t-1 (C fetched into
+// registers, the product read with tcgen05.ld -- warp w owns TMEM lanes 32w..32w+31 = rows
+// of C -- and subtracted) overlaps the MMAs of tile t.  Operand tiles are loaded with
+// float4 loads when the leading dimension and pointers allow it.  The three-term split keeps the product within a
 // few FP32 units of roundoff, which the FP64 iterative refinement of the solve expects.
 //
 // The mbarrier wait is bounded: after kSpinLimit polls the CTA records an error flag,
@@ -33,6 +33,7 @@ constexpr uint32_t kABytes = kTM * kTK * 4;          // 32 KB per A operand tile
 constexpr uint32_t kBBytes = kTN * kTK * 4;          // 16 KB per B operand tile
 constexpr uint32_t kSmemBytes = 2 * kABytes + 2 * kBBytes + 64;
 constexpr long long kSpinLimit = 1ll << 24;
+constexpr int kTilesN = 4;                           // 64-column tiles of C per CTA
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -71,6 +72,71 @@ __device__ __forceinline__ void put_pair(unsigned char* hi, unsigned char* lo, u
     *reinterpret_cast<float*>(lo + o) = x - h;
 }
 
+// Stage B (64 k x 64 columns from column n0) as TF32 hi/lo pairs in the K-major layout.
+__device__ __forceinline__ void stage_b(const float* __restrict__ B, int64_t ldb, int64_t N, int64_t n0, bool fast,
+                                        unsigned char* b_hi, unsigned char* b_lo, int tid) {
+    if (fast) {
+        float4 vb[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int c = tid / 16 + 8 * j;
+            vb[j] = *reinterpret_cast<const float4*>(B + 4 * (tid % 16) + (n0 + c) * ldb);
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int c = tid / 16 + 8 * j, k = 4 * (tid % 16);
+            put_pair(b_hi, b_lo, kmajor_off(c, k), vb[j].x);
+            put_pair(b_hi, b_lo, kmajor_off(c, k + 1), vb[j].y);
+            put_pair(b_hi, b_lo, kmajor_off(c, k + 2), vb[j].z);
+            put_pair(b_hi, b_lo, kmajor_off(c, k + 3), vb[j].w);
+        }
+    } else {
+        for (int idx = tid; idx < kTN * kTK; idx += 128) {
+            const int k = idx % kTK, c = idx / kTK;
+            const int64_t gn = n0 + c;
+            put_pair(b_hi, b_lo, kmajor_off(c, k), (gn < N) ? B[k + gn * ldb] : 0.f);
+        }
+    }
+}
+
+// C[row, n0 .. n0+63] -= accumulator columns [col0, col0 + 64) of TMEM (warp w owns lanes
+// 32w .. 32w+31 = rows of the tile), 32 columns at a time, each C segment fetched before
+// its TMEM read.
+__device__ __forceinline__ void epilogue(float* __restrict__ C, int64_t ldc, int64_t M, int64_t N, int64_t row,
+                                         int64_t n0, uint32_t tmem, uint32_t col0, int warp) {
+#pragma unroll
+    for (int cb = 0; cb < kTN; cb += 32) {
+        float cv[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int64_t col = n0 + cb + j;
+            cv[j] = (row < M && col < N) ? C[row + col * ldc] : 0.f;
+        }
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + col0 + (uint32_t)cb;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+            "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+              "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+              "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if (row < M) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int64_t col = n0 + cb + j;
+                if (col < N) C[row + col * ldc] = cv[j] - __uint_as_float(v[j]);
+            }
+        }
+    }
+}
+
+// Each CTA stages its 128-row A tile once and walks kTilesN consecutive 64-column tiles of
+// C.  Two accumulators in tensor memory (columns 0..63 and 64..127) alternate, so while the
+// tensor core runs the MMAs of tile t the threads write tile t-1 back.
 __global__ void __launch_bounds__(128, 2) k_tc_update(int64_t M, int64_t N, const float* __restrict__ A, int64_t lda,
                                                        const float* __restrict__ B, int64_t ldb, float* __restrict__ C,
                                                        int64_t ldc, int vec, int* __restrict__ err) {
@@ -82,25 +148,20 @@ __global__ void __launch_bounds__(128, 2) k_tc_update(int64_t M, int64_t N, cons
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * kABytes + 2 * kBBytes);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 2 * kABytes + 2 * kBBytes + 16);
 
-    const int64_t m0 = (int64_t)blockIdx.x * kTM, n0 = (int64_t)blockIdx.y * kTN;
+    const int64_t m0 = (int64_t)blockIdx.x * kTM;
+    const int64_t tiles_n = (N + kTN - 1) / kTN;
+    const int64_t t0 = (int64_t)blockIdx.y * kTilesN;
+    const int nt = (int)min((int64_t)kTilesN, tiles_n - t0);
     const int tid = threadIdx.x, warp = tid >> 5;
-    const bool full = (m0 + kTM <= M) && (n0 + kTN <= N);
+    const bool full_m = m0 + kTM <= M;
 
-    // ---- stage A (128 rows x 64 k, column-major source) and B (64 k x 64 columns)
-    if (vec && full) {
-        // A: thread t takes rows 4 (t % 32) .. +3 of columns t / 32 + 4 j, j < 16
+    // ---- stage A (128 rows x 64 k, column-major source) once
+    if (vec && full_m) {
         float4 va[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             const int k = tid / 32 + 4 * j;
             va[j] = *reinterpret_cast<const float4*>(A + m0 + 4 * (tid % 32) + (int64_t)k * lda);
-        }
-        // B: thread t takes k = 4 (t % 16) .. +3 of columns t / 16 + 8 j, j < 8
-        float4 vb[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int c = tid / 16 + 8 * j;
-            vb[j] = *reinterpret_cast<const float4*>(B + 4 * (tid % 16) + (n0 + c) * ldb);
         }
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
@@ -110,114 +171,83 @@ __global__ void __launch_bounds__(128, 2) k_tc_update(int64_t M, int64_t N, cons
             put_pair(a_hi, a_lo, kmajor_off(r + 2, k), va[j].z);
             put_pair(a_hi, a_lo, kmajor_off(r + 3, k), va[j].w);
         }
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int c = tid / 16 + 8 * j, k = 4 * (tid % 16);
-            put_pair(b_hi, b_lo, kmajor_off(c, k), vb[j].x);
-            put_pair(b_hi, b_lo, kmajor_off(c, k + 1), vb[j].y);
-            put_pair(b_hi, b_lo, kmajor_off(c, k + 2), vb[j].z);
-            put_pair(b_hi, b_lo, kmajor_off(c, k + 3), vb[j].w);
-        }
     } else {
         for (int idx = tid; idx < kTM * kTK; idx += 128) {
             const int r = idx % kTM, k = idx / kTM;
             const int64_t gm = m0 + r;
             put_pair(a_hi, a_lo, kmajor_off(r, k), (gm < M) ? A[gm + (int64_t)k * lda] : 0.f);
         }
-        for (int idx = tid; idx < kTN * kTK; idx += 128) {
-            const int k = idx % kTK, c = idx / kTK;
-            const int64_t gn = n0 + c;
-            put_pair(b_hi, b_lo, kmajor_off(c, k), (gn < N) ? B[k + gn * ldb] : 0.f);
-        }
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
-    // make the generic-proxy smem writes visible to the tensor core (async proxy)
-    asm volatile("fence.proxy.async.shared::cta;");
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(kTN));
+                     "r"(2 * kTN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
-
-    // ---- issue the 24 MMAs from one thread: lo*hi, hi*lo, hi*hi over 8 K-steps of 8
-    if (tid == 0) {
-        const unsigned char* As[3] = {a_lo, a_hi, a_hi};  // lo*hi, hi*lo, hi*hi
-        const unsigned char* Bs[3] = {b_hi, b_lo, b_hi};
-        uint32_t first = 1;
-        for (int t = 0; t < 3; ++t) {
-            for (int ks = 0; ks < kTK / 8; ++ks) {
-                // one K-step of 8 TF32 = two core matrices along K = 2 * LBO bytes
-                const uint64_t ad = make_desc(smem_u32(As[t]) + (uint32_t)ks * 2u * kLBO);
-                const uint64_t bd = make_desc(smem_u32(Bs[t]) + (uint32_t)ks * 2u * kLBO);
-                const uint32_t acc = first ? 0u : 1u;
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
-                first = 0;
-            }
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(mbar)));
-    }
-
-    // ---- fetch this thread's row of the C tile while the MMAs run
     const int64_t row = m0 + warp * 32 + (tid & 31);
-    float cv[kTN];
-#pragma unroll
-    for (int j = 0; j < kTN; ++j) {
-        const int64_t col = n0 + j;
-        cv[j] = (row < M && col < N) ? C[row + col * ldc] : 0.f;
-    }
 
-    // ---- bounded wait for the MMAs (phase 0)
-    uint32_t done = 0;
-    for (long long it = 0; it < kSpinLimit && !done; ++it) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(smem_u32(mbar)));
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    const int ok = __syncthreads_and((int)done);
-    if (!ok) {
-        if (tid == 0) atomicExch(err, 1);
-    } else {
-        // ---- epilogue: warp w reads TMEM lanes 32w + (0..31) = rows of the tile, 32 columns
-        //      at a time, and stores C - product (consecutive rows per column: coalesced)
-#pragma unroll
-        for (int cb = 0; cb < kTN; cb += 32) {
-            uint32_t v[32];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-                "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
-            if (row < M) {
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int64_t col = n0 + cb + j;
-                    if (col < N) C[row + col * ldc] = cv[cb + j] - __uint_as_float(v[j]);
+    int ok = 1;
+    for (int t = 0; t < nt; ++t) {
+        const int64_t n0 = (t0 + t) * kTN;
+        // the MMAs of tile t-1 have completed (waited below), so B may be overwritten
+        stage_b(B, ldb, N, n0, vec && full_m && (n0 + kTN <= N), b_hi, b_lo, tid);
+        // make the generic-proxy smem writes visible to the tensor core (async proxy)
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t col0 = (uint32_t)(t & 1) * (uint32_t)kTN;
+        // ---- 24 MMAs from one thread into accumulator t & 1: lo*hi, hi*lo, hi*hi, 8 K-steps
+        if (tid == 0) {
+            const unsigned char* As[3] = {a_lo, a_hi, a_hi};
+            const unsigned char* Bs[3] = {b_hi, b_lo, b_hi};
+            uint32_t first = 1;
+            for (int q = 0; q < 3; ++q) {
+                for (int ks = 0; ks < kTK / 8; ++ks) {
+                    const uint64_t ad = make_desc(smem_u32(As[q]) + (uint32_t)ks * 2u * kLBO);
+                    const uint64_t bd = make_desc(smem_u32(Bs[q]) + (uint32_t)ks * 2u * kLBO);
+                    const uint32_t acc = first ? 0u : 1u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + col0),
+                        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+                    first = 0;
                 }
             }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(mbar)));
         }
+        // ---- write back tile t-1 while the tensor core works on tile t
+        if (t > 0) epilogue(C, ldc, M, N, row, n0 - kTN, tmem, (uint32_t)((t - 1) & 1) * (uint32_t)kTN, warp);
+        // ---- bounded wait for the MMAs of tile t (the t-th completion: parity t & 1)
+        uint32_t done = 0;
+        const uint32_t parity = (uint32_t)(t & 1);
+        for (long long it = 0; it < kSpinLimit && !done; ++it) {
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(done)
+                : "r"(smem_u32(mbar)), "r"(parity));
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        ok = __syncthreads_and((int)done);
+        if (!ok) break;
+    }
+    if (!ok) {
+        if (tid == 0) atomicExch(err, 1);
+    } else if (nt > 0) {
+        epilogue(C, ldc, M, N, row, (t0 + nt - 1) * kTN, tmem, (uint32_t)((nt - 1) & 1) * (uint32_t)kTN, warp);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTN));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTN));
 }
 
 }  // namespace
@@ -233,7 +263,8 @@ cudaError_t tc_update_f32(int64_t M, int64_t N, const float* A, int64_t lda, con
     }
     // vector loads need 16-byte aligned columns
     const int vec = (lda % 4 == 0) && (ldb % 4 == 0) && (((uintptr_t)A & 15) == 0) && (((uintptr_t)B & 15) == 0);
-    dim3 grid((unsigned)((M + kTM - 1) / kTM), (unsigned)((N + kTN - 1) / kTN));
+    const int64_t tiles_n = (N + kTN - 1) / kTN;
+    dim3 grid((unsigned)((M + kTM - 1) / kTM), (unsigned)((tiles_n + kTilesN - 1) / kTilesN));
     k_tc_update<<<grid, 128, kSmemBytes, s>>>(M, N, A, lda, B, ldb, C, ldc, vec, err);
     return cudaGetLastError();
 }
