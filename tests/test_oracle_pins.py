@@ -781,3 +781,41 @@ def test_am_unassigned_elements_and_bad_tiling():
     bad[0] = bad[1] if bad[1] != bad[0] else bad[0] + 1
     with pytest.raises(ValueError):
         O.eval_am(g, sigma, g.primitives, bad, 0, pts)
+
+
+def test_thgem_inversion_symmetry():
+    """The rhombic 5 x 5 image set {k1 a1 + k2 a2} is symmetric under (x, y) -> (-x, -y),
+    and so is the THGEM mesh (96 sectors): sigma of an element equals sigma of its rotated
+    partner, Phi(-x, -y, z) = Phi(x, y, z) and (E_x, E_y) change sign.  (The x and y
+    mirrors map the rhombus to another rhombus, so they are not symmetries here.)"""
+    g = I.thgem(I.PlateSpec(n_phi=24, n_r=3, n_zc=1, n_zf=4), n_plane=3)
+    sigma, _, _ = O.solve(g)
+    c, _, _ = O.centroids(g)
+    flip = c * np.array([-1.0, -1.0, 1.0])
+    # partner of every element: the one whose centroid is the rotated centroid
+    d = np.linalg.norm(flip[:, None, :] - c[None, :, :], axis=2)
+    partner = d.argmin(1)
+    assert d[np.arange(g.n), partner].max() < 1e-12
+    # rounding of the FP64 solve (condition number ~1e4) allows ~1e-11; a wrong image index
+    # or sign breaks the symmetry at the 1e-3 level
+    assert np.abs(sigma[partner] - sigma).max() <= 1e-9 * np.abs(sigma).max()
+    pts = I.cell_points(g, 20, I.rng(0, 63))
+    p1, E1 = O.eval_points(g, sigma, pts)
+    p2, E2 = O.eval_points(g, sigma, pts * np.array([-1.0, -1.0, 1.0]))
+    assert np.abs(p1 - p2).max() <= 1e-9 * np.abs(p1).max()
+    assert np.abs(E1 * np.array([-1.0, -1.0, 1.0]) - E2).max() <= 1e-9 * np.abs(E1).max()
+
+
+def test_two_carriers_coulomb():
+    """Two softened point charges: phi = ke q / sqrt(r^2 + s^2), E = ke q d / (r^2 + s^2)^1.5."""
+    q = np.array([2.0e-15, -3.0e-15])
+    pos = np.array([[0.0, 0.0, 0.0], [3e-6, -4e-6, 12e-6]])
+    s = 1e-6
+    phi, E = O.space_charge(pos, q, soft=s)
+    d = pos[0] - pos[1]
+    r2 = d @ d + s * s
+    ke = O.ke()
+    assert abs(phi[0] - ke * q[1] / np.sqrt(r2)) <= 1e-15 * abs(phi[0])
+    assert np.abs(E[0] - ke * q[1] * d / r2 ** 1.5).max() <= 1e-14 * np.abs(E[0]).max()
+    assert abs(phi[1] - ke * q[0] / np.sqrt(r2)) <= 1e-15 * abs(phi[1])
+    assert np.abs(E[1] + ke * q[0] * d / r2 ** 1.5).max() <= 1e-14 * np.abs(E[1]).max()
