@@ -389,7 +389,11 @@ typedef struct nebem_server_options {
 int nebem_server_default_options(nebem_server_options *opt);
 
 /* Create a server over n_ctx solved contexts (all on one device; they must stay alive
- * until nebem_server_destroy).  Geometry index g in submit refers to ctxs[g]. */
+ * until nebem_server_destroy).  Geometry index g in submit refers to ctxs[g].  The server
+ * evaluates the elements' field (with images) from the context's current charge
+ * densities; a context with known charges (nebem_space_charge) or with Adaptive
+ * Modelling on (nebem_set_primitives) is refused with NEBEM_BAD_STATE, here and at
+ * submit, as is a context whose densities have been invalidated. */
 int nebem_server_create(nebem_server **out, nebem_ctx *const *ctxs, int32_t n_ctx,
                         const nebem_server_options *opt);
 

@@ -55,7 +55,7 @@ Ctx::~Ctx() {
                       &d_x, &d_r, &d_r32, &d_small, &d_pts, &d_phi, &d_E, &d_car, &d_q, &d_car2, &d_sc_tgt,
                       &d_sc_phi, &d_sc_E, &d_scratch, &d_cjk, &d_cell_start, &d_cell_items, &d_fv_ax, &d_fv_ay, &d_fv_az, &d_fv_phi,
                       &d_fv_E, &d_vkeys, &d_vflags, &d_vbsum, &d_vpartial, &d_vgrid, &d_lines, &d_linesf, &d_line_vox,
-                      &d_am_start, &d_am_items, &d_am_elarea, &d_am_parea, &d_am_tmp})
+                      &d_am_start, &d_am_items, &d_am_elarea, &d_am_parea, &d_am_tmp, &d_perm64, &d_perm32, &d_swork})
         b->release();
     am_near.release_all();
     am_far.release_all();
@@ -414,7 +414,16 @@ int nebem_lu_solve_device(nebem_ctx* ctx, const double* d_LU, int64_t n, const i
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     CK(cudaSetDevice(c->device));
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
-    CK(lu_solve_f64(d_LU, n, d_piv, d_b, s));
+    // stream-ordered scratch: calls in flight on different streams never share it
+    const size_t wbytes = lu_solve_work_bytes(n, sizeof(double));
+    void* scratch = nullptr;
+    CK(cudaMallocAsync(&scratch, wbytes + sizeof(int32_t) * (size_t)n + 256, s));
+    int32_t* perm = reinterpret_cast<int32_t*>(static_cast<char*>(scratch) + ((wbytes + 255) & ~(size_t)255));
+    cudaError_t e = lu_make_perm(d_piv, n, perm, s);
+    if (e == cudaSuccess) e = lu_solve_f64(d_LU, n, perm, d_b, scratch, s);
+    const cudaError_t ef = cudaFreeAsync(scratch, s);
+    if (e != cudaSuccess) return cuda_fail(e, "lu_solve_f64");
+    CK(ef);
     return NEBEM_OK;
 }
 

@@ -75,6 +75,7 @@ struct Ctx {
 
     // matrix and factors
     DevBuf d_K, d_LU64, d_LU32, d_piv64, d_piv32, d_work;
+    DevBuf d_perm64, d_perm32, d_swork;  // pivot permutations, solve / residual work space
     bool K_valid = false, fac64_valid = false, fac32_valid = false;
     DevBuf d_b, d_x, d_r, d_r32, d_small;
 

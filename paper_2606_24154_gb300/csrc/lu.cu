@@ -404,100 +404,151 @@ cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_inf
 }
 
 // ---------------------------------------------------------------- triangular solves
-constexpr int kTB = 64;  // solve block
+constexpr int kTB = 64;          // solve block
+constexpr int kSweepThreads = 128;
+constexpr int kResRows = 256;    // residual: rows per CTA
+constexpr int kResChunk = 2048;  // residual: columns per partial sum
 
-// b[perm] gather is done by applying swaps sequentially (single thread; n swaps).
-__global__ void k_apply_piv_f64(double* b, int64_t n, const int32_t* piv) {
+// Row permutation of the pivots: applying the swaps (k, piv[k]), k = 0..n-1, to b gives
+// b'[i] = b[perm[i]].  The swaps are sequential; they run on an index array in shared
+// memory (one thread) when it fits, else in global memory.
+__global__ void k_make_perm_smem(const int32_t* __restrict__ piv, int64_t n, int32_t* __restrict__ perm) {
+    extern __shared__ int32_t sp[];
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) sp[i] = (int32_t)i;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int64_t k = 0; k < n; ++k) {
+            const int32_t p = (piv[k] >= k && piv[k] < n) ? piv[k] : (int32_t)k;  // caller pivots: stay in range
+            if (p != k) {
+                const int32_t t = sp[k];
+                sp[k] = sp[p];
+                sp[p] = t;
+            }
+        }
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) perm[i] = sp[i];
+}
+
+__global__ void k_make_perm_global(const int32_t* __restrict__ piv, int64_t n, int32_t* __restrict__ perm) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int64_t i = 0; i < n; ++i) perm[i] = (int32_t)i;
     for (int64_t k = 0; k < n; ++k) {
-        const int64_t p = piv[k];
+        const int32_t p = (piv[k] >= k && piv[k] < n) ? piv[k] : (int32_t)k;
         if (p != k) {
-            const double t = b[k];
-            b[k] = b[p];
-            b[p] = t;
+            const int32_t t = perm[k];
+            perm[k] = perm[p];
+            perm[p] = t;
         }
     }
 }
-__global__ void k_apply_piv_f32(float* b, int64_t n, const int32_t* piv) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    for (int64_t k = 0; k < n; ++k) {
-        const int64_t p = piv[k];
-        if (p != k) {
-            const float t = b[k];
-            b[k] = b[p];
-            b[p] = t;
-        }
-    }
-}
 
-// Solve the diagonal block [r0, r1) of L (unit lower, lower=1) or U (upper, lower=0) in place.
 template <typename T>
-__global__ void k_trsv_diag(const T* __restrict__ LU, int64_t n, int64_t r0, int64_t r1, T* __restrict__ b,
-                            int lower) {
+__global__ void k_permute(const T* __restrict__ b, const int32_t* __restrict__ perm, int64_t n, T* __restrict__ y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = b[perm[i]];
+}
+
+template <typename T>
+__global__ void k_copy_vec(const T* __restrict__ a, int64_t n, T* __restrict__ b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+
+// One block row of a triangular sweep.  Every CTA stages the diagonal block in shared
+// memory and solves it by substitution (one warp, lanes in step with __syncwarp; the
+// operation order of a plain column-oriented substitution), from the untouched right-hand
+// side block R[r0:r1); CTA 0 stores the block's solution to X[r0:r1); then each CTA
+// updates its share of the rows still to be solved: R[r] -= LU[r, r0:r1) x, rows [r1, n)
+// for the lower (unit-diagonal L) sweep, [0, r0) for the upper (U) one.
+template <typename T>
+__global__ void __launch_bounds__(kSweepThreads) k_sweep_block(const T* __restrict__ LU, int64_t n, int64_t r0,
+                                                               int64_t r1, int lower, T* __restrict__ R,
+                                                               T* __restrict__ X) {
+    __shared__ T D[kTB][kTB + 1];
     __shared__ T x[kTB];
     const int w = (int)(r1 - r0);
-    if (threadIdx.x < w) x[threadIdx.x] = b[r0 + threadIdx.x];
+    for (int idx = threadIdx.x; idx < w * w; idx += kSweepThreads) {
+        const int r = idx % w, c = idx / w;
+        D[r][c] = LU[(r0 + r) + (r0 + c) * n];
+    }
+    if (threadIdx.x < w) x[threadIdx.x] = R[r0 + threadIdx.x];
     __syncthreads();
-    if (lower) {
-        for (int c = 0; c < w; ++c) {
-            const T xc = x[c];
-            if (threadIdx.x > c && threadIdx.x < w) x[threadIdx.x] -= LU[(r0 + threadIdx.x) + (r0 + c) * n] * xc;
-            __syncthreads();
-        }
-    } else {
-        for (int c = w - 1; c >= 0; --c) {
-            if (threadIdx.x == c) x[c] = x[c] / LU[(r0 + c) + (r0 + c) * n];
-            __syncthreads();
-            const T xc = x[c];
-            if (threadIdx.x < c) x[threadIdx.x] -= LU[(r0 + threadIdx.x) + (r0 + c) * n] * xc;
-            __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        if (lower) {
+            for (int c = 0; c < w; ++c) {
+                const T xc = x[c];
+                for (int r = lane; r < w; r += 32)
+                    if (r > c) x[r] -= D[r][c] * xc;
+                __syncwarp();
+            }
+        } else {
+            for (int c = w - 1; c >= 0; --c) {
+                if (lane == (c & 31)) x[c] = x[c] / D[c][c];
+                __syncwarp();
+                const T xc = x[c];
+                for (int r = lane; r < c; r += 32) x[r] -= D[r][c] * xc;
+                __syncwarp();
+            }
         }
     }
-    if (threadIdx.x < w) b[r0 + threadIdx.x] = x[threadIdx.x];
-}
-
-// b[rows] -= LU[rows, c0:c1] * b[c0:c1] for rows in [q0, q1).
-template <typename T>
-__global__ void k_trsv_update(const T* __restrict__ LU, int64_t n, int64_t c0, int64_t c1, int64_t q0, int64_t q1,
-                              T* __restrict__ b) {
-    __shared__ T xs[kTB];
-    const int w = (int)(c1 - c0);
-    if (threadIdx.x < w) xs[threadIdx.x] = b[c0 + threadIdx.x];
     __syncthreads();
-    const int64_t r = q0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0 && threadIdx.x < w) X[r0 + threadIdx.x] = x[threadIdx.x];
+    const int64_t q0 = lower ? r1 : 0, q1 = lower ? n : r0;
+    const int64_t r = q0 + (int64_t)blockIdx.x * kSweepThreads + threadIdx.x;
     if (r >= q1) return;
-    T s = (T)0;
-    for (int c = 0; c < w; ++c) s = fma(LU[r + (c0 + c) * n], xs[c], s);
-    b[r] -= s;
+    T acc = (T)0;
+    for (int c = 0; c < w; ++c) acc = fma(LU[r + (r0 + c) * n], x[c], acc);
+    R[r] -= acc;
 }
 
 template <typename T>
-cudaError_t lu_solve(const T* LU, int64_t n, const int32_t* piv, T* b, cudaStream_t s) {
+cudaError_t lu_solve(const T* LU, int64_t n, const int32_t* perm, T* b, T* work, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    if constexpr (sizeof(T) == 8)
-        k_apply_piv_f64<<<1, 1, 0, s>>>(reinterpret_cast<double*>(b), n, piv);
-    else
-        k_apply_piv_f32<<<1, 1, 0, s>>>(reinterpret_cast<float*>(b), n, piv);
-    for (int64_t r0 = 0; r0 < n; r0 += kTB) {
-        const int64_t r1 = std::min<int64_t>(n, r0 + kTB);
-        k_trsv_diag<T><<<1, kTB, 0, s>>>(LU, n, r0, r1, b, 1);
-        if (r1 < n) k_trsv_update<T><<<(unsigned)((n - r1 + 127) / 128), 128, 0, s>>>(LU, n, r0, r1, r1, n, b);
+    const int64_t nblk = (n + kTB - 1) / kTB;
+    T* y = work;
+    const unsigned g = (unsigned)((n + 255) / 256);
+    k_permute<T><<<g, 256, 0, s>>>(b, perm, n, y);
+    // forward sweep: R = y (its rows below each block updated), block solutions into b
+    for (int64_t k = 0; k < nblk; ++k) {
+        const int64_t r0 = k * kTB, r1 = std::min<int64_t>(n, r0 + kTB);
+        const int64_t rows = n - r1;
+        const unsigned grid = (unsigned)std::max<int64_t>(1, (rows + kSweepThreads - 1) / kSweepThreads);
+        k_sweep_block<T><<<grid, kSweepThreads, 0, s>>>(LU, n, r0, r1, 1, y, b);
     }
-    const int64_t last = ((n - 1) / kTB) * kTB;
-    for (int64_t r0 = last; r0 >= 0; r0 -= kTB) {
-        const int64_t r1 = std::min<int64_t>(n, r0 + kTB);
-        k_trsv_diag<T><<<1, kTB, 0, s>>>(LU, n, r0, r1, b, 0);
-        if (r0 > 0) k_trsv_update<T><<<(unsigned)((r0 + 127) / 128), 128, 0, s>>>(LU, n, r0, r1, 0, r0, b);
+    // backward sweep: R = b (its rows above each block updated), block solutions into y
+    for (int64_t k = nblk - 1; k >= 0; --k) {
+        const int64_t r0 = k * kTB, r1 = std::min<int64_t>(n, r0 + kTB);
+        const unsigned grid = (unsigned)std::max<int64_t>(1, (r0 + kSweepThreads - 1) / kSweepThreads);
+        k_sweep_block<T><<<grid, kSweepThreads, 0, s>>>(LU, n, r0, r1, 0, b, y);
     }
+    k_copy_vec<T><<<g, 256, 0, s>>>(y, n, b);
     return cudaGetLastError();
 }
 
-__global__ void k_residual(const double* __restrict__ K, int64_t n, const double* __restrict__ x,
-                           const double* __restrict__ b, double* __restrict__ r) {
+// r = b - K x for column-major K: partial sums over column chunks of kResChunk (one CTA per
+// rows x chunk), then the chunks added in order per row.
+__global__ void __launch_bounds__(kResRows) k_residual_partial(const double* __restrict__ K, int64_t n,
+                                                               const double* __restrict__ x,
+                                                               double* __restrict__ part) {
+    const int64_t i = (int64_t)blockIdx.x * kResRows + threadIdx.x;
+    const int64_t j0 = (int64_t)blockIdx.y * kResChunk, j1 = min(n, j0 + (int64_t)kResChunk);
+    __shared__ double xs[kResChunk];
+    for (int64_t j = j0 + threadIdx.x; j < j1; j += kResRows) xs[j - j0] = x[j];
+    __syncthreads();
+    if (i >= n) return;
+    double s = 0.0;
+    for (int64_t j = j0; j < j1; ++j) s = fma(K[i + j * n], xs[j - j0], s);
+    part[(int64_t)blockIdx.y * n + i] = s;
+}
+
+__global__ void k_residual_final(const double* __restrict__ part, int64_t nchunk, int64_t n,
+                                 const double* __restrict__ b, double* __restrict__ r) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double s = 0.0;
-    for (int64_t j = 0; j < n; ++j) s = fma(K[i + j * n], x[j], s);
+    for (int64_t c = 0; c < nchunk; ++c) s += part[c * n + i];
     r[i] = b[i] - s;
 }
 
@@ -560,15 +611,39 @@ cudaError_t lu_factor_f64(double* A, int64_t n, int32_t* piv, int nb, double* wo
 cudaError_t lu_factor_f32(float* A, int64_t n, int32_t* piv, int nb, float* work, int* d_info, cudaStream_t s) {
     return lu_factor<float>(A, n, piv, nb, work, d_info, s);
 }
-cudaError_t lu_solve_f64(const double* LU, int64_t n, const int32_t* piv, double* b, cudaStream_t s) {
-    return lu_solve<double>(LU, n, piv, b, s);
+size_t lu_solve_work_bytes(int64_t n, size_t tsize) { return tsize * (size_t)n + 256; }
+
+size_t residual_work_bytes(int64_t n) {
+    return sizeof(double) * (size_t)((n + kResChunk - 1) / kResChunk) * (size_t)n + 256;
 }
-cudaError_t lu_solve_f32(const float* LU, int64_t n, const int32_t* piv, float* b, cudaStream_t s) {
-    return lu_solve<float>(LU, n, piv, b, s);
-}
-cudaError_t gemv_residual(const double* K, int64_t n, const double* x, const double* b, double* r, cudaStream_t s) {
+
+cudaError_t lu_make_perm(const int32_t* piv, int64_t n, int32_t* perm, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    k_residual<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(K, n, x, b, r);
+    const size_t bytes = sizeof(int32_t) * (size_t)n;
+    if (bytes <= 200 * 1024) {
+        // set for the current device on every call (an attribute is per device)
+        NB_TRY(cudaFuncSetAttribute(k_make_perm_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        k_make_perm_smem<<<1, 1024, bytes, s>>>(piv, n, perm);
+    } else {
+        k_make_perm_global<<<1, 1, 0, s>>>(piv, n, perm);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t lu_solve_f64(const double* LU, int64_t n, const int32_t* perm, double* b, void* work, cudaStream_t s) {
+    return lu_solve<double>(LU, n, perm, b, static_cast<double*>(work), s);
+}
+cudaError_t lu_solve_f32(const float* LU, int64_t n, const int32_t* perm, float* b, void* work, cudaStream_t s) {
+    return lu_solve<float>(LU, n, perm, b, static_cast<float*>(work), s);
+}
+cudaError_t gemv_residual(const double* K, int64_t n, const double* x, const double* b, double* r, void* work,
+                          cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int64_t nchunk = (n + kResChunk - 1) / kResChunk;
+    double* part = static_cast<double*>(work);
+    dim3 grid((unsigned)((n + kResRows - 1) / kResRows), (unsigned)nchunk);
+    k_residual_partial<<<grid, kResRows, 0, s>>>(K, n, x, part);
+    k_residual_final<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, nchunk, n, b, r);
     return cudaGetLastError();
 }
 cudaError_t copy_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s) {

@@ -255,12 +255,9 @@ __global__ void __launch_bounds__(128, 2) k_tc_update(int64_t M, int64_t N, cons
 cudaError_t tc_update_f32(int64_t M, int64_t N, const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
                           int64_t ldc, int* err, cudaStream_t s) {
     if (M <= 0 || N <= 0) return cudaSuccess;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // set for the current device on every call (an attribute is per device)
+    cudaError_t e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
     // vector loads need 16-byte aligned columns
     const int vec = (lda % 4 == 0) && (ldb % 4 == 0) && (((uintptr_t)A & 15) == 0) && (((uintptr_t)B & 15) == 0);
     const int64_t tiles_n = (N + kTN - 1) / kTN;

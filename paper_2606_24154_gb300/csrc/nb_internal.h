@@ -123,11 +123,17 @@ cudaError_t lu_factor_f64(double* A, int64_t n, int32_t* piv, int nb, double* wo
 cudaError_t lu_factor_f32(float* A, int64_t n, int32_t* piv, int nb, float* work, int* d_info,
                           cudaStream_t s);
 size_t lu_work_elems(int64_t n, int nb);
-cudaError_t lu_solve_f64(const double* LU, int64_t n, const int32_t* piv, double* b, cudaStream_t s);
-cudaError_t lu_solve_f32(const float* LU, int64_t n, const int32_t* piv, float* b, cudaStream_t s);
+// Solves with the factors: perm from lu_make_perm (b'[i] = b[perm[i]] applies the pivot
+// swaps), work of lu_solve_work_bytes(n, sizeof(T)) bytes (16-byte aligned).
+cudaError_t lu_make_perm(const int32_t* piv, int64_t n, int32_t* perm, cudaStream_t s);
+size_t lu_solve_work_bytes(int64_t n, size_t tsize);
+cudaError_t lu_solve_f64(const double* LU, int64_t n, const int32_t* perm, double* b, void* work, cudaStream_t s);
+cudaError_t lu_solve_f32(const float* LU, int64_t n, const int32_t* perm, float* b, void* work, cudaStream_t s);
 cudaError_t convert_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
-cudaError_t gemv_residual(const double* K, int64_t n, const double* x, const double* b, double* r,
-                          cudaStream_t s);  // r = b - K x
+// r = b - K x; work of residual_work_bytes(n) bytes
+size_t residual_work_bytes(int64_t n);
+cudaError_t gemv_residual(const double* K, int64_t n, const double* x, const double* b, double* r, void* work,
+                          cudaStream_t s);
 cudaError_t ir_update(double* x, const float* d, int64_t n, double* d_norms, cudaStream_t s);
 cudaError_t copy_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
 cudaError_t launch_gather(const double* a, const int64_t* idx, int64_t n, double* out, cudaStream_t s);

@@ -274,6 +274,9 @@ int nebem_server_create(nebem_server** out, nebem_ctx* const* ctxs, int32_t n_ct
         Ctx* c = reinterpret_cast<Ctx*>(ctxs[i]);
         if (!c) return fail(NEBEM_INVALID_ARG, "NULL context");
         if (!c->sigma_valid) return fail(NEBEM_BAD_STATE, "context " + std::to_string(i) + " has no charge densities");
+        if (c->n_car > 0 || c->am_on)
+            return fail(NEBEM_BAD_STATE, "context " + std::to_string(i) +
+                                             " has known charges or Adaptive Modelling, which the server does not apply");
         if (c->device != reinterpret_cast<Ctx*>(ctxs[0])->device)
             return fail(NEBEM_INVALID_ARG, "all contexts must share one device");
         cs.push_back(c);
@@ -342,6 +345,12 @@ int nebem_server_submit(nebem_server* srv, int32_t geometry, const double* pts, 
     if (!srv || !req_id) return fail(NEBEM_INVALID_ARG, "NULL argument");
     Server* s = reinterpret_cast<Server*>(srv);
     if (geometry < 0 || geometry >= (int32_t)s->ctxs.size()) return fail(NEBEM_INVALID_ARG, "bad geometry index");
+    {
+        const Ctx* c = s->ctxs[geometry];
+        if (!c->sigma_valid) return fail(NEBEM_BAD_STATE, "the geometry's charge densities are no longer valid");
+        if (c->n_car > 0 || c->am_on)
+            return fail(NEBEM_BAD_STATE, "the geometry has known charges or Adaptive Modelling, which the server does not apply");
+    }
     if (n <= 0 || !pts) return fail(NEBEM_INVALID_ARG, "need n > 0 points");
     if (precision != NEBEM_FP64 && precision != NEBEM_MIXED) return fail(NEBEM_INVALID_ARG, "bad precision");
     if (n > s->opt.arena_points) return fail(NEBEM_TOO_LARGE, "request larger than the point arena");

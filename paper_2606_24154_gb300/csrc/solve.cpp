@@ -59,6 +59,8 @@ int ensure_factors(Ctx* c, int precision, double* ms) {
         if (rc) return rc;
         CK(cudaMemcpy(&h_info, c->d_small.ptr, sizeof(int), cudaMemcpyDeviceToHost));
         if (h_info) return fail(NEBEM_SINGULAR, "zero pivot at column " + std::to_string(h_info - 1));
+        CK(c->d_perm64.ensure(sizeof(int32_t) * n));
+        CK(lu_make_perm(c->d_piv64.as<int32_t>(), n, c->d_perm64.as<int32_t>(), c->stream));
         c->fac64_valid = true;
     } else {
         if (c->fac32_valid) return 0;
@@ -77,6 +79,8 @@ int ensure_factors(Ctx* c, int precision, double* ms) {
         h_info = h2[0];
         if (h2[1]) return fail(NEBEM_TIMEOUT, "tensor-core trailing update: bounded wait gave up");
         if (h_info) return fail(NEBEM_SINGULAR, "zero pivot at column " + std::to_string(h_info - 1));
+        CK(c->d_perm32.ensure(sizeof(int32_t) * n));
+        CK(lu_make_perm(c->d_piv32.as<int32_t>(), n, c->d_perm32.as<int32_t>(), c->stream));
         c->fac32_valid = true;
     }
     return 0;
@@ -107,11 +111,13 @@ int solve_with_factors(Ctx* c, int precision, nebem_solve_info* info) {
     double* b = c->d_b.as<double>();
     double* r = c->d_r.as<double>();
     double* norms = reinterpret_cast<double*>(c->d_small.as<char>() + 64);
+    CK(c->d_swork.ensure(std::max(lu_solve_work_bytes(n, sizeof(double)), residual_work_bytes(n))));
+    void* work = c->d_swork.ptr;
     CK(cudaEventRecord(c->ev0, c->stream));
     int status = 0;
     if (precision == NEBEM_FP64) {
         CK(cudaMemcpyAsync(x, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
-        CK(lu_solve_f64(c->d_LU64.as<double>(), n, c->d_piv64.as<int32_t>(), x, c->stream));
+        CK(lu_solve_f64(c->d_LU64.as<double>(), n, c->d_perm64.as<int32_t>(), x, work, c->stream));
     } else {
         CK(c->d_r32.ensure(sizeof(float) * n));
         float* d32 = c->d_r32.as<float>();
@@ -122,14 +128,14 @@ int solve_with_factors(Ctx* c, int precision, nebem_solve_info* info) {
         status = NEBEM_NOT_CONVERGED;
         for (it = 1; it <= c->opt.ir_max_iter; ++it) {
             CK(copy_f64_to_f32(r, d32, n, c->stream));
-            CK(lu_solve_f32(c->d_LU32.as<float>(), n, c->d_piv32.as<int32_t>(), d32, c->stream));
+            CK(lu_solve_f32(c->d_LU32.as<float>(), n, c->d_perm32.as<int32_t>(), d32, work, c->stream));
             CK(ir_update(x, d32, n, norms, c->stream));
             double h[2];
             CK(cudaMemcpyAsync(h, norms, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
             CK(cudaStreamSynchronize(c->stream));
             corr = (h[1] > 0.0) ? h[0] / h[1] : 0.0;
             if (!std::isfinite(corr)) break;
-            CK(gemv_residual(c->d_K.as<double>(), n, x, b, r, c->stream));
+            CK(gemv_residual(c->d_K.as<double>(), n, x, b, r, work, c->stream));
             if (corr <= c->opt.ir_tol) {
                 status = 0;
                 break;
@@ -145,7 +151,7 @@ int solve_with_factors(Ctx* c, int precision, nebem_solve_info* info) {
     if (rc) return rc;
     if (info) info->ms_solve = ms;
     // residual diagnostic ||K x - b||_inf / (||K||_inf-ish ||x||_inf)
-    CK(gemv_residual(c->d_K.as<double>(), n, x, b, r, c->stream));
+    CK(gemv_residual(c->d_K.as<double>(), n, x, b, r, work, c->stream));
     CK(vec_absmax(r, n, norms, c->stream));
     CK(vec_absmax(x, n, norms + 1, c->stream));
     double h[2];

@@ -145,3 +145,29 @@ def test_server_small_requests_split_by_element_chunks(N, prec):
             assert np.array_equal(phi, rphi) and np.array_equal(E, rE)
     finally:
         N.nebem_server_destroy(srv)
+
+
+def test_server_refuses_contexts_it_cannot_reproduce(N):
+    """The server evaluates element sums only: a context with known charges or Adaptive
+    Modelling (whose nebem_eval results include them) is refused, at create and submit."""
+    g = I.thgem(I.PlateSpec(n_phi=24, n_r=3, n_zc=1, n_zf=4), n_plane=3)
+    c = N.Context().set_geometry(g)
+    c.solve(N.NEBEM_MIXED)
+    srv = N.nebem_server_create([c.h])
+    try:
+        N.nebem_space_charge(c.h, np.zeros((2, 3)) + 1e-4, np.array([1e-15, -1e-15]), 1e-6)
+        c.solve(N.NEBEM_MIXED)
+        with pytest.raises(N.NebemError) as e:
+            N.nebem_server_submit(srv, 0, np.zeros((3, 3)), None, None, N.NEBEM_MIXED)
+        assert e.value.code == N.NEBEM_BAD_STATE
+    finally:
+        N.nebem_server_destroy(srv)
+    with pytest.raises(N.NebemError) as e:
+        N.nebem_server_create([c.h])
+    assert e.value.code == N.NEBEM_BAD_STATE
+    c2 = N.Context().set_geometry(g)
+    c2.solve(N.NEBEM_MIXED)
+    N.nebem_set_primitives(c2.h, g.primitives, g.prim_of, 0)
+    with pytest.raises(N.NebemError) as e:
+        N.nebem_server_create([c2.h])
+    assert e.value.code == N.NEBEM_BAD_STATE
