@@ -229,7 +229,8 @@ int nebem_space_charge(nebem_ctx *ctx, const double *pos, const double *q, int64
  *   n_lines  (may be NULL) receives the number of lines.
  * Invalidates sigma, keeps the factors.
  * Errors: NEBEM_BAD_STATE (no point charges), NEBEM_TOO_LARGE (more than 2^26 points, or
- * voxels * points >= 4e18), NEBEM_INVALID_ARG. */
+ * voxels * points >= 4e18), NEBEM_INVALID_ARG (an edge <= 0, or dx, dy so small against dz
+ * that the near-line search, (3 dz/dx + 3)(3 dz/dy + 3) 5 voxels per target, exceeds 2e5). */
 int nebem_space_charge_lines(nebem_ctx *ctx, const double *voxel, int64_t *n_lines);
 
 /* Copy the current line charges to the host: start[L][3], stop[L][3] (m), lambda[L] (C/m),

@@ -544,6 +544,7 @@ __global__ void __launch_bounds__(kLT) k_line_near(const LineF* __restrict__ lin
     if (nl == 0) return;
     const int64_t p = target_index(perm, perm_div, t);
     const double px = tgt[3 * p], py = tgt[3 * p + 1], pz = tgt[3 * p + 2];
+    if (!isfinite(px) || !isfinite(py) || !isfinite(pz)) return;  // no near line (the far sum is NaN)
     float thx, thy, thz, tlx, tly, tlz;
     split_target(px, py, pz, thx, thy, thz, tlx, tly, tlz);
     const double reach = 1.5 * g->d[2] * (1.0 + 1e-3);  // 3 half lengths, padded

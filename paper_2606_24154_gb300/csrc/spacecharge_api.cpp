@@ -202,6 +202,13 @@ int nebem_space_charge_lines(nebem_ctx* ctx, const double* voxel, int64_t* n_lin
     if (!ctx || !voxel) return fail(NEBEM_INVALID_ARG, "ctx or voxel is NULL");
     for (int a = 0; a < 3; ++a)
         if (!(voxel[a] > 0.0) || !std::isfinite(voxel[a])) return fail(NEBEM_INVALID_ARG, "voxel edges must be > 0");
+    // the near-line search of a target visits the voxels within 3 half lengths (1.5 dz):
+    // about (3 dz/dx + 3) (3 dz/dy + 3) 5 of them; refuse shapes that make it huge
+    {
+        const double cand = (3.0 * voxel[2] / voxel[0] + 3.0) * (3.0 * voxel[2] / voxel[1] + 3.0) * 5.0;
+        if (!(cand <= 2.0e5))
+            return fail(NEBEM_INVALID_ARG, "voxel edges dx, dy too small relative to dz (near-line search)");
+    }
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     if (c->n_car == 0) return fail(NEBEM_BAD_STATE, "no point charges to reduce");
     if (c->n_car > kVoxMaxPoints) return fail(NEBEM_TOO_LARGE, "more than 2^26 point charges");

@@ -189,6 +189,9 @@ def test_line_state_errors(N):
             N.nebem_space_charge_lines(ctx.h, bad)
         assert e.value.code == N.NEBEM_INVALID_ARG
     with pytest.raises(N.NebemError) as e:
+        N.nebem_space_charge_lines(ctx.h, [1e-6, 1e-6, 1e-3])  # needle voxels: near search too wide
+    assert e.value.code == N.NEBEM_INVALID_ARG
+    with pytest.raises(N.NebemError) as e:
         N.nebem_space_charge_lines(ctx.h, [1e-15, 1e-15, 1e-15])  # ~1e37 voxels
     assert e.value.code == N.NEBEM_TOO_LARGE
     # still point charges: self exclusion works, lines are refused
