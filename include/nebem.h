@@ -161,9 +161,13 @@ int nebem_set_geometry(nebem_ctx *ctx, const nebem_element *el, int64_t n, const
 int nebem_set_bc(nebem_ctx *ctx, const double *voltages, int32_t n_conductors);
 
 /* Solve K sigma = b (Eq. Matrix; Alg. 1 with an LU solve instead of an explicit inverse).
- *   precision  NEBEM_FP64: FP64 fill, FP64 blocked LU with partial pivoting, FP64
- *              triangular solves.  NEBEM_MIXED: FP64 fill, FP32 LU, FP64 iterative
- *              refinement (residual with the FP64 K) until ir_tol.
+ *   precision  NEBEM_FP64: FP64 fill (closed forms for every pair), FP64 blocked LU with
+ *              partial pivoting, FP64 triangular solves.  NEBEM_MIXED: mixed fill (pairs
+ *              at >= 6 element radii by Gauss rules in two-float arithmetic, truncation
+ *              below ~3e-12 of the pair, nearer pairs by the FP64 closed forms; an FP64
+ *              matrix from an earlier FP64 fill is reused instead), FP32 LU with tensor-core
+ *              trailing updates, FP64 iterative refinement (residual with that K) until
+ *              ir_tol.
  *   Conductor rows: K_ij = ke sum_k Phi'(c_i; j + t_k), b_i = V - phi_sc(c_i).
  *   Interface rows: K_ij = ke sum_k n_i . E'(c_i; j + t_k) (principal value on the own
  *   element) + delta_ij (eps_a + eps_b) / (2 eps0 (eps_b - eps_a)), b_i = -n_i . E_sc(c_i).
@@ -181,8 +185,9 @@ int nebem_set_sigma(nebem_ctx *ctx, const double *sigma, int64_t n);
 /* Copy the current charge densities (n values) to host memory.  NEBEM_BAD_STATE if none. */
 int nebem_get_sigma(nebem_ctx *ctx, double *sigma_out, int64_t n);
 
-/* Fill the influence matrix (as nebem_solve does) and copy it to host memory in
- * column-major order, K_out[i + j*n] = K_ij.  K_out may be NULL (device copy only). */
+/* Fill the influence matrix (as nebem_solve does in this precision) and copy it to host
+ * memory in column-major order, K_out[i + j*n] = K_ij.  K_out may be NULL (device copy
+ * only).  A current FP64 matrix also answers a NEBEM_MIXED request. */
 int nebem_fill(nebem_ctx *ctx, int32_t precision, double *K_out);
 
 /* Gather entries of the current influence matrix (filled on demand as nebem_fill does):

@@ -55,7 +55,8 @@ Ctx::~Ctx() {
                       &d_x, &d_r, &d_r32, &d_small, &d_pts, &d_phi, &d_E, &d_car, &d_q, &d_car2, &d_sc_tgt,
                       &d_sc_phi, &d_sc_E, &d_scratch, &d_cjk, &d_cell_start, &d_cell_items, &d_fv_ax, &d_fv_ay, &d_fv_az, &d_fv_phi,
                       &d_fv_E, &d_vkeys, &d_vflags, &d_vbsum, &d_vpartial, &d_vgrid, &d_lines, &d_linesf, &d_line_vox,
-                      &d_am_start, &d_am_items, &d_am_elarea, &d_am_parea, &d_am_tmp, &d_perm64, &d_perm32, &d_swork})
+                      &d_am_start, &d_am_items, &d_am_elarea, &d_am_parea, &d_am_tmp, &d_perm64, &d_perm32, &d_swork,
+                      &d_fill_el, &d_fill_nodes, &d_fill_tau, &d_fill_cell_start, &d_fill_cell_items})
         b->release();
     am_near.release_all();
     am_far.release_all();
@@ -185,6 +186,7 @@ int nebem_set_geometry(nebem_ctx* ctx, const nebem_element* el, int64_t n, const
     // invalidate everything that depends on the geometry
     c->n = 0;
     c->K_valid = c->fac64_valid = c->fac32_valid = c->sigma_valid = false;
+    c->fill_tables = false;
     ++c->sigma_version;
     c->bc_set = false;
     c->n_car = 0;
@@ -251,7 +253,7 @@ int nebem_fill(nebem_ctx* ctx, int32_t precision, double* K_out) {
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     if (c->n == 0) return fail(NEBEM_BAD_STATE, "set_geometry first");
     CK(cudaSetDevice(c->device));
-    int rc = ensure_fill(c, nullptr);
+    int rc = ensure_fill(c, precision, nullptr);
     if (rc) return rc;
     if (K_out) {
         CK(cudaMemcpyAsync(K_out, c->d_K.ptr, sizeof(double) * c->n * c->n, cudaMemcpyDeviceToHost, c->stream));
@@ -269,7 +271,7 @@ int nebem_matrix_entries(nebem_ctx* ctx, const int64_t* rows, const int64_t* col
             return fail(NEBEM_INVALID_ARG, "entry index out of range");
     if (count == 0) return NEBEM_OK;
     CK(cudaSetDevice(c->device));
-    int rc = ensure_fill(c, nullptr);
+    int rc = ensure_fill(c, c->K_valid ? c->K_prec : NEBEM_FP64, nullptr);
     if (rc) return rc;
     DevBuf idx, val;
     CK(idx.ensure(sizeof(int64_t) * count));
@@ -295,7 +297,7 @@ int nebem_solve(nebem_ctx* ctx, int32_t precision, double* sigma_out, nebem_solv
     nebem_solve_info inf;
     std::memset(&inf, 0, sizeof(inf));
     inf.precision = precision;
-    int rc = ensure_fill(c, &inf.ms_fill);
+    int rc = ensure_fill(c, precision, &inf.ms_fill);
     if (rc) return rc;
     c->sc_precision = precision;
     rc = ensure_factors(c, precision, &inf.ms_factor);

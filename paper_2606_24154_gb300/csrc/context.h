@@ -73,7 +73,14 @@ struct Ctx {
     DevBuf d_am_start, d_am_items, d_am_elarea, d_am_parea, d_am_tmp;
     int64_t am_sigma_version = -1;
 
-    // matrix and factors
+    // mixed fill tables (built on the first mixed fill of a geometry): element records,
+    // two-float nodes, tau = t_k . frame, and the cell list for its near radius
+    DevBuf d_fill_el, d_fill_nodes, d_fill_tau, d_fill_cell_start, d_fill_cell_items;
+    NearGrid fill_grid{};
+    bool fill_tables = false;
+
+    // matrix and factors; K_prec = the fill that made K (NEBEM_FP64 or NEBEM_MIXED)
+    int K_prec = NEBEM_FP64;
     DevBuf d_K, d_LU64, d_LU32, d_piv64, d_piv32, d_work;
     DevBuf d_perm64, d_perm32, d_swork;  // pivot permutations, solve / residual work space
     bool K_valid = false, fac64_valid = false, fac32_valid = false;
@@ -100,7 +107,8 @@ int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* where);
 
 // solve.cpp
-int ensure_fill(Ctx* c, double* ms);
+// K in the given precision; an FP64 matrix also serves a mixed request
+int ensure_fill(Ctx* c, int precision, double* ms);
 int ensure_factors(Ctx* c, int precision, double* ms);
 int build_rhs(Ctx* c);
 int solve_with_factors(Ctx* c, int precision, nebem_solve_info* info);

@@ -1,0 +1,375 @@
+// fill_mixed.cu -- mixed-precision influence-matrix fill (Eq. Matrix, collocation at
+// centroids, periodic images):
+//   conductor row i:  K_ij = ke sum_k Phi'(c_i - t_k; j)
+//   interface row i:  K_ij = ke sum_k n_i . E'(c_i - t_k; j) + delta_ij diag_i
+//
+// Far pairs (distance to the image centroid >= kFillRatioC element radii) use Gauss rules
+// whose truncation error stays below ~3e-12 of the pair (tiers in nb_internal.h), evaluated
+// in two-float arithmetic: every quantity is an unevaluated sum hi + lo of two FP32 values
+// and products and sums keep their rounding errors through error-free transformations
+// (Dekker / Knuth TwoSum, FMA-based TwoProd), about 44 significant bits.  Near pairs use the
+// FP64 closed forms of influence.cuh.  The FP32 pipe runs 64 times the FP64 rate on this
+// GPU, so a two-float node (50-85 FP32 operations) costs about as much as one FP64 operation.
+//
+// Geometry of one pair in the local frame of the column element j (origin anywhere, axes
+// ex, ey = normal, ez): D = c_i - (c_j + t_k) has components
+//   X = (c_i - c_j) . ex - t_k . ex,  Y, Z likewise,
+// the first term once per (i, j), the second (tau) tabulated per (j, k).  A node at
+// offset s = centroid - node (in the element plane, local (s_x, s_z)) sees the target at
+// P - node = D + s, so
+//   r^2 = |D|^2 + q,  q = 2 (X s_x + Z s_z) + |s|^2,
+// which needs only two products per node.  1/r comes from one MUFU rsqrt refined by one
+// Newton step carried in two-float form; Phi' += w / r, n . E' += w (n . (D + s)) / r^3.
+//
+// Kernel k_fill_far: thread per row i, grid.y over column chunks; column tiles (element
+// records, tier-a nodes, tau, image centroids) staged in shared memory.  It writes
+// ke * (far sum) (+ the interface diagonal) to every entry.  Kernel k_fill_near: thread
+// per row i; it visits the image centroids in the 27 grid cells around c_i (cell edge >=
+// the largest near radius) and adds ke * (FP64 closed form) of every near pair.  Both
+// decide "near" by the same rounded FP32 squared distance (pair_d2 of eval_blocks.cuh) on
+// the same two-float inputs, so every pair is counted exactly once.
+#include "eval_blocks.cuh"
+
+namespace nb {
+
+namespace {
+
+constexpr int kFT = 128;       // threads per block (one row each)
+constexpr int kFillCols = 64;  // columns per block (grid.y)
+
+// ---------------------------------------------------------------- two-float arithmetic
+// All operations are the explicitly rounded intrinsics, so no contraction or reordering
+// can change the error-free transformations.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// requires |a| >= |b| (or a == 0)
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& t) {
+    s = __fadd_rn(a, b);
+    t = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// (ah + al) - (bh + bl), unnormalised
+__device__ __forceinline__ void df_sub(float ah, float al, float bh, float bl, float& h, float& l) {
+    float t;
+    two_sum(ah, -bh, h, t);
+    l = __fadd_rn(t, __fsub_rn(al, bl));
+}
+
+// a . b for three-vectors of two-float components
+__device__ __forceinline__ void df_dot3(const float (&ah)[3], const float (&al)[3], const float4& bh, const float4& bl,
+                                        float& h, float& l) {
+    float p0, e0, p1, e1, p2, e2, t1, t2, s;
+    two_prod(ah[0], bh.x, p0, e0);
+    two_prod(ah[1], bh.y, p1, e1);
+    two_prod(ah[2], bh.z, p2, e2);
+    two_sum(p0, p1, s, t1);
+    two_sum(s, p2, h, t2);
+    float lo = __fadd_rn(__fadd_rn(e0, e1), __fadd_rn(e2, __fadd_rn(t1, t2)));
+    lo = __fmaf_rn(ah[0], bl.x, lo);
+    lo = __fmaf_rn(al[0], bh.x, lo);
+    lo = __fmaf_rn(ah[1], bl.y, lo);
+    lo = __fmaf_rn(al[1], bh.y, lo);
+    lo = __fmaf_rn(ah[2], bl.z, lo);
+    lo = __fmaf_rn(al[2], bh.z, lo);
+    l = lo;
+}
+
+// squared norm of (X, Y, Z), two-float components
+__device__ __forceinline__ void df_norm2(float xh, float xl, float yh, float yl, float zh, float zl, float& h,
+                                         float& l) {
+    float px, ex, py, ey, pz, ez, s, t1, t2;
+    two_prod(xh, xh, px, ex);
+    two_prod(yh, yh, py, ey);
+    two_prod(zh, zh, pz, ez);
+    ex = __fmaf_rn(__fadd_rn(xh, xh), xl, ex);
+    ey = __fmaf_rn(__fadd_rn(yh, yh), yl, ey);
+    ez = __fmaf_rn(__fadd_rn(zh, zh), zl, ez);
+    two_sum(px, py, s, t1);
+    two_sum(s, pz, h, t2);
+    l = __fadd_rn(__fadd_rn(ex, ey), __fadd_rn(ez, __fadd_rn(t1, t2)));
+}
+
+// Per-image quantities of one pair in the column element's frame.
+struct PairDF {
+    float xh, xl, zh, zl;  // X, Z
+    float d2h, d2l;        // |D|^2
+    float ndh, ndl;        // n_i . D (interface rows)
+};
+
+// r^2 and 1/r (two-float) for one node; returns y0 (= hi of 1/r), yl, and the exact square
+// y0^2 = a + ae.
+__device__ __forceinline__ void node_rinv(const PairDF& P, const float4& u, const float4& v, float& y0, float& yl,
+                                          float& a, float& ae) {
+    float p1, e1, p2, e2, qh, t, t2, r2h, t3;
+    two_prod(P.xh, u.x, p1, e1);
+    two_prod(P.zh, u.y, p2, e2);
+    two_sum(p1, p2, qh, t);
+    float lo = __fadd_rn(t, __fadd_rn(e1, e2));
+    lo = __fmaf_rn(P.xh, v.x, lo);
+    lo = __fmaf_rn(P.xl, u.x, lo);
+    lo = __fmaf_rn(P.zh, v.y, lo);
+    lo = __fmaf_rn(P.zl, u.y, lo);
+    two_sum(qh, u.z, qh, t2);
+    lo = __fadd_rn(lo, __fadd_rn(t2, v.z));
+    // |D|^2 >= |q| for d >= kFillRatioC rho (|q| <= 2 d rho + rho^2)
+    fast_two_sum(P.d2h, qh, r2h, t3);
+    const float r2l = __fadd_rn(P.d2l, __fadd_rn(lo, t3));
+    // Newton step for r^-1/2 from the MUFU estimate: y = y0 (1 + h/2), h = 1 - r^2 y0^2
+    y0 = rsqrtf(r2h);
+    float b, be;
+    two_prod(y0, y0, a, ae);
+    two_prod(r2h, a, b, be);
+    float h = __fsub_rn(__fsub_rn(1.0f, b), be);  // 1 - b is exact (b within 2^-20 of 1)
+    h = __fmaf_rn(-r2h, ae, h);
+    h = __fmaf_rn(-r2l, a, h);
+    yl = __fmul_rn(__fmul_rn(0.5f, y0), h);
+}
+
+// Phi' nodes: S += w / r
+__device__ __forceinline__ void nodes_phi(const float4* __restrict__ nd, int cnt, const PairDF& P, float& sh,
+                                          float& sl) {
+    for (int q = 0; q < cnt; ++q) {
+        const float4 u = nd[2 * q], v = nd[2 * q + 1];
+        float y0, yl, a, ae;
+        node_rinv(P, u, v, y0, yl, a, ae);
+        float m, me, t;
+        two_prod(u.w, y0, m, me);
+        me = __fmaf_rn(u.w, yl, me);
+        me = __fmaf_rn(v.w, y0, me);
+        two_sum(sh, m, sh, t);
+        sl = __fadd_rn(sl, __fadd_rn(me, t));
+    }
+}
+
+// n . E' nodes: S += w (n . (D + s)) / r^3, with n . s = (n . ex) s_x + (n . ez) s_z
+__device__ __forceinline__ void nodes_nE(const float4* __restrict__ nd, int cnt, const PairDF& P, float nxh,
+                                         float nxl, float nzh, float nzl, float& sh, float& sl) {
+    for (int q = 0; q < cnt; ++q) {
+        const float4 u = nd[2 * q], v = nd[2 * q + 1];
+        float y0, yl, a, ae;
+        node_rinv(P, u, v, y0, yl, a, ae);
+        // 2 (n . s)
+        float p1, e1, p2, e2, ns, t;
+        two_prod(nxh, u.x, p1, e1);
+        two_prod(nzh, u.y, p2, e2);
+        two_sum(p1, p2, ns, t);
+        float nsl = __fadd_rn(t, __fadd_rn(e1, e2));
+        nsl = __fmaf_rn(nxh, v.x, nsl);
+        nsl = __fmaf_rn(nxl, u.x, nsl);
+        nsl = __fmaf_rn(nzh, v.y, nsl);
+        nsl = __fmaf_rn(nzl, u.y, nsl);
+        // n . (D + s)
+        float gh, t2;
+        two_sum(P.ndh, __fmul_rn(0.5f, ns), gh, t2);
+        const float gl = __fadd_rn(P.ndl, __fadd_rn(__fmul_rn(0.5f, nsl), t2));
+        // y^3 = (y0 + yl)^3: y^2 = a + (ae + 2 y0 yl), y^3 = y^2 y
+        const float y2l = __fmaf_rn(__fadd_rn(y0, y0), yl, ae);
+        float c3, c3e;
+        two_prod(a, y0, c3, c3e);
+        c3e = __fmaf_rn(a, yl, c3e);
+        c3e = __fmaf_rn(y2l, y0, c3e);
+        // w y^3
+        float m, me;
+        two_prod(u.w, c3, m, me);
+        me = __fmaf_rn(u.w, c3e, me);
+        me = __fmaf_rn(v.w, c3, me);
+        // (w y^3) (n . (D + s))
+        float f, fe;
+        two_prod(m, gh, f, fe);
+        fe = __fmaf_rn(m, gl, fe);
+        fe = __fmaf_rn(me, gh, fe);
+        float t3;
+        two_sum(sh, f, sh, t3);
+        sl = __fadd_rn(sl, __fadd_rn(fe, t3));
+    }
+}
+
+__device__ __forceinline__ void stage(float4* dst, const float4* __restrict__ src, int cnt) {
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) dst[i] = src[i];
+}
+
+// Dynamic shared memory per tile of te elements: FillEl (9 float4), tier-a nodes (18 float4),
+// tau and image centroids (2 float4 each per image).
+__host__ __device__ constexpr int fill_tile_f4(int te, int nimg) { return te * (9 + 2 * kFillNodesA + 4 * nimg); }
+
+__global__ void __launch_bounds__(kFT, 4)
+    k_fill_far(const FillEl* __restrict__ fe, const float4* __restrict__ nodes, const float4* __restrict__ tau,
+               const float4* __restrict__ cjk, const double* __restrict__ diag_in, int64_t n, int nimg, int te,
+               double* __restrict__ K) {
+    extern __shared__ float4 sm[];
+    FillEl* s_fe = reinterpret_cast<FillEl*>(sm);
+    float4* s_na = sm + 9 * te;
+    float4* s_tau = s_na + 2 * kFillNodesA * te;
+    float4* s_c = s_tau + 2 * nimg * te;
+
+    const int64_t i = (int64_t)blockIdx.x * kFT + threadIdx.x;
+    const bool active = i < n;
+    // row data: centroid and normal (two floats each), row type
+    float ch[3] = {0.f, 0.f, 0.f}, cl[3] = {0.f, 0.f, 0.f}, nh[3] = {0.f, 0.f, 0.f}, nl[3] = {0.f, 0.f, 0.f};
+    bool iface = false;
+    double diag = 0.0;
+    if (active) {
+        const FillEl r = fe[i];
+        ch[0] = r.ch.x, ch[1] = r.ch.y, ch[2] = r.ch.z;
+        cl[0] = r.cl.x, cl[1] = r.cl.y, cl[2] = r.cl.z;
+        nh[0] = r.eyh.x, nh[1] = r.eyh.y, nh[2] = r.eyh.z;
+        nl[0] = r.eyl.x, nl[1] = r.eyl.y, nl[2] = r.eyl.z;
+        diag = diag_in[i];
+        iface = diag != 0.0;  // interface rows carry the nonzero diagonal term
+    }
+    const double ke = 1.0 / (4.0 * kPi * kEps0);
+    const int64_t j0 = (int64_t)blockIdx.y * kFillCols;
+    const int64_t j1 = min(n, j0 + kFillCols);
+    for (int64_t base = j0; base < j1; base += te) {
+        const int cnt = (int)min((int64_t)te, j1 - base);
+        __syncthreads();
+        stage(reinterpret_cast<float4*>(s_fe), reinterpret_cast<const float4*>(fe + base), 9 * cnt);
+        for (int e = threadIdx.x; e < cnt * 2 * kFillNodesA; e += blockDim.x) {
+            const int jj = e / (2 * kFillNodesA), q = e - jj * 2 * kFillNodesA;
+            s_na[e] = nodes[(base + jj) * kFillNodeRec + q];
+        }
+        stage(s_tau, tau + 2 * base * nimg, 2 * cnt * nimg);
+        stage(s_c, cjk + 2 * base * nimg, 2 * cnt * nimg);
+        __syncthreads();
+        for (int jj = 0; jj < cnt; ++jj) {
+            const FillEl& E = s_fe[jj];
+            const int64_t j = base + jj;
+            const float4 hdr = E.hdr;
+            const int na = (int)hdr.w;
+            // c_i - c_j and its local components
+            float dh[3], dl[3];
+            df_sub(ch[0], cl[0], E.ch.x, E.cl.x, dh[0], dl[0]);
+            df_sub(ch[1], cl[1], E.ch.y, E.cl.y, dh[1], dl[1]);
+            df_sub(ch[2], cl[2], E.ch.z, E.cl.z, dh[2], dl[2]);
+            float x0h, x0l, y0h, y0l, z0h, z0l;
+            df_dot3(dh, dl, E.exh, E.exl, x0h, x0l);
+            df_dot3(dh, dl, E.eyh, E.eyl, y0h, y0l);
+            df_dot3(dh, dl, E.ezh, E.ezl, z0h, z0l);
+            float nxh = 0.f, nxl = 0.f, nyh = 0.f, nyl = 0.f, nzh = 0.f, nzl = 0.f;
+            if (iface) {
+                df_dot3(nh, nl, E.exh, E.exl, nxh, nxl);
+                df_dot3(nh, nl, E.eyh, E.eyl, nyh, nyl);
+                df_dot3(nh, nl, E.ezh, E.ezl, nzh, nzl);
+            }
+            float sh = 0.f, sl = 0.f;
+            for (int k = 0; k < nimg; ++k) {
+                float dx, dy, dz;
+                const float d2 = pair_d2(ch[0], ch[1], ch[2], cl[0], cl[1], cl[2], s_c[2 * (jj * nimg + k)],
+                                         s_c[2 * (jj * nimg + k) + 1], dx, dy, dz);
+                if (!(d2 >= hdr.z)) continue;  // near pair: k_fill_near
+                const float4 th = s_tau[2 * (jj * nimg + k)], tl = s_tau[2 * (jj * nimg + k) + 1];
+                PairDF P;
+                float yh, yl;
+                df_sub(x0h, x0l, th.x, tl.x, P.xh, P.xl);
+                df_sub(y0h, y0l, th.y, tl.y, yh, yl);
+                df_sub(z0h, z0l, th.z, tl.z, P.zh, P.zl);
+                df_norm2(P.xh, P.xl, yh, yl, P.zh, P.zl, P.d2h, P.d2l);
+                const float4* nd;
+                int nn;
+                if (d2 >= hdr.x) {
+                    nd = s_na + jj * 2 * kFillNodesA;
+                    nn = na;
+                } else if (d2 >= hdr.y) {
+                    nd = nodes + j * kFillNodeRec + kFillOffB;
+                    nn = kFillNodesB;
+                } else {
+                    nd = nodes + j * kFillNodeRec + kFillOffC;
+                    nn = kFillNodesC;
+                }
+                if (!iface) {
+                    nodes_phi(nd, nn, P, sh, sl);
+                } else {
+                    const float Xh[3] = {P.xh, yh, P.zh}, Xl[3] = {P.xl, yl, P.zl};
+                    df_dot3(Xh, Xl, make_float4(nxh, nyh, nzh, 0.f), make_float4(nxl, nyl, nzl, 0.f), P.ndh, P.ndl);
+                    nodes_nE(nd, nn, P, nxh, nxl, nzh, nzl, sh, sl);
+                }
+            }
+            if (active) {
+                const double acc = (double)sh + (double)sl;
+                K[i + j * n] = (i == j) ? fma(ke, acc, diag) : ke * acc;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) k_fill_near(const Elem* __restrict__ el, const FillEl* __restrict__ fe,
+                                                   const float4* __restrict__ cjk, int64_t n, const ImageTable img,
+                                                   const NearGrid grid, const int32_t* __restrict__ cell_start,
+                                                   const int32_t* __restrict__ cell_items, double* __restrict__ K) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Elem& ei = el[i];
+    const double Px = ei.c[0], Py = ei.c[1], Pz = ei.c[2];
+    const double nx = ei.ey[0], ny = ei.ey[1], nz = ei.ey[2];
+    const bool cond = ei.bc == NEBEM_CONDUCTOR;
+    const FillEl ri = fe[i];
+    const int nimg = img.n;
+    int cc[3];
+    const double P[3] = {Px, Py, Pz};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        double f = floor((P[a] - grid.origin[a]) * grid.inv_h);
+        f = fmin(fmax(f, -2.0), (double)grid.dims[a] + 1.0);
+        cc[a] = (int)f;
+    }
+    const double ke = 1.0 / (4.0 * kPi * kEps0);
+    for (int z = max(cc[2] - 1, 0); z <= min(cc[2] + 1, grid.dims[2] - 1); ++z)
+        for (int y = max(cc[1] - 1, 0); y <= min(cc[1] + 1, grid.dims[1] - 1); ++y)
+            for (int x = max(cc[0] - 1, 0); x <= min(cc[0] + 1, grid.dims[0] - 1); ++x) {
+                const int64_t cell = ((int64_t)z * grid.dims[1] + y) * grid.dims[0] + x;
+                for (int32_t it = cell_start[cell]; it < cell_start[cell + 1]; ++it) {
+                    const int32_t jk = cell_items[it];
+                    const int32_t j = jk / nimg, k = jk - j * nimg;
+                    float dx, dy, dz;
+                    const float d2 = pair_d2(ri.ch.x, ri.ch.y, ri.ch.z, ri.cl.x, ri.cl.y, ri.cl.z, cjk[2 * (int64_t)jk],
+                                             cjk[2 * (int64_t)jk + 1], dx, dy, dz);
+                    if (d2 >= fe[j].hdr.z) continue;  // far pair: k_fill_far
+                    const Elem& e = el[j];
+                    const bool self = (i == j) && (k == img.k0);
+                    double f, gx, gy, gz;
+                    elem_local_f64(e, Px - img.t[k][0], Py - img.t[k][1], Pz - img.t[k][2], self, f, gx, gy, gz);
+                    double v;
+                    if (cond) {
+                        v = f;
+                    } else {
+                        const double Ex = fma(gx, e.ex[0], fma(gy, e.ey[0], gz * e.ez[0]));
+                        const double Ey = fma(gx, e.ex[1], fma(gy, e.ey[1], gz * e.ez[1]));
+                        const double Ez = fma(gx, e.ex[2], fma(gy, e.ey[2], gz * e.ez[2]));
+                        v = fma(nx, Ex, fma(ny, Ey, nz * Ez));
+                    }
+                    K[i + (int64_t)j * n] += ke * v;
+                }
+            }
+}
+
+}  // namespace
+
+cudaError_t launch_fill_mixed(const Elem* el, const FillEl* fe, const float4* nodes, const float4* tau,
+                              const float4* cjk, const double* diag, int64_t n, const ImageTable& img,
+                              const NearGrid& grid, const int32_t* cell_start, const int32_t* cell_items, double* K,
+                              cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    // column tile: as many elements as fit in ~40 KB (four blocks per SM), at most 16
+    int te = 16;
+    while (te > 1 && fill_tile_f4(te, img.n) * (int)sizeof(float4) > 40 * 1024) --te;
+    const size_t smem = (size_t)fill_tile_f4(te, img.n) * sizeof(float4);
+    cudaError_t e = cudaFuncSetAttribute(k_fill_far, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 g1((unsigned)((n + kFT - 1) / kFT), (unsigned)((n + kFillCols - 1) / kFillCols));
+    k_fill_far<<<g1, kFT, smem, s>>>(fe, nodes, tau, cjk, diag, n, img.n, te, K);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_fill_near<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(el, fe, cjk, n, img, grid, cell_start, cell_items, K);
+    return cudaGetLastError();
+}
+
+}  // namespace nb

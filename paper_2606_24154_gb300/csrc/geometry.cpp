@@ -280,6 +280,133 @@ int build_element(const nebem_element& r, const nebem_options& opt, Elem& e, dou
     return NEBEM_OK;
 }
 
+namespace {
+
+inline void split_f(double x, float& hi, float& lo) {
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
+
+inline float4 f4(float a, float b, float c, float d) {
+    float4 r;
+    r.x = a;
+    r.y = b;
+    r.z = c;
+    r.w = d;
+    return r;
+}
+
+// Two-float node record (u = hi parts, v = lo parts) of the offset s = centroid - node in
+// the local frame and the weight w.
+inline void fill_node(double sx, double sz, double w, float4* dst) {
+    float a[4], b[4];
+    split_f(2.0 * sx, a[0], b[0]);
+    split_f(2.0 * sz, a[1], b[1]);
+    split_f(sx * sx + sz * sz, a[2], b[2]);
+    split_f(w, a[3], b[3]);
+    dst[0] = f4(a[0], a[1], a[2], a[3]);
+    dst[1] = f4(b[0], b[1], b[2], b[3]);
+}
+
+}  // namespace
+
+void build_fill_tables(const std::vector<Elem>& el, const ImageTable& img, std::vector<FillEl>& fe,
+                       std::vector<float4>& nodes, std::vector<float4>& tau) {
+    const int64_t n = (int64_t)el.size();
+    const int m = img.n;
+    fe.assign((size_t)n, FillEl{});
+    nodes.assign((size_t)n * kFillNodeRec, f4(0.f, 0.f, 0.f, 0.f));
+    tau.assign((size_t)n * m * 2, f4(0.f, 0.f, 0.f, 0.f));
+    for (int64_t j = 0; j < n; ++j) {
+        const Elem& e = el[j];
+        FillEl& r = fe[j];
+        float h[3], l[3];
+        for (int a = 0; a < 3; ++a) split_f(e.c[a], h[a], l[a]);
+        r.ch = f4(h[0], h[1], h[2], 0.f);
+        r.cl = f4(l[0], l[1], l[2], 0.f);
+        const double* ax[3] = {e.ex, e.ey, e.ez};
+        float4* dh[3] = {&r.exh, &r.eyh, &r.ezh};
+        float4* dl[3] = {&r.exl, &r.eyl, &r.ezl};
+        for (int v = 0; v < 3; ++v) {
+            for (int a = 0; a < 3; ++a) split_f(ax[v][a], h[a], l[a]);
+            *dh[v] = f4(h[0], h[1], h[2], 0.f);
+            *dl[v] = f4(l[0], l[1], l[2], 0.f);
+        }
+        const double ra = kFillRatioA * e.rho, rb = kFillRatioB * e.rho, rc = kFillRatioC * e.rho;
+        const int nv = e.nv;
+        // centroid in the local frame (origin v0)
+        double d[3];
+        sub3(e.c, e.o, d);
+        const double cx = dot3(d, e.ex), cz = dot3(d, e.ez);
+        const double* qx = e.qx;
+        const double* qz = e.qz;
+        float4* out = nodes.data() + j * kFillNodeRec;
+        auto put = [&](float4* dst, double px, double pz, double w) { fill_node(cx - px, cz - pz, w, dst); };
+        int n_a = 0;
+        if (nv == 4) {
+            // tensor Gauss-Legendre on the bilinear map x(s, t) = q0 + s e1 + t e3 + s t tw,
+            // weight ws wt |x_s x x_t|
+            const double e1x = qx[1] - qx[0], e1z = qz[1] - qz[0];
+            const double e3x = qx[3] - qx[0], e3z = qz[3] - qz[0];
+            const double twx = qx[2] - qx[1] - e3x, twz = qz[2] - qz[1] - e3z;
+            auto tensor = [&](int mq, float4* dst) {
+                double x[16], w[16];
+                gauss_legendre01(mq, x, w);
+                int cnt = 0;
+                for (int a = 0; a < mq; ++a)
+                    for (int b = 0; b < mq; ++b) {
+                        const double px = qx[0] + x[a] * e1x + x[b] * e3x + x[a] * x[b] * twx;
+                        const double pz = qz[0] + x[a] * e1z + x[b] * e3z + x[a] * x[b] * twz;
+                        const double sx = e1x + x[b] * twx, sz = e1z + x[b] * twz;
+                        const double tx = e3x + x[a] * twx, tz = e3z + x[a] * twz;
+                        const double jac = std::fabs(sx * tz - sz * tx);
+                        put(dst + 2 * cnt, px, pz, w[a] * w[b] * jac);
+                        ++cnt;
+                    }
+                return cnt;
+            };
+            n_a = tensor(3, out);
+            tensor(4, out + kFillOffB);
+            tensor(6, out + kFillOffC);
+        } else {
+            const double area = 0.5 * e.twoA[0];
+            for (int g2 = 0; g2 < 2; ++g2)
+                for (int rr = 0; rr < 3; ++rr) {
+                    double bc[3] = {kTriA[g2], kTriA[g2], kTriA[g2]};
+                    bc[rr] = 1.0 - 2.0 * kTriA[g2];
+                    const double px = bc[0] * qx[0] + bc[1] * qx[1] + bc[2] * qx[2];
+                    const double pz = bc[0] * qz[0] + bc[1] * qz[1] + bc[2] * qz[2];
+                    put(out + 2 * n_a, px, pz, kTriW[g2] * area);
+                    ++n_a;
+                }
+            // collapsed (Duffy) product rules: x = q0 + s e1 + t (1 - s) e2, weight 2 ws wt (1 - s) A
+            auto collapsed = [&](int mq, float4* dst) {
+                double x[16], w[16];
+                gauss_legendre01(mq, x, w);
+                int cnt = 0;
+                for (int a = 0; a < mq; ++a)
+                    for (int b = 0; b < mq; ++b) {
+                        const double sa = x[a], tb = x[b] * (1.0 - x[a]);
+                        const double px = qx[0] + sa * (qx[1] - qx[0]) + tb * (qx[2] - qx[0]);
+                        const double pz = qz[0] + sa * (qz[1] - qz[0]) + tb * (qz[2] - qz[0]);
+                        put(dst + 2 * cnt, px, pz, 2.0 * w[a] * w[b] * (1.0 - x[a]) * area);
+                        ++cnt;
+                    }
+                return cnt;
+            };
+            collapsed(4, out + kFillOffB);
+            collapsed(6, out + kFillOffC);
+        }
+        r.hdr = f4((float)(ra * ra), (float)(rb * rb), (float)(rc * rc), (float)n_a);
+        for (int k = 0; k < m; ++k) {
+            float th[3], tl[3];
+            for (int v = 0; v < 3; ++v) split_f(dot3(img.t[k], ax[v]), th[v], tl[v]);
+            tau[((size_t)j * m + k) * 2] = f4(th[0], th[1], th[2], 0.f);
+            tau[((size_t)j * m + k) * 2 + 1] = f4(tl[0], tl[1], tl[2], 0.f);
+        }
+    }
+}
+
 int build_near_grid(const std::vector<Elem>& el, const ImageTable& img, double ratio_near, NearGrid& grid,
                     std::vector<int32_t>& cell_start, std::vector<int32_t>& cell_items, std::string& why) {
     const int64_t n = (int64_t)el.size(), m = img.n, total = n * m;

@@ -21,6 +21,12 @@ void gauss_legendre01(int m, double* x, double* w);
 int build_near_grid(const std::vector<Elem>& el, const ImageTable& img, double ratio_near, NearGrid& grid,
                     std::vector<int32_t>& cell_start, std::vector<int32_t>& cell_items, std::string& why);
 
+// Tables of the mixed fill: per element the FillEl record and kFillNodeRec float4 of
+// two-float Gauss nodes (local frame); per (element, image) the two float4 of
+// tau = t_k . (ex, ey, ez) (hi, lo).
+void build_fill_tables(const std::vector<Elem>& el, const ImageTable& img, std::vector<FillEl>& fe,
+                       std::vector<float4>& nodes, std::vector<float4>& tau);
+
 // Image translations t = k1 a1 + k2 a2, index (k1-lo)*m + (k2-lo); lattice NULL -> one
 // zero translation.
 int build_images(const double* lattice, int lo, int hi, ImageTable& img, std::string& why);

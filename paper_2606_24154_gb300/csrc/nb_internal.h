@@ -61,6 +61,35 @@ struct __align__(16) FarNodes {
     int32_t pad[3];
 };
 
+// Mixed-precision fill (Eq. Matrix with far pairs by Gauss rules in two-float arithmetic).
+// Pairs are tiered by the distance d from the collocation point to the image centroid, in
+// radii rho of the column element:
+//   d >= kFillRatioA rho   tier a: rectangle / quadrilateral 3x3, triangle 6-point rule
+//   d >= kFillRatioB rho   tier b: 4x4 / collapsed 4x4
+//   d >= kFillRatioC rho   tier c: 6x6 / collapsed 6x6
+//   nearer                 FP64 closed form
+// The rule truncation errors at these distances (worst over thin rectangles, obtuse and
+// sliver triangles and skewed quadrilaterals) stay below ~3e-12 of the pair's value.
+// Nodes are kept in the element's local (x, z) frame as offsets s = centroid - node; every
+// value is stored as an unevaluated sum of two floats (hi + lo):
+//   node  u = (2 s_x hi, 2 s_z hi, |s|^2 hi, w hi),  v = the lo parts, w = weight x area.
+constexpr double kFillRatioA = 96.0;
+constexpr double kFillRatioB = 32.0;
+constexpr double kFillRatioC = 6.0;
+constexpr int kFillNodesA = 9;  // capacity (6 used by triangles)
+constexpr int kFillNodesB = 16;
+constexpr int kFillNodesC = 36;
+constexpr int kFillNodeRec = 2 * (kFillNodesA + kFillNodesB + kFillNodesC);  // float4 per element
+constexpr int kFillOffB = 2 * kFillNodesA;
+constexpr int kFillOffC = 2 * (kFillNodesA + kFillNodesB);
+// Per element: centroid c and frame (ex, ey, ez) as hi + lo floats; hdr = squared tier
+// distances (a, b, c) in m^2 and the tier-a node count.
+struct __align__(16) FillEl {
+    float4 ch, cl;
+    float4 exh, exl, eyh, eyl, ezh, ezl;
+    float4 hdr;
+};
+
 struct ImageTable {
     int32_t n;
     int32_t k0;  // index of the zero translation
@@ -109,6 +138,13 @@ size_t eval_mixed_scratch_bytes(int64_t npts);
 cudaError_t launch_image_centroids(const Elem* el, int64_t n, const ImageTable& img, float4* cjk, cudaStream_t s);
 cudaError_t launch_fill_f64(const Elem* el, const double* diag, int64_t n, const ImageTable& img, double* K,
                             cudaStream_t s);
+// Mixed fill: far pairs (tiers a-c) write K; near pairs (grid of image centroids with
+// the near radius kFillRatioC rho) add their FP64 closed forms afterwards.  tau[j][k] =
+// t_k . (ex_j, ey_j, ez_j) as (hi, lo) float4 pairs; nodes of kFillNodeRec float4 per element.
+cudaError_t launch_fill_mixed(const Elem* el, const FillEl* fe, const float4* nodes, const float4* tau,
+                              const float4* cjk, const double* diag, int64_t n, const ImageTable& img,
+                              const NearGrid& grid, const int32_t* cell_start, const int32_t* cell_items, double* K,
+                              cudaStream_t s);
 cudaError_t launch_element_influence(const Elem* el, int64_t n_el, const double* pts, int64_t npts,
                                      double* phi, double* E, cudaStream_t s);
 

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "context.h"
+#include "geometry.h"
 
 namespace nb {
 
@@ -28,15 +29,53 @@ static int elapsed_ms(Ctx* c, double* ms) {
     return 0;
 }
 
-int ensure_fill(Ctx* c, double* ms) {
-    if (c->K_valid) return 0;
+static int ensure_fill_tables(Ctx* c) {
+    if (c->fill_tables) return 0;
+    std::vector<FillEl> fe;
+    std::vector<float4> nodes, tau;
+    build_fill_tables(c->h_el, c->img, fe, nodes, tau);
+    std::vector<int32_t> cell_start, cell_items;
+    std::string why;
+    int rc = build_near_grid(c->h_el, c->img, kFillRatioC, c->fill_grid, cell_start, cell_items, why);
+    if (rc) return fail(rc, why);
+    CK(c->d_fill_el.ensure(sizeof(FillEl) * fe.size()));
+    CK(c->d_fill_nodes.ensure(sizeof(float4) * nodes.size()));
+    CK(c->d_fill_tau.ensure(sizeof(float4) * tau.size()));
+    CK(c->d_fill_cell_start.ensure(sizeof(int32_t) * cell_start.size()));
+    CK(c->d_fill_cell_items.ensure(sizeof(int32_t) * cell_items.size()));
+    CK(cudaMemcpyAsync(c->d_fill_el.ptr, fe.data(), sizeof(FillEl) * fe.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_fill_nodes.ptr, nodes.data(), sizeof(float4) * nodes.size(), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(c->d_fill_tau.ptr, tau.data(), sizeof(float4) * tau.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_fill_cell_start.ptr, cell_start.data(), sizeof(int32_t) * cell_start.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_fill_cell_items.ptr, cell_items.data(), sizeof(int32_t) * cell_items.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));  // the host vectors go out of scope
+    c->fill_tables = true;
+    return 0;
+}
+
+int ensure_fill(Ctx* c, int precision, double* ms) {
+    if (c->K_valid && (c->K_prec == NEBEM_FP64 || c->K_prec == precision)) return 0;
     const int64_t n = c->n;
+    if (precision == NEBEM_MIXED) {
+        int rc = ensure_fill_tables(c);
+        if (rc) return rc;
+    }
     CK(c->d_K.ensure(sizeof(double) * n * n));
     CK(cudaEventRecord(c->ev0, c->stream));
-    CK(launch_fill_f64(c->d_el.as<Elem>(), c->d_diag.as<double>(), n, c->img, c->d_K.as<double>(), c->stream));
+    if (precision == NEBEM_MIXED)
+        CK(launch_fill_mixed(c->d_el.as<Elem>(), c->d_fill_el.as<FillEl>(), c->d_fill_nodes.as<float4>(),
+                             c->d_fill_tau.as<float4>(), c->d_cjk.as<float4>(), c->d_diag.as<double>(), n, c->img,
+                             c->fill_grid, c->d_fill_cell_start.as<int32_t>(), c->d_fill_cell_items.as<int32_t>(),
+                             c->d_K.as<double>(), c->stream));
+    else
+        CK(launch_fill_f64(c->d_el.as<Elem>(), c->d_diag.as<double>(), n, c->img, c->d_K.as<double>(), c->stream));
     int rc = elapsed_ms(c, ms);
     if (rc) return rc;
     c->K_valid = true;
+    c->K_prec = precision;
     c->fac64_valid = c->fac32_valid = false;
     return 0;
 }

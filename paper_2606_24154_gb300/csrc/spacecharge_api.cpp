@@ -157,7 +157,7 @@ int nebem_step(nebem_ctx* ctx, int32_t steps, double mu, double dt, int32_t prec
     if (c->n_car == 0) return fail(NEBEM_BAD_STATE, "no known-charge set");
     CK(cudaSetDevice(c->device));
     const int64_t m = c->n_car;
-    int rc = ensure_fill(c, nullptr);
+    int rc = ensure_fill(c, precision, nullptr);
     if (rc) return rc;
     rc = ensure_factors(c, precision, nullptr);
     if (rc) return rc;

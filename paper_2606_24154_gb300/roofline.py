@@ -79,3 +79,60 @@ def fp32_peak_ops(sm_mhz):
 
 def mufu_peak(sm_mhz):
     return N_SM * MUFU_PER_SM * sm_mhz * 1e6
+
+
+# ---------------------------------------------------------------- mixed fill
+# Two-float (hi + lo FP32) operations of the mixed fill kernel, counted from its code:
+# per (row, column): c_i - c_j (3 two-float differences, 8 each) and its local components
+# (3 two-float dot products, 28 each); interface rows add the normal's local components
+# (3 more dot products).  Per far image pair: the FP32 tier test (12 + 3 compares), X, Y, Z
+# (3 differences) and |D|^2 (28); interface rows add n . D (28).  Per Gauss node: r^2 and
+# the refined 1/r (39, plus one MUFU rsqrt), then w / r accumulated (12) on conductor rows,
+# or w (n . (D + s)) / r^3 accumulated (48) on interface rows.
+FILL_OPS_COLUMN = (108, 192)   # conductor, interface row
+FILL_OPS_IMAGE = (67, 95)
+FILL_OPS_NODE = (51, 87)
+FILL_RATIOS = (96.0, 32.0, 6.0)
+
+
+def fill_tier_counts(g, rows=256, seed=0, chunk=16):
+    """Pair and node counts of the mixed fill on a sample of rows (collocation points), by
+    row type, with the fill's distance tiers; scale = n / rows."""
+    c, rho, nv = _element_table(g)
+    t = _images(g)
+    C = (c[:, None, :] + t[None]).reshape(-1, 3)
+    R = np.repeat(rho, t.shape[0])
+    NV = np.repeat(nv, t.shape[0])
+    na = np.where(NV == 4, 9, 6)
+    bc = g.elements["bc"]
+    n = c.shape[0]
+    sel = np.random.default_rng(seed).choice(n, min(rows, n), replace=False)
+    out = {k: {"rows": 0, "pairs": 0, "far_pairs": 0, "nodes": 0, "near_pairs": 0} for k in ("cond", "iface")}
+    for s in range(0, sel.size, chunk):
+        r = sel[s:s + chunk]
+        d = np.linalg.norm(c[r, None, :] - C[None], axis=2) / R[None]
+        ta = d >= FILL_RATIOS[0]
+        tb = (~ta) & (d >= FILL_RATIOS[1])
+        tc = (d < FILL_RATIOS[1]) & (d >= FILL_RATIOS[2])
+        far = ta | tb | tc
+        nodes = (ta * na[None]).sum(1) + 16 * tb.sum(1) + 36 * tc.sum(1)
+        for k, key in ((0, "cond"), (1, "iface")):
+            m = bc[r] == k
+            o = out[key]
+            o["rows"] += int(m.sum())
+            o["pairs"] += int(m.sum()) * d.shape[1]
+            o["far_pairs"] += int(far[m].sum())
+            o["near_pairs"] += int((~far[m]).sum())
+            o["nodes"] += int(nodes[m].sum())
+    out["sample_rows"] = int(sel.size)
+    return out
+
+
+def fill_ops(counts, n):
+    """Two-float FP32 operations of one mixed fill of an n x n matrix, from fill_tier_counts."""
+    scale = n / counts["sample_rows"]
+    ops = 0.0
+    for k, key in enumerate(("cond", "iface")):
+        o = counts[key]
+        ops += o["rows"] * n * FILL_OPS_COLUMN[k] + o["far_pairs"] * FILL_OPS_IMAGE[k] + o["nodes"] * FILL_OPS_NODE[k]
+    return ops * scale
