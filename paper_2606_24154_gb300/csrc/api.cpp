@@ -397,7 +397,7 @@ int nebem_lu_factor_device_f32(nebem_ctx* ctx, float* d_A, int64_t n, int32_t* d
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
     const int nb = c->opt.lu_block;
     DevBuf work, info;
-    CK(work.ensure(sizeof(double) * lu_work_elems(n, nb)));
+    CK(work.ensure(lu_work_bytes_f32(n, nb)));
     CK(info.ensure(2 * sizeof(int)));
     CK(lu_factor_f32(d_A, n, d_piv, nb, work.as<float>(), info.as<int>(), s));
     int h2[2] = {0, 0};

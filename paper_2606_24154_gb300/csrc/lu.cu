@@ -133,7 +133,7 @@ __global__ void k_scale_update(T* __restrict__ A, int64_t n, int64_t j, int64_t 
 // With do_pivot = 0 only (a) runs (the launch after the panel's last column).  The
 // per-element arithmetic is that of the three separate steps, in the same order.
 template <typename T>
-__global__ void __launch_bounds__(kPivThreads) k_panel_col(T* __restrict__ A, int64_t n, int64_t j, int64_t k0,
+__global__ void __launch_bounds__(kPivThreads, 2) k_panel_col(T* __restrict__ A, int64_t n, int64_t j, int64_t k0,
                                                             int64_t k1, int do_pivot, double* __restrict__ pval,
                                                             int64_t* __restrict__ pidx, int* __restrict__ ticket,
                                                             int32_t* __restrict__ piv, int* __restrict__ info) {
@@ -156,13 +156,32 @@ __global__ void __launch_bounds__(kPivThreads) k_panel_col(T* __restrict__ A, in
     double best = -1.0;
     int64_t bidx = INT64_MAX;
     for (int64_t i = j + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T aj;  // A[i, j] after the update
         if (update && ok) {
             const T l = A[i + jm * n] * inv;
             A[i + jm * n] = l;
-            for (int c = 0; c < w; ++c) A[i + (j + c) * n] -= l * urow[c];
+            // the row's panel values in batches of 16 independent loads (one memory round
+            // trip per batch instead of one per column), then the updates
+            T* row = A + i + j * n;
+            aj = (T)0;
+            for (int c0 = 0; c0 < w; c0 += 16) {
+                T v[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (c0 + q < w) v[q] = row[(int64_t)(c0 + q) * n];
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    if (c0 + q < w) {
+                        v[q] -= l * urow[c0 + q];
+                        row[(int64_t)(c0 + q) * n] = v[q];
+                    }
+                if (c0 == 0) aj = v[0];
+            }
+        } else {
+            aj = A[i + j * n];
         }
         if (do_pivot) {
-            const double v = fabs((double)A[i + j * n]);
+            const double v = fabs((double)aj);
             if (v > best || (v == best && i < bidx)) {
                 best = v;
                 bidx = i;
@@ -248,27 +267,34 @@ __global__ void k_laswp(T* __restrict__ A, int64_t n, int64_t k0, int64_t k1, co
     }
 }
 
-// Inverse of the unit-lower nb x nb diagonal block at (k0, k0) into W (nb x nb, ld nb).
+// Inverse of the unit-lower nb x nb diagonal block at (k0, k0) into W (nb x nb, ld nb):
+// X = I, then for q = 0 .. nb-2 (row q of X is final) X[r][c] -= L[r][q] X[q][c] for
+// r > q, c <= q -- forward substitution of all columns at once, one block barrier per q,
+// L and X in shared memory.
 template <typename T>
-__global__ void k_trtri_unit_lower(const T* __restrict__ A, int64_t n, int64_t k0, int nb, T* __restrict__ W) {
+__global__ void __launch_bounds__(256) k_trtri_unit_lower(const T* __restrict__ A, int64_t n, int64_t k0, int nb,
+                                                          T* __restrict__ W) {
     extern __shared__ unsigned char smem_raw[];
-    T* L = reinterpret_cast<T*>(smem_raw);  // nb x (nb+1)
     const int ld = nb + 1;
+    T* L = reinterpret_cast<T*>(smem_raw);  // nb x (nb+1)
+    T* X = L + nb * ld;                       // nb x (nb+1)
     for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
         const int r = idx % nb, c = idx / nb;
         L[r + c * ld] = A[(k0 + r) + (k0 + c) * n];
+        X[r + c * ld] = (r == c) ? (T)1 : (T)0;
     }
     __syncthreads();
-    // thread c computes column c of X = L^-1: x_c = 1, x_r = -sum_{c<=s<r} L[r][s] x_s
-    for (int c = threadIdx.x; c < nb; c += blockDim.x) {
-        T* x = W + (int64_t)c * nb;
-        for (int r = 0; r < c; ++r) x[r] = (T)0;
-        x[c] = (T)1;
-        for (int r = c + 1; r < nb; ++r) {
-            T s = (T)0;
-            for (int q = c; q < r; ++q) s += L[r + q * ld] * x[q];
-            x[r] = -s;
+    for (int q = 0; q + 1 < nb; ++q) {
+        const int rows = nb - 1 - q;
+        for (int idx = threadIdx.x; idx < rows * (q + 1); idx += blockDim.x) {
+            const int r = q + 1 + idx % rows, c = idx / rows;
+            X[r + c * ld] -= L[r + q * ld] * X[q + c * ld];
         }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < nb * nb; idx += blockDim.x) {
+        const int r = idx % nb, c = idx / nb;
+        W[r + (int64_t)c * nb] = X[r + c * ld];
     }
 }
 
@@ -354,7 +380,7 @@ cudaError_t gemm(int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t l
 // work layout: [0, nb*nb) L11 inverse; [nb*nb, nb*nb + nb*n) U12 staging;
 // then kPivBlocks doubles + kPivBlocks int64 for the pivot search and one int ticket.
 template <typename T>
-cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_info, cudaStream_t s) {
+cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_info, void* split, cudaStream_t s) {
     // d_info[0]: first zero pivot (1-based) or 0; d_info[1]: tensor-core update gave up
     NB_TRY(cudaMemsetAsync(d_info, 0, 2 * sizeof(int), s));
     T* Linv = work;
@@ -382,7 +408,9 @@ cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_inf
         k_laswp<T><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(A, n, k0, k1, piv);
         if (k1 < n) {
             const int64_t m = n - k1;
-            k_trtri_unit_lower<T><<<1, 128, sizeof(T) * w * (w + 1), s>>>(A, n, k0, w, Linv);
+            const int tri_smem = (int)(2 * sizeof(T) * w * (w + 1));
+            NB_TRY(cudaFuncSetAttribute(k_trtri_unit_lower<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, tri_smem));
+            k_trtri_unit_lower<T><<<1, 256, tri_smem, s>>>(A, n, k0, w, Linv);
             // W = Linv * A12  (w x m), then A12 = W
             NB_TRY(gemm<T>(w, m, w, (T)1, Linv, w, A + k0 + k1 * n, n, (T)0, W, w, s));
             k_copy_block<T><<<(unsigned)((w * m + 255) / 256), 256, 0, s>>>(W, w, A + k0 + k1 * n, n, w, m);
@@ -392,7 +420,7 @@ cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_inf
                 if (w == 64) {
                     NB_TRY(tc_update_f32(m, m, reinterpret_cast<const float*>(A + k1 + k0 * n), n,
                                          reinterpret_cast<const float*>(A + k0 + k1 * n), n,
-                                         reinterpret_cast<float*>(A + k1 + k1 * n), n, d_info + 1, s));
+                                         reinterpret_cast<float*>(A + k1 + k1 * n), n, split, d_info + 1, s));
                     continue;
                 }
             }
@@ -606,10 +634,14 @@ size_t lu_work_elems(int64_t n, int nb) {
 }
 
 cudaError_t lu_factor_f64(double* A, int64_t n, int32_t* piv, int nb, double* work, int* d_info, cudaStream_t s) {
-    return lu_factor<double>(A, n, piv, nb, work, d_info, s);
+    return lu_factor<double>(A, n, piv, nb, work, d_info, nullptr, s);
 }
+static size_t split_offset(int64_t n, int nb) { return (sizeof(float) * lu_work_elems(n, nb) + 255) & ~(size_t)255; }
+size_t lu_work_bytes_f32(int64_t n, int nb) { return split_offset(n, nb) + tc_split_bytes(n, n); }
 cudaError_t lu_factor_f32(float* A, int64_t n, int32_t* piv, int nb, float* work, int* d_info, cudaStream_t s) {
-    return lu_factor<float>(A, n, piv, nb, work, d_info, s);
+    // work: lu_work_bytes_f32(n, nb) bytes, 256-byte aligned
+    void* split = reinterpret_cast<char*>(work) + split_offset(n, nb);
+    return lu_factor<float>(A, n, piv, nb, work, d_info, split, s);
 }
 size_t lu_solve_work_bytes(int64_t n, size_t tsize) { return tsize * (size_t)n + 256; }
 

@@ -19,6 +19,10 @@
 //
 // The mbarrier wait is bounded: after kSpinLimit polls the CTA records an error flag,
 // skips the epilogue, still frees its tensor memory and returns.
+#include <cuda.h>
+
+#include <algorithm>
+
 #include "nb_internal.h"
 
 namespace nb {
@@ -250,11 +254,313 @@ __global__ void __launch_bounds__(128, 2) k_tc_update(int64_t M, int64_t N, cons
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTN));
 }
 
+// ---------------------------------------------------------------- bulk-asynchronous path
+// Operands are split once per panel (k_split_ab) into TF32 hi/lo tiles already in the UMMA
+// K-major layout, so a CTA moves them with single bulk copies; the C tiles move by TMA
+// (a 2-D tensor map over C: 128 rows x 64 columns per box, out-of-range elements zero on
+// load and clipped on store).  One CTA per SM walks tiles_per_cta column tiles of its
+// 128-row strip with every transfer asynchronous:
+//   smem  A hi/lo (64 KB) | B hi/lo x 2 buffers (64 KB) | C x 2 buffers (64 KB) | barriers
+//   tile t: wait B(t) -> 24 MMAs into accumulator t & 1; wait MMAs(t-1) -> prefetch B(t+1);
+//           wait C(t-1) -> C(t-1) -= accumulator in shared memory -> TMA store C(t-1) ->
+//           (store has read the buffer) -> TMA load C(t+1) into it.
+// Each C tile load is issued two tiles ahead of its use and each B tile one tile ahead.
+constexpr uint32_t kASplit = 2 * kABytes;            // 64 KB per 128-row operand tile
+constexpr uint32_t kBSplit = 2 * kBBytes;            // 32 KB per 64-column operand tile
+constexpr uint32_t kCTile = kTM * kTN * 4;           // 32 KB
+constexpr uint32_t kBulkSmem = kASplit + 2 * kBSplit + 2 * kCTile + 128;
+
+__device__ __forceinline__ void mbar_init(uint64_t* b) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(b)));
+}
+__device__ __forceinline__ void mbar_expect(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+// bounded wait for completion `parity` of barrier b; 1 = completed
+__device__ __forceinline__ int mbar_wait(uint64_t* b, uint32_t parity) {
+    uint32_t done = 0;
+    for (long long it = 0; it < kSpinLimit && !done; ++it) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_u32(b)), "r"(parity)
+            : "memory");
+    }
+    return (int)done;
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(b))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_c(void* dst, const CUtensorMap* map, int x, int y, uint64_t* b) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(b))
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_c(const CUtensorMap* map, int x, int y, const void* src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(smem_u32(src))
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// A (M x 64, column-major) and B (64 x N) into TF32 hi/lo operand tiles: A tile tm at
+// asplit + tm * 64 KB (hi, then lo), B tile tn at bsplit + tn * 32 KB; rows of A beyond M
+// and columns of B beyond N are zero.
+__global__ void k_split_ab(const float* __restrict__ A, int64_t lda, const float* __restrict__ B, int64_t ldb,
+                           int64_t M, int64_t N, int64_t tiles_m, int64_t tiles_n, unsigned char* __restrict__ asplit,
+                           unsigned char* __restrict__ bsplit) {
+    const int64_t na = tiles_m * (kTM * kTK), nb = tiles_n * (kTN * kTK);
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < na + nb;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        if (idx < na) {
+            const int64_t tm = idx / (kTM * kTK);
+            const int e = (int)(idx - tm * (kTM * kTK));
+            const int r = e % kTM, k = e / kTM;
+            const int64_t gm = tm * kTM + r;
+            const float x = gm < M ? A[gm + (int64_t)k * lda] : 0.f;
+            unsigned char* t = asplit + tm * kASplit;
+            put_pair(t, t + kABytes, kmajor_off(r, k), x);
+        } else {
+            const int64_t i2 = idx - na;
+            const int64_t tn = i2 / (kTN * kTK);
+            const int e = (int)(i2 - tn * (kTN * kTK));
+            const int k = e % kTK, c = e / kTK;
+            const int64_t gn = tn * kTN + c;
+            const float x = gn < N ? B[k + gn * ldb] : 0.f;
+            unsigned char* t = bsplit + tn * kBSplit;
+            put_pair(t, t + kBBytes, kmajor_off(c, k), x);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128, 1)
+    k_tc_update_bulk(const __grid_constant__ CUtensorMap cmap, int64_t M, int64_t N,
+                     const unsigned char* __restrict__ asplit, const unsigned char* __restrict__ bsplit, int tpc,
+                     int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sA = smem;
+    unsigned char* sB0 = smem + kASplit;
+    unsigned char* sC0 = smem + kASplit + 2 * kBSplit;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kASplit + 2 * kBSplit + 2 * kCTile);
+    uint64_t* barA = bar;
+    uint64_t* barB = bar + 1;  // [2]
+    uint64_t* barC = bar + 3;  // [2]
+    uint64_t* barM = bar + 5;  // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 8);
+
+    const int64_t tiles_n = (N + kTN - 1) / kTN;
+    const int64_t t0 = (int64_t)blockIdx.y * tpc;
+    const int nt = (int)min((int64_t)tpc, tiles_n - t0);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = (int)(blockIdx.x * kTM);
+    auto sB = [&](int s) { return sB0 + s * kBSplit; };
+    auto sC = [&](int s) { return reinterpret_cast<float*>(sC0 + s * kCTile); };
+    auto load_b = [&](int t) {
+        const int s = t & 1;
+        mbar_expect(barB + s, kBSplit);
+        bulk_load(sB(s), bsplit + (t0 + t) * (int64_t)kBSplit, kBSplit, barB + s);
+    };
+    auto load_c = [&](int t) {
+        const int s = t & 1;
+        mbar_expect(barC + s, kCTile);
+        tma_load_c(sC(s), &cmap, m0, (int)((t0 + t) * kTN), barC + s);
+    };
+
+    if (tid == 0) {
+        for (int b = 0; b < 7; ++b) mbar_init(bar + b);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_expect(barA, kASplit);
+        bulk_load(sA, asplit + (int64_t)blockIdx.x * kASplit, kASplit, barA);
+        if (nt > 0) {
+            load_b(0);
+            load_c(0);
+        }
+        if (nt > 1) {
+            load_b(1);
+            load_c(1);
+        }
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(2 * kTN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tmem_slot;
+
+    // completions consumed per barrier (the next wait's parity) and loads / commits issued
+    int used_b[2] = {0, 0}, used_c[2] = {0, 0}, used_m[2] = {0, 0};
+    int iss_b[2] = {nt > 0, nt > 1}, iss_c[2] = {nt > 0, nt > 1}, iss_m[2] = {0, 0}, a_used = 0;
+    int ok = 1;
+
+    // C(t) -= accumulator (t & 1), in shared memory, then stored by TMA
+    auto finish_tile = [&](int t) -> int {
+        const int s = t & 1;
+        int w = mbar_wait(barM + s, (uint32_t)(used_m[s] & 1));
+        if (!__syncthreads_and(w)) return 0;
+        ++used_m[s];
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        // the MMAs of tile t have read B buffer s: prefetch B(t + 2)
+        if (tid == 0 && t + 2 < nt) {
+            load_b(t + 2);
+            iss_b[s]++;
+        }
+        w = mbar_wait(barC + s, (uint32_t)(used_c[s] & 1));
+        if (!__syncthreads_and(w)) return 0;
+        ++used_c[s];
+        float* c = sC(s);
+        const int r = warp * 32 + lane;
+#pragma unroll
+        for (int cb = 0; cb < kTN; cb += 32) {
+            uint32_t v[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * kTN + cb);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 32; ++j) c[(cb + j) * kTM + r] -= __uint_as_float(v[j]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        if (tid == 0) {
+            tma_store_c(&cmap, m0, (int)((t0 + t) * kTN), c);
+            if (t + 2 < nt) {
+                // the store must have read the buffer before the next tile lands in it
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                load_c(t + 2);
+                iss_c[s]++;
+            }
+        }
+        return 1;
+    };
+
+    for (int t = 0; t < nt && ok; ++t) {
+        const int s = t & 1;
+        int w = mbar_wait(barB + s, (uint32_t)(used_b[s] & 1));
+        if (t == 0) w = w && mbar_wait(barA, 0);
+        if (!__syncthreads_and(w)) {
+            ok = 0;
+            break;
+        }
+        ++used_b[s];
+        a_used = 1;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (tid == 0) {
+            const unsigned char* As[3] = {sA + kABytes, sA, sA};
+            const unsigned char* Bs[3] = {sB(s), sB(s) + kBBytes, sB(s)};
+            uint32_t first = 1;
+            for (int q = 0; q < 3; ++q) {
+                for (int ks = 0; ks < kTK / 8; ++ks) {
+                    const uint64_t ad = make_desc(smem_u32(As[q]) + (uint32_t)ks * 2u * kLBO);
+                    const uint64_t bd = make_desc(smem_u32(Bs[q]) + (uint32_t)ks * 2u * kLBO);
+                    const uint32_t acc = first ? 0u : 1u;
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + (uint32_t)(s * kTN)),
+                        "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+                    first = 0;
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(barM + s)));
+        }
+        iss_m[s]++;
+        if (t > 0 && !finish_tile(t - 1)) ok = 0;
+    }
+    if (ok && nt > 0 && !finish_tile(nt - 1)) ok = 0;
+
+    if (!ok) {
+        if (tid == 0) atomicExch(err, 1);
+        // let every transfer and MMA this CTA started finish (bounded) before its shared
+        // and tensor memory go away
+        if (tid == 0) {
+            if (!a_used) mbar_wait(barA, 0);
+            for (int s = 0; s < 2; ++s) {
+                if (iss_b[s] > used_b[s]) mbar_wait(barB + s, (uint32_t)(used_b[s] & 1));
+                if (iss_c[s] > used_c[s]) mbar_wait(barC + s, (uint32_t)(used_c[s] & 1));
+                if (iss_m[s] > used_m[s]) mbar_wait(barM + s, (uint32_t)(used_m[s] & 1));
+            }
+        }
+    }
+    if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTN));
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
 }  // namespace
 
+size_t tc_split_bytes(int64_t M, int64_t N) {
+    return (size_t)((M + kTM - 1) / kTM) * kASplit + (size_t)((N + kTN - 1) / kTN) * kBSplit;
+}
+
 cudaError_t tc_update_f32(int64_t M, int64_t N, const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
-                          int64_t ldc, int* err, cudaStream_t s) {
+                          int64_t ldc, void* split, int* err, cudaStream_t s) {
     if (M <= 0 || N <= 0) return cudaSuccess;
+    // bulk-asynchronous path: C rows in 16-byte units (TMA strides and coordinates)
+    EncodeTiledFn enc = split ? encode_tiled() : nullptr;
+    if (enc && (ldc % 4) == 0 && (((uintptr_t)C & 15) == 0) && M <= INT32_MAX && N <= INT32_MAX) {
+        CUtensorMap map;
+        const cuuint64_t dims[2] = {(cuuint64_t)M, (cuuint64_t)N};
+        const cuuint64_t strides[1] = {(cuuint64_t)ldc * sizeof(float)};
+        const cuuint32_t box[2] = {(cuuint32_t)kTM, (cuuint32_t)kTN};
+        const cuuint32_t estr[2] = {1, 1};
+        if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, C, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+            const int64_t tiles_m = (M + kTM - 1) / kTM, tiles_n = (N + kTN - 1) / kTN;
+            unsigned char* asplit = static_cast<unsigned char*>(split);
+            unsigned char* bsplit = asplit + (size_t)tiles_m * kASplit;
+            const int64_t total = tiles_m * kTM * kTK + tiles_n * kTN * kTK;
+            k_split_ab<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16), 256, 0, s>>>(
+                A, lda, B, ldb, M, N, tiles_m, tiles_n, asplit, bsplit);
+            cudaError_t e = cudaFuncSetAttribute(k_tc_update_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)kBulkSmem);
+            if (e != cudaSuccess) return e;
+            // column tiles per CTA: enough CTAs for two waves of the SMs, at most 16 tiles each
+            int64_t tpc = (tiles_m * tiles_n) / (2 * 152);
+            tpc = std::max<int64_t>(1, std::min<int64_t>(16, tpc));
+            dim3 grid((unsigned)tiles_m, (unsigned)((tiles_n + tpc - 1) / tpc));
+            k_tc_update_bulk<<<grid, 128, kBulkSmem, s>>>(map, M, N, asplit, bsplit, (int)tpc, err);
+            return cudaGetLastError();
+        }
+    }
     // set for the current device on every call (an attribute is per device)
     cudaError_t e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;

@@ -149,9 +149,12 @@ cudaError_t launch_element_influence(const Elem* el, int64_t n_el, const double*
                                      double* phi, double* E, cudaStream_t s);
 
 // C[M x N] -= A[M x 64] * B[64 x N] on tcgen05 tensor cores (TF32 x3 split, FP32
-// accumulation); *err is set if the bounded wait for the MMAs gave up.
+// accumulation); *err is set if a bounded wait gave up.  split (may be NULL): device work
+// space of tc_split_bytes(M, N) bytes (256-byte aligned) for the pre-split operand tiles of
+// the bulk-asynchronous path, taken when ldc % 4 == 0 and C is 16-byte aligned.
 cudaError_t tc_update_f32(int64_t M, int64_t N, const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
-                          int64_t ldc, int* err, cudaStream_t s);
+                          int64_t ldc, void* split, int* err, cudaStream_t s);
+size_t tc_split_bytes(int64_t M, int64_t N);
 
 // Dense LU (column-major, lda = n).  d_info: two ints (first zero pivot, tensor-core timeout).  Scratch: pivots int32[n], work as documented in lu.cu.
 cudaError_t lu_factor_f64(double* A, int64_t n, int32_t* piv, int nb, double* work, int* d_info,
@@ -159,6 +162,9 @@ cudaError_t lu_factor_f64(double* A, int64_t n, int32_t* piv, int nb, double* wo
 cudaError_t lu_factor_f32(float* A, int64_t n, int32_t* piv, int nb, float* work, int* d_info,
                           cudaStream_t s);
 size_t lu_work_elems(int64_t n, int nb);
+// bytes of work space lu_factor_f32 takes (lu_work_elems floats, then the split operands of
+// the tensor-core updates)
+size_t lu_work_bytes_f32(int64_t n, int nb);
 // Solves with the factors: perm from lu_make_perm (b'[i] = b[perm[i]] applies the pivot
 // swaps), work of lu_solve_work_bytes(n, sizeof(T)) bytes (16-byte aligned).
 cudaError_t lu_make_perm(const int32_t* piv, int64_t n, int32_t* perm, cudaStream_t s);

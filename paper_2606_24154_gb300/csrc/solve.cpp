@@ -105,7 +105,7 @@ int ensure_factors(Ctx* c, int precision, double* ms) {
         if (c->fac32_valid) return 0;
         CK(c->d_LU32.ensure(sizeof(float) * n * n));
         CK(c->d_piv32.ensure(sizeof(int32_t) * n));
-        CK(c->d_work.ensure(sizeof(double) * lu_work_elems(n, nb)));
+        CK(c->d_work.ensure(std::max(sizeof(double) * lu_work_elems(n, nb), lu_work_bytes_f32(n, nb))));
         CK(c->d_small.ensure(256));
         CK(cudaEventRecord(c->ev0, c->stream));
         CK(copy_f64_to_f32(c->d_K.as<double>(), c->d_LU32.as<float>(), n * n, c->stream));

@@ -1,6 +1,8 @@
 """FP32 LU with tensor-core (tcgen05, TF32 hi/lo split) trailing updates: the factors
 reproduce P A = L U to FP32-level accuracy on ragged sizes (several 128 x 128 tiles and
-partial tiles), and refined solutions match the FP64 oracle."""
+partial tiles), and refined solutions match the FP64 oracle.  Sizes with n % 4 == 0 take
+the bulk-asynchronous update (pre-split operands, TMA-moved C tiles; 4100 gives CTAs
+several column tiles each), the others the register-staged update."""
 import numpy as np
 import pytest
 
@@ -29,7 +31,7 @@ def _unpack(LU, piv):
     return L, U, perm
 
 
-@pytest.mark.parametrize("n", [64, 200, 333, 700])
+@pytest.mark.parametrize("n", [64, 200, 333, 700, 1028, 4100])
 def test_fp32_tensor_core_lu_reconstructs(N, n):
     import torch
     gen = np.random.default_rng(n)
