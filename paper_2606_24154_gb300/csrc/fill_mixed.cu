@@ -9,7 +9,8 @@
 // and products and sums keep their rounding errors through error-free transformations
 // (Dekker / Knuth TwoSum, FMA-based TwoProd), about 44 significant bits.  Near pairs use the
 // FP64 closed forms of influence.cuh.  The FP32 pipe runs 64 times the FP64 rate on this
-// GPU, so a two-float node (50-85 FP32 operations) costs about as much as one FP64 operation.
+// GPU, so a two-float node (54-91 FP32 lane operations, issued two nodes per packed FP32x2
+// instruction) costs about as much as one FP64 operation.
 //
 // Geometry of one pair in the local frame of the column element j (origin anywhere, axes
 // ex, ey = normal, ez): D = c_i - (c_j + t_k) has components
@@ -98,98 +99,137 @@ __device__ __forceinline__ void df_norm2(float xh, float xl, float yh, float yl,
     l = __fadd_rn(__fadd_rn(ex, ey), __fadd_rn(ez, __fadd_rn(t1, t2)));
 }
 
-// Per-image quantities of one pair in the column element's frame.
-struct PairDF {
-    float xh, xl, zh, zl;  // X, Z
-    float d2h, d2l;        // |D|^2
-    float ndh, ndl;        // n_i . D (interface rows)
-};
-
-// r^2 and 1/r (two-float) for one node; returns y0 (= hi of 1/r), yl, and the exact square
-// y0^2 = a + ae.
-__device__ __forceinline__ void node_rinv(const PairDF& P, const float4& u, const float4& v, float& y0, float& yl,
-                                          float& a, float& ae) {
-    float p1, e1, p2, e2, qh, t, t2, r2h, t3;
-    two_prod(P.xh, u.x, p1, e1);
-    two_prod(P.zh, u.y, p2, e2);
-    two_sum(p1, p2, qh, t);
-    float lo = __fadd_rn(t, __fadd_rn(e1, e2));
-    lo = __fmaf_rn(P.xh, v.x, lo);
-    lo = __fmaf_rn(P.xl, u.x, lo);
-    lo = __fmaf_rn(P.zh, v.y, lo);
-    lo = __fmaf_rn(P.zl, u.y, lo);
-    two_sum(qh, u.z, qh, t2);
-    lo = __fadd_rn(lo, __fadd_rn(t2, v.z));
-    // |D|^2 >= |q| for d >= kFillRatioC rho (|q| <= 2 d rho + rho^2)
-    fast_two_sum(P.d2h, qh, r2h, t3);
-    const float r2l = __fadd_rn(P.d2l, __fadd_rn(lo, t3));
-    // Newton step for r^-1/2 from the MUFU estimate: y = y0 (1 + h/2), h = 1 - r^2 y0^2
-    y0 = rsqrtf(r2h);
-    float b, be;
-    two_prod(y0, y0, a, ae);
-    two_prod(r2h, a, b, be);
-    float h = __fsub_rn(__fsub_rn(1.0f, b), be);  // 1 - b is exact (b within 2^-20 of 1)
-    h = __fmaf_rn(-r2h, ae, h);
-    h = __fmaf_rn(-r2l, a, h);
-    yl = __fmul_rn(__fmul_rn(0.5f, y0), h);
+// ---------------------------------------------------------------- packed two-float nodes
+// Two Gauss nodes per instruction in the packed FP32x2 forms (__fadd2_rn, __fmul2_rn,
+// __ffma2_rn; a - b as fma(b, -1, a), exact like a subtraction).  Error terms of products
+// come out negated, e_neg = fma(-a, b, a b) = -(a b - fl(a b)), so that no extra negation is
+// needed; the running sum keeps its low part negated as well (NL = -lo).
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& t) {
+    s = __fadd2_rn(a, b);
+    const float2 bb = sub2(s, a);
+    t = __fadd2_rn(sub2(a, sub2(s, bb)), sub2(b, bb));
 }
 
-// Phi' nodes: S += w / r
-__device__ __forceinline__ void nodes_phi(const float4* __restrict__ nd, int cnt, const PairDF& P, float& sh,
-                                          float& sl) {
-    for (int q = 0; q < cnt; ++q) {
-        const float4 u = nd[2 * q], v = nd[2 * q + 1];
-        float y0, yl, a, ae;
-        node_rinv(P, u, v, y0, yl, a, ae);
-        float m, me, t;
-        two_prod(u.w, y0, m, me);
-        me = __fmaf_rn(u.w, yl, me);
-        me = __fmaf_rn(v.w, y0, me);
-        two_sum(sh, m, sh, t);
-        sl = __fadd_rn(sl, __fadd_rn(me, t));
+// Per-image quantities of one pair in the column element's frame, broadcast to both lanes
+// (negated copies for the error terms of products).
+struct PairDF2 {
+    float2 xh, nxh, xl, zh, nzh, zl;  // X, Z
+    float2 d2h, d2l;                  // |D|^2
+};
+struct NormDF2 {
+    float2 nxh, nnxh, nxl, nzh, nnzh, nzl;  // local components of the row normal (x, z)
+    float2 ndh, ndl;                        // n_i . D
+};
+
+// r^2 = |D|^2 + 2 (X s_x + Z s_z) + |s|^2 and 1/r for a node pair: y0 (MUFU estimate), the
+// Newton correction negated (nyl = -yl), y0^2 = a exactly with its negated error nae.
+__device__ __forceinline__ void node_rinv2(const PairDF2& P, const float4& q0, const float4& q1, const float4& q2,
+                                           const float4& q3, float2& y0, float2& ny0, float2& nyl, float2& a,
+                                           float2& na, float2& nae) {
+    const float2 m1 = bc2(-1.f);
+    const float2 sx = make_float2(q0.x, q0.y), sz = make_float2(q0.z, q0.w);
+    const float2 s2 = make_float2(q1.x, q1.y);
+    const float2 sxl = make_float2(q2.x, q2.y), szl = make_float2(q2.z, q2.w);
+    const float2 s2l = make_float2(q3.x, q3.y);
+    const float2 p1 = __fmul2_rn(P.xh, sx), ne1 = __ffma2_rn(P.nxh, sx, p1);
+    const float2 p2 = __fmul2_rn(P.zh, sz), ne2 = __ffma2_rn(P.nzh, sz, p2);
+    float2 qh, t, t2;
+    two_sum2(p1, p2, qh, t);
+    float2 lo = __ffma2_rn(ne1, m1, t);
+    lo = __ffma2_rn(ne2, m1, lo);
+    lo = __ffma2_rn(P.xh, sxl, lo);
+    lo = __ffma2_rn(P.xl, sx, lo);
+    lo = __ffma2_rn(P.zh, szl, lo);
+    lo = __ffma2_rn(P.zl, sz, lo);
+    two_sum2(qh, s2, qh, t2);
+    lo = __fadd2_rn(lo, __fadd2_rn(t2, s2l));
+    // |D|^2 >= |q| for d >= kFillRatioC rho (|q| <= 2 d rho + rho^2)
+    const float2 r2h = __fadd2_rn(P.d2h, qh);
+    const float2 t3 = sub2(qh, sub2(r2h, P.d2h));
+    const float2 r2l = __fadd2_rn(P.d2l, __fadd2_rn(lo, t3));
+    y0 = make_float2(rsqrtf(r2h.x), rsqrtf(r2h.y));
+    ny0 = __fmul2_rn(y0, m1);
+    a = __fmul2_rn(y0, y0);
+    nae = __ffma2_rn(ny0, y0, a);  // a - y0^2
+    na = __fmul2_rn(ny0, y0);
+    const float2 b = __fmul2_rn(r2h, a);
+    const float2 nbe = __ffma2_rn(r2h, na, b);  // b - r2h a
+    // h = 1 - r^2 y0^2 (1 - b is exact: b within 2^-20 of 1)
+    float2 h = __ffma2_rn(b, m1, bc2(1.f));
+    h = __fadd2_rn(h, nbe);
+    h = __ffma2_rn(r2h, nae, h);
+    h = __ffma2_rn(r2l, na, h);
+    nyl = __fmul2_rn(__fmul2_rn(bc2(-0.5f), y0), h);
+}
+
+// Phi' nodes: S += w / r (sh = hi sum, nl = -lo sum), two nodes per step
+__device__ __forceinline__ void nodes_phi2(const float4* __restrict__ nd, int pairs, const PairDF2& P, float2& sh,
+                                           float2& nl) {
+    const float2 m1 = bc2(-1.f);
+    for (int q = 0; q < pairs; ++q) {
+        const float4 q0 = nd[4 * q], q1 = nd[4 * q + 1], q2 = nd[4 * q + 2], q3 = nd[4 * q + 3];
+        float2 y0, ny0, nyl, a, na, nae;
+        node_rinv2(P, q0, q1, q2, q3, y0, ny0, nyl, a, na, nae);
+        const float2 w = make_float2(q1.z, q1.w), wl = make_float2(q3.z, q3.w);
+        const float2 m = __fmul2_rn(w, y0);
+        float2 nme = __ffma2_rn(w, ny0, m);  // m - w y0
+        nme = __ffma2_rn(w, nyl, nme);
+        nme = __ffma2_rn(wl, ny0, nme);
+        float2 t;
+        two_sum2(sh, m, sh, t);
+        nl = __ffma2_rn(t, m1, __fadd2_rn(nl, nme));
     }
 }
 
 // n . E' nodes: S += w (n . (D + s)) / r^3, with n . s = (n . ex) s_x + (n . ez) s_z
-__device__ __forceinline__ void nodes_nE(const float4* __restrict__ nd, int cnt, const PairDF& P, float nxh,
-                                         float nxl, float nzh, float nzl, float& sh, float& sl) {
-    for (int q = 0; q < cnt; ++q) {
-        const float4 u = nd[2 * q], v = nd[2 * q + 1];
-        float y0, yl, a, ae;
-        node_rinv(P, u, v, y0, yl, a, ae);
+__device__ __forceinline__ void nodes_nE2(const float4* __restrict__ nd, int pairs, const PairDF2& P,
+                                          const NormDF2& Nn, float2& sh, float2& nl) {
+    const float2 m1 = bc2(-1.f), half = bc2(0.5f);
+    for (int q = 0; q < pairs; ++q) {
+        const float4 q0 = nd[4 * q], q1 = nd[4 * q + 1], q2 = nd[4 * q + 2], q3 = nd[4 * q + 3];
+        float2 y0, ny0, nyl, a, na, nae;
+        node_rinv2(P, q0, q1, q2, q3, y0, ny0, nyl, a, na, nae);
+        const float2 sx = make_float2(q0.x, q0.y), sz = make_float2(q0.z, q0.w);
+        const float2 sxl = make_float2(q2.x, q2.y), szl = make_float2(q2.z, q2.w);
         // 2 (n . s)
-        float p1, e1, p2, e2, ns, t;
-        two_prod(nxh, u.x, p1, e1);
-        two_prod(nzh, u.y, p2, e2);
-        two_sum(p1, p2, ns, t);
-        float nsl = __fadd_rn(t, __fadd_rn(e1, e2));
-        nsl = __fmaf_rn(nxh, v.x, nsl);
-        nsl = __fmaf_rn(nxl, u.x, nsl);
-        nsl = __fmaf_rn(nzh, v.y, nsl);
-        nsl = __fmaf_rn(nzl, u.y, nsl);
-        // n . (D + s)
-        float gh, t2;
-        two_sum(P.ndh, __fmul_rn(0.5f, ns), gh, t2);
-        const float gl = __fadd_rn(P.ndl, __fadd_rn(__fmul_rn(0.5f, nsl), t2));
-        // y^3 = (y0 + yl)^3: y^2 = a + (ae + 2 y0 yl), y^3 = y^2 y
-        const float y2l = __fmaf_rn(__fadd_rn(y0, y0), yl, ae);
-        float c3, c3e;
-        two_prod(a, y0, c3, c3e);
-        c3e = __fmaf_rn(a, yl, c3e);
-        c3e = __fmaf_rn(y2l, y0, c3e);
-        // w y^3
-        float m, me;
-        two_prod(u.w, c3, m, me);
-        me = __fmaf_rn(u.w, c3e, me);
-        me = __fmaf_rn(v.w, c3, me);
-        // (w y^3) (n . (D + s))
-        float f, fe;
-        two_prod(m, gh, f, fe);
-        fe = __fmaf_rn(m, gl, fe);
-        fe = __fmaf_rn(me, gh, fe);
-        float t3;
-        two_sum(sh, f, sh, t3);
-        sl = __fadd_rn(sl, __fadd_rn(fe, t3));
+        const float2 p1 = __fmul2_rn(Nn.nxh, sx), ne1 = __ffma2_rn(Nn.nnxh, sx, p1);
+        const float2 p2 = __fmul2_rn(Nn.nzh, sz), ne2 = __ffma2_rn(Nn.nnzh, sz, p2);
+        float2 ns, t;
+        two_sum2(p1, p2, ns, t);
+        float2 nsl = __ffma2_rn(ne1, m1, t);
+        nsl = __ffma2_rn(ne2, m1, nsl);
+        nsl = __ffma2_rn(Nn.nxh, sxl, nsl);
+        nsl = __ffma2_rn(Nn.nxl, sx, nsl);
+        nsl = __ffma2_rn(Nn.nzh, szl, nsl);
+        nsl = __ffma2_rn(Nn.nzl, sz, nsl);
+        // g = n . (D + s)
+        float2 gh, t2;
+        two_sum2(Nn.ndh, __fmul2_rn(half, ns), gh, t2);
+        const float2 gl = __fadd2_rn(__ffma2_rn(half, nsl, Nn.ndl), t2);
+        // y^3 = y^2 y, y^2 = a + (ae + 2 y0 yl): negated low parts
+        const float2 ny2l = __ffma2_rn(__fadd2_rn(y0, y0), nyl, nae);
+        const float2 c3 = __fmul2_rn(a, y0);
+        float2 nc3e = __ffma2_rn(na, y0, c3);  // c3 - a y0
+        nc3e = __ffma2_rn(a, nyl, nc3e);
+        nc3e = __ffma2_rn(ny2l, y0, nc3e);
+        // w y^3 = m + me
+        const float2 w = make_float2(q1.z, q1.w), wl = make_float2(q3.z, q3.w);
+        const float2 nc3 = __fmul2_rn(c3, m1);
+        const float2 m = __fmul2_rn(w, c3);
+        float2 nme = __ffma2_rn(w, nc3, m);  // m - w c3
+        nme = __ffma2_rn(w, nc3e, nme);
+        nme = __ffma2_rn(wl, nc3, nme);
+        // (w y^3) g = f + fe
+        const float2 nm = __fmul2_rn(m, m1);
+        const float2 f = __fmul2_rn(m, gh);
+        float2 nfe = __ffma2_rn(nm, gh, f);  // f - m gh
+        nfe = __ffma2_rn(nm, gl, nfe);
+        nfe = __ffma2_rn(nme, gh, nfe);
+        float2 t3;
+        two_sum2(sh, f, sh, t3);
+        nl = __ffma2_rn(t3, m1, __fadd2_rn(nl, nfe));
     }
 }
 
@@ -199,7 +239,7 @@ __device__ __forceinline__ void stage(float4* dst, const float4* __restrict__ sr
 
 // Dynamic shared memory per tile of te elements: FillEl (9 float4), tier-a nodes (18 float4),
 // tau and image centroids (2 float4 each per image).
-__host__ __device__ constexpr int fill_tile_f4(int te, int nimg) { return te * (9 + 2 * kFillNodesA + 4 * nimg); }
+__host__ __device__ constexpr int fill_tile_f4(int te, int nimg) { return te * (9 + 4 * kFillPairsA + 4 * nimg); }
 
 __global__ void __launch_bounds__(kFT, 4)
     k_fill_far(const FillEl* __restrict__ fe, const float4* __restrict__ nodes, const float4* __restrict__ tau,
@@ -208,7 +248,7 @@ __global__ void __launch_bounds__(kFT, 4)
     extern __shared__ float4 sm[];
     FillEl* s_fe = reinterpret_cast<FillEl*>(sm);
     float4* s_na = sm + 9 * te;
-    float4* s_tau = s_na + 2 * kFillNodesA * te;
+    float4* s_tau = s_na + 4 * kFillPairsA * te;
     float4* s_c = s_tau + 2 * nimg * te;
 
     const int64_t i = (int64_t)blockIdx.x * kFT + threadIdx.x;
@@ -233,8 +273,8 @@ __global__ void __launch_bounds__(kFT, 4)
         const int cnt = (int)min((int64_t)te, j1 - base);
         __syncthreads();
         stage(reinterpret_cast<float4*>(s_fe), reinterpret_cast<const float4*>(fe + base), 9 * cnt);
-        for (int e = threadIdx.x; e < cnt * 2 * kFillNodesA; e += blockDim.x) {
-            const int jj = e / (2 * kFillNodesA), q = e - jj * 2 * kFillNodesA;
+        for (int e = threadIdx.x; e < cnt * 4 * kFillPairsA; e += blockDim.x) {
+            const int jj = e / (4 * kFillPairsA), q = e - jj * 4 * kFillPairsA;
             s_na[e] = nodes[(base + jj) * kFillNodeRec + q];
         }
         stage(s_tau, tau + 2 * base * nimg, 2 * cnt * nimg);
@@ -260,41 +300,52 @@ __global__ void __launch_bounds__(kFT, 4)
                 df_dot3(nh, nl, E.eyh, E.eyl, nyh, nyl);
                 df_dot3(nh, nl, E.ezh, E.ezl, nzh, nzl);
             }
-            float sh = 0.f, sl = 0.f;
+            NormDF2 Nn;
+            if (iface) {
+                Nn.nxh = bc2(nxh), Nn.nnxh = bc2(-nxh), Nn.nxl = bc2(nxl);
+                Nn.nzh = bc2(nzh), Nn.nnzh = bc2(-nzh), Nn.nzl = bc2(nzl);
+            }
+            float2 sh = bc2(0.f), snl = bc2(0.f);  // sum: hi, negated lo
             for (int k = 0; k < nimg; ++k) {
                 float dx, dy, dz;
                 const float d2 = pair_d2(ch[0], ch[1], ch[2], cl[0], cl[1], cl[2], s_c[2 * (jj * nimg + k)],
                                          s_c[2 * (jj * nimg + k) + 1], dx, dy, dz);
                 if (!(d2 >= hdr.z)) continue;  // near pair: k_fill_near
                 const float4 th = s_tau[2 * (jj * nimg + k)], tl = s_tau[2 * (jj * nimg + k) + 1];
-                PairDF P;
-                float yh, yl;
-                df_sub(x0h, x0l, th.x, tl.x, P.xh, P.xl);
+                float xh, xl, yh, yl, zh, zl, d2h, d2l;
+                df_sub(x0h, x0l, th.x, tl.x, xh, xl);
                 df_sub(y0h, y0l, th.y, tl.y, yh, yl);
-                df_sub(z0h, z0l, th.z, tl.z, P.zh, P.zl);
-                df_norm2(P.xh, P.xl, yh, yl, P.zh, P.zl, P.d2h, P.d2l);
+                df_sub(z0h, z0l, th.z, tl.z, zh, zl);
+                df_norm2(xh, xl, yh, yl, zh, zl, d2h, d2l);
+                PairDF2 P;
+                P.xh = bc2(xh), P.nxh = bc2(-xh), P.xl = bc2(xl);
+                P.zh = bc2(zh), P.nzh = bc2(-zh), P.zl = bc2(zl);
+                P.d2h = bc2(d2h), P.d2l = bc2(d2l);
                 const float4* nd;
-                int nn;
+                int np;
                 if (d2 >= hdr.x) {
-                    nd = s_na + jj * 2 * kFillNodesA;
-                    nn = na;
+                    nd = s_na + jj * 4 * kFillPairsA;
+                    np = na;
                 } else if (d2 >= hdr.y) {
                     nd = nodes + j * kFillNodeRec + kFillOffB;
-                    nn = kFillNodesB;
+                    np = kFillPairsB;
                 } else {
                     nd = nodes + j * kFillNodeRec + kFillOffC;
-                    nn = kFillNodesC;
+                    np = kFillPairsC;
                 }
                 if (!iface) {
-                    nodes_phi(nd, nn, P, sh, sl);
+                    nodes_phi2(nd, np, P, sh, snl);
                 } else {
-                    const float Xh[3] = {P.xh, yh, P.zh}, Xl[3] = {P.xl, yl, P.zl};
-                    df_dot3(Xh, Xl, make_float4(nxh, nyh, nzh, 0.f), make_float4(nxl, nyl, nzl, 0.f), P.ndh, P.ndl);
-                    nodes_nE(nd, nn, P, nxh, nxl, nzh, nzl, sh, sl);
+                    const float Xh[3] = {xh, yh, zh}, Xl[3] = {xl, yl, zl};
+                    float ndh, ndl;
+                    df_dot3(Xh, Xl, make_float4(nxh, nyh, nzh, 0.f), make_float4(nxl, nyl, nzl, 0.f), ndh, ndl);
+                    Nn.ndh = bc2(ndh), Nn.ndl = bc2(ndl);
+                    nodes_nE2(nd, np, P, Nn, sh, snl);
                 }
             }
             if (active) {
-                const double acc = (double)sh + (double)sl;
+                // the two lanes' sums (hi + lo each) in FP64
+                const double acc = ((double)sh.x - (double)snl.x) + ((double)sh.y - (double)snl.y);
                 K[i + j * n] = (i == j) ? fma(ke, acc, diag) : ke * acc;
             }
         }

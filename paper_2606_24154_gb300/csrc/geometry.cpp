@@ -296,16 +296,30 @@ inline float4 f4(float a, float b, float c, float d) {
     return r;
 }
 
-// Two-float node record (u = hi parts, v = lo parts) of the offset s = centroid - node in
-// the local frame and the weight w.
-inline void fill_node(double sx, double sz, double w, float4* dst) {
-    float a[4], b[4];
-    split_f(2.0 * sx, a[0], b[0]);
-    split_f(2.0 * sz, a[1], b[1]);
-    split_f(sx * sx + sz * sz, a[2], b[2]);
-    split_f(w, a[3], b[3]);
-    dst[0] = f4(a[0], a[1], a[2], a[3]);
-    dst[1] = f4(b[0], b[1], b[2], b[3]);
+// Two-float node record of the offset s = centroid - node (local frame) and weight w, for
+// a node pair (a, b): see nb_internal.h.
+struct FillNode {
+    double sx, sz, w;
+};
+
+inline void pack_fill_pairs(const FillNode* nd, int cnt, float4* dst) {
+    for (int p = 0; p < (cnt + 1) / 2; ++p) {
+        const FillNode a = nd[2 * p];
+        FillNode b = (2 * p + 1 < cnt) ? nd[2 * p + 1] : nd[2 * p];
+        if (2 * p + 1 >= cnt) b.w = 0.0;
+        float h[2][4], l[2][4];
+        const FillNode* ab[2] = {&a, &b};
+        for (int q = 0; q < 2; ++q) {
+            split_f(2.0 * ab[q]->sx, h[q][0], l[q][0]);
+            split_f(2.0 * ab[q]->sz, h[q][1], l[q][1]);
+            split_f(ab[q]->sx * ab[q]->sx + ab[q]->sz * ab[q]->sz, h[q][2], l[q][2]);
+            split_f(ab[q]->w, h[q][3], l[q][3]);
+        }
+        dst[4 * p + 0] = f4(h[0][0], h[1][0], h[0][1], h[1][1]);
+        dst[4 * p + 1] = f4(h[0][2], h[1][2], h[0][3], h[1][3]);
+        dst[4 * p + 2] = f4(l[0][0], l[1][0], l[0][1], l[1][1]);
+        dst[4 * p + 3] = f4(l[0][2], l[1][2], l[0][3], l[1][3]);
+    }
 }
 
 }  // namespace
@@ -341,8 +355,10 @@ void build_fill_tables(const std::vector<Elem>& el, const ImageTable& img, std::
         const double* qx = e.qx;
         const double* qz = e.qz;
         float4* out = nodes.data() + j * kFillNodeRec;
-        auto put = [&](float4* dst, double px, double pz, double w) { fill_node(cx - px, cz - pz, w, dst); };
-        int n_a = 0;
+        FillNode nd[36];
+        int cnt = 0;
+        auto put = [&](double px, double pz, double w) { nd[cnt++] = FillNode{cx - px, cz - pz, w}; };
+        int n_a = 0;  // tier-a node pairs
         if (nv == 4) {
             // tensor Gauss-Legendre on the bilinear map x(s, t) = q0 + s e1 + t e3 + s t tw,
             // weight ws wt |x_s x x_t|
@@ -352,47 +368,47 @@ void build_fill_tables(const std::vector<Elem>& el, const ImageTable& img, std::
             auto tensor = [&](int mq, float4* dst) {
                 double x[16], w[16];
                 gauss_legendre01(mq, x, w);
-                int cnt = 0;
+                cnt = 0;
                 for (int a = 0; a < mq; ++a)
                     for (int b = 0; b < mq; ++b) {
                         const double px = qx[0] + x[a] * e1x + x[b] * e3x + x[a] * x[b] * twx;
                         const double pz = qz[0] + x[a] * e1z + x[b] * e3z + x[a] * x[b] * twz;
                         const double sx = e1x + x[b] * twx, sz = e1z + x[b] * twz;
                         const double tx = e3x + x[a] * twx, tz = e3z + x[a] * twz;
-                        const double jac = std::fabs(sx * tz - sz * tx);
-                        put(dst + 2 * cnt, px, pz, w[a] * w[b] * jac);
-                        ++cnt;
+                        put(px, pz, w[a] * w[b] * std::fabs(sx * tz - sz * tx));
                     }
-                return cnt;
+                pack_fill_pairs(nd, cnt, dst);
+                return (cnt + 1) / 2;
             };
             n_a = tensor(3, out);
             tensor(4, out + kFillOffB);
             tensor(6, out + kFillOffC);
         } else {
             const double area = 0.5 * e.twoA[0];
+            cnt = 0;
             for (int g2 = 0; g2 < 2; ++g2)
                 for (int rr = 0; rr < 3; ++rr) {
                     double bc[3] = {kTriA[g2], kTriA[g2], kTriA[g2]};
                     bc[rr] = 1.0 - 2.0 * kTriA[g2];
                     const double px = bc[0] * qx[0] + bc[1] * qx[1] + bc[2] * qx[2];
                     const double pz = bc[0] * qz[0] + bc[1] * qz[1] + bc[2] * qz[2];
-                    put(out + 2 * n_a, px, pz, kTriW[g2] * area);
-                    ++n_a;
+                    put(px, pz, kTriW[g2] * area);
                 }
+            pack_fill_pairs(nd, cnt, out);
+            n_a = (cnt + 1) / 2;
             // collapsed (Duffy) product rules: x = q0 + s e1 + t (1 - s) e2, weight 2 ws wt (1 - s) A
             auto collapsed = [&](int mq, float4* dst) {
                 double x[16], w[16];
                 gauss_legendre01(mq, x, w);
-                int cnt = 0;
+                cnt = 0;
                 for (int a = 0; a < mq; ++a)
                     for (int b = 0; b < mq; ++b) {
                         const double sa = x[a], tb = x[b] * (1.0 - x[a]);
                         const double px = qx[0] + sa * (qx[1] - qx[0]) + tb * (qx[2] - qx[0]);
                         const double pz = qz[0] + sa * (qz[1] - qz[0]) + tb * (qz[2] - qz[0]);
-                        put(dst + 2 * cnt, px, pz, 2.0 * w[a] * w[b] * (1.0 - x[a]) * area);
-                        ++cnt;
+                        put(px, pz, 2.0 * w[a] * w[b] * (1.0 - x[a]) * area);
                     }
-                return cnt;
+                pack_fill_pairs(nd, cnt, dst);
             };
             collapsed(4, out + kFillOffB);
             collapsed(6, out + kFillOffC);

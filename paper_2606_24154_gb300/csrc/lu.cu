@@ -477,58 +477,204 @@ __global__ void k_permute(const T* __restrict__ b, const int32_t* __restrict__ p
     if (i < n) y[i] = b[perm[i]];
 }
 
-template <typename T>
-__global__ void k_copy_vec(const T* __restrict__ a, int64_t n, T* __restrict__ b) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) b[i] = a[i];
+// One triangular sweep in one launch.  Block rows of kTB rows; the CTA with ticket t (taken
+// from an atomic counter, so tickets follow the order in which CTAs start) solves block k =
+// t (lower sweep, unit-diagonal L) or nblk-1-t (upper sweep, U):
+//   x_k = D_k^-1 (rhs_k - sum_c M_kc x_c),  c < k (lower) or c > k (upper),
+// taking the blocks c in sweep order as their solutions are published (flags[c] set with
+// release semantics after x_c is written); when more than one block may be ready, one poll
+// reads the flags of the next blockDim.x blocks and the ready prefix is consumed.  A CTA
+// only waits for blocks of lower tickets, whose CTAs have started, so the waits end.  Each
+// thread owns one row of the block and a quarter of its columns; the matrix values of the
+// next block are loaded before its flag is awaited, so only x_c is read after it.  The
+// four partial sums are added in a fixed order, so the result does not depend on timing.
+// Diagonal block: FP64 sweeps solve it by substitution in one warp (lanes in step with
+// __syncwarp; U's diagonal through reciprocals); FP32 sweeps (the inner solves of the
+// iterative refinement) invert it in shared memory while the CTA waits, so that the step
+// on the critical path is a 64 x 64 matrix-vector product.  Every wait is bounded: on
+// giving up the CTA records *err, writes NaN for its block and still publishes it.
+constexpr int kSvThreads = 256;
+constexpr long long kSvSpinLimit = 1ll << 22;
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// One block row of a triangular sweep.  Every CTA stages the diagonal block in shared
-// memory and solves it by substitution (one warp, lanes in step with __syncwarp; the
-// operation order of a plain column-oriented substitution), from the untouched right-hand
-// side block R[r0:r1); CTA 0 stores the block's solution to X[r0:r1); then each CTA
-// updates its share of the rows still to be solved: R[r] -= LU[r, r0:r1) x, rows [r1, n)
-// for the lower (unit-diagonal L) sweep, [0, r0) for the upper (U) one.
 template <typename T>
-__global__ void __launch_bounds__(kSweepThreads) k_sweep_block(const T* __restrict__ LU, int64_t n, int64_t r0,
-                                                               int64_t r1, int lower, T* __restrict__ R,
-                                                               T* __restrict__ X) {
+__global__ void __launch_bounds__(kSvThreads) k_trsv(const T* __restrict__ LU, int64_t n, int64_t nblk, int lower,
+                                                     const T* __restrict__ rhs, T* x, int* flags, int* ticket,
+                                                     int* err) {
+    constexpr bool kInv = sizeof(T) == 4;  // explicit inverse of the diagonal block (FP32)
     __shared__ T D[kTB][kTB + 1];
-    __shared__ T x[kTB];
+    __shared__ T Xi[kInv ? kTB : 1][kTB + 1];
+    __shared__ T part[kSvThreads / kTB][kTB];
+    __shared__ T xs[kTB];
+    __shared__ T dinv[kTB];
+    __shared__ int s_t, s_ready, s_ok;
+    if (threadIdx.x == 0) s_t = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int64_t t = s_t;
+    const int64_t k = lower ? t : nblk - 1 - t;
+    const int64_t r0 = k * kTB, r1 = min(n, r0 + (int64_t)kTB);
     const int w = (int)(r1 - r0);
-    for (int idx = threadIdx.x; idx < w * w; idx += kSweepThreads) {
+    constexpr int kGroups = kSvThreads / kTB, kCols = kTB / kGroups;
+    const int row = threadIdx.x % kTB, grp = threadIdx.x / kTB;
+    for (int idx = threadIdx.x; idx < w * w; idx += kSvThreads) {
         const int r = idx % w, c = idx / w;
         D[r][c] = LU[(r0 + r) + (r0 + c) * n];
     }
-    if (threadIdx.x < w) x[threadIdx.x] = R[r0 + threadIdx.x];
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
+    // independent of the other blocks: the block's right-hand side and, for U, the
+    // reciprocals of its diagonal
+    const T rhs_own = (threadIdx.x < w) ? rhs[r0 + threadIdx.x] : (T)0;
+    if (!lower && threadIdx.x < w) dinv[threadIdx.x] = (T)1 / LU[(r0 + threadIdx.x) + (r0 + threadIdx.x) * n];
+    if constexpr (kInv) {
+        // X = D^-1 by forward (L, unit diagonal) or backward (U) substitution of all
+        // columns at once, one block barrier per step
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < kTB * kTB; idx += kSvThreads) {
+            const int r = idx % kTB, c = idx / kTB;
+            Xi[r][c] = (r == c && r < w) ? (T)1 : (T)0;
+        }
+        __syncthreads();
         if (lower) {
-            for (int c = 0; c < w; ++c) {
-                const T xc = x[c];
-                for (int r = lane; r < w; r += 32)
-                    if (r > c) x[r] -= D[r][c] * xc;
-                __syncwarp();
+            for (int q = 0; q + 1 < w; ++q) {
+                const int rows = w - 1 - q;
+                for (int idx = threadIdx.x; idx < rows * (q + 1); idx += kSvThreads) {
+                    const int r = q + 1 + idx % rows, c = idx / rows;
+                    Xi[r][c] -= D[r][q] * Xi[q][c];
+                }
+                __syncthreads();
             }
         } else {
-            for (int c = w - 1; c >= 0; --c) {
-                if (lane == (c & 31)) x[c] = x[c] / D[c][c];
-                __syncwarp();
-                const T xc = x[c];
-                for (int r = lane; r < c; r += 32) x[r] -= D[r][c] * xc;
-                __syncwarp();
+            for (int q = w - 1; q >= 0; --q) {
+                // row q of X is final once scaled by 1 / U[q][q]; then eliminate above
+                const int cols = w - q;
+                for (int c = q + threadIdx.x; c < w; c += kSvThreads) Xi[q][c] *= dinv[q];
+                __syncthreads();
+                for (int idx = threadIdx.x; idx < q * cols; idx += kSvThreads) {
+                    const int r = idx % q, c = q + idx / q;
+                    Xi[r][c] -= D[r][q] * Xi[q][c];
+                }
+                __syncthreads();
+            }
+        }
+    }
+    T acc = (T)0;
+    const int64_t total = lower ? k : nblk - 1 - k;
+    // matrix values of block i (sweep order) for this thread: row `row`, kCols columns
+    T mv[kCols];
+    auto load_block = [&](int64_t i) {
+        const int64_t c0 = (lower ? i : nblk - 1 - i) * kTB + grp * kCols;
+        const T* col = LU + (r0 + row) + c0 * n;
+        const int wc = (int)min((int64_t)kCols, n - c0);
+#pragma unroll
+        for (int q = 0; q < kCols; ++q) mv[q] = (row < w && q < wc) ? col[(int64_t)q * n] : (T)0;
+    };
+    auto use_block = [&](int64_t i) {
+        const int64_t c0 = (lower ? i : nblk - 1 - i) * kTB + grp * kCols;
+        const int wc = (int)min((int64_t)kCols, n - c0);
+#pragma unroll
+        for (int q = 0; q < kCols; ++q)
+            if (q < wc) acc = fma(mv[q], __ldcg(x + c0 + q), acc);
+    };
+    if (total > 0) load_block(0);
+    int64_t done = 0;
+    long long spins = 0;  // used by thread 0
+    bool ok = true;
+    while (done < total) {
+        // one thread waits (bounded) for the next block in sweep order; if more blocks may
+        // be ready, all threads read the flags of the following ones and take the ready prefix
+        if (threadIdx.x == 0) {
+            const int* fp = flags + (lower ? done : nblk - 1 - done);
+            int f = ld_acquire(fp);
+            while (!f && ++spins <= kSvSpinLimit) {
+                __nanosleep(32);
+                f = ld_acquire(fp);
+            }
+            s_ok = f != 0;
+            s_ready = kSvThreads;
+        }
+        __syncthreads();
+        if (!s_ok) {
+            ok = false;
+            break;
+        }
+        int64_t ready = 1;
+        if (total - done > 1) {
+            const int64_t idx = done + threadIdx.x;
+            if (threadIdx.x > 0 && idx < total && ld_acquire(flags + (lower ? idx : nblk - 1 - idx)) == 0)
+                atomicMin(&s_ready, (int)threadIdx.x);
+            __syncthreads();
+            ready = min((int64_t)s_ready, total - done);
+        }
+        __syncthreads();  // s_ready and s_ok are rewritten by the next poll
+        use_block(done);
+        for (int64_t i = done + 1; i < done + ready; ++i) {
+            load_block(i);
+            use_block(i);
+        }
+        done += ready;
+        if (done < total) load_block(done);  // in flight while the next flag is awaited
+    }
+    if (!ok) atomicExch(err, 1);
+    part[grp][row] = acc;
+    __syncthreads();
+    if (threadIdx.x < w) {
+        T sum = part[0][threadIdx.x];
+#pragma unroll
+        for (int g = 1; g < kGroups; ++g) sum += part[g][threadIdx.x];
+        xs[threadIdx.x] = rhs_own - sum;
+    }
+    __syncthreads();
+    if constexpr (kInv) {
+        // x = X (rhs - sum): row `row`, columns of group grp, then the groups in order
+        T v = (T)0;
+        if (row < w) {
+#pragma unroll
+            for (int q = 0; q < kCols; ++q) {
+                const int c = grp * kCols + q;
+                if (c < w) v = fma(Xi[row][c], xs[c], v);
+            }
+        }
+        part[grp][row] = v;
+        __syncthreads();
+        if (threadIdx.x < w) {
+            T sum = part[0][threadIdx.x];
+#pragma unroll
+            for (int g = 1; g < kGroups; ++g) sum += part[g][threadIdx.x];
+            xs[threadIdx.x] = sum;
+        }
+    } else {
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            if (lower) {
+                for (int c = 0; c < w; ++c) {
+                    const T xc = xs[c];
+                    for (int r = lane; r < w; r += 32)
+                        if (r > c) xs[r] -= D[r][c] * xc;
+                    __syncwarp();
+                }
+            } else {
+                for (int c = w - 1; c >= 0; --c) {
+                    if (lane == (c & 31)) xs[c] = xs[c] * dinv[c];
+                    __syncwarp();
+                    const T xc = xs[c];
+                    for (int r = lane; r < c; r += 32) xs[r] -= D[r][c] * xc;
+                    __syncwarp();
+                }
             }
         }
     }
     __syncthreads();
-    if (blockIdx.x == 0 && threadIdx.x < w) X[r0 + threadIdx.x] = x[threadIdx.x];
-    const int64_t q0 = lower ? r1 : 0, q1 = lower ? n : r0;
-    const int64_t r = q0 + (int64_t)blockIdx.x * kSweepThreads + threadIdx.x;
-    if (r >= q1) return;
-    T acc = (T)0;
-    for (int c = 0; c < w; ++c) acc = fma(LU[r + (r0 + c) * n], x[c], acc);
-    R[r] -= acc;
+    if (threadIdx.x < w) x[r0 + threadIdx.x] = ok ? xs[threadIdx.x] : (T)NAN;
+    // the block barrier orders the CTA's stores before thread 0's release (cumulative)
+    __syncthreads();
+    if (threadIdx.x == 0) st_release(flags + k, 1);
 }
 
 template <typename T>
@@ -536,22 +682,17 @@ cudaError_t lu_solve(const T* LU, int64_t n, const int32_t* perm, T* b, T* work,
     if (n == 0) return cudaSuccess;
     const int64_t nblk = (n + kTB - 1) / kTB;
     T* y = work;
+    T* z = work + n;
+    // flags of both sweeps, their tickets and the error flag (16-byte aligned after z)
+    const uintptr_t fo = ((uintptr_t)(z + n) + 15) & ~(uintptr_t)15;
+    int* flags = reinterpret_cast<int*>(fo);
+    int* tickets = flags + 2 * nblk;
+    int* err = tickets + 2;
+    NB_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * (2 * nblk + 3), s));
     const unsigned g = (unsigned)((n + 255) / 256);
     k_permute<T><<<g, 256, 0, s>>>(b, perm, n, y);
-    // forward sweep: R = y (its rows below each block updated), block solutions into b
-    for (int64_t k = 0; k < nblk; ++k) {
-        const int64_t r0 = k * kTB, r1 = std::min<int64_t>(n, r0 + kTB);
-        const int64_t rows = n - r1;
-        const unsigned grid = (unsigned)std::max<int64_t>(1, (rows + kSweepThreads - 1) / kSweepThreads);
-        k_sweep_block<T><<<grid, kSweepThreads, 0, s>>>(LU, n, r0, r1, 1, y, b);
-    }
-    // backward sweep: R = b (its rows above each block updated), block solutions into y
-    for (int64_t k = nblk - 1; k >= 0; --k) {
-        const int64_t r0 = k * kTB, r1 = std::min<int64_t>(n, r0 + kTB);
-        const unsigned grid = (unsigned)std::max<int64_t>(1, (r0 + kSweepThreads - 1) / kSweepThreads);
-        k_sweep_block<T><<<grid, kSweepThreads, 0, s>>>(LU, n, r0, r1, 0, b, y);
-    }
-    k_copy_vec<T><<<g, 256, 0, s>>>(y, n, b);
+    k_trsv<T><<<(unsigned)nblk, kSvThreads, 0, s>>>(LU, n, nblk, 1, y, z, flags, tickets, err);
+    k_trsv<T><<<(unsigned)nblk, kSvThreads, 0, s>>>(LU, n, nblk, 0, z, b, flags + nblk, tickets + 1, err);
     return cudaGetLastError();
 }
 
@@ -643,7 +784,9 @@ cudaError_t lu_factor_f32(float* A, int64_t n, int32_t* piv, int nb, float* work
     void* split = reinterpret_cast<char*>(work) + split_offset(n, nb);
     return lu_factor<float>(A, n, piv, nb, work, d_info, split, s);
 }
-size_t lu_solve_work_bytes(int64_t n, size_t tsize) { return tsize * (size_t)n + 256; }
+size_t lu_solve_work_bytes(int64_t n, size_t tsize) {
+    return 2 * tsize * (size_t)n + 16 + sizeof(int) * (size_t)(2 * ((n + kTB - 1) / kTB) + 3) + 256;
+}
 
 size_t residual_work_bytes(int64_t n) {
     return sizeof(double) * (size_t)((n + kResChunk - 1) / kResChunk) * (size_t)n + 256;

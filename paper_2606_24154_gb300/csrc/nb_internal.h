@@ -71,19 +71,22 @@ struct __align__(16) FarNodes {
 // The rule truncation errors at these distances (worst over thin rectangles, obtuse and
 // sliver triangles and skewed quadrilaterals) stay below ~3e-12 of the pair's value.
 // Nodes are kept in the element's local (x, z) frame as offsets s = centroid - node; every
-// value is stored as an unevaluated sum of two floats (hi + lo):
-//   node  u = (2 s_x hi, 2 s_z hi, |s|^2 hi, w hi),  v = the lo parts, w = weight x area.
+// value is stored as an unevaluated sum of two floats (hi + lo), two nodes per record for
+// the packed FP32x2 arithmetic (an odd count is padded with a copy of the last node of
+// weight 0):
+//   q0 = (2 s_x hi, 2 s_z hi) of nodes (a, b) as (a, b, a, b),  q1 = (|s|^2 hi, w hi),
+//   q2 = (2 s_x lo, 2 s_z lo),  q3 = (|s|^2 lo, w lo),   w = weight x area.
 constexpr double kFillRatioA = 96.0;
 constexpr double kFillRatioB = 32.0;
 constexpr double kFillRatioC = 6.0;
-constexpr int kFillNodesA = 9;  // capacity (6 used by triangles)
-constexpr int kFillNodesB = 16;
-constexpr int kFillNodesC = 36;
-constexpr int kFillNodeRec = 2 * (kFillNodesA + kFillNodesB + kFillNodesC);  // float4 per element
-constexpr int kFillOffB = 2 * kFillNodesA;
-constexpr int kFillOffC = 2 * (kFillNodesA + kFillNodesB);
+constexpr int kFillPairsA = 5;  // capacity (3 used by triangles)
+constexpr int kFillPairsB = 8;
+constexpr int kFillPairsC = 18;
+constexpr int kFillNodeRec = 4 * (kFillPairsA + kFillPairsB + kFillPairsC);  // float4 per element
+constexpr int kFillOffB = 4 * kFillPairsA;
+constexpr int kFillOffC = 4 * (kFillPairsA + kFillPairsB);
 // Per element: centroid c and frame (ex, ey, ez) as hi + lo floats; hdr = squared tier
-// distances (a, b, c) in m^2 and the tier-a node count.
+// distances (a, b, c) in m^2 and the tier-a node-pair count.
 struct __align__(16) FillEl {
     float4 ch, cl;
     float4 exh, exl, eyh, eyl, ezh, ezl;
