@@ -82,16 +82,18 @@ def mufu_peak(sm_mhz):
 
 
 # ---------------------------------------------------------------- mixed fill
-# Two-float (hi + lo FP32) operations of the mixed fill kernel, counted from its code:
-# per (row, column): c_i - c_j (3 two-float differences, 8 each) and its local components
-# (3 two-float dot products, 28 each); interface rows add the normal's local components
-# (3 more dot products).  Per far image pair: the FP32 tier test (12 + 3 compares), X, Y, Z
-# (3 differences) and |D|^2 (28); interface rows add n . D (28).  Per Gauss node: r^2 and
-# the refined 1/r (39, plus one MUFU rsqrt), then w / r accumulated (12) on conductor rows,
-# or w (n . (D + s)) / r^3 accumulated (48) on interface rows.
+# Two-float (hi + lo FP32) operations of the mixed fill kernel, counted from its code (FP32
+# lane operations; the node loops run two nodes per packed FP32x2 instruction, one lane
+# each): per (row, column): c_i - c_j (3 two-float differences, 8 each) and its local
+# components (3 two-float dot products, 28 each); interface rows add the normal's local
+# components (3 more dot products).  Per far image pair: the FP32 tier test (12 + 3
+# compares), X, Y, Z (3 differences), |D|^2 (28) and two negations; interface rows add
+# n . D (28).  Per Gauss node: r^2 and the refined 1/r (41, plus one MUFU rsqrt), then w / r
+# accumulated (12) on conductor rows, or w (n . (D + s)) / r^3 accumulated (49) on
+# interface rows.
 FILL_OPS_COLUMN = (108, 192)   # conductor, interface row
-FILL_OPS_IMAGE = (67, 95)
-FILL_OPS_NODE = (51, 87)
+FILL_OPS_IMAGE = (69, 97)
+FILL_OPS_NODE = (53, 90)
 FILL_RATIOS = (96.0, 32.0, 6.0)
 
 
