@@ -12,6 +12,7 @@
 // Templated on the element type: double (FP64 solves) and float (mixed solves, the
 // FP64 iterative refinement lives in the caller).
 #include <algorithm>
+#include <climits>
 #include <vector>
 
 #include "nb_internal.h"
@@ -252,6 +253,201 @@ __global__ void __launch_bounds__(kPivThreads, 2) k_panel_col(T* __restrict__ A,
     }
 }
 
+// The whole panel of the FP32 factorisation in one cooperative launch (all CTAs resident).
+// CTA b holds rows [k0 + b R, k0 + (b+1) R) of the panel columns in shared memory
+// (column-major, R rows); per column j of the panel:
+//   (a) scale column j-1 by the previous pivot and apply its rank-1 update to the rows
+//       below it (the same per-element arithmetic as k_panel_col);
+//   (b) each CTA finds its largest |a_ij| (lowest row on ties) and publishes it with its
+//       row (candidate slot of parity j & 1); the CTA holding row j publishes row j;
+//   (c) one grid barrier; every CTA reduces the candidates to the pivot p, reads the
+//       pivot row, and the holders of rows j and p swap them in shared memory.
+// The candidate slots alternate between two parities: a CTA writes slot j+1 only after it
+// has passed barrier j, by which time every CTA has finished reading slot j-1.  The grid
+// barrier (arrival counter, generation number) waits a bounded number of polls; on giving
+// up a CTA records *err and leaves the panel (the host reports a timeout).
+constexpr int kCoopThreads = 256;
+constexpr int kCoopMaxG = 1024;
+constexpr long long kCoopSpinLimit = 1ll << 22;
+
+struct CoopScratch {
+    double cval[2][kCoopMaxG];
+    long long cidx[2][kCoopMaxG];
+    float cand[2][kCoopMaxG][64];
+    float srow[2][64];
+    unsigned int bar[4];  // arrival count, generation
+    int err;
+};
+
+__device__ __forceinline__ unsigned int ld_acquire_u(const unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_acquire_i(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// every CTA of the grid arrives; false if the wait gave up
+__device__ bool coop_barrier(CoopScratch* cs, unsigned int nblocks, bool* s_flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int gen = ld_acquire_u(&cs->bar[1]);
+        __threadfence();
+        bool ok = true;
+        if (atomicAdd(&cs->bar[0], 1u) == nblocks - 1) {
+            atomicExch(&cs->bar[0], 0u);
+            __threadfence();
+            atomicAdd(&cs->bar[1], 1u);
+        } else {
+            long long spins = 0;
+            while (ld_acquire_u(&cs->bar[1]) == gen) {
+                // give up after the poll limit, or at once when another CTA has given up
+                if (++spins > kCoopSpinLimit || ((spins & 1023) == 0 && ld_acquire_i(&cs->err))) {
+                    ok = false;
+                    break;
+                }
+                __nanosleep(20);
+            }
+        }
+        __threadfence();
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag;
+}
+
+__global__ void __launch_bounds__(kCoopThreads, 1)
+    k_panel_coop(float* __restrict__ A, int64_t n, int64_t k0, int64_t k1, int R, int32_t* __restrict__ piv,
+                 int* __restrict__ info, int* __restrict__ tmo, CoopScratch* cs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (ld_acquire_i(&cs->err)) return;  // an earlier panel gave up: leave the matrix as it is
+    const int w = (int)(k1 - k0);
+    float* S = reinterpret_cast<float*>(smem_raw);  // R x w, column-major
+    __shared__ float prow[64];
+    __shared__ double sv[kCoopThreads];
+    __shared__ long long si[kCoopThreads];
+    __shared__ bool s_flag;
+    const int G = gridDim.x, b = blockIdx.x;
+    const int64_t rb0 = k0 + (int64_t)b * R;
+    const int nr = (int)max((int64_t)0, min((int64_t)R, n - rb0));
+    for (int idx = threadIdx.x; idx < nr * w; idx += kCoopThreads) {
+        const int r = idx % nr, c = idx / nr;
+        S[c * R + r] = A[(rb0 + r) + (k0 + c) * n];
+    }
+    __syncthreads();
+    bool ok_piv = true;  // the previous pivot was nonzero
+    for (int jj = 0; jj < w; ++jj) {
+        const int64_t j = k0 + jj;
+        const int par = jj & 1;
+        // (a) column jj-1: scale and rank-1 update of this CTA's rows below it
+        if (jj > 0 && ok_piv) {
+            const float inv = 1.0f / prow[jj - 1];
+            for (int r = threadIdx.x; r < nr; r += kCoopThreads) {
+                if (rb0 + r < j) continue;
+                const float l = S[(jj - 1) * R + r] * inv;
+                S[(jj - 1) * R + r] = l;
+                for (int c = jj; c < w; ++c) S[c * R + r] -= l * prow[c];
+            }
+        }
+        __syncthreads();
+        // (b) this CTA's candidate for column jj
+        double best = -1.0;
+        long long bidx = LLONG_MAX;
+        for (int r = threadIdx.x; r < nr; r += kCoopThreads) {
+            if (rb0 + r < j) continue;
+            const double v = fabs((double)S[jj * R + r]);
+            if (v > best || (v == best && rb0 + r < bidx)) {
+                best = v;
+                bidx = rb0 + r;
+            }
+        }
+        sv[threadIdx.x] = best;
+        si[threadIdx.x] = bidx;
+        __syncthreads();
+        for (int st = kCoopThreads / 2; st > 0; st >>= 1) {
+            if (threadIdx.x < st) {
+                const double v = sv[threadIdx.x + st];
+                const long long ix = si[threadIdx.x + st];
+                if (v > sv[threadIdx.x] || (v == sv[threadIdx.x] && ix < si[threadIdx.x])) {
+                    sv[threadIdx.x] = v;
+                    si[threadIdx.x] = ix;
+                }
+            }
+            __syncthreads();
+        }
+        const long long mine = si[0];
+        if (threadIdx.x == 0) {
+            cs->cval[par][b] = sv[0];
+            cs->cidx[par][b] = mine;
+        }
+        if (threadIdx.x < w) {
+            cs->cand[par][b][threadIdx.x] = (mine != LLONG_MAX) ? S[threadIdx.x * R + (int)(mine - rb0)] : 0.f;
+            if (j >= rb0 && j < rb0 + nr) cs->srow[par][threadIdx.x] = S[threadIdx.x * R + (int)(j - rb0)];
+        }
+        if (!coop_barrier(cs, (unsigned)G, &s_flag)) {
+            if (threadIdx.x == 0) {
+                atomicExch(&cs->err, 1);
+                atomicExch(tmo, 1);
+            }
+            return;
+        }
+        // (c) the pivot: largest |a| over the candidates, lowest row on ties
+        best = -1.0;
+        bidx = LLONG_MAX;
+        for (int q = threadIdx.x; q < G; q += kCoopThreads) {
+            const double v = __ldcg(&cs->cval[par][q]);
+            const long long ix = __ldcg(&cs->cidx[par][q]);
+            if (v > best || (v == best && ix < bidx)) {
+                best = v;
+                bidx = ix;
+            }
+        }
+        sv[threadIdx.x] = best;
+        si[threadIdx.x] = bidx;
+        __syncthreads();
+        for (int st = kCoopThreads / 2; st > 0; st >>= 1) {
+            if (threadIdx.x < st) {
+                const double v = sv[threadIdx.x + st];
+                const long long ix = si[threadIdx.x + st];
+                if (v > sv[threadIdx.x] || (v == sv[threadIdx.x] && ix < si[threadIdx.x])) {
+                    sv[threadIdx.x] = v;
+                    si[threadIdx.x] = ix;
+                }
+            }
+            __syncthreads();
+        }
+        const int64_t p = (si[0] >= j && si[0] < n) ? si[0] : j;
+        const int owner = (int)((p - k0) / R);
+        if (threadIdx.x < w) prow[threadIdx.x] = __ldcg(&cs->cand[par][owner][threadIdx.x]);
+        if (b == 0 && threadIdx.x == 0) {
+            piv[j] = (int32_t)p;
+            if (!(sv[0] > 0.0) && *info == 0) *info = (int)(j + 1);
+        }
+        __syncthreads();
+        ok_piv = prow[jj] != 0.f;  // the scaling below is skipped for a zero pivot, as in k_panel_col
+        if (threadIdx.x < w) {
+            if (j >= rb0 && j < rb0 + nr) S[threadIdx.x * R + (int)(j - rb0)] = prow[threadIdx.x];
+            if (p != j && p >= rb0 && p < rb0 + nr)
+                S[threadIdx.x * R + (int)(p - rb0)] = __ldcg(&cs->srow[par][threadIdx.x]);
+        }
+        __syncthreads();
+    }
+    // scale the last panel column below the panel
+    if (ok_piv) {
+        const float inv = 1.0f / prow[w - 1];
+        for (int r = threadIdx.x; r < nr; r += kCoopThreads)
+            if (rb0 + r >= k1) S[(w - 1) * R + r] *= inv;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nr * w; idx += kCoopThreads) {
+        const int r = idx % nr, c = idx / nr;
+        A[(rb0 + r) + (k0 + c) * n] = S[c * R + r];
+    }
+}
+
 // Apply the row swaps of panel rows [k0, k1) to columns outside the panel.
 template <typename T>
 __global__ void k_laswp(T* __restrict__ A, int64_t n, int64_t k0, int64_t k1, const int32_t* __restrict__ piv) {
@@ -380,7 +576,8 @@ cudaError_t gemm(int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t l
 // work layout: [0, nb*nb) L11 inverse; [nb*nb, nb*nb + nb*n) U12 staging;
 // then kPivBlocks doubles + kPivBlocks int64 for the pivot search and one int ticket.
 template <typename T>
-cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_info, void* split, cudaStream_t s) {
+cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_info, void* split, void* coop,
+                      cudaStream_t s) {
     // d_info[0]: first zero pivot (1-based) or 0; d_info[1]: tensor-core update gave up
     NB_TRY(cudaMemsetAsync(d_info, 0, 2 * sizeof(int), s));
     T* Linv = work;
@@ -392,17 +589,55 @@ cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_inf
     int* ticket = reinterpret_cast<int*>(pidx + kPivBlocks);
     NB_TRY(cudaMemsetAsync(ticket, 0, sizeof(int), s));
     if (nb > 64) return cudaErrorInvalidValue;  // k_panel_col stages at most 64 row values
+    // FP32: the whole panel in one cooperative launch when every CTA's rows fit in shared
+    // memory (R rows x 64 columns, R = max(64, rows / SMs)) and all CTAs can be resident
+    int gmax = 0;
+    CoopScratch* cs = static_cast<CoopScratch*>(coop);
+    if constexpr (sizeof(T) == 4) {
+        int dev = 0, sms = 0, can = 0;
+        if (cs && cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&can, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && can) {
+            const int g = std::min(kCoopMaxG, sms);
+            const int64_t R0 = std::max<int64_t>(64, (n + g - 1) / g);
+            const int smem0 = (int)(R0 * 64 * sizeof(float));
+            int per_sm = 0;
+            if (smem0 <= 200 * 1024 &&
+                cudaFuncSetAttribute(k_panel_coop, cudaFuncAttributeMaxDynamicSharedMemorySize, smem0) ==
+                    cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_panel_coop, kCoopThreads, smem0) ==
+                    cudaSuccess &&
+                per_sm >= 1) {
+                gmax = g;
+                NB_TRY(cudaMemsetAsync(cs, 0, sizeof(CoopScratch), s));
+            }
+        }
+        cudaGetLastError();  // a refused attribute or query leaves the per-column path
+    }
     for (int64_t k0 = 0; k0 < n; k0 += nb) {
         const int64_t k1 = std::min<int64_t>(n, k0 + nb);
         const int w = (int)(k1 - k0);
-        // columns k0..k1-1: update by the previous column + pivot of this one; then the
-        // last column's scaling of the rows below the panel
-        for (int64_t j = k0; j <= k1; ++j) {
-            if (j == n) break;
-            const int64_t rows = n - j;
-            const int pb = (int)std::min<int64_t>(kPivBlocks, (rows + kPivThreads - 1) / kPivThreads);
-            k_panel_col<T><<<pb, kPivThreads, 0, s>>>(A, n, j, k0, k1, j < k1 ? 1 : 0, pval, pidx, ticket, piv,
-                                                      d_info);
+        if (gmax > 0) {
+            const int64_t rows = n - k0;
+            const int R = (int)std::max<int64_t>(64, (rows + gmax - 1) / gmax);
+            const int G = (int)((rows + R - 1) / R);
+            float* Af = reinterpret_cast<float*>(A);
+            int64_t nn = n, kk0 = k0, kk1 = k1;
+            int RR = R;
+            int* tmo = d_info + 1;
+            void* args[] = {&Af, &nn, &kk0, &kk1, &RR, &piv, &d_info, &tmo, &cs};
+            NB_TRY(cudaLaunchCooperativeKernel((const void*)k_panel_coop, dim3((unsigned)G), dim3(kCoopThreads), args,
+                                               (size_t)R * w * sizeof(float), s));
+        } else {
+            // columns k0..k1-1: update by the previous column + pivot of this one; then the
+            // last column's scaling of the rows below the panel
+            for (int64_t j = k0; j <= k1; ++j) {
+                if (j == n) break;
+                const int64_t rows = n - j;
+                const int pb = (int)std::min<int64_t>(kPivBlocks, (rows + kPivThreads - 1) / kPivThreads);
+                k_panel_col<T><<<pb, kPivThreads, 0, s>>>(A, n, j, k0, k1, j < k1 ? 1 : 0, pval, pidx, ticket, piv,
+                                                          d_info);
+            }
         }
         NB_TRY(cudaGetLastError());
         k_laswp<T><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(A, n, k0, k1, piv);
@@ -775,14 +1010,19 @@ size_t lu_work_elems(int64_t n, int nb) {
 }
 
 cudaError_t lu_factor_f64(double* A, int64_t n, int32_t* piv, int nb, double* work, int* d_info, cudaStream_t s) {
-    return lu_factor<double>(A, n, piv, nb, work, d_info, nullptr, s);
+    return lu_factor<double>(A, n, piv, nb, work, d_info, nullptr, nullptr, s);
 }
 static size_t split_offset(int64_t n, int nb) { return (sizeof(float) * lu_work_elems(n, nb) + 255) & ~(size_t)255; }
-size_t lu_work_bytes_f32(int64_t n, int nb) { return split_offset(n, nb) + tc_split_bytes(n, n); }
+static size_t coop_offset(int64_t n, int nb) {
+    return (split_offset(n, nb) + tc_split_bytes(n, n) + 255) & ~(size_t)255;
+}
+size_t lu_work_bytes_f32(int64_t n, int nb) { return coop_offset(n, nb) + sizeof(CoopScratch); }
 cudaError_t lu_factor_f32(float* A, int64_t n, int32_t* piv, int nb, float* work, int* d_info, cudaStream_t s) {
-    // work: lu_work_bytes_f32(n, nb) bytes, 256-byte aligned
+    // work: lu_work_bytes_f32(n, nb) bytes, 256-byte aligned: panel staging, then the
+    // tensor-core split operands, then the cooperative panel's candidates and barrier
     void* split = reinterpret_cast<char*>(work) + split_offset(n, nb);
-    return lu_factor<float>(A, n, piv, nb, work, d_info, split, s);
+    void* coop = reinterpret_cast<char*>(work) + coop_offset(n, nb);
+    return lu_factor<float>(A, n, piv, nb, work, d_info, split, coop, s);
 }
 size_t lu_solve_work_bytes(int64_t n, size_t tsize) {
     return 2 * tsize * (size_t)n + 16 + sizeof(int) * (size_t)(2 * ((n + kTB - 1) / kTB) + 3) + 256;
