@@ -256,15 +256,16 @@ __global__ void __launch_bounds__(128, 2) k_tc_update(int64_t M, int64_t N, cons
 
 // ---------------------------------------------------------------- bulk-asynchronous path
 // Operands are split once per panel (k_split_ab) into TF32 hi/lo tiles already in the UMMA
-// K-major layout, so a CTA moves them with single bulk copies; the C tiles move by TMA
-// (a 2-D tensor map over C: 128 rows x 64 columns per box, out-of-range elements zero on
-// load and clipped on store).  One CTA per SM walks tiles_per_cta column tiles of its
-// 128-row strip with every transfer asynchronous:
-//   smem  A hi/lo (64 KB) | B hi/lo x 2 buffers (64 KB) | C x 2 buffers (64 KB) | barriers
+// K-major layout, A negated, so a CTA moves them with single bulk copies and the MMAs
+// accumulate -A B.  C is never loaded by the SMs: each finished 128 x 64 product tile goes
+// from tensor memory to shared memory and is added to C by a TMA reduce-add (a 2-D tensor
+// map over C; the read-modify-write happens in L2, out-of-range elements are skipped).
+// c + (-v) rounds exactly like c - v, so the factors equal those of the register-staged
+// kernel.  One CTA per SM walks tiles_per_cta column tiles of its 128-row strip:
+//   smem  A hi/lo (64 KB) | B hi/lo x 2 buffers (64 KB) | product x 2 buffers (64 KB) | barriers
 //   tile t: wait B(t) -> 24 MMAs into accumulator t & 1; wait MMAs(t-1) -> prefetch B(t+1);
-//           wait C(t-1) -> C(t-1) -= accumulator in shared memory -> TMA store C(t-1) ->
-//           (store has read the buffer) -> TMA load C(t+1) into it.
-// Each C tile load is issued two tiles ahead of its use and each B tile one tile ahead.
+//           product(t-1) -> shared buffer (t-1) & 1 (once the reduce of tile t-3 has read
+//           it) -> TMA reduce-add into C.
 constexpr uint32_t kASplit = 2 * kABytes;            // 64 KB per 128-row operand tile
 constexpr uint32_t kBSplit = 2 * kBBytes;            // 32 KB per 64-column operand tile
 constexpr uint32_t kCTile = kTM * kTN * 4;           // 32 KB
@@ -295,24 +296,17 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         "l"(src), "r"(bytes), "r"(smem_u32(b))
         : "memory");
 }
-__device__ __forceinline__ void tma_load_c(void* dst, const CUtensorMap* map, int x, int y, uint64_t* b) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
-        "[%4];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(b))
-        : "memory");
-}
-__device__ __forceinline__ void tma_store_c(const CUtensorMap* map, int x, int y, const void* src) {
-    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+__device__ __forceinline__ void tma_reduce_add_c(const CUtensorMap* map, int x, int y, const void* src) {
+    asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
                      reinterpret_cast<uint64_t>(map)),
                  "r"(x), "r"(y), "r"(smem_u32(src))
                  : "memory");
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 
-// A (M x 64, column-major) and B (64 x N) into TF32 hi/lo operand tiles: A tile tm at
+// -A (M x 64, column-major) and B (64 x N) into TF32 hi/lo operand tiles: A tile tm at
 // asplit + tm * 64 KB (hi, then lo), B tile tn at bsplit + tn * 32 KB; rows of A beyond M
-// and columns of B beyond N are zero.
+// and columns of B beyond N are zero.  The TF32 split of -x is the negated split of x.
 __global__ void k_split_ab(const float* __restrict__ A, int64_t lda, const float* __restrict__ B, int64_t ldb,
                            int64_t M, int64_t N, int64_t tiles_m, int64_t tiles_n, unsigned char* __restrict__ asplit,
                            unsigned char* __restrict__ bsplit) {
@@ -324,7 +318,7 @@ __global__ void k_split_ab(const float* __restrict__ A, int64_t lda, const float
             const int e = (int)(idx - tm * (kTM * kTK));
             const int r = e % kTM, k = e / kTM;
             const int64_t gm = tm * kTM + r;
-            const float x = gm < M ? A[gm + (int64_t)k * lda] : 0.f;
+            const float x = gm < M ? -A[gm + (int64_t)k * lda] : 0.f;
             unsigned char* t = asplit + tm * kASplit;
             put_pair(t, t + kABytes, kmajor_off(r, k), x);
         } else {
@@ -347,13 +341,12 @@ __global__ void __launch_bounds__(128, 1)
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA = smem;
     unsigned char* sB0 = smem + kASplit;
-    unsigned char* sC0 = smem + kASplit + 2 * kBSplit;
+    unsigned char* sP0 = smem + kASplit + 2 * kBSplit;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kASplit + 2 * kBSplit + 2 * kCTile);
     uint64_t* barA = bar;
     uint64_t* barB = bar + 1;  // [2]
-    uint64_t* barC = bar + 3;  // [2]
-    uint64_t* barM = bar + 5;  // [2]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 8);
+    uint64_t* barM = bar + 3;  // [2]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 6);
 
     const int64_t tiles_n = (N + kTN - 1) / kTN;
     const int64_t t0 = (int64_t)blockIdx.y * tpc;
@@ -361,31 +354,20 @@ __global__ void __launch_bounds__(128, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = (int)(blockIdx.x * kTM);
     auto sB = [&](int s) { return sB0 + s * kBSplit; };
-    auto sC = [&](int s) { return reinterpret_cast<float*>(sC0 + s * kCTile); };
+    auto sP = [&](int s) { return reinterpret_cast<float*>(sP0 + s * kCTile); };
     auto load_b = [&](int t) {
         const int s = t & 1;
         mbar_expect(barB + s, kBSplit);
         bulk_load(sB(s), bsplit + (t0 + t) * (int64_t)kBSplit, kBSplit, barB + s);
     };
-    auto load_c = [&](int t) {
-        const int s = t & 1;
-        mbar_expect(barC + s, kCTile);
-        tma_load_c(sC(s), &cmap, m0, (int)((t0 + t) * kTN), barC + s);
-    };
 
     if (tid == 0) {
-        for (int b = 0; b < 7; ++b) mbar_init(bar + b);
+        for (int b = 0; b < 5; ++b) mbar_init(bar + b);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         mbar_expect(barA, kASplit);
         bulk_load(sA, asplit + (int64_t)blockIdx.x * kASplit, kASplit, barA);
-        if (nt > 0) {
-            load_b(0);
-            load_c(0);
-        }
-        if (nt > 1) {
-            load_b(1);
-            load_c(1);
-        }
+        if (nt > 0) load_b(0);
+        if (nt > 1) load_b(1);
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -397,27 +379,30 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
 
-    // completions consumed per barrier (the next wait's parity) and loads / commits issued
-    int used_b[2] = {0, 0}, used_c[2] = {0, 0}, used_m[2] = {0, 0};
-    int iss_b[2] = {nt > 0, nt > 1}, iss_c[2] = {nt > 0, nt > 1}, iss_m[2] = {0, 0}, a_used = 0;
+    // completions consumed per barrier (the next wait's parity), loads / commits issued
+    int used_b0 = 0, used_b1 = 0, used_m0 = 0, used_m1 = 0;
+    int iss_b0 = nt > 0, iss_b1 = nt > 1, iss_m0 = 0, iss_m1 = 0, a_used = 0;
     int ok = 1;
 
-    // C(t) -= accumulator (t & 1), in shared memory, then stored by TMA
+    // product tile t (accumulator t & 1 = -(A B) for the tile) -> shared buffer t & 1 -> reduce-add into C
     auto finish_tile = [&](int t) -> int {
         const int s = t & 1;
-        int w = mbar_wait(barM + s, (uint32_t)(used_m[s] & 1));
+        int& used_m = s ? used_m1 : used_m0;
+        int w = mbar_wait(barM + s, (uint32_t)(used_m & 1));
         if (!__syncthreads_and(w)) return 0;
-        ++used_m[s];
+        ++used_m;
         asm volatile("tcgen05.fence::after_thread_sync;");
-        // the MMAs of tile t have read B buffer s: prefetch B(t + 2)
-        if (tid == 0 && t + 2 < nt) {
-            load_b(t + 2);
-            iss_b[s]++;
+        // the MMAs of tile t have read B buffer s: prefetch B(t + 2); the reduce of tile
+        // t - 2 must have read product buffer s before it is rewritten
+        if (tid == 0) {
+            if (t + 2 < nt) {
+                load_b(t + 2);
+                (s ? iss_b1 : iss_b0)++;
+            }
+            asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
         }
-        w = mbar_wait(barC + s, (uint32_t)(used_c[s] & 1));
-        if (!__syncthreads_and(w)) return 0;
-        ++used_c[s];
-        float* c = sC(s);
+        __syncthreads();
+        float* pbuf = sP(s);
         const int r = warp * 32 + lane;
 #pragma unroll
         for (int cb = 0; cb < kTN; cb += 32) {
@@ -434,32 +419,25 @@ __global__ void __launch_bounds__(128, 1)
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int j = 0; j < 32; ++j) c[(cb + j) * kTM + r] -= __uint_as_float(v[j]);
+            for (int j = 0; j < 32; ++j) pbuf[(cb + j) * kTM + r] = __uint_as_float(v[j]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
-        if (tid == 0) {
-            tma_store_c(&cmap, m0, (int)((t0 + t) * kTN), c);
-            if (t + 2 < nt) {
-                // the store must have read the buffer before the next tile lands in it
-                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-                load_c(t + 2);
-                iss_c[s]++;
-            }
-        }
+        if (tid == 0) tma_reduce_add_c(&cmap, m0, (int)((t0 + t) * kTN), pbuf);
         return 1;
     };
 
     for (int t = 0; t < nt && ok; ++t) {
         const int s = t & 1;
-        int w = mbar_wait(barB + s, (uint32_t)(used_b[s] & 1));
+        int& used_b = s ? used_b1 : used_b0;
+        int w = mbar_wait(barB + s, (uint32_t)(used_b & 1));
         if (t == 0) w = w && mbar_wait(barA, 0);
         if (!__syncthreads_and(w)) {
             ok = 0;
             break;
         }
-        ++used_b[s];
+        ++used_b;
         a_used = 1;
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (tid == 0) {
@@ -481,7 +459,7 @@ __global__ void __launch_bounds__(128, 1)
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_u32(barM + s)));
         }
-        iss_m[s]++;
+        (s ? iss_m1 : iss_m0)++;
         if (t > 0 && !finish_tile(t - 1)) ok = 0;
     }
     if (ok && nt > 0 && !finish_tile(nt - 1)) ok = 0;
@@ -492,11 +470,10 @@ __global__ void __launch_bounds__(128, 1)
         // and tensor memory go away
         if (tid == 0) {
             if (!a_used) mbar_wait(barA, 0);
-            for (int s = 0; s < 2; ++s) {
-                if (iss_b[s] > used_b[s]) mbar_wait(barB + s, (uint32_t)(used_b[s] & 1));
-                if (iss_c[s] > used_c[s]) mbar_wait(barC + s, (uint32_t)(used_c[s] & 1));
-                if (iss_m[s] > used_m[s]) mbar_wait(barM + s, (uint32_t)(used_m[s] & 1));
-            }
+            if (iss_b0 > used_b0) mbar_wait(barB, (uint32_t)(used_b0 & 1));
+            if (iss_b1 > used_b1) mbar_wait(barB + 1, (uint32_t)(used_b1 & 1));
+            if (iss_m0 > used_m0) mbar_wait(barM, (uint32_t)(used_m0 & 1));
+            if (iss_m1 > used_m1) mbar_wait(barM + 1, (uint32_t)(used_m1 & 1));
         }
     }
     if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
