@@ -246,6 +246,123 @@ __global__ void __launch_bounds__(kSC2Threads) k_sc_mixed(const float4* __restri
                      (double)aey.hi.y + (double)aey.lo.y, (double)aez.hi.y + (double)aez.lo.y, phi, E);
 }
 
+// Four targets per thread for large target sets: two pairs of FP32x2 lanes, (t, t + 128)
+// and (t + 256, t + 384) of a 512-target block, share every source load from shared memory,
+// and the two independent chains give the scheduler more to overlap.  Per target the
+// operations, their order, the 32-source flush groups (tiles of 512 sources hold sixteen of
+// them, aligned as in the 256-source tiles) and the running totals are those of
+// k_sc_mixed, so the two kernels give the same bits.
+constexpr int kSC4Threads = 128;
+constexpr int kSC4Tile = 4 * kSC4Threads;
+
+template <bool SELF>
+__device__ __forceinline__ void sc_tile_f32x2x2(const float4* __restrict__ A, const float4* __restrict__ B,
+                                                const float4* __restrict__ C, const float2* __restrict__ D, int k0,
+                                                int k1, const float2 (&th)[2][3], const float2 (&tl)[2][3], float2 s2,
+                                                const int (&self)[4], float2 (&ph)[2], float2 (&ex)[2],
+                                                float2 (&ey)[2], float2 (&ez)[2]) {
+#pragma unroll 2
+    for (int k = k0; k < k1; ++k) {
+        const float4 a = A[k], b = B[k], c = C[k];
+        const float2 d = D[k];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float2 dx =
+                __fadd2_rn(__fadd2_rn(th[h][0], make_float2(a.x, a.y)), __fadd2_rn(tl[h][0], make_float2(c.x, c.y)));
+            const float2 dy =
+                __fadd2_rn(__fadd2_rn(th[h][1], make_float2(a.z, a.w)), __fadd2_rn(tl[h][1], make_float2(c.z, c.w)));
+            const float2 dz = __fadd2_rn(__fadd2_rn(th[h][2], make_float2(b.x, b.y)), __fadd2_rn(tl[h][2], d));
+            const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, s2)));
+            const float2 ri = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+            float2 qq = make_float2(b.z, b.w);
+            if (SELF) {
+                if (k == self[2 * h]) qq.x = 0.f;
+                if (k == self[2 * h + 1]) qq.y = 0.f;
+            }
+            const float2 qr = __fmul2_rn(qq, ri);
+            const float2 qr3 = __fmul2_rn(qr, __fmul2_rn(ri, ri));
+            ph[h] = __fadd2_rn(ph[h], qr);
+            ex[h] = __ffma2_rn(qr3, dx, ex[h]);
+            ey[h] = __ffma2_rn(qr3, dy, ey[h]);
+            ez[h] = __ffma2_rn(qr3, dz, ez[h]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kSC4Threads) k_sc_mixed4(const float4* __restrict__ shq,
+                                                           const float4* __restrict__ slo, int64_t nsrc,
+                                                           const double* __restrict__ tgt, int64_t ntgt,
+                                                           int exclude_self, float s2, double ke, int accumulate,
+                                                           double* __restrict__ phi, double* __restrict__ E) {
+    __shared__ float4 sA[kSC4Tile], sB[kSC4Tile], sC[kSC4Tile];
+    __shared__ float2 sD[kSC4Tile];
+    int64_t tq[4];
+    float2 th[2][3], tl[2][3];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        float hx[2], hy[2], hz[2], lx[2], ly[2], lz[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            tq[2 * h + q] = (int64_t)blockIdx.x * kSC4Tile + threadIdx.x + (2 * h + q) * kSC4Threads;
+            load_target_2f(tgt, tq[2 * h + q], tq[2 * h + q] < ntgt, hx[q], hy[q], hz[q], lx[q], ly[q], lz[q]);
+        }
+        th[h][0] = make_float2(hx[0], hx[1]), th[h][1] = make_float2(hy[0], hy[1]), th[h][2] = make_float2(hz[0], hz[1]);
+        tl[h][0] = make_float2(lx[0], lx[1]), tl[h][1] = make_float2(ly[0], ly[1]), tl[h][2] = make_float2(lz[0], lz[1]);
+    }
+    const float2 s22 = make_float2(s2, s2);
+    const float2 zero = make_float2(0.f, 0.f);
+    F2Acc aph[2] = {{zero, zero}, {zero, zero}}, aex[2] = {{zero, zero}, {zero, zero}},
+          aey[2] = {{zero, zero}, {zero, zero}}, aez[2] = {{zero, zero}, {zero, zero}};
+    for (int64_t base = 0; base < nsrc; base += kSC4Tile) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < kSC4Tile; i += kSC4Threads) {
+            const int64_t c = base + i;
+            if (c < nsrc) {
+                const float4 h = shq[c], l = slo[c];
+                sA[i] = make_float4(-h.x, -h.x, -h.y, -h.y);
+                sB[i] = make_float4(-h.z, -h.z, h.w, h.w);
+                sC[i] = make_float4(-l.x, -l.x, -l.y, -l.y);
+                sD[i] = make_float2(-l.z, -l.z);
+            }
+        }
+        __syncthreads();
+        const int cnt = (int)min((int64_t)kSC4Tile, nsrc - base);
+        const bool self_tile = exclude_self && (base == (int64_t)blockIdx.x * kSC4Tile);
+        int self[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) self[q] = self_tile ? (int)threadIdx.x + q * kSC4Threads : -1;
+        for (int sub = 0; sub < cnt; sub += kFlush) {
+            const int m = min(kFlush, cnt - sub);
+            float2 fph[2] = {zero, zero}, fex[2] = {zero, zero}, fey[2] = {zero, zero}, fez[2] = {zero, zero};
+            bool hit = false;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) hit |= self[q] >= sub && self[q] < sub + m;
+            if (hit)
+                sc_tile_f32x2x2<true>(sA, sB, sC, sD, sub, sub + m, th, tl, s22, self, fph, fex, fey, fez);
+            else
+                sc_tile_f32x2x2<false>(sA, sB, sC, sD, sub, sub + m, th, tl, s22, self, fph, fex, fey, fez);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                acc_add(aph[h], fph[h]);
+                acc_add(aex[h], fex[h]);
+                acc_add(aey[h], fey[h]);
+                acc_add(aez[h], fez[h]);
+            }
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (tq[2 * h] < ntgt)
+            store_target(tq[2 * h], accumulate, ke, (double)aph[h].hi.x + (double)aph[h].lo.x,
+                         (double)aex[h].hi.x + (double)aex[h].lo.x, (double)aey[h].hi.x + (double)aey[h].lo.x,
+                         (double)aez[h].hi.x + (double)aez[h].lo.x, phi, E);
+        if (tq[2 * h + 1] < ntgt)
+            store_target(tq[2 * h + 1], accumulate, ke, (double)aph[h].hi.y + (double)aph[h].lo.y,
+                         (double)aex[h].hi.y + (double)aex[h].lo.y, (double)aey[h].hi.y + (double)aey[h].lo.y,
+                         (double)aez[h].hi.y + (double)aez[h].lo.y, phi, E);
+    }
+}
+
 // b_i -= phi_sc(c_i) on conductor rows, b_i -= n_i . E_sc(c_i) on interface rows.
 __global__ void k_rhs_sc(const Elem* __restrict__ el, int64_t n, const double* __restrict__ phi,
                          const double* __restrict__ E, double* __restrict__ b) {
@@ -295,6 +412,9 @@ cudaError_t launch_sc_eval(int precision, const double* src, const double* q, co
     if (precision == NEBEM_FP64)
         k_sc_f64<<<blocks, kSCThreads, 0, s>>>(src, q, nsrc, tgt, ntgt, exclude_self, soft * soft, ke, accumulate, phi,
                                                E);
+    else if (ntgt >= (int64_t)152 * 4 * kSC4Tile)  // enough 512-target blocks for several waves
+        k_sc_mixed4<<<(unsigned)((ntgt + kSC4Tile - 1) / kSC4Tile), kSC4Threads, 0, s>>>(
+            hq, lo, nsrc, tgt, ntgt, exclude_self, (float)(soft * soft), ke, accumulate, phi, E);
     else
         k_sc_mixed<<<(unsigned)((ntgt + kSC2Tile - 1) / kSC2Tile), kSC2Threads, 0, s>>>(
             hq, lo, nsrc, tgt, ntgt, exclude_self, (float)(soft * soft), ke, accumulate, phi, E);

@@ -222,6 +222,32 @@ def test_space_charge_parity(N, prec):
         assert (np.linalg.norm(E - rE, axis=1) / absE).max() <= 3e-7
 
 
+def test_space_charge_large_target_sets_same_bits(N):
+    """Target sets of >= 311,296 points take the four-targets-per-thread kernel: per target
+    the same operations in the same order as the two-target kernel used for small sets, so
+    the results agree bit for bit; with self exclusion, sampled carriers against the oracle."""
+    g = I.cube(n_per_edge=2)
+    pos, q = I.carrier_cloud(I.thgem(), 320_000, I.rng(3, 5))
+    ctx = N.Context().set_geometry(g)
+    N.nebem_space_charge(ctx.h, pos, q, 1e-6)
+    phi4, E4 = N.nebem_space_charge_eval(ctx.h, pos, N.NEBEM_MIXED)
+    phi2, E2 = N.nebem_space_charge_eval(ctx.h, pos[:3000], N.NEBEM_MIXED)
+    assert np.array_equal(phi4[:3000], phi2) and np.array_equal(E4[:3000], E2)
+    phi, E = N.nebem_space_charge_eval(ctx.h, pos, N.NEBEM_MIXED, exclude_self=True)
+    idx = I.rng(3, 6).choice(pos.shape[0], 12, replace=False)
+    for i in idx:
+        keep = np.ones(pos.shape[0], bool)
+        keep[i] = False
+        rphi, rE = O.space_charge(pos[keep], q[keep], tgt=pos[i:i + 1], soft=1e-6)
+        # the +/-e terms cancel at a carrier of a net-neutral cloud: FP32 per-term accuracy
+        # bounds the error by the sums of |terms| (as in test_space_charge_parity)
+        absphi, _ = O.space_charge(pos[keep], np.abs(q[keep]), tgt=pos[i:i + 1], soft=1e-6)
+        d = pos[i] - pos[keep]
+        absE = O.ke() * (np.abs(q[keep]) / ((d * d).sum(1) + 1e-12)).sum()
+        assert abs(phi[i] - rphi[0]) <= 3e-7 * absphi[0]
+        assert np.linalg.norm(E[i] - rE[0]) <= 3e-7 * absE
+
+
 def test_dynamic_step_parity(N):
     g = I.cube(n_per_edge=4)
     gen = np.random.default_rng(37)
