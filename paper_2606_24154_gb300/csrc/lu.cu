@@ -724,9 +724,9 @@ __global__ void k_permute(const T* __restrict__ b, const int32_t* __restrict__ p
 // next block are loaded before its flag is awaited, so only x_c is read after it.  The
 // four partial sums are added in a fixed order, so the result does not depend on timing.
 // Diagonal block: FP64 sweeps solve it by substitution in one warp (lanes in step with
-// __syncwarp; U's diagonal through reciprocals); FP32 sweeps (the inner solves of the
-// iterative refinement) invert it in shared memory while the CTA waits, so that the step
-// on the critical path is a 64 x 64 matrix-vector product.  Every wait is bounded: on
+// __syncwarp, one synchronisation per column; U's diagonal through reciprocals); FP32
+// sweeps (the inner solves of the iterative refinement) invert it in shared memory while
+// the CTA waits, so that the step on the critical path is a 64 x 64 matrix-vector product.  Every wait is bounded: on
 // giving up the CTA records *err, writes NaN for its block and still publishes it.
 constexpr int kSvThreads = 256;
 constexpr long long kSvSpinLimit = 1ll << 22;
@@ -749,6 +749,7 @@ __global__ void __launch_bounds__(kSvThreads) k_trsv(const T* __restrict__ LU, i
     __shared__ T Xi[kInv ? kTB : 1][kTB + 1];
     __shared__ T part[kSvThreads / kTB][kTB];
     __shared__ T xs[kTB];
+    __shared__ T xo[kInv ? 1 : kTB];
     __shared__ T dinv[kTB];
     __shared__ int s_t, s_ready, s_ok;
     if (threadIdx.x == 0) s_t = atomicAdd(ticket, 1);
@@ -895,13 +896,15 @@ __global__ void __launch_bounds__(kSvThreads) k_trsv(const T* __restrict__ LU, i
                     __syncwarp();
                 }
             } else {
+                // every lane scales x_c itself (the same rounded product), the owner lane
+                // keeps it in xo: one warp synchronisation per column
                 for (int c = w - 1; c >= 0; --c) {
-                    if (lane == (c & 31)) xs[c] = xs[c] * dinv[c];
-                    __syncwarp();
-                    const T xc = xs[c];
+                    const T xc = xs[c] * dinv[c];
+                    if (lane == (c & 31)) xo[c] = xc;
                     for (int r = lane; r < c; r += 32) xs[r] -= D[r][c] * xc;
                     __syncwarp();
                 }
+                for (int r = lane; r < w; r += 32) xs[r] = xo[r];
             }
         }
     }
