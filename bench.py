@@ -371,9 +371,22 @@ def run_native(args):
                          "E_pointwise_rel_err_floor1e-3": pp_E, "sample_points": ns,
                          "sigma_refinement": {"iterations": info.iterations, "correction": info.correction}},
             "fp64_path": {"value": fp64_rate, "unit": "evals/s", "sample_points": ns,
-                          "speedup_mixed_over_fp64": value / world / fp64_rate},
+                          "speedup_mixed_over_fp64": value / world / fp64_rate,
+                          "roofline": {"bound": "fp64",
+                                       "achieved": fp64_rate * R.FP64_INST_PER_PAIR / 1e12,
+                                       "peak": R.fp64_peak_inst(peaks.get("sm_max_mhz", 2070.0)) / 1e12,
+                                       "unit": "T FP64 instructions/s",
+                                       "frac": fp64_rate * R.FP64_INST_PER_PAIR
+                                       / R.fp64_peak_inst(peaks.get("sm_max_mhz", 2070.0)),
+                                       "note": "278 FP64 instructions per pair (ncu count); peak = 152 SMs x "
+                                               "2 FP64 instructions per clock x max SM clock"}},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
                          "frac": achieved / peak_ops,
+                         "mufu": {"achieved": counts["nodes"] * (npts / CHECK_SAMPLE) / (ms * 1e-3) / 1e12,
+                                  "peak": R.mufu_peak(peaks.get("sm_max_mhz", 2070.0)) / 1e12,
+                                  "unit": "T rsqrt/s",
+                                  "frac": counts["nodes"] * (npts / CHECK_SAMPLE) / (ms * 1e-3)
+                                  / R.mufu_peak(peaks.get("sm_max_mhz", 2070.0))},
                          "traffic": FAR_TRAFFIC_BYTES_1E6 if npts == N_POINTS else None,
                          "note": "FP32 lane ops (Gauss nodes x 13 + pairs x 12) per launch / event time; peak = "
                                  "152 SMs x 128 lanes x max SM clock; traffic = DRAM bytes per far-kernel launch "

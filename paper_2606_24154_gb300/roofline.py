@@ -81,6 +81,18 @@ def mufu_peak(sm_mhz):
     return N_SM * MUFU_PER_SM * sm_mhz * 1e6
 
 
+# FP64 closed form: FP64 instructions per (point, element, image) pair of the FP64
+# evaluation kernel, from an ncu instruction count on the THGEM cell (166 DFMA, 59 DADD,
+# 53 DMUL); the FP64 pipe issues 2 such instructions per clock per SM on this GPU
+# (1.25 TFLOP/s nominal with an FMA as 2 flops).
+FP64_INST_PER_PAIR = 278
+FP64_INST_PER_SM_CLK = 2
+
+
+def fp64_peak_inst(sm_mhz):
+    return N_SM * FP64_INST_PER_SM_CLK * sm_mhz * 1e6
+
+
 # ---------------------------------------------------------------- mixed fill
 # Two-float (hi + lo FP32) operations of the mixed fill kernel, counted from its code (FP32
 # lane operations; the node loops run two nodes per packed FP32x2 instruction, one lane
