@@ -54,3 +54,28 @@ def test_mixed_solve_bem_matrix_refines_to_oracle(N):
     sig, info, _ = ctx.solve(N.NEBEM_MIXED)
     assert np.abs(sig - sig_r).max() <= 1e-8 * np.abs(sig_r).max()
     assert info.iterations <= 12
+
+
+@pytest.mark.parametrize("n", [1, 2, 63, 65, 129, 1000])
+def test_lu_edge_sizes_fp64_solve_and_fp32_factor(N, n):
+    """Sizes around the 64-row block of the single-launch triangular sweeps and the panel
+    width: FP64 factor + solve against numpy; FP32 factor (cooperative panel) reconstructs."""
+    import torch
+    gen = np.random.default_rng(1000 + n)
+    A = gen.normal(size=(n, n)) + 2.0 * np.sqrt(n) * np.eye(n)
+    b = gen.normal(size=n)
+    ctx = N.Context()
+    dA = torch.tensor(np.asfortranarray(A).ravel(order="F"), device="cuda")
+    dp = torch.empty(n, dtype=torch.int32, device="cuda")
+    N.nebem_lu_factor_device(ctx.h, dA.data_ptr(), n, dp.data_ptr())
+    db = torch.tensor(b, device="cuda")
+    N.nebem_lu_solve_device(ctx.h, dA.data_ptr(), n, dp.data_ptr(), db.data_ptr())
+    torch.cuda.synchronize()
+    x = db.cpu().numpy()
+    xr = np.linalg.solve(A, b)
+    assert np.abs(x - xr).max() <= 1e-12 * np.abs(xr).max()
+    dA32 = torch.tensor(np.asfortranarray(A).ravel(order="F").astype(np.float32), device="cuda")
+    N.nebem_lu_factor_device_f32(ctx.h, dA32.data_ptr(), n, dp.data_ptr())
+    LU = dA32.cpu().numpy().astype(np.float64).reshape(n, n, order="F")
+    L, U, perm = _unpack(LU, dp.cpu().numpy())
+    assert np.abs(A[perm] - L @ U).max() / np.abs(A).max() <= 2e-5
