@@ -47,12 +47,6 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
     t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// requires |a| >= |b| (or a == 0)
-__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& t) {
-    s = __fadd_rn(a, b);
-    t = __fsub_rn(b, __fsub_rn(s, a));
-}
-
 __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
     p = __fmul_rn(a, b);
     e = __fmaf_rn(a, b, -p);
