@@ -264,8 +264,8 @@ __global__ void __launch_bounds__(kPivThreads, 2) k_panel_col(T* __restrict__ A,
 //       pivot row, and the holders of rows j and p swap them in shared memory.
 // The candidate slots alternate between two parities: a CTA writes slot j+1 only after it
 // has passed barrier j, by which time every CTA has finished reading slot j-1.  The grid
-// barrier (arrival counter, generation number) waits a bounded number of polls; on giving
-// up a CTA records *err and leaves the panel (the host reports a timeout).
+// barrier (a cumulative arrival counter) waits a bounded number of polls; on giving up a
+// CTA records *err and leaves the panel (the host reports a timeout).
 constexpr int kCoopThreads = 256;
 constexpr int kCoopMaxG = 1024;
 constexpr long long kCoopSpinLimit = 1ll << 22;
@@ -275,7 +275,7 @@ struct CoopScratch {
     long long cidx[2][kCoopMaxG];
     float cand[2][kCoopMaxG][64];
     float srow[2][64];
-    unsigned int bar[4];  // arrival count, generation
+    unsigned int bar[4];  // bar[0]: grid-barrier arrivals of the factorisation
     int err;
 };
 
@@ -290,20 +290,20 @@ __device__ __forceinline__ int ld_acquire_i(const int* p) {
     return v;
 }
 
-// every CTA of the grid arrives; false if the wait gave up
-__device__ bool coop_barrier(CoopScratch* cs, unsigned int nblocks, bool* s_flag) {
+// every CTA of the grid arrives; false if the wait gave up.  bar[0] counts all arrivals
+// of the factorisation (never reset): each CTA adds 1 with acquire-release semantics and
+// waits until the count reaches `target` (this barrier's total), so one atomic and one
+// polled load make the barrier, and the last arrival publishes everyone's writes (the
+// acquire load that sees the final count synchronises with every add before it).
+__device__ bool coop_barrier(CoopScratch* cs, unsigned int target, bool* s_flag) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned int gen = ld_acquire_u(&cs->bar[1]);
-        __threadfence();
+        unsigned int v;
+        asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(v) : "l"(&cs->bar[0]) : "memory");
         bool ok = true;
-        if (atomicAdd(&cs->bar[0], 1u) == nblocks - 1) {
-            atomicExch(&cs->bar[0], 0u);
-            __threadfence();
-            atomicAdd(&cs->bar[1], 1u);
-        } else {
+        if (v + 1u < target) {
             long long spins = 0;
-            while (ld_acquire_u(&cs->bar[1]) == gen) {
+            while (ld_acquire_u(&cs->bar[0]) < target) {
                 // give up after the poll limit, or at once when another CTA has given up
                 if (++spins > kCoopSpinLimit || ((spins & 1023) == 0 && ld_acquire_i(&cs->err))) {
                     ok = false;
@@ -312,7 +312,6 @@ __device__ bool coop_barrier(CoopScratch* cs, unsigned int nblocks, bool* s_flag
                 __nanosleep(20);
             }
         }
-        __threadfence();
         *s_flag = ok;
     }
     __syncthreads();
@@ -321,7 +320,7 @@ __device__ bool coop_barrier(CoopScratch* cs, unsigned int nblocks, bool* s_flag
 
 __global__ void __launch_bounds__(kCoopThreads, 1)
     k_panel_coop(float* __restrict__ A, int64_t n, int64_t k0, int64_t k1, int R, int32_t* __restrict__ piv,
-                 int* __restrict__ info, int* __restrict__ tmo, CoopScratch* cs) {
+                 int* __restrict__ info, int* __restrict__ tmo, CoopScratch* cs, unsigned int bar_base) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (ld_acquire_i(&cs->err)) return;  // an earlier panel gave up: leave the matrix as it is
     const int w = (int)(k1 - k0);
@@ -387,7 +386,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1)
             cs->cand[par][b][threadIdx.x] = (mine != LLONG_MAX) ? S[threadIdx.x * R + (int)(mine - rb0)] : 0.f;
             if (j >= rb0 && j < rb0 + nr) cs->srow[par][threadIdx.x] = S[threadIdx.x * R + (int)(j - rb0)];
         }
-        if (!coop_barrier(cs, (unsigned)G, &s_flag)) {
+        if (!coop_barrier(cs, bar_base + (unsigned)(jj + 1) * (unsigned)G, &s_flag)) {
             if (threadIdx.x == 0) {
                 atomicExch(&cs->err, 1);
                 atomicExch(tmo, 1);
@@ -614,6 +613,7 @@ cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_inf
         }
         cudaGetLastError();  // a refused attribute or query leaves the per-column path
     }
+    unsigned int arrivals = 0;  // grid-barrier arrivals of the cooperative panels so far
     for (int64_t k0 = 0; k0 < n; k0 += nb) {
         const int64_t k1 = std::min<int64_t>(n, k0 + nb);
         const int w = (int)(k1 - k0);
@@ -625,9 +625,11 @@ cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_inf
             int64_t nn = n, kk0 = k0, kk1 = k1;
             int RR = R;
             int* tmo = d_info + 1;
-            void* args[] = {&Af, &nn, &kk0, &kk1, &RR, &piv, &d_info, &tmo, &cs};
+            unsigned int base = arrivals;
+            void* args[] = {&Af, &nn, &kk0, &kk1, &RR, &piv, &d_info, &tmo, &cs, &base};
             NB_TRY(cudaLaunchCooperativeKernel((const void*)k_panel_coop, dim3((unsigned)G), dim3(kCoopThreads), args,
                                                (size_t)R * w * sizeof(float), s));
+            arrivals += (unsigned int)G * (unsigned int)w;
         } else {
             // columns k0..k1-1: update by the previous column + pivot of this one; then the
             // last column's scaling of the rows below the panel
