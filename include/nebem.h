@@ -385,7 +385,7 @@ typedef struct nebem_server nebem_server;
 
 typedef struct nebem_server_options {
     int64_t arena_points;   /* device staging capacity in points (default 4,194,304) */
-    int32_t chunk_points;   /* points per work item (default 1024) */
+    int32_t chunk_points;   /* points per work item (128, the only value accepted) */
     int32_t max_requests;   /* in-flight request slots (default 256) */
     int32_t workers;        /* persistent CTAs (0 = 2 per SM) */
     int32_t idle_us;        /* a persistent kernel with no work exits after this (default 2000) */

@@ -5,9 +5,9 @@
 // point arena has room for its points and the work ring has room for its items: its
 // points are copied into the arena, its remaining point-block counter is set, and its
 // items are appended to the ring in host-mapped memory before `tail` is advanced.  An
-// item is 128 points over all elements; a small mixed request (<= 1024 points) instead
-// gets one item per (point block, chunk of 1024 elements), so that its few points still
-// spread over many CTAs (its latency would otherwise be one CTA's pass over all elements).  A persistent kernel (relaunched whenever admitted work exists and no
+// item is 128 points over all elements; a request of up to 16384 points instead gets one
+// item per (point block, chunk of 1024 elements), so that its points still spread over
+// many CTAs (its latency would otherwise be one CTA's pass over all elements).  A persistent kernel (relaunched whenever admitted work exists and no
 // instance is running) claims items as they appear, so requests admitted while others
 // run join the running launch.  On completion the outputs are copied to the caller's
 // buffers and the arena range, slot and ring items are released.
@@ -36,9 +36,11 @@ namespace {
     } while (0)
 
 constexpr int kItemPoints = 128;
-constexpr int64_t kSmallPoints = 1024;      // mixed requests up to this size are split by element chunks
-constexpr int64_t kSmallPointsF64 = 16384;  // FP64 requests up to this size too (one block per SM already
-                                            // keeps the FP64 pipe busy, so larger ones need no split)
+// Requests up to this many points are split by element chunks (when the partial-sum blocks
+// are free), so that a request of a few hundred point blocks still spreads over every SM; a
+// point's chunk sums are added in a fixed order, so the split does not change its bits.
+constexpr int64_t kSmallPoints = 16384;     // mixed
+constexpr int64_t kSmallPointsF64 = 16384;  // FP64
 constexpr int kPartialBlocks = 512;     // point blocks with chunk partial sums in flight
 
 struct Interval {

@@ -9,7 +9,7 @@
 namespace nb {
 
 // One work item: up to 128 points of one request, at `offset` in the point arena, over
-// all elements (chunk < 0) or over one chunk of kChunkEl elements (small mixed requests:
+// all elements (chunk < 0) or over one chunk of kChunkEl elements (requests up to 16384 points:
 // every chunk of a point block is a separate item, so a few points still spread over many
 // CTAs; the block's partial sums live in partial block `pblock`).
 struct WorkItem {
