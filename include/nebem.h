@@ -303,13 +303,19 @@ int nebem_lu_factor_device(nebem_ctx *ctx, double *d_A, int64_t n, int32_t *d_pi
 
 /* FP32 variant (the factorisation inside mixed solves): d_A is float, n x n column-major.
  * The rank-64 trailing updates run on the tensor cores (tcgen05, TF32 with a hi/lo split
- * of both operands, FP32 accumulation); panels, swaps and the unit-lower block inverse
- * run in FP32 on the CUDA cores.  Errors as nebem_lu_factor_device, plus NEBEM_TIMEOUT if
- * a tensor-core update's bounded wait gave up. */
+ * of both operands, FP32 accumulation; with n % 4 == 0 and d_A 16-byte aligned the
+ * operands move by bulk copies and the products are added to the matrix by TMA
+ * reduce-add).  Each 64-column panel is factored in one cooperative launch (all CTAs
+ * resident, one bounded grid barrier per column) when the device supports it; pivots are
+ * those of partial pivoting with the lowest row on ties.  Swaps and the unit-lower block
+ * inverse run in FP32 on the CUDA cores.  Errors as nebem_lu_factor_device, plus
+ * NEBEM_TIMEOUT if a bounded wait (tensor-core update or panel barrier) gave up. */
 int nebem_lu_factor_device_f32(nebem_ctx *ctx, float *d_A, int64_t n, int32_t *d_piv, void *stream);
 
 /* Solve A x = b in place with factors from nebem_lu_factor_device: d_b (device, n) is
- * overwritten by x.  Asynchronous on `stream` (NULL = the context stream). */
+ * overwritten by x.  Asynchronous on `stream` (NULL = the context stream).  Each
+ * triangular sweep is one launch over 64-row blocks that wait (bounded) for the blocks
+ * before them; a wait that gives up writes NaN for its block instead of hanging. */
 int nebem_lu_solve_device(nebem_ctx *ctx, const double *d_LU, int64_t n, const int32_t *d_piv, double *d_b,
                           void *stream);
 
