@@ -124,14 +124,14 @@ def test_server_argument_errors(N, ctxs):
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_server_small_requests_split_by_element_chunks(N, prec):
-    """Small requests on the full THGEM cell (10 element chunks) run as one item per
-    (point block, chunk); their results equal the standalone evaluation bit for bit.
-    Mixed requests up to 1024 points and FP64 requests up to 16384 points are split."""
+    """Requests on the full THGEM cell (10 element chunks) of up to 16384 points run as one
+    item per (point block, chunk), larger ones as one item per point block; either way the
+    results equal the standalone evaluation bit for bit (sizes on both sides of the limit)."""
     g = I.thgem()
     c = N.Context().set_geometry(g)
     c.solve(N.NEBEM_MIXED)
     p = N.NEBEM_MIXED if prec == "mixed" else N.NEBEM_FP64
-    sizes = [1, 50, 129, 300, 1024, 1025] if prec == "mixed" else [1, 129, 700, 2000]
+    sizes = [1, 50, 129, 300, 1024, 1025, 5000, 16384, 16385] if prec == "mixed" else [1, 129, 2000, 16384, 16385]
     srv = N.nebem_server_create([c.h])
     try:
         reqs = []
