@@ -819,3 +819,79 @@ def test_two_carriers_coulomb():
     assert np.abs(E[0] - ke * q[1] * d / r2 ** 1.5).max() <= 1e-14 * np.abs(E[0]).max()
     assert abs(phi[1] - ke * q[0] / np.sqrt(r2)) <= 1e-15 * abs(phi[1])
     assert np.abs(E[1] + ke * q[0] * d / r2 ** 1.5).max() <= 1e-14 * np.abs(E[1]).max()
+
+
+def test_pair_tiers_match_fp64_distance_classes():
+    """The FP32 tier decision of the oracle (two-float differences, FP32 squared distance)
+    agrees with the classification of the FP64 distance d / rho_j wherever d is not
+    within 1e-5 (relative) of a threshold; near thresholds either neighbouring tier is
+    accepted.  Covers all five codes (points in the hole, near the Cu and FR4 surfaces)."""
+    g = I.thgem(I.PlateSpec(n_phi=12, n_r=2, n_zc=1, n_zf=3), n_plane=2)
+    gen = np.random.default_rng(71)
+    pts = I.cell_points(g, 60, gen)
+    # points close to element centroids give the near tiers
+    v = g.elements["v"]
+    kinds = g.elements["kind"]
+    c = np.where((kinds == I.KIND_TRI)[:, None], v[:, :3].mean(1), v[:, :4].mean(1))
+    pick = gen.choice(g.n, 20, replace=False)
+    pts = np.vstack([pts, c[pick] + gen.normal(size=(20, 3)) * 2e-5])
+    ratios = (64.0, 24.0, 8.0, 3.0)
+    codes = O.pair_tiers(g, pts, ratios)
+    nv = np.where(kinds == I.KIND_TRI, 3, 4)
+    d = np.linalg.norm(v - c[:, None, :], axis=2)
+    d[nv == 3, 3] = 0.0
+    rho = d.max(1)
+    t = O.image_table(g.lattice, g.img_lo, g.img_hi)
+    C = c[:, None, :] + t[None]                                   # (n, img, 3)
+    dist = np.linalg.norm(pts[:, None, None, :] - C[None], axis=3) / rho[None, :, None]
+    expect = np.full(dist.shape, 4, np.uint8)
+    for code, r in reversed(list(enumerate(ratios))):
+        expect[dist >= r] = code
+    near_thr = np.zeros(dist.shape, bool)
+    for r in ratios:
+        near_thr |= np.abs(dist / r - 1.0) <= 1e-5
+    ok = (codes == expect) | (near_thr & (np.abs(codes.astype(int) - expect.astype(int)) == 1))
+    assert ok.all()
+    assert set(np.unique(codes)) == {0, 1, 2, 3, 4}
+
+
+def test_fastvol_oracle_interpolation():
+    """FastVolume oracle (Sec. 3.3): node values are the evaluation at the nodes exactly;
+    an edge midpoint is the mean of its two nodes; points outside the box take the value
+    at the clamped point; and the interpolation error at fixed off-node points falls like
+    h^2 (trilinear, second order) as the grid is refined."""
+    g = I.cube(n_per_edge=4)
+    sigma, _, _ = O.solve(g)
+    ax = np.linspace(0.01, 0.02, 3)
+    ay = np.linspace(-0.004, 0.004, 3)
+    az = np.linspace(-0.003, 0.005, 3)
+    X, Y, Z = np.meshgrid(ax, ay, az, indexing="ij")
+    nodes = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    phi, E = O.fastvol(g, sigma, ax, ay, az, nodes)
+    rphi, rE = O.eval_points(g, sigma, nodes)
+    assert np.array_equal(phi, rphi) and np.array_equal(E, rE)
+    mid = np.array([[0.5 * (ax[0] + ax[1]), ay[1], az[2]]])
+    m_phi, m_E = O.fastvol(g, sigma, ax, ay, az, mid)
+    ends = np.array([[ax[0], ay[1], az[2]], [ax[1], ay[1], az[2]]])
+    e_phi, e_E = O.eval_points(g, sigma, ends)
+    assert abs(m_phi[0] - 0.5 * e_phi.sum()) <= 1e-14 * abs(e_phi).max()
+    assert np.abs(m_E[0] - 0.5 * e_E.sum(0)).max() <= 1e-14 * np.abs(e_E).max()
+    out = np.array([[0.03, 0.0, 0.0], [0.015, -0.01, 0.009]])
+    clamp = np.array([[0.02, 0.0, 0.0], [0.015, -0.004, 0.005]])
+    o_phi, o_E = O.fastvol(g, sigma, ax, ay, az, out)
+    c_phi, c_E = O.fastvol(g, sigma, ax, ay, az, clamp)
+    assert np.array_equal(o_phi, c_phi) and np.array_equal(o_E, c_E)
+    # second-order convergence outside the cube: the RMS error over random points of the box
+    # falls like h^2 (fitted log-log slope; first order would give 1)
+    probe = np.random.default_rng(72).uniform([0.012, -0.003, -0.003], [0.018, 0.003, 0.003], size=(200, 3))
+    ref, _ = O.eval_points(g, sigma, probe)
+    hs, errs = [], []
+    for m in (9, 17, 33, 65):
+        bx = np.linspace(0.012, 0.018, m)
+        by = np.linspace(-0.003, 0.003, m)
+        bz = np.linspace(-0.003, 0.003, m)
+        p, _ = O.fastvol(g, sigma, bx, by, bz, probe)
+        hs.append(0.006 / (m - 1))
+        errs.append(np.sqrt(np.mean((p - ref) ** 2)))
+    slope = np.polyfit(np.log(hs), np.log(errs), 1)[0]
+    assert 1.7 <= slope <= 2.3, (slope, errs)
