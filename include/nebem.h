@@ -297,8 +297,12 @@ int nebem_step(nebem_ctx *ctx, int32_t steps, double mu, double dt, int32_t prec
  *   d_piv  device int32[n]; row k was swapped with row d_piv[k] at step k.
  * Runs on `stream` (NULL = the context stream) and synchronises it before returning.
  * Allocates its work buffer (about (lu_block + 1) * n doubles) on the context's device
- * for the duration of the call.  Errors: NEBEM_SINGULAR (zero pivot; the factors are
- * incomplete), NEBEM_INVALID_ARG, NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
+ * for the duration of the call.  An exact zero pivot (the whole remaining column is zero)
+ * does not stop the factorisation: that column is left unscaled, the remaining columns
+ * are factored, and the call returns NEBEM_SINGULAR naming the first such column in
+ * nebem_last_error.  d_A and d_piv then hold complete factors, P A = L U, with an exact
+ * zero on U's diagonal there (which nebem_lu_solve_device cannot use).  Other errors:
+ * NEBEM_INVALID_ARG, NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
 int nebem_lu_factor_device(nebem_ctx *ctx, double *d_A, int64_t n, int32_t *d_piv, void *stream);
 
 /* FP32 variant (the factorisation inside mixed solves): d_A is float, n x n column-major.

@@ -53,3 +53,22 @@ def test_status_strings_and_defaults(lib):
     assert lib.nebem_status_string(nebem.NEBEM_SINGULAR) == b"NEBEM_SINGULAR"
     o = nebem.nebem_default_options()
     assert o.ir_tol == 1e-8 and o.lu_block == 64 and o.softening == 1e-6
+
+
+@pytest.mark.parametrize("field,value", [
+    ("lu_block", 48), ("lu_block", 16), ("lu_block", 128),
+    ("ir_max_iter", 0), ("ir_tol", 0.0), ("ir_tol", float("nan")),
+    ("ratio_near", 1.0), ("ratio_b", 2.0), ("ratio_a", 7.0), ("ratio_0", 20.0), ("ratio_0", 1e7),
+    ("softening", 0.0), ("softening", -1e-6),
+])
+def test_bad_options_refused_before_any_device_call(lib, field, value):
+    """Context options are checked on the host before the device is touched: every bad
+    value is NEBEM_INVALID_ARG (with or without a GPU), never a silently corrected
+    default.  The tier ratios must keep 1.5 <= ratio_near <= ratio_b <= ratio_a <= ratio_0."""
+    from paper_2606_24154_gb300 import nebem
+    o = nebem.nebem_default_options()
+    setattr(o, field, value)
+    with pytest.raises(nebem.NebemError) as ei:
+        nebem.nebem_create(o)
+    assert ei.value.code == nebem.NEBEM_INVALID_ARG
+    assert lib.nebem_last_error() != b""

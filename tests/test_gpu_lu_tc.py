@@ -79,3 +79,55 @@ def test_lu_edge_sizes_fp64_solve_and_fp32_factor(N, n):
     LU = dA32.cpu().numpy().astype(np.float64).reshape(n, n, order="F")
     L, U, perm = _unpack(LU, dp.cpu().numpy())
     assert np.abs(A[perm] - L @ U).max() / np.abs(A).max() <= 2e-5
+
+
+@pytest.mark.parametrize("zero_col", [0, 70, 299])
+def test_exact_zero_pivot_reported_and_factorisation_completed(N, zero_col):
+    """A matrix with an exactly zero column keeps that column zero through every row swap
+    and update (each update term is a multiple of one of its entries), so the pivot search
+    meets an exact zero there.  Both factorisations report NEBEM_SINGULAR naming the
+    column, skip that column's scaling (there is nothing below the diagonal to eliminate)
+    and run to the end: every pivot row lies in [k, n), U has an exact zero on its
+    diagonal at the column, and P A = L U holds as for a regular matrix."""
+    import torch
+    n = 300
+    gen = np.random.default_rng(77 + zero_col)
+    A = gen.normal(size=(n, n)) + 2.0 * np.sqrt(n) * np.eye(n)
+    A[:, zero_col] = 0.0
+    ctx = N.Context()
+    cases = ((np.float64, N.nebem_lu_factor_device, 1e-12), (np.float32, N.nebem_lu_factor_device_f32, 2e-5))
+    for dtype, factor, tol in cases:
+        dA = torch.tensor(np.asfortranarray(A).ravel(order="F").astype(dtype), device="cuda")
+        dp = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        with pytest.raises(N.NebemError) as e:
+            factor(ctx.h, dA.data_ptr(), n, dp.data_ptr())
+        assert e.value.code == N.NEBEM_SINGULAR
+        assert f"zero pivot at column {zero_col}" in str(e.value)
+        piv = dp.cpu().numpy()
+        assert np.all(piv >= np.arange(n)) and np.all(piv < n)
+        LU = dA.cpu().numpy().astype(np.float64).reshape(n, n, order="F")
+        L, U, perm = _unpack(LU, piv)
+        assert U[zero_col, zero_col] == 0.0
+        assert np.abs(A[perm] - L @ U).max() / np.abs(A).max() <= tol
+
+
+def test_refinement_limit_reports_not_converged(N):
+    """With the refinement limit at one iteration the mixed solve stops after its first
+    correction.  x starts at zero, so that correction is all of x (relative size exactly
+    1): NEBEM_NOT_CONVERGED, one iteration, sigma still written (the FP32-LU solution,
+    within FP32 accuracy of the oracle) and usable by the evaluation.  The default limit
+    converges on the same system."""
+    g = I.cube(n_per_edge=4)
+    ref, _, _ = O.solve(g)
+    ctx = N.Context(ir_max_iter=1).set_geometry(g)
+    sig, info, rc = N.nebem_solve(ctx.h, N.NEBEM_MIXED, g.n, allow_not_converged=True)
+    assert rc == N.NEBEM_NOT_CONVERGED
+    assert info.iterations == 1 and info.correction == 1.0
+    assert np.abs(sig - ref).max() <= 1e-4 * np.abs(ref).max()
+    pts = np.array([[0.0, 0.0, 0.03], [0.02, -0.01, 0.005]])
+    phi, _ = ctx.eval(pts, N.NEBEM_FP64)
+    rphi, _ = O.eval_points(g, sig, pts)
+    assert np.abs(phi - rphi).max() <= 1e-10 * np.abs(rphi).max()
+    sig2, info2, rc2 = N.Context().set_geometry(g).solve(N.NEBEM_MIXED)
+    assert rc2 == N.NEBEM_OK and info2.correction <= 1e-8
+    assert np.abs(sig2 - ref).max() <= 1e-8 * np.abs(ref).max()

@@ -39,10 +39,12 @@ def _worker(rank, world, port, out):
 def test_two_rank_reduction_and_shards():
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
-    out = mgr.dict()
-    mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
-    r0, r1 = out[0], out[1]
+    # every process (the manager's too) is spawned, never forked from a process that may
+    # hold threads or a CUDA context
+    with mp.get_context("spawn").Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
+        r0, r1 = out[0], out[1]
     assert r0[0] == r1[0] == 15.0                      # max over ranks
     assert r0[1] == r1[1] == 2 * 100 * 24 * 1          # total evaluations of both ranks
     assert r0[2] != r1[2]                              # ranks draw different points
