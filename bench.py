@@ -38,7 +38,7 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) of one k_eval_far launch on the default workload (1e6 points),
 # from ncu dram__bytes_read.sum + dram__bytes_write.sum (profiles/eval_mixed_thgem.md);
 # reported only for that workload and for the kernel version it was taken on.
-FAR_TRAFFIC_BYTES_1E6 = 73.45e6 + 24.29e6
+FAR_TRAFFIC_BYTES_1E6 = 74.07e6 + 25.28e6
 
 
 def parse():

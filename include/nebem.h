@@ -200,8 +200,9 @@ int nebem_matrix_entries(nebem_ctx *ctx, const int64_t *rows, const int64_t *col
  * densities; Sec. 4.1 PFAtPoint = element part + known-charge part): phi(x) =
  * ke sum_j sigma_j sum_k Phi'(x; j + t_k) [+ ke sum_c q_c / sqrt(r^2 + s^2) when a
  * known-charge set is present], E likewise.  pts[n][3] row-major (host);
- * phi[n] and/or E[n][3] (host) may be NULL.  n = 0 is allowed.
- * Errors: NEBEM_BAD_STATE (no charge densities), NEBEM_INVALID_ARG. */
+ * phi[n] and/or E[n][3] (host) may be NULL.  n = 0 is allowed.  A point with a NaN or
+ * infinite coordinate gets NaN phi and E (both precisions; the other points are not
+ * affected).  Errors: NEBEM_BAD_STATE (no charge densities), NEBEM_INVALID_ARG. */
 int nebem_eval(nebem_ctx *ctx, const double *pts, int64_t n, double *phi, double *E, int32_t precision);
 
 /* Device variant of nebem_eval: d_pts, d_phi, d_E are device pointers (d_phi or d_E may
@@ -360,7 +361,8 @@ int nebem_fastvol_build(nebem_ctx *ctx, const double *x_nodes, int32_t nx, const
 
 /* Trilinear interpolation of the map at points (host buffers as in nebem_eval): the
  * eight nodes of the cell that holds the point, weights from its fractional position;
- * points outside the grid box take the value at the nearest point of the box. */
+ * points outside the grid box take the value at the nearest point of the box; a point
+ * with a NaN or infinite coordinate gets NaN. */
 int nebem_fastvol_eval(nebem_ctx *ctx, const double *pts, int64_t n, double *phi, double *E);
 
 /* Device variant of nebem_fastvol_eval (asynchronous on `stream`, NULL = context stream). */

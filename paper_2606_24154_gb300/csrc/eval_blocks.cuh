@@ -184,13 +184,20 @@ __device__ __forceinline__ void load_point_2f(const double* __restrict__ pts, in
     split2f(Pz, phz, plz);
 }
 
-__device__ __forceinline__ void store_far(double* __restrict__ phi, double* __restrict__ E, int64_t p, const Sum4& s) {
+// Stores ke * sum for point p.  A point with a non-finite coordinate has no field: it gets
+// NaN in both precisions (the FP32 tiers would otherwise fail every distance test for it
+// and leave zeros).  Its coordinates are read again here rather than kept in a register
+// through the element loop.
+__device__ __forceinline__ void store_far(const double* __restrict__ pts, double* __restrict__ phi,
+                                          double* __restrict__ E, int64_t p, const Sum4& s) {
     const double ke = 1.0 / (4.0 * kPi * kEps0);
-    if (phi) phi[p] = ke * s.phi;
+    const bool finite = isfinite(pts[3 * p]) && isfinite(pts[3 * p + 1]) && isfinite(pts[3 * p + 2]);
+    const double f = finite ? ke : __longlong_as_double(0x7ff8000000000000ll);
+    if (phi) phi[p] = f * s.phi;
     if (E) {
-        E[3 * p] = ke * s.x;
-        E[3 * p + 1] = ke * s.y;
-        E[3 * p + 2] = ke * s.z;
+        E[3 * p] = f * s.x;
+        E[3 * p + 1] = f * s.y;
+        E[3 * p + 2] = f * s.z;
     }
 }
 
@@ -213,7 +220,7 @@ __device__ __forceinline__ void far_block(const GeomView& g, const double* __res
         tot.y += c.y;
         tot.z += c.z;
     }
-    if (active) store_far(phi, E, p, tot);
+    if (active) store_far(pts, phi, E, p, tot);
 }
 
 // Near part (FP64 closed forms) of one target; adds ke * sum to phi[p] / E[p].
@@ -337,7 +344,7 @@ __device__ __forceinline__ void f64_block(const Elem* __restrict__ el, const dou
         tot.y += c.y;
         tot.z += c.z;
     }
-    if (active) store_far(phi, E, p, tot);
+    if (active) store_far(pts, phi, E, p, tot);
 }
 
 }  // namespace nb

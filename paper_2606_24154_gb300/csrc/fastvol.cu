@@ -40,7 +40,8 @@ __device__ __forceinline__ int find_cell(const double* __restrict__ a, int n, do
 }
 
 // Trilinear interpolation of (phi, Ex, Ey, Ez) node values; points outside the box take the
-// values of the nearest face (coordinates clamped to the box).
+// values of the nearest face (coordinates clamped to the box).  A point with a non-finite
+// coordinate gets NaN (clamping would otherwise map it to a face).
 __global__ void k_fastvol_lookup(const double* __restrict__ ax, const double* __restrict__ ay,
                                  const double* __restrict__ az, int nx, int ny, int nz,
                                  const double* __restrict__ vphi, const double* __restrict__ vE,
@@ -48,6 +49,12 @@ __global__ void k_fastvol_lookup(const double* __restrict__ ax, const double* __
                                  double* __restrict__ E) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
+    if (!isfinite(pts[3 * p]) || !isfinite(pts[3 * p + 1]) || !isfinite(pts[3 * p + 2])) {
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        if (phi) phi[p] = nan;
+        if (E) E[3 * p] = E[3 * p + 1] = E[3 * p + 2] = nan;
+        return;
+    }
     const double x = fmin(fmax(pts[3 * p], ax[0]), ax[nx - 1]);
     const double y = fmin(fmax(pts[3 * p + 1], ay[0]), ay[ny - 1]);
     const double z = fmin(fmax(pts[3 * p + 2], az[0]), az[nz - 1]);

@@ -91,7 +91,8 @@ __global__ void __launch_bounds__(kMM) k_minmax_partial(const double* __restrict
 
 // Grid of the reduction: corner = minimum, dims = floor((max - min) / d) + 1.  A grid
 // whose flat voxel index, or whose key voxel * n + point, would not fit in 62 bits is
-// flagged (err, and sticky for a sequence of steps).
+// flagged (err, and sticky for a sequence of steps); so is a set with no finite extent
+// (every position NaN leaves the bounds at +inf / -inf).
 __global__ void __launch_bounds__(kMMBlocks) k_minmax_final(const double* __restrict__ partial, int nblk, int64_t n,
                                                             double d0, double d1, double d2, VoxGrid* __restrict__ g) {
     __shared__ double smn[3][kMMBlocks], smx[3][kMMBlocks];
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(kMMBlocks) k_minmax_final(const double* __rest
     double total = 1.0;
     for (int a = 0; a < 3; ++a) {
         const double na = floor(__ddiv_rn(__dsub_rn(smx[a][0], smn[a][0]), d[a])) + 1.0;
-        if (!(na < 4.0e18)) err = 1;
+        if (!(na >= 1.0 && na < 4.0e18)) err = 1;
         total *= na;
         g->lo[a] = smn[a][0];
         g->d[a] = d[a];

@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restr
                     tot.z += __ldcg(q + 3);
                 }
                 if (active) {
-                    store_far(arena_phi, arena_E, p, tot);
+                    store_far(arena_pts, arena_phi, arena_E, p, tot);
                     if (mixed) near_point(G.view, G.img, arena_pts, p, arena_phi, arena_E);
                 }
                 if (threadIdx.x == 0) pblock_count[it.pblock] = 0;

@@ -161,3 +161,45 @@ def test_eval_device_on_caller_stream(N, prec):
     N.nebem_eval_device(ctx.h, d_pts.data_ptr(), pts.shape[0], d_phi.data_ptr(), d_E.data_ptr(), p, st.cuda_stream)
     st.synchronize()
     assert np.array_equal(d_phi.cpu().numpy(), hphi) and np.array_equal(d_E.cpu().numpy(), hE)
+
+
+def test_non_finite_points_give_nan_and_leave_the_batch_unchanged(N):
+    """A point with a NaN or infinite coordinate has no field.  The FP32 tiers would fail
+    every distance test for it and return zeros, so every evaluation path writes NaN for
+    it instead: FP64 and mixed evaluation, the serving kernel (requests below its
+    whole-block size run as element chunks) and the FastVolume lookup.  The finite points
+    of the same batch keep their bits."""
+    g = I.thgem(I.PlateSpec(n_phi=24, n_r=3, n_zc=1, n_zf=4), n_plane=3)
+    ctx = N.Context().set_geometry(g)
+    ctx.solve(N.NEBEM_MIXED)
+    pts = I.cell_points(g, 400, I.rng(0, 31))
+    bad = np.array([3, 128, 255, 399])
+    dirty = pts.copy()
+    dirty[3, 0] = np.nan
+    dirty[128, 1] = np.inf
+    dirty[255, 2] = -np.inf
+    dirty[399] = np.nan
+    ok = np.setdiff1d(np.arange(pts.shape[0]), bad)
+    for prec in (N.NEBEM_FP64, N.NEBEM_MIXED):
+        phi, E = ctx.eval(dirty, prec)
+        assert np.isnan(phi[bad]).all() and np.isnan(E[bad]).all()
+        cphi, cE = ctx.eval(pts[ok], prec)
+        assert np.array_equal(phi[ok], cphi) and np.array_equal(E[ok], cE)
+    srv = N.nebem_server_create([ctx.h])
+    try:
+        for prec in (N.NEBEM_FP64, N.NEBEM_MIXED):
+            phi = np.empty(pts.shape[0])
+            E = np.empty((pts.shape[0], 3))
+            rid = N.nebem_server_submit(srv, 0, dirty, phi, E, prec)
+            N.nebem_server_wait(srv, rid, 120000)
+            rphi, rE = ctx.eval(dirty, prec)
+            assert np.array_equal(phi, rphi, equal_nan=True) and np.array_equal(E, rE, equal_nan=True)
+    finally:
+        N.nebem_server_destroy(srv)
+    p = g.pitch
+    N.nebem_fastvol_build(ctx.h, np.linspace(-0.5 * p, 0.5 * p, 9), np.linspace(-0.5 * p, 0.5 * p, 9),
+                          np.linspace(1.2e-3, 3.0e-3, 7), N.NEBEM_FP64)
+    phi, E = N.nebem_fastvol_eval(ctx.h, dirty)
+    assert np.isnan(phi[bad]).all() and np.isnan(E[bad]).all()
+    cphi, cE = N.nebem_fastvol_eval(ctx.h, pts[ok])
+    assert np.array_equal(phi[ok], cphi) and np.array_equal(E[ok], cE)
