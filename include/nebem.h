@@ -60,6 +60,11 @@ typedef enum nebem_status {
     NEBEM_TOO_LARGE = -10          /* size beyond a documented limit */
 } nebem_status;
 
+/* Every count a call takes (points, carriers, matrix entries, the order of a dense
+ * matrix) is at most NEBEM_MAX_COUNT; a larger one returns NEBEM_TOO_LARGE before any
+ * buffer is read or any size is computed from it. */
+#define NEBEM_MAX_COUNT 2147483647LL
+
 typedef enum nebem_precision { NEBEM_FP64 = 0, NEBEM_MIXED = 1 } nebem_precision;
 
 typedef enum nebem_kind { NEBEM_RECT = 0, NEBEM_TRI = 1, NEBEM_QUAD = 2 } nebem_kind;

@@ -49,17 +49,14 @@ cudaError_t DevBuf::ensure(size_t nbytes) {
     return cudaSuccess;
 }
 
+int check_count(int64_t n, const char* what) {
+    if (n > NEBEM_MAX_COUNT) return fail(NEBEM_TOO_LARGE, std::string(what) + " above 2^31 - 1");
+    return 0;
+}
+
 Ctx::~Ctx() {
+    // the device buffers free themselves after this body, on the device set here
     cudaSetDevice(device);
-    for (DevBuf* b : {&d_el, &d_far, &d_diag, &d_sigma, &d_K, &d_LU64, &d_LU32, &d_piv64, &d_piv32, &d_work, &d_b,
-                      &d_x, &d_r, &d_r32, &d_small, &d_pts, &d_phi, &d_E, &d_car, &d_q, &d_car2, &d_sc_tgt,
-                      &d_sc_phi, &d_sc_E, &d_scratch, &d_cjk, &d_cell_start, &d_cell_items, &d_fv_ax, &d_fv_ay, &d_fv_az, &d_fv_phi,
-                      &d_fv_E, &d_vkeys, &d_vflags, &d_vbsum, &d_vpartial, &d_vgrid, &d_lines, &d_linesf, &d_line_vox,
-                      &d_am_start, &d_am_items, &d_am_elarea, &d_am_parea, &d_am_tmp, &d_perm64, &d_perm32, &d_swork,
-                      &d_fill_el, &d_fill_nodes, &d_fill_tau, &d_fill_cell_start, &d_fill_cell_items})
-        b->release();
-    am_near.release_all();
-    am_far.release_all();
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     if (stream) cudaStreamDestroy(stream);
@@ -264,6 +261,7 @@ int nebem_fill(nebem_ctx* ctx, int32_t precision, double* K_out) {
 
 int nebem_matrix_entries(nebem_ctx* ctx, const int64_t* rows, const int64_t* cols, int64_t count, double* out) {
     if (!ctx || count < 0 || (count > 0 && (!rows || !cols || !out))) return fail(NEBEM_INVALID_ARG, "bad argument");
+    if (int rc = check_count(count, "entry count")) return rc;
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     if (c->n == 0) return fail(NEBEM_BAD_STATE, "set_geometry first");
     for (int64_t e = 0; e < count; ++e)
@@ -341,6 +339,7 @@ int nebem_eval_device(nebem_ctx* ctx, const double* d_pts, int64_t n, double* d_
                       void* stream) {
     if (!ctx) return fail(NEBEM_INVALID_ARG, "ctx is NULL");
     if (n < 0 || (n > 0 && !d_pts)) return fail(NEBEM_INVALID_ARG, "bad points");
+    if (int rc = check_count(n, "point count")) return rc;
     if (precision != NEBEM_FP64 && precision != NEBEM_MIXED) return fail(NEBEM_INVALID_ARG, "bad precision");
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     if (!c->sigma_valid) return fail(NEBEM_BAD_STATE, "no charge densities (solve or set_sigma first)");
@@ -353,6 +352,7 @@ int nebem_eval_device(nebem_ctx* ctx, const double* d_pts, int64_t n, double* d_
 int nebem_eval(nebem_ctx* ctx, const double* pts, int64_t n, double* phi, double* E, int32_t precision) {
     if (!ctx) return fail(NEBEM_INVALID_ARG, "ctx is NULL");
     if (n < 0 || (n > 0 && !pts)) return fail(NEBEM_INVALID_ARG, "bad points");
+    if (int rc = check_count(n, "point count")) return rc;
     if (precision != NEBEM_FP64 && precision != NEBEM_MIXED) return fail(NEBEM_INVALID_ARG, "bad precision");
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     if (!c->sigma_valid) return fail(NEBEM_BAD_STATE, "no charge densities (solve or set_sigma first)");
@@ -373,6 +373,7 @@ int nebem_eval(nebem_ctx* ctx, const double* pts, int64_t n, double* phi, double
 
 int nebem_lu_factor_device(nebem_ctx* ctx, double* d_A, int64_t n, int32_t* d_piv, void* stream) {
     if (!ctx || n <= 0 || !d_A || !d_piv) return fail(NEBEM_INVALID_ARG, "bad argument");
+    if (int rc = check_count(n, "matrix order")) return rc;
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     CK(cudaSetDevice(c->device));
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
@@ -392,6 +393,7 @@ int nebem_lu_factor_device(nebem_ctx* ctx, double* d_A, int64_t n, int32_t* d_pi
 
 int nebem_lu_factor_device_f32(nebem_ctx* ctx, float* d_A, int64_t n, int32_t* d_piv, void* stream) {
     if (!ctx || n <= 0 || !d_A || !d_piv) return fail(NEBEM_INVALID_ARG, "bad argument");
+    if (int rc = check_count(n, "matrix order")) return rc;
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     CK(cudaSetDevice(c->device));
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
@@ -413,6 +415,7 @@ int nebem_lu_factor_device_f32(nebem_ctx* ctx, float* d_A, int64_t n, int32_t* d
 int nebem_lu_solve_device(nebem_ctx* ctx, const double* d_LU, int64_t n, const int32_t* d_piv, double* d_b,
                           void* stream) {
     if (!ctx || n <= 0 || !d_LU || !d_piv || !d_b) return fail(NEBEM_INVALID_ARG, "bad argument");
+    if (int rc = check_count(n, "matrix order")) return rc;
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     CK(cudaSetDevice(c->device));
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
@@ -433,6 +436,7 @@ int nebem_pair_tiers(nebem_ctx* ctx, const double* pts, int64_t n, uint8_t* code
     if (!ctx || n < 0 || (n > 0 && (!pts || !codes))) return fail(NEBEM_INVALID_ARG, "bad argument");
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     if (c->n == 0) return fail(NEBEM_BAD_STATE, "set_geometry first");
+    if (n > 200000000LL) return fail(NEBEM_TOO_LARGE, "more than 2e8 pairs");
     const int64_t total = n * c->n * c->img.n;
     if (total > 200000000LL) return fail(NEBEM_TOO_LARGE, "more than 2e8 pairs");
     if (total == 0) return NEBEM_OK;
@@ -454,7 +458,8 @@ int nebem_element_influence(nebem_ctx* ctx, const nebem_element* el, int64_t n_e
                             double* phi_out, double* E_out) {
     if (!ctx || !el || !pts || !phi_out || !E_out || n_el <= 0 || n_pts <= 0)
         return fail(NEBEM_INVALID_ARG, "bad argument");
-    if (n_el * n_pts > 100000000LL) return fail(NEBEM_TOO_LARGE, "more than 1e8 pairs");
+    if (n_el > 100000000LL || n_pts > 100000000LL || n_el * n_pts > 100000000LL)
+        return fail(NEBEM_TOO_LARGE, "more than 1e8 pairs");
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     CK(cudaSetDevice(c->device));
     std::vector<Elem> h((size_t)n_el);

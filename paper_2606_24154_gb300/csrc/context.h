@@ -9,10 +9,16 @@
 
 namespace nb {
 
-// A device allocation owned by the context (grown on demand, freed on destroy).
+// A device allocation (grown on demand).  It owns its memory: freed by release() or when
+// the buffer goes out of scope, so an entry point that returns early on an error frees
+// its work buffers too.  Not copyable (a copy would free the memory twice).
 struct DevBuf {
     void* ptr = nullptr;
     size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
     cudaError_t ensure(size_t nbytes);
     void release();
     template <typename T>
@@ -104,6 +110,8 @@ struct Ctx {
 };
 
 int fail(int code, const std::string& msg);
+// NEBEM_TOO_LARGE for a count above NEBEM_MAX_COUNT, else 0
+int check_count(int64_t n, const char* what);
 int cuda_fail(cudaError_t e, const char* where);
 
 // solve.cpp

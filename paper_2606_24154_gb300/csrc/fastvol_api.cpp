@@ -68,6 +68,7 @@ static int fastvol_check(Ctx* c) {
 int nebem_fastvol_eval_device(nebem_ctx* ctx, const double* d_pts, int64_t n, double* d_phi, double* d_E,
                               void* stream) {
     if (!ctx || n < 0 || (n > 0 && !d_pts)) return fail(NEBEM_INVALID_ARG, "bad argument");
+    if (int rc = check_count(n, "point count")) return rc;
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     int rc = fastvol_check(c);
     if (rc) return rc;
@@ -82,6 +83,7 @@ int nebem_fastvol_eval_device(nebem_ctx* ctx, const double* d_pts, int64_t n, do
 
 int nebem_fastvol_eval(nebem_ctx* ctx, const double* pts, int64_t n, double* phi, double* E) {
     if (!ctx || n < 0 || (n > 0 && !pts)) return fail(NEBEM_INVALID_ARG, "bad argument");
+    if (int rc = check_count(n, "point count")) return rc;
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     int rc = fastvol_check(c);
     if (rc) return rc;

@@ -127,9 +127,7 @@ struct Server {
 
     ~Server() {
         cudaSetDevice(device);
-        if (compute) cudaStreamSynchronize(compute);
-        for (DevBuf* b : {&d_geoms, &d_pts, &d_phi, &d_E, &d_head, &d_remaining, &d_partials, &d_pcount})
-            b->release();
+        if (compute) cudaStreamSynchronize(compute);  // the device buffers free themselves after this body
         if (h_ring) cudaFreeHost(h_ring);
         if (h_tail) cudaFreeHost(h_tail);
         if (h_done) cudaFreeHost(h_done);

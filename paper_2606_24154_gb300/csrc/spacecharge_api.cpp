@@ -98,6 +98,7 @@ extern "C" {
 int nebem_space_charge(nebem_ctx* ctx, const double* pos, const double* q, int64_t n, double softening) {
     if (!ctx) return fail(NEBEM_INVALID_ARG, "ctx is NULL");
     if (n < 0 || (n > 0 && (!pos || !q))) return fail(NEBEM_INVALID_ARG, "bad carriers");
+    if (int rc = check_count(n, "carrier count")) return rc;
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     if (c->n == 0) return fail(NEBEM_BAD_STATE, "set_geometry first");
     for (int64_t i = 0; i < n; ++i)
@@ -128,6 +129,7 @@ int nebem_space_charge_eval(nebem_ctx* ctx, const double* pts, int64_t n, double
                             int32_t exclude_self) {
     if (!ctx) return fail(NEBEM_INVALID_ARG, "ctx is NULL");
     if (n < 0 || (n > 0 && !pts)) return fail(NEBEM_INVALID_ARG, "bad points");
+    if (int rc = check_count(n, "point count")) return rc;
     if (precision != NEBEM_FP64 && precision != NEBEM_MIXED) return fail(NEBEM_INVALID_ARG, "bad precision");
     Ctx* c = reinterpret_cast<Ctx*>(ctx);
     if (c->n_car == 0) return fail(NEBEM_BAD_STATE, "no known-charge set");

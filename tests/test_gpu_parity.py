@@ -288,6 +288,41 @@ def test_error_paths(N):
     assert e.value.code == N.NEBEM_TOO_LARGE
 
 
+
+def test_counts_above_the_limit_refused_before_any_access(N):
+    """A count above NEBEM_MAX_COUNT (2^31 - 1) is refused with NEBEM_TOO_LARGE before
+    any buffer is read and before any size is computed from it: every buffer passed here
+    holds a single point (or a 1 x 1 matrix)."""
+    import ctypes as C
+
+    import torch
+    L = N.load()
+    ctx = N.Context().set_geometry(I.cube(n_per_edge=2))
+    big = 2 ** 31
+    one = np.zeros(3)
+    d1 = N._dp(one)
+    i1 = np.zeros(1, np.int64).ctypes.data_as(C.POINTER(C.c_int64))
+    dev = torch.zeros(3, dtype=torch.float64, device="cuda")
+    piv = torch.zeros(1, dtype=torch.int32, device="cuda")
+    calls = {
+        "nebem_eval": lambda: L.nebem_eval(ctx.h, d1, big, d1, d1, N.NEBEM_FP64),
+        "nebem_eval_device": lambda: L.nebem_eval_device(ctx.h, dev.data_ptr(), big, dev.data_ptr(), None,
+                                                         N.NEBEM_MIXED, None),
+        "nebem_space_charge": lambda: L.nebem_space_charge(ctx.h, d1, d1, big, 1e-6),
+        "nebem_space_charge_eval": lambda: L.nebem_space_charge_eval(ctx.h, d1, big, d1, d1, N.NEBEM_FP64, 0),
+        "nebem_fastvol_eval": lambda: L.nebem_fastvol_eval(ctx.h, d1, big, d1, d1),
+        "nebem_matrix_entries": lambda: L.nebem_matrix_entries(ctx.h, i1, i1, big, d1),
+        "nebem_lu_factor_device": lambda: L.nebem_lu_factor_device(ctx.h, dev.data_ptr(), big, piv.data_ptr(), None),
+        "nebem_lu_solve_device": lambda: L.nebem_lu_solve_device(ctx.h, dev.data_ptr(), big, piv.data_ptr(),
+                                                                 dev.data_ptr(), None),
+    }
+    for name, call in calls.items():
+        assert call() == N.NEBEM_TOO_LARGE, name
+        assert b"above 2^31 - 1" in L.nebem_last_error(), name
+    # the context is still usable
+    N.nebem_set_bc(ctx.h, [1.0])
+    ctx.solve(N.NEBEM_FP64)
+
 def test_fill_parity_double_thgem_full_size_sampled(N):
     """The 40,368-element double THGEM (25 images): sampled entries of the GPU-filled
     matrix against the oracle computed entry by entry (incl. diagonal/self terms)."""
