@@ -72,3 +72,50 @@ def test_bad_options_refused_before_any_device_call(lib, field, value):
         nebem.nebem_create(o)
     assert ei.value.code == nebem.NEBEM_INVALID_ARG
     assert lib.nebem_last_error() != b""
+
+
+def test_oracle_and_product_share_no_code():
+    """The oracle and the CUDA path are independent: no Python module of the package
+    imports oracle/, the oracle imports nothing of the package, and neither side's C/CUDA
+    sources include the other's headers.  Only the seeded input generators are shared
+    (by the tests and the bench, not by either implementation)."""
+    import ast
+    pkg = os.path.join(ROOT, "paper_2606_24154_gb300")
+    orc = os.path.join(ROOT, "oracle")
+
+    def py_imports(path):
+        names = set()
+        for node in ast.walk(ast.parse(open(path).read())):
+            if isinstance(node, ast.Import):
+                names |= {a.name for a in node.names}
+            elif isinstance(node, ast.ImportFrom):
+                names.add(("." * node.level) + (node.module or ""))
+        return names
+
+    for f in os.listdir(pkg):
+        if f.endswith(".py"):
+            assert not any(n.split(".")[0].lstrip(".") == "oracle" for n in py_imports(os.path.join(pkg, f))), f
+    for f in os.listdir(orc):
+        if f.endswith(".py"):
+            assert not any("paper_2606_24154_gb300" in n for n in py_imports(os.path.join(orc, f))), f
+    csrc = os.path.join(pkg, "csrc")
+    for f in os.listdir(csrc):
+        inc = re.findall(r'#include\s+"([^"]+)"', open(os.path.join(csrc, f)).read())
+        assert all("oracle" not in i for i in inc), (f, inc)
+    for f in os.listdir(orc):
+        if f.endswith((".c", ".h")):
+            inc = re.findall(r'#include\s+[<"]([^">]+)[">]', open(os.path.join(orc, f)).read())
+            assert all(i in {"math.h", "stdint.h", "stdlib.h", "string.h", "omp.h", "stdio.h"} for i in inc), (f, inc)
+
+
+def test_missing_library_fails_loudly():
+    """Without libnebem.so the binding raises: no call falls back to another code path."""
+    import subprocess
+    import sys
+    code = ("from paper_2606_24154_gb300 import nebem\n"
+            "try:\n"
+            "    nebem.load('/nonexistent/libnebem.so')\n"
+            "except RuntimeError as e:\n"
+            "    print('raised', 'not found' in str(e))\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert r.stdout.strip() == "raised True", r.stdout + r.stderr
