@@ -127,21 +127,29 @@ typedef struct nebem_solve_info {
 
 typedef struct nebem_ctx nebem_ctx;
 
-/* Fill *opt with the defaults listed above. */
+/* Fill *opt with the defaults listed above (a library utility: no counterpart in the
+ * paper).  Errors: NEBEM_INVALID_ARG (opt NULL). */
 int nebem_default_options(nebem_options *opt);
 
 /* Create a context on opt->device (opt may be NULL: defaults).  *out receives the
- * context; it owns all device memory it allocates and frees it in nebem_destroy.
+ * context; it owns all device memory it allocates and frees it in nebem_destroy.  The
+ * context holds one problem of Sec. 2 (geometry, voltages, charge densities, matrix and
+ * factors); it has no counterpart of its own in the paper.  The options are checked on
+ * the host before the device is touched.
  * Errors: NEBEM_INVALID_ARG (out NULL or bad option), NEBEM_NO_DEVICE, NEBEM_CUDA. */
 int nebem_create(nebem_ctx **out, const nebem_options *opt);
 
-/* Destroy a context and free its device memory.  NULL is accepted (no-op). */
+/* Destroy a context and free its device memory (waits for its stream first).  NULL is
+ * accepted (no-op).  Always returns NEBEM_OK.  A library utility with no counterpart in
+ * the paper. */
 int nebem_destroy(nebem_ctx *ctx);
 
-/* Message for the last failed call on this thread (static storage, never NULL). */
+/* Message for the last failed call on this thread (thread-local storage, valid until
+ * the thread's next failing call; never NULL, never fails).  A library utility. */
 const char *nebem_last_error(void);
 
-/* Name of a status code (static storage, never NULL). */
+/* Name of a status code (static storage; never NULL, never fails; unknown codes get a
+ * generic name).  A library utility. */
 const char *nebem_status_string(int status);
 
 /* Define the geometry (Sec. 2: discretised boundaries; Sec. 5 Case 2: periodic
@@ -162,7 +170,10 @@ int nebem_set_geometry(nebem_ctx *ctx, const nebem_element *el, int64_t n, const
 
 /* Conductor potentials (Sec. 2: Dirichlet boundary conditions; Sec. 2.1: K does not
  * depend on them, so the factors are kept).  voltages[n_conductors] is copied.  Every
- * conductor element's index must be < n_conductors.  Invalidates sigma only. */
+ * conductor element's index must be < n_conductors.  Invalidates sigma only.
+ * Errors: NEBEM_BAD_STATE (no geometry), NEBEM_INVALID_ARG (voltages NULL with
+ * n_conductors > 0, n_conductors < 0, a conductor index out of range, a non-finite
+ * voltage). */
 int nebem_set_bc(nebem_ctx *ctx, const double *voltages, int32_t n_conductors);
 
 /* Solve K sigma = b (Eq. Matrix; Alg. 1 with an LU solve instead of an explicit inverse).
@@ -183,22 +194,28 @@ int nebem_set_bc(nebem_ctx *ctx, const double *voltages, int32_t n_conductors);
  * NEBEM_NOT_CONVERGED (sigma and info are still written), NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
 int nebem_solve(nebem_ctx *ctx, int32_t precision, double *sigma_out, nebem_solve_info *info);
 
-/* Replace the charge densities (n values, host) without solving, e.g. to evaluate a
- * stored solution.  Errors: NEBEM_BAD_STATE (no geometry). */
+/* Replace the charge densities (sigma_j of Eq. Potential; n values, host, copied)
+ * without solving, e.g. to evaluate a stored solution.  Errors: NEBEM_BAD_STATE (no
+ * geometry), NEBEM_INVALID_ARG (NULL, or n not the element count), NEBEM_CUDA. */
 int nebem_set_sigma(nebem_ctx *ctx, const double *sigma, int64_t n);
 
-/* Copy the current charge densities (n values) to host memory.  NEBEM_BAD_STATE if none. */
+/* Copy the current charge densities (sigma of Eq. Matrix; n values) to host memory.
+ * Errors: NEBEM_BAD_STATE (none), NEBEM_INVALID_ARG (NULL, or n not the element count),
+ * NEBEM_CUDA. */
 int nebem_get_sigma(nebem_ctx *ctx, double *sigma_out, int64_t n);
 
-/* Fill the influence matrix (as nebem_solve does in this precision) and copy it to host
- * memory in column-major order, K_out[i + j*n] = K_ij.  K_out may be NULL (device copy
- * only).  A current FP64 matrix also answers a NEBEM_MIXED request. */
+/* Fill the influence matrix (Eq. Matrix; LHMatrix of Sec. 4.1), as nebem_solve does in
+ * this precision, and copy it to host memory in column-major order, K_out[i + j*n] =
+ * K_ij.  K_out may be NULL (device copy only).  A current FP64 matrix also answers a
+ * NEBEM_MIXED request.  Errors: NEBEM_INVALID_ARG (bad precision), NEBEM_BAD_STATE (no
+ * geometry), NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
 int nebem_fill(nebem_ctx *ctx, int32_t precision, double *K_out);
 
-/* Gather entries of the current influence matrix (filled on demand as nebem_fill does):
- * out[e] = K[rows[e], cols[e]] for e < count (host arrays; indices 0 <= r, c < n).  For
- * checks of matrices too large to copy whole.  Errors: NEBEM_BAD_STATE (no geometry),
- * NEBEM_INVALID_ARG (index out of range). */
+/* Gather entries of the current influence matrix (Eq. Matrix; filled on demand as
+ * nebem_fill does): out[e] = K[rows[e], cols[e]] for e < count (host arrays; indices
+ * 0 <= r, c < n).  For checks of matrices too large to copy whole.  Errors:
+ * NEBEM_BAD_STATE (no geometry), NEBEM_INVALID_ARG (NULL or index out of range),
+ * NEBEM_TOO_LARGE (count), NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
 int nebem_matrix_entries(nebem_ctx *ctx, const int64_t *rows, const int64_t *cols, int64_t count, double *out);
 
 /* Potential and field at points (Eq. Potential and Eq. Field with the element charge
@@ -210,16 +227,22 @@ int nebem_matrix_entries(nebem_ctx *ctx, const int64_t *rows, const int64_t *col
  * affected).  Errors: NEBEM_BAD_STATE (no charge densities), NEBEM_INVALID_ARG. */
 int nebem_eval(nebem_ctx *ctx, const double *pts, int64_t n, double *phi, double *E, int32_t precision);
 
-/* Device variant of nebem_eval: d_pts, d_phi, d_E are device pointers (d_phi or d_E may
- * be NULL); runs asynchronously on `stream` (a cudaStream_t, NULL = context stream).
- * Uses context-owned scratch, so calls on one context must not overlap in time. */
+/* Device variant of nebem_eval (same equations: Eq. Potential, Eq. Field): d_pts, d_phi, d_E are device pointers
+ * (d_phi or d_E may be NULL); runs asynchronously on `stream` (a cudaStream_t, NULL =
+ * context stream).  Uses context-owned scratch, so calls on one context must not overlap
+ * in time.  Errors: as nebem_eval, plus NEBEM_TOO_LARGE (n), NEBEM_OUT_OF_MEMORY
+ * (scratch) and NEBEM_CUDA (a launch failed); faults inside the kernels surface at the
+ * caller's next synchronisation. */
 int nebem_eval_device(nebem_ctx *ctx, const double *d_pts, int64_t n, double *d_phi, double *d_E,
                       int32_t precision, void *stream);
 
 /* Set the known-charge set (Sec. 4.2 OptKnCh; Alg. 4 UpdateSpaceCharge): n point
  * carriers at pos[n][3] (m) with charges q[n] (C), Plummer softening `softening` (m,
  * > 0; <= 0 selects the context default).  Copied to the device.  n = 0 clears it.
- * Invalidates sigma (the right-hand side changes), keeps the factors. */
+ * Invalidates sigma (the right-hand side changes), keeps the factors.  Errors:
+ * NEBEM_BAD_STATE (no geometry), NEBEM_INVALID_ARG (NULL buffers with n > 0, n < 0, a
+ * non-finite position or charge, index in nebem_last_error), NEBEM_TOO_LARGE (n),
+ * NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
 int nebem_space_charge(nebem_ctx *ctx, const double *pos, const double *q, int64_t n, double softening);
 
 /* Point -> line charge reduction (Sec. 4.2, Alg. 3) of the current point-charge set, which
@@ -244,7 +267,7 @@ int nebem_space_charge(nebem_ctx *ctx, const double *pos, const double *q, int64
  * that the near-line search, (3 dz/dx + 3)(3 dz/dy + 3) 5 voxels per target, exceeds 2e5). */
 int nebem_space_charge_lines(nebem_ctx *ctx, const double *voxel, int64_t *n_lines);
 
-/* Copy the current line charges to the host: start[L][3], stop[L][3] (m), lambda[L] (C/m),
+/* Copy the current line charges (Sec. 4.2, Alg. 3) to the host: start[L][3], stop[L][3] (m), lambda[L] (C/m),
  * each may be NULL.  *n_lines (may be NULL) receives L.  capacity = 0 only queries L;
  * 0 < capacity < L returns NEBEM_TOO_LARGE and writes nothing.
  * Errors: NEBEM_BAD_STATE when the known charges are point charges. */
@@ -278,7 +301,10 @@ int nebem_set_primitives(nebem_ctx *ctx, const nebem_element *prims, int32_t n_p
  * carrier count) and is excluded.  With line charges in use (nebem_space_charge_lines) the
  * sum runs over the lines instead, exclude_self must be 0, and mixed precision evaluates
  * lines farther than 3 half-lengths with FP32 Gauss-Legendre nodes along the line (2 to
- * 6 by distance), nearer ones in FP64.  Host buffers as in nebem_eval. */
+ * 6 by distance), nearer ones in FP64.  Host buffers as in nebem_eval.  Errors:
+ * NEBEM_BAD_STATE (no known-charge set), NEBEM_INVALID_ARG (bad precision, NULL points,
+ * exclude_self with n != carrier count or with lines), NEBEM_TOO_LARGE (n),
+ * NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
 int nebem_space_charge_eval(nebem_ctx *ctx, const double *pts, int64_t n, double *phi, double *E,
                             int32_t precision, int32_t exclude_self);
 
@@ -311,7 +337,7 @@ int nebem_step(nebem_ctx *ctx, int32_t steps, double mu, double dt, int32_t prec
  * NEBEM_INVALID_ARG, NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
 int nebem_lu_factor_device(nebem_ctx *ctx, double *d_A, int64_t n, int32_t *d_piv, void *stream);
 
-/* FP32 variant (the factorisation inside mixed solves): d_A is float, n x n column-major.
+/* FP32 variant (Sec. 4.1, Alg. 1; the factorisation inside mixed solves): d_A is float, n x n column-major.
  * The rank-64 trailing updates run on the tensor cores (tcgen05, TF32 with a hi/lo split
  * of both operands, FP32 accumulation; with n % 4 == 0 and d_A 16-byte aligned the
  * operands move by bulk copies and the products are added to the matrix by TMA
@@ -322,10 +348,13 @@ int nebem_lu_factor_device(nebem_ctx *ctx, double *d_A, int64_t n, int32_t *d_pi
  * NEBEM_TIMEOUT if a bounded wait (tensor-core update or panel barrier) gave up. */
 int nebem_lu_factor_device_f32(nebem_ctx *ctx, float *d_A, int64_t n, int32_t *d_piv, void *stream);
 
-/* Solve A x = b in place with factors from nebem_lu_factor_device: d_b (device, n) is
- * overwritten by x.  Asynchronous on `stream` (NULL = the context stream).  Each
- * triangular sweep is one launch over 64-row blocks that wait (bounded) for the blocks
- * before them; a wait that gives up writes NaN for its block instead of hanging. */
+/* Solve A x = b in place with factors from nebem_lu_factor_device (Sec. 4.1, Alg. 1:
+ * the solve with retained factors, P then L then U): d_b (device, n) is overwritten by
+ * x.  Asynchronous on `stream` (NULL = the context stream); its work space is
+ * stream-ordered.  Each triangular sweep is one launch over 64-row blocks that wait
+ * (bounded) for the blocks before them; a wait that gives up writes NaN for its block
+ * instead of hanging.  Errors: NEBEM_INVALID_ARG (NULL or n <= 0), NEBEM_TOO_LARGE (n),
+ * NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
 int nebem_lu_solve_device(nebem_ctx *ctx, const double *d_LU, int64_t n, const int32_t *d_piv, double *d_b,
                           void *stream);
 
@@ -364,31 +393,41 @@ int nebem_lu_factor_device_noalloc(double *d_A, int64_t n, int32_t *d_piv, void 
 int nebem_fastvol_build(nebem_ctx *ctx, const double *x_nodes, int32_t nx, const double *y_nodes, int32_t ny,
                         const double *z_nodes, int32_t nz, int32_t precision);
 
-/* Trilinear interpolation of the map at points (host buffers as in nebem_eval): the
- * eight nodes of the cell that holds the point, weights from its fractional position;
- * points outside the grid box take the value at the nearest point of the box; a point
- * with a NaN or infinite coordinate gets NaN. */
+/* Trilinear interpolation of the map at points (Sec. 3.3, the FastVolume lookup; host
+ * buffers as in nebem_eval): the eight nodes of the cell that holds the point, weights
+ * from its fractional position; points outside the grid box take the value at the
+ * nearest point of the box; a point with a NaN or infinite coordinate gets NaN.
+ * Errors: NEBEM_BAD_STATE (no map, or the charge densities changed since it was built),
+ * NEBEM_INVALID_ARG, NEBEM_TOO_LARGE (n), NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
 int nebem_fastvol_eval(nebem_ctx *ctx, const double *pts, int64_t n, double *phi, double *E);
 
-/* Device variant of nebem_fastvol_eval (asynchronous on `stream`, NULL = context stream). */
+/* Device variant of nebem_fastvol_eval (Sec. 3.3; asynchronous on `stream`, NULL = context
+ * stream; device pointers, d_phi or d_E may be NULL).  Errors as nebem_fastvol_eval. */
 int nebem_fastvol_eval_device(nebem_ctx *ctx, const double *d_pts, int64_t n, double *d_phi, double *d_E,
                               void *stream);
 
-/* Image translations of the current geometry in index order (count * 3 doubles,
- * host).  *count receives the number of images; t_out may be NULL to query it. */
+/* Image translations of the current geometry in index order (the virtual copies of
+ * Sec. 5 Case 2; count * 3 doubles, host).  *count receives the number of images; t_out
+ * may be NULL to query it.  Errors: NEBEM_INVALID_ARG (count NULL), NEBEM_BAD_STATE (no
+ * geometry). */
 int nebem_image_table(nebem_ctx *ctx, double *t_out, int64_t *count);
 
 /* Distance tier that the mixed evaluation assigns to every (point, element, image) pair,
  * for checks: codes[(p * n_el + j) * n_images + k] = 0 (FP32 4-node rule), 1 (6/9-node),
  * 2 (16-node), 3 (36-node) or 4 (FP64 closed form), decided in FP32 from two-float
  * coordinates against (ratio * element radius)^2 (the options' ratio_0, ratio_a, ratio_b,
- * ratio_near).  pts[n][3] and codes are host arrays; at most 2e8 pairs. */
+ * ratio_near).  pts[n][3] and codes are host arrays; at most 2e8 pairs.  A check of the
+ * mixed evaluation with no counterpart in the paper.  Errors: NEBEM_INVALID_ARG,
+ * NEBEM_BAD_STATE (no geometry), NEBEM_TOO_LARGE, NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
 int nebem_pair_tiers(nebem_ctx *ctx, const double *pts, int64_t n, uint8_t *codes);
 
-/* Influence of single elements (no charge density, no images) at points, for kernel
- * checks: for element e and point p, phi_out[e*n_pts + p] = Phi'(p) (m) and
+/* Influence of single elements (Sec. 2.1: the closed forms Phi' and E' of a uniformly
+ * charged flat element; no charge density, no images) at points, for kernel checks: for
+ * element e and point p, phi_out[e*n_pts + p] = Phi'(p) (m) and
  * E_out[(e*n_pts + p)*3 + c] = E'_c(p) (dimensionless), in FP64 closed form.
- * Host buffers; needs no geometry (a context provides the device).  At most 1e8 pairs. */
+ * Host buffers; needs no geometry (a context provides the device).  At most 1e8 pairs.
+ * Errors: NEBEM_INVALID_ARG (NULL or a size <= 0), NEBEM_DEGENERATE_ELEMENT (index in
+ * nebem_last_error), NEBEM_TOO_LARGE, NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
 int nebem_element_influence(nebem_ctx *ctx, const nebem_element *el, int64_t n_el, const double *pts,
                             int64_t n_pts, double *phi_out, double *E_out);
 
@@ -397,7 +436,9 @@ int nebem_element_influence(nebem_ctx *ctx, const nebem_element *el, int64_t n_e
  * Requests are admitted as device memory frees up, split into point chunks that a
  * persistent batched evaluation kernel pulls from a device work queue; requests that
  * arrive while others run join the running kernel.  Results are bit-identical to
- * the same request evaluated alone. */
+ * the same request evaluated alone.  The serving layer has no counterpart in the paper:
+ * each request is the evaluation of Eq. Potential and Eq. Field at its points (the
+ * element part of Sec. 4.1 PFAtPoint, with images). */
 typedef struct nebem_server nebem_server;
 
 typedef struct nebem_server_options {
@@ -409,6 +450,7 @@ typedef struct nebem_server_options {
     double reserved[4];
 } nebem_server_options;
 
+/* Fill *opt with the defaults listed above.  Errors: NEBEM_INVALID_ARG (opt NULL). */
 int nebem_server_default_options(nebem_server_options *opt);
 
 /* Create a server over n_ctx solved contexts (all on one device; they must stay alive
@@ -416,7 +458,9 @@ int nebem_server_default_options(nebem_server_options *opt);
  * evaluates the elements' field (with images) from the context's current charge
  * densities; a context with known charges (nebem_space_charge) or with Adaptive
  * Modelling on (nebem_set_primitives) is refused with NEBEM_BAD_STATE, here and at
- * submit, as is a context whose densities have been invalidated. */
+ * submit, as is a context whose densities have been invalidated.  Errors: NEBEM_INVALID_ARG
+ * (NULL or empty context list, bad options, contexts on different devices),
+ * NEBEM_BAD_STATE, NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
 int nebem_server_create(nebem_server **out, nebem_ctx *const *ctxs, int32_t n_ctx,
                         const nebem_server_options *opt);
 
@@ -429,18 +473,24 @@ int nebem_server_submit(nebem_server *srv, int32_t geometry, const double *pts, 
                         double *E, int32_t precision, int64_t *req_id);
 
 /* Drive the server (admission, launches, completions) and report whether req_id is
- * done (*done = 1; its outputs are written) or not (*done = 0). */
+ * done (*done = 1; its outputs are written) or not (*done = 0).  Errors:
+ * NEBEM_INVALID_ARG (NULL or unknown req_id), NEBEM_CUDA. */
 int nebem_server_poll(nebem_server *srv, int64_t req_id, int32_t *done);
 
-/* Drive the server until req_id completes or timeout_ms passes (NEBEM_TIMEOUT). */
+/* Drive the server until req_id completes or timeout_ms passes.  Errors:
+ * NEBEM_TIMEOUT (the request keeps running), NEBEM_INVALID_ARG (NULL or unknown req_id),
+ * NEBEM_CUDA. */
 int nebem_server_wait(nebem_server *srv, int64_t req_id, int64_t timeout_ms);
 
 /* Per-request timing (host clock, seconds since server creation): submit, admission,
- * completion.  NEBEM_BAD_STATE if not complete. */
+ * completion (each output may be NULL).  Errors: NEBEM_BAD_STATE (not complete),
+ * NEBEM_INVALID_ARG (NULL server or unknown req_id). */
 int nebem_server_request_times(nebem_server *srv, int64_t req_id, double *t_submit, double *t_admit,
                                double *t_done);
 
-/* Finish outstanding work and free the server (contexts are not destroyed). */
+/* Finish the admitted work and free the server (contexts are not destroyed); requests
+ * still waiting for admission are dropped, their outputs left unwritten.  NULL is
+ * accepted.  Always returns NEBEM_OK. */
 int nebem_server_destroy(nebem_server *srv);
 
 #ifdef __cplusplus
