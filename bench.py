@@ -268,6 +268,9 @@ def run_native(args):
             step()
             ev[k][1].record(stream)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     wall = time.perf_counter() - t0
     clocks = sampler.stop()
