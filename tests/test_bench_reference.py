@@ -1,6 +1,8 @@
-"""The reference arm of bench.py (the FP64 oracle timed on the host cores): one JSON
-line with the keys the benchmark line carries, on the same metric, unit and workload as
-the GPU arm; ranks other than 0 print nothing and exit 0.  CPU only."""
+"""Host logic of bench.py, CPU only: the reference arm (the FP64 oracle timed on the host
+cores) prints one JSON line with the keys the benchmark line carries, on the same metric,
+unit and workload as the GPU arm, and ranks other than 0 print nothing and exit 0; the
+clock sampler reduces nvidia-smi rows to the median SM clock and the throttle reasons
+seen."""
 import json
 import os
 import subprocess
@@ -38,3 +40,31 @@ def test_reference_line_contract():
 
 def test_reference_other_ranks_silent():
     assert _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}, "--steps", "1", "--warmup", "0") == []
+
+
+class _FakeProc:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_sampler_reduces_rows():
+    import bench
+    cs = bench.ClockSampler(0)
+    cs.proc = _FakeProc()
+    na, act = "Not Active", "Active"
+    cs.rows = [
+        ["0", "2070", "2070", "900.1", "0x0", na, na, na, na],
+        ["0", "2055", "2070", "1390.0", "0x4", na, na, na, act],
+        ["0", "2070", "2070", "1400.0", "0x4", na, na, na, act],
+        ["0", "[N/A]", "2070", "1.0", "0x0", na, na, na, na],
+    ]
+    out = cs.stop()
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 4
+    assert out["reasons"] == ["sw_power_cap"]
+    cs.rows.append(["0", "1500", "2070", "700.0", "0x48", act, na, act, na])
+    assert bench.ClockSampler.stop(cs)["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
+    none = bench.ClockSampler(0)
+    assert none.stop()["reasons"] == ["nvidia-smi unavailable"]
