@@ -1,0 +1,37 @@
+"""The work counts behind bench.py's roofline (paper_2606_24154_gb300/roofline.py), CPU
+only: the host-side tier counts agree with the oracle's own pair classification (up to
+pairs within FP32 rounding of a threshold), and the peaks are the unit counts times the
+clock."""
+import numpy as np
+
+from oracle import oracle as O
+from paper_2606_24154_gb300 import inputs as I
+from paper_2606_24154_gb300 import roofline as R
+
+
+def test_tier_counts_match_the_oracle_classification():
+    g = I.thgem(I.PlateSpec(n_phi=24, n_r=3, n_zc=1, n_zf=4), n_plane=3)
+    pts = I.cell_points(g, 48, I.rng(0, 70))
+    counts = R.tier_counts(g, pts, sample=48)
+    codes = O.pair_tiers(g, pts)
+    n_img = g.n_images
+    assert counts["pairs"] == codes.size == 48 * g.n * n_img
+    rect = np.repeat((g.elements["kind"] != I.KIND_TRI)[None, :, None], n_img, axis=2)
+    rect = np.broadcast_to(rect, codes.shape)
+    ref = {"t0": int((codes == 0).sum()), "a": int((codes == 1).sum()), "b": int((codes == 2).sum()),
+           "c": int((codes == 3).sum()), "near": int((codes == 4).sum())}
+    ref_nodes = int(4 * ref["t0"] + 9 * ((codes == 1) & rect).sum() + 6 * ((codes == 1) & ~rect).sum()
+                    + 16 * ref["b"] + 36 * ref["c"])
+    # FP64 distances (host count) against the FP32 decision (oracle): only pairs within a
+    # few ulps of a threshold may differ
+    for k in ref:
+        assert abs(counts[k] - ref[k]) <= max(2, 1e-4 * counts["pairs"]), (k, counts[k], ref[k])
+    assert abs(counts["nodes"] - ref_nodes) <= 1e-4 * ref_nodes
+    ops = R.fp32_ops_per_launch(counts, 2.0)
+    assert ops == 2.0 * (13 * counts["nodes"] + 12 * counts["pairs"])
+
+
+def test_peaks_from_unit_counts():
+    assert R.fp32_peak_ops(2070.0) == 152 * 128 * 2070e6
+    assert R.mufu_peak(2070.0) == 152 * 16 * 2070e6
+    assert R.fp64_peak_inst(2070.0) == 152 * 2 * 2070e6
