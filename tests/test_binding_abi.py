@@ -97,3 +97,29 @@ def test_struct_layouts_match_c(tmp_path):
     assert got[("nebem_element", "size")] == I.ELEMENT_DTYPE.itemsize
     for fname in I.ELEMENT_DTYPE.names:
         assert got[("nebem_element", fname)] == I.ELEMENT_DTYPE.fields[fname][1], fname
+
+
+def test_oracle_argtypes_match_its_c_definitions():
+    """The same check for the oracle's own ctypes table (test infrastructure): argument
+    count, scalar widths and pointee types of every exported function it declares."""
+    from oracle import oracle as O
+    src = open(os.path.join(ROOT, "oracle", "nebem_oracle.c")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    defs = {}
+    for m in re.finditer(r"^(int|void|int64_t|double)\s+(or_\w+)\(([^)]*)\)\s*\{", src, re.M | re.S):
+        params = " ".join(m.group(3).split())
+        defs[m.group(2)] = (m.group(1), [] if params in ("", "void") else [p.strip() for p in params.split(",")])
+    L = O.lib()
+    checked = 0
+    for name, (ret, params) in defs.items():
+        f = getattr(L, name, None)
+        if f is None or f.argtypes is None:
+            continue
+        assert len(f.argtypes) == len(params), (name, params, f.argtypes)
+        for i, (p, a) in enumerate(zip(params, f.argtypes)):
+            decl = re.sub(r"\b\w+\s*(\[\d*\])?$", lambda mm: "*" if mm.group(1) else "", p).strip()
+            _check_param(name, i, decl if decl else p, a)
+        if ret == "int64_t":
+            assert f.restype is C.c_int64, name
+        checked += 1
+    assert checked >= 19, checked  # every function the oracle gives argtypes
