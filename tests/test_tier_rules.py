@@ -96,7 +96,7 @@ def test_rule_truncation_at_the_tier_boundary(shape, tier):
         pts, wts = tri_rule(v[:3], tier)
         c = v[:3].mean(0)
     rho = np.linalg.norm(v[:4 if kind == "rect" else 3] - c, axis=1).max()
-    gen = np.random.default_rng(abs(hash((shape, tier))) % 2 ** 32)
+    gen = I.rng(0, 1000 + 10 * list(SHAPES).index(shape) + list(RATIOS).index(tier))
     u = gen.normal(size=(200, 3))
     u /= np.linalg.norm(u, axis=1, keepdims=True)
     P = c + RATIOS[tier] * rho * u
