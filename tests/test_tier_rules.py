@@ -105,3 +105,49 @@ def test_rule_truncation_at_the_tier_boundary(shape, tier):
     ephi = np.abs(qphi - phi) / np.abs(phi)
     eE = np.linalg.norm(qE - E, axis=1) / np.linalg.norm(E, axis=1)
     assert ephi.max() <= BOUND and eE.max() <= BOUND, (ephi.max(), eE.max())
+
+
+FILL_RATIOS = {"a": 96.0, "b": 32.0, "c": 6.0}
+FILL_BOUND = 1e-11  # per pair: the fill's entries must stay near 1e-11 for the FP64 refinement
+
+
+def _converged(kind, v):
+    """The defining integrals of Sec. 2.1 by a 24 x 24 Gauss product (collapsed on
+    triangles): converged to rounding at these distances, independent of the closed form."""
+    if kind == "rect":
+        return rect_rule(v[0], v[1] - v[0], v[3] - v[0], 24)
+    x, wx = gl01(24)
+    area = 0.5 * np.linalg.norm(np.cross(v[1] - v[0], v[2] - v[0]))
+    pts, w = [], []
+    for s, ws in zip(x, wx):
+        for t, wt in zip(x, wx):
+            tt = t * (1 - s)
+            pts.append((1 - s - tt) * v[0] + s * v[1] + tt * v[2])
+            w.append(2 * ws * wt * (1 - s) * area)
+    return np.array(pts), np.array(w)
+
+
+@pytest.mark.parametrize("shape", list(SHAPES))
+@pytest.mark.parametrize("tier", list(FILL_RATIOS))
+def test_fill_rule_truncation_at_the_tier_boundary(shape, tier):
+    """The mixed fill's tiers (96, 32, 6 rho: 3x3 / 6-point, 4x4 / collapsed 4x4, 6x6 /
+    collapsed 6x6) truncate by at most 1e-11 of the pair, against the converged integral."""
+    kind, v = SHAPES[shape]
+    if kind == "rect":
+        m = {"a": 3, "b": 4, "c": 6}[tier]
+        pts, wts = rect_rule(v[0], v[1] - v[0], v[3] - v[0], m)
+        c = v.mean(0)
+    else:
+        pts, wts = tri_rule(v[:3], {"a": "a", "b": "b", "c": "c"}[tier])
+        c = v[:3].mean(0)
+    rho = np.linalg.norm(v[:4 if kind == "rect" else 3] - c, axis=1).max()
+    gen = I.rng(0, 2000 + 10 * list(SHAPES).index(shape) + list(FILL_RATIOS).index(tier))
+    u = gen.normal(size=(200, 3))
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    P = c + FILL_RATIOS[tier] * rho * u
+    rpts, rw = _converged(kind, v)
+    phi, E = quad(rpts, rw, P)
+    qphi, qE = quad(pts, wts, P)
+    ephi = np.abs(qphi - phi) / np.abs(phi)
+    eE = np.linalg.norm(qE - E, axis=1) / np.linalg.norm(E, axis=1)
+    assert ephi.max() <= FILL_BOUND and eE.max() <= FILL_BOUND, (ephi.max(), eE.max())
