@@ -110,7 +110,10 @@ typedef struct nebem_options {
                                 difference from exact two-float coordinates (default 1e-4) */
     int32_t lu_block;        /* LU panel width, 32 or 64 (default 64) */
     int32_t reserved0;
-    double reserved[4];
+    double mixed_point_tol;  /* mixed eval: a point whose estimated error exceeds this fraction
+                                of its |phi| or |E| is evaluated again in two-float arithmetic
+                                (see nebem_eval_err); 0 keeps the single FP32 pass (default 1e-6) */
+    double reserved[3];
 } nebem_options;
 
 /* Result report of nebem_solve. */
@@ -224,7 +227,10 @@ int nebem_matrix_entries(nebem_ctx *ctx, const int64_t *rows, const int64_t *col
  * known-charge set is present], E likewise.  pts[n][3] row-major (host);
  * phi[n] and/or E[n][3] (host) may be NULL.  n = 0 is allowed.  A point with a NaN or
  * infinite coordinate gets NaN phi and E (both precisions; the other points are not
- * affected).  Errors: NEBEM_BAD_STATE (no charge densities), NEBEM_INVALID_ARG. */
+ * affected).  precision NEBEM_FP64: closed forms for every pair.  NEBEM_MIXED: FP32 Gauss
+ * rules for far pairs and FP64 closed forms for near ones, then a two-float re-evaluation of
+ * every point whose estimated error exceeds mixed_point_tol of its |phi| or |E| (see
+ * nebem_eval_err).  Errors: NEBEM_BAD_STATE (no charge densities), NEBEM_INVALID_ARG. */
 int nebem_eval(nebem_ctx *ctx, const double *pts, int64_t n, double *phi, double *E, int32_t precision);
 
 /* Device variant of nebem_eval (same equations: Eq. Potential, Eq. Field): d_pts, d_phi, d_E are device pointers
@@ -235,6 +241,33 @@ int nebem_eval(nebem_ctx *ctx, const double *pts, int64_t n, double *phi, double
  * caller's next synchronisation. */
 int nebem_eval_device(nebem_ctx *ctx, const double *d_pts, int64_t n, double *d_phi, double *d_E,
                       int32_t precision, void *stream);
+
+/* Mixed-precision evaluation (Sec. 2, Eq. Potential / Eq. Field: the same sums as
+ * nebem_eval with precision NEBEM_MIXED) with an error estimate for every result.  The FP32
+ * pass keeps, per point, the scale of its rounding and truncation errors: B_phi =
+ * ke sum_j |sigma_j| |sum_k Phi'_jk| and B_E = ke sum_j |sigma_j| |sum_k E'_jk|_1 over its
+ * FP32 (element, image) pairs.  Its estimated absolute errors are 1.5e-7 B_phi (V) and
+ * 1.5e-7 B_E (of |E|, V/m): the factor is 1.6 times or more the largest error-to-scale
+ * ratio measured against the FP64 path (a statistical estimate, not a bound).  A point
+ * whose estimate exceeds mixed_point_tol times its
+ * |phi| or |E| (context option, default 1e-6) is evaluated again in two-float arithmetic
+ * (Gauss rules truncated below ~3e-12 of each pair, FP64 closed forms within 6 element
+ * radii); its estimate becomes 1e-11 B.  nebem_eval / nebem_eval_device with NEBEM_MIXED
+ * apply the same refinement; these calls also return the estimates.
+ *   pts / d_pts  n x 3 points (host memory, copied / device memory).
+ *   phi, E       outputs as in nebem_eval (either may be NULL; a NULL output is not used
+ *                to decide the refinement).
+ *   err / d_err  n x 2 output: estimated absolute error of phi and of |E| per point; may be
+ *                NULL (then nothing is written).
+ *   n_refined    (host variant, may be NULL) number of points evaluated again.
+ *   stream       as in nebem_eval_device (asynchronous, device pointers).
+ * Known charges (nebem_space_charge) are added after the refinement, in their own
+ * precision; their sum is not part of the estimate.  Not available with Adaptive
+ * Modelling (NEBEM_BAD_STATE).  Errors as nebem_eval. */
+int nebem_eval_err(nebem_ctx *ctx, const double *pts, int64_t n, double *phi, double *E, double *err,
+                   int64_t *n_refined);
+int nebem_eval_device_err(nebem_ctx *ctx, const double *d_pts, int64_t n, double *d_phi, double *d_E, double *d_err,
+                          void *stream);
 
 /* Set the known-charge set (Sec. 4.2 OptKnCh; Alg. 4 UpdateSpaceCharge): n point
  * carriers at pos[n][3] (m) with charges q[n] (C), Plummer softening `softening` (m,
@@ -369,8 +402,10 @@ int nebem_lu_solve_device(nebem_ctx *ctx, const double *d_LU, int64_t n, const i
  *               call synchronises it before returning.
  * Needs no context: it runs on the calling thread's current device.  Its work space is a
  * fixed static device array of the library (about 2.1 MB, held on every GPU that loads
- * the library until the process exits); the first call on a device looks up that array's
- * device address and caches it.  All calls on a device share the array, so calls whose
+ * the library until the process exits); every call looks up that array's device address
+ * in the context current on the calling thread (no cached address, so a cudaDeviceReset
+ * or a caller-made non-primary context is followed correctly; the first call in a context
+ * loads the library's device code there).  All calls on a device share the array, so calls whose
  * GPU work overlaps in time race on it: serialise them.  No memory is allocated by the
  * call (it issues only kernel launches, a memset and one small device-to-host copy).
  * Errors: NEBEM_INVALID_ARG, NEBEM_TOO_LARGE, NEBEM_SINGULAR, NEBEM_CUDA. */

@@ -106,6 +106,7 @@ int nebem_default_options(nebem_options* opt) {
     opt->softening = 1e-6;
     opt->sc_near = 1e-4;
     opt->lu_block = 64;
+    opt->mixed_point_tol = 1e-6;
     return NEBEM_OK;
 }
 
@@ -121,6 +122,8 @@ int nebem_create(nebem_ctx** out, const nebem_options* opt) {
         !(o.ratio_0 >= o.ratio_a) || !(o.ratio_0 < 1e6))
         return fail(NEBEM_INVALID_ARG, "need 1.5 <= ratio_near <= ratio_b <= ratio_a <= ratio_0");
     if (!(o.softening > 0.0)) return fail(NEBEM_INVALID_ARG, "softening must be > 0");
+    if (!(o.mixed_point_tol >= 0.0) || !(o.mixed_point_tol < 1.0))
+        return fail(NEBEM_INVALID_ARG, "mixed_point_tol must be in [0, 1)");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();
@@ -368,6 +371,50 @@ int nebem_eval(nebem_ctx* ctx, const double* pts, int64_t n, double* phi, double
     if (phi) CK(cudaMemcpyAsync(phi, c->d_phi.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
     if (E) CK(cudaMemcpyAsync(E, c->d_E.ptr, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    return NEBEM_OK;
+}
+
+int nebem_eval_device_err(nebem_ctx* ctx, const double* d_pts, int64_t n, double* d_phi, double* d_E, double* d_err,
+                          void* stream) {
+    if (!ctx) return fail(NEBEM_INVALID_ARG, "ctx is NULL");
+    if (n < 0 || (n > 0 && !d_pts)) return fail(NEBEM_INVALID_ARG, "bad points");
+    if (int rc = check_count(n, "point count")) return rc;
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (!c->sigma_valid) return fail(NEBEM_BAD_STATE, "no charge densities (solve or set_sigma first)");
+    if (c->am_on) return fail(NEBEM_BAD_STATE, "error estimates are not made with Adaptive Modelling");
+    if (n == 0) return NEBEM_OK;
+    CK(cudaSetDevice(c->device));
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    return eval_points(c, d_pts, n, d_phi, d_E, NEBEM_MIXED, s, d_err);
+}
+
+int nebem_eval_err(nebem_ctx* ctx, const double* pts, int64_t n, double* phi, double* E, double* err,
+                   int64_t* n_refined) {
+    if (!ctx) return fail(NEBEM_INVALID_ARG, "ctx is NULL");
+    if (n < 0 || (n > 0 && !pts)) return fail(NEBEM_INVALID_ARG, "bad points");
+    if (int rc = check_count(n, "point count")) return rc;
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (!c->sigma_valid) return fail(NEBEM_BAD_STATE, "no charge densities (solve or set_sigma first)");
+    if (c->am_on) return fail(NEBEM_BAD_STATE, "error estimates are not made with Adaptive Modelling");
+    if (n_refined) *n_refined = 0;
+    if (n == 0) return NEBEM_OK;
+    CK(cudaSetDevice(c->device));
+    CK(c->d_pts.ensure(sizeof(double) * 3 * n));
+    CK(c->d_phi.ensure(sizeof(double) * n));
+    CK(c->d_E.ensure(sizeof(double) * 3 * n));
+    CK(c->d_err.ensure(sizeof(double) * 2 * n));
+    CK(cudaMemcpyAsync(c->d_pts.ptr, pts, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, c->stream));
+    c->refine_list = nullptr;
+    int rc = eval_points(c, (const double*)c->d_pts.ptr, n, phi ? (double*)c->d_phi.ptr : nullptr,
+                         E ? (double*)c->d_E.ptr : nullptr, NEBEM_MIXED, c->stream, (double*)c->d_err.ptr);
+    if (rc) return rc;
+    int32_t h_ref = 0;
+    if (c->refine_list) CK(cudaMemcpyAsync(&h_ref, c->refine_list, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    if (phi) CK(cudaMemcpyAsync(phi, c->d_phi.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    if (E) CK(cudaMemcpyAsync(E, c->d_E.ptr, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
+    if (err) CK(cudaMemcpyAsync(err, c->d_err.ptr, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (n_refined) *n_refined = h_ref;
     return NEBEM_OK;
 }
 

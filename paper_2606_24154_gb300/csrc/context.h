@@ -92,8 +92,10 @@ struct Ctx {
     bool K_valid = false, fac64_valid = false, fac32_valid = false;
     DevBuf d_b, d_x, d_r, d_r32, d_small;
 
-    // evaluation staging (host-pointer variant) and scratch
-    DevBuf d_pts, d_phi, d_E, d_scratch;
+    // evaluation staging (host-pointer variant) and scratch; refine_list = device count of
+    // the points the last refined mixed evaluation re-evaluated (inside d_scratch)
+    DevBuf d_pts, d_phi, d_E, d_err, d_scratch;
+    const int32_t* refine_list = nullptr;
 
     // known-charge set (space charge)
     int64_t n_car = 0;
@@ -120,15 +122,20 @@ int ensure_fill(Ctx* c, int precision, double* ms);
 int ensure_factors(Ctx* c, int precision, double* ms);
 int build_rhs(Ctx* c);
 int solve_with_factors(Ctx* c, int precision, nebem_solve_info* info);
-// elements only (with images)
-int eval_elements(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision, cudaStream_t s);
+// two-float tables of the mixed fill and of the refined evaluation (built on first use)
+int ensure_fill_tables(Ctx* c);
+// elements only (with images); err (may be NULL, n x 2): per-point error estimates of a
+// mixed evaluation (see eval_acc.cu)
+int eval_elements(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision, cudaStream_t s,
+                  double* err = nullptr);
 // one evaluation set (elements or primitives with their images)
 int eval_set(Ctx* c, const EvalSet& es, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision,
              cudaStream_t s);
 // am_api.cpp: the adaptive evaluation (near copies by elements, distant ones by primitives)
 int eval_adaptive(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision, cudaStream_t s);
 // elements + known charges (PFAtPoint)
-int eval_points(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision, cudaStream_t s);
+int eval_points(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision, cudaStream_t s,
+                double* err = nullptr);
 
 // spacecharge_api.cpp
 int rhs_known_charge(Ctx* c);

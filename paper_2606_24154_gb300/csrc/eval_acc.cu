@@ -1,0 +1,388 @@
+// eval_acc.cu -- refinement of the mixed-precision evaluation (Eq. Potential / Eq. Field
+// over elements and periodic images): per-point error estimates of the FP32 pass, and a
+// two-float re-evaluation of the points whose estimate exceeds the requested tolerance.
+//
+// Error estimate.  The FP32 pass (eval_blocks.cuh) leaves per point the scales
+// B_phi = ke sum_j |sigma_j| |sum_k Phi'_jk| and B_E = ke sum_j |sigma_j| |sum_k E'_jk|_1
+// of its FP32 pairs.  Its error comes from rounding the point-to-centroid difference and
+// the node arithmetic to FP32 (about u = 2^-24 relative per operation), the FP32 charge
+// densities and node weights, and the truncation of the Gauss rules; none of these grows
+// with the result, so a point whose |phi| (|E|) is small next to B_phi (B_E) -- a
+// potential near zero inside the plate, the weak field inside a conductor -- loses its
+// relative accuracy there.  The estimate is gamma * B with gamma = 1.5e-7 for both.
+// Measured against the FP64 path, the largest error-to-scale ratios were 3.2e-8 (phi) and
+// 5.9e-8 (E) over 40,000 points of the THGEM cell, and 8.2e-8 (phi) and 9.2e-8 (E) on the
+// cube's 10,000-point grid; the factor leaves a margin of 1.6x or more over all of them.
+// The estimate is statistical, not a bound: rounding errors of many pairs add up like a
+// random sum whose ratio to B spreads about fivefold between its median and its maximum.
+//
+// Refinement.  A point is re-evaluated when gamma B_phi > tol |phi| or gamma B_E > tol |E|.
+// The re-evaluation uses the arithmetic of the mixed fill (fill_mixed.cu): Gauss rules
+// whose truncation stays below ~3e-12 of the pair (tiers kFillRatioA / B / C) in two-float
+// arithmetic (about 44 bits) for pairs at >= kFillRatioC element radii, and the FP64
+// closed form (influence.cuh) for nearer pairs.  Its estimate is 1e-11 B.  In the frame of
+// element j (axes ex, ey = normal, ez), a pair (point, image k) has D = P - c_j - t_k with
+// local components X = (P - c_j) . ex - tau_k.x (likewise Y, Z; tau tabulated per element
+// and image); a node at offset s = centroid - node (in the element plane) sees the point at
+// D + s, so r^2 = |D|^2 + 2 (X s_x + Z s_z) + |s|^2 and
+//   Phi' = sum w / r,   E'_local = D sum w / r^3 + (sum w s_x / r^3, 0, sum w s_z / r^3).
+// Per element the image sums are rotated to the global frame and weighted by sigma_j in
+// FP64.  Every flagged point's arithmetic depends on that point only, so its result does
+// not depend on which other points are flagged or share the launch.
+#include "twofloat.cuh"
+
+namespace nb {
+
+namespace {
+
+constexpr int kAT = 128;             // threads (flagged points) per block
+constexpr double kGammaPhi = 1.5e-7; // FP32 pass: error of phi <= kGammaPhi * B_phi
+constexpr double kGammaE = 1.5e-7;   // FP32 pass: error of |E| <= kGammaE * B_E
+constexpr double kGammaAcc = 1e-11;  // two-float pass with fill-grade rules
+
+// Per-pair node sums S0 = sum w / r^3, S2x = sum w (2 s_x) / r^3, S2z = sum w (2 s_z) / r^3
+// as packed two-float values (hi, negated lo) over the two lanes of the node pairs.
+struct PairSums2 {
+    float2 s0, ns0, sx, nsx, sz, nsz;
+};
+
+// Phi' (per element, accumulated over its images: ph, nph) and the pair sums of one tier's
+// node pairs.  Node records as in nb_internal.h (kFillNodeRec layout): q0 = (2 s_x, 2 s_z)
+// hi, q1 = (|s|^2, w) hi, q2 / q3 the lo parts.
+__device__ __forceinline__ void nodes_acc2(const float4* __restrict__ nd, int pairs, const PairDF2& P, float2& ph,
+                                           float2& nph, PairSums2& S) {
+    const float2 m1 = bc2(-1.f);
+    for (int q = 0; q < pairs; ++q) {
+        const float4 q0 = nd[4 * q], q1 = nd[4 * q + 1], q2 = nd[4 * q + 2], q3 = nd[4 * q + 3];
+        float2 y0, ny0, nyl, a, na, nae;
+        node_rinv2(P, q0, q1, q2, q3, y0, ny0, nyl, a, na, nae);
+        const float2 w = make_float2(q1.z, q1.w), wl = make_float2(q3.z, q3.w);
+        float2 t;
+        // w / r = m - nme
+        const float2 m = __fmul2_rn(w, y0);
+        float2 nme = __ffma2_rn(w, ny0, m);
+        nme = __ffma2_rn(w, nyl, nme);
+        nme = __ffma2_rn(wl, ny0, nme);
+        two_sum2(ph, m, ph, t);
+        nph = __ffma2_rn(t, m1, __fadd2_rn(nph, nme));
+        // y^3 = c3 - nc3e (y^2 = a - ny2l)
+        const float2 ny2l = __ffma2_rn(__fadd2_rn(y0, y0), nyl, nae);
+        const float2 c3 = __fmul2_rn(a, y0);
+        float2 nc3e = __ffma2_rn(na, y0, c3);
+        nc3e = __ffma2_rn(a, nyl, nc3e);
+        nc3e = __ffma2_rn(ny2l, y0, nc3e);
+        const float2 nc3 = __fmul2_rn(c3, m1);
+        // w y^3 = m3 - nm3e
+        const float2 m3 = __fmul2_rn(w, c3);
+        float2 nm3e = __ffma2_rn(w, nc3, m3);
+        nm3e = __ffma2_rn(w, nc3e, nm3e);
+        nm3e = __ffma2_rn(wl, nc3, nm3e);
+        two_sum2(S.s0, m3, S.s0, t);
+        S.ns0 = __ffma2_rn(t, m1, __fadd2_rn(S.ns0, nm3e));
+        // (w y^3) (2 s_x), (w y^3) (2 s_z)
+        const float2 nm3 = __fmul2_rn(m3, m1);
+        const float2 sx = make_float2(q0.x, q0.y), sz = make_float2(q0.z, q0.w);
+        const float2 sxl = make_float2(q2.x, q2.y), szl = make_float2(q2.z, q2.w);
+        const float2 fx = __fmul2_rn(m3, sx);
+        float2 nfx = __ffma2_rn(nm3, sx, fx);
+        nfx = __ffma2_rn(nm3, sxl, nfx);
+        nfx = __ffma2_rn(nm3e, sx, nfx);
+        two_sum2(S.sx, fx, S.sx, t);
+        S.nsx = __ffma2_rn(t, m1, __fadd2_rn(S.nsx, nfx));
+        const float2 fz = __fmul2_rn(m3, sz);
+        float2 nfz = __ffma2_rn(nm3, sz, fz);
+        nfz = __ffma2_rn(nm3, szl, nfz);
+        nfz = __ffma2_rn(nm3e, sz, nfz);
+        two_sum2(S.sz, fz, S.sz, t);
+        S.nsz = __ffma2_rn(t, m1, __fadd2_rn(S.nsz, nfz));
+    }
+}
+
+// the two lanes of a packed (hi, negated lo) sum as one two-float value, times `scale`
+// (a power of two, exact)
+__device__ __forceinline__ void lanes_to_df(float2 h, float2 nl, float scale, float& oh, float& ol) {
+    float t;
+    two_sum(h.x, h.y, oh, t);
+    ol = __fsub_rn(__fsub_rn(t, nl.x), nl.y);
+    oh = __fmul_rn(oh, scale);
+    ol = __fmul_rn(ol, scale);
+}
+
+// (Sh, Sl) += (ah + al) (bh + bl) + (ch + cl)
+__device__ __forceinline__ void df_fma_acc(float ah, float al, float bh, float bl, float ch, float cl, float& Sh,
+                                           float& Sl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    float h, t, t2;
+    two_sum(p, ch, h, t);
+    const float l = __fadd_rn(e, __fadd_rn(t, cl));
+    two_sum(Sh, h, Sh, t2);
+    Sl = __fadd_rn(Sl, __fadd_rn(t2, l));
+}
+
+// dynamic shared memory per tile of te elements: FillEl (9 float4), tier-a nodes, tau and
+// image centroids (2 float4 each per image)
+__host__ __device__ constexpr int acc_tile_f4(int te, int nimg) { return te * (9 + 4 * kFillPairsA + 4 * nimg); }
+
+// Raw sums (before ke) of the far pairs (>= kFillRatioC radii) of one point over the
+// elements [e0, e1), with the error scales; all threads of the block take part (tiles).
+__device__ __forceinline__ Sum6 acc_range(const AccView& A, int nimg, int te, float4* sm, const float (&ph)[3],
+                                          const float (&pl)[3], int64_t e0, int64_t e1) {
+    FillEl* s_fe = reinterpret_cast<FillEl*>(sm);
+    float4* s_na = sm + 9 * te;
+    float4* s_tau = s_na + 4 * kFillPairsA * te;
+    float4* s_c = s_tau + 2 * nimg * te;
+    Sum6 acc{0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int64_t base = e0; base < e1; base += te) {
+        const int cnt = (int)min((int64_t)te, e1 - base);
+        __syncthreads();
+        {
+            const float4* src = reinterpret_cast<const float4*>(A.fe + base);
+            float4* dst = reinterpret_cast<float4*>(s_fe);
+            for (int i = threadIdx.x; i < 9 * cnt; i += blockDim.x) dst[i] = src[i];
+        }
+        for (int e = threadIdx.x; e < cnt * 4 * kFillPairsA; e += blockDim.x) {
+            const int jj = e / (4 * kFillPairsA), q = e - jj * 4 * kFillPairsA;
+            s_na[e] = A.nodes[(base + jj) * kFillNodeRec + q];
+        }
+        for (int i = threadIdx.x; i < 2 * cnt * nimg; i += blockDim.x) {
+            s_tau[i] = A.tau[2 * base * nimg + i];
+            s_c[i] = A.cjk[2 * base * nimg + i];
+        }
+        __syncthreads();
+        for (int jj = 0; jj < cnt; ++jj) {
+            const FillEl& F = s_fe[jj];
+            const int64_t j = base + jj;
+            const float4 hdr = F.hdr;
+            const int na = (int)hdr.w;
+            float dh[3], dl[3];
+            df_sub(ph[0], pl[0], F.ch.x, F.cl.x, dh[0], dl[0]);
+            df_sub(ph[1], pl[1], F.ch.y, F.cl.y, dh[1], dl[1]);
+            df_sub(ph[2], pl[2], F.ch.z, F.cl.z, dh[2], dl[2]);
+            float x0h, x0l, y0h, y0l, z0h, z0l;
+            df_dot3(dh, dl, F.exh, F.exl, x0h, x0l);
+            df_dot3(dh, dl, F.eyh, F.eyl, y0h, y0l);
+            df_dot3(dh, dl, F.ezh, F.ezl, z0h, z0l);
+            float2 fph = bc2(0.f), fnph = bc2(0.f);
+            float exh = 0.f, exl = 0.f, eyh = 0.f, eyl = 0.f, ezh = 0.f, ezl = 0.f;
+            for (int k = 0; k < nimg; ++k) {
+                float dx, dy, dz;
+                const float d2 = pair_d2(ph[0], ph[1], ph[2], pl[0], pl[1], pl[2], s_c[2 * (jj * nimg + k)],
+                                         s_c[2 * (jj * nimg + k) + 1], dx, dy, dz);
+                if (!(d2 >= hdr.z)) continue;  // near pair: k_eval_acc_near
+                const float4 th = s_tau[2 * (jj * nimg + k)], tl = s_tau[2 * (jj * nimg + k) + 1];
+                float xh, xl, yh, yl, zh, zl, d2h, d2l;
+                df_sub(x0h, x0l, th.x, tl.x, xh, xl);
+                df_sub(y0h, y0l, th.y, tl.y, yh, yl);
+                df_sub(z0h, z0l, th.z, tl.z, zh, zl);
+                df_norm2(xh, xl, yh, yl, zh, zl, d2h, d2l);
+                PairDF2 P;
+                P.xh = bc2(xh), P.nxh = bc2(-xh), P.xl = bc2(xl);
+                P.zh = bc2(zh), P.nzh = bc2(-zh), P.zl = bc2(zl);
+                P.d2h = bc2(d2h), P.d2l = bc2(d2l);
+                const float4* nd;
+                int np;
+                if (d2 >= hdr.x) {
+                    nd = s_na + jj * 4 * kFillPairsA;
+                    np = na;
+                } else if (d2 >= hdr.y) {
+                    nd = A.nodes + j * kFillNodeRec + kFillOffB;
+                    np = kFillPairsB;
+                } else {
+                    nd = A.nodes + j * kFillNodeRec + kFillOffC;
+                    np = kFillPairsC;
+                }
+                PairSums2 S{bc2(0.f), bc2(0.f), bc2(0.f), bc2(0.f), bc2(0.f), bc2(0.f)};
+                nodes_acc2(nd, np, P, fph, fnph, S);
+                float s0h, s0l, sxh, sxl, szh, szl;
+                lanes_to_df(S.s0, S.ns0, 1.f, s0h, s0l);
+                lanes_to_df(S.sx, S.nsx, 0.5f, sxh, sxl);
+                lanes_to_df(S.sz, S.nsz, 0.5f, szh, szl);
+                df_fma_acc(xh, xl, s0h, s0l, sxh, sxl, exh, exl);
+                df_fma_acc(yh, yl, s0h, s0l, 0.f, 0.f, eyh, eyl);
+                df_fma_acc(zh, zl, s0h, s0l, szh, szl, ezh, ezl);
+            }
+            // element j: image sums in FP64, rotated to the global frame, weighted by sigma_j
+            const double fphi = ((double)fph.x - (double)fnph.x) + ((double)fph.y - (double)fnph.y);
+            const double lx = (double)exh + (double)exl, ly = (double)eyh + (double)eyl, lz = (double)ezh + (double)ezl;
+            const Elem& e = A.el[j];
+            const double gx = fma(lx, e.ex[0], fma(ly, e.ey[0], lz * e.ez[0]));
+            const double gy = fma(lx, e.ex[1], fma(ly, e.ey[1], lz * e.ez[1]));
+            const double gz = fma(lx, e.ex[2], fma(ly, e.ey[2], lz * e.ez[2]));
+            const double s = A.sigma[j];
+            acc.phi = fma(s, fphi, acc.phi);
+            acc.x = fma(s, gx, acc.x);
+            acc.y = fma(s, gy, acc.y);
+            acc.z = fma(s, gz, acc.z);
+            acc.bphi = fma(fabs(s), fabs(fphi), acc.bphi);
+            acc.bE = fma(fabs(s), fabs(gx) + fabs(gy) + fabs(gz), acc.bE);
+        }
+    }
+    return acc;
+}
+
+// Far part of every listed point (thread per point, blocks striding over the list of
+// *n_list points): writes ke * sum to phi / E and the refined estimate to err.
+__global__ void __launch_bounds__(kAT, 3)
+    k_eval_acc_far(const AccView A, int nimg, int te, const double* __restrict__ pts,
+                   const int32_t* __restrict__ list, const int32_t* __restrict__ n_list, double* __restrict__ phi,
+                   double* __restrict__ E, double* __restrict__ err) {
+    extern __shared__ float4 sm[];
+    const int64_t count = *n_list;
+    const double ke = 1.0 / (4.0 * kPi * kEps0);
+    for (int64_t base = (int64_t)blockIdx.x * kAT; base < count; base += (int64_t)gridDim.x * kAT) {
+        const bool active = base + threadIdx.x < count;
+        const int64_t p = active ? (int64_t)list[base + threadIdx.x] : 0;
+        float ph[3], pl[3];
+        load_point_2f(pts, p, active, ph[0], ph[1], ph[2], pl[0], pl[1], pl[2]);
+        Sum6 tot{0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int64_t e0 = 0; e0 < A.n_el; e0 += kChunkEl)
+            add6(tot, acc_range(A, nimg, te, sm, ph, pl, e0, min(e0 + (int64_t)kChunkEl, A.n_el)));
+        if (active) {
+            if (phi) phi[p] = ke * tot.phi;
+            if (E) {
+                E[3 * p] = ke * tot.x;
+                E[3 * p + 1] = ke * tot.y;
+                E[3 * p + 2] = ke * tot.z;
+            }
+            if (err) {
+                err[2 * p] = kGammaAcc * ke * tot.bphi;
+                err[2 * p + 1] = kGammaAcc * ke * tot.bE;
+            }
+        }
+    }
+}
+
+// Near part (FP64 closed forms of the pairs nearer than kFillRatioC radii, found through
+// the fill's cell list) of every listed point; adds ke * sum to phi / E.
+__global__ void __launch_bounds__(128)
+    k_eval_acc_near(const AccView A, const ImageTable img, const double* __restrict__ pts,
+                    const int32_t* __restrict__ list, const int32_t* __restrict__ n_list, double* __restrict__ phi,
+                    double* __restrict__ E) {
+    const int64_t count = *n_list;
+    const int nimg = img.n;
+    const double ke = 1.0 / (4.0 * kPi * kEps0);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = list[i];
+        const double Px = pts[3 * p], Py = pts[3 * p + 1], Pz = pts[3 * p + 2];
+        float phx, phy, phz, plx, ply, plz;
+        split2f(Px, phx, plx);
+        split2f(Py, phy, ply);
+        split2f(Pz, phz, plz);
+        const NearGrid& grid = A.grid;
+        int cc[3];
+        const double P[3] = {Px, Py, Pz};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            double f = floor((P[a] - grid.origin[a]) * grid.inv_h);
+            f = fmin(fmax(f, -2.0), (double)grid.dims[a] + 1.0);
+            cc[a] = (int)f;
+        }
+        double aphi = 0.0, aEx = 0.0, aEy = 0.0, aEz = 0.0;
+        for (int z = max(cc[2] - 1, 0); z <= min(cc[2] + 1, grid.dims[2] - 1); ++z)
+            for (int y = max(cc[1] - 1, 0); y <= min(cc[1] + 1, grid.dims[1] - 1); ++y)
+                for (int x = max(cc[0] - 1, 0); x <= min(cc[0] + 1, grid.dims[0] - 1); ++x) {
+                    const int64_t cell = ((int64_t)z * grid.dims[1] + y) * grid.dims[0] + x;
+                    for (int32_t it = A.cell_start[cell]; it < A.cell_start[cell + 1]; ++it) {
+                        const int32_t jk = A.cell_items[it];
+                        const int32_t j = jk / nimg, k = jk - j * nimg;
+                        float dx, dy, dz;
+                        const float d2 = pair_d2(phx, phy, phz, plx, ply, plz, A.cjk[2 * (int64_t)jk],
+                                                 A.cjk[2 * (int64_t)jk + 1], dx, dy, dz);
+                        if (!(d2 < A.fe[j].hdr.z)) continue;  // far pair: k_eval_acc_far
+                        const Elem& e = A.el[j];
+                        double f, ux, uy, uz;
+                        elem_local_f64(e, Px - img.t[k][0], Py - img.t[k][1], Pz - img.t[k][2], false, f, ux, uy, uz);
+                        const double s = A.sigma[j];
+                        aphi = fma(s, f, aphi);
+                        aEx = fma(s, fma(ux, e.ex[0], fma(uy, e.ey[0], uz * e.ez[0])), aEx);
+                        aEy = fma(s, fma(ux, e.ex[1], fma(uy, e.ey[1], uz * e.ez[1])), aEy);
+                        aEz = fma(s, fma(ux, e.ex[2], fma(uy, e.ey[2], uz * e.ez[2])), aEz);
+                    }
+                }
+        if (phi) phi[p] += ke * aphi;
+        if (E) {
+            E[3 * p] += ke * aEx;
+            E[3 * p + 1] += ke * aEy;
+            E[3 * p + 2] += ke * aEz;
+        }
+    }
+}
+
+// Flags and lists (in binned order within each block) the points whose FP32-pass estimate
+// exceeds tol times |phi| or |E| (refine != 0), and writes every point's estimate to err.
+__global__ void __launch_bounds__(256)
+    k_flag(const double* __restrict__ phi, const double* __restrict__ E, const float2* __restrict__ bound,
+           const int32_t* __restrict__ order, int64_t n, double tol, int refine, double* __restrict__ err,
+           int32_t* __restrict__ list, int32_t* __restrict__ n_list) {
+    __shared__ int32_t s_warp[8];
+    __shared__ int32_t s_base;
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    bool f = false;
+    int32_t p = 0;
+    if (i < n) {
+        p = order ? order[i] : (int32_t)i;
+        const float2 b = bound[p];
+        const double ep = kGammaPhi * (double)b.x, eE = kGammaE * (double)b.y;
+        if (phi && ep > tol * fabs(phi[p])) f = true;
+        if (E) {
+            const double ex = E[3 * p], ey = E[3 * p + 1], ez = E[3 * p + 2];
+            if (eE > tol * sqrt(ex * ex + ey * ey + ez * ez)) f = true;
+        }
+        f = f && refine;
+        if (err) {
+            err[2 * p] = ep;
+            err[2 * p + 1] = eE;
+        }
+    }
+    const unsigned ballot = __ballot_sync(0xffffffffu, f);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) s_warp[w] = __popc(ballot);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t run = 0;
+        for (int k = 0; k < 8; ++k) {
+            const int32_t c = s_warp[k];
+            s_warp[k] = run;
+            run += c;
+        }
+        s_base = run ? atomicAdd(n_list, run) : 0;
+    }
+    __syncthreads();
+    if (f) list[s_base + s_warp[w] + __popc(ballot & ((1u << lane) - 1u))] = p;
+}
+
+}  // namespace
+
+cudaError_t launch_eval_refine(const AccView& A, const ImageTable& img, const double* pts, int64_t npts,
+                               double* phi, double* E, double* err, double tol, const MixedScratch& ms, int sms,
+                               cudaStream_t s) {
+    if (npts == 0) return cudaSuccess;
+    if (npts > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
+    const bool refine = tol > 0.0 && (phi || E);
+    cudaError_t e = cudaMemsetAsync(ms.n_list, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    k_flag<<<(unsigned)((npts + 255) / 256), 256, 0, s>>>(phi, E, ms.bound, ms.order, npts, tol, refine ? 1 : 0, err,
+                                                         ms.list, ms.n_list);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || !refine) return e;
+    // element tile: a power of two (divides the chunk width), at most 16, within ~40 KB
+    int te = 16;
+    while (te > 1 && acc_tile_f4(te, img.n) * (int)sizeof(float4) > 40 * 1024) te /= 2;
+    const size_t smem = (size_t)acc_tile_f4(te, img.n) * sizeof(float4);
+    e = cudaFuncSetAttribute(k_eval_acc_far, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t want = (npts + kAT - 1) / kAT;
+    const unsigned gf = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 3 * (int64_t)sms));
+    k_eval_acc_far<<<gf, kAT, smem, s>>>(A, img.n, te, pts, ms.list, ms.n_list, phi, E, err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const unsigned gn = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 8 * (int64_t)sms));
+    k_eval_acc_near<<<gn, 128, 0, s>>>(A, img, pts, ms.list, ms.n_list, phi, E);
+    return cudaGetLastError();
+}
+
+}  // namespace nb

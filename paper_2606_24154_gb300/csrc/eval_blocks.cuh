@@ -34,6 +34,13 @@
 // over groups of kGroup elements and flushed to FP64.  Every decision depends only on the
 // pair, and each point's sums run in a fixed order, so a point's result is bit-identical
 // whatever other points share its launch.
+//
+// Error scale.  Beside the sums, the far part accumulates per point the scale of its
+// rounding and truncation errors: B_phi = sum_j |sigma_j| |sum_k Phi'_jk| and
+// B_E = sum_j |sigma_j| |sum_k E'_jk|_1 over the FP32 pairs.  The FP32 pass's error of Phi
+// (of E) stays below a small multiple of u B (u = 2^-24); eval_acc.cu turns these scales
+// into a per-point error estimate and refines the points whose estimate exceeds the
+// requested relative tolerance.  The scales do not enter the sums themselves.
 #pragma once
 #include "influence.cuh"
 
@@ -96,6 +103,19 @@ __device__ __forceinline__ void pairs0_reg(const float4 (&q)[2 * kPairs0], float
 struct Sum4 {
     double phi, x, y, z;
 };
+// far sums plus the error scales B_phi, B_E (raw, before the factor ke)
+struct Sum6 {
+    double phi, x, y, z, bphi, bE;
+};
+
+// Per-thread error scales of the far pass, (B_phi, B_E) raw: positive sums, FP32 is ample.
+// They live in a shared-memory slot (read and written once per element) rather than in
+// registers across the element loop; bound_reset() before a point's first range.
+__device__ __forceinline__ float2* bound_slot() {
+    __shared__ float2 s_bnd[kEvalThreads];
+    return &s_bnd[threadIdx.x];
+}
+__device__ __forceinline__ void bound_reset() { *bound_slot() = make_float2(0.f, 0.f); }
 
 __device__ __forceinline__ Sum4 far_range(const GeomView& g, float phx, float phy, float phz, float plx, float ply,
                                           float plz, int64_t e0, int64_t e1) {
@@ -111,6 +131,7 @@ __device__ __forceinline__ Sum4 far_range(const GeomView& g, float phx, float ph
     __shared__ float s_sig[kTileMax];
     __shared__ float4 s_c[kCjkMax][2];  // image centroids: hi, lo
 
+    float2* bslot = bound_slot();
     double aphi = 0.0, aEx = 0.0, aEy = 0.0, aEz = 0.0;
     for (int64_t base = e0; base < e1; base += tile_el) {
         const int cnt = (int)min((int64_t)tile_el, e1 - base);
@@ -155,10 +176,15 @@ __device__ __forceinline__ Sum4 far_range(const GeomView& g, float phx, float ph
                 // nearer pairs: k_eval_near
             }
             const float s = s_sig[jj];
-            gphi = fmaf(s, lphi.x + lphi.y, gphi);
-            gx = fmaf(s, lx.x + lx.y, gx);
-            gy = fmaf(s, ly.x + ly.y, gy);
-            gz = fmaf(s, lz.x + lz.y, gz);
+            const float fphi = lphi.x + lphi.y, fx = lx.x + lx.y, fy = ly.x + ly.y, fz = lz.x + lz.y;
+            gphi = fmaf(s, fphi, gphi);
+            gx = fmaf(s, fx, gx);
+            gy = fmaf(s, fy, gy);
+            gz = fmaf(s, fz, gz);
+            float2 b = *bslot;
+            b.x = fmaf(fabsf(s), fabsf(fphi), b.x);
+            b.y = fmaf(fabsf(s), fabsf(fx) + fabsf(fy) + fabsf(fz), b.y);
+            *bslot = b;
             if ((jj % kGroup) == kGroup - 1 || jj == cnt - 1) {
                 aphi += (double)gphi;
                 aEx += (double)gx;
@@ -188,8 +214,9 @@ __device__ __forceinline__ void load_point_2f(const double* __restrict__ pts, in
 // NaN in both precisions (the FP32 tiers would otherwise fail every distance test for it
 // and leave zeros).  Its coordinates are read again here rather than kept in a register
 // through the element loop.
+template <class S>
 __device__ __forceinline__ void store_far(const double* __restrict__ pts, double* __restrict__ phi,
-                                          double* __restrict__ E, int64_t p, const Sum4& s) {
+                                          double* __restrict__ E, int64_t p, const S& s) {
     const double ke = 1.0 / (4.0 * kPi * kEps0);
     const bool finite = isfinite(pts[3 * p]) && isfinite(pts[3 * p + 1]) && isfinite(pts[3 * p + 2]);
     const double f = finite ? ke : __longlong_as_double(0x7ff8000000000000ll);
@@ -201,26 +228,51 @@ __device__ __forceinline__ void store_far(const double* __restrict__ pts, double
     }
 }
 
+// ke * (B_phi, B_E) of point p (the FP32 pass's error scales, V and V/m)
+__device__ __forceinline__ void store_bound(float2* __restrict__ bound, int64_t p, float2 b) {
+    const double ke = 1.0 / (4.0 * kPi * kEps0);
+    if (bound) bound[p] = make_float2((float)(ke * b.x), (float)(ke * b.y));
+}
+
 // Far part (FP32 tiers) of `count` targets; writes ke * sum (overwrites phi / E).  Thread
 // t takes point idx[base + t] (or base + t when idx is null) of pts / phi / E.  The
 // elements are summed in chunks of kChunkEl whose FP64 sums are added in order, so that
 // a launch split over element chunks (the server's small requests) gives the same bits.
+// `bound` (may be null) receives ke * (B_phi, B_E) per point.
+__device__ __forceinline__ void add6(Sum6& t, const Sum6& c) {
+    t.phi += c.phi;
+    t.x += c.x;
+    t.y += c.y;
+    t.z += c.z;
+    t.bphi += c.bphi;
+    t.bE += c.bE;
+}
+
 __device__ __forceinline__ void far_block(const GeomView& g, const double* __restrict__ pts,
                                           const int32_t* __restrict__ idx, int64_t base, int count,
-                                          double* __restrict__ phi, double* __restrict__ E) {
+                                          double* __restrict__ phi, double* __restrict__ E,
+                                          float2* __restrict__ bound) {
     const bool active = (int)threadIdx.x < count;
     const int64_t p = active ? (idx ? (int64_t)idx[base + threadIdx.x] : base + threadIdx.x) : 0;
     float phx, phy, phz, plx, ply, plz;
     load_point_2f(pts, p, active, phx, phy, phz, plx, ply, plz);
     Sum4 tot{0.0, 0.0, 0.0, 0.0};
+    float2 btot = make_float2(0.f, 0.f);  // chunk scales added in chunk order (as the server does)
     for (int64_t e0 = 0; e0 < g.n_el; e0 += kChunkEl) {
+        bound_reset();
         const Sum4 c = far_range(g, phx, phy, phz, plx, ply, plz, e0, min(e0 + (int64_t)kChunkEl, g.n_el));
         tot.phi += c.phi;
         tot.x += c.x;
         tot.y += c.y;
         tot.z += c.z;
+        const float2 b = *bound_slot();
+        btot.x += b.x;
+        btot.y += b.y;
     }
-    if (active) store_far(pts, phi, E, p, tot);
+    if (active) {
+        store_far(pts, phi, E, p, tot);
+        store_bound(bound, p, btot);
+    }
 }
 
 // Near part (FP64 closed forms) of one target; adds ke * sum to phi[p] / E[p].

@@ -10,10 +10,11 @@ namespace {
 
 __global__ void __launch_bounds__(kEvalThreads, 6) k_eval_far(const GeomView g, const double* __restrict__ pts,
                                                             const int32_t* __restrict__ order, int64_t npts,
-                                                            double* __restrict__ phi, double* __restrict__ E) {
+                                                            double* __restrict__ phi, double* __restrict__ E,
+                                                            float2* __restrict__ bound) {
     const int64_t base = (int64_t)blockIdx.x * blockDim.x;
     const int count = (int)min((int64_t)blockDim.x, npts - base);
-    far_block(g, pts, order, base, count, phi, E);
+    far_block(g, pts, order, base, count, phi, E, bound);
 }
 
 __global__ void __launch_bounds__(kEvalThreads) k_eval_near(const GeomView g, const ImageTable img,
@@ -158,31 +159,50 @@ GeomView make_view(const Elem* el, const FarNodes* far, const float4* cjk, const
     return g;
 }
 
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+MixedScratch mixed_scratch(void* base, int64_t npts) {
+    char* p = static_cast<char*>(base);
+    MixedScratch m;
+    const size_t n = (size_t)npts;
+    m.count = reinterpret_cast<int32_t*>(p);
+    p += align256(sizeof(int32_t) * kBins);
+    m.key = reinterpret_cast<int32_t*>(p);
+    p += align256(sizeof(int32_t) * n);
+    m.order = reinterpret_cast<int32_t*>(p);
+    p += align256(sizeof(int32_t) * n);
+    m.bound = reinterpret_cast<float2*>(p);
+    p += align256(sizeof(float2) * n);
+    m.list = reinterpret_cast<int32_t*>(p);
+    p += align256(sizeof(int32_t) * n);
+    m.n_list = reinterpret_cast<int32_t*>(p);
+    return m;
+}
+
 size_t eval_mixed_scratch_bytes(int64_t npts) {
-    return sizeof(int32_t) * ((size_t)kBins + 2 * (size_t)npts);
+    const size_t n = (size_t)npts;
+    return align256(sizeof(int32_t) * kBins) + 3 * align256(sizeof(int32_t) * n) + align256(sizeof(float2) * n) +
+           256;
 }
 
 cudaError_t launch_eval_mixed(const Elem* el, const FarNodes* far, const float4* cjk, const double* sigma,
                               int64_t n_el, const ImageTable& img, const NearGrid& grid, const int32_t* cell_start,
                               const int32_t* cell_items, const double* pts, int64_t npts, double* phi, double* E,
-                              void* scratch, cudaStream_t s) {
+                              const MixedScratch& ms, cudaStream_t s) {
     if (npts == 0) return cudaSuccess;
     if (npts > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
     const GeomView g = make_view(el, far, cjk, sigma, n_el, img, grid, cell_start, cell_items);
-    int32_t* count = static_cast<int32_t*>(scratch);
-    int32_t* key = count + kBins;
-    int32_t* order = key + npts;
     const unsigned pblocks = (unsigned)((npts + 255) / 256);
-    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int32_t) * kBins, s);
+    cudaError_t e = cudaMemsetAsync(ms.count, 0, sizeof(int32_t) * kBins, s);
     if (e != cudaSuccess) return e;
-    k_bin_keys<<<pblocks, 256, 0, s>>>(pts, npts, grid, key, count);
-    k_bin_scan<<<1, 1024, 0, s>>>(count);
-    k_bin_scatter<<<pblocks, 256, 0, s>>>(key, npts, count, order);
+    k_bin_keys<<<pblocks, 256, 0, s>>>(pts, npts, grid, ms.key, ms.count);
+    k_bin_scan<<<1, 1024, 0, s>>>(ms.count);
+    k_bin_scatter<<<pblocks, 256, 0, s>>>(ms.key, npts, ms.count, ms.order);
     const unsigned blocks = (unsigned)((npts + kEvalThreads - 1) / kEvalThreads);
-    k_eval_far<<<blocks, kEvalThreads, 0, s>>>(g, pts, order, npts, phi, E);
+    k_eval_far<<<blocks, kEvalThreads, 0, s>>>(g, pts, ms.order, npts, phi, E, ms.bound);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_eval_near<<<blocks, kEvalThreads, 0, s>>>(g, img, pts, order, npts, phi, E);
+    k_eval_near<<<blocks, kEvalThreads, 0, s>>>(g, img, pts, ms.order, npts, phi, E);
     return cudaGetLastError();
 }
 

@@ -11,10 +11,11 @@
 // The array is a static __device__ object of this library: every GPU that loads the
 // library holds it (about 2.1 MB) until the process exits, and all calls on a device
 // share it, so calls whose GPU work overlaps in time race on it.  In host code its name
-// is only a host-side stand-in; the device address is obtained once per device with
-// cudaGetSymbolAddress (on the first call made with that device current) and cached.
-#include <mutex>
-
+// is only a host-side stand-in: every call asks the runtime for the array's address in
+// the context current on the calling thread (cudaGetSymbolAddress, which allocates
+// nothing).  The address is not cached: a cached one would go stale after a
+// cudaDeviceReset, and would belong to another context when the caller makes a
+// non-primary context current (each context holds its own instance of the array).
 #include "context.h"
 
 namespace nb {
@@ -30,19 +31,12 @@ constexpr size_t kScratchDoubles = kWorkDoubles + 32;  // + flags (two ints)
 
 static __device__ __align__(256) double g_lu_scratch[kScratchDoubles];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double* g_addr[kMaxDevices] = {nullptr};
-
-int scratch_address(int dev, double** out) {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_lu_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_lu_scratch)");
-        g_addr[dev] = static_cast<double*>(p);
-    }
-    *out = g_addr[dev];
+// Device address of the array in the current context (looked up on every call).
+int scratch_address(double** out) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_lu_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_lu_scratch)");
+    *out = static_cast<double*>(p);
     return NEBEM_OK;
 }
 
@@ -57,16 +51,12 @@ extern "C" int nebem_lu_factor_device_noalloc(double* d_A, int64_t n, int32_t* d
     if (n > kNoAllocMaxN)
         return fail(NEBEM_TOO_LARGE, "nebem_lu_factor_device_noalloc handles n <= 4096 (static work space)");
     static_assert(kWorkDoubles >= 64 * 64 + 64 * 4096 + 16 + 256 * 4, "work space too small");
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kMaxDevices) return fail(NEBEM_INVALID_ARG, "device ordinal beyond 63");
     double* scratch = nullptr;
-    int rc = scratch_address(dev, &scratch);
+    const int rc = scratch_address(&scratch);
     if (rc) return rc;
     int* info = reinterpret_cast<int*>(scratch + kWorkDoubles);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    e = lu_factor_f64(d_A, n, d_piv, kNoAllocBlock, scratch, info, s);  // clears the flag first
+    cudaError_t e = lu_factor_f64(d_A, n, d_piv, kNoAllocBlock, scratch, info, s);  // clears the flag first
     if (e != cudaSuccess) return cuda_fail(e, "lu_factor_f64");
     int h_info = 0;
     e = cudaMemcpyAsync(&h_info, info, sizeof(int), cudaMemcpyDeviceToHost, s);

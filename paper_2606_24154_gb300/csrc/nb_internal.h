@@ -130,14 +130,49 @@ GeomView make_view(const Elem* el, const FarNodes* far, const float4* cjk, const
 // Each returns cudaSuccess or the launch error.
 cudaError_t launch_eval_f64(const Elem* el, const double* sigma, int64_t n_el, const ImageTable& img,
                             const double* pts, int64_t npts, double* phi, double* E, cudaStream_t s);
+// Scratch of one mixed evaluation of npts points: binning (bin counts, keys, the binned
+// order), the FP32 pass's error scales ke * (B_phi, B_E) per point, and the list and count
+// of the points the refinement re-evaluates.
+struct MixedScratch {
+    int32_t* count;  // kBins
+    int32_t* key;    // npts
+    int32_t* order;  // npts
+    float2* bound;   // npts
+    int32_t* list;   // npts
+    int32_t* n_list; // 1
+};
+MixedScratch mixed_scratch(void* base, int64_t npts);
+// scratch bytes a mixed evaluation (FP32 pass and refinement) needs for npts points
+size_t eval_mixed_scratch_bytes(int64_t npts);
+// FP32 pass (binning, far tiers, FP64 near pairs); fills ms.order and ms.bound
 cudaError_t launch_eval_mixed(const Elem* el, const FarNodes* far, const float4* cjk, const double* sigma,
                               int64_t n_el, const ImageTable& img, const NearGrid& grid, const int32_t* cell_start,
                               const int32_t* cell_items, const double* pts, int64_t npts, double* phi, double* E,
-                              void* scratch, cudaStream_t s);
+                              const MixedScratch& ms, cudaStream_t s);
+// Tables of the two-float evaluation (the mixed fill's): element records, node records,
+// tau = t_k . frame, two-float image centroids, and the cell list with the near radius
+// kFillRatioC rho.
+struct AccView {
+    const Elem* el;
+    const FillEl* fe;
+    const float4* nodes;
+    const float4* tau;
+    const float4* cjk;
+    const double* sigma;
+    int64_t n_el;
+    NearGrid grid;
+    const int32_t* cell_start;
+    const int32_t* cell_items;
+};
+// Refinement after launch_eval_mixed: every point whose estimated error (gamma * bound)
+// exceeds tol times its |phi| or |E| is re-evaluated in two-float arithmetic with FP64 near
+// pairs (eval_acc.cu); err (may be NULL, n x 2) receives the estimated absolute error of
+// phi and |E| of every point.  sms = multiprocessors of the device.
+cudaError_t launch_eval_refine(const AccView& A, const ImageTable& img, const double* pts, int64_t npts,
+                               double* phi, double* E, double* err, double tol, const MixedScratch& ms, int sms,
+                               cudaStream_t s);
 cudaError_t launch_pair_tiers(const FarNodes* far, const float4* cjk, int64_t n_el, int nimg, const double* pts,
                               int64_t npts, uint8_t* codes, cudaStream_t s);
-// scratch bytes launch_eval_mixed needs for npts points (target binning)
-size_t eval_mixed_scratch_bytes(int64_t npts);
 cudaError_t launch_image_centroids(const Elem* el, int64_t n, const ImageTable& img, float4* cjk, cudaStream_t s);
 cudaError_t launch_fill_f64(const Elem* el, const double* diag, int64_t n, const ImageTable& img, double* K,
                             cudaStream_t s);

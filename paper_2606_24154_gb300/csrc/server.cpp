@@ -12,6 +12,12 @@
 // run join the running launch.  On completion the outputs are copied to the caller's
 // buffers and the arena range, slot and ring items are released.
 //
+// Mixed requests on a context whose mixed_point_tol is > 0 get the refinement of the
+// standalone evaluation: once their items are done, the host launches the flag and
+// two-float re-evaluation kernels (eval_acc.cu) on the request's arena range on a second
+// stream, and the request completes when that work has finished.  The kernels and the
+// error scales are those of nebem_eval, so every point gets the same bits either way.
+//
 // The server is driven from the caller's thread: submit, poll and wait each run one
 // round of completion -> admission -> launch.  Calls on one server must be serialised.
 #include <atomic>
@@ -92,7 +98,7 @@ struct Request {
     int32_t slot = -1;
     int64_t offset = -1, items = 0, gen = 0;
     std::vector<int32_t> pblocks;  // partial-sum blocks of a chunked request
-    int state = 0;  // 0 queued, 1 admitted, 2 done
+    int state = 0;  // 0 queued, 1 admitted, 2 done, 3 refining (items done, refinement queued)
 };
 
 }  // namespace
@@ -101,10 +107,12 @@ struct Server {
     int device = 0;
     nebem_server_options opt{};
     std::vector<Ctx*> ctxs;
-    cudaStream_t compute = nullptr, copy = nullptr;
+    cudaStream_t compute = nullptr, copy = nullptr, refine = nullptr;
     cudaEvent_t kernel_done = nullptr;
+    std::vector<cudaEvent_t> refine_done;  // per slot
     bool kernel_launched = false;
     DevBuf d_geoms, d_pts, d_phi, d_E, d_head, d_remaining, d_partials, d_pcount;
+    DevBuf d_bound, d_list, d_nlist;  // refinement: error scales, flagged lists (arena index), counts per slot
     std::vector<int32_t> nchunks;  // element chunks per geometry
     int32_t max_chunks = 1;
     std::vector<int32_t> free_pblocks;
@@ -131,19 +139,70 @@ struct Server {
         if (h_ring) cudaFreeHost(h_ring);
         if (h_tail) cudaFreeHost(h_tail);
         if (h_done) cudaFreeHost(h_done);
+        if (refine) cudaStreamSynchronize(refine);
+        for (cudaEvent_t e : refine_done)
+            if (e) cudaEventDestroy(e);
         if (kernel_done) cudaEventDestroy(kernel_done);
+        if (refine) cudaStreamDestroy(refine);
         if (compute) cudaStreamDestroy(compute);
         if (copy) cudaStreamDestroy(copy);
         for (auto& kv : reqs) delete kv.second;
     }
 
+    bool refines(const Request* r) const {
+        return r->precision == NEBEM_MIXED && ctxs[r->geom]->opt.mixed_point_tol > 0.0;
+    }
+
+    // the flag and re-evaluation kernels of the standalone evaluation on r's arena range
+    int launch_refine(Request* r) {
+        Ctx* c = ctxs[r->geom];
+        AccView A;
+        A.el = c->d_el.as<Elem>();
+        A.fe = c->d_fill_el.as<FillEl>();
+        A.nodes = c->d_fill_nodes.as<float4>();
+        A.tau = c->d_fill_tau.as<float4>();
+        A.cjk = c->d_cjk.as<float4>();
+        A.sigma = c->d_sigma.as<double>();
+        A.n_el = c->n;
+        A.grid = c->fill_grid;
+        A.cell_start = c->d_fill_cell_start.as<int32_t>();
+        A.cell_items = c->d_fill_cell_items.as<int32_t>();
+        MixedScratch ms{};
+        ms.order = nullptr;
+        ms.bound = d_bound.as<float2>() + r->offset;
+        ms.list = d_list.as<int32_t>() + r->offset;
+        ms.n_list = d_nlist.as<int32_t>() + r->slot;
+        CK(launch_eval_refine(A, c->img, d_pts.as<double>() + 3 * r->offset, r->n,
+                              r->phi ? d_phi.as<double>() + r->offset : nullptr,
+                              r->E ? d_E.as<double>() + 3 * r->offset : nullptr, nullptr, c->opt.mixed_point_tol, ms,
+                              c->props.multiProcessorCount, refine));
+        CK(cudaEventRecord(refine_done[r->slot], refine));
+        return 0;
+    }
+
     int complete() {
         for (size_t i = 0; i < admitted.size();) {
             Request* r = admitted[i];
-            const int64_t done = __atomic_load_n(&h_done[r->slot], __ATOMIC_ACQUIRE);
-            if (done != r->gen) {
-                ++i;
-                continue;
+            if (r->state == 3) {
+                const cudaError_t q = cudaEventQuery(refine_done[r->slot]);
+                if (q == cudaErrorNotReady) {
+                    ++i;
+                    continue;
+                }
+                if (q != cudaSuccess) return cuda_fail(q, "refinement kernels");
+            } else {
+                const int64_t done = __atomic_load_n(&h_done[r->slot], __ATOMIC_ACQUIRE);
+                if (done != r->gen) {
+                    ++i;
+                    continue;
+                }
+                if (refines(r)) {
+                    int rc = launch_refine(r);
+                    if (rc) return rc;
+                    r->state = 3;
+                    ++i;
+                    continue;
+                }
             }
             if (r->phi)
                 CK(cudaMemcpyAsync(r->phi, d_phi.as<double>() + r->offset,
@@ -225,7 +284,8 @@ struct Server {
             if (q != cudaSuccess) return cuda_fail(q, "serving kernel");
         }
         CK(launch_serve(d_geoms.as<ServeGeom>(), h_ring, ring_cap, h_tail, d_head.as<unsigned long long>(),
-                        d_pts.as<double>(), d_phi.as<double>(), d_E.as<double>(), d_remaining.as<int>(), h_done,
+                        d_pts.as<double>(), d_phi.as<double>(), d_E.as<double>(), d_bound.as<float2>(),
+                        d_remaining.as<int>(), h_done,
                         d_partials.as<double>(), d_pcount.as<int>(), max_chunks, (uint64_t)opt.idle_us * 1000ull,
                         opt.workers, compute));
         CK(cudaEventRecord(kernel_done, compute));
@@ -279,6 +339,12 @@ int nebem_server_create(nebem_server** out, nebem_ctx* const* ctxs, int32_t n_ct
                                              " has known charges or Adaptive Modelling, which the server does not apply");
         if (c->device != reinterpret_cast<Ctx*>(ctxs[0])->device)
             return fail(NEBEM_INVALID_ARG, "all contexts must share one device");
+        if (c->opt.mixed_point_tol > 0.0) {  // tables of the refinement, built before any request
+            const cudaError_t e = cudaSetDevice(c->device);
+            if (e != cudaSuccess) return cuda_fail(e, "nebem_server_create");
+            const int rc = ensure_fill_tables(c);
+            if (rc) return rc;
+        }
         cs.push_back(c);
     }
     Server* s = new (std::nothrow) Server();
@@ -294,6 +360,10 @@ int nebem_server_create(nebem_server** out, nebem_ctx* const* ctxs, int32_t n_ct
     cudaError_t e = cudaSetDevice(s->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->compute, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->copy, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->refine, cudaStreamNonBlocking);
+    s->refine_done.assign((size_t)o.max_requests, nullptr);
+    for (int32_t i = 0; i < o.max_requests && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&s->refine_done[(size_t)i], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->kernel_done, cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(cuda_fail(e, "nebem_server_create"));
     if (s->opt.workers == 0) s->opt.workers = 2 * cs[0]->props.multiProcessorCount;
@@ -316,8 +386,11 @@ int nebem_server_create(nebem_server** out, nebem_ctx* const* ctxs, int32_t n_ct
         (e = s->d_E.ensure(sizeof(double) * 3 * cap)) != cudaSuccess ||
         (e = s->d_head.ensure(sizeof(unsigned long long))) != cudaSuccess ||
         (e = s->d_remaining.ensure(sizeof(int) * o.max_requests)) != cudaSuccess ||
-        (e = s->d_partials.ensure(sizeof(double) * 4 * kItemPoints * (size_t)kPartialBlocks * s->max_chunks)) !=
-            cudaSuccess ||
+        (e = s->d_partials.ensure(sizeof(double) * kPartialDoubles * kItemPoints * (size_t)kPartialBlocks *
+                                  s->max_chunks)) != cudaSuccess ||
+        (e = s->d_bound.ensure(sizeof(float2) * cap)) != cudaSuccess ||
+        (e = s->d_list.ensure(sizeof(int32_t) * cap)) != cudaSuccess ||
+        (e = s->d_nlist.ensure(sizeof(int32_t) * o.max_requests)) != cudaSuccess ||
         (e = s->d_pcount.ensure(sizeof(int) * kPartialBlocks)) != cudaSuccess)
         return bail(cuda_fail(e, "server device buffers"));
     if ((e = cudaHostAlloc(&s->h_ring, sizeof(WorkItem) * s->ring_cap, cudaHostAllocMapped)) != cudaSuccess ||

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restr
                                                         int64_t ring_cap, int64_t* tail_mapped,
                                                         unsigned long long* head, const double* __restrict__ arena_pts,
                                                         double* __restrict__ arena_phi, double* __restrict__ arena_E,
-                                                        int* remaining, int64_t* done_mapped, double* partials,
+                                                        float2* __restrict__ arena_bound, int* remaining, int64_t* done_mapped, double* partials,
                                                         int* pblock_count, int max_chunks, uint64_t idle_ns) {
     __shared__ WorkItem it;
     __shared__ int have;
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restr
             f64_block(G.view.el, G.view.sigma, G.view.n_el, G.img, arena_pts + 3 * it.offset, it.count,
                       arena_phi + it.offset, arena_E + 3 * it.offset);
         } else if (it.chunk < 0) {
-            far_block(G.view, arena_pts, nullptr, it.offset, it.count, arena_phi, arena_E);
+            far_block(G.view, arena_pts, nullptr, it.offset, it.count, arena_phi, arena_E, arena_bound);
             if ((int)threadIdx.x < it.count)
                 near_point(G.view, G.img, arena_pts, it.offset + threadIdx.x, arena_phi, arena_E);
         } else {
@@ -78,20 +78,26 @@ __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restr
             const int64_t e0 = (int64_t)it.chunk * kChunkEl;
             const int64_t e1 = min(e0 + (int64_t)kChunkEl, G.view.n_el);
             Sum4 c;
+            float2 b = make_float2(0.f, 0.f);
             if (mixed) {
                 float phx, phy, phz, plx, ply, plz;
                 load_point_2f(arena_pts, p, active, phx, phy, phz, plx, ply, plz);
+                bound_reset();
                 c = far_range(G.view, phx, phy, phz, plx, ply, plz, e0, e1);
+                b = *bound_slot();
             } else {
                 const double Px = active ? arena_pts[3 * p] : 0.0, Py = active ? arena_pts[3 * p + 1] : 0.0,
                              Pz = active ? arena_pts[3 * p + 2] : 0.0;
                 c = f64_range(G.view.el, G.view.sigma, e0, e1, G.img, Px, Py, Pz);
             }
-            double* part = partials + ((int64_t)it.pblock * max_chunks + it.chunk) * (4 * kEvalThreads);
-            part[4 * threadIdx.x] = c.phi;
-            part[4 * threadIdx.x + 1] = c.x;
-            part[4 * threadIdx.x + 2] = c.y;
-            part[4 * threadIdx.x + 3] = c.z;
+            constexpr int kP = kPartialDoubles;
+            double* part = partials + ((int64_t)it.pblock * max_chunks + it.chunk) * (kP * kEvalThreads);
+            part[kP * threadIdx.x] = c.phi;
+            part[kP * threadIdx.x + 1] = c.x;
+            part[kP * threadIdx.x + 2] = c.y;
+            part[kP * threadIdx.x + 3] = c.z;
+            part[kP * threadIdx.x + 4] = (double)b.x;  // exact
+            part[kP * threadIdx.x + 5] = (double)b.y;
             __threadfence();
             __syncthreads();
             if (threadIdx.x == 0) last = (atomicAdd(&pblock_count[it.pblock], 1) == it.nchunks - 1);
@@ -100,16 +106,20 @@ __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restr
             if (last) {
                 __threadfence();
                 Sum4 tot{0.0, 0.0, 0.0, 0.0};
+                float2 btot = make_float2(0.f, 0.f);  // FP32 sums in chunk order, as far_block
                 for (int k = 0; k < it.nchunks; ++k) {
-                    const double* q = partials + ((int64_t)it.pblock * max_chunks + k) * (4 * kEvalThreads) +
-                                      4 * threadIdx.x;
+                    const double* q = partials + ((int64_t)it.pblock * max_chunks + k) * (kP * kEvalThreads) +
+                                      kP * threadIdx.x;
                     tot.phi += __ldcg(q);
                     tot.x += __ldcg(q + 1);
                     tot.y += __ldcg(q + 2);
                     tot.z += __ldcg(q + 3);
+                    btot.x += (float)__ldcg(q + 4);
+                    btot.y += (float)__ldcg(q + 5);
                 }
                 if (active) {
                     store_far(arena_pts, arena_phi, arena_E, p, tot);
+                    if (mixed) store_bound(arena_bound, p, btot);
                     if (mixed) near_point(G.view, G.img, arena_pts, p, arena_phi, arena_E);
                 }
                 if (threadIdx.x == 0) pblock_count[it.pblock] = 0;
@@ -132,10 +142,10 @@ __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restr
 
 cudaError_t launch_serve(const ServeGeom* geoms, const WorkItem* ring, int64_t ring_cap, int64_t* tail_mapped,
                          unsigned long long* head, const double* arena_pts, double* arena_phi, double* arena_E,
-                         int* remaining, int64_t* done_mapped, double* partials, int* pblock_count, int max_chunks,
-                         uint64_t idle_ns, int workers, cudaStream_t s) {
+                         float2* arena_bound, int* remaining, int64_t* done_mapped, double* partials,
+                         int* pblock_count, int max_chunks, uint64_t idle_ns, int workers, cudaStream_t s) {
     k_serve<<<workers, kEvalThreads, 0, s>>>(geoms, ring, ring_cap, tail_mapped, head, arena_pts, arena_phi, arena_E,
-                                             remaining, done_mapped, partials, pblock_count, max_chunks, idle_ns);
+                                             arena_bound, remaining, done_mapped, partials, pblock_count, max_chunks, idle_ns);
     return cudaGetLastError();
 }
 

@@ -29,7 +29,7 @@ static int elapsed_ms(Ctx* c, double* ms) {
     return 0;
 }
 
-static int ensure_fill_tables(Ctx* c) {
+int ensure_fill_tables(Ctx* c) {
     if (c->fill_tables) return 0;
     std::vector<FillEl> fe;
     std::vector<float4> nodes, tau;
@@ -209,28 +209,52 @@ int eval_set(Ctx* c, const EvalSet& es, const double* d_pts, int64_t n, double* 
         CK(c->d_scratch.ensure(eval_mixed_scratch_bytes(n)));
         CK(launch_eval_mixed(es.el, es.far, es.cjk.as<float4>(), es.sigma, es.n, es.img, es.grid,
                              es.cell_start.as<int32_t>(), es.cell_items.as<int32_t>(), d_pts, n, d_phi, d_E,
-                             c->d_scratch.ptr, s));
+                             mixed_scratch(c->d_scratch.ptr, n), s));
     } else {
         CK(launch_eval_f64(es.el, es.sigma, es.n, es.img, d_pts, n, d_phi, d_E, s));
     }
     return 0;
 }
 
-int eval_elements(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision, cudaStream_t s) {
+int eval_elements(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision, cudaStream_t s,
+                  double* err) {
     if (c->am_on) return eval_adaptive(c, d_pts, n, d_phi, d_E, precision, s);
     if (precision == NEBEM_MIXED) {
+        const bool refine = c->opt.mixed_point_tol > 0.0 && n > 0;
+        if (refine || err) {
+            const int rc = ensure_fill_tables(c);
+            if (rc) return rc;
+        }
         CK(c->d_scratch.ensure(eval_mixed_scratch_bytes(n)));
+        const MixedScratch ms = mixed_scratch(c->d_scratch.ptr, n);
         CK(launch_eval_mixed(c->d_el.as<Elem>(), c->d_far.as<FarNodes>(), c->d_cjk.as<float4>(),
                              c->d_sigma.as<double>(), c->n, c->img, c->grid, c->d_cell_start.as<int32_t>(),
-                             c->d_cell_items.as<int32_t>(), d_pts, n, d_phi, d_E, c->d_scratch.ptr, s));
+                             c->d_cell_items.as<int32_t>(), d_pts, n, d_phi, d_E, ms, s));
+        if (refine || err) {
+            AccView A;
+            A.el = c->d_el.as<Elem>();
+            A.fe = c->d_fill_el.as<FillEl>();
+            A.nodes = c->d_fill_nodes.as<float4>();
+            A.tau = c->d_fill_tau.as<float4>();
+            A.cjk = c->d_cjk.as<float4>();
+            A.sigma = c->d_sigma.as<double>();
+            A.n_el = c->n;
+            A.grid = c->fill_grid;
+            A.cell_start = c->d_fill_cell_start.as<int32_t>();
+            A.cell_items = c->d_fill_cell_items.as<int32_t>();
+            CK(launch_eval_refine(A, c->img, d_pts, n, d_phi, d_E, err, c->opt.mixed_point_tol, ms,
+                                  c->props.multiProcessorCount, s));
+            c->refine_list = ms.n_list;
+        }
     } else {
         CK(launch_eval_f64(c->d_el.as<Elem>(), c->d_sigma.as<double>(), c->n, c->img, d_pts, n, d_phi, d_E, s));
     }
     return 0;
 }
 
-int eval_points(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision, cudaStream_t s) {
-    int rc = eval_elements(c, d_pts, n, d_phi, d_E, precision, s);
+int eval_points(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision, cudaStream_t s,
+                double* err) {
+    int rc = eval_elements(c, d_pts, n, d_phi, d_E, precision, s, err);
     if (rc) return rc;
     return add_known_charge(c, d_pts, n, d_phi, d_E, precision, s);
 }

@@ -45,7 +45,8 @@ class nebem_options(C.Structure):
         ("sc_near", C.c_double),
         ("lu_block", C.c_int32),
         ("reserved0", C.c_int32),
-        ("reserved", C.c_double * 4),
+        ("mixed_point_tol", C.c_double),
+        ("reserved", C.c_double * 3),
     ]
 
 
@@ -94,6 +95,8 @@ SIGNATURES = {
     "nebem_matrix_entries": (C.c_int, [_vp, _i64p, _i64p, C.c_int64, _d]),
     "nebem_eval": (C.c_int, [_vp, _d, C.c_int64, _d, _d, C.c_int32]),
     "nebem_eval_device": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, C.c_int32, _vp]),
+    "nebem_eval_err": (C.c_int, [_vp, _d, C.c_int64, _d, _d, _d, _i64p]),
+    "nebem_eval_device_err": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp, _vp]),
     "nebem_space_charge": (C.c_int, [_vp, _d, _d, C.c_int64, C.c_double]),
     "nebem_space_charge_eval": (C.c_int, [_vp, _d, C.c_int64, _d, _d, C.c_int32, C.c_int32]),
     "nebem_space_charge_lines": (C.c_int, [_vp, _d, _i64p]),
@@ -241,6 +244,23 @@ def nebem_eval(ctx, pts, precision: int, want_phi=True, want_E=True):
 def nebem_eval_device(ctx, d_pts: int, n: int, d_phi: int | None, d_E: int | None, precision: int,
                       stream: int | None = None):
     _check(load().nebem_eval_device(ctx, d_pts, n, d_phi, d_E, precision, stream), "nebem_eval_device")
+
+
+def nebem_eval_err(ctx, pts, want_phi=True, want_E=True):
+    """Mixed evaluation with per-point error estimates: (phi, E, err[n, 2], refined count)."""
+    p = _f64(pts, (-1, 3))
+    n = p.shape[0]
+    phi = np.empty(n) if want_phi else None
+    E = np.empty((n, 3)) if want_E else None
+    err = np.empty((n, 2))
+    nref = C.c_int64(0)
+    _check(load().nebem_eval_err(ctx, _dp(p), n, _dp(phi), _dp(E), _dp(err), C.byref(nref)), "nebem_eval_err")
+    return phi, E, err, int(nref.value)
+
+
+def nebem_eval_device_err(ctx, d_pts: int, n: int, d_phi: int | None, d_E: int | None, d_err: int | None,
+                          stream: int | None = None):
+    _check(load().nebem_eval_device_err(ctx, d_pts, n, d_phi, d_E, d_err, stream), "nebem_eval_device_err")
 
 
 def nebem_space_charge(ctx, pos, q, softening=0.0):
@@ -440,6 +460,9 @@ class Context:
 
     def eval(self, pts, precision=NEBEM_FP64):
         return nebem_eval(self.h, pts, precision)
+
+    def eval_err(self, pts):
+        return nebem_eval_err(self.h, pts)
 
     def eval_device(self, d_pts, n, d_phi, d_E, precision=NEBEM_FP64, stream=None):
         nebem_eval_device(self.h, d_pts, n, d_phi, d_E, precision, stream)

@@ -53,6 +53,7 @@ def test_status_strings_and_defaults(lib):
     assert lib.nebem_status_string(nebem.NEBEM_SINGULAR) == b"NEBEM_SINGULAR"
     o = nebem.nebem_default_options()
     assert o.ir_tol == 1e-8 and o.lu_block == 64 and o.softening == 1e-6
+    assert o.mixed_point_tol == 1e-6
 
 
 @pytest.mark.parametrize("field,value", [
@@ -60,6 +61,7 @@ def test_status_strings_and_defaults(lib):
     ("ir_max_iter", 0), ("ir_tol", 0.0), ("ir_tol", float("nan")),
     ("ratio_near", 1.0), ("ratio_b", 2.0), ("ratio_a", 7.0), ("ratio_0", 20.0), ("ratio_0", 1e7),
     ("softening", 0.0), ("softening", -1e-6),
+    ("mixed_point_tol", -1e-6), ("mixed_point_tol", 1.0), ("mixed_point_tol", float("nan")),
 ])
 def test_bad_options_refused_before_any_device_call(lib, field, value):
     """Context options are checked on the host before the device is touched: every bad

@@ -80,5 +80,10 @@ def test_gpu_matches_stored_values(N):
     assert np.abs(phi - t["phi_V"]).max() <= 1e-10 * np.abs(t["phi_V"]).max()
     assert np.abs(E - np.array(t["E_V_per_m"])).max() <= 1e-10 * np.abs(t["E_V_per_m"]).max()
     phi, E = ctx.eval(np.array(t["points_m"]), N.NEBEM_MIXED)
-    assert np.abs(phi - t["phi_V"]).max() <= 1e-6 * np.abs(t["phi_V"]).max()
-    assert np.abs(E - np.array(t["E_V_per_m"])).max() <= 1e-6 * np.abs(t["E_V_per_m"]).max()
+    rphi, rE = np.array(t["phi_V"]), np.array(t["E_V_per_m"])
+    assert np.abs(phi - rphi).max() <= 1e-6 * np.abs(rphi).max()
+    assert np.abs(E - rE).max() <= 1e-6 * np.abs(rE).max()
+    # per point (floor 1e-6 of the largest value; E as a vector)
+    assert (np.abs(phi - rphi) / np.maximum(np.abs(rphi), 1e-6 * np.abs(rphi).max())).max() <= 1e-6
+    m = np.linalg.norm(rE, axis=1)
+    assert (np.linalg.norm(E - rE, axis=1) / np.maximum(m, 1e-6 * m.max())).max() <= 1e-6

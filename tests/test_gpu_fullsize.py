@@ -2,7 +2,8 @@
 benchmark times (all points / carriers in one call), checked against the oracle on
 sampled outputs or through properties that hold at any size:
 
-  - THGEM cell, 1e6 points, mixed evaluation: 200 sampled points against the oracle;
+  - THGEM cell, 1e6 points, mixed evaluation (with its refinement): 200 sampled points
+    against the oracle, normwise and per point;
   - double THGEM (40,368 elements), mixed solve (FP32 tensor-core LU + FP64 refinement):
     the residual of sampled rows of the oracle's own matrix times the GPU's charge
     densities;
@@ -49,6 +50,11 @@ def test_headline_eval_1e6_points_sampled(N, thgem_solved):
     rphi, rE = O.eval_points(g, sigma, pts[idx])
     assert rel_norm(phi[idx], rphi) <= TOL_MIXED
     assert rel_norm(E[idx], rE) <= TOL_MIXED
+    # per point, with the floor 1e-6 of the largest value (E as a vector)
+    r = np.abs(rphi)
+    assert (np.abs(phi[idx] - rphi) / np.maximum(r, 1e-6 * r.max())).max() <= TOL_MIXED
+    m = np.linalg.norm(rE, axis=1)
+    assert (np.linalg.norm(E[idx] - rE, axis=1) / np.maximum(m, 1e-6 * m.max())).max() <= TOL_MIXED
 
 
 def test_double_thgem_solve_residual_on_oracle_rows(N):

@@ -1,6 +1,8 @@
-"""Mixed-precision evaluation (FP32 far-field Gauss rules + FP64 near closed forms)
-against the FP64 oracle: <= 1e-6 relative (normwise per quantity), and bit-identical
-per point whatever the batch it is evaluated in."""
+"""Mixed-precision evaluation (FP32 far-field Gauss rules + FP64 near closed forms, then a
+two-float re-evaluation of the points whose estimated error exceeds 1e-6 of their own
+value) against the FP64 oracle and the FP64 path: <= 1e-6 relative per point, with the
+floor 1e-6 of the largest value (|dPhi_i| / max(|Phi_i|, 1e-6 max|Phi|), and the same for
+the field vector), and bit-identical per point whatever the batch it is evaluated in."""
 import numpy as np
 import pytest
 
@@ -28,6 +30,24 @@ def rel_vec(a, ref):
     return float(np.linalg.norm(a - ref, axis=1).max() / np.linalg.norm(ref, axis=1).max())
 
 
+def pp_scalar(a, ref):
+    """largest per-point relative error, floor 1e-6 of the largest |ref|"""
+    r = np.abs(ref)
+    return float((np.abs(a - ref) / np.maximum(r, 1e-6 * r.max())).max())
+
+
+def pp_vec(a, ref):
+    """the same for vectors (rows): |a_i - ref_i| / max(|ref_i|, 1e-6 max |ref|)"""
+    r = np.linalg.norm(ref, axis=1)
+    return float((np.linalg.norm(a - ref, axis=1) / np.maximum(r, 1e-6 * r.max())).max())
+
+
+def assert_mixed(phi, E, rphi, rE):
+    assert pp_scalar(phi, rphi) <= TOL_MIXED, pp_scalar(phi, rphi)
+    assert pp_vec(E, rE) <= TOL_MIXED, pp_vec(E, rE)
+    assert rel_norm(phi, rphi) <= TOL_MIXED and rel_vec(E, rE) <= TOL_MIXED
+
+
 def structured_sigma(g):
     """A smooth, physically shaped charge density: conductor elements carry
     eps0 * V / 1 mm with a smooth modulation, interface elements a tenth of the scale."""
@@ -49,8 +69,7 @@ def test_mixed_eval_cube_grid(N):
     ctx.set_sigma(sig_r)
     phi, E = ctx.eval(pts, N.NEBEM_MIXED)
     rphi, rE = O.eval_points(g, sig_r, pts)
-    assert rel_norm(phi, rphi) <= TOL_MIXED
-    assert rel_vec(E, rE) <= TOL_MIXED
+    assert_mixed(phi, E, rphi, rE)
 
 
 def test_mixed_eval_thgem_full_geometry_sampled(N):
@@ -61,8 +80,7 @@ def test_mixed_eval_thgem_full_geometry_sampled(N):
     ctx.set_sigma(sigma)
     phi, E = ctx.eval(pts, N.NEBEM_MIXED)
     rphi, rE = O.eval_points(g, sigma, pts)
-    assert rel_norm(phi, rphi) <= TOL_MIXED, rel_norm(phi, rphi)
-    assert rel_vec(E, rE) <= TOL_MIXED, rel_vec(E, rE)
+    assert_mixed(phi, E, rphi, rE)
 
 
 def test_mixed_matches_fp64_path_on_many_points(N):
@@ -78,8 +96,7 @@ def test_mixed_matches_fp64_path_on_many_points(N):
     ctx.set_sigma(sigma)
     phi, E = ctx.eval(pts, N.NEBEM_MIXED)
     phi64, E64 = ctx.eval(pts, N.NEBEM_FP64)
-    assert rel_norm(phi, phi64) <= TOL_MIXED
-    assert rel_vec(E, E64) <= TOL_MIXED
+    assert_mixed(phi, E, phi64, E64)
 
 
 def test_mixed_result_independent_of_batch(N):
@@ -110,7 +127,7 @@ def test_mixed_ragged_and_empty(N):
         phi, E = ctx.eval(pts, N.NEBEM_MIXED)
         if n:
             rphi, rE = O.eval_points(g, sig_r, pts)
-            assert rel_norm(phi, rphi) <= TOL_MIXED and rel_vec(E, rE) <= TOL_MIXED
+            assert_mixed(phi, E, rphi, rE)
 
 
 def test_pair_tiers_bit_exact_with_oracle(N):
@@ -138,7 +155,7 @@ def test_mixed_eval_121_images(N):
     pts = I.cell_points(g, 200, I.rng(1, 33))
     phi, E = ctx.eval(pts, N.NEBEM_MIXED)
     rphi, rE = O.eval_points(g, sigma, pts)
-    assert rel_norm(phi, rphi) <= TOL_MIXED and rel_vec(E, rE) <= TOL_MIXED
+    assert_mixed(phi, E, rphi, rE)
     assert N.nebem_image_table(ctx.h).shape[0] == 121
 
 
@@ -203,3 +220,47 @@ def test_non_finite_points_give_nan_and_leave_the_batch_unchanged(N):
     assert np.isnan(phi[bad]).all() and np.isnan(E[bad]).all()
     cphi, cE = N.nebem_fastvol_eval(ctx.h, pts[ok])
     assert np.array_equal(phi[ok], cphi) and np.array_equal(E[ok], cE)
+
+
+def test_error_estimates_and_refinement(N):
+    """nebem_eval_err: the single FP32 pass (mixed_point_tol = 0) and the refined evaluation
+    (default 1e-6) on THGEM points, against the FP64 path.
+      - the single pass misses the per-point bound where its result is small next to its
+        error scale (inside the plate, inside the copper), which is what the refinement is for;
+      - every estimate of the single pass covers its actual error;
+      - the refinement re-evaluates exactly the points whose estimate exceeds 1e-6 of their
+        |phi| or |E|, leaves every other point's bits unchanged, and meets the bound at every
+        point; the refined points' estimates cover their errors too."""
+    g = I.thgem()
+    ctx = N.Context().set_geometry(g)
+    sigma, _, _ = ctx.solve(N.NEBEM_MIXED)
+    fast = N.Context(mixed_point_tol=0.0).set_geometry(g)
+    fast.set_sigma(sigma)
+    gen = I.rng(1, 41)
+    pts = I.cell_points(g, 12000, gen)
+    plate = pts[:3000].copy()
+    plate[:, 2] = (gen.random(3000) - 0.5) * 0.65e-3  # through the plate and both copper layers
+    pts = np.concatenate([pts, plate])
+    phi64, E64 = ctx.eval(pts, N.NEBEM_FP64)
+    fphi, fE, ferr, n0 = fast.eval_err(pts)
+    phi, E, err, nref = ctx.eval_err(pts)
+    assert n0 == 0 and nref > 0
+    # the single pass: estimates cover the errors; the bound is missed somewhere
+    dphi_f = np.abs(fphi - phi64)
+    dE_f = np.linalg.norm(fE - E64, axis=1)
+    assert (dphi_f <= ferr[:, 0]).all(), (dphi_f / ferr[:, 0]).max()
+    assert (dE_f <= ferr[:, 1]).all(), (dE_f / ferr[:, 1]).max()
+    assert pp_vec(fE, E64) > TOL_MIXED or pp_scalar(fphi, phi64) > TOL_MIXED
+    # which points were refined: exactly the flagged ones
+    flag = (ferr[:, 0] > 1e-6 * np.abs(fphi)) | (ferr[:, 1] > 1e-6 * np.linalg.norm(fE, axis=1))
+    assert int(flag.sum()) == nref
+    changed = (phi != fphi) | (E != fE).any(axis=1)
+    assert not changed[~flag].any()
+    assert np.array_equal(err[~flag], ferr[~flag])
+    # refined: the bound at every point, and covered estimates
+    assert_mixed(phi, E, phi64, E64)
+    assert (np.abs(phi - phi64)[flag] <= err[flag, 0] + 1e-12 * np.abs(phi64[flag])).all()
+    assert (np.linalg.norm(E - E64, axis=1)[flag] <= err[flag, 1] + 1e-12 * np.linalg.norm(E64[flag], axis=1)).all()
+    # nebem_eval with NEBEM_MIXED gives the refined result
+    ephi, eE = ctx.eval(pts, N.NEBEM_MIXED)
+    assert np.array_equal(ephi, phi) and np.array_equal(eE, E)
