@@ -7,9 +7,13 @@ Gauss rules, FP64 near-field closed forms), charge densities from a mixed solve 
 FP64 refinement.  One step = one evaluation of all points (the whole hot path of the
 evaluation: every element, every image, every point).  Synthetic, seeded inputs.
 
-Reported next to it: the plain FP64 path's rate (on a point sample), the mixed path's
-error against the FP64 path, the roofline of the dominant kernel, the end-to-end rate
-through the host-buffer C-ABI call, and the FP64 CPU oracle timed on a bounded sample.
+The timed step is the mixed evaluation as it meets 1e-6 relative error per point (FP32
+pass, then a two-float re-evaluation of the points whose estimated error exceeds 1e-6 of
+their own value).  Reported next to it: the single FP32 pass alone with its per-point
+error, the plain FP64 path's rate (on a point sample), both mixed forms' errors against
+the FP64 path (normwise and per point), the stage times, the roofline of the dominant
+kernel, the end-to-end rate through the host-buffer C-ABI call, and the FP64 CPU oracle
+timed on a bounded sample.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -30,15 +34,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_POINTS = 1_000_000
-HEADLINE_METRIC = "element-point influence evals/s (mixed FP32/FP64, <=1e-6 rel err vs FP64 path)"
+HEADLINE_METRIC = "element-point influence evals/s (mixed FP32/FP64, <=1e-6 rel err per point vs FP64 path)"
 FP64_SAMPLE = 19_456
 CHECK_SAMPLE = 512
+ROOFLINE_SAMPLE = 8192  # points whose refinement decision is taken again to count the refined pairs
 ORACLE_SAMPLE = 2_048
 L2_FLUSH_BYTES = 512 << 20
-# DRAM bytes (read + write) of one k_eval_far launch on the default workload (1e6 points),
-# from ncu dram__bytes_read.sum + dram__bytes_write.sum (profiles/eval_mixed_thgem.md);
-# reported only for that workload and for the kernel version it was taken on.
-FAR_TRAFFIC_BYTES_1E6 = 74.07e6 + 25.28e6
 
 
 def parse():
@@ -213,6 +214,45 @@ def serving_run(N, ctxs, geoms, n_req, scale, precision, seed):
             "size_scale": scale}
 
 
+def pointwise(a, ref):
+    """largest per-point relative error |a_i - ref_i| / max(|ref_i|, 1e-6 max|ref|); rows of
+    a 2-D array are vectors (E)"""
+    if a.ndim == 1:
+        r, d = ref.abs(), (a - ref).abs()
+    else:
+        r, d = ref.norm(dim=1), (a - ref).norm(dim=1)
+    return float((d / r.clamp(min=1e-6 * float(r.max()))).max())
+
+
+def timed_steps(step, stream, flush, steps, warmup, sampler=None, barrier=None):
+    """W untimed steps, then K steps each bracketed by CUDA events on `stream`, with an L2
+    flush (512 MB write) before each; `barrier` (ranks) and a device synchronisation on both
+    sides of the timed region.  Returns the per-step ms and the wall time."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            step()
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+        torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for k in range(steps):
+            flush.fill_(float(k))
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if barrier:
+        barrier()
+        torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev], time.perf_counter() - t0
+
+
 def run_native(args):
     import torch
     import torch.distributed as dist
@@ -236,6 +276,9 @@ def run_native(args):
     n_el, n_img = g.n, g.n_images
     ctx = N.Context(device=local).set_geometry(g)
     sigma, info, _ = ctx.solve(N.NEBEM_MIXED)
+    # the single FP32 pass (no refinement) on the same charge densities, for comparison
+    single = N.Context(device=local, mixed_point_tol=0.0).set_geometry(g)
+    single.set_sigma(sigma)
 
     stream = torch.cuda.Stream(device=dev)
     s_handle = stream.cuda_stream
@@ -248,39 +291,29 @@ def run_native(args):
     def step():
         N.nebem_eval_device(ctx.h, pts.data_ptr(), npts, phi.data_ptr(), E.data_ptr(), N.NEBEM_MIXED, s_handle)
 
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            step()
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-
     sampler = ClockSampler(local)
-    sampler.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    t0 = time.perf_counter()
     torch.cuda.nvtx.range_push("timed")
-    with torch.cuda.stream(stream):
-        for k in range(args.steps):
-            flush.fill_(float(k))  # evict L2 (512 MB > 129 MB) between timed steps
-            ev[k][0].record(stream)
-            step()
-            ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
+    step_ms, wall = timed_steps(step, stream, flush, args.steps, args.warmup, sampler,
+                                dist.barrier if world > 1 else None)
     torch.cuda.nvtx.range_pop()
-    wall = time.perf_counter() - t0
     clocks = sampler.stop()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+    stats = N.nebem_eval_stats(ctx.h)  # stage times and refined counts of the last timed step
     ms = statistics.mean(step_ms)
     evals = npts * n_el * n_img
     ms, total_evals = S.reduce_step_time(ms, evals, dev)
     value = total_evals / (ms * 1e-3)
 
-    # ---- accuracy of the mixed path against the FP64 path, and the FP64 path's rate
+    # ---- the single FP32 pass, same protocol
+    phi1 = torch.empty_like(phi)
+    E1 = torch.empty_like(E)
+
+    def step1():
+        N.nebem_eval_device(single.h, pts.data_ptr(), npts, phi1.data_ptr(), E1.data_ptr(), N.NEBEM_MIXED, s_handle)
+
+    single_ms = statistics.mean(timed_steps(step1, stream, flush, args.steps, args.warmup)[0])
+    single_value = evals / (single_ms * 1e-3)
+
+    # ---- accuracy against the FP64 path on a sample, and the FP64 path's rate
     ns = min(args.fp64_points, npts)
     phi64 = torch.empty(ns, dtype=torch.float64, device=dev)
     E64 = torch.empty((ns, 3), dtype=torch.float64, device=dev)
@@ -291,20 +324,29 @@ def run_native(args):
         b.record(stream)
     torch.cuda.synchronize()
     fp64_rate = ns * n_el * n_img / (a.elapsed_time(b) * 1e-3)
-    d_phi = (phi[:ns] - phi64).abs().max().item() / phi64.abs().max().item()
-    d_E = (E[:ns] - E64).norm(dim=1).max().item() / E64.norm(dim=1).max().item()
-    emag = E64.norm(dim=1)
-    floor = 1e-3 * emag.max()
-    pp_E = ((E[:ns] - E64).norm(dim=1) / torch.maximum(emag, floor)).max().item()
+    accuracy = {"sample_points": ns, "reference": "FP64 GPU path (closed forms for every pair)",
+                "pointwise_form": "|d_i| / max(|ref_i|, 1e-6 max|ref|), E as a vector"}
+    for name, (p_, e_) in (("refined", (phi, E)), ("single_pass", (phi1, E1))):
+        accuracy[name] = {"phi_pointwise": pointwise(p_[:ns], phi64), "E_pointwise": pointwise(e_[:ns], E64),
+                          "phi_normwise": float((p_[:ns] - phi64).abs().max() / phi64.abs().max()),
+                          "E_normwise": float((e_[:ns] - E64).norm(dim=1).max() / E64.norm(dim=1).max())}
+    accuracy["sigma_refinement"] = {"iterations": info.iterations, "correction": info.correction}
 
-    # ---- roofline of the dominant kernel (mixed eval): FP32 lane operations
+    # ---- roofline of the dominant kernel: the first refinement level (two-float, FP32 lanes)
     from paper_2606_24154_gb300 import roofline as R
-    counts = R.tier_counts(g, pts_h, sample=CHECK_SAMPLE)
-    alg_ops = R.fp32_ops_per_launch(counts, npts / CHECK_SAMPLE)
     peaks, peak_src = load_peaks()
-    peak_ops = R.fp32_peak_ops(peaks.get("sm_max_mhz", 2070.0))
-    achieved = alg_ops / (ms * 1e-3)
-
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    peak_ops = R.fp32_peak_ops(sm_max)
+    sub = pts_h[:min(ROOFLINE_SAMPLE, npts)]
+    _, _, err_r, _ = N.nebem_eval_err(ctx.h, sub)
+    _, _, err_s, _ = N.nebem_eval_err(single.h, sub)
+    refined_sub = sub[(err_r != err_s).any(axis=1)]
+    counts_l1 = R.tier_counts(g, refined_sub, sample=CHECK_SAMPLE)
+    ops_l1 = stats.refined_level1 * R.acc1_ops_per_point(counts_l1, n_el)
+    ach_l1 = ops_l1 / (stats.ms_level1 * 1e-3)
+    counts = R.tier_counts(g, pts_h, sample=CHECK_SAMPLE)
+    ops_fp32 = R.fp32_ops_per_launch(counts, npts / CHECK_SAMPLE)
+    ach_fp32 = ops_fp32 / (stats.ms_fp32 * 1e-3)
     # ---- end to end through the host-buffer call (pinned host memory, copies inside)
     pts_pin = torch.from_numpy(pts_h).pin_memory()
     phi_pin = torch.empty(npts, dtype=torch.float64).pin_memory()
@@ -367,40 +409,47 @@ def run_native(args):
             "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": f"thgem_cell N={n_el} images={n_img} points={npts} mixed eval",
+            "config": {"workload": f"thgem_cell N={n_el} images={n_img} points={npts} mixed eval, "
+                                   f"refined to 1e-6 per point",
                        "elements": n_el, "images": n_img, "points_per_gpu": npts,
                        "l2": "flushed between timed steps (512 MB write)", "parallelism": f"points sharded x{world}"},
-            "accuracy": {"phi_rel_err_vs_fp64": d_phi, "E_rel_err_vs_fp64": d_E,
-                         "E_pointwise_rel_err_floor1e-3": pp_E, "sample_points": ns,
-                         "sigma_refinement": {"iterations": info.iterations, "correction": info.correction}},
+            "stages": {"ms_fp32_pass": stats.ms_fp32, "ms_refine_level1": stats.ms_level1,
+                       "ms_refine_level2": stats.ms_level2, "points": stats.points,
+                       "refined_level1": stats.refined_level1, "refined_level2": stats.refined_level2},
+            "single_pass": {"value": single_value, "unit": "evals/s", "ms_per_step": single_ms,
+                            "note": "the FP32 pass alone (mixed_point_tol = 0): its per-point error is in "
+                                    "accuracy.single_pass"},
+            "accuracy": accuracy,
             "fp64_path": {"value": fp64_rate, "unit": "evals/s", "sample_points": ns,
-                          "speedup_mixed_over_fp64": value / world / fp64_rate,
+                          "speedup_refined_over_fp64": value / world / fp64_rate,
                           "roofline": {"bound": "fp64",
                                        "achieved": fp64_rate * R.FP64_INST_PER_PAIR / 1e12,
-                                       "peak": R.fp64_peak_inst(peaks.get("sm_max_mhz", 2070.0)) / 1e12,
+                                       "peak": R.fp64_peak_inst(sm_max) / 1e12,
                                        "unit": "T FP64 instructions/s",
-                                       "frac": fp64_rate * R.FP64_INST_PER_PAIR
-                                       / R.fp64_peak_inst(peaks.get("sm_max_mhz", 2070.0)),
+                                       "frac": fp64_rate * R.FP64_INST_PER_PAIR / R.fp64_peak_inst(sm_max),
                                        "note": "278 FP64 instructions per pair (ncu count); peak = 152 SMs x "
                                                "2 FP64 instructions per clock x max SM clock"}},
-            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
-                         "frac": achieved / peak_ops,
-                         "mufu": {"achieved": counts["nodes"] * (npts / CHECK_SAMPLE) / (ms * 1e-3) / 1e12,
-                                  "peak": R.mufu_peak(peaks.get("sm_max_mhz", 2070.0)) / 1e12,
-                                  "unit": "T rsqrt/s",
-                                  "frac": counts["nodes"] * (npts / CHECK_SAMPLE) / (ms * 1e-3)
-                                  / R.mufu_peak(peaks.get("sm_max_mhz", 2070.0))},
-                         "traffic": FAR_TRAFFIC_BYTES_1E6 if npts == N_POINTS else None,
-                         "note": "FP32 lane ops (Gauss nodes x 13 + pairs x 12) per launch / event time; peak = "
-                                 "152 SMs x 128 lanes x max SM clock; traffic = DRAM bytes per far-kernel launch "
-                                 "(ncu, 1e6 points)"},
+            "roofline": {"bound": "alu", "kernel": "k_eval_acc_far<1> (first refinement level, two-float)",
+                         "achieved": ach_l1 / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                         "frac": ach_l1 / peak_ops, "traffic": None,
+                         "note": "FP32 lane operations counted from the code (roofline.ACC1_*) x the refined "
+                                 "points' pair and node counts / the level's event time (flag step and FP64 near "
+                                 "pairs included); peak = 152 SMs x 128 lanes x max SM clock (unit counts); "
+                                 "traffic: no capture of this kernel version",
+                         "fp32_pass": {"kernel": "k_eval_far", "achieved": ach_fp32 / 1e12,
+                                       "frac": ach_fp32 / peak_ops,
+                                       "mufu_frac": counts["nodes"] * (npts / CHECK_SAMPLE) / (stats.ms_fp32 * 1e-3)
+                                       / R.mufu_peak(sm_max)}},
             "tiers": counts,
+            "tiers_refined": counts_l1,
             "solve_thgem": solve,
             "serving": serving,
             "e2e": {"value": e2e_val, "unit": "evals/s", "h2d_bytes_per_step": int(pts_pin.numel() * 8),
                     "d2h_bytes_per_step": int((phi_pin.numel() + E_pin.numel()) * 8)},
             "cpu_baseline": cpu,
-            "gpu_launches": 5 * args.steps,  # k_bin_keys, k_bin_scan, k_bin_scatter, k_eval_far, k_eval_near per step
+            # per step: k_bin_keys, k_bin_scan, k_bin_scatter, k_eval_far, k_eval_near, then
+            # k_flag + k_eval_acc_far + near per refinement level
+            "gpu_launches": 11 * args.steps,
             "clocks": clocks,
             "wall_s_timed_region": wall,
         }
@@ -408,6 +457,7 @@ def run_native(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+    single.close()
     ctx.close()
     return 0
 

@@ -251,15 +251,17 @@ int nebem_eval_device(nebem_ctx *ctx, const double *d_pts, int64_t n, double *d_
  * ratio measured against the FP64 path (a statistical estimate, not a bound).  A point
  * whose estimate exceeds mixed_point_tol times its
  * |phi| or |E| (context option, default 1e-6) is evaluated again in two-float arithmetic
- * (Gauss rules truncated below ~3e-12 of each pair, FP64 closed forms within 6 element
- * radii); its estimate becomes 1e-11 B.  nebem_eval / nebem_eval_device with NEBEM_MIXED
+ * (about 44 bits): first with the same Gauss rules and FP64 near pairs (estimate 1e-9 B),
+ * and where that estimate still exceeds the tolerance, with rules truncated below ~3e-12 of
+ * each pair and FP64 closed forms within 6 element radii (estimate 1e-11 B).
+ * nebem_eval / nebem_eval_device with NEBEM_MIXED
  * apply the same refinement; these calls also return the estimates.
  *   pts / d_pts  n x 3 points (host memory, copied / device memory).
  *   phi, E       outputs as in nebem_eval (either may be NULL; a NULL output is not used
  *                to decide the refinement).
  *   err / d_err  n x 2 output: estimated absolute error of phi and of |E| per point; may be
  *                NULL (then nothing is written).
- *   n_refined    (host variant, may be NULL) number of points evaluated again.
+ *   n_refined    (host variant, may be NULL) number of points evaluated again (first level).
  *   stream       as in nebem_eval_device (asynchronous, device pointers).
  * Known charges (nebem_space_charge) are added after the refinement, in their own
  * precision; their sum is not part of the estimate.  Not available with Adaptive
@@ -268,6 +270,24 @@ int nebem_eval_err(nebem_ctx *ctx, const double *pts, int64_t n, double *phi, do
                    int64_t *n_refined);
 int nebem_eval_device_err(nebem_ctx *ctx, const double *d_pts, int64_t n, double *d_phi, double *d_E, double *d_err,
                           void *stream);
+
+/* Stage report of the last mixed evaluation of this context that ran without Adaptive
+ * Modelling (nebem_eval, nebem_eval_device, nebem_eval_err and friends; a library utility
+ * with no counterpart in the paper).  Waits for that evaluation to finish.  Device times
+ * (ms, CUDA events on the evaluation's stream) of the FP32 pass (binning, far tiers, FP64
+ * near pairs), of the flag step plus the first two-float level, and of the second flag
+ * step plus the second level; point counts of the evaluation and of both levels.
+ * Errors: NEBEM_INVALID_ARG (NULL), NEBEM_BAD_STATE (no such evaluation yet), NEBEM_CUDA. */
+typedef struct nebem_eval_stats_t {
+    int64_t points;
+    int64_t refined_level1;
+    int64_t refined_level2;
+    double ms_fp32;
+    double ms_level1;
+    double ms_level2;
+    double reserved[4];
+} nebem_eval_stats_t;
+int nebem_eval_stats(nebem_ctx *ctx, nebem_eval_stats_t *out);
 
 /* Set the known-charge set (Sec. 4.2 OptKnCh; Alg. 4 UpdateSpaceCharge): n point
  * carriers at pos[n][3] (m) with charges q[n] (C), Plummer softening `softening` (m,

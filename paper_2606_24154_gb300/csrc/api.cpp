@@ -59,6 +59,8 @@ Ctx::~Ctx() {
     cudaSetDevice(device);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
+    for (cudaEvent_t e : ev_eval)
+        if (e) cudaEventDestroy(e);
     if (stream) cudaStreamDestroy(stream);
 }
 
@@ -138,6 +140,7 @@ int nebem_create(nebem_ctx** out, const nebem_options* opt) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&c->ev1);
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev_eval[k]);
     if (e == cudaSuccess) e = cudaGetDeviceProperties(&c->props, c->device);
     if (e != cudaSuccess) {
         delete c;
@@ -415,6 +418,26 @@ int nebem_eval_err(nebem_ctx* ctx, const double* pts, int64_t n, double* phi, do
     if (err) CK(cudaMemcpyAsync(err, c->d_err.ptr, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (n_refined) *n_refined = h_ref;
+    return NEBEM_OK;
+}
+
+int nebem_eval_stats(nebem_ctx* ctx, nebem_eval_stats_t* out) {
+    if (!ctx || !out) return fail(NEBEM_INVALID_ARG, "NULL argument");
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (!c->eval_timed || !c->refine_list) return fail(NEBEM_BAD_STATE, "no plain mixed evaluation yet");
+    CK(cudaSetDevice(c->device));
+    CK(cudaEventSynchronize(c->ev_eval[3]));
+    float t[3] = {0.f, 0.f, 0.f};
+    for (int k = 0; k < 3; ++k) CK(cudaEventElapsedTime(&t[k], c->ev_eval[k], c->ev_eval[k + 1]));
+    int32_t n2[2] = {0, 0};
+    CK(cudaMemcpy(n2, c->refine_list, sizeof(n2), cudaMemcpyDeviceToHost));
+    std::memset(out, 0, sizeof(*out));
+    out->points = c->eval_points_n;
+    out->refined_level1 = n2[0];
+    out->refined_level2 = n2[1];
+    out->ms_fp32 = t[0];
+    out->ms_level1 = t[1];
+    out->ms_level2 = t[2];
     return NEBEM_OK;
 }
 

@@ -45,6 +45,10 @@ struct Ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // stage times of the last plain mixed evaluation (FP32 pass, refinement levels 1 and 2)
+    cudaEvent_t ev_eval[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool eval_timed = false;
+    int64_t eval_points_n = 0;
     cudaDeviceProp props{};
 
     // geometry

@@ -16,11 +16,14 @@
 // The estimate is statistical, not a bound: rounding errors of many pairs add up like a
 // random sum whose ratio to B spreads about fivefold between its median and its maximum.
 //
-// Refinement.  A point is re-evaluated when gamma B_phi > tol |phi| or gamma B_E > tol |E|.
-// The re-evaluation uses the arithmetic of the mixed fill (fill_mixed.cu): Gauss rules
-// whose truncation stays below ~3e-12 of the pair (tiers kFillRatioA / B / C) in two-float
-// arithmetic (about 44 bits) for pairs at >= kFillRatioC element radii, and the FP64
-// closed form (influence.cuh) for nearer pairs.  Its estimate is 1e-11 B.  In the frame of
+// Refinement.  A point is re-evaluated when gamma B_phi > tol |phi| or gamma B_E > tol |E|,
+// in two-float arithmetic (about 44 bits; the error-free transformations of twofloat.cuh),
+// in two levels.  Level 1 keeps the FP32 pass's Gauss rules and tiers and its FP64 near
+// pairs: their truncation, measured against the closed forms on THGEM points, stays below
+// ~2e-10 of B, so its estimate is 1e-9 B.  Points whose level-1 estimate still exceeds the
+// tolerance go to level 2, the rules of the mixed fill (fill_mixed.cu: truncation below
+// ~3e-12 of each pair, FP64 closed forms within kFillRatioC element radii), estimate
+// 1e-11 B.  In the frame of
 // element j (axes ex, ey = normal, ez), a pair (point, image k) has D = P - c_j - t_k with
 // local components X = (P - c_j) . ex - tau_k.x (likewise Y, Z; tau tabulated per element
 // and image); a node at offset s = centroid - node (in the element plane) sees the point at
@@ -38,7 +41,8 @@ namespace {
 constexpr int kAT = 128;             // threads (flagged points) per block
 constexpr double kGammaPhi = 1.5e-7; // FP32 pass: error of phi <= kGammaPhi * B_phi
 constexpr double kGammaE = 1.5e-7;   // FP32 pass: error of |E| <= kGammaE * B_E
-constexpr double kGammaAcc = 1e-11;  // two-float pass with fill-grade rules
+constexpr double kGammaL1 = 1e-9;    // two-float, the FP32 pass's rules (truncation ~1e-10 B)
+constexpr double kGammaL2 = 1e-11;   // two-float, fill-grade rules
 
 // Per-pair node sums S0 = sum w / r^3, S2x = sum w (2 s_x) / r^3, S2z = sum w (2 s_z) / r^3
 // as packed two-float values (hi, negated lo) over the two lanes of the node pairs.
@@ -122,18 +126,44 @@ __device__ __forceinline__ void df_fma_acc(float ah, float al, float bh, float b
     Sl = __fadd_rn(Sl, __fadd_rn(t2, l));
 }
 
-// dynamic shared memory per tile of te elements: FillEl (9 float4), tier-a nodes, tau and
-// image centroids (2 float4 each per image)
-__host__ __device__ constexpr int acc_tile_f4(int te, int nimg) { return te * (9 + 4 * kFillPairsA + 4 * nimg); }
+// Two levels of re-evaluation, both two-float: level 1 takes the tiers of the FP32 pass
+// (nb_internal.h FarNodes: 2x2 / 4-point, 3x3 / 6-point, 4x4, 6x6 rules at ratio_0, ratio_a,
+// ratio_b, ratio_near radii; FP64 closed forms nearer), whose truncation stays near 1e-10 of
+// B; level 2 takes the fill's tiers (truncation below ~3e-12 of each pair, FP64 within
+// kFillRatioC radii).  Staged in shared memory per element: the level's most frequent node
+// set (tier 0 for level 1, tier a for level 2) and, for level 1, the tier radii.
+template <int L>
+struct Level;
+template <>
+struct Level<1> {
+    static constexpr int kStaged = 4 * kFillPairs0;  // float4 of the staged node set
+    static constexpr int kStagedOff = kFillOff0;
+    static constexpr int kHdr = 1;                   // FarNodes radii per element
+};
+template <>
+struct Level<2> {
+    static constexpr int kStaged = 4 * kFillPairsA;
+    static constexpr int kStagedOff = 0;
+    static constexpr int kHdr = 0;
+};
 
-// Raw sums (before ke) of the far pairs (>= kFillRatioC radii) of one point over the
-// elements [e0, e1), with the error scales; all threads of the block take part (tiles).
+// dynamic shared memory per tile of te elements: FillEl (9 float4), the staged node set,
+// tau and image centroids (2 float4 each per image), the level-1 tier radii
+__host__ __device__ constexpr int acc_tile_f4(int te, int nimg, int staged, int hdr) {
+    return te * (9 + staged + 4 * nimg + hdr);
+}
+
+// Raw sums (before ke) of the far pairs of one point over the elements [e0, e1) at level L,
+// with the error scales; all threads of the block take part (tiles).
+template <int L>
 __device__ __forceinline__ Sum6 acc_range(const AccView& A, int nimg, int te, float4* sm, const float (&ph)[3],
                                           const float (&pl)[3], int64_t e0, int64_t e1) {
+    using Lv = Level<L>;
     FillEl* s_fe = reinterpret_cast<FillEl*>(sm);
     float4* s_na = sm + 9 * te;
-    float4* s_tau = s_na + 4 * kFillPairsA * te;
+    float4* s_tau = s_na + Lv::kStaged * te;
     float4* s_c = s_tau + 2 * nimg * te;
+    float4* s_hdr = s_c + 2 * nimg * te;
     Sum6 acc{0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (int64_t base = e0; base < e1; base += te) {
         const int cnt = (int)min((int64_t)te, e1 - base);
@@ -143,20 +173,24 @@ __device__ __forceinline__ Sum6 acc_range(const AccView& A, int nimg, int te, fl
             float4* dst = reinterpret_cast<float4*>(s_fe);
             for (int i = threadIdx.x; i < 9 * cnt; i += blockDim.x) dst[i] = src[i];
         }
-        for (int e = threadIdx.x; e < cnt * 4 * kFillPairsA; e += blockDim.x) {
-            const int jj = e / (4 * kFillPairsA), q = e - jj * 4 * kFillPairsA;
-            s_na[e] = A.nodes[(base + jj) * kFillNodeRec + q];
+        for (int e = threadIdx.x; e < cnt * Lv::kStaged; e += blockDim.x) {
+            const int jj = e / Lv::kStaged, q = e - jj * Lv::kStaged;
+            s_na[e] = A.nodes[(base + jj) * kFillNodeRec + Lv::kStagedOff + q];
         }
         for (int i = threadIdx.x; i < 2 * cnt * nimg; i += blockDim.x) {
             s_tau[i] = A.tau[2 * base * nimg + i];
             s_c[i] = A.cjk[2 * base * nimg + i];
         }
+        if (Lv::kHdr)
+            for (int i = threadIdx.x; i < cnt; i += blockDim.x) s_hdr[i] = A.far[base + i].hdr;
         __syncthreads();
         for (int jj = 0; jj < cnt; ++jj) {
             const FillEl& F = s_fe[jj];
             const int64_t j = base + jj;
-            const float4 hdr = F.hdr;
-            const int na = (int)hdr.w;
+            // squared tier radii, largest first, and the nearest (FP64) radius
+            const float4 hdr = Lv::kHdr ? s_hdr[jj] : F.hdr;
+            const float near2 = Lv::kHdr ? hdr.w : hdr.z;
+            const int na = (int)F.hdr.w;
             float dh[3], dl[3];
             df_sub(ph[0], pl[0], F.ch.x, F.cl.x, dh[0], dl[0]);
             df_sub(ph[1], pl[1], F.ch.y, F.cl.y, dh[1], dl[1]);
@@ -171,7 +205,7 @@ __device__ __forceinline__ Sum6 acc_range(const AccView& A, int nimg, int te, fl
                 float dx, dy, dz;
                 const float d2 = pair_d2(ph[0], ph[1], ph[2], pl[0], pl[1], pl[2], s_c[2 * (jj * nimg + k)],
                                          s_c[2 * (jj * nimg + k) + 1], dx, dy, dz);
-                if (!(d2 >= hdr.z)) continue;  // near pair: k_eval_acc_near
+                if (!(d2 >= near2)) continue;  // near pair: the level's FP64 kernel
                 const float4 th = s_tau[2 * (jj * nimg + k)], tl = s_tau[2 * (jj * nimg + k) + 1];
                 float xh, xl, yh, yl, zh, zl, d2h, d2l;
                 df_sub(x0h, x0l, th.x, tl.x, xh, xl);
@@ -184,10 +218,13 @@ __device__ __forceinline__ Sum6 acc_range(const AccView& A, int nimg, int te, fl
                 P.d2h = bc2(d2h), P.d2l = bc2(d2l);
                 const float4* nd;
                 int np;
-                if (d2 >= hdr.x) {
-                    nd = s_na + jj * 4 * kFillPairsA;
+                if (d2 >= hdr.x) {  // the staged set
+                    nd = s_na + jj * Lv::kStaged;
+                    np = (L == 1) ? kFillPairs0 : na;
+                } else if (L == 1 && d2 >= hdr.y) {
+                    nd = A.nodes + j * kFillNodeRec;
                     np = na;
-                } else if (d2 >= hdr.y) {
+                } else if (d2 >= (L == 1 ? hdr.z : hdr.y)) {
                     nd = A.nodes + j * kFillNodeRec + kFillOffB;
                     np = kFillPairsB;
                 } else {
@@ -223,15 +260,18 @@ __device__ __forceinline__ Sum6 acc_range(const AccView& A, int nimg, int te, fl
     return acc;
 }
 
-// Far part of every listed point (thread per point, blocks striding over the list of
-// *n_list points): writes ke * sum to phi / E and the refined estimate to err.
+// Far part of every listed point at level L (thread per point, blocks striding over the
+// list of *n_list points): writes ke * sum to phi / E, the level's estimate to err, and
+// (level 1) ke * (B_phi, B_E) to bound for the next flag step.
+template <int L>
 __global__ void __launch_bounds__(kAT, 3)
     k_eval_acc_far(const AccView A, int nimg, int te, const double* __restrict__ pts,
                    const int32_t* __restrict__ list, const int32_t* __restrict__ n_list, double* __restrict__ phi,
-                   double* __restrict__ E, double* __restrict__ err) {
+                   double* __restrict__ E, double* __restrict__ err, float2* __restrict__ bound) {
     extern __shared__ float4 sm[];
     const int64_t count = *n_list;
     const double ke = 1.0 / (4.0 * kPi * kEps0);
+    const double gamma = (L == 1) ? kGammaL1 : kGammaL2;
     for (int64_t base = (int64_t)blockIdx.x * kAT; base < count; base += (int64_t)gridDim.x * kAT) {
         const bool active = base + threadIdx.x < count;
         const int64_t p = active ? (int64_t)list[base + threadIdx.x] : 0;
@@ -239,7 +279,7 @@ __global__ void __launch_bounds__(kAT, 3)
         load_point_2f(pts, p, active, ph[0], ph[1], ph[2], pl[0], pl[1], pl[2]);
         Sum6 tot{0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         for (int64_t e0 = 0; e0 < A.n_el; e0 += kChunkEl)
-            add6(tot, acc_range(A, nimg, te, sm, ph, pl, e0, min(e0 + (int64_t)kChunkEl, A.n_el)));
+            add6(tot, acc_range<L>(A, nimg, te, sm, ph, pl, e0, min(e0 + (int64_t)kChunkEl, A.n_el)));
         if (active) {
             if (phi) phi[p] = ke * tot.phi;
             if (E) {
@@ -248,15 +288,74 @@ __global__ void __launch_bounds__(kAT, 3)
                 E[3 * p + 2] = ke * tot.z;
             }
             if (err) {
-                err[2 * p] = kGammaAcc * ke * tot.bphi;
-                err[2 * p + 1] = kGammaAcc * ke * tot.bE;
+                err[2 * p] = gamma * ke * tot.bphi;
+                err[2 * p + 1] = gamma * ke * tot.bE;
             }
+            if (L == 1) bound[p] = make_float2((float)(ke * tot.bphi), (float)(ke * tot.bE));
         }
     }
 }
 
-// Near part (FP64 closed forms of the pairs nearer than kFillRatioC radii, found through
-// the fill's cell list) of every listed point; adds ke * sum to phi / E.
+// The same far sums split over element chunks, for a few points spread over many CTAs:
+// block (bx, chunk) writes the chunk's Sum6 of its listed points to part[(chunk * cap + i)]
+// (i = list position); k_acc_reduce then adds the chunks in order, which is the order
+// k_eval_acc_far adds them in, so a point gets the same bits either way.
+template <int L>
+__global__ void __launch_bounds__(kAT, 3)
+    k_eval_acc_far_chunk(const AccView A, int nimg, int te, const double* __restrict__ pts,
+                         const int32_t* __restrict__ list, const int32_t* __restrict__ n_list, int64_t cap,
+                         Sum6* __restrict__ part) {
+    extern __shared__ float4 sm[];
+    const int64_t count = *n_list;
+    const int64_t base = (int64_t)blockIdx.x * kAT;
+    if (base >= count) return;  // whole block: no barrier is skipped by part of it
+    const bool active = base + threadIdx.x < count;
+    const int64_t p = active ? (int64_t)list[base + threadIdx.x] : 0;
+    float ph[3], pl[3];
+    load_point_2f(pts, p, active, ph[0], ph[1], ph[2], pl[0], pl[1], pl[2]);
+    const int64_t e0 = (int64_t)blockIdx.y * kChunkEl;
+    const Sum6 c = acc_range<L>(A, nimg, te, sm, ph, pl, e0, min(e0 + (int64_t)kChunkEl, A.n_el));
+    if (active) part[(int64_t)blockIdx.y * cap + base + threadIdx.x] = c;
+}
+
+template <int L>
+__global__ void __launch_bounds__(256)
+    k_acc_reduce(const int32_t* __restrict__ list, const int32_t* __restrict__ n_list, int64_t cap, int nchunks,
+                 const Sum6* __restrict__ part, double* __restrict__ phi, double* __restrict__ E,
+                 double* __restrict__ err, float2* __restrict__ bound) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= *n_list) return;
+    const int64_t p = list[i];
+    Sum6 tot{0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < nchunks; ++k) add6(tot, part[(int64_t)k * cap + i]);
+    const double ke = 1.0 / (4.0 * kPi * kEps0);
+    const double gamma = (L == 1) ? kGammaL1 : kGammaL2;
+    if (phi) phi[p] = ke * tot.phi;
+    if (E) {
+        E[3 * p] = ke * tot.x;
+        E[3 * p + 1] = ke * tot.y;
+        E[3 * p + 2] = ke * tot.z;
+    }
+    if (err) {
+        err[2 * p] = gamma * ke * tot.bphi;
+        err[2 * p + 1] = gamma * ke * tot.bE;
+    }
+    if (L == 1) bound[p] = make_float2((float)(ke * tot.bphi), (float)(ke * tot.bE));
+}
+
+// Level-1 near part: the FP64 closed forms of the pairs nearer than ratio_near radii, as the
+// FP32 pass adds them (near_point, its cell list); adds ke * sum to phi / E.
+__global__ void __launch_bounds__(kEvalThreads)
+    k_eval_acc_near1(const GeomView g, const ImageTable img, const double* __restrict__ pts,
+                     const int32_t* __restrict__ list, const int32_t* __restrict__ n_list, double* __restrict__ phi,
+                     double* __restrict__ E) {
+    const int64_t count = *n_list;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        near_point(g, img, pts, list[i], phi, E);
+}
+
+// Level-2 near part (FP64 closed forms of the pairs nearer than kFillRatioC radii, found
+// through the fill's cell list) of every listed point; adds ke * sum to phi / E.
 __global__ void __launch_bounds__(128)
     k_eval_acc_near(const AccView A, const ImageTable img, const double* __restrict__ pts,
                     const int32_t* __restrict__ list, const int32_t* __restrict__ n_list, double* __restrict__ phi,
@@ -292,7 +391,7 @@ __global__ void __launch_bounds__(128)
                         float dx, dy, dz;
                         const float d2 = pair_d2(phx, phy, phz, plx, ply, plz, A.cjk[2 * (int64_t)jk],
                                                  A.cjk[2 * (int64_t)jk + 1], dx, dy, dz);
-                        if (!(d2 < A.fe[j].hdr.z)) continue;  // far pair: k_eval_acc_far
+                        if (!(d2 < A.fe[j].hdr.z)) continue;  // far pair: k_eval_acc_far<2>
                         const Elem& e = A.el[j];
                         double f, ux, uy, uz;
                         elem_local_f64(e, Px - img.t[k][0], Py - img.t[k][1], Pz - img.t[k][2], false, f, ux, uy, uz);
@@ -312,21 +411,24 @@ __global__ void __launch_bounds__(128)
     }
 }
 
-// Flags and lists (in binned order within each block) the points whose FP32-pass estimate
-// exceeds tol times |phi| or |E| (refine != 0), and writes every point's estimate to err.
+// Flags and lists (in their input order within each block) the points whose estimate
+// gamma * bound exceeds tol times |phi| or |E| (when refine != 0).  Input: order[i] (or i
+// when order is null) for i < n, or i < *n_dev when n_dev is given.  err (may be null)
+// receives every input point's estimate.
 __global__ void __launch_bounds__(256)
     k_flag(const double* __restrict__ phi, const double* __restrict__ E, const float2* __restrict__ bound,
-           const int32_t* __restrict__ order, int64_t n, double tol, int refine, double* __restrict__ err,
-           int32_t* __restrict__ list, int32_t* __restrict__ n_list) {
+           const int32_t* __restrict__ order, int64_t n, const int32_t* __restrict__ n_dev, double gphi, double gE,
+           double tol, int refine, double* __restrict__ err, int32_t* __restrict__ list, int32_t* __restrict__ n_list) {
     __shared__ int32_t s_warp[8];
     __shared__ int32_t s_base;
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const int64_t count = n_dev ? (int64_t)*n_dev : n;
     bool f = false;
     int32_t p = 0;
-    if (i < n) {
+    if (i < count) {
         p = order ? order[i] : (int32_t)i;
         const float2 b = bound[p];
-        const double ep = kGammaPhi * (double)b.x, eE = kGammaE * (double)b.y;
+        const double ep = gphi * (double)b.x, eE = gE * (double)b.y;
         if (phi && ep > tol * fabs(phi[p])) f = true;
         if (E) {
             const double ex = E[3 * p], ey = E[3 * p + 1], ez = E[3 * p + 2];
@@ -355,34 +457,75 @@ __global__ void __launch_bounds__(256)
     if (f) list[s_base + s_warp[w] + __popc(ballot & ((1u << lane) - 1u))] = p;
 }
 
-}  // namespace
-
-cudaError_t launch_eval_refine(const AccView& A, const ImageTable& img, const double* pts, int64_t npts,
-                               double* phi, double* E, double* err, double tol, const MixedScratch& ms, int sms,
-                               cudaStream_t s) {
-    if (npts == 0) return cudaSuccess;
-    if (npts > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
-    const bool refine = tol > 0.0 && (phi || E);
-    cudaError_t e = cudaMemsetAsync(ms.n_list, 0, sizeof(int32_t), s);
-    if (e != cudaSuccess) return e;
-    k_flag<<<(unsigned)((npts + 255) / 256), 256, 0, s>>>(phi, E, ms.bound, ms.order, npts, tol, refine ? 1 : 0, err,
-                                                         ms.list, ms.n_list);
-    e = cudaGetLastError();
-    if (e != cudaSuccess || !refine) return e;
+template <int L>
+cudaError_t launch_level(const AccView& A, const ImageTable& img, const double* pts, int64_t npts, double* phi,
+                         double* E, double* err, float2* bound, const int32_t* list, const int32_t* n_list, int sms,
+                         Sum6* part, cudaStream_t s) {
+    using Lv = Level<L>;
     // element tile: a power of two (divides the chunk width), at most 16, within ~40 KB
     int te = 16;
-    while (te > 1 && acc_tile_f4(te, img.n) * (int)sizeof(float4) > 40 * 1024) te /= 2;
-    const size_t smem = (size_t)acc_tile_f4(te, img.n) * sizeof(float4);
-    e = cudaFuncSetAttribute(k_eval_acc_far, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    while (te > 1 && acc_tile_f4(te, img.n, Lv::kStaged, Lv::kHdr) * (int)sizeof(float4) > 40 * 1024) te /= 2;
+    const size_t smem = (size_t)acc_tile_f4(te, img.n, Lv::kStaged, Lv::kHdr) * sizeof(float4);
     const int64_t want = (npts + kAT - 1) / kAT;
-    const unsigned gf = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 3 * (int64_t)sms));
-    k_eval_acc_far<<<gf, kAT, smem, s>>>(A, img.n, te, pts, ms.list, ms.n_list, phi, E, err);
+    cudaError_t e;
+    if (part) {  // split over element chunks (a few points)
+        e = cudaFuncSetAttribute(k_eval_acc_far_chunk<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const int nch = (int)((A.n_el + kChunkEl - 1) / kChunkEl);
+        k_eval_acc_far_chunk<L><<<dim3((unsigned)want, (unsigned)nch), kAT, smem, s>>>(A, img.n, te, pts, list, n_list,
+                                                                                       npts, part);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_acc_reduce<L><<<(unsigned)((npts + 255) / 256), 256, 0, s>>>(list, n_list, npts, nch, part, phi, E, err,
+                                                                         bound);
+    } else {
+        e = cudaFuncSetAttribute(k_eval_acc_far<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const unsigned gf = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 3 * (int64_t)sms));
+        k_eval_acc_far<L><<<gf, kAT, smem, s>>>(A, img.n, te, pts, list, n_list, phi, E, err, bound);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const unsigned gn = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 8 * (int64_t)sms));
-    k_eval_acc_near<<<gn, 128, 0, s>>>(A, img, pts, ms.list, ms.n_list, phi, E);
+    if (L == 1)
+        k_eval_acc_near1<<<gn, kEvalThreads, 0, s>>>(A.view, img, pts, list, n_list, phi, E);
+    else
+        k_eval_acc_near<<<gn, 128, 0, s>>>(A, img, pts, list, n_list, phi, E);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t refine_chunk_bytes(int64_t npts, int64_t n_el) {
+    return sizeof(Sum6) * (size_t)npts * (size_t)((n_el + kChunkEl - 1) / kChunkEl);
+}
+
+cudaError_t launch_eval_refine(const AccView& A, const ImageTable& img, const double* pts, int64_t npts,
+                               double* phi, double* E, double* err, double tol, const MixedScratch& ms, int sms,
+                               cudaStream_t s, cudaEvent_t* ev, void* chunk_part) {
+    Sum6* part = static_cast<Sum6*>(chunk_part);
+    if (npts == 0) return cudaSuccess;
+    if (npts > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
+    const bool refine = tol > 0.0 && (phi || E);
+    cudaError_t e = cudaMemsetAsync(ms.n_list, 0, 2 * sizeof(int32_t), s);  // both levels' counts
+    if (e != cudaSuccess) return e;
+    const unsigned fb = (unsigned)((npts + 255) / 256);
+    k_flag<<<fb, 256, 0, s>>>(phi, E, ms.bound, ms.order, npts, nullptr, kGammaPhi, kGammaE, tol, refine ? 1 : 0, err,
+                              ms.list, ms.n_list);
+    e = cudaGetLastError();
+    if (e == cudaSuccess && refine)  // level 1 on the flagged points; it leaves their level-1 scales in ms.bound
+        e = launch_level<1>(A, img, pts, npts, phi, E, err, ms.bound, ms.list, ms.n_list, sms, part, s);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], s);
+    if (e == cudaSuccess && refine) {
+        // level 2 on the points whose level-1 estimate still exceeds the tolerance
+        k_flag<<<fb, 256, 0, s>>>(phi, E, ms.bound, ms.list, npts, ms.n_list, kGammaL1, kGammaL1, tol, 1, nullptr,
+                                  ms.list2, ms.n_list + 1);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = launch_level<2>(A, img, pts, npts, phi, E, err, nullptr, ms.list2, ms.n_list + 1, sms, part, s);
+    }
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
+    return e;
 }
 
 }  // namespace nb

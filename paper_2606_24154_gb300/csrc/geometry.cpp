@@ -383,6 +383,7 @@ void build_fill_tables(const std::vector<Elem>& el, const ImageTable& img, std::
             n_a = tensor(3, out);
             tensor(4, out + kFillOffB);
             tensor(6, out + kFillOffC);
+            tensor(2, out + kFillOff0);
         } else {
             const double area = 0.5 * e.twoA[0];
             cnt = 0;
@@ -412,6 +413,14 @@ void build_fill_tables(const std::vector<Elem>& el, const ImageTable& img, std::
             };
             collapsed(4, out + kFillOffB);
             collapsed(6, out + kFillOffC);
+            // degree-3 four-point rule (tier 0 of the mixed evaluation)
+            cnt = 0;
+            for (int q = 0; q < 4; ++q) {
+                const double px = kTri3B[q][0] * qx[0] + kTri3B[q][1] * qx[1] + kTri3B[q][2] * qx[2];
+                const double pz = kTri3B[q][0] * qz[0] + kTri3B[q][1] * qz[1] + kTri3B[q][2] * qz[2];
+                put(px, pz, kTri3W[q] * area);
+            }
+            pack_fill_pairs(nd, cnt, out + kFillOff0);
         }
         r.hdr = f4((float)(ra * ra), (float)(rb * rb), (float)(rc * rc), (float)n_a);
         for (int k = 0; k < m; ++k) {

@@ -82,9 +82,13 @@ constexpr double kFillRatioC = 6.0;
 constexpr int kFillPairsA = 5;  // capacity (3 used by triangles)
 constexpr int kFillPairsB = 8;
 constexpr int kFillPairsC = 18;
-constexpr int kFillNodeRec = 4 * (kFillPairsA + kFillPairsB + kFillPairsC);  // float4 per element
+// tier 0 of the mixed evaluation (2x2 / 4-point rule) in the same two-float form, appended
+// for the two-float re-evaluation of eval_acc.cu (the fill does not use it)
+constexpr int kFillPairs0 = 2;
 constexpr int kFillOffB = 4 * kFillPairsA;
 constexpr int kFillOffC = 4 * (kFillPairsA + kFillPairsB);
+constexpr int kFillOff0 = 4 * (kFillPairsA + kFillPairsB + kFillPairsC);
+constexpr int kFillNodeRec = kFillOff0 + 4 * kFillPairs0;  // float4 per element
 // Per element: centroid c and frame (ex, ey, ez) as hi + lo floats; hdr = squared tier
 // distances (a, b, c) in m^2 and the tier-a node-pair count.
 struct __align__(16) FillEl {
@@ -138,8 +142,9 @@ struct MixedScratch {
     int32_t* key;    // npts
     int32_t* order;  // npts
     float2* bound;   // npts
-    int32_t* list;   // npts
-    int32_t* n_list; // 1
+    int32_t* list;   // npts: points of the first refinement level
+    int32_t* list2;  // npts: points of the second level
+    int32_t* n_list; // 2: the two lists' lengths
 };
 MixedScratch mixed_scratch(void* base, int64_t npts);
 // scratch bytes a mixed evaluation (FP32 pass and refinement) needs for npts points
@@ -153,7 +158,9 @@ cudaError_t launch_eval_mixed(const Elem* el, const FarNodes* far, const float4*
 // tau = t_k . frame, two-float image centroids, and the cell list with the near radius
 // kFillRatioC rho.
 struct AccView {
+    GeomView view;  // the FP32 pass's tables (tier radii, near cell list) for the first level
     const Elem* el;
+    const FarNodes* far;
     const FillEl* fe;
     const float4* nodes;
     const float4* tau;
@@ -166,11 +173,15 @@ struct AccView {
 };
 // Refinement after launch_eval_mixed: every point whose estimated error (gamma * bound)
 // exceeds tol times its |phi| or |E| is re-evaluated in two-float arithmetic with FP64 near
-// pairs (eval_acc.cu); err (may be NULL, n x 2) receives the estimated absolute error of
-// phi and |E| of every point.  sms = multiprocessors of the device.
+// pairs, in two levels (eval_acc.cu); err (may be NULL, n x 2) receives the estimated
+// absolute error of phi and |E| of every point.  sms = multiprocessors of the device.
+// ev (may be NULL): two events recorded after the first and after the second level.
+// chunk_part (may be NULL): refine_chunk_bytes(npts, n_el) bytes of partial sums; when
+// given, each level is split over element chunks (more CTAs for a few points; same bits).
 cudaError_t launch_eval_refine(const AccView& A, const ImageTable& img, const double* pts, int64_t npts,
                                double* phi, double* E, double* err, double tol, const MixedScratch& ms, int sms,
-                               cudaStream_t s);
+                               cudaStream_t s, cudaEvent_t* ev = nullptr, void* chunk_part = nullptr);
+size_t refine_chunk_bytes(int64_t npts, int64_t n_el);
 cudaError_t launch_pair_tiers(const FarNodes* far, const float4* cjk, int64_t n_el, int nimg, const double* pts,
                               int64_t npts, uint8_t* codes, cudaStream_t s);
 cudaError_t launch_image_centroids(const Elem* el, int64_t n, const ImageTable& img, float4* cjk, cudaStream_t s);

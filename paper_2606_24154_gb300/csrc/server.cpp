@@ -20,6 +20,7 @@
 //
 // The server is driven from the caller's thread: submit, poll and wait each run one
 // round of completion -> admission -> launch.  Calls on one server must be serialised.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <cstring>
@@ -112,7 +113,9 @@ struct Server {
     std::vector<cudaEvent_t> refine_done;  // per slot
     bool kernel_launched = false;
     DevBuf d_geoms, d_pts, d_phi, d_E, d_head, d_remaining, d_partials, d_pcount;
-    DevBuf d_bound, d_list, d_nlist;  // refinement: error scales, flagged lists (arena index), counts per slot
+    DevBuf d_rpart;                           // refinement partial sums of a small request
+    DevBuf d_bound, d_list, d_list2, d_nlist;  // refinement: error scales, the two levels' lists (arena
+                                               // index), their counts (two per slot)
     std::vector<int32_t> nchunks;  // element chunks per geometry
     int32_t max_chunks = 1;
     std::vector<int32_t> free_pblocks;
@@ -157,6 +160,9 @@ struct Server {
     int launch_refine(Request* r) {
         Ctx* c = ctxs[r->geom];
         AccView A;
+        A.view = make_view(c->d_el.as<Elem>(), c->d_far.as<FarNodes>(), c->d_cjk.as<float4>(), c->d_sigma.as<double>(),
+                           c->n, c->img, c->grid, c->d_cell_start.as<int32_t>(), c->d_cell_items.as<int32_t>());
+        A.far = c->d_far.as<FarNodes>();
         A.el = c->d_el.as<Elem>();
         A.fe = c->d_fill_el.as<FillEl>();
         A.nodes = c->d_fill_nodes.as<float4>();
@@ -171,11 +177,16 @@ struct Server {
         ms.order = nullptr;
         ms.bound = d_bound.as<float2>() + r->offset;
         ms.list = d_list.as<int32_t>() + r->offset;
-        ms.n_list = d_nlist.as<int32_t>() + r->slot;
+        ms.list2 = d_list2.as<int32_t>() + r->offset;
+        ms.n_list = d_nlist.as<int32_t>() + 2 * r->slot;
+        // a small request's re-evaluation is split over element chunks, so that its few points
+        // still spread over many CTAs (same bits; the refine stream runs one request at a time,
+        // so one partial-sum area serves them all)
+        void* part = (r->n <= kSmallPoints) ? d_rpart.ptr : nullptr;
         CK(launch_eval_refine(A, c->img, d_pts.as<double>() + 3 * r->offset, r->n,
                               r->phi ? d_phi.as<double>() + r->offset : nullptr,
                               r->E ? d_E.as<double>() + 3 * r->offset : nullptr, nullptr, c->opt.mixed_point_tol, ms,
-                              c->props.multiProcessorCount, refine));
+                              c->props.multiProcessorCount, refine, nullptr, part));
         CK(cudaEventRecord(refine_done[r->slot], refine));
         return 0;
     }
@@ -373,6 +384,8 @@ int nebem_server_create(nebem_server** out, nebem_ctx* const* ctxs, int32_t n_ct
         geoms.push_back(make_serve_geom(c->d_el.as<Elem>(), c->d_far.as<FarNodes>(), c->d_cjk.as<float4>(),
                                         c->d_sigma.as<double>(), c->n, c->img, c->grid,
                                         c->d_cell_start.as<int32_t>(), c->d_cell_items.as<int32_t>()));
+    int64_t max_el = 1;
+    for (Ctx* c : cs) max_el = std::max<int64_t>(max_el, c->n);
     for (Ctx* c : cs) {
         const int32_t nc = (int32_t)((c->n + kChunkElements - 1) / kChunkElements);
         s->nchunks.push_back(nc);
@@ -390,7 +403,9 @@ int nebem_server_create(nebem_server** out, nebem_ctx* const* ctxs, int32_t n_ct
                                   s->max_chunks)) != cudaSuccess ||
         (e = s->d_bound.ensure(sizeof(float2) * cap)) != cudaSuccess ||
         (e = s->d_list.ensure(sizeof(int32_t) * cap)) != cudaSuccess ||
-        (e = s->d_nlist.ensure(sizeof(int32_t) * o.max_requests)) != cudaSuccess ||
+        (e = s->d_list2.ensure(sizeof(int32_t) * cap)) != cudaSuccess ||
+        (e = s->d_rpart.ensure(refine_chunk_bytes(std::min<int64_t>(kSmallPoints, cap), max_el))) != cudaSuccess ||
+        (e = s->d_nlist.ensure(2 * sizeof(int32_t) * o.max_requests)) != cudaSuccess ||
         (e = s->d_pcount.ensure(sizeof(int) * kPartialBlocks)) != cudaSuccess)
         return bail(cuda_fail(e, "server device buffers"));
     if ((e = cudaHostAlloc(&s->h_ring, sizeof(WorkItem) * s->ring_cap, cudaHostAllocMapped)) != cudaSuccess ||

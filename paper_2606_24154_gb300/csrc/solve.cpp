@@ -227,11 +227,18 @@ int eval_elements(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double*
         }
         CK(c->d_scratch.ensure(eval_mixed_scratch_bytes(n)));
         const MixedScratch ms = mixed_scratch(c->d_scratch.ptr, n);
+        c->eval_timed = false;
+        CK(cudaEventRecord(c->ev_eval[0], s));
         CK(launch_eval_mixed(c->d_el.as<Elem>(), c->d_far.as<FarNodes>(), c->d_cjk.as<float4>(),
                              c->d_sigma.as<double>(), c->n, c->img, c->grid, c->d_cell_start.as<int32_t>(),
                              c->d_cell_items.as<int32_t>(), d_pts, n, d_phi, d_E, ms, s));
+        CK(cudaEventRecord(c->ev_eval[1], s));
         if (refine || err) {
             AccView A;
+            A.view = make_view(c->d_el.as<Elem>(), c->d_far.as<FarNodes>(), c->d_cjk.as<float4>(),
+                               c->d_sigma.as<double>(), c->n, c->img, c->grid, c->d_cell_start.as<int32_t>(),
+                               c->d_cell_items.as<int32_t>());
+            A.far = c->d_far.as<FarNodes>();
             A.el = c->d_el.as<Elem>();
             A.fe = c->d_fill_el.as<FillEl>();
             A.nodes = c->d_fill_nodes.as<float4>();
@@ -243,9 +250,16 @@ int eval_elements(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double*
             A.cell_start = c->d_fill_cell_start.as<int32_t>();
             A.cell_items = c->d_fill_cell_items.as<int32_t>();
             CK(launch_eval_refine(A, c->img, d_pts, n, d_phi, d_E, err, c->opt.mixed_point_tol, ms,
-                                  c->props.multiProcessorCount, s));
+                                  c->props.multiProcessorCount, s, &c->ev_eval[2]));
+            c->refine_list = ms.n_list;
+        } else {
+            CK(cudaMemsetAsync(ms.n_list, 0, 2 * sizeof(int32_t), s));
+            CK(cudaEventRecord(c->ev_eval[2], s));
+            CK(cudaEventRecord(c->ev_eval[3], s));
             c->refine_list = ms.n_list;
         }
+        c->eval_timed = true;
+        c->eval_points_n = n;
     } else {
         CK(launch_eval_f64(c->d_el.as<Elem>(), c->d_sigma.as<double>(), c->n, c->img, d_pts, n, d_phi, d_E, s));
     }

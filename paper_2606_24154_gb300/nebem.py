@@ -63,6 +63,18 @@ class nebem_solve_info(C.Structure):
     ]
 
 
+class nebem_eval_stats_t(C.Structure):
+    _fields_ = [
+        ("points", C.c_int64),
+        ("refined_level1", C.c_int64),
+        ("refined_level2", C.c_int64),
+        ("ms_fp32", C.c_double),
+        ("ms_level1", C.c_double),
+        ("ms_level2", C.c_double),
+        ("reserved", C.c_double * 4),
+    ]
+
+
 class nebem_server_options(C.Structure):
     _fields_ = [
         ("arena_points", C.c_int64),
@@ -97,6 +109,7 @@ SIGNATURES = {
     "nebem_eval_device": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, C.c_int32, _vp]),
     "nebem_eval_err": (C.c_int, [_vp, _d, C.c_int64, _d, _d, _d, _i64p]),
     "nebem_eval_device_err": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp, _vp]),
+    "nebem_eval_stats": (C.c_int, [_vp, C.POINTER(nebem_eval_stats_t)]),
     "nebem_space_charge": (C.c_int, [_vp, _d, _d, C.c_int64, C.c_double]),
     "nebem_space_charge_eval": (C.c_int, [_vp, _d, C.c_int64, _d, _d, C.c_int32, C.c_int32]),
     "nebem_space_charge_lines": (C.c_int, [_vp, _d, _i64p]),
@@ -261,6 +274,12 @@ def nebem_eval_err(ctx, pts, want_phi=True, want_E=True):
 def nebem_eval_device_err(ctx, d_pts: int, n: int, d_phi: int | None, d_E: int | None, d_err: int | None,
                           stream: int | None = None):
     _check(load().nebem_eval_device_err(ctx, d_pts, n, d_phi, d_E, d_err, stream), "nebem_eval_device_err")
+
+
+def nebem_eval_stats(ctx) -> nebem_eval_stats_t:
+    st = nebem_eval_stats_t()
+    _check(load().nebem_eval_stats(ctx, C.byref(st)), "nebem_eval_stats")
+    return st
 
 
 def nebem_space_charge(ctx, pos, q, softening=0.0):

@@ -49,7 +49,8 @@ def tier_counts(g, pts, sample=4096, ratio_0=64.0, ratio_a=24.0, ratio_b=8.0, ra
     R = np.repeat(rho, t.shape[0])
     NV = np.repeat(nv, t.shape[0])
     na = np.where(NV == 4, 9, 6)
-    counts = {"pairs": 0, "t0": 0, "a": 0, "b": 0, "c": 0, "near": 0, "nodes": 0, "sample_points": 0}
+    slots_a = np.where(NV == 4, 10, 6)  # tier-a node slots in pairs (a 9-node rule is padded to 10)
+    counts = {"pairs": 0, "t0": 0, "a": 0, "b": 0, "c": 0, "near": 0, "nodes": 0, "slots": 0, "sample_points": 0}
     P = pts[:sample]
     for s in range(0, P.shape[0], chunk):
         d = np.linalg.norm(P[s:s + chunk, None, :] - C[None], axis=2) / R[None]
@@ -65,6 +66,7 @@ def tier_counts(g, pts, sample=4096, ratio_0=64.0, ratio_a=24.0, ratio_b=8.0, ra
         counts["c"] += int(tc.sum())
         counts["near"] += int(tn.sum())
         counts["nodes"] += int(4 * t0.sum() + (ta * na[None]).sum() + 16 * tb.sum() + 36 * tc.sum())
+        counts["slots"] += int(4 * t0.sum() + (ta * slots_a[None]).sum() + 16 * tb.sum() + 36 * tc.sum())
     counts["sample_points"] = int(P.shape[0])
     return counts
 
@@ -150,3 +152,28 @@ def fill_ops(counts, n):
         o = counts[key]
         ops += o["rows"] * n * FILL_OPS_COLUMN[k] + o["far_pairs"] * FILL_OPS_IMAGE[k] + o["nodes"] * FILL_OPS_NODE[k]
     return ops * scale
+
+
+# ---------------------------------------------------------------- refinement, first level
+# Two-float re-evaluation of flagged points with the FP32 pass's tiers (eval_acc.cu), FP32
+# lane operations counted from its code (node pairs run in the packed FP32x2 instructions,
+# two lanes each; a node slot is one lane of a node pair, padding included):
+#   per (point, element): P - c_j (3 two-float differences, 8 each) and its local
+#     components (3 two-float dot products, 28 each);
+#   per far (point, element, image) pair: the FP32 tier test (12 + 4 compares), X, Y, Z
+#     (3 differences, 24), |D|^2 (28), negations (3), the three node-pair sums folded to
+#     two-float values (30) and E_local += D S0 + S (3 two-float multiply-adds, 60);
+#   per node slot: r^2 and the refined 1/r (41, plus one MUFU rsqrt), w / r accumulated
+#     (12), w / r^3 (11) accumulated (8), and w (2 s_x) / r^3, w (2 s_z) / r^3 accumulated
+#     (1 + 12 + 12).
+ACC1_OPS_ELEMENT = 108
+ACC1_OPS_PAIR = 161
+ACC1_OPS_SLOT = 97
+
+
+def acc1_ops_per_point(counts, n_el):
+    """FP32 lane operations of the first refinement level per refined point, from
+    tier_counts taken on a sample of refined points."""
+    per = counts["sample_points"]
+    far = counts["t0"] + counts["a"] + counts["b"] + counts["c"]
+    return ACC1_OPS_ELEMENT * n_el + (ACC1_OPS_PAIR * far + ACC1_OPS_SLOT * counts["slots"]) / per

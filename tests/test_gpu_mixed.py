@@ -264,3 +264,8 @@ def test_error_estimates_and_refinement(N):
     # nebem_eval with NEBEM_MIXED gives the refined result
     ephi, eE = ctx.eval(pts, N.NEBEM_MIXED)
     assert np.array_equal(ephi, phi) and np.array_equal(eE, E)
+    # the stage report of that evaluation
+    st = N.nebem_eval_stats(ctx.h)
+    assert st.points == pts.shape[0] and st.refined_level1 == nref
+    assert 0 <= st.refined_level2 <= st.refined_level1
+    assert st.ms_fp32 > 0.0 and st.ms_level1 > 0.0 and st.ms_level2 >= 0.0

@@ -35,3 +35,16 @@ def test_peaks_from_unit_counts():
     assert R.fp32_peak_ops(2070.0) == 152 * 128 * 2070e6
     assert R.mufu_peak(2070.0) == 152 * 16 * 2070e6
     assert R.fp64_peak_inst(2070.0) == 152 * 2 * 2070e6
+
+
+def test_refinement_counts():
+    """Node slots count a 9-node tier-a rule as 10 (five packed pairs); the first refinement
+    level's operations are the per-element, per-pair and per-slot counts added up."""
+    g = I.thgem(I.PlateSpec(n_phi=24, n_r=3, n_zc=1, n_zf=4), n_plane=3)
+    pts = I.cell_points(g, 16, I.rng(0, 71))
+    c = R.tier_counts(g, pts, sample=16)
+    rect_a = (c["slots"] - c["nodes"])  # one padding slot per rectangle tier-a pair
+    assert rect_a >= 0 and c["slots"] - rect_a == c["nodes"]
+    far = c["t0"] + c["a"] + c["b"] + c["c"]
+    per = R.acc1_ops_per_point(c, g.n)
+    assert per == R.ACC1_OPS_ELEMENT * g.n + (R.ACC1_OPS_PAIR * far + R.ACC1_OPS_SLOT * c["slots"]) / 16
