@@ -109,7 +109,10 @@ typedef struct nebem_options {
     double sc_near;          /* space charge: pairs closer than this (m) form the FP32
                                 difference from exact two-float coordinates (default 1e-4) */
     int32_t lu_block;        /* LU panel width, 32 or 64 (default 64) */
-    int32_t reserved0;
+    int32_t wait_polls;      /* poll limit of the software waits on the device (the FP32
+                                panel's grid barrier, the triangular sweeps' block flags);
+                                0 = 4,194,304 polls (about 0.1-0.3 s).  A wait that runs out
+                                gives NEBEM_TIMEOUT (see nebem_solve); default 0 */
     double mixed_point_tol;  /* mixed eval: a point whose estimated error exceeds this fraction
                                 of its |phi| or |E| is evaluated again in two-float arithmetic
                                 (see nebem_eval_err); 0 keeps the single FP32 pass (default 1e-6) */
@@ -194,7 +197,11 @@ int nebem_set_bc(nebem_ctx *ctx, const double *voltages, int32_t n_conductors);
  * voltages or a new known-charge set.  sigma_out[n] (host, may be NULL) receives the
  * charge densities; info (may be NULL) the report.
  * Errors: NEBEM_BAD_STATE (no geometry or no voltages), NEBEM_SINGULAR,
- * NEBEM_NOT_CONVERGED (sigma and info are still written), NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
+ * NEBEM_NOT_CONVERGED (sigma and info are still written), NEBEM_TIMEOUT (a bounded device
+ * wait ran out -- see wait_polls: in the FP32 factorisation, nothing is written; in a
+ * triangular sweep, sigma_out is written with NaN in the 64-row blocks whose wait ran out,
+ * and the context holds no valid charge densities until the next solve; every kernel has
+ * returned, so the context stays usable), NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
 int nebem_solve(nebem_ctx *ctx, int32_t precision, double *sigma_out, nebem_solve_info *info);
 
 /* Replace the charge densities (sigma_j of Eq. Potential; n values, host, copied)
@@ -270,6 +277,11 @@ int nebem_eval_err(nebem_ctx *ctx, const double *pts, int64_t n, double *phi, do
                    int64_t *n_refined);
 int nebem_eval_device_err(nebem_ctx *ctx, const double *d_pts, int64_t n, double *d_phi, double *d_E, double *d_err,
                           void *stream);
+
+/* Set the context's wait_polls option (see nebem_options) for the following calls; 0
+ * restores the default.  A library utility with no counterpart in the paper.  Errors:
+ * NEBEM_INVALID_ARG (NULL, polls < 0). */
+int nebem_set_wait_polls(nebem_ctx *ctx, int32_t polls);
 
 /* Stage report of the last mixed evaluation of this context that ran without Adaptive
  * Modelling (nebem_eval, nebem_eval_device, nebem_eval_err and friends; a library utility

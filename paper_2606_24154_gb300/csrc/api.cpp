@@ -126,6 +126,7 @@ int nebem_create(nebem_ctx** out, const nebem_options* opt) {
     if (!(o.softening > 0.0)) return fail(NEBEM_INVALID_ARG, "softening must be > 0");
     if (!(o.mixed_point_tol >= 0.0) || !(o.mixed_point_tol < 1.0))
         return fail(NEBEM_INVALID_ARG, "mixed_point_tol must be in [0, 1)");
+    if (o.wait_polls < 0) return fail(NEBEM_INVALID_ARG, "wait_polls must be >= 0");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();
@@ -309,7 +310,9 @@ int nebem_solve(nebem_ctx* ctx, int32_t precision, double* sigma_out, nebem_solv
     rc = build_rhs(c);
     if (rc) return rc;
     rc = solve_with_factors(c, precision, &inf);
-    if (sigma_out && (rc == NEBEM_OK || rc == NEBEM_NOT_CONVERGED)) {
+    // sigma is written on success, at the refinement limit, and after a sweep's wait gave up
+    // (NaN in its blocks; a factorisation that gave up returned above)
+    if (sigma_out && (rc == NEBEM_OK || rc == NEBEM_NOT_CONVERGED || rc == NEBEM_TIMEOUT)) {
         CK(cudaMemcpyAsync(sigma_out, c->d_sigma.ptr, sizeof(double) * c->n, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
     }
@@ -418,6 +421,12 @@ int nebem_eval_err(nebem_ctx* ctx, const double* pts, int64_t n, double* phi, do
     if (err) CK(cudaMemcpyAsync(err, c->d_err.ptr, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (n_refined) *n_refined = h_ref;
+    return NEBEM_OK;
+}
+
+int nebem_set_wait_polls(nebem_ctx* ctx, int32_t polls) {
+    if (!ctx || polls < 0) return fail(NEBEM_INVALID_ARG, "bad argument");
+    reinterpret_cast<Ctx*>(ctx)->opt.wait_polls = polls;
     return NEBEM_OK;
 }
 

@@ -295,7 +295,7 @@ __device__ __forceinline__ int ld_acquire_i(const int* p) {
 // waits until the count reaches `target` (this barrier's total), so one atomic and one
 // polled load make the barrier, and the last arrival publishes everyone's writes (the
 // acquire load that sees the final count synchronises with every add before it).
-__device__ bool coop_barrier(CoopScratch* cs, unsigned int target, bool* s_flag) {
+__device__ bool coop_barrier(CoopScratch* cs, unsigned int target, bool* s_flag, long long limit) {
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned int v;
@@ -305,7 +305,7 @@ __device__ bool coop_barrier(CoopScratch* cs, unsigned int target, bool* s_flag)
             long long spins = 0;
             while (ld_acquire_u(&cs->bar[0]) < target) {
                 // give up after the poll limit, or at once when another CTA has given up
-                if (++spins > kCoopSpinLimit || ((spins & 1023) == 0 && ld_acquire_i(&cs->err))) {
+                if (++spins > limit || ((spins & 1023) == 0 && ld_acquire_i(&cs->err))) {
                     ok = false;
                     break;
                 }
@@ -320,7 +320,8 @@ __device__ bool coop_barrier(CoopScratch* cs, unsigned int target, bool* s_flag)
 
 __global__ void __launch_bounds__(kCoopThreads, 1)
     k_panel_coop(float* __restrict__ A, int64_t n, int64_t k0, int64_t k1, int R, int32_t* __restrict__ piv,
-                 int* __restrict__ info, int* __restrict__ tmo, CoopScratch* cs, unsigned int bar_base) {
+                 int* __restrict__ info, int* __restrict__ tmo, CoopScratch* cs, unsigned int bar_base,
+                 long long limit) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (ld_acquire_i(&cs->err)) return;  // an earlier panel gave up: leave the matrix as it is
     const int w = (int)(k1 - k0);
@@ -386,7 +387,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1)
             cs->cand[par][b][threadIdx.x] = (mine != LLONG_MAX) ? S[threadIdx.x * R + (int)(mine - rb0)] : 0.f;
             if (j >= rb0 && j < rb0 + nr) cs->srow[par][threadIdx.x] = S[threadIdx.x * R + (int)(j - rb0)];
         }
-        if (!coop_barrier(cs, bar_base + (unsigned)(jj + 1) * (unsigned)G, &s_flag)) {
+        if (!coop_barrier(cs, bar_base + (unsigned)(jj + 1) * (unsigned)G, &s_flag, limit)) {
             if (threadIdx.x == 0) {
                 atomicExch(&cs->err, 1);
                 atomicExch(tmo, 1);
@@ -454,7 +455,9 @@ __global__ void k_laswp(T* __restrict__ A, int64_t n, int64_t k0, int64_t k1, co
     if (c >= n || (c >= k0 && c < k1)) return;
     for (int64_t r = k0; r < k1; ++r) {
         const int64_t p = piv[r];
-        if (p != r) {
+        // a partial pivot lies in [r, n); anything else is a row no panel wrote (its panel
+        // gave up a bounded wait), and is skipped rather than used as an index
+        if (p != r && p > r && p < n) {
             const T a = A[r + c * n];
             A[r + c * n] = A[p + c * n];
             A[p + c * n] = a;
@@ -576,8 +579,10 @@ cudaError_t gemm(int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t l
 // then kPivBlocks doubles + kPivBlocks int64 for the pivot search and one int ticket.
 template <typename T>
 cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_info, void* split, void* coop,
-                      cudaStream_t s) {
-    // d_info[0]: first zero pivot (1-based) or 0; d_info[1]: tensor-core update gave up
+                      cudaStream_t s, long long polls) {
+    // d_info[0]: first zero pivot (1-based) or 0; d_info[1]: a bounded wait gave up (the
+    // tensor-core update or the cooperative panel's barrier); polls > 0: the barrier's
+    // poll limit (default kCoopSpinLimit)
     NB_TRY(cudaMemsetAsync(d_info, 0, 2 * sizeof(int), s));
     T* Linv = work;
     T* W = work + (size_t)nb * nb;
@@ -626,7 +631,8 @@ cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_inf
             int RR = R;
             int* tmo = d_info + 1;
             unsigned int base = arrivals;
-            void* args[] = {&Af, &nn, &kk0, &kk1, &RR, &piv, &d_info, &tmo, &cs, &base};
+            long long lim = polls > 0 ? polls : kCoopSpinLimit;
+            void* args[] = {&Af, &nn, &kk0, &kk1, &RR, &piv, &d_info, &tmo, &cs, &base, &lim};
             NB_TRY(cudaLaunchCooperativeKernel((const void*)k_panel_coop, dim3((unsigned)G), dim3(kCoopThreads), args,
                                                (size_t)R * w * sizeof(float), s));
             arrivals += (unsigned int)G * (unsigned int)w;
@@ -745,7 +751,7 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 template <typename T>
 __global__ void __launch_bounds__(kSvThreads) k_trsv(const T* __restrict__ LU, int64_t n, int64_t nblk, int lower,
                                                      const T* __restrict__ rhs, T* x, int* flags, int* ticket,
-                                                     int* err) {
+                                                     int* err, long long limit) {
     constexpr bool kInv = sizeof(T) == 4;  // explicit inverse of the diagonal block (FP32)
     __shared__ T D[kTB][kTB + 1];
     __shared__ T Xi[kInv ? kTB : 1][kTB + 1];
@@ -830,7 +836,7 @@ __global__ void __launch_bounds__(kSvThreads) k_trsv(const T* __restrict__ LU, i
         if (threadIdx.x == 0) {
             const int* fp = flags + (lower ? done : nblk - 1 - done);
             int f = ld_acquire(fp);
-            while (!f && ++spins <= kSvSpinLimit) {
+            while (!f && ++spins <= limit) {
                 __nanosleep(32);
                 f = ld_acquire(fp);
             }
@@ -918,7 +924,7 @@ __global__ void __launch_bounds__(kSvThreads) k_trsv(const T* __restrict__ LU, i
 }
 
 template <typename T>
-cudaError_t lu_solve(const T* LU, int64_t n, const int32_t* perm, T* b, T* work, cudaStream_t s) {
+cudaError_t lu_solve(const T* LU, int64_t n, const int32_t* perm, T* b, T* work, cudaStream_t s, long long polls) {
     if (n == 0) return cudaSuccess;
     const int64_t nblk = (n + kTB - 1) / kTB;
     T* y = work;
@@ -931,8 +937,9 @@ cudaError_t lu_solve(const T* LU, int64_t n, const int32_t* perm, T* b, T* work,
     NB_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * (2 * nblk + 3), s));
     const unsigned g = (unsigned)((n + 255) / 256);
     k_permute<T><<<g, 256, 0, s>>>(b, perm, n, y);
-    k_trsv<T><<<(unsigned)nblk, kSvThreads, 0, s>>>(LU, n, nblk, 1, y, z, flags, tickets, err);
-    k_trsv<T><<<(unsigned)nblk, kSvThreads, 0, s>>>(LU, n, nblk, 0, z, b, flags + nblk, tickets + 1, err);
+    const long long limit = polls > 0 ? polls : kSvSpinLimit;
+    k_trsv<T><<<(unsigned)nblk, kSvThreads, 0, s>>>(LU, n, nblk, 1, y, z, flags, tickets, err, limit);
+    k_trsv<T><<<(unsigned)nblk, kSvThreads, 0, s>>>(LU, n, nblk, 0, z, b, flags + nblk, tickets + 1, err, limit);
     return cudaGetLastError();
 }
 
@@ -1015,19 +1022,20 @@ size_t lu_work_elems(int64_t n, int nb) {
 }
 
 cudaError_t lu_factor_f64(double* A, int64_t n, int32_t* piv, int nb, double* work, int* d_info, cudaStream_t s) {
-    return lu_factor<double>(A, n, piv, nb, work, d_info, nullptr, nullptr, s);
+    return lu_factor<double>(A, n, piv, nb, work, d_info, nullptr, nullptr, s, 0);
 }
 static size_t split_offset(int64_t n, int nb) { return (sizeof(float) * lu_work_elems(n, nb) + 255) & ~(size_t)255; }
 static size_t coop_offset(int64_t n, int nb) {
     return (split_offset(n, nb) + tc_split_bytes(n, n) + 255) & ~(size_t)255;
 }
 size_t lu_work_bytes_f32(int64_t n, int nb) { return coop_offset(n, nb) + sizeof(CoopScratch); }
-cudaError_t lu_factor_f32(float* A, int64_t n, int32_t* piv, int nb, float* work, int* d_info, cudaStream_t s) {
+cudaError_t lu_factor_f32(float* A, int64_t n, int32_t* piv, int nb, float* work, int* d_info, cudaStream_t s,
+                          long long polls) {
     // work: lu_work_bytes_f32(n, nb) bytes, 256-byte aligned: panel staging, then the
     // tensor-core split operands, then the cooperative panel's candidates and barrier
     void* split = reinterpret_cast<char*>(work) + split_offset(n, nb);
     void* coop = reinterpret_cast<char*>(work) + coop_offset(n, nb);
-    return lu_factor<float>(A, n, piv, nb, work, d_info, split, coop, s);
+    return lu_factor<float>(A, n, piv, nb, work, d_info, split, coop, s, polls);
 }
 size_t lu_solve_work_bytes(int64_t n, size_t tsize) {
     return 2 * tsize * (size_t)n + 16 + sizeof(int) * (size_t)(2 * ((n + kTB - 1) / kTB) + 3) + 256;
@@ -1050,11 +1058,20 @@ cudaError_t lu_make_perm(const int32_t* piv, int64_t n, int32_t* perm, cudaStrea
     return cudaGetLastError();
 }
 
-cudaError_t lu_solve_f64(const double* LU, int64_t n, const int32_t* perm, double* b, void* work, cudaStream_t s) {
-    return lu_solve<double>(LU, n, perm, b, static_cast<double*>(work), s);
+cudaError_t lu_solve_f64(const double* LU, int64_t n, const int32_t* perm, double* b, void* work, cudaStream_t s,
+                         long long polls) {
+    return lu_solve<double>(LU, n, perm, b, static_cast<double*>(work), s, polls);
 }
-cudaError_t lu_solve_f32(const float* LU, int64_t n, const int32_t* perm, float* b, void* work, cudaStream_t s) {
-    return lu_solve<float>(LU, n, perm, b, static_cast<float*>(work), s);
+cudaError_t lu_solve_f32(const float* LU, int64_t n, const int32_t* perm, float* b, void* work, cudaStream_t s,
+                         long long polls) {
+    return lu_solve<float>(LU, n, perm, b, static_cast<float*>(work), s, polls);
+}
+const int* lu_solve_err_flag(const void* work, int64_t n, size_t tsize) {
+    // as laid out by lu_solve: y, z (n values each), then 16-byte aligned flags of both
+    // sweeps (nblk each), the two tickets and the error flag
+    const uintptr_t fo = ((uintptr_t)static_cast<const char*>(work) + 2 * tsize * (size_t)n + 15) & ~(uintptr_t)15;
+    const int64_t nblk = (n + kTB - 1) / kTB;
+    return reinterpret_cast<const int*>(fo) + 2 * nblk + 2;
 }
 cudaError_t gemv_residual(const double* K, int64_t n, const double* x, const double* b, double* r, void* work,
                           cudaStream_t s) {

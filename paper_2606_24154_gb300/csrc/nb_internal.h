@@ -208,8 +208,10 @@ size_t tc_split_bytes(int64_t M, int64_t N);
 // Dense LU (column-major, lda = n).  d_info: two ints (first zero pivot, tensor-core timeout).  Scratch: pivots int32[n], work as documented in lu.cu.
 cudaError_t lu_factor_f64(double* A, int64_t n, int32_t* piv, int nb, double* work, int* d_info,
                           cudaStream_t s);
+// polls > 0: poll limit of the software waits (the cooperative panel's grid barrier, the
+// triangular sweeps' block flags); 0 = their defaults
 cudaError_t lu_factor_f32(float* A, int64_t n, int32_t* piv, int nb, float* work, int* d_info,
-                          cudaStream_t s);
+                          cudaStream_t s, long long polls = 0);
 size_t lu_work_elems(int64_t n, int nb);
 // bytes of work space lu_factor_f32 takes (lu_work_elems floats, then the split operands of
 // the tensor-core updates)
@@ -218,8 +220,13 @@ size_t lu_work_bytes_f32(int64_t n, int nb);
 // swaps), work of lu_solve_work_bytes(n, sizeof(T)) bytes (16-byte aligned).
 cudaError_t lu_make_perm(const int32_t* piv, int64_t n, int32_t* perm, cudaStream_t s);
 size_t lu_solve_work_bytes(int64_t n, size_t tsize);
-cudaError_t lu_solve_f64(const double* LU, int64_t n, const int32_t* perm, double* b, void* work, cudaStream_t s);
-cudaError_t lu_solve_f32(const float* LU, int64_t n, const int32_t* perm, float* b, void* work, cudaStream_t s);
+cudaError_t lu_solve_f64(const double* LU, int64_t n, const int32_t* perm, double* b, void* work, cudaStream_t s,
+                         long long polls = 0);
+cudaError_t lu_solve_f32(const float* LU, int64_t n, const int32_t* perm, float* b, void* work, cudaStream_t s,
+                         long long polls = 0);
+// the solves' give-up flag (nonzero: a block flag wait ran out and the sweep wrote NaN)
+// inside their work space
+const int* lu_solve_err_flag(const void* work, int64_t n, size_t tsize);
 cudaError_t convert_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
 // r = b - K x; work of residual_work_bytes(n) bytes
 size_t residual_work_bytes(int64_t n);

@@ -110,13 +110,13 @@ int ensure_factors(Ctx* c, int precision, double* ms) {
         CK(cudaEventRecord(c->ev0, c->stream));
         CK(copy_f64_to_f32(c->d_K.as<double>(), c->d_LU32.as<float>(), n * n, c->stream));
         CK(lu_factor_f32(c->d_LU32.as<float>(), n, c->d_piv32.as<int32_t>(), nb, c->d_work.as<float>(),
-                         c->d_small.as<int>(), c->stream));
+                         c->d_small.as<int>(), c->stream, c->opt.wait_polls));
         int rc = elapsed_ms(c, ms);
         if (rc) return rc;
         int h2[2] = {0, 0};
         CK(cudaMemcpy(h2, c->d_small.ptr, sizeof(h2), cudaMemcpyDeviceToHost));
         h_info = h2[0];
-        if (h2[1]) return fail(NEBEM_TIMEOUT, "tensor-core trailing update: bounded wait gave up");
+        if (h2[1]) return fail(NEBEM_TIMEOUT, "FP32 factorisation: a bounded wait gave up (panel barrier or tensor-core update)");
         if (h_info) return fail(NEBEM_SINGULAR, "zero pivot at column " + std::to_string(h_info - 1));
         CK(c->d_perm32.ensure(sizeof(int32_t) * n));
         CK(lu_make_perm(c->d_piv32.as<int32_t>(), n, c->d_perm32.as<int32_t>(), c->stream));
@@ -154,9 +154,12 @@ int solve_with_factors(Ctx* c, int precision, nebem_solve_info* info) {
     void* work = c->d_swork.ptr;
     CK(cudaEventRecord(c->ev0, c->stream));
     int status = 0;
+    int gave_up = 0;  // a block-flag wait of a triangular sweep ran out (its block is NaN)
     if (precision == NEBEM_FP64) {
         CK(cudaMemcpyAsync(x, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
-        CK(lu_solve_f64(c->d_LU64.as<double>(), n, c->d_perm64.as<int32_t>(), x, work, c->stream));
+        CK(lu_solve_f64(c->d_LU64.as<double>(), n, c->d_perm64.as<int32_t>(), x, work, c->stream, c->opt.wait_polls));
+        CK(cudaMemcpyAsync(&gave_up, lu_solve_err_flag(work, n, sizeof(double)), sizeof(int), cudaMemcpyDeviceToHost,
+                           c->stream));
     } else {
         CK(c->d_r32.ensure(sizeof(float) * n));
         float* d32 = c->d_r32.as<float>();
@@ -167,11 +170,18 @@ int solve_with_factors(Ctx* c, int precision, nebem_solve_info* info) {
         status = NEBEM_NOT_CONVERGED;
         for (it = 1; it <= c->opt.ir_max_iter; ++it) {
             CK(copy_f64_to_f32(r, d32, n, c->stream));
-            CK(lu_solve_f32(c->d_LU32.as<float>(), n, c->d_perm32.as<int32_t>(), d32, work, c->stream));
+            CK(lu_solve_f32(c->d_LU32.as<float>(), n, c->d_perm32.as<int32_t>(), d32, work, c->stream,
+                            c->opt.wait_polls));
+            CK(cudaMemcpyAsync(&gave_up, lu_solve_err_flag(work, n, sizeof(float)), sizeof(int),
+                               cudaMemcpyDeviceToHost, c->stream));
             CK(ir_update(x, d32, n, norms, c->stream));
             double h[2];
             CK(cudaMemcpyAsync(h, norms, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
             CK(cudaStreamSynchronize(c->stream));
+            if (gave_up) {
+                status = NEBEM_TIMEOUT;
+                break;
+            }
             corr = (h[1] > 0.0) ? h[0] / h[1] : 0.0;
             if (!std::isfinite(corr)) break;
             CK(gemv_residual(c->d_K.as<double>(), n, x, b, r, work, c->stream));
@@ -197,8 +207,12 @@ int solve_with_factors(Ctx* c, int precision, nebem_solve_info* info) {
     CK(cudaMemcpyAsync(h, norms, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     if (info) info->residual = (h[1] > 0.0) ? h[0] / h[1] : 0.0;
-    c->sigma_valid = true;
     ++c->sigma_version;
+    if (gave_up || status == NEBEM_TIMEOUT) {
+        c->sigma_valid = false;  // NaN in the blocks whose wait ran out
+        return fail(NEBEM_TIMEOUT, "triangular sweep: a bounded wait gave up (sigma is NaN there)");
+    }
+    c->sigma_valid = true;
     if (status) return fail(status, "iterative refinement did not reach the tolerance");
     return 0;
 }

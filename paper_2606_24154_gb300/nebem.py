@@ -44,7 +44,7 @@ class nebem_options(C.Structure):
         ("softening", C.c_double),
         ("sc_near", C.c_double),
         ("lu_block", C.c_int32),
-        ("reserved0", C.c_int32),
+        ("wait_polls", C.c_int32),
         ("mixed_point_tol", C.c_double),
         ("reserved", C.c_double * 3),
     ]
@@ -110,6 +110,7 @@ SIGNATURES = {
     "nebem_eval_err": (C.c_int, [_vp, _d, C.c_int64, _d, _d, _d, _i64p]),
     "nebem_eval_device_err": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp, _vp]),
     "nebem_eval_stats": (C.c_int, [_vp, C.POINTER(nebem_eval_stats_t)]),
+    "nebem_set_wait_polls": (C.c_int, [_vp, C.c_int32]),
     "nebem_space_charge": (C.c_int, [_vp, _d, _d, C.c_int64, C.c_double]),
     "nebem_space_charge_eval": (C.c_int, [_vp, _d, C.c_int64, _d, _d, C.c_int32, C.c_int32]),
     "nebem_space_charge_lines": (C.c_int, [_vp, _d, _i64p]),
@@ -274,6 +275,10 @@ def nebem_eval_err(ctx, pts, want_phi=True, want_E=True):
 def nebem_eval_device_err(ctx, d_pts: int, n: int, d_phi: int | None, d_E: int | None, d_err: int | None,
                           stream: int | None = None):
     _check(load().nebem_eval_device_err(ctx, d_pts, n, d_phi, d_E, d_err, stream), "nebem_eval_device_err")
+
+
+def nebem_set_wait_polls(ctx, polls: int):
+    _check(load().nebem_set_wait_polls(ctx, polls), "nebem_set_wait_polls")
 
 
 def nebem_eval_stats(ctx) -> nebem_eval_stats_t:

@@ -62,6 +62,7 @@ def test_status_strings_and_defaults(lib):
     ("ratio_near", 1.0), ("ratio_b", 2.0), ("ratio_a", 7.0), ("ratio_0", 20.0), ("ratio_0", 1e7),
     ("softening", 0.0), ("softening", -1e-6),
     ("mixed_point_tol", -1e-6), ("mixed_point_tol", 1.0), ("mixed_point_tol", float("nan")),
+    ("wait_polls", -1),
 ])
 def test_bad_options_refused_before_any_device_call(lib, field, value):
     """Context options are checked on the host before the device is touched: every bad
