@@ -37,7 +37,8 @@ N_POINTS = 1_000_000
 HEADLINE_METRIC = "element-point influence evals/s (mixed FP32/FP64, <=1e-6 rel err per point vs FP64 path)"
 FP64_SAMPLE = 19_456
 CHECK_SAMPLE = 512
-ROOFLINE_SAMPLE = 8192  # points whose refinement decision is taken again to count the refined pairs
+ROOFLINE_SAMPLE = 8192
+SC_CARRIERS = 1_000_000  # points whose refinement decision is taken again to count the refined pairs
 ORACLE_SAMPLE = 2_048
 L2_FLUSH_BYTES = 512 << 20
 
@@ -54,6 +55,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=40)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-space-charge", action="store_true")
     ap.add_argument("--workload", default="thgem_eval",
                     choices=["thgem_eval", "double_thgem_solve", "space_charge", "lu", "am", "fastvol"])
     return ap.parse_args()
@@ -176,12 +178,13 @@ def run_reference(args):
     return 0
 
 
-def serving_run(N, ctxs, geoms, n_req, scale, precision, seed):
-    """Replay a seeded Poisson trace (2000 requests/s, sizes log-uniform in [1e2, 1e6]
+def serving_run(N, ctxs, geoms, n_req, scale, precision, seed, rate_hz=2000.0, max_wall_s=90.0):
+    """Replay a seeded Poisson trace (rate_hz requests/s, sizes log-uniform in [1e2, 1e6]
     times `scale`, geometry uniform over the resident contexts) through the server;
-    returns p50/p99 latency (submit -> outputs in host memory) and points/s."""
+    returns p50/p99 latency (submit -> outputs in host memory) and points/s.  No request is
+    submitted after max_wall_s (the submitted ones are drained and reported)."""
     from paper_2606_24154_gb300 import inputs as I
-    t_arr, sizes, geo = I.serving_trace(n_req, I.rng(4, seed), n_geometries=len(ctxs))
+    t_arr, sizes, geo = I.serving_trace(n_req, I.rng(4, seed), rate_hz=rate_hz, n_geometries=len(ctxs))
     sizes = np.maximum(1, (sizes * scale).astype(np.int64))
     reqs = []
     for k in range(n_req):
@@ -191,27 +194,40 @@ def serving_run(N, ctxs, geoms, n_req, scale, precision, seed):
     srv = N.nebem_server_create([c.h for c in ctxs])
     ids = [None] * n_req
     done = [False] * n_req
+    break_cap = False
     t0 = time.perf_counter()
     i = 0
-    while i < n_req or not all(done):
+    first = 0  # oldest request not known to be complete
+    while i < n_req or not all(done[:i]):
         now = time.perf_counter() - t0
         if now > 900.0:
             N.nebem_server_destroy(srv)
             raise RuntimeError("serving trace did not complete within 900 s")
+        if now > max_wall_s and i < n_req:
+            n_req = i  # capped: drain what was submitted
+            break_cap = True
         while i < n_req and t_arr[i] <= now:
             ids[i] = N.nebem_server_submit(srv, int(geo[i]), reqs[i][0], reqs[i][1], reqs[i][2], precision)
             i += 1
-        for k in range(i):
-            if not done[k]:
-                done[k] = N.nebem_server_poll(srv, ids[k])
+        # one poll per round drives the server, which completes (and timestamps) every
+        # finished request; then the oldest pending requests are checked in order
+        while first < i and N.nebem_server_poll(srv, ids[first]):
+            done[first] = True
+            first += 1
         time.sleep(50e-6)
+    for k in range(n_req):  # every request is complete by now; this only records it
+        done[k] = done[k] or N.nebem_server_poll(srv, ids[k])
+    ids, sizes = ids[:n_req], sizes[:n_req]
     times = np.array([N.nebem_server_request_times(srv, r) for r in ids])
     N.nebem_server_destroy(srv)
+    print(f"bench: serving {n_req} requests at {rate_hz:g}/s x{scale:g} precision {precision}: "
+          f"{time.perf_counter() - t0:.1f} s", file=sys.stderr, flush=True)
     lat = (times[:, 2] - times[:, 0]) * 1e3
     span = times[:, 2].max() - times[:, 0].min()
-    return {"requests": n_req, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "points_per_s": float(sizes.sum() / span), "points": int(sizes.sum()), "makespan_s": float(span),
-            "size_scale": scale}
+    return {"requests": n_req, "rate_hz": rate_hz, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "points_per_s": float(sizes.sum() / span),
+            "points": int(sizes.sum()), "makespan_s": float(span), "size_scale": scale,
+            "wall_s": time.perf_counter() - t0, "capped": break_cap}
 
 
 def pointwise(a, ref):
@@ -251,6 +267,72 @@ def timed_steps(step, stream, flush, steps, warmup, sampler=None, barrier=None):
         barrier()
         torch.cuda.synchronize()
     return [a.elapsed_time(b) for a, b in ev], time.perf_counter() - t0
+
+
+def space_charge_section(N, g, n_car, steps, dev):
+    """Dynamic space charge on the THGEM cell (1e6 point carriers, Gaussian cloud sigma
+    0.1 mm in the hole, half ions): the mixed dynamic step, the carrier-carrier sum alone,
+    and the FP64 GPU path on a sample of targets with the mixed sums' errors against it
+    (per target, at the carriers and at points of the cell away from the net-neutral cloud)."""
+    import torch
+    from paper_2606_24154_gb300 import inputs as I
+    from paper_2606_24154_gb300 import roofline as R
+    pos, q = I.carrier_cloud(g, n_car, I.rng(3, 0))
+    c = N.Context().set_geometry(g)
+    c.solve(N.NEBEM_MIXED)
+    N.nebem_space_charge(c.h, pos, q, 1e-6)
+    N.nebem_step(c.h, 1, 1e-4, 1e-9, N.NEBEM_MIXED, n_car)  # warm-up
+    N.nebem_space_charge(c.h, pos, q, 1e-6)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    N.nebem_step(c.h, steps, 1e-4, 1e-9, N.NEBEM_MIXED, n_car)
+    s_step = (time.perf_counter() - t) / steps
+    # the carrier-carrier sum alone (every carrier, self excluded)
+    N.nebem_space_charge(c.h, pos, q, 1e-6)
+    N.nebem_space_charge_eval(c.h, pos[:4096], N.NEBEM_MIXED, exclude_self=True)
+    t = time.perf_counter()
+    N.nebem_space_charge_eval(c.h, pos, N.NEBEM_MIXED, exclude_self=True)
+    t_sum = time.perf_counter() - t
+    pairs = n_car * (n_car - 1)
+    peaks, _ = load_peaks()
+    peak_ops = R.fp32_peak_ops(peaks.get("sm_max_mhz", 2070.0))
+    mphi_all, mE_all = N.nebem_space_charge_eval(c.h, pos, N.NEBEM_MIXED, exclude_self=True)
+    # FP64 path on samples: carriers and points of the cell.  Self exclusion needs the whole
+    # carrier set as targets, so at the sampled carriers the FP64 sums include each carrier's
+    # own term, ke q / s in phi (zero in E), which is taken out again.
+    ns = 2048
+    tgt = pos[:ns]
+    t = time.perf_counter()
+    rphi, rE = N.nebem_space_charge_eval(c.h, tgt, N.NEBEM_FP64)
+    t64 = time.perf_counter() - t
+    ke = 1.0 / (4.0 * np.pi * 8.8541878128e-12)
+    rphi = rphi - ke * q[:ns] / 1e-6
+    mphi, mE = mphi_all[:ns], mE_all[:ns]
+    far = I.cell_points(g, 512, I.rng(3, 2))
+    fphi64, fE64 = N.nebem_space_charge_eval(c.h, far, N.NEBEM_FP64)
+    fphi, fE = N.nebem_space_charge_eval(c.h, far, N.NEBEM_MIXED)
+    c.close()
+
+    def per_target(a, ref):
+        a, ref = torch.from_numpy(a), torch.from_numpy(ref)
+        return {"pointwise": pointwise(a, ref),
+                "normwise": float((a - ref).abs().max() / ref.abs().max()) if a.ndim == 1
+                else float((a - ref).norm(dim=1).max() / ref.norm(dim=1).max())}
+
+    return {"workload": f"thgem_cell N={g.n}, {n_car} carriers (Gaussian 0.1 mm, half ions), mu 1e-4 m^2/Vs, "
+                        f"dt 1 ns", "steps": steps,
+            "mixed_s_per_step": s_step,
+            "carrier_pairs_per_s_in_step": (pairs + g.n * n_car) / s_step,
+            "carrier_sum": {"s": t_sum, "pairs_per_s": pairs / t_sum,
+                            "lane_op_frac": pairs * R.SC_OPS_PER_PAIR / t_sum / peak_ops,
+                            "note": "host-timed nebem_space_charge_eval of all carriers at all carriers; "
+                                    f"{R.SC_OPS_PER_PAIR} FP32 lane ops per pair"},
+            "fp64_path": {"sample_targets": ns, "pairs_per_s": ns * (n_car - 1) / t64,
+                          "speedup_mixed_over_fp64": (pairs / t_sum) / (ns * (n_car - 1) / t64)},
+            "accuracy_vs_fp64": {"at_carriers_phi": per_target(mphi, rphi), "at_carriers_E": per_target(mE, rE),
+                                 "away_from_cloud_phi": per_target(fphi, fphi64),
+                                 "away_from_cloud_E": per_target(fE, fE64),
+                                 "pointwise_form": "|d_i| / max(|ref_i|, 1e-6 max|ref|), E as a vector"}}
 
 
 def run_native(args):
@@ -385,16 +467,42 @@ def run_native(args):
         sctx[0].solve(N.NEBEM_MIXED)
         _, inf2, _ = sctx[2].solve(N.NEBEM_MIXED)
         setup = time.perf_counter() - t
-        serving = {"trace": "Poisson 2000/s, sizes log-uniform 1e2..1e6, geometry uniform over 3 resident",
-                   "mixed": serving_run(N, sctx, geoms, args.serving_requests, 1.0, N.NEBEM_MIXED, 0),
-                   "mixed_small": serving_run(N, sctx, geoms, 20, 0.01, N.NEBEM_MIXED, 1),
-                   "fp64_small": serving_run(N, sctx, geoms, 20, 0.01, N.NEBEM_FP64, 1),
+        print(f"bench: serving setup {setup:.1f} s", file=sys.stderr, flush=True)
+        # the same three geometries and densities with the single FP32 pass (no refinement)
+        single_s = []
+        for k, c_ in enumerate(sctx):
+            c1 = N.Context(device=local, mixed_point_tol=0.0).set_geometry(geoms[k])
+            c1.set_sigma(c_.sigma())
+            single_s.append(c1)
+        small = 0.01
+        serving = {"trace": "Poisson arrivals, sizes log-uniform 1e2..1e6 (x size_scale), geometry uniform over "
+                            "3 resident (cube, THGEM cell, double THGEM)",
+                   "full_trace_2000_per_s": serving_run(N, sctx, geoms, args.serving_requests, 1.0, N.NEBEM_MIXED,
+                                                        0, 2000.0, 60.0),
+                   "note": "the full-size trace at 2000/s is an overload (drain rate); the rate sweeps use the "
+                           "trace with sizes x 0.01, below and above each mode's capacity",
+                   "sweep_mixed_single_pass": [serving_run(N, single_s, geoms, n, small, N.NEBEM_MIXED, 2 + i, rate,
+                                                           30.0)
+                                               for i, (rate, n) in enumerate(((50.0, 200), (150.0, 200),
+                                                                               (2000.0, 200)))],
+                   "sweep_mixed_refined": [serving_run(N, sctx, geoms, n, small, N.NEBEM_MIXED, 2 + i, rate, 40.0)
+                                           for i, (rate, n) in enumerate(((4.0, 100), (8.0, 100), (2000.0, 40)))],
+                   "sweep_fp64": [serving_run(N, sctx, geoms, 16, small, N.NEBEM_FP64, 2, 0.4, 60.0)],
                    "double_thgem_solve": {"elements": geoms[2].n, "ms_fill": inf2.ms_fill,
                                           "ms_factor_fp32": inf2.ms_factor, "ms_refine": inf2.ms_solve,
                                           "iterations": inf2.iterations, "correction": inf2.correction},
                    "setup_s": setup}
+        for c1 in single_s:
+            c1.close()
         sctx[0].close()
         sctx[2].close()
+
+    space = None
+    if rank == 0 and world == 1 and not args.no_space_charge:
+        t = time.perf_counter()
+        space = space_charge_section(N, g, SC_CARRIERS, 2, dev)
+        space["section_s"] = time.perf_counter() - t
+        print(f"bench: space charge {space['section_s']:.1f} s", file=sys.stderr, flush=True)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -444,6 +552,7 @@ def run_native(args):
             "tiers_refined": counts_l1,
             "solve_thgem": solve,
             "serving": serving,
+            "space_charge": space,
             "e2e": {"value": e2e_val, "unit": "evals/s", "h2d_bytes_per_step": int(pts_pin.numel() * 8),
                     "d2h_bytes_per_step": int((phi_pin.numel() + E_pin.numel()) * 8)},
             "cpu_baseline": cpu,

@@ -294,6 +294,8 @@ struct Server {
             if (q == cudaErrorNotReady) return 0;
             if (q != cudaSuccess) return cuda_fail(q, "serving kernel");
         }
+        // a new launch is open (the last one closed itself when it ran dry)
+        CK(cudaMemsetAsync(d_head.as<unsigned long long>() + 2, 0, sizeof(unsigned long long), compute));
         CK(launch_serve(d_geoms.as<ServeGeom>(), h_ring, ring_cap, h_tail, d_head.as<unsigned long long>(),
                         d_pts.as<double>(), d_phi.as<double>(), d_E.as<double>(), d_bound.as<float2>(),
                         d_remaining.as<int>(), h_done,
@@ -397,7 +399,7 @@ int nebem_server_create(nebem_server** out, nebem_ctx* const* ctxs, int32_t n_ct
         (e = s->d_pts.ensure(sizeof(double) * 3 * cap)) != cudaSuccess ||
         (e = s->d_phi.ensure(sizeof(double) * cap)) != cudaSuccess ||
         (e = s->d_E.ensure(sizeof(double) * 3 * cap)) != cudaSuccess ||
-        (e = s->d_head.ensure(sizeof(unsigned long long))) != cudaSuccess ||
+        (e = s->d_head.ensure(3 * sizeof(unsigned long long))) != cudaSuccess ||  // claimed, finished, closing
         (e = s->d_remaining.ensure(sizeof(int) * o.max_requests)) != cudaSuccess ||
         (e = s->d_partials.ensure(sizeof(double) * kPartialDoubles * kItemPoints * (size_t)kPartialBlocks *
                                   s->max_chunks)) != cudaSuccess ||
@@ -417,7 +419,7 @@ int nebem_server_create(nebem_server** out, nebem_ctx* const* ctxs, int32_t n_ct
     std::memset(s->h_done, 0, sizeof(int64_t) * o.max_requests);
     if ((e = cudaMemcpy(s->d_geoms.ptr, geoms.data(), sizeof(ServeGeom) * geoms.size(), cudaMemcpyHostToDevice)) !=
             cudaSuccess ||
-        (e = cudaMemset(s->d_head.ptr, 0, sizeof(unsigned long long))) != cudaSuccess ||
+        (e = cudaMemset(s->d_head.ptr, 0, 3 * sizeof(unsigned long long))) != cudaSuccess ||
         (e = cudaMemset(s->d_pcount.ptr, 0, sizeof(int) * kPartialBlocks)) != cudaSuccess)
         return bail(cuda_fail(e, "server setup copies"));
     for (int32_t i = kPartialBlocks - 1; i >= 0; --i) s->free_pblocks.push_back(i);

@@ -8,9 +8,16 @@
 // the request's remaining-item count; the CTA that finishes the last item publishes the
 // request's generation number to a host-mapped completion word.
 //
-// Every wait is bounded: a CTA that finds no claimable item for `idle_ns` (read from
-// %globaltimer) exits, and the kernel ends when all CTAs have; the host relaunches it
-// when new work arrives.  No CTA ever waits on another.
+// Every wait is bounded.  A CTA that has found no claimable item for `idle_ns` (read from
+// %globaltimer), at a moment when every item claimed so far has finished (head[1] counts
+// finished items), closes the launch: it sets head[2], and every CTA that sees it leaves
+// without claiming more, so the whole kernel ends and the host relaunches it, with all its
+// CTAs, when new work arrives (items published meanwhile wait in the ring for that
+// launch).  Leaving together matters: if CTAs left one by one, a trickle of requests could
+// keep a few of them, and so the kernel, alive, and no relaunch would restore the rest.
+// While any item is still being evaluated, idle CTAs stay.  No CTA ever waits on another:
+// an item's processing has no waits of its own.  Idle polls of the host-mapped tail back
+// off from 1 to 32 us.
 #include <cuda/atomic>
 
 #include "eval_blocks.cuh"
@@ -40,9 +47,11 @@ __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restr
     for (;;) {
         if (threadIdx.x == 0) {
             have = 0;
-            const uint64_t t0 = global_ns();
+            uint64_t t0 = global_ns();
+            unsigned sleep_ns = 1000;  // back-off between polls of the host-mapped tail
             cuda::atomic_ref<int64_t, cuda::thread_scope_system> tail(*tail_mapped);
             for (;;) {
+                if (atomicAdd(head + 2, 0ull) != 0ull) break;  // the launch is closing
                 const int64_t t = tail.load(cuda::memory_order_acquire);
                 const unsigned long long h = atomicAdd(head, 0ull);
                 if ((int64_t)h < t) {
@@ -53,8 +62,15 @@ __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restr
                     }
                     continue;
                 }
-                if (global_ns() - t0 > idle_ns) break;
-                __nanosleep(2000);
+                if (global_ns() - t0 > idle_ns) {
+                    if (atomicAdd(head + 1, 0ull) >= h) {  // every claimed item has finished
+                        atomicExch(head + 2, 1ull);        // close the launch for every CTA
+                        break;
+                    }
+                    t0 = global_ns();  // items still in progress: stay for what may arrive
+                }
+                __nanosleep(sleep_ns);
+                sleep_ns = min(2u * sleep_ns, 32000u);
             }
         }
         __syncthreads();
@@ -134,6 +150,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restr
                 d.store(it.gen, cuda::memory_order_release);
             }
         }
+        if (threadIdx.x == 0) atomicAdd(head + 1, 1ull);  // one more item finished
         __syncthreads();
     }
 }

@@ -177,3 +177,9 @@ def acc1_ops_per_point(counts, n_el):
     per = counts["sample_points"]
     far = counts["t0"] + counts["a"] + counts["b"] + counts["c"]
     return ACC1_OPS_ELEMENT * n_el + (ACC1_OPS_PAIR * far + ACC1_OPS_SLOT * counts["slots"]) / per
+
+
+# Space-charge carrier sum (spacecharge.cu, mixed): per (target, source) pair, the two-float
+# difference (9), r^2 + s^2 (3), then q / r and q / r^3 and the four accumulations (7), plus
+# one MUFU rsqrt.
+SC_OPS_PER_PAIR = 19

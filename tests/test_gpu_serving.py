@@ -171,3 +171,42 @@ def test_server_refuses_contexts_it_cannot_reproduce(N):
     with pytest.raises(N.NebemError) as e:
         N.nebem_server_create([c2.h])
     assert e.value.code == N.NEBEM_BAD_STATE
+
+
+def test_server_keeps_its_workers_under_a_trickle(N, ctxs):
+    """Requests that arrive a few at a time, with gaps longer than the kernel's idle time
+    and small bursts, are all served at the rate they arrive: the persistent kernel closes
+    as a whole when it runs dry and is relaunched with every CTA.  (When CTAs left one by
+    one, a trickle kept a few of them alive and the backlog grew to tens of seconds.)"""
+    import time
+    gen = I.rng(4, 77)
+    n_req = 80
+    gaps = gen.exponential(1.0 / 50.0, n_req)  # ~50 requests/s, Poisson
+    sizes = gen.integers(1, 3000, n_req)
+    geo = gen.integers(0, len(ctxs), n_req)
+    reqs = []
+    for k in range(n_req):
+        pts = _request_points(ctxs[geo[k]][0], int(sizes[k]), 500 + k)
+        reqs.append((pts, np.empty(pts.shape[0]), np.empty((pts.shape[0], 3))))
+    srv = N.nebem_server_create([c.h for _, c in ctxs])
+    try:
+        t_arr = np.cumsum(gaps) - gaps[0]
+        ids, first, i = [], 0, 0
+        t0 = time.perf_counter()
+        while first < n_req:
+            now = time.perf_counter() - t0
+            assert now < 60.0, "trickle not served"
+            while i < n_req and t_arr[i] <= now:
+                p, ph, E = reqs[i]
+                ids.append(N.nebem_server_submit(srv, int(geo[i]), p, ph, E, N.NEBEM_MIXED))
+                i += 1
+            while first < i and N.nebem_server_poll(srv, ids[first]):
+                first += 1
+            time.sleep(50e-6)
+        lat = np.array([np.subtract(*N.nebem_server_request_times(srv, r)[2::-2]) for r in ids])
+        span = t_arr[-1]
+        # served about as fast as they arrive: the backlog never builds up
+        assert time.perf_counter() - t0 < span + 5.0
+        assert np.percentile(lat, 99) < 3.0, np.percentile(lat, 99)
+    finally:
+        N.nebem_server_destroy(srv)
