@@ -289,7 +289,7 @@ def space_charge_section(N, g, n_car, steps, dev):
     s_step = (time.perf_counter() - t) / steps
     # the carrier-carrier sum alone (every carrier, self excluded)
     N.nebem_space_charge(c.h, pos, q, 1e-6)
-    N.nebem_space_charge_eval(c.h, pos[:4096], N.NEBEM_MIXED, exclude_self=True)
+    N.nebem_space_charge_eval(c.h, pos[:4096], N.NEBEM_MIXED)  # warm-up
     t = time.perf_counter()
     N.nebem_space_charge_eval(c.h, pos, N.NEBEM_MIXED, exclude_self=True)
     t_sum = time.perf_counter() - t

@@ -180,6 +180,22 @@ def test_eval_parity_thgem_full_geometry_sampled(N):
     assert rel_norm(E, rE) <= TOL64
 
 
+def test_eval_fp64_full_thgem_per_point_1000(N):
+    """Full-size THGEM cell with its solved charge densities, 1,000 points against the
+    oracle point by point: |d_i| / max(|ref_i|, 1e-6 max|ref|) <= 1e-10 for phi and for the
+    field vector."""
+    g = I.thgem()
+    ctx = N.Context().set_geometry(g)
+    sigma, _, _ = ctx.solve(N.NEBEM_MIXED)
+    pts = I.cell_points(g, 1000, I.rng(1, 77))
+    phi, E = ctx.eval(pts, N.NEBEM_FP64)
+    rphi, rE = O.eval_points(g, sigma, pts)
+    r = np.abs(rphi)
+    assert (np.abs(phi - rphi) / np.maximum(r, 1e-6 * r.max())).max() <= TOL64
+    m = np.linalg.norm(rE, axis=1)
+    assert (np.linalg.norm(E - rE, axis=1) / np.maximum(m, 1e-6 * m.max())).max() <= TOL64
+
+
 def test_eval_ragged_and_empty(N):
     g = small_thgem()
     sigma = I.rng(0, 3).normal(size=g.n)

@@ -182,13 +182,20 @@ def test_server_keeps_its_workers_under_a_trickle(N, ctxs):
     gen = I.rng(4, 77)
     n_req = 80
     gaps = gen.exponential(1.0 / 50.0, n_req)  # ~50 requests/s, Poisson
-    sizes = gen.integers(1, 3000, n_req)
+    sizes = gen.integers(1, 1000, n_req)
     geo = gen.integers(0, len(ctxs), n_req)
     reqs = []
     for k in range(n_req):
         pts = _request_points(ctxs[geo[k]][0], int(sizes[k]), 500 + k)
         reqs.append((pts, np.empty(pts.shape[0]), np.empty((pts.shape[0], 3))))
-    srv = N.nebem_server_create([c.h for _, c in ctxs])
+    # the single FP32 pass, far below the server's capacity at this rate: any backlog would
+    # come from lost workers, not from the work itself
+    single = []
+    for g, c in ctxs:
+        c1 = N.Context(mixed_point_tol=0.0).set_geometry(g)
+        c1.set_sigma(c.sigma())
+        single.append(c1)
+    srv = N.nebem_server_create([c.h for c in single])
     try:
         t_arr = np.cumsum(gaps) - gaps[0]
         ids, first, i = [], 0, 0
@@ -206,7 +213,7 @@ def test_server_keeps_its_workers_under_a_trickle(N, ctxs):
         lat = np.array([np.subtract(*N.nebem_server_request_times(srv, r)[2::-2]) for r in ids])
         span = t_arr[-1]
         # served about as fast as they arrive: the backlog never builds up
-        assert time.perf_counter() - t0 < span + 5.0
-        assert np.percentile(lat, 99) < 3.0, np.percentile(lat, 99)
+        assert time.perf_counter() - t0 < span + 2.0
+        assert np.percentile(lat, 99) < 0.5, np.percentile(lat, 99)
     finally:
         N.nebem_server_destroy(srv)
