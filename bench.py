@@ -294,8 +294,8 @@ def space_charge_section(N, g, n_car, steps, dev):
     N.nebem_space_charge_eval(c.h, pos, N.NEBEM_MIXED, exclude_self=True)
     t_sum = time.perf_counter() - t
     pairs = n_car * (n_car - 1)
-    peaks, _ = load_peaks()
-    peak_ops = R.fp32_peak_ops(peaks.get("sm_max_mhz", 2070.0))
+    meas = N.nebem_peak_rates(c.h)
+    peak_ops = max(meas["ffma"], meas["ffma2_lanes"])  # measured FP32 lane-op peak
     mphi_all, mE_all = N.nebem_space_charge_eval(c.h, pos, N.NEBEM_MIXED, exclude_self=True)
     # FP64 path on samples: carriers and points of the cell.  Self exclusion needs the whole
     # carrier set as targets, so at the sampled carriers the FP64 sums include each carrier's
@@ -326,7 +326,8 @@ def space_charge_section(N, g, n_car, steps, dev):
             "carrier_sum": {"s": t_sum, "pairs_per_s": pairs / t_sum,
                             "lane_op_frac": pairs * R.SC_OPS_PER_PAIR / t_sum / peak_ops,
                             "note": "host-timed nebem_space_charge_eval of all carriers at all carriers; "
-                                    f"{R.SC_OPS_PER_PAIR} FP32 lane ops per pair"},
+                                    f"{R.SC_OPS_PER_PAIR} FP32 lane ops per pair; peak measured "
+                                    "(nebem_peak_rates)"},
             "fp64_path": {"sample_targets": ns, "pairs_per_s": ns * (n_car - 1) / t64,
                           "speedup_mixed_over_fp64": (pairs / t_sum) / (ns * (n_car - 1) / t64)},
             "accuracy_vs_fp64": {"at_carriers_phi": per_target(mphi, rphi), "at_carriers_E": per_target(mE, rE),
@@ -418,7 +419,11 @@ def run_native(args):
     from paper_2606_24154_gb300 import roofline as R
     peaks, peak_src = load_peaks()
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    peak_ops = R.fp32_peak_ops(sm_max)
+    # peaks of the pipes, measured on this GPU (FP32 lanes: the better of scalar and packed FMA)
+    meas = N.nebem_peak_rates(ctx.h)
+    peak_ops = max(meas["ffma"], meas["ffma2_lanes"])
+    peak_mufu = meas["mufu_rsqrt"]
+    peak_fp64 = meas["dfma"]
     sub = pts_h[:min(ROOFLINE_SAMPLE, npts)]
     _, _, err_r, _ = N.nebem_eval_err(ctx.h, sub)
     _, _, err_s, _ = N.nebem_eval_err(single.h, sub)
@@ -532,22 +537,25 @@ def run_native(args):
                           "speedup_refined_over_fp64": value / world / fp64_rate,
                           "roofline": {"bound": "fp64",
                                        "achieved": fp64_rate * R.FP64_INST_PER_PAIR / 1e12,
-                                       "peak": R.fp64_peak_inst(sm_max) / 1e12,
+                                       "peak": peak_fp64 / 1e12,
                                        "unit": "T FP64 instructions/s",
-                                       "frac": fp64_rate * R.FP64_INST_PER_PAIR / R.fp64_peak_inst(sm_max),
-                                       "note": "278 FP64 instructions per pair (ncu count); peak = 152 SMs x "
-                                               "2 FP64 instructions per clock x max SM clock"}},
+                                       "frac": fp64_rate * R.FP64_INST_PER_PAIR / peak_fp64,
+                                       "note": "278 FP64 instructions per pair (ncu count); peak = measured FP64 "
+                                               "FMA rate (nebem_peak_rates)"}},
             "roofline": {"bound": "alu", "kernel": "k_eval_acc_far<1> (first refinement level, two-float)",
                          "achieved": ach_l1 / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
                          "frac": ach_l1 / peak_ops, "traffic": None,
+                         "peak_source": "measured on this GPU (nebem_peak_rates: the better of scalar and "
+                                        "packed FP32 FMA, lanes counted)",
+                         "peak_unit_counts": R.fp32_peak_ops(sm_max) / 1e12,
+                         "peaks_measured": {k: v / 1e12 for k, v in meas.items()},
                          "note": "FP32 lane operations counted from the code (roofline.ACC1_*) x the refined "
                                  "points' pair and node counts / the level's event time (flag step and FP64 near "
-                                 "pairs included); peak = 152 SMs x 128 lanes x max SM clock (unit counts); "
-                                 "traffic: no capture of this kernel version",
+                                 "pairs included); traffic: no capture of this kernel version",
                          "fp32_pass": {"kernel": "k_eval_far", "achieved": ach_fp32 / 1e12,
                                        "frac": ach_fp32 / peak_ops,
                                        "mufu_frac": counts["nodes"] * (npts / CHECK_SAMPLE) / (stats.ms_fp32 * 1e-3)
-                                       / R.mufu_peak(sm_max)}},
+                                       / peak_mufu}},
             "tiers": counts,
             "tiers_refined": counts_l1,
             "solve_thgem": solve,

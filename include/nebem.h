@@ -283,6 +283,14 @@ int nebem_eval_device_err(nebem_ctx *ctx, const double *d_pts, int64_t n, double
  * NEBEM_INVALID_ARG (NULL, polls < 0). */
 int nebem_set_wait_polls(nebem_ctx *ctx, int32_t polls);
 
+/* Measured throughput of the pipes the evaluation kernels use, on the context's device (a
+ * measurement utility with no counterpart in the paper; about 0.1 s): rates[0] scalar FP32
+ * FMA, rates[1] packed FP32x2 FMA (each lane counted), rates[2] MUFU reciprocal square
+ * root, rates[3] FP64 FMA, in operations per second (an FMA counts as one operation).
+ * Best of three timed launches after a warm-up, CUDA events on the context stream.
+ * Errors: NEBEM_INVALID_ARG (NULL), NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
+int nebem_peak_rates(nebem_ctx *ctx, double *rates);
+
 /* Stage report of the last mixed evaluation of this context that ran without Adaptive
  * Modelling (nebem_eval, nebem_eval_device, nebem_eval_err and friends; a library utility
  * with no counterpart in the paper).  Waits for that evaluation to finish.  Device times

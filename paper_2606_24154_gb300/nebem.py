@@ -111,6 +111,7 @@ SIGNATURES = {
     "nebem_eval_device_err": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp, _vp]),
     "nebem_eval_stats": (C.c_int, [_vp, C.POINTER(nebem_eval_stats_t)]),
     "nebem_set_wait_polls": (C.c_int, [_vp, C.c_int32]),
+    "nebem_peak_rates": (C.c_int, [_vp, _d]),
     "nebem_space_charge": (C.c_int, [_vp, _d, _d, C.c_int64, C.c_double]),
     "nebem_space_charge_eval": (C.c_int, [_vp, _d, C.c_int64, _d, _d, C.c_int32, C.c_int32]),
     "nebem_space_charge_lines": (C.c_int, [_vp, _d, _i64p]),
@@ -275,6 +276,12 @@ def nebem_eval_err(ctx, pts, want_phi=True, want_E=True):
 def nebem_eval_device_err(ctx, d_pts: int, n: int, d_phi: int | None, d_E: int | None, d_err: int | None,
                           stream: int | None = None):
     _check(load().nebem_eval_device_err(ctx, d_pts, n, d_phi, d_E, d_err, stream), "nebem_eval_device_err")
+
+
+def nebem_peak_rates(ctx) -> dict:
+    r = np.zeros(4)
+    _check(load().nebem_peak_rates(ctx, _dp(r)), "nebem_peak_rates")
+    return {"ffma": r[0], "ffma2_lanes": r[1], "mufu_rsqrt": r[2], "dfma": r[3]}
 
 
 def nebem_set_wait_polls(ctx, polls: int):

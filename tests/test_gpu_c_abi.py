@@ -50,3 +50,18 @@ def test_c_program_solves_and_evaluates(lib_dir, tmp_path):
     _, _, area = O.centroids(g)
     C = (sigma * area).sum()
     assert abs(C / (0.6607 * 4 * np.pi * O.eps0() * 0.01) - 1.0) < 0.02
+
+
+def test_peak_rates_are_plausible():
+    """nebem_peak_rates measures the FP32, packed FP32x2, MUFU and FP64 pipes; each rate is
+    positive and within a factor of a few of the unit counts (152 SMs x 128 FP32 lanes, 16
+    MUFU and 2 FP64 per clock at up to 2.07 GHz; the clock under load may be lower)."""
+    from paper_2606_24154_gb300 import build, nebem as N
+    build.build()
+    N.load()
+    ctx = N.Context()  # held: the handle lives as long as this object
+    r = N.nebem_peak_rates(ctx.h)
+    clk = 2.07e9
+    for key, units in (("ffma", 128), ("ffma2_lanes", 128), ("mufu_rsqrt", 16), ("dfma", 2)):
+        nominal = 152 * units * clk
+        assert 0.2 * nominal < r[key] < 2.5 * nominal, (key, r[key], nominal)

@@ -76,6 +76,7 @@ def test_panel_barrier_wait_runs_out_then_solves(N):
 
 
 def test_wait_polls_option_checked(N):
+    ctx = N.Context()  # held: the handle lives as long as this object
     with pytest.raises(N.NebemError) as e:
-        N.nebem_set_wait_polls(N.Context().h, -1)
+        N.nebem_set_wait_polls(ctx.h, -1)
     assert e.value.code == N.NEBEM_INVALID_ARG
