@@ -39,6 +39,7 @@ namespace nb {
 namespace {
 
 constexpr int kAT = 128;             // threads (flagged points) per block
+constexpr int kATBlocks = 4;         // resident far blocks per SM (128 registers a thread)
 constexpr double kGammaPhi = 1.5e-7; // FP32 pass: error of phi <= kGammaPhi * B_phi
 constexpr double kGammaE = 1.5e-7;   // FP32 pass: error of |E| <= kGammaE * B_E
 constexpr double kGammaL1 = 1e-9;    // two-float, the FP32 pass's rules (truncation ~1e-10 B)
@@ -260,74 +261,12 @@ __device__ __forceinline__ Sum6 acc_range(const AccView& A, int nimg, int te, fl
     return acc;
 }
 
-// Far part of every listed point at level L (thread per point, blocks striding over the
-// list of *n_list points): writes ke * sum to phi / E, the level's estimate to err, and
-// (level 1) ke * (B_phi, B_E) to bound for the next flag step.
+// ke * sums of point p at level L into phi / E, the level's estimate into err, and (level 1)
+// ke * (B_phi, B_E) into bound for the next flag step.
 template <int L>
-__global__ void __launch_bounds__(kAT, 3)
-    k_eval_acc_far(const AccView A, int nimg, int te, const double* __restrict__ pts,
-                   const int32_t* __restrict__ list, const int32_t* __restrict__ n_list, double* __restrict__ phi,
-                   double* __restrict__ E, double* __restrict__ err, float2* __restrict__ bound) {
-    extern __shared__ float4 sm[];
-    const int64_t count = *n_list;
-    const double ke = 1.0 / (4.0 * kPi * kEps0);
-    const double gamma = (L == 1) ? kGammaL1 : kGammaL2;
-    for (int64_t base = (int64_t)blockIdx.x * kAT; base < count; base += (int64_t)gridDim.x * kAT) {
-        const bool active = base + threadIdx.x < count;
-        const int64_t p = active ? (int64_t)list[base + threadIdx.x] : 0;
-        float ph[3], pl[3];
-        load_point_2f(pts, p, active, ph[0], ph[1], ph[2], pl[0], pl[1], pl[2]);
-        Sum6 tot{0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        for (int64_t e0 = 0; e0 < A.n_el; e0 += kChunkEl)
-            add6(tot, acc_range<L>(A, nimg, te, sm, ph, pl, e0, min(e0 + (int64_t)kChunkEl, A.n_el)));
-        if (active) {
-            if (phi) phi[p] = ke * tot.phi;
-            if (E) {
-                E[3 * p] = ke * tot.x;
-                E[3 * p + 1] = ke * tot.y;
-                E[3 * p + 2] = ke * tot.z;
-            }
-            if (err) {
-                err[2 * p] = gamma * ke * tot.bphi;
-                err[2 * p + 1] = gamma * ke * tot.bE;
-            }
-            if (L == 1) bound[p] = make_float2((float)(ke * tot.bphi), (float)(ke * tot.bE));
-        }
-    }
-}
-
-// The same far sums split over element chunks, for a few points spread over many CTAs:
-// block (bx, chunk) writes the chunk's Sum6 of its listed points to part[(chunk * cap + i)]
-// (i = list position); k_acc_reduce then adds the chunks in order, which is the order
-// k_eval_acc_far adds them in, so a point gets the same bits either way.
-template <int L>
-__global__ void __launch_bounds__(kAT, 3)
-    k_eval_acc_far_chunk(const AccView A, int nimg, int te, const double* __restrict__ pts,
-                         const int32_t* __restrict__ list, const int32_t* __restrict__ n_list, int64_t cap,
-                         Sum6* __restrict__ part) {
-    extern __shared__ float4 sm[];
-    const int64_t count = *n_list;
-    const int64_t base = (int64_t)blockIdx.x * kAT;
-    if (base >= count) return;  // whole block: no barrier is skipped by part of it
-    const bool active = base + threadIdx.x < count;
-    const int64_t p = active ? (int64_t)list[base + threadIdx.x] : 0;
-    float ph[3], pl[3];
-    load_point_2f(pts, p, active, ph[0], ph[1], ph[2], pl[0], pl[1], pl[2]);
-    const int64_t e0 = (int64_t)blockIdx.y * kChunkEl;
-    const Sum6 c = acc_range<L>(A, nimg, te, sm, ph, pl, e0, min(e0 + (int64_t)kChunkEl, A.n_el));
-    if (active) part[(int64_t)blockIdx.y * cap + base + threadIdx.x] = c;
-}
-
-template <int L>
-__global__ void __launch_bounds__(256)
-    k_acc_reduce(const int32_t* __restrict__ list, const int32_t* __restrict__ n_list, int64_t cap, int nchunks,
-                 const Sum6* __restrict__ part, double* __restrict__ phi, double* __restrict__ E,
-                 double* __restrict__ err, float2* __restrict__ bound) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= *n_list) return;
-    const int64_t p = list[i];
-    Sum6 tot{0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int k = 0; k < nchunks; ++k) add6(tot, part[(int64_t)k * cap + i]);
+__device__ __forceinline__ void store_acc(int64_t p, const Sum6& tot, double* __restrict__ phi,
+                                          double* __restrict__ E, double* __restrict__ err,
+                                          float2* __restrict__ bound) {
     const double ke = 1.0 / (4.0 * kPi * kEps0);
     const double gamma = (L == 1) ? kGammaL1 : kGammaL2;
     if (phi) phi[p] = ke * tot.phi;
@@ -343,8 +282,67 @@ __global__ void __launch_bounds__(256)
     if (L == 1) bound[p] = make_float2((float)(ke * tot.bphi), (float)(ke * tot.bE));
 }
 
-// Level-1 near part: the FP64 closed forms of the pairs nearer than ratio_near radii, as the
-// FP32 pass adds them (near_point, its cell list); adds ke * sum to phi / E.
+// Far part of every listed point at level L, thread per point, kAT points (a group) per
+// block pass.  The G = ceil(*n_list / kAT) groups are split so that every resident block
+// gets the same work: the first Gm = floor(G / gridDim) * gridDim groups are taken whole,
+// round-robin; the R = G - Gm left over are cut into R * nch pieces (group, element chunk of
+// kChunkEl), also round-robin, whose Sum6 go to part[chunk * cap + (group - Gm) * kAT + t]
+// for k_acc_reduce.  A whole group adds its chunks' sums in chunk order, as k_acc_reduce
+// does, so a point gets the same bits whichever way it is taken.
+template <int L>
+__global__ void __launch_bounds__(kAT, kATBlocks)
+    k_eval_acc_far(const AccView A, int nimg, int te, const double* __restrict__ pts,
+                   const int32_t* __restrict__ list, const int32_t* __restrict__ n_list, int nch, int64_t cap,
+                   Sum6* __restrict__ part, double* __restrict__ phi, double* __restrict__ E,
+                   double* __restrict__ err, float2* __restrict__ bound) {
+    extern __shared__ float4 sm[];
+    const int64_t count = *n_list;
+    const int64_t gb = gridDim.x;
+    const int64_t G = (count + kAT - 1) / kAT;
+    const int64_t Gm = (G / gb) * gb;
+    for (int64_t g = blockIdx.x; g < Gm; g += gb) {
+        const int64_t base = g * kAT;
+        const bool active = base + threadIdx.x < count;
+        const int64_t p = active ? (int64_t)list[base + threadIdx.x] : 0;
+        float ph[3], pl[3];
+        load_point_2f(pts, p, active, ph[0], ph[1], ph[2], pl[0], pl[1], pl[2]);
+        Sum6 tot{0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int64_t e0 = 0; e0 < A.n_el; e0 += kChunkEl)
+            add6(tot, acc_range<L>(A, nimg, te, sm, ph, pl, e0, min(e0 + (int64_t)kChunkEl, A.n_el)));
+        if (active) store_acc<L>(p, tot, phi, E, err, bound);
+    }
+    const int64_t R = G - Gm;
+    for (int64_t q = blockIdx.x; q < R * nch; q += gb) {
+        const int64_t r = q % R, ch = q / R;  // consecutive blocks: the same chunk, other groups
+        const int64_t base = (Gm + r) * kAT;
+        const bool active = base + threadIdx.x < count;
+        const int64_t p = active ? (int64_t)list[base + threadIdx.x] : 0;
+        float ph[3], pl[3];
+        load_point_2f(pts, p, active, ph[0], ph[1], ph[2], pl[0], pl[1], pl[2]);
+        const int64_t e0 = ch * kChunkEl;
+        const Sum6 c = acc_range<L>(A, nimg, te, sm, ph, pl, e0, min(e0 + (int64_t)kChunkEl, A.n_el));
+        if (active) part[ch * cap + r * kAT + threadIdx.x] = c;
+    }
+}
+
+// The left-over groups of k_eval_acc_far launched with gb blocks: adds each point's chunk
+// sums in chunk order and stores them.
+template <int L>
+__global__ void __launch_bounds__(256)
+    k_acc_reduce(const int32_t* __restrict__ list, const int32_t* __restrict__ n_list, int64_t gb, int nch,
+                 int64_t cap, const Sum6* __restrict__ part, double* __restrict__ phi, double* __restrict__ E,
+                 double* __restrict__ err, float2* __restrict__ bound) {
+    const int64_t count = *n_list;
+    const int64_t G = (count + kAT - 1) / kAT;
+    const int64_t Gm = (G / gb) * gb;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cap || Gm * kAT + i >= count) return;
+    const int64_t p = list[Gm * kAT + i];
+    Sum6 tot{0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < nch; ++k) add6(tot, part[(int64_t)k * cap + i]);
+    store_acc<L>(p, tot, phi, E, err, bound);
+}
+
 __global__ void __launch_bounds__(kEvalThreads)
     k_eval_acc_near1(const GeomView g, const ImageTable img, const double* __restrict__ pts,
                      const int32_t* __restrict__ list, const int32_t* __restrict__ n_list, double* __restrict__ phi,
@@ -457,6 +455,23 @@ __global__ void __launch_bounds__(256)
     if (f) list[s_base + s_warp[w] + __popc(ballot & ((1u << lane) - 1u))] = p;
 }
 
+// Blocks of a far launch and the partial-sum layout of its left-over groups, from the
+// largest possible list (npts points): gb resident blocks at most (kATBlocks per SM), no more than
+// there are pieces; cap >= kAT * R for any list length (R < gb, and R <= the groups of npts).
+struct RefineGrid {
+    int64_t gb, cap;
+    int nch;
+};
+
+RefineGrid refine_grid(int64_t npts, int sms, int64_t n_el) {
+    RefineGrid r;
+    const int64_t want = std::max<int64_t>(1, (npts + kAT - 1) / kAT);
+    r.nch = (int)std::max<int64_t>(1, (n_el + kChunkEl - 1) / kChunkEl);
+    r.gb = std::max<int64_t>(1, std::min<int64_t>(want * r.nch, kATBlocks * (int64_t)sms));
+    r.cap = std::min(want, r.gb) * kAT;
+    return r;
+}
+
 template <int L>
 cudaError_t launch_level(const AccView& A, const ImageTable& img, const double* pts, int64_t npts, double* phi,
                          double* E, double* err, float2* bound, const int32_t* list, const int32_t* n_list, int sms,
@@ -466,26 +481,18 @@ cudaError_t launch_level(const AccView& A, const ImageTable& img, const double* 
     int te = 16;
     while (te > 1 && acc_tile_f4(te, img.n, Lv::kStaged, Lv::kHdr) * (int)sizeof(float4) > 40 * 1024) te /= 2;
     const size_t smem = (size_t)acc_tile_f4(te, img.n, Lv::kStaged, Lv::kHdr) * sizeof(float4);
-    const int64_t want = (npts + kAT - 1) / kAT;
-    cudaError_t e;
-    if (part) {  // split over element chunks (a few points)
-        e = cudaFuncSetAttribute(k_eval_acc_far_chunk<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        const int nch = (int)((A.n_el + kChunkEl - 1) / kChunkEl);
-        k_eval_acc_far_chunk<L><<<dim3((unsigned)want, (unsigned)nch), kAT, smem, s>>>(A, img.n, te, pts, list, n_list,
-                                                                                       npts, part);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        k_acc_reduce<L><<<(unsigned)((npts + 255) / 256), 256, 0, s>>>(list, n_list, npts, nch, part, phi, E, err,
-                                                                         bound);
-    } else {
-        e = cudaFuncSetAttribute(k_eval_acc_far<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        const unsigned gf = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 3 * (int64_t)sms));
-        k_eval_acc_far<L><<<gf, kAT, smem, s>>>(A, img.n, te, pts, list, n_list, phi, E, err, bound);
-    }
+    const RefineGrid rg = refine_grid(npts, sms, A.n_el);
+    cudaError_t e = cudaFuncSetAttribute(k_eval_acc_far<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_eval_acc_far<L><<<(unsigned)rg.gb, kAT, smem, s>>>(A, img.n, te, pts, list, n_list, rg.nch, rg.cap, part, phi,
+                                                         E, err, bound);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    k_acc_reduce<L><<<(unsigned)((rg.cap + 255) / 256), 256, 0, s>>>(list, n_list, rg.gb, rg.nch, rg.cap, part, phi,
+                                                                      E, err, bound);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t want = (npts + kAT - 1) / kAT;
     const unsigned gn = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 8 * (int64_t)sms));
     if (L == 1)
         k_eval_acc_near1<<<gn, kEvalThreads, 0, s>>>(A.view, img, pts, list, n_list, phi, E);
@@ -496,14 +503,16 @@ cudaError_t launch_level(const AccView& A, const ImageTable& img, const double* 
 
 }  // namespace
 
-size_t refine_chunk_bytes(int64_t npts, int64_t n_el) {
-    return sizeof(Sum6) * (size_t)npts * (size_t)((n_el + kChunkEl - 1) / kChunkEl);
+size_t refine_part_bytes(int64_t npts, int sms, int64_t n_el) {
+    const RefineGrid rg = refine_grid(npts, sms, n_el);
+    return sizeof(Sum6) * (size_t)rg.cap * (size_t)rg.nch;
 }
 
 cudaError_t launch_eval_refine(const AccView& A, const ImageTable& img, const double* pts, int64_t npts,
                                double* phi, double* E, double* err, double tol, const MixedScratch& ms, int sms,
-                               cudaStream_t s, cudaEvent_t* ev, void* chunk_part) {
-    Sum6* part = static_cast<Sum6*>(chunk_part);
+                               cudaStream_t s, cudaEvent_t* ev, void* part_buf) {
+    Sum6* part = static_cast<Sum6*>(part_buf);
+    if (!part) return cudaErrorInvalidValue;
     if (npts == 0) return cudaSuccess;
     if (npts > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
     const bool refine = tol > 0.0 && (phi || E);

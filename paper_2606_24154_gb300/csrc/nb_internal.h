@@ -176,12 +176,12 @@ struct AccView {
 // pairs, in two levels (eval_acc.cu); err (may be NULL, n x 2) receives the estimated
 // absolute error of phi and |E| of every point.  sms = multiprocessors of the device.
 // ev (may be NULL): two events recorded after the first and after the second level.
-// chunk_part (may be NULL): refine_chunk_bytes(npts, n_el) bytes of partial sums; when
-// given, each level is split over element chunks (more CTAs for a few points; same bits).
+// part: refine_part_bytes(npts, sms, n_el) bytes of device scratch for the partial sums of
+// the point groups that a level splits over element chunks to keep every block busy.
 cudaError_t launch_eval_refine(const AccView& A, const ImageTable& img, const double* pts, int64_t npts,
                                double* phi, double* E, double* err, double tol, const MixedScratch& ms, int sms,
-                               cudaStream_t s, cudaEvent_t* ev = nullptr, void* chunk_part = nullptr);
-size_t refine_chunk_bytes(int64_t npts, int64_t n_el);
+                               cudaStream_t s, cudaEvent_t* ev, void* part);
+size_t refine_part_bytes(int64_t npts, int sms, int64_t n_el);
 cudaError_t launch_pair_tiers(const FarNodes* far, const float4* cjk, int64_t n_el, int nimg, const double* pts,
                               int64_t npts, uint8_t* codes, cudaStream_t s);
 cudaError_t launch_image_centroids(const Elem* el, int64_t n, const ImageTable& img, float4* cjk, cudaStream_t s);

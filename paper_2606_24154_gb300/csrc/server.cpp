@@ -113,7 +113,7 @@ struct Server {
     std::vector<cudaEvent_t> refine_done;  // per slot
     bool kernel_launched = false;
     DevBuf d_geoms, d_pts, d_phi, d_E, d_head, d_remaining, d_partials, d_pcount;
-    DevBuf d_rpart;                           // refinement partial sums of a small request
+    DevBuf d_rpart;                           // refinement partial sums (groups split over chunks)
     DevBuf d_bound, d_list, d_list2, d_nlist;  // refinement: error scales, the two levels' lists (arena
                                                // index), their counts (two per slot)
     std::vector<int32_t> nchunks;  // element chunks per geometry
@@ -179,10 +179,8 @@ struct Server {
         ms.list = d_list.as<int32_t>() + r->offset;
         ms.list2 = d_list2.as<int32_t>() + r->offset;
         ms.n_list = d_nlist.as<int32_t>() + 2 * r->slot;
-        // a small request's re-evaluation is split over element chunks, so that its few points
-        // still spread over many CTAs (same bits; the refine stream runs one request at a time,
-        // so one partial-sum area serves them all)
-        void* part = (r->n <= kSmallPoints) ? d_rpart.ptr : nullptr;
+        // the refine stream runs one request at a time, so one partial-sum area serves them all
+        void* part = d_rpart.ptr;
         CK(launch_eval_refine(A, c->img, d_pts.as<double>() + 3 * r->offset, r->n,
                               r->phi ? d_phi.as<double>() + r->offset : nullptr,
                               r->E ? d_E.as<double>() + 3 * r->offset : nullptr, nullptr, c->opt.mixed_point_tol, ms,
@@ -406,7 +404,7 @@ int nebem_server_create(nebem_server** out, nebem_ctx* const* ctxs, int32_t n_ct
         (e = s->d_bound.ensure(sizeof(float2) * cap)) != cudaSuccess ||
         (e = s->d_list.ensure(sizeof(int32_t) * cap)) != cudaSuccess ||
         (e = s->d_list2.ensure(sizeof(int32_t) * cap)) != cudaSuccess ||
-        (e = s->d_rpart.ensure(refine_chunk_bytes(std::min<int64_t>(kSmallPoints, cap), max_el))) != cudaSuccess ||
+        (e = s->d_rpart.ensure(refine_part_bytes(cap, cs[0]->props.multiProcessorCount, max_el))) != cudaSuccess ||
         (e = s->d_nlist.ensure(2 * sizeof(int32_t) * o.max_requests)) != cudaSuccess ||
         (e = s->d_pcount.ensure(sizeof(int) * kPartialBlocks)) != cudaSuccess)
         return bail(cuda_fail(e, "server device buffers"));

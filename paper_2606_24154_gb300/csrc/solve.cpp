@@ -239,7 +239,8 @@ int eval_elements(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double*
             const int rc = ensure_fill_tables(c);
             if (rc) return rc;
         }
-        CK(c->d_scratch.ensure(eval_mixed_scratch_bytes(n)));
+        const size_t ms_bytes = eval_mixed_scratch_bytes(n);  // a multiple of 256
+        CK(c->d_scratch.ensure(ms_bytes + refine_part_bytes(n, c->props.multiProcessorCount, c->n)));
         const MixedScratch ms = mixed_scratch(c->d_scratch.ptr, n);
         c->eval_timed = false;
         CK(cudaEventRecord(c->ev_eval[0], s));
@@ -264,7 +265,8 @@ int eval_elements(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double*
             A.cell_start = c->d_fill_cell_start.as<int32_t>();
             A.cell_items = c->d_fill_cell_items.as<int32_t>();
             CK(launch_eval_refine(A, c->img, d_pts, n, d_phi, d_E, err, c->opt.mixed_point_tol, ms,
-                                  c->props.multiProcessorCount, s, &c->ev_eval[2]));
+                                  c->props.multiProcessorCount, s, &c->ev_eval[2],
+                                  static_cast<char*>(c->d_scratch.ptr) + ms_bytes));
             c->refine_list = ms.n_list;
         } else {
             CK(cudaMemsetAsync(ms.n_list, 0, 2 * sizeof(int32_t), s));
