@@ -460,6 +460,26 @@ def run_native(args):
         _, inf, _ = c2.solve(prec)
         solve[name] = {"ms_fill": inf.ms_fill, "ms_factor": inf.ms_factor, "ms_solve": inf.ms_solve,
                        "refinement_iterations": inf.iterations}
+        # weighting fields of every conductor (Sec. 2.1) with the retained factors: the k
+        # right-hand sides through each sweep together, against k single unit-voltage solves
+        k = len(g.voltages)
+        ro = list(range(k))
+        N.nebem_weighting_fields(c2.h, ro, prec, g.n)  # warm-up (work space)
+        t = time.perf_counter()
+        W, winf, _ = N.nebem_weighting_fields(c2.h, ro, prec, g.n)
+        wall_multi = time.perf_counter() - t
+        ms_single, t = 0.0, time.perf_counter()
+        for r in ro:
+            v = np.zeros(k)
+            v[r] = 1.0
+            N.nebem_set_bc(c2.h, v)
+            _, sinf, _ = c2.solve(prec)
+            ms_single += sinf.ms_solve
+        wall_single = time.perf_counter() - t
+        solve[name]["weighting"] = {"readouts": k, "ms_multi_rhs": winf.ms_solve, "ms_k_single_solves": ms_single,
+                                    "wall_ms_multi_rhs": wall_multi * 1e3, "wall_ms_k_single_solves": wall_single * 1e3,
+                                    "refinement_iterations": winf.iterations, "residual": winf.residual}
+        N.nebem_set_bc(c2.h, g.voltages)
         c2.close()
 
     # ---- serving: configs 0-2 resident (cube, THGEM cell, double THGEM), continuous batching

@@ -204,6 +204,30 @@ int nebem_set_bc(nebem_ctx *ctx, const double *voltages, int32_t n_conductors);
  * returned, so the context stays usable), NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
 int nebem_solve(nebem_ctx *ctx, int32_t precision, double *sigma_out, nebem_solve_info *info);
 
+/* Weighting fields (Sec. 2.1: the influence matrix does not depend on the voltages, so a
+ * weighting field is one more solve with the retained factors and a unit-readout
+ * right-hand side): for each readout[j] (j < k), the charge densities with unit potential
+ * on the elements of conductor readout[j], 0 on every other conductor, 0 on interface rows
+ * and no known charges.  The matrix and factors are made on first use as in nebem_solve and
+ * kept; all k right-hand sides go through each triangular sweep together (8 per pass, the
+ * factors read once per pass), each column with the arithmetic of a single solve, so
+ * column j equals nebem_set_bc (unit voltages) + nebem_solve bit for bit when no known
+ * charges are set.  NEBEM_MIXED: FP32 solves with FP64 iterative refinement, each column
+ * stopping when its own correction meets ir_tol.  The context's charge densities and
+ * voltages are not changed.
+ *   readout    k conductor indices (host), each the index of at least one conductor
+ *              element; repeats allowed.  1 <= k <= 64.
+ *   sigma_out  host, n * k doubles, column-major (column j = readout[j]'s densities);
+ *              may be NULL.  info (may be NULL): iterations and correction are the largest
+ *              over the columns, residual the largest ||K x_j - b_j|| / ||x_j||.
+ * Errors: NEBEM_INVALID_ARG (NULL, k, precision, a readout with no element),
+ * NEBEM_BAD_STATE (no geometry), NEBEM_SINGULAR, NEBEM_NOT_CONVERGED (some column missed
+ * ir_tol; sigma_out is still written), NEBEM_TIMEOUT (a sweep's bounded wait ran out, see
+ * wait_polls: sigma_out is written with NaN in the blocks whose wait ran out; the context's
+ * own densities are not affected), NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
+int nebem_weighting_fields(nebem_ctx *ctx, const int32_t *readout, int32_t k, int32_t precision, double *sigma_out,
+                           nebem_solve_info *info);
+
 /* Replace the charge densities (sigma_j of Eq. Potential; n values, host, copied)
  * without solving, e.g. to evaluate a stored solution.  Errors: NEBEM_BAD_STATE (no
  * geometry), NEBEM_INVALID_ARG (NULL, or n not the element count), NEBEM_CUDA. */
@@ -462,8 +486,7 @@ int nebem_lu_factor_device_noalloc(double *d_A, int64_t n, int32_t *d_piv, void 
  * exactly on an element's edge or vertex takes the field there, which diverges
  * logarithmically (non-finite values that reach the cells around that node): keep nodes
  * off element boundaries, e.g. by offsetting regular grids by a small fraction.
- * For a weighting-field map, set unit voltages on the readout (nebem_set_bc), solve with
- * the retained factors and build.  Errors: NEBEM_BAD_STATE (no charge densities),
+ * Weighting-field maps, one per readout, come from nebem_weighting_fastvol_build.  Errors: NEBEM_BAD_STATE (no charge densities),
  * NEBEM_INVALID_ARG, NEBEM_TOO_LARGE, NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
 int nebem_fastvol_build(nebem_ctx *ctx, const double *x_nodes, int32_t nx, const double *y_nodes, int32_t ny,
                         const double *z_nodes, int32_t nz, int32_t precision);
@@ -480,6 +503,34 @@ int nebem_fastvol_eval(nebem_ctx *ctx, const double *pts, int64_t n, double *phi
  * stream; device pointers, d_phi or d_E may be NULL).  Errors as nebem_fastvol_eval. */
 int nebem_fastvol_eval_device(nebem_ctx *ctx, const double *d_pts, int64_t n, double *d_phi, double *d_E,
                               void *stream);
+
+/* Weighting-field FastVolume maps (Sec. 2.1 weighting fields, Sec. 3.3 FastVolume): one
+ * map per readout, each a handle of its own (independent of the context and of one
+ * another; the context's own map and charge densities are not changed).  The k weighting
+ * fields are solved as in nebem_weighting_fields, then the potential and field of each are
+ * evaluated at the grid nodes (axes as in nebem_fastvol_build; elements with images only,
+ * no known charges) in `precision` (NEBEM_MIXED: the refined mixed evaluation).
+ * maps_out[k] receives the handles (each freed with nebem_fvmap_destroy); on an error none
+ * is returned.  info (may be NULL) as in nebem_weighting_fields.  Errors: those of
+ * nebem_weighting_fields and nebem_fastvol_build, NEBEM_BAD_STATE (Adaptive Modelling on),
+ * NEBEM_OUT_OF_MEMORY. */
+typedef struct nebem_fvmap nebem_fvmap;
+int nebem_weighting_fastvol_build(nebem_ctx *ctx, const int32_t *readout, int32_t k, const double *x_nodes,
+                                  int32_t nx, const double *y_nodes, int32_t ny, const double *z_nodes, int32_t nz,
+                                  int32_t precision, nebem_fvmap **maps_out, nebem_solve_info *info);
+
+/* Trilinear lookup of one map (as nebem_fastvol_eval; host buffers, phi or E may be NULL;
+ * the map's own stream, synchronised before return).  Errors: NEBEM_INVALID_ARG,
+ * NEBEM_TOO_LARGE (n), NEBEM_OUT_OF_MEMORY, NEBEM_CUDA. */
+int nebem_fvmap_eval(nebem_fvmap *map, const double *pts, int64_t n, double *phi, double *E);
+
+/* Device variant (asynchronous on `stream`, NULL = the map's own stream; device pointers,
+ * d_phi or d_E may be NULL).  Errors as nebem_fvmap_eval. */
+int nebem_fvmap_eval_device(nebem_fvmap *map, const double *d_pts, int64_t n, double *d_phi, double *d_E,
+                            void *stream);
+
+/* Free a map (NULL is allowed).  Always NEBEM_OK. */
+int nebem_fvmap_destroy(nebem_fvmap *map);
 
 /* Image translations of the current geometry in index order (the virtual copies of
  * Sec. 5 Case 2; count * 3 doubles, host).  *count receives the number of images; t_out

@@ -320,6 +320,38 @@ int nebem_solve(nebem_ctx* ctx, int32_t precision, double* sigma_out, nebem_solv
     return rc;
 }
 
+int nebem_weighting_fields(nebem_ctx* ctx, const int32_t* readout, int32_t k, int32_t precision, double* sigma_out,
+                           nebem_solve_info* info) {
+    if (!ctx || !readout) return fail(NEBEM_INVALID_ARG, "NULL argument");
+    if (k < 1 || k > 64) return fail(NEBEM_INVALID_ARG, "k must be 1..64");
+    if (precision != NEBEM_FP64 && precision != NEBEM_MIXED) return fail(NEBEM_INVALID_ARG, "bad precision");
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    if (c->n == 0) return fail(NEBEM_BAD_STATE, "set_geometry first");
+    for (int32_t j = 0; j < k; ++j) {
+        bool found = false;
+        for (int64_t i = 0; i < c->n && !found; ++i)
+            found = c->h_bc[i] == NEBEM_CONDUCTOR && c->h_cond[i] == readout[j];
+        if (!found)
+            return fail(NEBEM_INVALID_ARG, "readout " + std::to_string(readout[j]) + " is no conductor of the geometry");
+    }
+    CK(cudaSetDevice(c->device));
+    nebem_solve_info inf;
+    std::memset(&inf, 0, sizeof(inf));
+    inf.precision = precision;
+    int rc = ensure_fill(c, precision, &inf.ms_fill);
+    if (rc) return rc;
+    rc = ensure_factors(c, precision, &inf.ms_factor);
+    if (rc) return rc;
+    rc = weighting_solve(c, readout, k, precision, &inf);
+    if (sigma_out && (rc == NEBEM_OK || rc == NEBEM_NOT_CONVERGED || rc == NEBEM_TIMEOUT)) {
+        CK(cudaMemcpyAsync(sigma_out, c->d_wX.ptr, sizeof(double) * (size_t)c->n * (size_t)k, cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    if (info) *info = inf;
+    return rc;
+}
+
 int nebem_set_sigma(nebem_ctx* ctx, const double* sigma, int64_t n) {
     if (!ctx || !sigma) return fail(NEBEM_INVALID_ARG, "NULL argument");
     Ctx* c = reinterpret_cast<Ctx*>(ctx);

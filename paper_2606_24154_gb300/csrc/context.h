@@ -95,6 +95,8 @@ struct Ctx {
     DevBuf d_perm64, d_perm32, d_swork;  // pivot permutations, solve / residual work space
     bool K_valid = false, fac64_valid = false, fac32_valid = false;
     DevBuf d_b, d_x, d_r, d_r32, d_small;
+    // weighting fields: unit right-hand sides, solutions, residuals (n x k), FP32 corrections
+    DevBuf d_wB, d_wX, d_wR, d_wR32;
 
     // evaluation staging (host-pointer variant) and scratch; refine_list = device count of
     // the points the last refined mixed evaluation re-evaluated (inside d_scratch)
@@ -126,6 +128,9 @@ int ensure_fill(Ctx* c, int precision, double* ms);
 int ensure_factors(Ctx* c, int precision, double* ms);
 int build_rhs(Ctx* c);
 int solve_with_factors(Ctx* c, int precision, nebem_solve_info* info);
+// k weighting-field solutions (unit potential on readout[j], 0 on the other conductors, no
+// known charges) into c->d_wX (n x k, column-major) with the retained factors
+int weighting_solve(Ctx* c, const int32_t* readout, int k, int precision, nebem_solve_info* info);
 // two-float tables of the mixed fill and of the refined evaluation (built on first use)
 int ensure_fill_tables(Ctx* c);
 // elements only (with images); err (may be NULL, n x 2): per-point error estimates of a

@@ -676,7 +676,6 @@ cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_inf
 
 // ---------------------------------------------------------------- triangular solves
 constexpr int kTB = 64;          // solve block
-constexpr int kSweepThreads = 128;
 constexpr int kResRows = 256;    // residual: rows per CTA
 constexpr int kResChunk = 2048;  // residual: columns per partial sum
 
@@ -923,6 +922,209 @@ __global__ void __launch_bounds__(kSvThreads) k_trsv(const T* __restrict__ LU, i
     if (threadIdx.x == 0) st_release(flags + k, 1);
 }
 
+// The same sweep for nr <= kMR right-hand sides at once (columns of rhs and x, leading
+// dimension n; used for the weighting fields of several readouts, Sec. 2.1).  Each factor
+// block is read once for all columns; per column the arithmetic is k_trsv's, in its order
+// (the fma chain over blocks and columns, the four group sums, the diagonal block: FP64
+// substitution, one warp per column; FP32 explicit inverse), so column j equals k_trsv on
+// that column bit for bit.  Waits, give-up and publication as in k_trsv.
+constexpr int kMR = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kSvThreads) k_trsm(const T* __restrict__ LU, int64_t n, int64_t nblk, int lower,
+                                                     const T* __restrict__ rhs, T* x, int nr, int* flags,
+                                                     int* ticket, int* err, long long limit) {
+    constexpr bool kInv = sizeof(T) == 4;
+    __shared__ T D[kTB][kTB + 1];
+    __shared__ T Xi[kInv ? kTB : 1][kTB + 1];
+    __shared__ T part[kSvThreads / kTB][kTB];
+    __shared__ T xs[kMR][kTB];
+    __shared__ T xo[kInv ? 1 : kMR][kTB];
+    __shared__ T dinv[kTB];
+    __shared__ int s_t, s_ready, s_ok;
+    if (threadIdx.x == 0) s_t = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int64_t t = s_t;
+    const int64_t k = lower ? t : nblk - 1 - t;
+    const int64_t r0 = k * kTB, r1 = min(n, r0 + (int64_t)kTB);
+    const int w = (int)(r1 - r0);
+    constexpr int kGroups = kSvThreads / kTB, kCols = kTB / kGroups;
+    const int row = threadIdx.x % kTB, grp = threadIdx.x / kTB;
+    for (int idx = threadIdx.x; idx < w * w; idx += kSvThreads) {
+        const int r = idx % w, c = idx / w;
+        D[r][c] = LU[(r0 + r) + (r0 + c) * n];
+    }
+    T rhs_own[kMR];
+#pragma unroll
+    for (int j = 0; j < kMR; ++j) rhs_own[j] = (threadIdx.x < w && j < nr) ? rhs[r0 + threadIdx.x + j * n] : (T)0;
+    if (!lower && threadIdx.x < w) dinv[threadIdx.x] = (T)1 / LU[(r0 + threadIdx.x) + (r0 + threadIdx.x) * n];
+    if constexpr (kInv) {
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < kTB * kTB; idx += kSvThreads) {
+            const int r = idx % kTB, c = idx / kTB;
+            Xi[r][c] = (r == c && r < w) ? (T)1 : (T)0;
+        }
+        __syncthreads();
+        if (lower) {
+            for (int q = 0; q + 1 < w; ++q) {
+                const int rows = w - 1 - q;
+                for (int idx = threadIdx.x; idx < rows * (q + 1); idx += kSvThreads) {
+                    const int r = q + 1 + idx % rows, c = idx / rows;
+                    Xi[r][c] -= D[r][q] * Xi[q][c];
+                }
+                __syncthreads();
+            }
+        } else {
+            for (int q = w - 1; q >= 0; --q) {
+                const int cols = w - q;
+                for (int c = q + threadIdx.x; c < w; c += kSvThreads) Xi[q][c] *= dinv[q];
+                __syncthreads();
+                for (int idx = threadIdx.x; idx < q * cols; idx += kSvThreads) {
+                    const int r = idx % q, c = q + idx / q;
+                    Xi[r][c] -= D[r][q] * Xi[q][c];
+                }
+                __syncthreads();
+            }
+        }
+    }
+    T acc[kMR];
+#pragma unroll
+    for (int j = 0; j < kMR; ++j) acc[j] = (T)0;
+    const int64_t total = lower ? k : nblk - 1 - k;
+    T mv[kCols];
+    auto load_block = [&](int64_t i) {
+        const int64_t c0 = (lower ? i : nblk - 1 - i) * kTB + grp * kCols;
+        const T* col = LU + (r0 + row) + c0 * n;
+        const int wc = (int)min((int64_t)kCols, n - c0);
+#pragma unroll
+        for (int q = 0; q < kCols; ++q) mv[q] = (row < w && q < wc) ? col[(int64_t)q * n] : (T)0;
+    };
+    auto use_block = [&](int64_t i) {
+        const int64_t c0 = (lower ? i : nblk - 1 - i) * kTB + grp * kCols;
+        const int wc = (int)min((int64_t)kCols, n - c0);
+#pragma unroll
+        for (int q = 0; q < kCols; ++q)
+            if (q < wc) {
+#pragma unroll
+                for (int j = 0; j < kMR; ++j)
+                    if (j < nr) acc[j] = fma(mv[q], __ldcg(x + c0 + q + (int64_t)j * n), acc[j]);
+            }
+    };
+    if (total > 0) load_block(0);
+    int64_t done = 0;
+    long long spins = 0;
+    bool ok = true;
+    while (done < total) {
+        if (threadIdx.x == 0) {
+            const int* fp = flags + (lower ? done : nblk - 1 - done);
+            int f = ld_acquire(fp);
+            while (!f && ++spins <= limit) {
+                __nanosleep(32);
+                f = ld_acquire(fp);
+            }
+            s_ok = f != 0;
+            s_ready = kSvThreads;
+        }
+        __syncthreads();
+        if (!s_ok) {
+            ok = false;
+            break;
+        }
+        int64_t ready = 1;
+        if (total - done > 1) {
+            const int64_t idx = done + threadIdx.x;
+            if (threadIdx.x > 0 && idx < total && ld_acquire(flags + (lower ? idx : nblk - 1 - idx)) == 0)
+                atomicMin(&s_ready, (int)threadIdx.x);
+            __syncthreads();
+            ready = min((int64_t)s_ready, total - done);
+        }
+        __syncthreads();
+        use_block(done);
+        for (int64_t i = done + 1; i < done + ready; ++i) {
+            load_block(i);
+            use_block(i);
+        }
+        done += ready;
+        if (done < total) load_block(done);
+    }
+    if (!ok) atomicExch(err, 1);
+    // per column: the four group sums in order, subtracted from the block's right-hand side
+    for (int j = 0; j < nr; ++j) {
+        part[grp][row] = acc[0];
+        __syncthreads();
+        if (threadIdx.x < w) {
+            T sum = part[0][threadIdx.x];
+#pragma unroll
+            for (int g = 1; g < kGroups; ++g) sum += part[g][threadIdx.x];
+            xs[j][threadIdx.x] = rhs_own[0] - sum;
+        }
+        __syncthreads();
+        // next column into slot 0 (registers are not indexed by a runtime j)
+#pragma unroll
+        for (int q = 0; q + 1 < kMR; ++q) {
+            acc[q] = acc[q + 1];
+            rhs_own[q] = rhs_own[q + 1];
+        }
+    }
+    if constexpr (kInv) {
+        for (int j = 0; j < nr; ++j) {
+            T v = (T)0;
+            if (row < w) {
+#pragma unroll
+                for (int q = 0; q < kCols; ++q) {
+                    const int c = grp * kCols + q;
+                    if (c < w) v = fma(Xi[row][c], xs[j][c], v);
+                }
+            }
+            part[grp][row] = v;
+            __syncthreads();
+            if (threadIdx.x < w) {
+                T sum = part[0][threadIdx.x];
+#pragma unroll
+                for (int g = 1; g < kGroups; ++g) sum += part[g][threadIdx.x];
+                xs[j][threadIdx.x] = sum;
+            }
+            __syncthreads();
+        }
+    } else {
+        const int j = threadIdx.x / 32, lane = threadIdx.x % 32;
+        if (j < nr) {
+            if (lower) {
+                for (int c = 0; c < w; ++c) {
+                    const T xc = xs[j][c];
+                    for (int r = lane; r < w; r += 32)
+                        if (r > c) xs[j][r] -= D[r][c] * xc;
+                    __syncwarp();
+                }
+            } else {
+                for (int c = w - 1; c >= 0; --c) {
+                    const T xc = xs[j][c] * dinv[c];
+                    if (lane == (c & 31)) xo[j][c] = xc;
+                    for (int r = lane; r < c; r += 32) xs[j][r] -= D[r][c] * xc;
+                    __syncwarp();
+                }
+                for (int r = lane; r < w; r += 32) xs[j][r] = xo[j][r];
+            }
+        }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < w * nr; idx += kSvThreads) {
+        const int j = idx / w, r = idx - j * w;
+        x[r0 + r + (int64_t)j * n] = ok ? xs[j][r] : (T)NAN;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) st_release(flags + k, 1);
+}
+
+template <typename T>
+__global__ void k_permute_m(const T* __restrict__ b, const int32_t* __restrict__ perm, int64_t n, int nr,
+                            T* __restrict__ y) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * nr) return;
+    const int64_t j = idx / n, i = idx - j * n;
+    y[idx] = b[perm[i] + j * n];
+}
+
 template <typename T>
 cudaError_t lu_solve(const T* LU, int64_t n, const int32_t* perm, T* b, T* work, cudaStream_t s, long long polls) {
     if (n == 0) return cudaSuccess;
@@ -966,6 +1168,77 @@ __global__ void k_residual_final(const double* __restrict__ part, int64_t nchunk
     double s = 0.0;
     for (int64_t c = 0; c < nchunk; ++c) s += part[c * n + i];
     r[i] = b[i] - s;
+}
+
+// r_j = b_j - K x_j for nr <= kMR columns at once (leading dimension n): K is read once for
+// all columns; per column the sums are k_residual_partial's (an fma chain over the chunk's
+// columns in order) and k_residual_final's (the chunks in order), so column j equals the
+// single-column residual bit for bit.  x is staged in shared memory kResTile columns at a time.
+constexpr int kResTile = 512;
+
+__global__ void __launch_bounds__(kResRows) k_residual_partial_m(const double* __restrict__ K, int64_t n,
+                                                                 const double* __restrict__ x, int nr,
+                                                                 double* __restrict__ part) {
+    const int64_t i = (int64_t)blockIdx.x * kResRows + threadIdx.x;
+    const int64_t j0 = (int64_t)blockIdx.y * kResChunk, j1 = min(n, j0 + (int64_t)kResChunk);
+    __shared__ double xs[kResTile][kMR];
+    double s[kMR];
+#pragma unroll
+    for (int c = 0; c < kMR; ++c) s[c] = 0.0;
+    for (int64_t t0 = j0; t0 < j1; t0 += kResTile) {
+        const int64_t t1 = min(j1, t0 + (int64_t)kResTile);
+        __syncthreads();
+        for (int64_t idx = threadIdx.x; idx < (t1 - t0) * nr; idx += kResRows) {
+            const int64_t c = idx / (t1 - t0), j = idx - c * (t1 - t0);
+            xs[j][c] = x[t0 + j + c * n];
+        }
+        __syncthreads();
+        if (i < n)
+            for (int64_t j = t0; j < t1; ++j) {
+                const double kv = K[i + j * n];
+#pragma unroll
+                for (int c = 0; c < kMR; ++c)
+                    if (c < nr) s[c] = fma(kv, xs[j - t0][c], s[c]);
+            }
+    }
+    if (i < n)
+#pragma unroll
+        for (int c = 0; c < kMR; ++c)
+            if (c < nr) part[((int64_t)blockIdx.y * kMR + c) * n + i] = s[c];
+}
+
+__global__ void k_residual_final_m(const double* __restrict__ part, int64_t nchunk, int64_t n, int nr,
+                                   const double* __restrict__ b, double* __restrict__ r) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * nr) return;
+    const int64_t c = idx / n, i = idx - c * n;
+    double s = 0.0;
+    for (int64_t q = 0; q < nchunk; ++q) s += part[(q * kMR + c) * n + i];
+    r[idx] = b[idx] - s;
+}
+
+// x_j += d_j for the columns j whose bit is set in `active`; norms[2j] = max|d_j|,
+// norms[2j + 1] = max|x_j| (as k_ir_update, one column per blockIdx.y).
+__global__ void k_ir_update_m(double* __restrict__ x, const float* __restrict__ d, int64_t n, uint32_t active,
+                              double* norms) {
+    const int64_t c = blockIdx.y;
+    if (!((active >> c) & 1u)) return;
+    double md = 0.0, mx = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double di = (double)d[i + c * n];
+        const double xi = x[i + c * n] + di;
+        x[i + c * n] = xi;
+        md = fmax(md, fabs(di));
+        mx = fmax(mx, fabs(xi));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        md = fmax(md, __shfl_xor_sync(0xffffffffu, md, o));
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(reinterpret_cast<unsigned long long*>(norms + 2 * c), __double_as_longlong(md));
+        atomicMax(reinterpret_cast<unsigned long long*>(norms + 2 * c + 1), __double_as_longlong(mx));
+    }
 }
 
 __global__ void k_f64_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
@@ -1097,6 +1370,86 @@ cudaError_t vec_absmax(const double* a, int64_t n, double* out, cudaStream_t s) 
     NB_TRY(cudaMemsetAsync(out, 0, sizeof(double), s));
     k_absmax<<<(unsigned)std::min<int64_t>(1024, (n + 255) / 256), 256, 0, s>>>(a, n, out);
     return cudaGetLastError();
+}
+
+// ---- several right-hand sides (columns of leading dimension n), kMR per pass
+size_t lu_solve_multi_work_bytes(int64_t n, size_t tsize) {
+    return 2 * tsize * (size_t)n * kMR + 16 + sizeof(int) * (size_t)(2 * ((n + kTB - 1) / kTB) + 3) + 256;
+}
+static int* multi_flags(const void* work, int64_t n, size_t tsize) {
+    // y, z (n x kMR values each), then 16-byte aligned flags of both sweeps, the two
+    // tickets and the error flag
+    const uintptr_t fo =
+        ((uintptr_t)static_cast<const char*>(work) + 2 * tsize * (size_t)n * kMR + 15) & ~(uintptr_t)15;
+    return reinterpret_cast<int*>(fo);
+}
+const int* lu_solve_multi_err_flag(const void* work, int64_t n, size_t tsize) {
+    return multi_flags(work, n, tsize) + 2 * ((n + kTB - 1) / kTB) + 2;
+}
+template <typename T>
+static cudaError_t lu_solve_multi(const T* LU, int64_t n, const int32_t* perm, T* B, int64_t nrhs, void* work,
+                                  cudaStream_t s, long long polls) {
+    if (n == 0 || nrhs == 0) return cudaSuccess;
+    const int64_t nblk = (n + kTB - 1) / kTB;
+    T* y = static_cast<T*>(work);
+    T* z = y + n * kMR;
+    int* flags = multi_flags(work, n, sizeof(T));
+    int* tickets = flags + 2 * nblk;
+    int* err = tickets + 2;
+    NB_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
+    const long long limit = polls > 0 ? polls : kSvSpinLimit;
+    for (int64_t c0 = 0; c0 < nrhs; c0 += kMR) {
+        const int nr = (int)std::min<int64_t>(kMR, nrhs - c0);
+        T* b = B + c0 * n;
+        NB_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * (2 * nblk + 2), s));
+        k_permute_m<T><<<(unsigned)((n * nr + 255) / 256), 256, 0, s>>>(b, perm, n, nr, y);
+        k_trsm<T><<<(unsigned)nblk, kSvThreads, 0, s>>>(LU, n, nblk, 1, y, z, nr, flags, tickets, err, limit);
+        k_trsm<T><<<(unsigned)nblk, kSvThreads, 0, s>>>(LU, n, nblk, 0, z, b, nr, flags + nblk, tickets + 1, err,
+                                                        limit);
+        NB_TRY(cudaGetLastError());
+    }
+    return cudaSuccess;
+}
+cudaError_t lu_solve_multi_f64(const double* LU, int64_t n, const int32_t* perm, double* B, int64_t nrhs, void* work,
+                               cudaStream_t s, long long polls) {
+    return lu_solve_multi<double>(LU, n, perm, B, nrhs, work, s, polls);
+}
+cudaError_t lu_solve_multi_f32(const float* LU, int64_t n, const int32_t* perm, float* B, int64_t nrhs, void* work,
+                               cudaStream_t s, long long polls) {
+    return lu_solve_multi<float>(LU, n, perm, B, nrhs, work, s, polls);
+}
+size_t residual_multi_work_bytes(int64_t n) {
+    return sizeof(double) * (size_t)((n + kResChunk - 1) / kResChunk) * kMR * (size_t)n + 256;
+}
+cudaError_t gemv_residual_multi(const double* K, int64_t n, const double* X, int64_t nrhs, const double* B, double* R,
+                                void* work, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int64_t nchunk = (n + kResChunk - 1) / kResChunk;
+    double* part = static_cast<double*>(work);
+    for (int64_t c0 = 0; c0 < nrhs; c0 += kMR) {
+        const int nr = (int)std::min<int64_t>(kMR, nrhs - c0);
+        dim3 grid((unsigned)((n + kResRows - 1) / kResRows), (unsigned)nchunk);
+        k_residual_partial_m<<<grid, kResRows, 0, s>>>(K, n, X + c0 * n, nr, part);
+        k_residual_final_m<<<(unsigned)((n * nr + 255) / 256), 256, 0, s>>>(part, nchunk, n, nr, B + c0 * n,
+                                                                           R + c0 * n);
+        NB_TRY(cudaGetLastError());
+    }
+    return cudaSuccess;
+}
+cudaError_t ir_update_multi(double* X, const float* D, int64_t n, int64_t nrhs, uint64_t active, double* d_norms,
+                            cudaStream_t s) {
+    if (nrhs > 64) return cudaErrorInvalidValue;
+    NB_TRY(cudaMemsetAsync(d_norms, 0, 2 * sizeof(double) * (size_t)nrhs, s));
+    if (n == 0) return cudaSuccess;
+    for (int64_t c0 = 0; c0 < nrhs; c0 += kMR) {
+        const int nr = (int)std::min<int64_t>(kMR, nrhs - c0);
+        const uint32_t act = (uint32_t)((active >> c0) & ((1ull << nr) - 1ull));
+        if (!act) continue;
+        dim3 grid((unsigned)std::min<int64_t>(1024, (n + 255) / 256), (unsigned)nr);
+        k_ir_update_m<<<grid, 256, 0, s>>>(X + c0 * n, D + c0 * n, n, act, d_norms + 2 * c0);
+        NB_TRY(cudaGetLastError());
+    }
+    return cudaSuccess;
 }
 
 }  // namespace nb

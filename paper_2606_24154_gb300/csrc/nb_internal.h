@@ -236,6 +236,23 @@ cudaError_t ir_update(double* x, const float* d, int64_t n, double* d_norms, cud
 cudaError_t copy_f64_to_f32(const double* a, float* b, int64_t n, cudaStream_t s);
 cudaError_t launch_gather(const double* a, const int64_t* idx, int64_t n, double* out, cudaStream_t s);
 cudaError_t vec_absmax(const double* a, int64_t n, double* out, cudaStream_t s);
+// Several right-hand sides (nrhs columns of leading dimension n, solved in place), each
+// column with the single solve's arithmetic (bit for bit); work of
+// lu_solve_multi_work_bytes(n, sizeof(T)) bytes, its give-up flag at lu_solve_multi_err_flag.
+size_t lu_solve_multi_work_bytes(int64_t n, size_t tsize);
+const int* lu_solve_multi_err_flag(const void* work, int64_t n, size_t tsize);
+cudaError_t lu_solve_multi_f64(const double* LU, int64_t n, const int32_t* perm, double* B, int64_t nrhs, void* work,
+                               cudaStream_t s, long long polls);
+cudaError_t lu_solve_multi_f32(const float* LU, int64_t n, const int32_t* perm, float* B, int64_t nrhs, void* work,
+                               cudaStream_t s, long long polls);
+// R = B - K X per column (bit for bit gemv_residual's), work of residual_multi_work_bytes(n)
+size_t residual_multi_work_bytes(int64_t n);
+cudaError_t gemv_residual_multi(const double* K, int64_t n, const double* X, int64_t nrhs, const double* B, double* R,
+                                void* work, cudaStream_t s);
+// X_j += D_j for the columns whose bit is set in active (nrhs <= 64); norms: 2 nrhs doubles
+// (max |D_j|, max |X_j|)
+cudaError_t ir_update_multi(double* X, const float* D, int64_t n, int64_t nrhs, uint64_t active, double* d_norms,
+                            cudaStream_t s);
 
 // space charge (spacecharge.cu)
 cudaError_t launch_sc_split(const double* pos, const double* q, int64_t n, float4* hq, float4* lo, cudaStream_t s);

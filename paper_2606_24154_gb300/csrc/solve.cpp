@@ -217,6 +217,106 @@ int solve_with_factors(Ctx* c, int precision, nebem_solve_info* info) {
     return 0;
 }
 
+// Weighting fields (Sec. 2.1): K does not depend on the voltages, so the k unit-readout
+// right-hand sides are solved with the factors already made, all columns in one pass of
+// each triangular sweep.  FP64: one multi-column solve.  MIXED: FP32 solves of the
+// residuals with FP64 iterative refinement, every column stepping exactly as a single
+// solve of its own right-hand side would (it drops out when its correction meets ir_tol),
+// so column j equals that solve bit for bit.
+int weighting_solve(Ctx* c, const int32_t* readout, int k, int precision, nebem_solve_info* info) {
+    const int64_t n = c->n;
+    const size_t nk = (size_t)n * (size_t)k;
+    std::vector<double> b(nk, 0.0);
+    for (int j = 0; j < k; ++j)
+        for (int64_t i = 0; i < n; ++i)
+            if (c->h_bc[i] == NEBEM_CONDUCTOR && c->h_cond[i] == readout[j]) b[(size_t)j * n + i] = 1.0;
+    CK(c->d_wB.ensure(sizeof(double) * nk));
+    CK(c->d_wX.ensure(sizeof(double) * nk));
+    CK(c->d_wR.ensure(sizeof(double) * nk));
+    CK(c->d_small.ensure(256));
+    CK(c->d_r.ensure(sizeof(double) * 2 * 64));  // per-column norms
+    const size_t tsize = (precision == NEBEM_FP64) ? sizeof(double) : sizeof(float);
+    CK(c->d_swork.ensure(std::max(lu_solve_multi_work_bytes(n, tsize), residual_multi_work_bytes(n))));
+    void* work = c->d_swork.ptr;
+    double* B = c->d_wB.as<double>();
+    double* X = c->d_wX.as<double>();
+    double* R = c->d_wR.as<double>();
+    double* norms = c->d_r.as<double>();
+    CK(cudaMemcpyAsync(B, b.data(), sizeof(double) * nk, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaEventRecord(c->ev0, c->stream));
+    int gave_up = 0, status = 0, iters = 0;
+    double corr_max = 0.0;
+    if (precision == NEBEM_FP64) {
+        CK(cudaMemcpyAsync(X, B, sizeof(double) * nk, cudaMemcpyDeviceToDevice, c->stream));
+        CK(lu_solve_multi_f64(c->d_LU64.as<double>(), n, c->d_perm64.as<int32_t>(), X, k, work, c->stream,
+                              c->opt.wait_polls));
+        CK(cudaMemcpyAsync(&gave_up, lu_solve_multi_err_flag(work, n, tsize), sizeof(int), cudaMemcpyDeviceToHost,
+                           c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    } else {
+        CK(c->d_wR32.ensure(sizeof(float) * nk));
+        float* D = c->d_wR32.as<float>();
+        CK(cudaMemsetAsync(X, 0, sizeof(double) * nk, c->stream));
+        CK(cudaMemcpyAsync(R, B, sizeof(double) * nk, cudaMemcpyDeviceToDevice, c->stream));
+        uint64_t active = (k == 64) ? ~0ull : ((1ull << k) - 1ull);
+        uint64_t converged = 0;
+        std::vector<double> h(2 * (size_t)k);
+        std::vector<double> corr((size_t)k, 1.0);
+        int it = 0;
+        for (it = 1; it <= c->opt.ir_max_iter && active; ++it) {
+            CK(copy_f64_to_f32(R, D, (int64_t)nk, c->stream));
+            CK(lu_solve_multi_f32(c->d_LU32.as<float>(), n, c->d_perm32.as<int32_t>(), D, k, work, c->stream,
+                                  c->opt.wait_polls));
+            CK(cudaMemcpyAsync(&gave_up, lu_solve_multi_err_flag(work, n, tsize), sizeof(int), cudaMemcpyDeviceToHost,
+                               c->stream));
+            CK(ir_update_multi(X, D, n, k, active, norms, c->stream));
+            CK(cudaMemcpyAsync(h.data(), norms, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            if (gave_up) break;
+            uint64_t next = active;
+            for (int j = 0; j < k; ++j) {
+                if (!((active >> j) & 1ull)) continue;
+                corr[j] = (h[2 * j + 1] > 0.0) ? h[2 * j] / h[2 * j + 1] : 0.0;
+                if (!std::isfinite(corr[j])) next &= ~(1ull << j);  // stops unconverged
+            }
+            CK(gemv_residual_multi(c->d_K.as<double>(), n, X, k, B, R, work, c->stream));
+            for (int j = 0; j < k; ++j)
+                if (((next >> j) & 1ull) && corr[j] <= c->opt.ir_tol) {
+                    next &= ~(1ull << j);
+                    converged |= 1ull << j;
+                }
+            iters = it;
+            active = next;
+        }
+        const uint64_t all = (k == 64) ? ~0ull : ((1ull << k) - 1ull);
+        if (converged != all) status = NEBEM_NOT_CONVERGED;
+        for (int j = 0; j < k; ++j) corr_max = std::max(corr_max, corr[j]);
+    }
+    double ms = 0.0;
+    int rc = elapsed_ms(c, &ms);
+    if (rc) return rc;
+    // residual diagnostic per column, the largest ||K x_j - b_j||_inf / ||x_j||_inf
+    CK(gemv_residual_multi(c->d_K.as<double>(), n, X, k, B, R, work, c->stream));
+    double res = 0.0;
+    for (int j = 0; j < k; ++j) {
+        CK(vec_absmax(R + (size_t)j * n, n, norms, c->stream));
+        CK(vec_absmax(X + (size_t)j * n, n, norms + 1, c->stream));
+        double hh[2];
+        CK(cudaMemcpyAsync(hh, norms, sizeof(hh), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        res = std::max(res, hh[1] > 0.0 ? hh[0] / hh[1] : 0.0);
+    }
+    if (info) {
+        info->iterations = iters;
+        info->correction = corr_max;
+        info->residual = res;
+        info->ms_solve = ms;
+    }
+    if (gave_up) return fail(NEBEM_TIMEOUT, "triangular sweep: a bounded wait gave up (NaN in its blocks)");
+    if (status) return fail(status, "iterative refinement did not reach the tolerance for every readout");
+    return 0;
+}
+
 int eval_set(Ctx* c, const EvalSet& es, const double* d_pts, int64_t n, double* d_phi, double* d_E, int precision,
              cudaStream_t s) {
     if (precision == NEBEM_MIXED) {

@@ -125,6 +125,12 @@ SIGNATURES = {
     "nebem_fastvol_build": (C.c_int, [_vp, _d, C.c_int32, _d, C.c_int32, _d, C.c_int32, C.c_int32]),
     "nebem_fastvol_eval": (C.c_int, [_vp, _d, C.c_int64, _d, _d]),
     "nebem_fastvol_eval_device": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp]),
+    "nebem_weighting_fields": (C.c_int, [_vp, _i32p, C.c_int32, C.c_int32, _d, C.POINTER(nebem_solve_info)]),
+    "nebem_weighting_fastvol_build": (C.c_int, [_vp, _i32p, C.c_int32, _d, C.c_int32, _d, C.c_int32, _d, C.c_int32,
+                                                C.c_int32, C.POINTER(_vp), C.POINTER(nebem_solve_info)]),
+    "nebem_fvmap_eval": (C.c_int, [_vp, _d, C.c_int64, _d, _d]),
+    "nebem_fvmap_eval_device": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp]),
+    "nebem_fvmap_destroy": (C.c_int, [_vp]),
     "nebem_image_table": (C.c_int, [_vp, _d, _i64p]),
     "nebem_pair_tiers": (C.c_int, [_vp, _d, C.c_int64, C.POINTER(C.c_uint8)]),
     "nebem_element_influence": (C.c_int, [_vp, _vp, C.c_int64, _d, C.c_int64, _d, _d]),
@@ -375,6 +381,61 @@ def nebem_fastvol_eval(ctx, pts):
 def nebem_fastvol_eval_device(ctx, d_pts: int, n: int, d_phi: int | None, d_E: int | None,
                               stream: int | None = None):
     _check(load().nebem_fastvol_eval_device(ctx, d_pts, n, d_phi, d_E, stream), "nebem_fastvol_eval_device")
+
+
+def nebem_weighting_fields(ctx, readout, precision: int, n: int, allow_not_converged=False):
+    """Weighting-field densities of the readout conductors: (sigma[n, k] with column j for
+    readout[j], info, status)."""
+    r = np.ascontiguousarray(readout, dtype=np.int32)
+    k = r.shape[0]
+    out = np.empty((k, n))  # row j of this C-ordered array is column j of the n x k result
+    info = nebem_solve_info()
+    rc = load().nebem_weighting_fields(ctx, r.ctypes.data_as(_i32p), k, precision, _dp(out), C.byref(info))
+    if not (allow_not_converged and rc == NEBEM_NOT_CONVERGED):
+        _check(rc, "nebem_weighting_fields")
+    return np.ascontiguousarray(out.T), info, rc
+
+
+class FvMap:
+    """One weighting-field FastVolume map (owns its nebem_fvmap handle)."""
+
+    def __init__(self, h):
+        self.h = h
+
+    def eval(self, pts):
+        p = _f64(pts, (-1, 3))
+        n = p.shape[0]
+        phi = np.empty(n)
+        E = np.empty((n, 3))
+        _check(load().nebem_fvmap_eval(self.h, _dp(p), n, _dp(phi), _dp(E)), "nebem_fvmap_eval")
+        return phi, E
+
+    def eval_device(self, d_pts: int, n: int, d_phi: int | None, d_E: int | None, stream: int | None = None):
+        _check(load().nebem_fvmap_eval_device(self.h, d_pts, n, d_phi, d_E, stream), "nebem_fvmap_eval_device")
+
+    def close(self):
+        if self.h is not None:
+            load().nebem_fvmap_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def nebem_weighting_fastvol_build(ctx, readout, x_nodes, y_nodes, z_nodes, precision: int):
+    """One FastVolume map per readout conductor: (list of FvMap, info)."""
+    r = np.ascontiguousarray(readout, dtype=np.int32)
+    k = r.shape[0]
+    ax, ay, az = _f64(x_nodes), _f64(y_nodes), _f64(z_nodes)
+    hs = (_vp * k)()
+    info = nebem_solve_info()
+    _check(load().nebem_weighting_fastvol_build(ctx, r.ctypes.data_as(_i32p), k, _dp(ax), ax.shape[0], _dp(ay),
+                                                ay.shape[0], _dp(az), az.shape[0], precision, hs, C.byref(info)),
+           "nebem_weighting_fastvol_build")
+    return [FvMap(hs[j]) for j in range(k)], info
 
 
 def nebem_image_table(ctx):
