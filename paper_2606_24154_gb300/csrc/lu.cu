@@ -449,20 +449,99 @@ __global__ void __launch_bounds__(kCoopThreads, 1)
 }
 
 // Apply the row swaps of panel rows [k0, k1) to columns outside the panel.
+// The row swaps of panel rows [k0, k1) (LAPACK order: row r with piv[r]) composed into one
+// permutation of the rows they touch (at most 2 (k1 - k0)): after it, row dst[i] holds what
+// row src[i] held before; *cnt = number of moved rows.  One warp: the touched rows are the
+// panel rows (slot r - k0) and the distinct pivot rows below the panel (found by a
+// warp-wide search of the list so far).  A pivot outside [r, n) is a row no panel wrote (its
+// panel gave up a bounded wait) and is skipped, as in the swaps themselves.
+constexpr int kSwapMax = 128;
+
+__global__ void __launch_bounds__(32) k_swap_perm(const int32_t* __restrict__ piv, int64_t n, int64_t k0, int64_t k1,
+                                                  int32_t* __restrict__ perm) {
+    __shared__ int64_t row_of[kSwapMax];  // slot -> row
+    __shared__ int32_t content[kSwapMax]; // slot -> slot whose original row is there now
+    __shared__ int32_t pv[kSwapMax / 2];  // the panel's pivots
+    __shared__ int n_slots;
+    const int lane = threadIdx.x;
+    const int w = (int)(k1 - k0);
+    for (int q = lane; q < w; q += 32) pv[q] = piv[k0 + q];
+    for (int s = lane; s < kSwapMax; s += 32) {
+        row_of[s] = s < w ? k0 + s : -1;
+        content[s] = s;
+    }
+    if (lane == 0) n_slots = w;
+    __syncwarp();
+    for (int64_t r = k0; r < k1; ++r) {
+        const int64_t p = pv[r - k0];
+        if (!(p != r && p > r && p < n)) continue;
+        int sp;
+        if (p < k1) {
+            sp = (int)(p - k0);
+        } else {
+            const int ns = n_slots;
+            int found = -1;
+            for (int base = w; base < ns && found < 0; base += 32) {
+                const int s = base + lane;
+                const unsigned hit = __ballot_sync(0xffffffffu, s < ns && row_of[s] == p);
+                if (hit) found = base + __ffs(hit) - 1;
+            }
+            if (found < 0) {
+                found = ns;
+                if (lane == 0) {
+                    row_of[ns] = p;
+                    n_slots = ns + 1;
+                }
+            }
+            sp = found;
+        }
+        __syncwarp();
+        if (lane == 0) {
+            const int sr = (int)(r - k0);
+            const int t = content[sr];
+            content[sr] = content[sp];
+            content[sp] = t;
+        }
+        __syncwarp();
+    }
+    // moved rows: (dst, src) pairs after the count
+    if (lane == 0) {
+        int c = 0;
+        for (int s = 0; s < n_slots; ++s)
+            if (content[s] != s) {
+                perm[1 + 2 * c] = (int32_t)row_of[s];
+                perm[2 + 2 * c] = (int32_t)row_of[content[s]];
+                ++c;
+            }
+        perm[0] = c;
+    }
+}
+
+// The composed swaps applied to every column outside the panel: each thread loads all the
+// moved values of its column (independent loads, staged in shared memory), then stores
+// them; the result equals the swaps applied one after the other.
+constexpr int kSwapThreads = 64;
+
 template <typename T>
-__global__ void k_laswp(T* __restrict__ A, int64_t n, int64_t k0, int64_t k1, const int32_t* __restrict__ piv) {
+__global__ void __launch_bounds__(kSwapThreads) k_laswp(T* __restrict__ A, int64_t n, int64_t k0, int64_t k1,
+                                                        const int32_t* __restrict__ perm) {
+    extern __shared__ __align__(16) unsigned char swap_sm[];
+    T* vals = reinterpret_cast<T*>(swap_sm);  // [kSwapMax][kSwapThreads]
+    const int cnt = perm[0];
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= n || (c >= k0 && c < k1)) return;
-    for (int64_t r = k0; r < k1; ++r) {
-        const int64_t p = piv[r];
-        // a partial pivot lies in [r, n); anything else is a row no panel wrote (its panel
-        // gave up a bounded wait), and is skipped rather than used as an index
-        if (p != r && p > r && p < n) {
-            const T a = A[r + c * n];
-            A[r + c * n] = A[p + c * n];
-            A[p + c * n] = a;
-        }
+    T* col = A + c * n;
+    // loads in batches of 16 held in registers, so that they are in flight together
+    for (int i0 = 0; i0 < cnt; i0 += 16) {
+        T v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (i0 + q < cnt) v[q] = col[perm[2 + 2 * (i0 + q)]];
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (i0 + q < cnt) vals[(i0 + q) * kSwapThreads + threadIdx.x] = v[q];
     }
+    for (int i = 0; i < cnt; ++i) col[perm[1 + 2 * i]] = vals[i * kSwapThreads + threadIdx.x];
 }
 
 // Inverse of the unit-lower nb x nb diagonal block at (k0, k0) into W (nb x nb, ld nb):
@@ -498,6 +577,80 @@ __global__ void __launch_bounds__(256) k_trtri_unit_lower(const T* __restrict__ 
 
 // C = alpha * A * B + beta * C; column-major, M x N x K; 64 x 64 tiles, 256 threads, 4x4
 // register tile per thread.
+// U12 of a block row: X = L^-1 A[K0 : K0 + 64 nbk, c0 : c1] for the unit-lower L of nbk
+// diagonal 64-blocks at (K0, K0), by block forward substitution
+//   X_i = Linv_i (A_i - sum_{j < i} L_ij X_j),
+// with Linv_i (nbk blocks of 64 x 64, ld 64) from k_trtri_unit_lower and L_ij read from A.
+// One CTA per kTrsmCols columns holds its tile of the block row in shared memory (all nbk
+// blocks), staging one 64 x 64 block of L (or Linv) at a time; thread t owns row t % 64 and
+// columns 8 (t / 64) .. + 7 of the current 64-row block.  Dynamic shared memory:
+// trsm_block_smem<T>(nbk).
+constexpr int kTrsmCols = 32;
+
+template <typename T>
+__host__ __device__ constexpr size_t trsm_block_smem(int nbk) {
+    return sizeof(T) * ((size_t)64 * nbk * (kTrsmCols + 1) + (size_t)64 * 65);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_trsm_block(T* __restrict__ A, int64_t n, int64_t K0, int nbk,
+                                                    const T* __restrict__ Linv, int64_t c0, int64_t c1) {
+    extern __shared__ __align__(16) unsigned char trsm_blk_sm[];
+    T(*X)[kTrsmCols + 1] = reinterpret_cast<T(*)[kTrsmCols + 1]>(trsm_blk_sm);
+    T(*L)[65] = reinterpret_cast<T(*)[65]>(trsm_blk_sm + sizeof(T) * 64 * nbk * (kTrsmCols + 1));
+    const int64_t cb = c0 + (int64_t)blockIdx.x * kTrsmCols;
+    const int wc = (int)min((int64_t)kTrsmCols, c1 - cb);
+    const int rows = 64 * nbk;
+    const int r = threadIdx.x % 64, g = threadIdx.x / 64;
+    for (int idx = threadIdx.x; idx < rows * kTrsmCols; idx += 256) {
+        const int rr = idx % rows, cc = idx / rows;
+        X[rr][cc] = cc < wc ? A[(K0 + rr) + (cb + cc) * n] : (T)0;
+    }
+    T acc[8];
+    for (int i = 0; i < nbk; ++i) {
+        // X_i -= L_ij X_j, j < i
+        for (int j = 0; j < i; ++j) {
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < 64 * 64; idx += 256) {
+                const int rr = idx % 64, q = idx / 64;
+                L[rr][q] = A[(K0 + 64 * i + rr) + (K0 + 64 * j + q) * n];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] = (T)0;
+            for (int q = 0; q < 64; ++q) {
+                const T l = L[r][q];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[c] = fma(l, X[64 * j + q][8 * g + c], acc[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) X[64 * i + r][8 * g + c] -= acc[c];
+        }
+        // X_i = Linv_i X_i
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < 64 * 64; idx += 256) {
+            const int rr = idx % 64, q = idx / 64;
+            L[rr][q] = Linv[(size_t)i * 64 * 64 + rr + q * 64];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = (T)0;
+        for (int q = 0; q < 64; ++q) {
+            const T l = L[r][q];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] = fma(l, X[64 * i + q][8 * g + c], acc[c]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < 8; ++c) X[64 * i + r][8 * g + c] = acc[c];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < rows * kTrsmCols; idx += 256) {
+        const int rr = idx % rows, cc = idx / rows;
+        if (cc < wc) A[(K0 + rr) + (cb + cc) * n] = X[rr][cc];
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemm(int64_t M, int64_t N, int64_t K, T alpha, const T* __restrict__ A,
                                               int64_t lda, const T* __restrict__ B, int64_t ldb, T beta,
@@ -575,7 +728,9 @@ cudaError_t gemm(int64_t M, int64_t N, int64_t K, T alpha, const T* A, int64_t l
         if (e_ != cudaSuccess) return e_;      \
     } while (0)
 
-// work layout: [0, nb*nb) L11 inverse; [nb*nb, nb*nb + nb*n) U12 staging;
+constexpr int kSuperPanels = 4;  // panels per super-panel of the two-level FP32 factorisation
+
+// work layout: [0, 4 nb*nb) unit-lower inverses; then nb*n U12 staging;
 // then kPivBlocks doubles + kPivBlocks int64 for the pivot search and one int ticket.
 template <typename T>
 cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_info, void* split, void* coop,
@@ -584,14 +739,17 @@ cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_inf
     // tensor-core update or the cooperative panel's barrier); polls > 0: the barrier's
     // poll limit (default kCoopSpinLimit)
     NB_TRY(cudaMemsetAsync(d_info, 0, 2 * sizeof(int), s));
-    T* Linv = work;
-    T* W = work + (size_t)nb * nb;
+    T* Linv = work;                                         // kSuperPanels unit-lower inverses
+    T* W = work + (size_t)kSuperPanels * nb * nb;
     char* tail = reinterpret_cast<char*>(W + (size_t)nb * n);
     size_t off = ((uintptr_t)tail + 15) & ~(uintptr_t)15;
     double* pval = reinterpret_cast<double*>(off);
     int64_t* pidx = reinterpret_cast<int64_t*>(pval + kPivBlocks);
     int* ticket = reinterpret_cast<int*>(pidx + kPivBlocks);
+    int32_t* swap_perm = reinterpret_cast<int32_t*>(ticket + 4);  // 1 + 2 kSwapMax ints
     NB_TRY(cudaMemsetAsync(ticket, 0, sizeof(int), s));
+    const int swap_smem = (int)(sizeof(T) * kSwapMax * kSwapThreads);
+    NB_TRY(cudaFuncSetAttribute(k_laswp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, swap_smem));
     if (nb > 64) return cudaErrorInvalidValue;  // k_panel_col stages at most 64 row values
     // FP32: the whole panel in one cooperative launch when every CTA's rows fit in shared
     // memory (R rows x 64 columns, R = max(64, rows / SMs)) and all CTAs can be resident
@@ -619,57 +777,104 @@ cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_inf
         cudaGetLastError();  // a refused attribute or query leaves the per-column path
     }
     unsigned int arrivals = 0;  // grid-barrier arrivals of the cooperative panels so far
-    for (int64_t k0 = 0; k0 < n; k0 += nb) {
-        const int64_t k1 = std::min<int64_t>(n, k0 + nb);
-        const int w = (int)(k1 - k0);
-        if (gmax > 0) {
-            const int64_t rows = n - k0;
-            const int R = (int)std::max<int64_t>(64, (rows + gmax - 1) / gmax);
-            const int G = (int)((rows + R - 1) / R);
-            float* Af = reinterpret_cast<float*>(A);
-            int64_t nn = n, kk0 = k0, kk1 = k1;
-            int RR = R;
-            int* tmo = d_info + 1;
-            unsigned int base = arrivals;
-            long long lim = polls > 0 ? polls : kCoopSpinLimit;
-            void* args[] = {&Af, &nn, &kk0, &kk1, &RR, &piv, &d_info, &tmo, &cs, &base, &lim};
-            NB_TRY(cudaLaunchCooperativeKernel((const void*)k_panel_coop, dim3((unsigned)G), dim3(kCoopThreads), args,
-                                               (size_t)R * w * sizeof(float), s));
-            arrivals += (unsigned int)G * (unsigned int)w;
-        } else {
-            // columns k0..k1-1: update by the previous column + pivot of this one; then the
-            // last column's scaling of the rows below the panel
-            for (int64_t j = k0; j <= k1; ++j) {
-                if (j == n) break;
-                const int64_t rows = n - j;
-                const int pb = (int)std::min<int64_t>(kPivBlocks, (rows + kPivThreads - 1) / kPivThreads);
-                k_panel_col<T><<<pb, kPivThreads, 0, s>>>(A, n, j, k0, k1, j < k1 ? 1 : 0, pval, pidx, ticket, piv,
-                                                          d_info);
-            }
-        }
-        NB_TRY(cudaGetLastError());
-        k_laswp<T><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(A, n, k0, k1, piv);
-        if (k1 < n) {
-            const int64_t m = n - k1;
-            const int tri_smem = (int)(2 * sizeof(T) * w * (w + 1));
-            NB_TRY(cudaFuncSetAttribute(k_trtri_unit_lower<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, tri_smem));
-            k_trtri_unit_lower<T><<<1, 256, tri_smem, s>>>(A, n, k0, w, Linv);
-            // W = Linv * A12  (w x m), then A12 = W
-            NB_TRY(gemm<T>(w, m, w, (T)1, Linv, w, A + k0 + k1 * n, n, (T)0, W, w, s));
-            k_copy_block<T><<<(unsigned)((w * m + 255) / 256), 256, 0, s>>>(W, w, A + k0 + k1 * n, n, w, m);
-            // A22 -= L21 * U12: tensor cores (TF32 x3) for the FP32 factorisation's 64-wide
-            // panels, FP64 FMA for the FP64 factorisation
-            if constexpr (sizeof(T) == 4) {
-                if (w == 64) {
-                    NB_TRY(tc_update_f32(m, m, reinterpret_cast<const float*>(A + k1 + k0 * n), n,
-                                         reinterpret_cast<const float*>(A + k0 + k1 * n), n,
-                                         reinterpret_cast<float*>(A + k1 + k1 * n), n, split, d_info + 1, s));
-                    continue;
+    // FP32 with the bulk tensor-core path: two-level blocking.  Super-panels of kSuperPanels
+    // panels; inside one, each panel's U12 and update stop at the super-panel's last column;
+    // after it, the block row's U12 by block forward substitution and one trailing update of
+    // depth kSuperPanels * nb, so C is read and written once per super-panel.
+    bool super = false;
+    if constexpr (sizeof(T) == 4) super = split && nb == 64 && (n % 4) == 0 && n > (int64_t)kSuperPanels * nb;
+    const int64_t sp = super ? (int64_t)kSuperPanels * nb : (int64_t)nb;
+    auto trsm_rows = [&](int64_t r0, int wr, int64_t c0, int64_t c1) -> cudaError_t {
+        // A[r0 : r0 + wr, c0 : c1] = L(r0 block)^-1 A[r0 : r0 + wr, c0 : c1] (unit lower wr x wr)
+        const int64_t m = c1 - c0;
+        const int tri_smem = (int)(2 * sizeof(T) * wr * (wr + 1));
+        NB_TRY(cudaFuncSetAttribute(k_trtri_unit_lower<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, tri_smem));
+        k_trtri_unit_lower<T><<<1, 256, tri_smem, s>>>(A, n, r0, wr, Linv);
+        NB_TRY(gemm<T>(wr, m, wr, (T)1, Linv, wr, A + r0 + c0 * n, n, (T)0, W, wr, s));
+        k_copy_block<T><<<(unsigned)((wr * m + 255) / 256), 256, 0, s>>>(W, wr, A + r0 + c0 * n, n, wr, m);
+        return cudaGetLastError();
+    };
+    auto trsm_block = [&](int64_t r0, int nbk, const T* inv, int64_t c0, int64_t c1) -> cudaError_t {
+        const int smem = (int)trsm_block_smem<T>(nbk);
+        NB_TRY(cudaFuncSetAttribute(k_trsm_block<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        k_trsm_block<T><<<(unsigned)((c1 - c0 + kTrsmCols - 1) / kTrsmCols), 256, smem, s>>>(A, n, r0, nbk, inv, c0,
+                                                                                            c1);
+        return cudaGetLastError();
+    };
+    for (int64_t K0 = 0; K0 < n; K0 += sp) {
+        const int64_t K1 = std::min<int64_t>(n, K0 + sp);
+        const int64_t e1 = super ? K1 : n;  // last column (exclusive) the panels' updates reach
+        for (int64_t k0 = K0; k0 < K1; k0 += nb) {
+            const int64_t k1 = std::min<int64_t>(n, k0 + nb);
+            const int w = (int)(k1 - k0);
+            if (gmax > 0) {
+                const int64_t rows = n - k0;
+                const int R = (int)std::max<int64_t>(64, (rows + gmax - 1) / gmax);
+                const int G = (int)((rows + R - 1) / R);
+                float* Af = reinterpret_cast<float*>(A);
+                int64_t nn = n, kk0 = k0, kk1 = k1;
+                int RR = R;
+                int* tmo = d_info + 1;
+                unsigned int base = arrivals;
+                long long lim = polls > 0 ? polls : kCoopSpinLimit;
+                void* args[] = {&Af, &nn, &kk0, &kk1, &RR, &piv, &d_info, &tmo, &cs, &base, &lim};
+                NB_TRY(cudaLaunchCooperativeKernel((const void*)k_panel_coop, dim3((unsigned)G), dim3(kCoopThreads),
+                                                   args, (size_t)R * w * sizeof(float), s));
+                arrivals += (unsigned int)G * (unsigned int)w;
+            } else {
+                // columns k0..k1-1: update by the previous column + pivot of this one; then the
+                // last column's scaling of the rows below the panel
+                for (int64_t j = k0; j <= k1; ++j) {
+                    if (j == n) break;
+                    const int64_t rows = n - j;
+                    const int pb = (int)std::min<int64_t>(kPivBlocks, (rows + kPivThreads - 1) / kPivThreads);
+                    k_panel_col<T><<<pb, kPivThreads, 0, s>>>(A, n, j, k0, k1, j < k1 ? 1 : 0, pval, pidx, ticket,
+                                                              piv, d_info);
                 }
             }
-            NB_TRY(gemm<T>(m, m, w, (T)-1, A + k1 + k0 * n, n, A + k0 + k1 * n, n, (T)1, A + k1 + k1 * n, n, s));
+            NB_TRY(cudaGetLastError());
+            k_swap_perm<<<1, 32, 0, s>>>(piv, n, k0, k1, swap_perm);
+            k_laswp<T><<<(unsigned)((n + kSwapThreads - 1) / kSwapThreads), kSwapThreads, swap_smem, s>>>(A, n, k0,
+                                                                                                    k1, swap_perm);
+            if (super && (k1 < K1 || K1 < n)) {
+                // the panel's unit-lower inverse, kept in its slot for the block row's U12
+                T* slot = Linv + (size_t)((k0 - K0) / nb) * nb * nb;
+                const int tri_smem = (int)(2 * sizeof(T) * w * (w + 1));
+                NB_TRY(cudaFuncSetAttribute(k_trtri_unit_lower<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            tri_smem));
+                k_trtri_unit_lower<T><<<1, 256, tri_smem, s>>>(A, n, k0, w, slot);
+            }
+            if (k1 < e1) {
+                const int64_t m = n - k1, mc = e1 - k1;
+                if (super)
+                    NB_TRY(trsm_block(k0, 1, Linv + (size_t)((k0 - K0) / nb) * nb * nb, k1, e1));
+                else
+                    NB_TRY(trsm_rows(k0, w, k1, e1));
+                // A22 -= L21 * U12 over the columns up to e1: tensor cores (TF32 x3) for the
+                // FP32 factorisation's 64-wide panels, FP64 FMA for the FP64 factorisation
+                if constexpr (sizeof(T) == 4) {
+                    if (w == 64) {
+                        NB_TRY(tc_update_f32(m, mc, reinterpret_cast<const float*>(A + k1 + k0 * n), n,
+                                             reinterpret_cast<const float*>(A + k0 + k1 * n), n,
+                                             reinterpret_cast<float*>(A + k1 + k1 * n), n, split, d_info + 1, s));
+                        continue;
+                    }
+                }
+                NB_TRY(gemm<T>(m, mc, w, (T)-1, A + k1 + k0 * n, n, A + k0 + k1 * n, n, (T)1, A + k1 + k1 * n, n, s));
+            }
+            NB_TRY(cudaGetLastError());
         }
-        NB_TRY(cudaGetLastError());
+        if constexpr (sizeof(T) == 4) {
+            if (super && K1 < n) {
+                const int64_t m = n - K1;
+                // U12 of the block row [K0, K1) over the trailing columns: block forward
+                // substitution with the super-panel's unit-lower blocks and their inverses
+                NB_TRY(trsm_block(K0, kSuperPanels, Linv, K1, n));
+                NB_TRY(tc_update_f32_k(m, m, K1 - K0, reinterpret_cast<const float*>(A + K1 + K0 * n), n,
+                                       reinterpret_cast<const float*>(A + K0 + K1 * n), n,
+                                       reinterpret_cast<float*>(A + K1 + K1 * n), n, split, d_info + 1, s));
+            }
+        }
     }
     return cudaSuccess;
 }
@@ -677,7 +882,7 @@ cudaError_t lu_factor(T* A, int64_t n, int32_t* piv, int nb, T* work, int* d_inf
 // ---------------------------------------------------------------- triangular solves
 constexpr int kTB = 64;          // solve block
 constexpr int kResRows = 256;    // residual: rows per CTA
-constexpr int kResChunk = 2048;  // residual: columns per partial sum
+constexpr int kResChunk = 512;   // residual: columns per partial sum (enough (row, chunk) threads to keep HBM busy)
 
 // Row permutation of the pivots: applying the swaps (k, piv[k]), k = 0..n-1, to b gives
 // b'[i] = b[perm[i]].  The swaps are sequential; they run on an index array in shared
@@ -924,23 +1129,35 @@ __global__ void __launch_bounds__(kSvThreads) k_trsv(const T* __restrict__ LU, i
 
 // The same sweep for nr <= kMR right-hand sides at once (columns of rhs and x, leading
 // dimension n; used for the weighting fields of several readouts, Sec. 2.1).  Each factor
-// block is read once for all columns; per column the arithmetic is k_trsv's, in its order
-// (the fma chain over blocks and columns, the four group sums, the diagonal block: FP64
-// substitution, one warp per column; FP32 explicit inverse), so column j equals k_trsv on
-// that column bit for bit.  Waits, give-up and publication as in k_trsv.
+// block is read once for all columns, and the columns share every block barrier.  Per
+// column the arithmetic is k_trsv's, in its order (the fma chain over blocks and columns,
+// the four group sums in order, the diagonal block: FP64 substitution, one warp per column;
+// FP32 explicit inverse), so column j equals k_trsv on that column bit for bit.  Waits,
+// give-up and publication as in k_trsv.  Dynamic shared memory, trsm_smem_bytes<T>():
+//   D[kTB][kTB+1], Xi[kTB][kTB+1] (FP32 only), part[groups][kMR][kTB] (FP64: shared with
+//   the substitution's xo[kMR][kTB]), xs[kMR][kTB] (the block's right-hand sides, then its
+//   solution), dinv[kTB].
 constexpr int kMR = 8;
+
+template <typename T>
+__host__ __device__ constexpr size_t trsm_smem_bytes() {
+    return sizeof(T) * ((size_t)kTB * (kTB + 1) * (sizeof(T) == 4 ? 2 : 1) + (size_t)(kSvThreads / kTB) * kMR * kTB +
+                        (size_t)kMR * kTB + kTB);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kSvThreads) k_trsm(const T* __restrict__ LU, int64_t n, int64_t nblk, int lower,
                                                      const T* __restrict__ rhs, T* x, int nr, int* flags,
                                                      int* ticket, int* err, long long limit) {
     constexpr bool kInv = sizeof(T) == 4;
-    __shared__ T D[kTB][kTB + 1];
-    __shared__ T Xi[kInv ? kTB : 1][kTB + 1];
-    __shared__ T part[kSvThreads / kTB][kTB];
-    __shared__ T xs[kMR][kTB];
-    __shared__ T xo[kInv ? 1 : kMR][kTB];
-    __shared__ T dinv[kTB];
+    constexpr int kGroups = kSvThreads / kTB, kCols = kTB / kGroups;
+    extern __shared__ __align__(16) unsigned char trsm_sm[];
+    T(*D)[kTB + 1] = reinterpret_cast<T(*)[kTB + 1]>(trsm_sm);
+    T(*Xi)[kTB + 1] = D + kTB;  // FP32 only
+    T(*part)[kMR][kTB] = reinterpret_cast<T(*)[kMR][kTB]>(reinterpret_cast<T*>(D + (kInv ? 2 : 1) * kTB));
+    T(*xo)[kTB] = part[0];  // FP64 substitution, after the group sums
+    T(*xs)[kTB] = reinterpret_cast<T(*)[kTB]>(reinterpret_cast<T*>(part + kGroups));
+    T* dinv = reinterpret_cast<T*>(xs + kMR);
     __shared__ int s_t, s_ready, s_ok;
     if (threadIdx.x == 0) s_t = atomicAdd(ticket, 1);
     __syncthreads();
@@ -948,15 +1165,15 @@ __global__ void __launch_bounds__(kSvThreads) k_trsm(const T* __restrict__ LU, i
     const int64_t k = lower ? t : nblk - 1 - t;
     const int64_t r0 = k * kTB, r1 = min(n, r0 + (int64_t)kTB);
     const int w = (int)(r1 - r0);
-    constexpr int kGroups = kSvThreads / kTB, kCols = kTB / kGroups;
     const int row = threadIdx.x % kTB, grp = threadIdx.x / kTB;
     for (int idx = threadIdx.x; idx < w * w; idx += kSvThreads) {
         const int r = idx % w, c = idx / w;
         D[r][c] = LU[(r0 + r) + (r0 + c) * n];
     }
-    T rhs_own[kMR];
-#pragma unroll
-    for (int j = 0; j < kMR; ++j) rhs_own[j] = (threadIdx.x < w && j < nr) ? rhs[r0 + threadIdx.x + j * n] : (T)0;
+    for (int idx = threadIdx.x; idx < w * nr; idx += kSvThreads) {
+        const int j = idx / w, r = idx - j * w;
+        xs[j][r] = rhs[r0 + r + (int64_t)j * n];
+    }
     if (!lower && threadIdx.x < w) dinv[threadIdx.x] = (T)1 / LU[(r0 + threadIdx.x) + (r0 + threadIdx.x) * n];
     if constexpr (kInv) {
         __syncthreads();
@@ -1048,43 +1265,43 @@ __global__ void __launch_bounds__(kSvThreads) k_trsm(const T* __restrict__ LU, i
         if (done < total) load_block(done);
     }
     if (!ok) atomicExch(err, 1);
-    // per column: the four group sums in order, subtracted from the block's right-hand side
-    for (int j = 0; j < nr; ++j) {
-        part[grp][row] = acc[0];
-        __syncthreads();
-        if (threadIdx.x < w) {
-            T sum = part[0][threadIdx.x];
+    // every column's four group sums, in order, subtracted from its right-hand side
 #pragma unroll
-            for (int g = 1; g < kGroups; ++g) sum += part[g][threadIdx.x];
-            xs[j][threadIdx.x] = rhs_own[0] - sum;
-        }
-        __syncthreads();
-        // next column into slot 0 (registers are not indexed by a runtime j)
+    for (int j = 0; j < kMR; ++j)
+        if (j < nr) part[grp][j][row] = acc[j];
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < w * nr; idx += kSvThreads) {
+        const int j = idx / w, r = idx - j * w;
+        T sum = part[0][j][r];
 #pragma unroll
-        for (int q = 0; q + 1 < kMR; ++q) {
-            acc[q] = acc[q + 1];
-            rhs_own[q] = rhs_own[q + 1];
-        }
+        for (int g = 1; g < kGroups; ++g) sum += part[g][j][r];
+        xs[j][r] = xs[j][r] - sum;
     }
+    __syncthreads();
     if constexpr (kInv) {
-        for (int j = 0; j < nr; ++j) {
-            T v = (T)0;
-            if (row < w) {
+        // x_j = X (rhs_j - sum_j): row `row`, columns of group grp, then the groups in order
+        T v[kMR];
+#pragma unroll
+        for (int j = 0; j < kMR; ++j) {
+            v[j] = (T)0;
+            if (j < nr && row < w) {
 #pragma unroll
                 for (int q = 0; q < kCols; ++q) {
                     const int c = grp * kCols + q;
-                    if (c < w) v = fma(Xi[row][c], xs[j][c], v);
+                    if (c < w) v[j] = fma(Xi[row][c], xs[j][c], v[j]);
                 }
             }
-            part[grp][row] = v;
-            __syncthreads();
-            if (threadIdx.x < w) {
-                T sum = part[0][threadIdx.x];
+        }
 #pragma unroll
-                for (int g = 1; g < kGroups; ++g) sum += part[g][threadIdx.x];
-                xs[j][threadIdx.x] = sum;
-            }
-            __syncthreads();
+        for (int j = 0; j < kMR; ++j)
+            if (j < nr) part[grp][j][row] = v[j];
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < w * nr; idx += kSvThreads) {
+            const int j = idx / w, r = idx - j * w;
+            T sum = part[0][j][r];
+#pragma unroll
+            for (int g = 1; g < kGroups; ++g) sum += part[g][j][r];
+            xs[j][r] = sum;
         }
     } else {
         const int j = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -1157,6 +1374,7 @@ __global__ void __launch_bounds__(kResRows) k_residual_partial(const double* __r
     __syncthreads();
     if (i >= n) return;
     double s = 0.0;
+#pragma unroll 8
     for (int64_t j = j0; j < j1; ++j) s = fma(K[i + j * n], xs[j - j0], s);
     part[(int64_t)blockIdx.y * n + i] = s;
 }
@@ -1176,35 +1394,42 @@ __global__ void k_residual_final(const double* __restrict__ part, int64_t nchunk
 // single-column residual bit for bit.  x is staged in shared memory kResTile columns at a time.
 constexpr int kResTile = 512;
 
+template <int NR>
 __global__ void __launch_bounds__(kResRows) k_residual_partial_m(const double* __restrict__ K, int64_t n,
-                                                                 const double* __restrict__ x, int nr,
+                                                                 const double* __restrict__ x,
                                                                  double* __restrict__ part) {
     const int64_t i = (int64_t)blockIdx.x * kResRows + threadIdx.x;
     const int64_t j0 = (int64_t)blockIdx.y * kResChunk, j1 = min(n, j0 + (int64_t)kResChunk);
-    __shared__ double xs[kResTile][kMR];
-    double s[kMR];
+    constexpr int kUnroll = NR > 4 ? 4 : 8;  // loads in flight, within the register budget
+    __shared__ double xs[kResTile][NR];
+    double s[NR];
 #pragma unroll
-    for (int c = 0; c < kMR; ++c) s[c] = 0.0;
+    for (int c = 0; c < NR; ++c) s[c] = 0.0;
     for (int64_t t0 = j0; t0 < j1; t0 += kResTile) {
         const int64_t t1 = min(j1, t0 + (int64_t)kResTile);
         __syncthreads();
-        for (int64_t idx = threadIdx.x; idx < (t1 - t0) * nr; idx += kResRows) {
+        for (int64_t idx = threadIdx.x; idx < (t1 - t0) * NR; idx += kResRows) {
             const int64_t c = idx / (t1 - t0), j = idx - c * (t1 - t0);
             xs[j][c] = x[t0 + j + c * n];
         }
         __syncthreads();
         if (i < n)
+#pragma unroll kUnroll
             for (int64_t j = t0; j < t1; ++j) {
                 const double kv = K[i + j * n];
 #pragma unroll
-                for (int c = 0; c < kMR; ++c)
-                    if (c < nr) s[c] = fma(kv, xs[j - t0][c], s[c]);
+                for (int c = 0; c < NR; ++c) s[c] = fma(kv, xs[j - t0][c], s[c]);
             }
     }
     if (i < n)
 #pragma unroll
-        for (int c = 0; c < kMR; ++c)
-            if (c < nr) part[((int64_t)blockIdx.y * kMR + c) * n + i] = s[c];
+        for (int c = 0; c < NR; ++c) part[((int64_t)blockIdx.y * kMR + c) * n + i] = s[c];
+}
+
+template <int NR>
+static void launch_residual_partial_m(dim3 grid, cudaStream_t s, const double* K, int64_t n, const double* x,
+                                      double* part) {
+    k_residual_partial_m<NR><<<grid, kResRows, 0, s>>>(K, n, x, part);
 }
 
 __global__ void k_residual_final_m(const double* __restrict__ part, int64_t nchunk, int64_t n, int nr,
@@ -1290,8 +1515,10 @@ cudaError_t launch_gather(const double* a, const int64_t* idx, int64_t n, double
 }
 
 size_t lu_work_elems(int64_t n, int nb) {
-    // L11^-1 + U12 staging + pivot partials and the ticket (in bytes / 4 rounded up, covers both types)
-    return (size_t)nb * nb + (size_t)nb * (size_t)n + 16 + (size_t)kPivBlocks * 4 + 16;
+    // L11^-1 + U12 staging + pivot partials, the ticket and the composed row swaps (in
+    // 4-byte units rounded up, which covers both types)
+    return (size_t)kSuperPanels * nb * nb + (size_t)nb * (size_t)n + 16 + (size_t)kPivBlocks * 4 + 16 +
+           (2 * kSwapMax + 16);
 }
 
 cudaError_t lu_factor_f64(double* A, int64_t n, int32_t* piv, int nb, double* work, int* d_info, cudaStream_t s) {
@@ -1299,7 +1526,7 @@ cudaError_t lu_factor_f64(double* A, int64_t n, int32_t* piv, int nb, double* wo
 }
 static size_t split_offset(int64_t n, int nb) { return (sizeof(float) * lu_work_elems(n, nb) + 255) & ~(size_t)255; }
 static size_t coop_offset(int64_t n, int nb) {
-    return (split_offset(n, nb) + tc_split_bytes(n, n) + 255) & ~(size_t)255;
+    return (split_offset(n, nb) + tc_split_bytes(n, n, kSuperPanels) + 255) & ~(size_t)255;
 }
 size_t lu_work_bytes_f32(int64_t n, int nb) { return coop_offset(n, nb) + sizeof(CoopScratch); }
 cudaError_t lu_factor_f32(float* A, int64_t n, int32_t* piv, int nb, float* work, int* d_info, cudaStream_t s,
@@ -1398,14 +1625,17 @@ static cudaError_t lu_solve_multi(const T* LU, int64_t n, const int32_t* perm, T
     int* err = tickets + 2;
     NB_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
     const long long limit = polls > 0 ? polls : kSvSpinLimit;
+    // set for the current device on every call (an attribute is per device)
+    const size_t smem = trsm_smem_bytes<T>();
+    NB_TRY(cudaFuncSetAttribute(k_trsm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     for (int64_t c0 = 0; c0 < nrhs; c0 += kMR) {
         const int nr = (int)std::min<int64_t>(kMR, nrhs - c0);
         T* b = B + c0 * n;
         NB_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * (2 * nblk + 2), s));
         k_permute_m<T><<<(unsigned)((n * nr + 255) / 256), 256, 0, s>>>(b, perm, n, nr, y);
-        k_trsm<T><<<(unsigned)nblk, kSvThreads, 0, s>>>(LU, n, nblk, 1, y, z, nr, flags, tickets, err, limit);
-        k_trsm<T><<<(unsigned)nblk, kSvThreads, 0, s>>>(LU, n, nblk, 0, z, b, nr, flags + nblk, tickets + 1, err,
-                                                        limit);
+        k_trsm<T><<<(unsigned)nblk, kSvThreads, smem, s>>>(LU, n, nblk, 1, y, z, nr, flags, tickets, err, limit);
+        k_trsm<T><<<(unsigned)nblk, kSvThreads, smem, s>>>(LU, n, nblk, 0, z, b, nr, flags + nblk, tickets + 1, err,
+                                                           limit);
         NB_TRY(cudaGetLastError());
     }
     return cudaSuccess;
@@ -1429,7 +1659,16 @@ cudaError_t gemv_residual_multi(const double* K, int64_t n, const double* X, int
     for (int64_t c0 = 0; c0 < nrhs; c0 += kMR) {
         const int nr = (int)std::min<int64_t>(kMR, nrhs - c0);
         dim3 grid((unsigned)((n + kResRows - 1) / kResRows), (unsigned)nchunk);
-        k_residual_partial_m<<<grid, kResRows, 0, s>>>(K, n, X + c0 * n, nr, part);
+        switch (nr) {  // the column count as a template argument: no predicated lanes
+            case 1: launch_residual_partial_m<1>(grid, s, K, n, X + c0 * n, part); break;
+            case 2: launch_residual_partial_m<2>(grid, s, K, n, X + c0 * n, part); break;
+            case 3: launch_residual_partial_m<3>(grid, s, K, n, X + c0 * n, part); break;
+            case 4: launch_residual_partial_m<4>(grid, s, K, n, X + c0 * n, part); break;
+            case 5: launch_residual_partial_m<5>(grid, s, K, n, X + c0 * n, part); break;
+            case 6: launch_residual_partial_m<6>(grid, s, K, n, X + c0 * n, part); break;
+            case 7: launch_residual_partial_m<7>(grid, s, K, n, X + c0 * n, part); break;
+            default: launch_residual_partial_m<8>(grid, s, K, n, X + c0 * n, part); break;
+        }
         k_residual_final_m<<<(unsigned)((n * nr + 255) / 256), 256, 0, s>>>(part, nchunk, n, nr, B + c0 * n,
                                                                            R + c0 * n);
         NB_TRY(cudaGetLastError());

@@ -25,8 +25,8 @@ namespace {
 constexpr int64_t kNoAllocMaxN = 4096;
 constexpr int kNoAllocBlock = 64;
 // lu_work_elems(kNoAllocMaxN, kNoAllocBlock) doubles of work space, then the flag
-constexpr size_t kWorkDoubles = (size_t)kNoAllocBlock * kNoAllocBlock + (size_t)kNoAllocBlock * kNoAllocMaxN + 16 +
-                                (size_t)256 * 4;
+constexpr size_t kWorkDoubles = (size_t)4 * kNoAllocBlock * kNoAllocBlock + (size_t)kNoAllocBlock * kNoAllocMaxN + 16 +
+                                (size_t)256 * 4 + 16 + (2 * 128 + 16);
 constexpr size_t kScratchDoubles = kWorkDoubles + 32;  // + flags (two ints)
 
 static __device__ __align__(256) double g_lu_scratch[kScratchDoubles];
@@ -50,7 +50,7 @@ extern "C" int nebem_lu_factor_device_noalloc(double* d_A, int64_t n, int32_t* d
     if (!d_A || !d_piv || n <= 0) return fail(NEBEM_INVALID_ARG, "bad argument");
     if (n > kNoAllocMaxN)
         return fail(NEBEM_TOO_LARGE, "nebem_lu_factor_device_noalloc handles n <= 4096 (static work space)");
-    static_assert(kWorkDoubles >= 64 * 64 + 64 * 4096 + 16 + 256 * 4, "work space too small");
+    static_assert(kWorkDoubles >= 4 * 64 * 64 + 64 * 4096 + 16 + 256 * 4 + 16 + 272, "work space too small");
     double* scratch = nullptr;
     const int rc = scratch_address(&scratch);
     if (rc) return rc;

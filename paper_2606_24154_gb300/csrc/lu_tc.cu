@@ -304,32 +304,33 @@ __device__ __forceinline__ void tma_reduce_add_c(const CUtensorMap* map, int x, 
     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 
-// -A (M x 64, column-major) and B (64 x N) into TF32 hi/lo operand tiles: A tile tm at
-// asplit + tm * 64 KB (hi, then lo), B tile tn at bsplit + tn * 32 KB; rows of A beyond M
-// and columns of B beyond N are zero.  The TF32 split of -x is the negated split of x.
+// -A (M x K, column-major) and B (K x N) into TF32 hi/lo operand tiles, in kc chunks of 64
+// along K (K <= 64 kc): A tile (tm, chunk c) at asplit + (tm kc + c) * 64 KB (hi, then lo),
+// B tile (tn, c) at bsplit + (tn kc + c) * 32 KB; rows of A beyond M, columns of B beyond
+// N and depths beyond K are zero.  The TF32 split of -x is the negated split of x.
 __global__ void k_split_ab(const float* __restrict__ A, int64_t lda, const float* __restrict__ B, int64_t ldb,
-                           int64_t M, int64_t N, int64_t tiles_m, int64_t tiles_n, unsigned char* __restrict__ asplit,
-                           unsigned char* __restrict__ bsplit) {
-    const int64_t na = tiles_m * (kTM * kTK), nb = tiles_n * (kTN * kTK);
+                           int64_t M, int64_t N, int64_t K, int kc, int64_t tiles_m, int64_t tiles_n,
+                           unsigned char* __restrict__ asplit, unsigned char* __restrict__ bsplit) {
+    const int64_t na = tiles_m * kc * (kTM * kTK), nb = tiles_n * kc * (kTN * kTK);
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < na + nb;
          idx += (int64_t)gridDim.x * blockDim.x) {
         if (idx < na) {
-            const int64_t tm = idx / (kTM * kTK);
-            const int e = (int)(idx - tm * (kTM * kTK));
+            const int64_t tc = idx / (kTM * kTK);  // tm * kc + c
+            const int e = (int)(idx - tc * (kTM * kTK));
             const int r = e % kTM, k = e / kTM;
-            const int64_t gm = tm * kTM + r;
-            const float x = gm < M ? -A[gm + (int64_t)k * lda] : 0.f;
-            unsigned char* t = asplit + tm * kASplit;
+            const int64_t gm = (tc / kc) * kTM + r, gk = (tc % kc) * kTK + k;
+            const float x = (gm < M && gk < K) ? -A[gm + gk * lda] : 0.f;
+            unsigned char* t = asplit + tc * kASplit;
             put_pair(t, t + kABytes, kmajor_off(r, k), x);
         } else {
             const int64_t i2 = idx - na;
-            const int64_t tn = i2 / (kTN * kTK);
-            const int e = (int)(i2 - tn * (kTN * kTK));
-            const int k = e % kTK, c = e / kTK;
-            const int64_t gn = tn * kTN + c;
-            const float x = gn < N ? B[k + gn * ldb] : 0.f;
-            unsigned char* t = bsplit + tn * kBSplit;
-            put_pair(t, t + kBBytes, kmajor_off(c, k), x);
+            const int64_t tc = i2 / (kTN * kTK);  // tn * kc + c
+            const int e = (int)(i2 - tc * (kTN * kTK));
+            const int k = e % kTK, col = e / kTK;
+            const int64_t gn = (tc / kc) * kTN + col, gk = (tc % kc) * kTK + k;
+            const float x = (gn < N && gk < K) ? B[gk + gn * ldb] : 0.f;
+            unsigned char* t = bsplit + tc * kBSplit;
+            put_pair(t, t + kBBytes, kmajor_off(col, k), x);
         }
     }
 }
@@ -482,6 +483,298 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kTN));
 }
 
+// ---- rank-K update in one pass over C (K <= 256): the trailing update of a super-panel.
+// Operands are split in chunks of 32 along K (canonical K-major layout, SBO = 1 KB):
+// A tile (tm, chunk c) 32 KB (hi 16 KB, lo 16 KB), B tile (tn, c) 16 KB (hi 8 KB, lo 8 KB).
+constexpr int kKT = 32;                                    // chunk depth
+constexpr uint32_t kSBO32 = (kKT / 4) * kCoreBytes;        // 1024 B
+constexpr uint32_t kABytes32 = kTM * kKT * 4;              // 16 KB
+constexpr uint32_t kBBytes32 = kTN * kKT * 4;              // 8 KB
+constexpr uint32_t kASplit32 = 2 * kABytes32;              // 32 KB
+constexpr uint32_t kBSplit32 = 2 * kBBytes32;              // 16 KB
+
+__device__ __forceinline__ uint32_t kmajor_off32(int r, int k) {
+    return (uint32_t)(r >> 3) * kSBO32 + (uint32_t)(k >> 2) * kLBO + (uint32_t)(r & 7) * 16u + (uint32_t)(k & 3) * 4u;
+}
+__device__ __forceinline__ uint64_t make_desc32(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(kLBO >> 4) << 16;
+    d |= (uint64_t)(kSBO32 >> 4) << 32;
+    d |= 1ull << 46;
+    return d;
+}
+
+// -A (M x K) and B (K x N) into 32-deep TF32 hi/lo tiles, kc = ceil(K / 32) chunks: A tile
+// (tm, c) at asplit + (tm kc + c) * 32 KB, B tile (tn, c) at bsplit + (tn kc + c) * 16 KB;
+// entries beyond M, N or K are zero.
+__global__ void k_split_ab32(const float* __restrict__ A, int64_t lda, const float* __restrict__ B, int64_t ldb,
+                             int64_t M, int64_t N, int64_t K, int kc, int64_t tiles_m, int64_t tiles_n,
+                             unsigned char* __restrict__ asplit, unsigned char* __restrict__ bsplit) {
+    const int64_t na = tiles_m * kc * (kTM * kKT), nb = tiles_n * kc * (kTN * kKT);
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < na + nb;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        if (idx < na) {
+            const int64_t tc = idx / (kTM * kKT);  // tm * kc + c
+            const int e = (int)(idx - tc * (kTM * kKT));
+            const int r = e % kTM, k = e / kTM;
+            const int64_t gm = (tc / kc) * kTM + r, gk = (tc % kc) * kKT + k;
+            const float x = (gm < M && gk < K) ? -A[gm + gk * lda] : 0.f;
+            unsigned char* t = asplit + tc * kASplit32;
+            put_pair(t, t + kABytes32, kmajor_off32(r, k), x);
+        } else {
+            const int64_t i2 = idx - na;
+            const int64_t tc = i2 / (kTN * kKT);  // tn * kc + c
+            const int e = (int)(i2 - tc * (kTN * kKT));
+            const int k = e % kKT, col = e / kKT;
+            const int64_t gn = (tc / kc) * kTN + col, gk = (tc % kc) * kKT + k;
+            const float x = (gn < N && gk < K) ? B[gk + gn * ldb] : 0.f;
+            unsigned char* t = bsplit + tc * kBSplit32;
+            put_pair(t, t + kBBytes32, kmajor_off32(col, k), x);
+        }
+    }
+}
+
+// One CTA per SM owns a 128-row strip of C and nt <= kAccTiles 64-column tiles, each with
+// its own accumulator (up to all 512 TMEM columns), so C is read and written once for the
+// whole depth instead of once per panel.  Work items (chunk c, tile t) run chunk-major,
+// i = c nt + t; an item is 12 MMAs (lo hi, hi lo, hi hi over 4 steps of 8) into
+// accumulator t, overwriting it at c = 0.  Warp-specialised, no block barrier in the
+// steady state:
+//   warp 4 (one lane)  producer: A chunks into a ring of kRA slots (32 KB), B items into a
+//                      ring of kRB slots (16 KB), each slot refilled once emptyA / emptyB
+//                      says the MMAs that read it are done;
+//   warp 5 (one lane)  MMA issue: waits fullB (and fullA at t = 0), issues the item,
+//                      commits to emptyB, to emptyA when it closes a chunk, and to accf[t]
+//                      when it is of the last chunk;
+//   warps 0-3          epilogue (warp w reads TMEM lanes 32w..): per tile, waits accf[t],
+//                      moves the accumulator through the product buffer (once the previous
+//                      reduce has read it; a named barrier among these four warps) into a
+//                      TMA reduce-add into C.
+// The u-th use of a ring slot completes its phase u, so every wait's parity follows from
+// the item or chunk number.  Waits are bounded: a role that gives up records *err and
+// raises the CTA's abort flag, the others stop at their next step; before the tensor
+// memory is freed, every copy and MMA that was started is waited for (bounded).
+constexpr int kAccTiles = 8;
+constexpr int kRA = 2, kRB = 8;
+constexpr int kUpdThreads = 192;
+constexpr uint32_t kKSmem = kRA * kASplit32 + kRB * kBSplit32 + kCTile + 512;
+
+__device__ __forceinline__ void named_sync_epilogue() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// barrier 1 among the 128 epilogue threads, returning the OR of v over them (the same
+// value in every one of them)
+__device__ __forceinline__ int named_sync_or_epilogue(int v) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\tbar.red.or.pred q, 1, 128, p;\n\t"
+        "selp.s32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(v)
+        : "memory");
+    return r;
+}
+// bounded wait that also gives up once the CTA's abort flag is raised
+__device__ __forceinline__ int mbar_wait_ab(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+    uint32_t done = 0;
+    for (long long it = 0; it < kSpinLimit && !done; ++it) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_u32(b)), "r"(parity)
+            : "memory");
+        if (!done && (it & 63) == 63 && *abort_flag) return 0;
+    }
+    return (int)done;
+}
+
+__global__ void __launch_bounds__(kUpdThreads, 1)
+    k_tc_update_k(const __grid_constant__ CUtensorMap cmap, int64_t M, int64_t N, int kc,
+                  const unsigned char* __restrict__ asplit, const unsigned char* __restrict__ bsplit, int tpc,
+                  int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sA0 = smem;
+    unsigned char* sB0 = smem + kRA * kASplit32;
+    float* pbuf = reinterpret_cast<float*>(smem + kRA * kASplit32 + kRB * kBSplit32);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kRA * kASplit32 + kRB * kBSplit32 + kCTile);
+    uint64_t* fullA = bar;                 // [kRA]
+    uint64_t* emptyA = bar + kRA;          // [kRA]
+    uint64_t* fullB = bar + 2 * kRA;       // [kRB]
+    uint64_t* emptyB = bar + 2 * kRA + kRB;  // [kRB]
+    uint64_t* accf = bar + 2 * kRA + 2 * kRB;  // [kAccTiles]
+    constexpr int kBars = 2 * kRA + 2 * kRB + kAccTiles;
+    int* sh = reinterpret_cast<int*>(bar + kBars);  // tmem address, abort, progress counters
+    volatile int* abort_flag = sh + 1;
+    int* prog = sh + 2;  // loadsA, loadsB, waitedA, waitedB, issued
+
+    const int64_t tiles_n = (N + kTN - 1) / kTN;
+    const int64_t t0 = (int64_t)blockIdx.y * tpc;
+    const int nt = (int)max((int64_t)0, min((int64_t)tpc, tiles_n - t0));
+    const int items = nt * kc;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = (int)(blockIdx.x * kTM);
+    uint32_t ncols = 64;  // tensor-memory columns: a power of two >= nt * 64
+    while (ncols < (uint32_t)(nt * kTN)) ncols *= 2;
+    auto fail = [&]() {
+        atomicExch(err, 1);
+        *abort_flag = 1;
+    };
+
+    if (tid == 0) {
+        for (int b = 0; b < kBars; ++b) mbar_init(bar + b);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        *abort_flag = 0;
+        for (int q = 0; q < 5; ++q) prog[q] = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(sh)),
+                     "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = static_cast<uint32_t>(sh[0]);
+
+    if (warp == 4) {
+        // ---- producer
+        if (lane == 0) {
+            int la = 0, lb = 0;
+            for (int i = 0; i < items && !*abort_flag; ++i) {
+                const int c = i / nt, t = i - c * nt;
+                if (t == 0) {
+                    const int a = c % kRA;
+                    if (c >= kRA && !mbar_wait_ab(emptyA + a, (uint32_t)(((c / kRA) - 1) & 1), abort_flag)) {
+                        fail();
+                        break;
+                    }
+                    mbar_expect(fullA + a, kASplit32);
+                    bulk_load(sA0 + a * kASplit32, asplit + ((int64_t)blockIdx.x * kc + c) * kASplit32, kASplit32,
+                              fullA + a);
+                    la = c + 1;
+                }
+                const int b = i % kRB;
+                if (i >= kRB && !mbar_wait_ab(emptyB + b, (uint32_t)(((i / kRB) - 1) & 1), abort_flag)) {
+                    fail();
+                    break;
+                }
+                mbar_expect(fullB + b, kBSplit32);
+                bulk_load(sB0 + b * kBSplit32, bsplit + ((t0 + t) * kc + c) * (int64_t)kBSplit32, kBSplit32,
+                          fullB + b);
+                lb = i + 1;
+            }
+            prog[0] = la;
+            prog[1] = lb;
+        }
+    } else if (warp == 5) {
+        // ---- MMA issue
+        if (lane == 0) {
+            int wa = 0, wb = 0, iss = 0;
+            for (int i = 0; i < items && !*abort_flag; ++i) {
+                const int c = i / nt, t = i - c * nt;
+                const int a = c % kRA, b = i % kRB;
+                if (!mbar_wait_ab(fullB + b, (uint32_t)((i / kRB) & 1), abort_flag)) {
+                    fail();
+                    break;
+                }
+                wb = i + 1;
+                if (t == 0) {
+                    if (!mbar_wait_ab(fullA + a, (uint32_t)((c / kRA) & 1), abort_flag)) {
+                        fail();
+                        break;
+                    }
+                    wa = c + 1;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const unsigned char* sA = sA0 + a * kASplit32;
+                const unsigned char* sB = sB0 + b * kBSplit32;
+                const unsigned char* As[3] = {sA + kABytes32, sA, sA};
+                const unsigned char* Bs[3] = {sB, sB + kBBytes32, sB};
+                uint32_t first = (c == 0) ? 1u : 0u;
+                for (int q = 0; q < 3; ++q) {
+                    for (int ks = 0; ks < kKT / 8; ++ks) {
+                        const uint64_t ad = make_desc32(smem_u32(As[q]) + (uint32_t)ks * 2u * kLBO);
+                        const uint64_t bd = make_desc32(smem_u32(Bs[q]) + (uint32_t)ks * 2u * kLBO);
+                        const uint32_t acc = first ? 0u : 1u;
+                        asm volatile(
+                            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+                                tmem + (uint32_t)(t * kTN)),
+                            "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+                        first = 0;
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(emptyB + b)));
+                if (t == nt - 1)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_u32(emptyA + a)));
+                if (c == kc - 1)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                        smem_u32(accf + t)));
+                iss = i + 1;
+            }
+            prog[2] = wa;
+            prog[3] = wb;
+            prog[4] = iss;
+        }
+    } else {
+        // ---- epilogue: warps 0-3, TMEM lanes 32 warp .. 32 warp + 31 = rows of the strip
+        const int r = warp * 32 + lane;
+        for (int t = 0; t < nt; ++t) {
+            const int w = mbar_wait_ab(accf + t, 0u, abort_flag);
+            if (!w && !*abort_flag) fail();
+            // one decision for all four warps (the flag may be raised between their reads)
+            if (named_sync_or_epilogue(!w || *abort_flag)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            // the previous tile's reduce-add has read the product buffer
+            if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            named_sync_epilogue();
+#pragma unroll
+            for (int cb = 0; cb < kTN; cb += 32) {
+                uint32_t v[32];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * kTN + cb);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                    "[%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                      "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < 32; ++q) pbuf[(cb + q) * kTM + r] = __uint_as_float(v[q]);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            named_sync_epilogue();
+            if (tid == 0) tma_reduce_add_c(&cmap, m0, (int)((t0 + t) * kTN), pbuf);
+        }
+        if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    // before the shared and tensor memory go away: every copy that was started has landed
+    // (loads no MMA waited for, after an abort), and every commit the MMA thread issued has
+    // arrived (the last use of each ring slot and accumulator is waited for by no one else)
+    if (tid == 128 && *abort_flag) {
+        for (int c = prog[2]; c < prog[0]; ++c) mbar_wait(fullA + c % kRA, (uint32_t)((c / kRA) & 1));
+        for (int i = prog[3]; i < prog[1]; ++i) mbar_wait(fullB + i % kRB, (uint32_t)((i / kRB) & 1));
+    }
+    if (tid == 160) {
+        const int iss = prog[4], closed = nt > 0 ? iss / nt : 0;
+        for (int j = max(0, iss - kRB); j < iss; ++j) mbar_wait(emptyB + j % kRB, (uint32_t)((j / kRB) & 1));
+        for (int c = max(0, closed - kRA); c < closed; ++c) mbar_wait(emptyA + c % kRA, (uint32_t)((c / kRA) & 1));
+        for (int t = 0; t < nt; ++t)
+            if ((kc - 1) * nt + t < iss) mbar_wait(accf + t, 0u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -503,8 +796,8 @@ EncodeTiledFn encode_tiled() {
 
 }  // namespace
 
-size_t tc_split_bytes(int64_t M, int64_t N) {
-    return (size_t)((M + kTM - 1) / kTM) * kASplit + (size_t)((N + kTN - 1) / kTN) * kBSplit;
+size_t tc_split_bytes(int64_t M, int64_t N, int kc) {
+    return ((size_t)((M + kTM - 1) / kTM) * kASplit + (size_t)((N + kTN - 1) / kTN) * kBSplit) * (size_t)kc;
 }
 
 cudaError_t tc_update_f32(int64_t M, int64_t N, const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
@@ -526,7 +819,7 @@ cudaError_t tc_update_f32(int64_t M, int64_t N, const float* A, int64_t lda, con
             unsigned char* bsplit = asplit + (size_t)tiles_m * kASplit;
             const int64_t total = tiles_m * kTM * kTK + tiles_n * kTN * kTK;
             k_split_ab<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16), 256, 0, s>>>(
-                A, lda, B, ldb, M, N, tiles_m, tiles_n, asplit, bsplit);
+                A, lda, B, ldb, M, N, kTK, 1, tiles_m, tiles_n, asplit, bsplit);
             cudaError_t e = cudaFuncSetAttribute(k_tc_update_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)kBulkSmem);
             if (e != cudaSuccess) return e;
@@ -547,6 +840,47 @@ cudaError_t tc_update_f32(int64_t M, int64_t N, const float* A, int64_t lda, con
     dim3 grid((unsigned)((M + kTM - 1) / kTM), (unsigned)((tiles_n + kTilesN - 1) / kTilesN));
     k_tc_update<<<grid, 128, kSmemBytes, s>>>(M, N, A, lda, B, ldb, C, ldc, vec, err);
     return cudaGetLastError();
+}
+
+cudaError_t tc_update_f32_k(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
+                            int64_t ldb, float* C, int64_t ldc, void* split, int* err, cudaStream_t s) {
+    if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
+    const int kc = (int)((K + kKT - 1) / kKT);  // 32-deep chunks
+    EncodeTiledFn enc = split ? encode_tiled() : nullptr;
+    if (K <= 256 && enc && (ldc % 4) == 0 && (((uintptr_t)C & 15) == 0) && M <= INT32_MAX && N <= INT32_MAX) {
+        CUtensorMap map;
+        const cuuint64_t dims[2] = {(cuuint64_t)M, (cuuint64_t)N};
+        const cuuint64_t strides[1] = {(cuuint64_t)ldc * sizeof(float)};
+        const cuuint32_t box[2] = {(cuuint32_t)kTM, (cuuint32_t)kTN};
+        const cuuint32_t estr[2] = {1, 1};
+        if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, C, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+            const int64_t tiles_m = (M + kTM - 1) / kTM, tiles_n = (N + kTN - 1) / kTN;
+            unsigned char* asplit = static_cast<unsigned char*>(split);
+            unsigned char* bsplit = asplit + (size_t)tiles_m * kc * kASplit32;
+            const int64_t total = (tiles_m * kTM * kKT + tiles_n * kTN * kKT) * kc;
+            k_split_ab32<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16), 256, 0, s>>>(
+                A, lda, B, ldb, M, N, K, kc, tiles_m, tiles_n, asplit, bsplit);
+            cudaError_t e =
+                cudaFuncSetAttribute(k_tc_update_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kKSmem);
+            if (e != cudaSuccess) return e;
+            // column tiles per CTA: enough CTAs for two waves of the SMs, at most kAccTiles
+            int64_t tpc = (tiles_m * tiles_n) / (2 * 152);
+            tpc = std::max<int64_t>(1, std::min<int64_t>(kAccTiles, tpc));
+            dim3 grid((unsigned)tiles_m, (unsigned)((tiles_n + tpc - 1) / tpc));
+            k_tc_update_k<<<grid, kUpdThreads, kKSmem, s>>>(map, M, N, kc, asplit, bsplit, (int)tpc, err);
+            return cudaGetLastError();
+        }
+    }
+    // no bulk path: one rank-64 pass per chunk
+    for (int64_t k0 = 0; k0 < K; k0 += kTK) {
+        const int64_t kw = std::min<int64_t>(kTK, K - k0);
+        if (kw != kTK) return cudaErrorInvalidValue;
+        cudaError_t e = tc_update_f32(M, N, A + k0 * lda, lda, B + k0, ldb, C, ldc, split, err, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace nb

@@ -199,11 +199,16 @@ cudaError_t launch_element_influence(const Elem* el, int64_t n_el, const double*
 
 // C[M x N] -= A[M x 64] * B[64 x N] on tcgen05 tensor cores (TF32 x3 split, FP32
 // accumulation); *err is set if a bounded wait gave up.  split (may be NULL): device work
-// space of tc_split_bytes(M, N) bytes (256-byte aligned) for the pre-split operand tiles of
-// the bulk-asynchronous path, taken when ldc % 4 == 0 and C is 16-byte aligned.
+// space of tc_split_bytes(M, N, 1) bytes (256-byte aligned) for the pre-split operand tiles
+// of the bulk-asynchronous path, taken when ldc % 4 == 0 and C is 16-byte aligned.
 cudaError_t tc_update_f32(int64_t M, int64_t N, const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
                           int64_t ldc, void* split, int* err, cudaStream_t s);
-size_t tc_split_bytes(int64_t M, int64_t N);
+// C[M x N] -= A[M x K] * B[K x N], K <= 256 (a multiple of 64 unless the bulk path runs), in
+// one pass over C: the products of the K/64 chunks accumulate in tensor memory.  split:
+// tc_split_bytes(M, N, ceil(K / 64)) bytes.  Without the bulk path: K/64 rank-64 updates.
+cudaError_t tc_update_f32_k(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
+                            int64_t ldb, float* C, int64_t ldc, void* split, int* err, cudaStream_t s);
+size_t tc_split_bytes(int64_t M, int64_t N, int kc);
 
 // Dense LU (column-major, lda = n).  d_info: two ints (first zero pivot, tensor-core timeout).  Scratch: pivots int32[n], work as documented in lu.cu.
 cudaError_t lu_factor_f64(double* A, int64_t n, int32_t* piv, int nb, double* work, int* d_info,
