@@ -484,34 +484,40 @@ __global__ void __launch_bounds__(128, 1)
 }
 
 // ---- rank-K update in one pass over C (K <= 256): the trailing update of a super-panel.
-// Operands are split in chunks of 32 along K (canonical K-major layout, SBO = 1 KB):
-// A tile (tm, chunk c) 32 KB (hi 16 KB, lo 16 KB), B tile (tn, c) 16 KB (hi 8 KB, lo 8 KB).
-constexpr int kKT = 32;                                    // chunk depth
-constexpr uint32_t kSBO32 = (kKT / 4) * kCoreBytes;        // 1024 B
-constexpr uint32_t kABytes32 = kTM * kKT * 4;              // 16 KB
-constexpr uint32_t kBBytes32 = kTN * kKT * 4;              // 8 KB
-constexpr uint32_t kASplit32 = 2 * kABytes32;              // 32 KB
-constexpr uint32_t kBSplit32 = 2 * kBBytes32;              // 16 KB
+// Wide tiles: each MMA is M = 128 x N = 256 x K = 8 (a 64-wide tile leaves the tensor core
+// mostly idle).  Operands are split in chunks of 16 along K (canonical K-major layout,
+// SBO = 512 B): A tile (tm, chunk c) 16 KB (hi 8 KB, lo 8 KB), B tile (256-column tile
+// tn, c) 32 KB (hi 16 KB, lo 16 KB).
+constexpr int kKT = 16;                                    // chunk depth
+constexpr int kTW = 256;                                   // columns per accumulator tile
+constexpr uint32_t kSBO16 = (kKT / 4) * kCoreBytes;        // 512 B
+constexpr uint32_t kABytes16 = kTM * kKT * 4;              // 8 KB
+constexpr uint32_t kBBytes16 = kTW * kKT * 4;              // 16 KB
+constexpr uint32_t kASplit16 = 2 * kABytes16;              // 16 KB
+constexpr uint32_t kBSplit16 = 2 * kBBytes16;              // 32 KB
+// instruction descriptor as kIdesc, N = 256
+constexpr uint32_t kIdescW = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTW >> 3) << 17) |
+                             ((uint32_t)(kTM >> 4) << 24);
 
-__device__ __forceinline__ uint32_t kmajor_off32(int r, int k) {
-    return (uint32_t)(r >> 3) * kSBO32 + (uint32_t)(k >> 2) * kLBO + (uint32_t)(r & 7) * 16u + (uint32_t)(k & 3) * 4u;
+__device__ __forceinline__ uint32_t kmajor_off16(int r, int k) {
+    return (uint32_t)(r >> 3) * kSBO16 + (uint32_t)(k >> 2) * kLBO + (uint32_t)(r & 7) * 16u + (uint32_t)(k & 3) * 4u;
 }
-__device__ __forceinline__ uint64_t make_desc32(uint32_t saddr) {
+__device__ __forceinline__ uint64_t make_desc16(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
     d |= (uint64_t)(kLBO >> 4) << 16;
-    d |= (uint64_t)(kSBO32 >> 4) << 32;
+    d |= (uint64_t)(kSBO16 >> 4) << 32;
     d |= 1ull << 46;
     return d;
 }
 
-// -A (M x K) and B (K x N) into 32-deep TF32 hi/lo tiles, kc = ceil(K / 32) chunks: A tile
-// (tm, c) at asplit + (tm kc + c) * 32 KB, B tile (tn, c) at bsplit + (tn kc + c) * 16 KB;
-// entries beyond M, N or K are zero.
-__global__ void k_split_ab32(const float* __restrict__ A, int64_t lda, const float* __restrict__ B, int64_t ldb,
+// -A (M x K) and B (K x N) into 16-deep TF32 hi/lo tiles, kc = ceil(K / 16) chunks: A tile
+// (tm, c) at asplit + (tm kc + c) * 16 KB, B tile (tn, c) (256 columns) at
+// bsplit + (tn kc + c) * 32 KB; entries beyond M, N or K are zero.
+__global__ void k_split_ab16(const float* __restrict__ A, int64_t lda, const float* __restrict__ B, int64_t ldb,
                              int64_t M, int64_t N, int64_t K, int kc, int64_t tiles_m, int64_t tiles_n,
                              unsigned char* __restrict__ asplit, unsigned char* __restrict__ bsplit) {
-    const int64_t na = tiles_m * kc * (kTM * kKT), nb = tiles_n * kc * (kTN * kKT);
+    const int64_t na = tiles_m * kc * (kTM * kKT), nb = tiles_n * kc * (kTW * kKT);
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < na + nb;
          idx += (int64_t)gridDim.x * blockDim.x) {
         if (idx < na) {
@@ -520,45 +526,45 @@ __global__ void k_split_ab32(const float* __restrict__ A, int64_t lda, const flo
             const int r = e % kTM, k = e / kTM;
             const int64_t gm = (tc / kc) * kTM + r, gk = (tc % kc) * kKT + k;
             const float x = (gm < M && gk < K) ? -A[gm + gk * lda] : 0.f;
-            unsigned char* t = asplit + tc * kASplit32;
-            put_pair(t, t + kABytes32, kmajor_off32(r, k), x);
+            unsigned char* t = asplit + tc * kASplit16;
+            put_pair(t, t + kABytes16, kmajor_off16(r, k), x);
         } else {
             const int64_t i2 = idx - na;
-            const int64_t tc = i2 / (kTN * kKT);  // tn * kc + c
-            const int e = (int)(i2 - tc * (kTN * kKT));
+            const int64_t tc = i2 / (kTW * kKT);  // tn * kc + c
+            const int e = (int)(i2 - tc * (kTW * kKT));
             const int k = e % kKT, col = e / kKT;
-            const int64_t gn = (tc / kc) * kTN + col, gk = (tc % kc) * kKT + k;
+            const int64_t gn = (tc / kc) * kTW + col, gk = (tc % kc) * kKT + k;
             const float x = (gn < N && gk < K) ? B[gk + gn * ldb] : 0.f;
-            unsigned char* t = bsplit + tc * kBSplit32;
-            put_pair(t, t + kBBytes32, kmajor_off32(col, k), x);
+            unsigned char* t = bsplit + tc * kBSplit16;
+            put_pair(t, t + kBBytes16, kmajor_off16(col, k), x);
         }
     }
 }
 
-// One CTA per SM owns a 128-row strip of C and nt <= kAccTiles 64-column tiles, each with
+// One CTA per SM owns a 128-row strip of C and nt <= kAccTiles 256-column tiles, each with
 // its own accumulator (up to all 512 TMEM columns), so C is read and written once for the
 // whole depth instead of once per panel.  Work items (chunk c, tile t) run chunk-major,
-// i = c nt + t; an item is 12 MMAs (lo hi, hi lo, hi hi over 4 steps of 8) into
+// i = c nt + t; an item is 6 MMAs (lo hi, hi lo, hi hi over 2 steps of 8) into
 // accumulator t, overwriting it at c = 0.  Warp-specialised, no block barrier in the
 // steady state:
-//   warp 4 (one lane)  producer: A chunks into a ring of kRA slots (32 KB), B items into a
-//                      ring of kRB slots (16 KB), each slot refilled once emptyA / emptyB
+//   warp 4 (one lane)  producer: A chunks into a ring of kRA slots (16 KB), B items into a
+//                      ring of kRB slots (32 KB), each slot refilled once emptyA / emptyB
 //                      says the MMAs that read it are done;
 //   warp 5 (one lane)  MMA issue: waits fullB (and fullA at t = 0), issues the item,
 //                      commits to emptyB, to emptyA when it closes a chunk, and to accf[t]
 //                      when it is of the last chunk;
 //   warps 0-3          epilogue (warp w reads TMEM lanes 32w..): per tile, waits accf[t],
-//                      moves the accumulator through the product buffer (once the previous
-//                      reduce has read it; a named barrier among these four warps) into a
-//                      TMA reduce-add into C.
+//                      moves the accumulator 64 columns at a time through the product
+//                      buffer (once the previous reduce has read it; a named barrier among
+//                      these four warps) into TMA reduce-adds into C.
 // The u-th use of a ring slot completes its phase u, so every wait's parity follows from
 // the item or chunk number.  Waits are bounded: a role that gives up records *err and
 // raises the CTA's abort flag, the others stop at their next step; before the tensor
 // memory is freed, every copy and MMA that was started is waited for (bounded).
-constexpr int kAccTiles = 8;
-constexpr int kRA = 2, kRB = 8;
+constexpr int kAccTiles = 2;
+constexpr int kRA = 4, kRB = 4;
 constexpr int kUpdThreads = 192;
-constexpr uint32_t kKSmem = kRA * kASplit32 + kRB * kBSplit32 + kCTile + 512;
+constexpr uint32_t kKSmem = kRA * kASplit16 + kRB * kBSplit16 + kCTile + 512;
 
 __device__ __forceinline__ void named_sync_epilogue() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 // barrier 1 among the 128 epilogue threads, returning the OR of v over them (the same
@@ -594,9 +600,9 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
                   int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sA0 = smem;
-    unsigned char* sB0 = smem + kRA * kASplit32;
-    float* pbuf = reinterpret_cast<float*>(smem + kRA * kASplit32 + kRB * kBSplit32);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kRA * kASplit32 + kRB * kBSplit32 + kCTile);
+    unsigned char* sB0 = smem + kRA * kASplit16;
+    float* pbuf = reinterpret_cast<float*>(smem + kRA * kASplit16 + kRB * kBSplit16);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kRA * kASplit16 + kRB * kBSplit16 + kCTile);
     uint64_t* fullA = bar;                 // [kRA]
     uint64_t* emptyA = bar + kRA;          // [kRA]
     uint64_t* fullB = bar + 2 * kRA;       // [kRB]
@@ -607,14 +613,14 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
     volatile int* abort_flag = sh + 1;
     int* prog = sh + 2;  // loadsA, loadsB, waitedA, waitedB, issued
 
-    const int64_t tiles_n = (N + kTN - 1) / kTN;
+    const int64_t tiles_n = (N + kTW - 1) / kTW;
     const int64_t t0 = (int64_t)blockIdx.y * tpc;
     const int nt = (int)max((int64_t)0, min((int64_t)tpc, tiles_n - t0));
     const int items = nt * kc;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m0 = (int)(blockIdx.x * kTM);
-    uint32_t ncols = 64;  // tensor-memory columns: a power of two >= nt * 64
-    while (ncols < (uint32_t)(nt * kTN)) ncols *= 2;
+    uint32_t ncols = 64;  // tensor-memory columns: a power of two >= nt * 256
+    while (ncols < (uint32_t)(nt * kTW)) ncols *= 2;
     auto fail = [&]() {
         atomicExch(err, 1);
         *abort_flag = 1;
@@ -648,8 +654,8 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
                         fail();
                         break;
                     }
-                    mbar_expect(fullA + a, kASplit32);
-                    bulk_load(sA0 + a * kASplit32, asplit + ((int64_t)blockIdx.x * kc + c) * kASplit32, kASplit32,
+                    mbar_expect(fullA + a, kASplit16);
+                    bulk_load(sA0 + a * kASplit16, asplit + ((int64_t)blockIdx.x * kc + c) * kASplit16, kASplit16,
                               fullA + a);
                     la = c + 1;
                 }
@@ -658,8 +664,8 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
                     fail();
                     break;
                 }
-                mbar_expect(fullB + b, kBSplit32);
-                bulk_load(sB0 + b * kBSplit32, bsplit + ((t0 + t) * kc + c) * (int64_t)kBSplit32, kBSplit32,
+                mbar_expect(fullB + b, kBSplit16);
+                bulk_load(sB0 + b * kBSplit16, bsplit + ((t0 + t) * kc + c) * (int64_t)kBSplit16, kBSplit16,
                           fullB + b);
                 lb = i + 1;
             }
@@ -686,21 +692,21 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
                     wa = c + 1;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const unsigned char* sA = sA0 + a * kASplit32;
-                const unsigned char* sB = sB0 + b * kBSplit32;
-                const unsigned char* As[3] = {sA + kABytes32, sA, sA};
-                const unsigned char* Bs[3] = {sB, sB + kBBytes32, sB};
+                const unsigned char* sA = sA0 + a * kASplit16;
+                const unsigned char* sB = sB0 + b * kBSplit16;
+                const unsigned char* As[3] = {sA + kABytes16, sA, sA};
+                const unsigned char* Bs[3] = {sB, sB + kBBytes16, sB};
                 uint32_t first = (c == 0) ? 1u : 0u;
                 for (int q = 0; q < 3; ++q) {
                     for (int ks = 0; ks < kKT / 8; ++ks) {
-                        const uint64_t ad = make_desc32(smem_u32(As[q]) + (uint32_t)ks * 2u * kLBO);
-                        const uint64_t bd = make_desc32(smem_u32(Bs[q]) + (uint32_t)ks * 2u * kLBO);
+                        const uint64_t ad = make_desc16(smem_u32(As[q]) + (uint32_t)ks * 2u * kLBO);
+                        const uint64_t bd = make_desc16(smem_u32(Bs[q]) + (uint32_t)ks * 2u * kLBO);
                         const uint32_t acc = first ? 0u : 1u;
                         asm volatile(
                             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(
-                                tmem + (uint32_t)(t * kTN)),
-                            "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+                                tmem + (uint32_t)(t * kTW)),
+                            "l"(ad), "l"(bd), "r"(kIdescW), "r"(acc));
                         first = 0;
                     }
                 }
@@ -727,31 +733,36 @@ __global__ void __launch_bounds__(kUpdThreads, 1)
             // one decision for all four warps (the flag may be raised between their reads)
             if (named_sync_or_epilogue(!w || *abort_flag)) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
-            // the previous tile's reduce-add has read the product buffer
-            if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-            named_sync_epilogue();
+            for (int pc = 0; pc < kTW / kTN; ++pc) {
+                const int64_t col0 = (t0 + t) * kTW + pc * kTN;
+                if (col0 >= N) break;  // the same for every epilogue thread
+                // the previous piece's reduce-add has read the product buffer
+                if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                named_sync_epilogue();
 #pragma unroll
-            for (int cb = 0; cb < kTN; cb += 32) {
-                uint32_t v[32];
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * kTN + cb);
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
-                    "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
-                    "[%32];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                      "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                      "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                for (int cb = 0; cb < kTN; cb += 32) {
+                    uint32_t v[32];
+                    const uint32_t taddr =
+                        tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * kTW + pc * kTN + cb);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                        "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
+                        "%30, %31}, [%32];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                          "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]),
+                          "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]),
+                          "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                        : "r"(taddr));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int q = 0; q < 32; ++q) pbuf[(cb + q) * kTM + r] = __uint_as_float(v[q]);
+                    for (int q = 0; q < 32; ++q) pbuf[(cb + q) * kTM + r] = __uint_as_float(v[q]);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                named_sync_epilogue();
+                if (tid == 0) tma_reduce_add_c(&cmap, m0, (int)col0, pbuf);
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            named_sync_epilogue();
-            if (tid == 0) tma_reduce_add_c(&cmap, m0, (int)((t0 + t) * kTN), pbuf);
         }
         if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     }
@@ -797,7 +808,8 @@ EncodeTiledFn encode_tiled() {
 }  // namespace
 
 size_t tc_split_bytes(int64_t M, int64_t N, int kc) {
-    return ((size_t)((M + kTM - 1) / kTM) * kASplit + (size_t)((N + kTN - 1) / kTN) * kBSplit) * (size_t)kc;
+    // kc 64-deep chunks; B counted in whole 256-column tiles, which covers both layouts
+    return ((size_t)((M + kTM - 1) / kTM) * kASplit + (size_t)((N + kTW - 1) / kTW) * 4 * kBSplit) * (size_t)kc;
 }
 
 cudaError_t tc_update_f32(int64_t M, int64_t N, const float* A, int64_t lda, const float* B, int64_t ldb, float* C,
@@ -845,7 +857,7 @@ cudaError_t tc_update_f32(int64_t M, int64_t N, const float* A, int64_t lda, con
 cudaError_t tc_update_f32_k(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
                             int64_t ldb, float* C, int64_t ldc, void* split, int* err, cudaStream_t s) {
     if (M <= 0 || N <= 0 || K <= 0) return cudaSuccess;
-    const int kc = (int)((K + kKT - 1) / kKT);  // 32-deep chunks
+    const int kc = (int)((K + kKT - 1) / kKT);  // 16-deep chunks
     EncodeTiledFn enc = split ? encode_tiled() : nullptr;
     if (K <= 256 && enc && (ldc % 4) == 0 && (((uintptr_t)C & 15) == 0) && M <= INT32_MAX && N <= INT32_MAX) {
         CUtensorMap map;
@@ -856,11 +868,11 @@ cudaError_t tc_update_f32_k(int64_t M, int64_t N, int64_t K, const float* A, int
         if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, C, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                 CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
-            const int64_t tiles_m = (M + kTM - 1) / kTM, tiles_n = (N + kTN - 1) / kTN;
+            const int64_t tiles_m = (M + kTM - 1) / kTM, tiles_n = (N + kTW - 1) / kTW;
             unsigned char* asplit = static_cast<unsigned char*>(split);
-            unsigned char* bsplit = asplit + (size_t)tiles_m * kc * kASplit32;
-            const int64_t total = (tiles_m * kTM * kKT + tiles_n * kTN * kKT) * kc;
-            k_split_ab32<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16), 256, 0, s>>>(
+            unsigned char* bsplit = asplit + (size_t)tiles_m * kc * kASplit16;
+            const int64_t total = (tiles_m * kTM * kKT + tiles_n * kTW * kKT) * kc;
+            k_split_ab16<<<(unsigned)std::min<int64_t>((total + 255) / 256, 152 * 16), 256, 0, s>>>(
                 A, lda, B, ldb, M, N, K, kc, tiles_m, tiles_n, asplit, bsplit);
             cudaError_t e =
                 cudaFuncSetAttribute(k_tc_update_k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kKSmem);
