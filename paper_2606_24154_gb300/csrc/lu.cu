@@ -271,8 +271,8 @@ constexpr int kCoopMaxG = 1024;
 constexpr long long kCoopSpinLimit = 1ll << 22;
 
 struct CoopScratch {
-    double cval[2][kCoopMaxG];
-    long long cidx[2][kCoopMaxG];
+    float cval[2][kCoopMaxG];
+    int cidx[2][kCoopMaxG];
     float cand[2][kCoopMaxG][64];
     float srow[2][64];
     unsigned int bar[4];  // bar[0]: grid-barrier arrivals of the factorisation
@@ -327,8 +327,6 @@ __global__ void __launch_bounds__(kCoopThreads, 1)
     const int w = (int)(k1 - k0);
     float* S = reinterpret_cast<float*>(smem_raw);  // R x w, column-major
     __shared__ float prow[64];
-    __shared__ double sv[kCoopThreads];
-    __shared__ long long si[kCoopThreads];
     __shared__ bool s_flag;
     const int G = gridDim.x, b = blockIdx.x;
     const int64_t rb0 = k0 + (int64_t)b * R;
@@ -339,52 +337,64 @@ __global__ void __launch_bounds__(kCoopThreads, 1)
     }
     __syncthreads();
     bool ok_piv = true;  // the previous pivot was nonzero
+    __shared__ float wv[kCoopThreads / 32];
+    __shared__ int wi[kCoopThreads / 32];
+    // (best, index) of the block: warp shuffles, then every thread over the warps' results;
+    // the largest value with the lowest index on ties, so the order of the reduction does
+    // not matter.  Magnitudes of FP32 values compare exactly in FP32 (no FP64 pipe), row
+    // indices fit in 32 bits (n < 2^31).  Every thread returns with the result in (v, ix).
+    auto block_best = [&](float& v, int& ix) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const float v2 = __shfl_xor_sync(0xffffffffu, v, o);
+            const int i2 = __shfl_xor_sync(0xffffffffu, ix, o);
+            if (v2 > v || (v2 == v && i2 < ix)) {
+                v = v2;
+                ix = i2;
+            }
+        }
+        if ((threadIdx.x & 31) == 0) {
+            wv[threadIdx.x >> 5] = v;
+            wi[threadIdx.x >> 5] = ix;
+        }
+        __syncthreads();
+        v = wv[0];
+        ix = wi[0];
+        for (int q = 1; q < kCoopThreads / 32; ++q)
+            if (wv[q] > v || (wv[q] == v && wi[q] < ix)) {
+                v = wv[q];
+                ix = wi[q];
+            }
+        __syncthreads();  // wv / wi are rewritten by the next reduction
+    };
     for (int jj = 0; jj < w; ++jj) {
         const int64_t j = k0 + jj;
         const int par = jj & 1;
-        // (a) column jj-1: scale and rank-1 update of this CTA's rows below it
-        if (jj > 0 && ok_piv) {
-            const float inv = 1.0f / prow[jj - 1];
-            for (int r = threadIdx.x; r < nr; r += kCoopThreads) {
-                if (rb0 + r < j) continue;
+        // (a) + (b): column jj-1 scaled and its rank-1 update applied to this thread's rows
+        // below it, then this thread's candidate for column jj from the same rows
+        float best = -1.0f;
+        int bidx = INT_MAX;
+        const float inv = (jj > 0 && ok_piv) ? 1.0f / prow[jj - 1] : 0.f;
+        for (int r = threadIdx.x; r < nr; r += kCoopThreads) {
+            if (rb0 + r < j) continue;
+            if (jj > 0 && ok_piv) {
                 const float l = S[(jj - 1) * R + r] * inv;
                 S[(jj - 1) * R + r] = l;
                 for (int c = jj; c < w; ++c) S[c * R + r] -= l * prow[c];
             }
-        }
-        __syncthreads();
-        // (b) this CTA's candidate for column jj
-        double best = -1.0;
-        long long bidx = LLONG_MAX;
-        for (int r = threadIdx.x; r < nr; r += kCoopThreads) {
-            if (rb0 + r < j) continue;
-            const double v = fabs((double)S[jj * R + r]);
-            if (v > best || (v == best && rb0 + r < bidx)) {
+            const float v = fabsf(S[jj * R + r]);
+            if (v > best || (v == best && (int)(rb0 + r) < bidx)) {
                 best = v;
-                bidx = rb0 + r;
+                bidx = (int)(rb0 + r);
             }
         }
-        sv[threadIdx.x] = best;
-        si[threadIdx.x] = bidx;
-        __syncthreads();
-        for (int st = kCoopThreads / 2; st > 0; st >>= 1) {
-            if (threadIdx.x < st) {
-                const double v = sv[threadIdx.x + st];
-                const long long ix = si[threadIdx.x + st];
-                if (v > sv[threadIdx.x] || (v == sv[threadIdx.x] && ix < si[threadIdx.x])) {
-                    sv[threadIdx.x] = v;
-                    si[threadIdx.x] = ix;
-                }
-            }
-            __syncthreads();
-        }
-        const long long mine = si[0];
+        block_best(best, bidx);
+        const int mine = bidx;
         if (threadIdx.x == 0) {
-            cs->cval[par][b] = sv[0];
+            cs->cval[par][b] = best;
             cs->cidx[par][b] = mine;
         }
         if (threadIdx.x < w) {
-            cs->cand[par][b][threadIdx.x] = (mine != LLONG_MAX) ? S[threadIdx.x * R + (int)(mine - rb0)] : 0.f;
+            cs->cand[par][b][threadIdx.x] = (mine != INT_MAX) ? S[threadIdx.x * R + (int)(mine - rb0)] : 0.f;
             if (j >= rb0 && j < rb0 + nr) cs->srow[par][threadIdx.x] = S[threadIdx.x * R + (int)(j - rb0)];
         }
         if (!coop_barrier(cs, bar_base + (unsigned)(jj + 1) * (unsigned)G, &s_flag, limit)) {
@@ -395,36 +405,23 @@ __global__ void __launch_bounds__(kCoopThreads, 1)
             return;
         }
         // (c) the pivot: largest |a| over the candidates, lowest row on ties
-        best = -1.0;
-        bidx = LLONG_MAX;
+        best = -1.0f;
+        bidx = INT_MAX;
         for (int q = threadIdx.x; q < G; q += kCoopThreads) {
-            const double v = __ldcg(&cs->cval[par][q]);
-            const long long ix = __ldcg(&cs->cidx[par][q]);
+            const float v = __ldcg(&cs->cval[par][q]);
+            const int ix = __ldcg(&cs->cidx[par][q]);
             if (v > best || (v == best && ix < bidx)) {
                 best = v;
                 bidx = ix;
             }
         }
-        sv[threadIdx.x] = best;
-        si[threadIdx.x] = bidx;
-        __syncthreads();
-        for (int st = kCoopThreads / 2; st > 0; st >>= 1) {
-            if (threadIdx.x < st) {
-                const double v = sv[threadIdx.x + st];
-                const long long ix = si[threadIdx.x + st];
-                if (v > sv[threadIdx.x] || (v == sv[threadIdx.x] && ix < si[threadIdx.x])) {
-                    sv[threadIdx.x] = v;
-                    si[threadIdx.x] = ix;
-                }
-            }
-            __syncthreads();
-        }
-        const int64_t p = (si[0] >= j && si[0] < n) ? si[0] : j;
+        block_best(best, bidx);
+        const int64_t p = ((int64_t)bidx >= j && (int64_t)bidx < n) ? (int64_t)bidx : j;
         const int owner = (int)((p - k0) / R);
         if (threadIdx.x < w) prow[threadIdx.x] = __ldcg(&cs->cand[par][owner][threadIdx.x]);
         if (b == 0 && threadIdx.x == 0) {
             piv[j] = (int32_t)p;
-            if (!(sv[0] > 0.0) && *info == 0) *info = (int)(j + 1);
+            if (!(best > 0.0f) && *info == 0) *info = (int)(j + 1);
         }
         __syncthreads();
         ok_piv = prow[jj] != 0.f;  // the scaling below is skipped for a zero pivot, as in k_panel_col
