@@ -275,12 +275,13 @@ int nebem_eval_device(nebem_ctx *ctx, const double *d_pts, int64_t n, double *d_
 
 /* Mixed-precision evaluation (Sec. 2, Eq. Potential / Eq. Field: the same sums as
  * nebem_eval with precision NEBEM_MIXED) with an error estimate for every result.  The FP32
- * pass keeps, per point, the scale of its rounding and truncation errors: B_phi =
- * ke sum_j |sigma_j| |sum_k Phi'_jk| and B_E = ke sum_j |sigma_j| |sum_k E'_jk|_1 over its
- * FP32 (element, image) pairs.  Its estimated absolute errors are 1.5e-7 B_phi (V) and
- * 1.5e-7 B_E (of |E|, V/m): the factor is 1.6 times or more the largest error-to-scale
- * ratio measured against the FP64 path (a statistical estimate, not a bound).  A point
- * whose estimate exceeds mixed_point_tol times its
+ * pass keeps, per point, the scales of its rounding and truncation errors, from the
+ * per-element terms b_j = |sigma_j| |sum_k Phi'_jk| (for E: |sigma_j| |sum_k E'_jk|_1) over
+ * its FP32 (element, image) pairs: B = ke sum_j b_j and S = ke sqrt(sum_j b_j^2).  Its
+ * estimated absolute error of x = phi (V) and x = |E| (V/m) is
+ * 1e-7 |x| + 7e-8 B + 5e-7 S (constants: nebem_set_error_model), which covers every error
+ * measured against the FP64 path by 1.7 times or more (a statistical estimate, not a
+ * bound).  A point whose estimate exceeds mixed_point_tol times its
  * |phi| or |E| (context option, default 1e-6) is evaluated again in two-float arithmetic
  * (about 44 bits): first with the same Gauss rules and FP64 near pairs (estimate 1e-9 B),
  * and where that estimate still exceeds the tolerance, with rules truncated below ~3e-12 of
@@ -301,6 +302,15 @@ int nebem_eval_err(nebem_ctx *ctx, const double *pts, int64_t n, double *phi, do
                    int64_t *n_refined);
 int nebem_eval_device_err(nebem_ctx *ctx, const double *d_pts, int64_t n, double *d_phi, double *d_E, double *d_err,
                           void *stream);
+
+/* Constants of the FP32 pass's error estimate (see nebem_eval_err) for the following
+ * mixed evaluations of this context: the estimate of each point is
+ * gamma_r |x| + gamma_b B + gamma_s S for x = phi and x = |E| alike, with B and S the
+ * point's error scales (see nebem_eval_err).  A negative constant restores its default.
+ * With (0, 1, 0) or (0, 0, 1) and mixed_point_tol = 0, nebem_eval_err returns the scales
+ * B or S themselves.  A library utility with no counterpart in the paper.  Errors:
+ * NEBEM_INVALID_ARG (NULL, a non-finite constant). */
+int nebem_set_error_model(nebem_ctx *ctx, double gamma_r, double gamma_b, double gamma_s);
 
 /* Set the context's wait_polls option (see nebem_options) for the following calls; 0
  * restores the default.  A library utility with no counterpart in the paper.  Errors:

@@ -456,6 +456,17 @@ int nebem_eval_err(nebem_ctx* ctx, const double* pts, int64_t n, double* phi, do
     return NEBEM_OK;
 }
 
+int nebem_set_error_model(nebem_ctx* ctx, double gamma_r, double gamma_b, double gamma_s) {
+    if (!ctx || !std::isfinite(gamma_r) || !std::isfinite(gamma_b) || !std::isfinite(gamma_s))
+        return fail(NEBEM_INVALID_ARG, "bad argument");
+    Ctx* c = reinterpret_cast<Ctx*>(ctx);
+    const ErrModel d = default_err_model();
+    c->err_model.gamma_r = gamma_r < 0.0 ? d.gamma_r : gamma_r;
+    c->err_model.gamma_b = gamma_b < 0.0 ? d.gamma_b : gamma_b;
+    c->err_model.gamma_s = gamma_s < 0.0 ? d.gamma_s : gamma_s;
+    return NEBEM_OK;
+}
+
 int nebem_set_wait_polls(nebem_ctx* ctx, int32_t polls) {
     if (!ctx || polls < 0) return fail(NEBEM_INVALID_ARG, "bad argument");
     reinterpret_cast<Ctx*>(ctx)->opt.wait_polls = polls;

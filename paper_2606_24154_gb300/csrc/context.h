@@ -102,6 +102,8 @@ struct Ctx {
     // the points the last refined mixed evaluation re-evaluated (inside d_scratch)
     DevBuf d_pts, d_phi, d_E, d_err, d_scratch;
     const int32_t* refine_list = nullptr;
+    // error model of the FP32 pass (nebem_set_error_model; default_err_model())
+    ErrModel err_model = default_err_model();
 
     // known-charge set (space charge)
     int64_t n_car = 0;

@@ -2,21 +2,28 @@
 // over elements and periodic images): per-point error estimates of the FP32 pass, and a
 // two-float re-evaluation of the points whose estimate exceeds the requested tolerance.
 //
-// Error estimate.  The FP32 pass (eval_blocks.cuh) leaves per point the scales
-// B_phi = ke sum_j |sigma_j| |sum_k Phi'_jk| and B_E = ke sum_j |sigma_j| |sum_k E'_jk|_1
-// of its FP32 pairs.  Its error comes from rounding the point-to-centroid difference and
-// the node arithmetic to FP32 (about u = 2^-24 relative per operation), the FP32 charge
-// densities and node weights, and the truncation of the Gauss rules; none of these grows
-// with the result, so a point whose |phi| (|E|) is small next to B_phi (B_E) -- a
-// potential near zero inside the plate, the weak field inside a conductor -- loses its
-// relative accuracy there.  The estimate is gamma * B with gamma = 1.5e-7 for both.
-// Measured against the FP64 path, the largest error-to-scale ratios were 3.2e-8 (phi) and
-// 5.9e-8 (E) over 40,000 points of the THGEM cell, and 8.2e-8 (phi) and 9.2e-8 (E) on the
-// cube's 10,000-point grid; the factor leaves a margin of 1.6x or more over all of them.
-// The estimate is statistical, not a bound: rounding errors of many pairs add up like a
-// random sum whose ratio to B spreads about fivefold between its median and its maximum.
+// Error estimate.  The FP32 pass (eval_blocks.cuh) leaves per point the scales of its FP32
+// pairs' errors, built from the per-element terms b_j = |sigma_j| |sum_k Phi'_jk| (for E:
+// |sigma_j| |sum_k E'_jk|_1): B = ke sum_j b_j and S = ke sqrt(sum_j b_j^2).  Its error
+// comes from rounding the point-to-centroid difference and the node arithmetic to FP32
+// (about u = 2^-24 relative per operation) and from the truncation of the Gauss rules.
+// These do not shrink with the result, so a point whose |phi| (|E|) is small next to B --
+// a potential near zero inside the plate, the weak field in the drift gap -- loses its
+// relative accuracy there.  The estimate for x = phi and x = |E| is
+//   gamma_r |x| + gamma_b B + gamma_s S,   gamma_r = 1e-7, gamma_b = 7e-8, gamma_s = 5e-7.
+// Calibration: against the FP64 path on 133,000 points (the THGEM cell with solved and
+// with structured densities, points in the gas, through the plate and 1-2 um off the Cu
+// faces; the cube with solved densities on its grid and at random points; a reduced THGEM
+// cell), the largest error ratios were 3.3e-8 B (phi) and 5.5e-8 B (E) on the THGEM cell
+// and 7.7e-8 of the result on the cube and the reduced cell, where B and the result are
+// close.  The constants cover every one of those errors by 1.7x or more (2x for phi).
+// Most of the error follows B, not S: many pairs round alike (every element of a plane sees
+// a point at the same z offset, identical elements carry identical FP32 node tables), so
+// their errors keep one sign instead of averaging out; the S term covers the rest.  The
+// estimate is statistical, not a bound.  The constants can be changed per context
+// (nebem_set_error_model).
 //
-// Refinement.  A point is re-evaluated when gamma B_phi > tol |phi| or gamma B_E > tol |E|,
+// Refinement.  A point is re-evaluated when its estimate exceeds tol |phi| or tol |E|,
 // in two-float arithmetic (about 44 bits; the error-free transformations of twofloat.cuh),
 // in two levels.  Level 1 keeps the FP32 pass's Gauss rules and tiers and its FP64 near
 // pairs: their truncation, measured against the closed forms on THGEM points, stays below
@@ -40,8 +47,9 @@ namespace {
 
 constexpr int kAT = 128;             // threads (flagged points) per block
 constexpr int kATBlocks = 4;         // resident far blocks per SM (128 registers a thread)
-constexpr double kGammaPhi = 1.5e-7; // FP32 pass: error of phi <= kGammaPhi * B_phi
-constexpr double kGammaE = 1.5e-7;   // FP32 pass: error of |E| <= kGammaE * B_E
+constexpr double kErrGammaR = 1e-7;   // FP32 pass: share of the result
+constexpr double kErrGammaB = 7e-8;   // FP32 pass: share of B
+constexpr double kErrGammaS = 5e-7;   // FP32 pass: share of S
 constexpr double kGammaL1 = 1e-9;    // two-float, the FP32 pass's rules (truncation ~1e-10 B)
 constexpr double kGammaL2 = 1e-11;   // two-float, fill-grade rules
 
@@ -262,11 +270,11 @@ __device__ __forceinline__ Sum6 acc_range(const AccView& A, int nimg, int te, fl
 }
 
 // ke * sums of point p at level L into phi / E, the level's estimate into err, and (level 1)
-// ke * (B_phi, B_E) into bound for the next flag step.
+// ke * (B_phi, B_E, 0, 0) into bound for the next flag step.
 template <int L>
 __device__ __forceinline__ void store_acc(int64_t p, const Sum6& tot, double* __restrict__ phi,
                                           double* __restrict__ E, double* __restrict__ err,
-                                          float2* __restrict__ bound) {
+                                          float4* __restrict__ bound) {
     const double ke = 1.0 / (4.0 * kPi * kEps0);
     const double gamma = (L == 1) ? kGammaL1 : kGammaL2;
     if (phi) phi[p] = ke * tot.phi;
@@ -279,7 +287,7 @@ __device__ __forceinline__ void store_acc(int64_t p, const Sum6& tot, double* __
         err[2 * p] = gamma * ke * tot.bphi;
         err[2 * p + 1] = gamma * ke * tot.bE;
     }
-    if (L == 1) bound[p] = make_float2((float)(ke * tot.bphi), (float)(ke * tot.bE));
+    if (L == 1) bound[p] = make_float4((float)(ke * tot.bphi), (float)(ke * tot.bE), 0.f, 0.f);
 }
 
 // Far part of every listed point at level L, thread per point, kAT points (a group) per
@@ -294,7 +302,7 @@ __global__ void __launch_bounds__(kAT, kATBlocks)
     k_eval_acc_far(const AccView A, int nimg, int te, const double* __restrict__ pts,
                    const int32_t* __restrict__ list, const int32_t* __restrict__ n_list, int nch, int64_t cap,
                    Sum6* __restrict__ part, double* __restrict__ phi, double* __restrict__ E,
-                   double* __restrict__ err, float2* __restrict__ bound) {
+                   double* __restrict__ err, float4* __restrict__ bound) {
     extern __shared__ float4 sm[];
     const int64_t count = *n_list;
     const int64_t gb = gridDim.x;
@@ -331,7 +339,7 @@ template <int L>
 __global__ void __launch_bounds__(256)
     k_acc_reduce(const int32_t* __restrict__ list, const int32_t* __restrict__ n_list, int64_t gb, int nch,
                  int64_t cap, const Sum6* __restrict__ part, double* __restrict__ phi, double* __restrict__ E,
-                 double* __restrict__ err, float2* __restrict__ bound) {
+                 double* __restrict__ err, float4* __restrict__ bound) {
     const int64_t count = *n_list;
     const int64_t G = (count + kAT - 1) / kAT;
     const int64_t Gm = (G / gb) * gb;
@@ -410,13 +418,14 @@ __global__ void __launch_bounds__(128)
 }
 
 // Flags and lists (in their input order within each block) the points whose estimate
-// gamma * bound exceeds tol times |phi| or |E| (when refine != 0).  Input: order[i] (or i
-// when order is null) for i < n, or i < *n_dev when n_dev is given.  err (may be null)
-// receives every input point's estimate.
+// gr |x| + gb B + gs S (x = phi or E, bound = (B_phi, B_E, S_phi, S_E)) exceeds tol |x| (when
+// refine != 0).  Input: order[i] (or i when order is null) for i < n, or i < *n_dev when
+// n_dev is given.  err (may be null) receives every input point's estimate.
 __global__ void __launch_bounds__(256)
-    k_flag(const double* __restrict__ phi, const double* __restrict__ E, const float2* __restrict__ bound,
-           const int32_t* __restrict__ order, int64_t n, const int32_t* __restrict__ n_dev, double gphi, double gE,
-           double tol, int refine, double* __restrict__ err, int32_t* __restrict__ list, int32_t* __restrict__ n_list) {
+    k_flag(const double* __restrict__ phi, const double* __restrict__ E, const float4* __restrict__ bound,
+           const int32_t* __restrict__ order, int64_t n, const int32_t* __restrict__ n_dev, double gr, double gb,
+           double gs, double tol, int refine, double* __restrict__ err, int32_t* __restrict__ list,
+           int32_t* __restrict__ n_list) {
     __shared__ int32_t s_warp[8];
     __shared__ int32_t s_base;
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
@@ -425,13 +434,17 @@ __global__ void __launch_bounds__(256)
     int32_t p = 0;
     if (i < count) {
         p = order ? order[i] : (int32_t)i;
-        const float2 b = bound[p];
-        const double ep = gphi * (double)b.x, eE = gE * (double)b.y;
-        if (phi && ep > tol * fabs(phi[p])) f = true;
+        const float4 b = bound[p];
+        const double ap = phi ? fabs(phi[p]) : 0.0;
+        double aE = 0.0;
         if (E) {
             const double ex = E[3 * p], ey = E[3 * p + 1], ez = E[3 * p + 2];
-            if (eE > tol * sqrt(ex * ex + ey * ey + ez * ez)) f = true;
+            aE = sqrt(ex * ex + ey * ey + ez * ez);
         }
+        const double ep = gr * ap + gb * (double)b.x + gs * (double)b.z;
+        const double eE = gr * aE + gb * (double)b.y + gs * (double)b.w;
+        if (phi && ep > tol * ap) f = true;
+        if (E && eE > tol * aE) f = true;
         f = f && refine;
         if (err) {
             err[2 * p] = ep;
@@ -474,7 +487,7 @@ RefineGrid refine_grid(int64_t npts, int sms, int64_t n_el) {
 
 template <int L>
 cudaError_t launch_level(const AccView& A, const ImageTable& img, const double* pts, int64_t npts, double* phi,
-                         double* E, double* err, float2* bound, const int32_t* list, const int32_t* n_list, int sms,
+                         double* E, double* err, float4* bound, const int32_t* list, const int32_t* n_list, int sms,
                          Sum6* part, cudaStream_t s) {
     using Lv = Level<L>;
     // element tile: a power of two (divides the chunk width), at most 16, within ~40 KB
@@ -503,14 +516,16 @@ cudaError_t launch_level(const AccView& A, const ImageTable& img, const double* 
 
 }  // namespace
 
+ErrModel default_err_model() { return ErrModel{kErrGammaR, kErrGammaB, kErrGammaS}; }
+
 size_t refine_part_bytes(int64_t npts, int sms, int64_t n_el) {
     const RefineGrid rg = refine_grid(npts, sms, n_el);
     return sizeof(Sum6) * (size_t)rg.cap * (size_t)rg.nch;
 }
 
 cudaError_t launch_eval_refine(const AccView& A, const ImageTable& img, const double* pts, int64_t npts,
-                               double* phi, double* E, double* err, double tol, const MixedScratch& ms, int sms,
-                               cudaStream_t s, cudaEvent_t* ev, void* part_buf) {
+                               double* phi, double* E, double* err, double tol, const ErrModel& em,
+                               const MixedScratch& ms, int sms, cudaStream_t s, cudaEvent_t* ev, void* part_buf) {
     Sum6* part = static_cast<Sum6*>(part_buf);
     if (!part) return cudaErrorInvalidValue;
     if (npts == 0) return cudaSuccess;
@@ -519,15 +534,15 @@ cudaError_t launch_eval_refine(const AccView& A, const ImageTable& img, const do
     cudaError_t e = cudaMemsetAsync(ms.n_list, 0, 2 * sizeof(int32_t), s);  // both levels' counts
     if (e != cudaSuccess) return e;
     const unsigned fb = (unsigned)((npts + 255) / 256);
-    k_flag<<<fb, 256, 0, s>>>(phi, E, ms.bound, ms.order, npts, nullptr, kGammaPhi, kGammaE, tol, refine ? 1 : 0, err,
-                              ms.list, ms.n_list);
+    k_flag<<<fb, 256, 0, s>>>(phi, E, ms.bound, ms.order, npts, nullptr, em.gamma_r, em.gamma_b, em.gamma_s, tol,
+                              refine ? 1 : 0, err, ms.list, ms.n_list);
     e = cudaGetLastError();
     if (e == cudaSuccess && refine)  // level 1 on the flagged points; it leaves their level-1 scales in ms.bound
         e = launch_level<1>(A, img, pts, npts, phi, E, err, ms.bound, ms.list, ms.n_list, sms, part, s);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], s);
     if (e == cudaSuccess && refine) {
         // level 2 on the points whose level-1 estimate still exceeds the tolerance
-        k_flag<<<fb, 256, 0, s>>>(phi, E, ms.bound, ms.list, npts, ms.n_list, kGammaL1, kGammaL1, tol, 1, nullptr,
+        k_flag<<<fb, 256, 0, s>>>(phi, E, ms.bound, ms.list, npts, ms.n_list, 0.0, kGammaL1, 0.0, tol, 1, nullptr,
                                   ms.list2, ms.n_list + 1);
         e = cudaGetLastError();
         if (e == cudaSuccess)

@@ -35,12 +35,15 @@
 // pair, and each point's sums run in a fixed order, so a point's result is bit-identical
 // whatever other points share its launch.
 //
-// Error scale.  Beside the sums, the far part accumulates per point the scale of its
-// rounding and truncation errors: B_phi = sum_j |sigma_j| |sum_k Phi'_jk| and
-// B_E = sum_j |sigma_j| |sum_k E'_jk|_1 over the FP32 pairs.  The FP32 pass's error of Phi
-// (of E) stays below a small multiple of u B (u = 2^-24); eval_acc.cu turns these scales
-// into a per-point error estimate and refines the points whose estimate exceeds the
-// requested relative tolerance.  The scales do not enter the sums themselves.
+// Error scales.  Beside the sums, the far part accumulates per point the scales of its
+// rounding and truncation errors from the per-element terms b_j = |sigma_j| |sum_k Phi'_jk|
+// (for E: |sigma_j| |sum_k E'_jk|_1) over the FP32 pairs: their sum B = sum_j b_j and their
+// root sum of squares S = sqrt(sum_j b_j^2).  Errors that keep their sign from element to
+// element (the Gauss rules' truncation) grow with B; rounding errors, whose signs vary
+// from element to element, add up like a random sum and grow with S, which is far smaller
+// than B when many elements contribute alike.  eval_acc.cu turns the scales into a
+// per-point error estimate and refines the points whose estimate exceeds the requested
+// relative tolerance.  The scales do not enter the sums themselves.
 #pragma once
 #include "influence.cuh"
 
@@ -108,14 +111,24 @@ struct Sum6 {
     double phi, x, y, z, bphi, bE;
 };
 
-// Per-thread error scales of the far pass, (B_phi, B_E) raw: positive sums, FP32 is ample.
-// They live in a shared-memory slot (read and written once per element) rather than in
-// registers across the element loop; bound_reset() before a point's first range.
-__device__ __forceinline__ float2* bound_slot() {
-    __shared__ float2 s_bnd[kEvalThreads];
+// Per-thread error scales of the far pass, raw (before the factor ke): (B_phi, B_E, the
+// sums of squares of the terms b_j of B_phi and B_E, each term scaled by kScaleSq first).
+// Positive sums, FP32 is ample.  They live in a shared-memory slot (read and written once
+// per element) rather than in registers across the element loop; bound_reset() before a
+// point's first range.
+// The squares are taken of b_j * 2^33 (2^33 ~ ke): a term of 1e-19 .. 1e19 volts then
+// squares to a normal FP32 number.
+constexpr float kScaleSq = 8589934592.0f;  // 2^33
+__device__ __forceinline__ float4* bound_slot() {
+    __shared__ float4 s_bnd[kEvalThreads];
     return &s_bnd[threadIdx.x];
 }
-__device__ __forceinline__ void bound_reset() { *bound_slot() = make_float2(0.f, 0.f); }
+__device__ __forceinline__ void bound_reset() { *bound_slot() = make_float4(0.f, 0.f, 0.f, 0.f); }
+// the point's scales summed over its element chunks (in chunk order), also in shared memory
+__device__ __forceinline__ float4* bound_total_slot() {
+    __shared__ float4 s_btot[kEvalThreads];
+    return &s_btot[threadIdx.x];
+}
 
 __device__ __forceinline__ Sum4 far_range(const GeomView& g, float phx, float phy, float phz, float plx, float ply,
                                           float plz, int64_t e0, int64_t e1) {
@@ -128,10 +141,10 @@ __device__ __forceinline__ Sum4 far_range(const GeomView& g, float phx, float ph
     __shared__ float4 s_a[kTileMax][2 * kPairsA];
     __shared__ int s_na[kTileMax];
     __shared__ float4 s_hdr[kTileMax];
-    __shared__ float s_sig[kTileMax];
+    __shared__ float2 s_sig[kTileMax];  // sigma_j (1 + wcorr_j) as hi + lo
     __shared__ float4 s_c[kCjkMax][2];  // image centroids: hi, lo
 
-    float2* bslot = bound_slot();
+    float4* bslot = bound_slot();
     double aphi = 0.0, aEx = 0.0, aEy = 0.0, aEz = 0.0;
     for (int64_t base = e0; base < e1; base += tile_el) {
         const int cnt = (int)min((int64_t)tile_el, e1 - base);
@@ -142,7 +155,9 @@ __device__ __forceinline__ Sum4 far_range(const GeomView& g, float phx, float ph
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
             s_hdr[i] = far[base + i].hdr;
             s_na[i] = far[base + i].n_a;
-            s_sig[i] = (float)sigma[base + i];
+            const double sd = fma(sigma[base + i], (double)far[base + i].wcorr, sigma[base + i]);
+            const float sh = __double2float_rn(sd);
+            s_sig[i] = make_float2(sh, __double2float_rn(sd - (double)sh));
         }
         const float4* src = cjk + 2 * base * nimg;
         for (int i = threadIdx.x; i < 2 * cnt * nimg; i += blockDim.x) s_c[i >> 1][i & 1] = src[i];
@@ -175,15 +190,22 @@ __device__ __forceinline__ Sum4 far_range(const GeomView& g, float phx, float ph
                 }
                 // nearer pairs: k_eval_near
             }
-            const float s = s_sig[jj];
+            const float2 sg = s_sig[jj];
+            const float s = sg.x;
             const float fphi = lphi.x + lphi.y, fx = lx.x + lx.y, fy = ly.x + ly.y, fz = lz.x + lz.y;
-            gphi = fmaf(s, fphi, gphi);
-            gx = fmaf(s, fx, gx);
-            gy = fmaf(s, fy, gy);
-            gz = fmaf(s, fz, gz);
-            float2 b = *bslot;
-            b.x = fmaf(fabsf(s), fabsf(fphi), b.x);
-            b.y = fmaf(fabsf(s), fabsf(fx) + fabsf(fy) + fabsf(fz), b.y);
+            // sigma in two floats: a density that is uniform over many elements (a plane far
+            // from the structure) would otherwise carry one FP32 rounding error for all of them
+            gphi = fmaf(s, fphi, fmaf(sg.y, fphi, gphi));
+            gx = fmaf(s, fx, fmaf(sg.y, fx, gx));
+            gy = fmaf(s, fy, fmaf(sg.y, fy, gy));
+            gz = fmaf(s, fz, fmaf(sg.y, fz, gz));
+            float4 b = *bslot;
+            const float t0 = fabsf(s) * fabsf(fphi), t1 = fabsf(s) * (fabsf(fx) + fabsf(fy) + fabsf(fz));
+            const float q0 = t0 * kScaleSq, q1 = t1 * kScaleSq;
+            b.x += t0;
+            b.y += t1;
+            b.z = fmaf(q0, q0, b.z);
+            b.w = fmaf(q1, q1, b.w);
             *bslot = b;
             if ((jj % kGroup) == kGroup - 1 || jj == cnt - 1) {
                 aphi += (double)gphi;
@@ -228,17 +250,27 @@ __device__ __forceinline__ void store_far(const double* __restrict__ pts, double
     }
 }
 
-// ke * (B_phi, B_E) of point p (the FP32 pass's error scales, V and V/m)
-__device__ __forceinline__ void store_bound(float2* __restrict__ bound, int64_t p, float2 b) {
+// ke * (B_phi, B_E, S_phi, S_E) of point p (the FP32 pass's error scales, V and V/m) from
+// the raw sums of bound_slot()
+__device__ __forceinline__ void store_bound(float4* __restrict__ bound, int64_t p, float4 b) {
     const double ke = 1.0 / (4.0 * kPi * kEps0);
-    if (bound) bound[p] = make_float2((float)(ke * b.x), (float)(ke * b.y));
+    const double inv = 1.0 / (double)kScaleSq;
+    if (bound)
+        bound[p] = make_float4((float)(ke * b.x), (float)(ke * b.y), (float)(ke * inv * sqrt((double)b.z)),
+                               (float)(ke * inv * sqrt((double)b.w)));
+}
+__device__ __forceinline__ void add4f(float4& t, const float4& c) {
+    t.x += c.x;
+    t.y += c.y;
+    t.z += c.z;
+    t.w += c.w;
 }
 
 // Far part (FP32 tiers) of `count` targets; writes ke * sum (overwrites phi / E).  Thread
 // t takes point idx[base + t] (or base + t when idx is null) of pts / phi / E.  The
 // elements are summed in chunks of kChunkEl whose FP64 sums are added in order, so that
 // a launch split over element chunks (the server's small requests) gives the same bits.
-// `bound` (may be null) receives ke * (B_phi, B_E) per point.
+// `bound` (may be null) receives ke * (B_phi, B_E, S_phi, S_E) per point.
 __device__ __forceinline__ void add6(Sum6& t, const Sum6& c) {
     t.phi += c.phi;
     t.x += c.x;
@@ -251,13 +283,14 @@ __device__ __forceinline__ void add6(Sum6& t, const Sum6& c) {
 __device__ __forceinline__ void far_block(const GeomView& g, const double* __restrict__ pts,
                                           const int32_t* __restrict__ idx, int64_t base, int count,
                                           double* __restrict__ phi, double* __restrict__ E,
-                                          float2* __restrict__ bound) {
+                                          float4* __restrict__ bound) {
     const bool active = (int)threadIdx.x < count;
     const int64_t p = active ? (idx ? (int64_t)idx[base + threadIdx.x] : base + threadIdx.x) : 0;
     float phx, phy, phz, plx, ply, plz;
     load_point_2f(pts, p, active, phx, phy, phz, plx, ply, plz);
     Sum4 tot{0.0, 0.0, 0.0, 0.0};
-    float2 btot = make_float2(0.f, 0.f);  // chunk scales added in chunk order (as the server does)
+    float4* btot = bound_total_slot();  // chunk scales added in chunk order (as the server does)
+    *btot = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int64_t e0 = 0; e0 < g.n_el; e0 += kChunkEl) {
         bound_reset();
         const Sum4 c = far_range(g, phx, phy, phz, plx, ply, plz, e0, min(e0 + (int64_t)kChunkEl, g.n_el));
@@ -265,13 +298,11 @@ __device__ __forceinline__ void far_block(const GeomView& g, const double* __res
         tot.x += c.x;
         tot.y += c.y;
         tot.z += c.z;
-        const float2 b = *bound_slot();
-        btot.x += b.x;
-        btot.y += b.y;
+        add4f(*btot, *bound_slot());
     }
     if (active) {
         store_far(pts, phi, E, p, tot);
-        store_bound(bound, p, btot);
+        store_bound(bound, p, *btot);
     }
 }
 

@@ -11,7 +11,7 @@ namespace {
 __global__ void __launch_bounds__(kEvalThreads, 6) k_eval_far(const GeomView g, const double* __restrict__ pts,
                                                             const int32_t* __restrict__ order, int64_t npts,
                                                             double* __restrict__ phi, double* __restrict__ E,
-                                                            float2* __restrict__ bound) {
+                                                            float4* __restrict__ bound) {
     const int64_t base = (int64_t)blockIdx.x * blockDim.x;
     const int count = (int)min((int64_t)blockDim.x, npts - base);
     far_block(g, pts, order, base, count, phi, E, bound);
@@ -171,8 +171,8 @@ MixedScratch mixed_scratch(void* base, int64_t npts) {
     p += align256(sizeof(int32_t) * n);
     m.order = reinterpret_cast<int32_t*>(p);
     p += align256(sizeof(int32_t) * n);
-    m.bound = reinterpret_cast<float2*>(p);
-    p += align256(sizeof(float2) * n);
+    m.bound = reinterpret_cast<float4*>(p);
+    p += align256(sizeof(float4) * n);
     m.list = reinterpret_cast<int32_t*>(p);
     p += align256(sizeof(int32_t) * n);
     m.list2 = reinterpret_cast<int32_t*>(p);
@@ -183,7 +183,7 @@ MixedScratch mixed_scratch(void* base, int64_t npts) {
 
 size_t eval_mixed_scratch_bytes(int64_t npts) {
     const size_t n = (size_t)npts;
-    return align256(sizeof(int32_t) * kBins) + 4 * align256(sizeof(int32_t) * n) + align256(sizeof(float2) * n) +
+    return align256(sizeof(int32_t) * kBins) + 4 * align256(sizeof(int32_t) * n) + align256(sizeof(float4) * n) +
            256;
 }
 

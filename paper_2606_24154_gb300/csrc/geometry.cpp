@@ -270,6 +270,35 @@ int build_element(const nebem_element& r, const nebem_options& opt, Elem& e, dou
         collapsed(4, fn.b);
         collapsed(6, fn.c);
     }
+    // Weight totals.  Rounding the weights to FP32 leaves each tier's total off the area by
+    // a relative error of order 2^-24, the same for every element of one shape (identical
+    // elements of a mesh ring or a plane), so its effect on the far field would add up with
+    // one sign over those elements instead of averaging out.  Tiers a-c get their largest
+    // weight set so that their totals come as close to tier 0's as FP32 allows (within
+    // 2^-25 of that weight), and the remaining factor area / (tier 0's total) goes into
+    // wcorr, which the evaluation applies to sigma in two-float form.  The totals of a few
+    // dozen FP32 numbers of similar size are exact in FP64.
+    auto wsum = [](const float4* t, int np) {
+        double sum = 0.0;
+        for (int i = 0; i < np; ++i) sum += (double)t[2 * i + 1].z + (double)t[2 * i + 1].w;
+        return sum;
+    };
+    const double total0 = wsum(fn.f, kPairs0);
+    auto match = [&](float4* t, int np) {
+        float* big = nullptr;
+        for (int i = 0; i < np; ++i) {
+            float* wz = &t[2 * i + 1].z;
+            float* ww = &t[2 * i + 1].w;
+            if (!big || std::fabs(*wz) > std::fabs(*big)) big = wz;
+            if (std::fabs(*ww) > std::fabs(*big)) big = ww;
+        }
+        const double rest = wsum(t, np) - (double)*big;
+        *big = (float)(total0 - rest);
+    };
+    match(fn.a, n_a);
+    match(fn.b, kPairsB);
+    match(fn.c, kPairsC);
+    fn.wcorr = (float)(area / total0 - 1.0);
     const double r0 = opt.ratio_0 * rho, ra = opt.ratio_a * rho, rb = opt.ratio_b * rho,
                  rn = opt.ratio_near * rho;
     fn.hdr.x = (float)(r0 * r0);

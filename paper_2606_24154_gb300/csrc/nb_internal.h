@@ -58,7 +58,8 @@ struct __align__(16) FarNodes {
     float4 c[2 * kPairsC];
     float4 hdr;
     int32_t n_a;
-    int32_t pad[3];
+    float wcorr;  // area / (tier 0's FP32 weight total) - 1: applied to sigma (geometry.cpp)
+    int32_t pad[2];
 };
 
 // Mixed-precision fill (Eq. Matrix with far pairs by Gauss rules in two-float arithmetic).
@@ -135,13 +136,13 @@ GeomView make_view(const Elem* el, const FarNodes* far, const float4* cjk, const
 cudaError_t launch_eval_f64(const Elem* el, const double* sigma, int64_t n_el, const ImageTable& img,
                             const double* pts, int64_t npts, double* phi, double* E, cudaStream_t s);
 // Scratch of one mixed evaluation of npts points: binning (bin counts, keys, the binned
-// order), the FP32 pass's error scales ke * (B_phi, B_E) per point, and the list and count
-// of the points the refinement re-evaluates.
+// order), the FP32 pass's error scales ke * (B_phi, B_E, S_phi, S_E) per point, and the
+// list and count of the points the refinement re-evaluates.
 struct MixedScratch {
     int32_t* count;  // kBins
     int32_t* key;    // npts
     int32_t* order;  // npts
-    float2* bound;   // npts
+    float4* bound;   // npts
     int32_t* list;   // npts: points of the first refinement level
     int32_t* list2;  // npts: points of the second level
     int32_t* n_list; // 2: the two lists' lengths
@@ -171,16 +172,23 @@ struct AccView {
     const int32_t* cell_start;
     const int32_t* cell_items;
 };
-// Refinement after launch_eval_mixed: every point whose estimated error (gamma * bound)
-// exceeds tol times its |phi| or |E| is re-evaluated in two-float arithmetic with FP64 near
-// pairs, in two levels (eval_acc.cu); err (may be NULL, n x 2) receives the estimated
-// absolute error of phi and |E| of every point.  sms = multiprocessors of the device.
+// Error model of the FP32 pass: estimate = gamma_r |x| + gamma_b B + gamma_s S for x = phi
+// and |E| (B, S: the scales in MixedScratch::bound); defaults in eval_acc.cu.
+struct ErrModel {
+    double gamma_r, gamma_b, gamma_s;
+};
+ErrModel default_err_model();
+// Refinement after launch_eval_mixed: every point whose estimated error (em, from the
+// scales in ms.bound) exceeds tol times its |phi| or |E| is re-evaluated in two-float
+// arithmetic with FP64 near pairs, in two levels (eval_acc.cu); err (may be NULL, n x 2)
+// receives the estimated absolute error of phi and |E| of every point.  sms =
+// multiprocessors of the device.
 // ev (may be NULL): two events recorded after the first and after the second level.
 // part: refine_part_bytes(npts, sms, n_el) bytes of device scratch for the partial sums of
 // the point groups that a level splits over element chunks to keep every block busy.
 cudaError_t launch_eval_refine(const AccView& A, const ImageTable& img, const double* pts, int64_t npts,
-                               double* phi, double* E, double* err, double tol, const MixedScratch& ms, int sms,
-                               cudaStream_t s, cudaEvent_t* ev, void* part);
+                               double* phi, double* E, double* err, double tol, const ErrModel& em,
+                               const MixedScratch& ms, int sms, cudaStream_t s, cudaEvent_t* ev, void* part);
 size_t refine_part_bytes(int64_t npts, int sms, int64_t n_el);
 cudaError_t launch_pair_tiers(const FarNodes* far, const float4* cjk, int64_t n_el, int nimg, const double* pts,
                               int64_t npts, uint8_t* codes, cudaStream_t s);

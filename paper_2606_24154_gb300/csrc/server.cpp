@@ -175,7 +175,7 @@ struct Server {
         A.cell_items = c->d_fill_cell_items.as<int32_t>();
         MixedScratch ms{};
         ms.order = nullptr;
-        ms.bound = d_bound.as<float2>() + r->offset;
+        ms.bound = d_bound.as<float4>() + r->offset;
         ms.list = d_list.as<int32_t>() + r->offset;
         ms.list2 = d_list2.as<int32_t>() + r->offset;
         ms.n_list = d_nlist.as<int32_t>() + 2 * r->slot;
@@ -183,8 +183,8 @@ struct Server {
         void* part = d_rpart.ptr;
         CK(launch_eval_refine(A, c->img, d_pts.as<double>() + 3 * r->offset, r->n,
                               r->phi ? d_phi.as<double>() + r->offset : nullptr,
-                              r->E ? d_E.as<double>() + 3 * r->offset : nullptr, nullptr, c->opt.mixed_point_tol, ms,
-                              c->props.multiProcessorCount, refine, nullptr, part));
+                              r->E ? d_E.as<double>() + 3 * r->offset : nullptr, nullptr, c->opt.mixed_point_tol,
+                              c->err_model, ms, c->props.multiProcessorCount, refine, nullptr, part));
         CK(cudaEventRecord(refine_done[r->slot], refine));
         return 0;
     }
@@ -295,7 +295,7 @@ struct Server {
         // a new launch is open (the last one closed itself when it ran dry)
         CK(cudaMemsetAsync(d_head.as<unsigned long long>() + 2, 0, sizeof(unsigned long long), compute));
         CK(launch_serve(d_geoms.as<ServeGeom>(), h_ring, ring_cap, h_tail, d_head.as<unsigned long long>(),
-                        d_pts.as<double>(), d_phi.as<double>(), d_E.as<double>(), d_bound.as<float2>(),
+                        d_pts.as<double>(), d_phi.as<double>(), d_E.as<double>(), d_bound.as<float4>(),
                         d_remaining.as<int>(), h_done,
                         d_partials.as<double>(), d_pcount.as<int>(), max_chunks, (uint64_t)opt.idle_us * 1000ull,
                         opt.workers, compute));
@@ -401,7 +401,7 @@ int nebem_server_create(nebem_server** out, nebem_ctx* const* ctxs, int32_t n_ct
         (e = s->d_remaining.ensure(sizeof(int) * o.max_requests)) != cudaSuccess ||
         (e = s->d_partials.ensure(sizeof(double) * kPartialDoubles * kItemPoints * (size_t)kPartialBlocks *
                                   s->max_chunks)) != cudaSuccess ||
-        (e = s->d_bound.ensure(sizeof(float2) * cap)) != cudaSuccess ||
+        (e = s->d_bound.ensure(sizeof(float4) * cap)) != cudaSuccess ||
         (e = s->d_list.ensure(sizeof(int32_t) * cap)) != cudaSuccess ||
         (e = s->d_list2.ensure(sizeof(int32_t) * cap)) != cudaSuccess ||
         (e = s->d_rpart.ensure(refine_part_bytes(cap, cs[0]->props.multiProcessorCount, max_el))) != cudaSuccess ||

@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restr
                                                         int64_t ring_cap, int64_t* tail_mapped,
                                                         unsigned long long* head, const double* __restrict__ arena_pts,
                                                         double* __restrict__ arena_phi, double* __restrict__ arena_E,
-                                                        float2* __restrict__ arena_bound, int* remaining, int64_t* done_mapped, double* partials,
+                                                        float4* __restrict__ arena_bound, int* remaining, int64_t* done_mapped, double* partials,
                                                         int* pblock_count, int max_chunks, uint64_t idle_ns) {
     __shared__ WorkItem it;
     __shared__ int have;
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restr
             const int64_t e0 = (int64_t)it.chunk * kChunkEl;
             const int64_t e1 = min(e0 + (int64_t)kChunkEl, G.view.n_el);
             Sum4 c;
-            float2 b = make_float2(0.f, 0.f);
+            float4 b = make_float4(0.f, 0.f, 0.f, 0.f);
             if (mixed) {
                 float phx, phy, phz, plx, ply, plz;
                 load_point_2f(arena_pts, p, active, phx, phy, phz, plx, ply, plz);
@@ -114,6 +114,8 @@ __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restr
             part[kP * threadIdx.x + 3] = c.z;
             part[kP * threadIdx.x + 4] = (double)b.x;  // exact
             part[kP * threadIdx.x + 5] = (double)b.y;
+            part[kP * threadIdx.x + 6] = (double)b.z;
+            part[kP * threadIdx.x + 7] = (double)b.w;
             __threadfence();
             __syncthreads();
             if (threadIdx.x == 0) last = (atomicAdd(&pblock_count[it.pblock], 1) == it.nchunks - 1);
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restr
             if (last) {
                 __threadfence();
                 Sum4 tot{0.0, 0.0, 0.0, 0.0};
-                float2 btot = make_float2(0.f, 0.f);  // FP32 sums in chunk order, as far_block
+                float4 btot = make_float4(0.f, 0.f, 0.f, 0.f);  // FP32 sums in chunk order, as far_block
                 for (int k = 0; k < it.nchunks; ++k) {
                     const double* q = partials + ((int64_t)it.pblock * max_chunks + k) * (kP * kEvalThreads) +
                                       kP * threadIdx.x;
@@ -132,6 +134,8 @@ __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restr
                     tot.z += __ldcg(q + 3);
                     btot.x += (float)__ldcg(q + 4);
                     btot.y += (float)__ldcg(q + 5);
+                    btot.z += (float)__ldcg(q + 6);
+                    btot.w += (float)__ldcg(q + 7);
                 }
                 if (active) {
                     store_far(arena_pts, arena_phi, arena_E, p, tot);
@@ -159,7 +163,7 @@ __global__ void __launch_bounds__(kEvalThreads) k_serve(const ServeGeom* __restr
 
 cudaError_t launch_serve(const ServeGeom* geoms, const WorkItem* ring, int64_t ring_cap, int64_t* tail_mapped,
                          unsigned long long* head, const double* arena_pts, double* arena_phi, double* arena_E,
-                         float2* arena_bound, int* remaining, int64_t* done_mapped, double* partials,
+                         float4* arena_bound, int* remaining, int64_t* done_mapped, double* partials,
                          int* pblock_count, int max_chunks, uint64_t idle_ns, int workers, cudaStream_t s) {
     k_serve<<<workers, kEvalThreads, 0, s>>>(geoms, ring, ring_cap, tail_mapped, head, arena_pts, arena_phi, arena_E,
                                              arena_bound, remaining, done_mapped, partials, pblock_count, max_chunks, idle_ns);

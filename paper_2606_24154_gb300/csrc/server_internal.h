@@ -36,15 +36,15 @@ ServeGeom make_serve_geom(const Elem* el, const FarNodes* far, const float4* cjk
                           const int32_t* cell_items);
 
 // Partial sums of chunked items: pblock p, chunk c, point t at partials[(p * max_chunks + c) *
-// 128 + t] (kPartialDoubles each: phi, E, and the chunk's error scales B_phi, B_E);
+// 128 + t] (kPartialDoubles each: phi, E, and the chunk's raw error scales of bound_slot());
 // pblock_count[p] counts finished chunks.
 constexpr int kChunkElements = 1024;  // = kChunkEl of the evaluation bodies
-constexpr int kPartialDoubles = 6;
+constexpr int kPartialDoubles = 8;
 // arena_bound: the FP32 pass's error scales of every mixed point (arena index), for the
 // refinement the host launches when a request's items are done.
 cudaError_t launch_serve(const ServeGeom* geoms, const WorkItem* ring, int64_t ring_cap, int64_t* tail_mapped,
                          unsigned long long* head, const double* arena_pts, double* arena_phi, double* arena_E,
-                         float2* arena_bound, int* remaining, int64_t* done_mapped, double* partials,
+                         float4* arena_bound, int* remaining, int64_t* done_mapped, double* partials,
                          int* pblock_count, int max_chunks, uint64_t idle_ns, int workers, cudaStream_t s);
 
 }  // namespace nb

@@ -364,8 +364,7 @@ int eval_elements(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double*
             A.grid = c->fill_grid;
             A.cell_start = c->d_fill_cell_start.as<int32_t>();
             A.cell_items = c->d_fill_cell_items.as<int32_t>();
-            CK(launch_eval_refine(A, c->img, d_pts, n, d_phi, d_E, err, c->opt.mixed_point_tol, ms,
-                                  c->props.multiProcessorCount, s, &c->ev_eval[2],
+            CK(launch_eval_refine(A, c->img, d_pts, n, d_phi, d_E, err, c->opt.mixed_point_tol, c->err_model, ms, c->props.multiProcessorCount, s, &c->ev_eval[2],
                                   static_cast<char*>(c->d_scratch.ptr) + ms_bytes));
             c->refine_list = ms.n_list;
         } else {

@@ -111,6 +111,7 @@ SIGNATURES = {
     "nebem_eval_device_err": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp, _vp]),
     "nebem_eval_stats": (C.c_int, [_vp, C.POINTER(nebem_eval_stats_t)]),
     "nebem_set_wait_polls": (C.c_int, [_vp, C.c_int32]),
+    "nebem_set_error_model": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double]),
     "nebem_peak_rates": (C.c_int, [_vp, _d]),
     "nebem_space_charge": (C.c_int, [_vp, _d, _d, C.c_int64, C.c_double]),
     "nebem_space_charge_eval": (C.c_int, [_vp, _d, C.c_int64, _d, _d, C.c_int32, C.c_int32]),
@@ -288,6 +289,10 @@ def nebem_peak_rates(ctx) -> dict:
     r = np.zeros(4)
     _check(load().nebem_peak_rates(ctx, _dp(r)), "nebem_peak_rates")
     return {"ffma": r[0], "ffma2_lanes": r[1], "mufu_rsqrt": r[2], "dfma": r[3]}
+
+
+def nebem_set_error_model(ctx, gamma_r: float, gamma_b: float, gamma_s: float):
+    _check(load().nebem_set_error_model(ctx, gamma_r, gamma_b, gamma_s), "nebem_set_error_model")
 
 
 def nebem_set_wait_polls(ctx, polls: int):

@@ -269,3 +269,45 @@ def test_error_estimates_and_refinement(N):
     assert st.points == pts.shape[0] and st.refined_level1 == nref
     assert 0 <= st.refined_level2 <= st.refined_level1
     assert st.ms_fp32 > 0.0 and st.ms_level1 > 0.0 and st.ms_level2 >= 0.0
+
+
+def test_error_scales_match_oracle(N):
+    """The FP32 pass's error scales B = ke sum_j b_j and S = ke sqrt(sum_j b_j^2), with
+    b_j = |sigma_j| |sum_k Phi'_jk| (for E: |sigma_j| |sum_k E'_jk|_1) over the pairs the
+    FP32 tiers take (tier codes 0-3), against the same sums formed from the oracle's
+    closed forms; the estimate gamma_r |x| + gamma_b B + gamma_s S is linear in its
+    constants."""
+    g = I.thgem(I.PlateSpec(n_phi=24, n_r=3, n_zc=1, n_zf=4), n_plane=3)
+    sigma = structured_sigma(g)
+    pts = I.cell_points(g, 12, I.rng(1, 51))
+    codes = O.pair_tiers(g, pts)
+    timg = O.image_table(g.lattice, g.img_lo, g.img_hi)
+    sp = np.zeros((pts.shape[0], g.n))
+    sE = np.zeros((pts.shape[0], g.n, 3))
+    for j in range(g.n):
+        for k in range(timg.shape[0]):
+            p, e = O.influence(g.elements[j], pts - timg[k])
+            far = codes[:, j, k] < 4
+            sp[:, j] += np.where(far, p, 0.0)
+            sE[:, j] += np.where(far[:, None], e, 0.0)
+    ke = O.ke()
+    bphi = np.abs(sigma) * np.abs(sp)
+    bE = np.abs(sigma) * np.abs(sE).sum(axis=2)
+    B = ke * np.stack([bphi.sum(1), bE.sum(1)], axis=1)
+    S = ke * np.stack([np.sqrt((bphi ** 2).sum(1)), np.sqrt((bE ** 2).sum(1))], axis=1)
+    f = N.Context(mixed_point_tol=0.0).set_geometry(g)
+    f.set_sigma(sigma)
+    N.nebem_set_error_model(f.h, 0.0, 1.0, 0.0)
+    phi, E, eb, _ = f.eval_err(pts)
+    N.nebem_set_error_model(f.h, 0.0, 0.0, 1.0)
+    _, _, es, _ = f.eval_err(pts)
+    N.nebem_set_error_model(f.h, 1.0, 0.0, 0.0)
+    _, _, er, _ = f.eval_err(pts)
+    N.nebem_set_error_model(f.h, -1.0, -1.0, -1.0)  # the defaults
+    _, _, ed, _ = f.eval_err(pts)
+    assert np.abs(eb / B - 1).max() < 1e-5
+    assert np.abs(es / S - 1).max() < 1e-5
+    x = np.stack([np.abs(phi), np.linalg.norm(E, axis=1)], axis=1)
+    assert np.allclose(er, x, rtol=1e-15, atol=0)
+    assert np.allclose(ed, 1e-7 * x + 7e-8 * eb + 5e-7 * es, rtol=1e-6, atol=0)
+    f.close()
