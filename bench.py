@@ -429,7 +429,9 @@ def run_native(args):
     _, _, err_s, _ = N.nebem_eval_err(single.h, sub)
     refined_sub = sub[(err_r != err_s).any(axis=1)]
     counts_l1 = R.tier_counts(g, refined_sub, sample=CHECK_SAMPLE)
-    ops_l1 = stats.refined_level1 * R.acc1_ops_per_point(counts_l1, n_el)
+    n_phi, n_E = stats.refined_level1_phi_only, stats.refined_level1_E_only
+    ops_l1 = ((stats.refined_level1 - n_phi - n_E) * R.acc1_ops_per_point(counts_l1, n_el)
+              + n_phi * R.acc1_ops_per_point(counts_l1, n_el, "phi") + n_E * R.acc1_ops_per_point(counts_l1, n_el, "E"))
     ach_l1 = ops_l1 / (stats.ms_level1 * 1e-3)
     counts = R.tier_counts(g, pts_h, sample=CHECK_SAMPLE)
     ops_fp32 = R.fp32_ops_per_launch(counts, npts / CHECK_SAMPLE)
@@ -548,7 +550,9 @@ def run_native(args):
                        "l2": "flushed between timed steps (512 MB write)", "parallelism": f"points sharded x{world}"},
             "stages": {"ms_fp32_pass": stats.ms_fp32, "ms_refine_level1": stats.ms_level1,
                        "ms_refine_level2": stats.ms_level2, "points": stats.points,
-                       "refined_level1": stats.refined_level1, "refined_level2": stats.refined_level2},
+                       "refined_level1": stats.refined_level1, "refined_level2": stats.refined_level2,
+                       "refined_level1_phi_only": stats.refined_level1_phi_only,
+                       "refined_level1_E_only": stats.refined_level1_E_only},
             "single_pass": {"value": single_value, "unit": "evals/s", "ms_per_step": single_ms,
                             "note": "the FP32 pass alone (mixed_point_tol = 0): its per-point error is in "
                                     "accuracy.single_pass"},

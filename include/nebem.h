@@ -330,7 +330,8 @@ int nebem_peak_rates(nebem_ctx *ctx, double *rates);
  * with no counterpart in the paper).  Waits for that evaluation to finish.  Device times
  * (ms, CUDA events on the evaluation's stream) of the FP32 pass (binning, far tiers, FP64
  * near pairs), of the flag step plus the first two-float level, and of the second flag
- * step plus the second level; point counts of the evaluation and of both levels.
+ * step plus the second level; point counts of the evaluation and of both levels, and of
+ * the first level's points that needed only phi or only E re-evaluated.
  * Errors: NEBEM_INVALID_ARG (NULL), NEBEM_BAD_STATE (no such evaluation yet), NEBEM_CUDA. */
 typedef struct nebem_eval_stats_t {
     int64_t points;
@@ -339,7 +340,10 @@ typedef struct nebem_eval_stats_t {
     double ms_fp32;
     double ms_level1;
     double ms_level2;
-    double reserved[4];
+    int64_t refined_level1_phi_only; /* of refined_level1: points whose E estimate was within
+                                        the tolerance (phi re-evaluated, E kept) */
+    int64_t refined_level1_E_only;   /* of refined_level1: E re-evaluated, phi kept */
+    double reserved[2];
 } nebem_eval_stats_t;
 int nebem_eval_stats(nebem_ctx *ctx, nebem_eval_stats_t *out);
 

@@ -446,13 +446,13 @@ int nebem_eval_err(nebem_ctx* ctx, const double* pts, int64_t n, double* phi, do
     int rc = eval_points(c, (const double*)c->d_pts.ptr, n, phi ? (double*)c->d_phi.ptr : nullptr,
                          E ? (double*)c->d_E.ptr : nullptr, NEBEM_MIXED, c->stream, (double*)c->d_err.ptr);
     if (rc) return rc;
-    int32_t h_ref = 0;
-    if (c->refine_list) CK(cudaMemcpyAsync(&h_ref, c->refine_list, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    int32_t h_ref[4] = {0, 0, 0, 0};  // level 1 (phi and E), level 2, level 1 phi only, level 1 E only
+    if (c->refine_list) CK(cudaMemcpyAsync(h_ref, c->refine_list, sizeof(h_ref), cudaMemcpyDeviceToHost, c->stream));
     if (phi) CK(cudaMemcpyAsync(phi, c->d_phi.ptr, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
     if (E) CK(cudaMemcpyAsync(E, c->d_E.ptr, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, c->stream));
     if (err) CK(cudaMemcpyAsync(err, c->d_err.ptr, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    if (n_refined) *n_refined = h_ref;
+    if (n_refined) *n_refined = (int64_t)h_ref[0] + h_ref[2] + h_ref[3];
     return NEBEM_OK;
 }
 
@@ -481,12 +481,14 @@ int nebem_eval_stats(nebem_ctx* ctx, nebem_eval_stats_t* out) {
     CK(cudaEventSynchronize(c->ev_eval[3]));
     float t[3] = {0.f, 0.f, 0.f};
     for (int k = 0; k < 3; ++k) CK(cudaEventElapsedTime(&t[k], c->ev_eval[k], c->ev_eval[k + 1]));
-    int32_t n2[2] = {0, 0};
-    CK(cudaMemcpy(n2, c->refine_list, sizeof(n2), cudaMemcpyDeviceToHost));
+    int32_t n4[4] = {0, 0, 0, 0};
+    CK(cudaMemcpy(n4, c->refine_list, sizeof(n4), cudaMemcpyDeviceToHost));
     std::memset(out, 0, sizeof(*out));
     out->points = c->eval_points_n;
-    out->refined_level1 = n2[0];
-    out->refined_level2 = n2[1];
+    out->refined_level1 = (int64_t)n4[0] + n4[2] + n4[3];
+    out->refined_level2 = n4[1];
+    out->refined_level1_phi_only = n4[2];
+    out->refined_level1_E_only = n4[3];
     out->ms_fp32 = t[0];
     out->ms_level1 = t[1];
     out->ms_level2 = t[2];

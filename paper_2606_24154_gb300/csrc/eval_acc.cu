@@ -53,6 +53,10 @@ constexpr double kErrGammaS = 5e-7;   // FP32 pass: share of S
 constexpr double kGammaL1 = 1e-9;    // two-float, the FP32 pass's rules (truncation ~1e-10 B)
 constexpr double kGammaL2 = 1e-11;   // two-float, fill-grade rules
 
+// What a refinement pass re-evaluates: both phi and E, phi only (its E estimate was within
+// the tolerance, E keeps the FP32 pass's value), or E only.
+constexpr int kBoth = 0, kPhiOnly = 1, kEOnly = 2;
+
 // Per-pair node sums S0 = sum w / r^3, S2x = sum w (2 s_x) / r^3, S2z = sum w (2 s_z) / r^3
 // as packed two-float values (hi, negated lo) over the two lanes of the node pairs.
 struct PairSums2 {
@@ -62,6 +66,7 @@ struct PairSums2 {
 // Phi' (per element, accumulated over its images: ph, nph) and the pair sums of one tier's
 // node pairs.  Node records as in nb_internal.h (kFillNodeRec layout): q0 = (2 s_x, 2 s_z)
 // hi, q1 = (|s|^2, w) hi, q2 / q3 the lo parts.
+template <int M>
 __device__ __forceinline__ void nodes_acc2(const float4* __restrict__ nd, int pairs, const PairDF2& P, float2& ph,
                                            float2& nph, PairSums2& S) {
     const float2 m1 = bc2(-1.f);
@@ -71,13 +76,16 @@ __device__ __forceinline__ void nodes_acc2(const float4* __restrict__ nd, int pa
         node_rinv2(P, q0, q1, q2, q3, y0, ny0, nyl, a, na, nae);
         const float2 w = make_float2(q1.z, q1.w), wl = make_float2(q3.z, q3.w);
         float2 t;
-        // w / r = m - nme
-        const float2 m = __fmul2_rn(w, y0);
-        float2 nme = __ffma2_rn(w, ny0, m);
-        nme = __ffma2_rn(w, nyl, nme);
-        nme = __ffma2_rn(wl, ny0, nme);
-        two_sum2(ph, m, ph, t);
-        nph = __ffma2_rn(t, m1, __fadd2_rn(nph, nme));
+        if constexpr (M != kEOnly) {
+            // w / r = m - nme
+            const float2 m = __fmul2_rn(w, y0);
+            float2 nme = __ffma2_rn(w, ny0, m);
+            nme = __ffma2_rn(w, nyl, nme);
+            nme = __ffma2_rn(wl, ny0, nme);
+            two_sum2(ph, m, ph, t);
+            nph = __ffma2_rn(t, m1, __fadd2_rn(nph, nme));
+        }
+        if constexpr (M == kPhiOnly) continue;
         // y^3 = c3 - nc3e (y^2 = a - ny2l)
         const float2 ny2l = __ffma2_rn(__fadd2_rn(y0, y0), nyl, nae);
         const float2 c3 = __fmul2_rn(a, y0);
@@ -163,8 +171,9 @@ __host__ __device__ constexpr int acc_tile_f4(int te, int nimg, int staged, int 
 }
 
 // Raw sums (before ke) of the far pairs of one point over the elements [e0, e1) at level L,
-// with the error scales; all threads of the block take part (tiles).
-template <int L>
+// with the error scales, of phi and E (M = kBoth), phi only or E only (the other sums stay
+// 0); all threads of the block take part (tiles).
+template <int L, int M>
 __device__ __forceinline__ Sum6 acc_range(const AccView& A, int nimg, int te, float4* sm, const float (&ph)[3],
                                           const float (&pl)[3], int64_t e0, int64_t e1) {
     using Lv = Level<L>;
@@ -241,7 +250,8 @@ __device__ __forceinline__ Sum6 acc_range(const AccView& A, int nimg, int te, fl
                     np = kFillPairsC;
                 }
                 PairSums2 S{bc2(0.f), bc2(0.f), bc2(0.f), bc2(0.f), bc2(0.f), bc2(0.f)};
-                nodes_acc2(nd, np, P, fph, fnph, S);
+                nodes_acc2<M>(nd, np, P, fph, fnph, S);
+                if constexpr (M == kPhiOnly) continue;
                 float s0h, s0l, sxh, sxl, szh, szl;
                 lanes_to_df(S.s0, S.ns0, 1.f, s0h, s0l);
                 lanes_to_df(S.sx, S.nsx, 0.5f, sxh, sxl);
@@ -251,43 +261,52 @@ __device__ __forceinline__ Sum6 acc_range(const AccView& A, int nimg, int te, fl
                 df_fma_acc(zh, zl, s0h, s0l, szh, szl, ezh, ezl);
             }
             // element j: image sums in FP64, rotated to the global frame, weighted by sigma_j
-            const double fphi = ((double)fph.x - (double)fnph.x) + ((double)fph.y - (double)fnph.y);
-            const double lx = (double)exh + (double)exl, ly = (double)eyh + (double)eyl, lz = (double)ezh + (double)ezl;
-            const Elem& e = A.el[j];
-            const double gx = fma(lx, e.ex[0], fma(ly, e.ey[0], lz * e.ez[0]));
-            const double gy = fma(lx, e.ex[1], fma(ly, e.ey[1], lz * e.ez[1]));
-            const double gz = fma(lx, e.ex[2], fma(ly, e.ey[2], lz * e.ez[2]));
             const double s = A.sigma[j];
-            acc.phi = fma(s, fphi, acc.phi);
-            acc.x = fma(s, gx, acc.x);
-            acc.y = fma(s, gy, acc.y);
-            acc.z = fma(s, gz, acc.z);
-            acc.bphi = fma(fabs(s), fabs(fphi), acc.bphi);
-            acc.bE = fma(fabs(s), fabs(gx) + fabs(gy) + fabs(gz), acc.bE);
+            if constexpr (M != kEOnly) {
+                const double fphi = ((double)fph.x - (double)fnph.x) + ((double)fph.y - (double)fnph.y);
+                acc.phi = fma(s, fphi, acc.phi);
+                acc.bphi = fma(fabs(s), fabs(fphi), acc.bphi);
+            }
+            if constexpr (M != kPhiOnly) {
+                const double lx = (double)exh + (double)exl, ly = (double)eyh + (double)eyl,
+                             lz = (double)ezh + (double)ezl;
+                const Elem& e = A.el[j];
+                const double gx = fma(lx, e.ex[0], fma(ly, e.ey[0], lz * e.ez[0]));
+                const double gy = fma(lx, e.ex[1], fma(ly, e.ey[1], lz * e.ez[1]));
+                const double gz = fma(lx, e.ex[2], fma(ly, e.ey[2], lz * e.ez[2]));
+                acc.x = fma(s, gx, acc.x);
+                acc.y = fma(s, gy, acc.y);
+                acc.z = fma(s, gz, acc.z);
+                acc.bE = fma(fabs(s), fabs(gx) + fabs(gy) + fabs(gz), acc.bE);
+            }
         }
     }
     return acc;
 }
 
 // ke * sums of point p at level L into phi / E, the level's estimate into err, and (level 1)
-// ke * (B_phi, B_E, 0, 0) into bound for the next flag step.
-template <int L>
+// ke * (B_phi, B_E, 0, 0) into bound for the next flag step; a quantity the pass does not
+// re-evaluate (M) keeps its value and estimate, and its level-1 scale is 0, so that the
+// next flag step does not take it up.
+template <int L, int M>
 __device__ __forceinline__ void store_acc(int64_t p, const Sum6& tot, double* __restrict__ phi,
                                           double* __restrict__ E, double* __restrict__ err,
                                           float4* __restrict__ bound) {
     const double ke = 1.0 / (4.0 * kPi * kEps0);
     const double gamma = (L == 1) ? kGammaL1 : kGammaL2;
-    if (phi) phi[p] = ke * tot.phi;
-    if (E) {
+    if (M != kEOnly && phi) phi[p] = ke * tot.phi;
+    if (M != kPhiOnly && E) {
         E[3 * p] = ke * tot.x;
         E[3 * p + 1] = ke * tot.y;
         E[3 * p + 2] = ke * tot.z;
     }
     if (err) {
-        err[2 * p] = gamma * ke * tot.bphi;
-        err[2 * p + 1] = gamma * ke * tot.bE;
+        if (M != kEOnly) err[2 * p] = gamma * ke * tot.bphi;
+        if (M != kPhiOnly) err[2 * p + 1] = gamma * ke * tot.bE;
     }
-    if (L == 1) bound[p] = make_float4((float)(ke * tot.bphi), (float)(ke * tot.bE), 0.f, 0.f);
+    if (L == 1)
+        bound[p] = make_float4(M != kEOnly ? (float)(ke * tot.bphi) : 0.f, M != kPhiOnly ? (float)(ke * tot.bE) : 0.f,
+                               0.f, 0.f);
 }
 
 // Far part of every listed point at level L, thread per point, kAT points (a group) per
@@ -296,8 +315,9 @@ __device__ __forceinline__ void store_acc(int64_t p, const Sum6& tot, double* __
 // round-robin; the R = G - Gm left over are cut into R * nch pieces (group, element chunk of
 // kChunkEl), also round-robin, whose Sum6 go to part[chunk * cap + (group - Gm) * kAT + t]
 // for k_acc_reduce.  A whole group adds its chunks' sums in chunk order, as k_acc_reduce
-// does, so a point gets the same bits whichever way it is taken.
-template <int L>
+// does, so a point gets the same bits whichever way it is taken.  M: which quantities the
+// pass re-evaluates (kBoth, kPhiOnly, kEOnly).
+template <int L, int M>
 __global__ void __launch_bounds__(kAT, kATBlocks)
     k_eval_acc_far(const AccView A, int nimg, int te, const double* __restrict__ pts,
                    const int32_t* __restrict__ list, const int32_t* __restrict__ n_list, int nch, int64_t cap,
@@ -316,8 +336,8 @@ __global__ void __launch_bounds__(kAT, kATBlocks)
         load_point_2f(pts, p, active, ph[0], ph[1], ph[2], pl[0], pl[1], pl[2]);
         Sum6 tot{0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         for (int64_t e0 = 0; e0 < A.n_el; e0 += kChunkEl)
-            add6(tot, acc_range<L>(A, nimg, te, sm, ph, pl, e0, min(e0 + (int64_t)kChunkEl, A.n_el)));
-        if (active) store_acc<L>(p, tot, phi, E, err, bound);
+            add6(tot, acc_range<L, M>(A, nimg, te, sm, ph, pl, e0, min(e0 + (int64_t)kChunkEl, A.n_el)));
+        if (active) store_acc<L, M>(p, tot, phi, E, err, bound);
     }
     const int64_t R = G - Gm;
     for (int64_t q = blockIdx.x; q < R * nch; q += gb) {
@@ -328,14 +348,14 @@ __global__ void __launch_bounds__(kAT, kATBlocks)
         float ph[3], pl[3];
         load_point_2f(pts, p, active, ph[0], ph[1], ph[2], pl[0], pl[1], pl[2]);
         const int64_t e0 = ch * kChunkEl;
-        const Sum6 c = acc_range<L>(A, nimg, te, sm, ph, pl, e0, min(e0 + (int64_t)kChunkEl, A.n_el));
+        const Sum6 c = acc_range<L, M>(A, nimg, te, sm, ph, pl, e0, min(e0 + (int64_t)kChunkEl, A.n_el));
         if (active) part[ch * cap + r * kAT + threadIdx.x] = c;
     }
 }
 
 // The left-over groups of k_eval_acc_far launched with gb blocks: adds each point's chunk
 // sums in chunk order and stores them.
-template <int L>
+template <int L, int M>
 __global__ void __launch_bounds__(256)
     k_acc_reduce(const int32_t* __restrict__ list, const int32_t* __restrict__ n_list, int64_t gb, int nch,
                  int64_t cap, const Sum6* __restrict__ part, double* __restrict__ phi, double* __restrict__ E,
@@ -348,7 +368,7 @@ __global__ void __launch_bounds__(256)
     const int64_t p = list[Gm * kAT + i];
     Sum6 tot{0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     for (int k = 0; k < nch; ++k) add6(tot, part[(int64_t)k * cap + i]);
-    store_acc<L>(p, tot, phi, E, err, bound);
+    store_acc<L, M>(p, tot, phi, E, err, bound);
 }
 
 __global__ void __launch_bounds__(kEvalThreads)
@@ -419,12 +439,14 @@ __global__ void __launch_bounds__(128)
 
 // Flags and lists (in their input order within each block) the points whose estimate
 // gr |x| + gb B + gs S (x = phi or E, bound = (B_phi, B_E, S_phi, S_E)) exceeds tol |x| (when
-// refine != 0).  Input: order[i] (or i when order is null) for i < n, or i < *n_dev when
-// n_dev is given.  err (may be null) receives every input point's estimate.
+// refine != 0): with sel < 0 every such point; with sel = kBoth, kPhiOnly or kEOnly the
+// points where both quantities, phi only or E only exceed it.  Input: order[i] (or i when
+// order is null) for i < n, or i < *n_dev when n_dev is given.  err (may be null) receives
+// every input point's estimate.
 __global__ void __launch_bounds__(256)
     k_flag(const double* __restrict__ phi, const double* __restrict__ E, const float4* __restrict__ bound,
            const int32_t* __restrict__ order, int64_t n, const int32_t* __restrict__ n_dev, double gr, double gb,
-           double gs, double tol, int refine, double* __restrict__ err, int32_t* __restrict__ list,
+           double gs, double tol, int refine, int sel, double* __restrict__ err, int32_t* __restrict__ list,
            int32_t* __restrict__ n_list) {
     __shared__ int32_t s_warp[8];
     __shared__ int32_t s_base;
@@ -443,9 +465,9 @@ __global__ void __launch_bounds__(256)
         }
         const double ep = gr * ap + gb * (double)b.x + gs * (double)b.z;
         const double eE = gr * aE + gb * (double)b.y + gs * (double)b.w;
-        if (phi && ep > tol * ap) f = true;
-        if (E && eE > tol * aE) f = true;
-        f = f && refine;
+        const bool fp = phi && ep > tol * ap, fe = E && eE > tol * aE;
+        const int mode = (fp && fe) ? kBoth : fp ? kPhiOnly : kEOnly;
+        f = refine && (fp || fe) && (sel < 0 || sel == mode);
         if (err) {
             err[2 * p] = ep;
             err[2 * p + 1] = eE;
@@ -485,7 +507,7 @@ RefineGrid refine_grid(int64_t npts, int sms, int64_t n_el) {
     return r;
 }
 
-template <int L>
+template <int L, int M>
 cudaError_t launch_level(const AccView& A, const ImageTable& img, const double* pts, int64_t npts, double* phi,
                          double* E, double* err, float4* bound, const int32_t* list, const int32_t* n_list, int sms,
                          Sum6* part, cudaStream_t s) {
@@ -495,22 +517,26 @@ cudaError_t launch_level(const AccView& A, const ImageTable& img, const double* 
     while (te > 1 && acc_tile_f4(te, img.n, Lv::kStaged, Lv::kHdr) * (int)sizeof(float4) > 40 * 1024) te /= 2;
     const size_t smem = (size_t)acc_tile_f4(te, img.n, Lv::kStaged, Lv::kHdr) * sizeof(float4);
     const RefineGrid rg = refine_grid(npts, sms, A.n_el);
-    cudaError_t e = cudaFuncSetAttribute(k_eval_acc_far<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_eval_acc_far<L, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_eval_acc_far<L><<<(unsigned)rg.gb, kAT, smem, s>>>(A, img.n, te, pts, list, n_list, rg.nch, rg.cap, part, phi,
-                                                         E, err, bound);
+    k_eval_acc_far<L, M><<<(unsigned)rg.gb, kAT, smem, s>>>(A, img.n, te, pts, list, n_list, rg.nch, rg.cap, part,
+                                                            phi, E, err, bound);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_acc_reduce<L><<<(unsigned)((rg.cap + 255) / 256), 256, 0, s>>>(list, n_list, rg.gb, rg.nch, rg.cap, part, phi,
-                                                                      E, err, bound);
+    k_acc_reduce<L, M><<<(unsigned)((rg.cap + 255) / 256), 256, 0, s>>>(list, n_list, rg.gb, rg.nch, rg.cap, part,
+                                                                         phi, E, err, bound);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    // the FP64 near pairs, added to the quantities this pass re-evaluated only
+    double* nphi = (M == kEOnly) ? nullptr : phi;
+    double* nE = (M == kPhiOnly) ? nullptr : E;
     const int64_t want = (npts + kAT - 1) / kAT;
     const unsigned gn = (unsigned)std::max<int64_t>(1, std::min<int64_t>(want, 8 * (int64_t)sms));
     if (L == 1)
-        k_eval_acc_near1<<<gn, kEvalThreads, 0, s>>>(A.view, img, pts, list, n_list, phi, E);
+        k_eval_acc_near1<<<gn, kEvalThreads, 0, s>>>(A.view, img, pts, list, n_list, nphi, nE);
     else
-        k_eval_acc_near<<<gn, 128, 0, s>>>(A, img, pts, list, n_list, phi, E);
+        k_eval_acc_near<<<gn, 128, 0, s>>>(A, img, pts, list, n_list, nphi, nE);
     return cudaGetLastError();
 }
 
@@ -531,22 +557,41 @@ cudaError_t launch_eval_refine(const AccView& A, const ImageTable& img, const do
     if (npts == 0) return cudaSuccess;
     if (npts > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
     const bool refine = tol > 0.0 && (phi || E);
-    cudaError_t e = cudaMemsetAsync(ms.n_list, 0, 2 * sizeof(int32_t), s);  // both levels' counts
+    // counts: [0] level 1, both quantities; [1] level 2; [2] level 1, phi only; [3] level 1, E only
+    cudaError_t e = cudaMemsetAsync(ms.n_list, 0, 4 * sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     const unsigned fb = (unsigned)((npts + 255) / 256);
     k_flag<<<fb, 256, 0, s>>>(phi, E, ms.bound, ms.order, npts, nullptr, em.gamma_r, em.gamma_b, em.gamma_s, tol,
-                              refine ? 1 : 0, err, ms.list, ms.n_list);
+                              refine ? 1 : 0, kBoth, err, ms.list, ms.n_list);
     e = cudaGetLastError();
-    if (e == cudaSuccess && refine)  // level 1 on the flagged points; it leaves their level-1 scales in ms.bound
-        e = launch_level<1>(A, img, pts, npts, phi, E, err, ms.bound, ms.list, ms.n_list, sms, part, s);
+    // level 1 on the flagged points, in three passes by what they need (warps then hold
+    // points of one kind); it leaves their level-1 scales in ms.bound
+    if (e == cudaSuccess && refine) {
+        k_flag<<<fb, 256, 0, s>>>(phi, E, ms.bound, ms.order, npts, nullptr, em.gamma_r, em.gamma_b, em.gamma_s,
+                                  tol, 1, kPhiOnly, nullptr, ms.list_p, ms.n_list + 2);
+        k_flag<<<fb, 256, 0, s>>>(phi, E, ms.bound, ms.order, npts, nullptr, em.gamma_r, em.gamma_b, em.gamma_s,
+                                  tol, 1, kEOnly, nullptr, ms.list_e, ms.n_list + 3);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && refine)
+        e = launch_level<1, kBoth>(A, img, pts, npts, phi, E, err, ms.bound, ms.list, ms.n_list, sms, part, s);
+    if (e == cudaSuccess && refine)
+        e = launch_level<1, kPhiOnly>(A, img, pts, npts, phi, E, err, ms.bound, ms.list_p, ms.n_list + 2, sms, part,
+                                      s);
+    if (e == cudaSuccess && refine)
+        e = launch_level<1, kEOnly>(A, img, pts, npts, phi, E, err, ms.bound, ms.list_e, ms.n_list + 3, sms, part, s);
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[0], s);
     if (e == cudaSuccess && refine) {
-        // level 2 on the points whose level-1 estimate still exceeds the tolerance
-        k_flag<<<fb, 256, 0, s>>>(phi, E, ms.bound, ms.list, npts, ms.n_list, 0.0, kGammaL1, 0.0, tol, 1, nullptr,
-                                  ms.list2, ms.n_list + 1);
+        // level 2 on the points whose level-1 estimate still exceeds the tolerance (a quantity
+        // that level 1 left alone has a level-1 scale of 0 and is not taken up again)
+        const int32_t* l1[3] = {ms.list, ms.list_p, ms.list_e};
+        const int32_t* c1[3] = {ms.n_list, ms.n_list + 2, ms.n_list + 3};
+        for (int k = 0; k < 3; ++k)
+            k_flag<<<fb, 256, 0, s>>>(phi, E, ms.bound, l1[k], npts, c1[k], 0.0, kGammaL1, 0.0, tol, 1, -1, nullptr,
+                                      ms.list2, ms.n_list + 1);
         e = cudaGetLastError();
         if (e == cudaSuccess)
-            e = launch_level<2>(A, img, pts, npts, phi, E, err, nullptr, ms.list2, ms.n_list + 1, sms, part, s);
+            e = launch_level<2, kBoth>(A, img, pts, npts, phi, E, err, nullptr, ms.list2, ms.n_list + 1, sms, part, s);
     }
     if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], s);
     return e;

@@ -177,13 +177,17 @@ MixedScratch mixed_scratch(void* base, int64_t npts) {
     p += align256(sizeof(int32_t) * n);
     m.list2 = reinterpret_cast<int32_t*>(p);
     p += align256(sizeof(int32_t) * n);
+    m.list_p = reinterpret_cast<int32_t*>(p);
+    p += align256(sizeof(int32_t) * n);
+    m.list_e = reinterpret_cast<int32_t*>(p);
+    p += align256(sizeof(int32_t) * n);
     m.n_list = reinterpret_cast<int32_t*>(p);
     return m;
 }
 
 size_t eval_mixed_scratch_bytes(int64_t npts) {
     const size_t n = (size_t)npts;
-    return align256(sizeof(int32_t) * kBins) + 4 * align256(sizeof(int32_t) * n) + align256(sizeof(float4) * n) +
+    return align256(sizeof(int32_t) * kBins) + 6 * align256(sizeof(int32_t) * n) + align256(sizeof(float4) * n) +
            256;
 }
 

@@ -143,9 +143,11 @@ struct MixedScratch {
     int32_t* key;    // npts
     int32_t* order;  // npts
     float4* bound;   // npts
-    int32_t* list;   // npts: points of the first refinement level
+    int32_t* list;   // npts: points of the first refinement level (phi and E)
     int32_t* list2;  // npts: points of the second level
-    int32_t* n_list; // 2: the two lists' lengths
+    int32_t* list_p; // npts: points of the first level, phi only
+    int32_t* list_e; // npts: points of the first level, E only
+    int32_t* n_list; // 4: the lengths of list, list2, list_p, list_e
 };
 MixedScratch mixed_scratch(void* base, int64_t npts);
 // scratch bytes a mixed evaluation (FP32 pass and refinement) needs for npts points

@@ -114,8 +114,9 @@ struct Server {
     bool kernel_launched = false;
     DevBuf d_geoms, d_pts, d_phi, d_E, d_head, d_remaining, d_partials, d_pcount;
     DevBuf d_rpart;                           // refinement partial sums (groups split over chunks)
-    DevBuf d_bound, d_list, d_list2, d_nlist;  // refinement: error scales, the two levels' lists (arena
-                                               // index), their counts (two per slot)
+    // refinement: error scales, the lists of the two levels (level 1 in three: phi and E,
+    // phi only, E only; arena indices), their counts (four per slot)
+    DevBuf d_bound, d_list, d_list2, d_list_p, d_list_e, d_nlist;
     std::vector<int32_t> nchunks;  // element chunks per geometry
     int32_t max_chunks = 1;
     std::vector<int32_t> free_pblocks;
@@ -178,7 +179,9 @@ struct Server {
         ms.bound = d_bound.as<float4>() + r->offset;
         ms.list = d_list.as<int32_t>() + r->offset;
         ms.list2 = d_list2.as<int32_t>() + r->offset;
-        ms.n_list = d_nlist.as<int32_t>() + 2 * r->slot;
+        ms.list_p = d_list_p.as<int32_t>() + r->offset;
+        ms.list_e = d_list_e.as<int32_t>() + r->offset;
+        ms.n_list = d_nlist.as<int32_t>() + 4 * r->slot;
         // the refine stream runs one request at a time, so one partial-sum area serves them all
         void* part = d_rpart.ptr;
         CK(launch_eval_refine(A, c->img, d_pts.as<double>() + 3 * r->offset, r->n,
@@ -404,8 +407,10 @@ int nebem_server_create(nebem_server** out, nebem_ctx* const* ctxs, int32_t n_ct
         (e = s->d_bound.ensure(sizeof(float4) * cap)) != cudaSuccess ||
         (e = s->d_list.ensure(sizeof(int32_t) * cap)) != cudaSuccess ||
         (e = s->d_list2.ensure(sizeof(int32_t) * cap)) != cudaSuccess ||
+        (e = s->d_list_p.ensure(sizeof(int32_t) * cap)) != cudaSuccess ||
+        (e = s->d_list_e.ensure(sizeof(int32_t) * cap)) != cudaSuccess ||
         (e = s->d_rpart.ensure(refine_part_bytes(cap, cs[0]->props.multiProcessorCount, max_el))) != cudaSuccess ||
-        (e = s->d_nlist.ensure(2 * sizeof(int32_t) * o.max_requests)) != cudaSuccess ||
+        (e = s->d_nlist.ensure(4 * sizeof(int32_t) * o.max_requests)) != cudaSuccess ||
         (e = s->d_pcount.ensure(sizeof(int) * kPartialBlocks)) != cudaSuccess)
         return bail(cuda_fail(e, "server device buffers"));
     if ((e = cudaHostAlloc(&s->h_ring, sizeof(WorkItem) * s->ring_cap, cudaHostAllocMapped)) != cudaSuccess ||

@@ -368,7 +368,7 @@ int eval_elements(Ctx* c, const double* d_pts, int64_t n, double* d_phi, double*
                                   static_cast<char*>(c->d_scratch.ptr) + ms_bytes));
             c->refine_list = ms.n_list;
         } else {
-            CK(cudaMemsetAsync(ms.n_list, 0, 2 * sizeof(int32_t), s));
+            CK(cudaMemsetAsync(ms.n_list, 0, 4 * sizeof(int32_t), s));
             CK(cudaEventRecord(c->ev_eval[2], s));
             CK(cudaEventRecord(c->ev_eval[3], s));
             c->refine_list = ms.n_list;

@@ -71,7 +71,9 @@ class nebem_eval_stats_t(C.Structure):
         ("ms_fp32", C.c_double),
         ("ms_level1", C.c_double),
         ("ms_level2", C.c_double),
-        ("reserved", C.c_double * 4),
+        ("refined_level1_phi_only", C.c_int64),
+        ("refined_level1_E_only", C.c_int64),
+        ("reserved", C.c_double * 2),
     ]
 
 

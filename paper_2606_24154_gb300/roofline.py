@@ -166,17 +166,27 @@ def fill_ops(counts, n):
 #   per node slot: r^2 and the refined 1/r (41, plus one MUFU rsqrt), w / r accumulated
 #     (12), w / r^3 (11) accumulated (8), and w (2 s_x) / r^3, w (2 s_z) / r^3 accumulated
 #     (1 + 12 + 12).
+# A point whose E estimate was within the tolerance has phi alone re-evaluated: per pair
+# without the folding and the E multiply-adds (161 - 90), per slot r^2, 1/r and w / r
+# (41 + 12).  A point whose phi estimate was within it has E alone re-evaluated: per slot
+# without w / r (97 - 12).
 ACC1_OPS_ELEMENT = 108
 ACC1_OPS_PAIR = 161
 ACC1_OPS_SLOT = 97
+ACC1_OPS_PAIR_PHI = 71
+ACC1_OPS_SLOT_PHI = 53
+ACC1_OPS_SLOT_E = 85
 
 
-def acc1_ops_per_point(counts, n_el):
+def acc1_ops_per_point(counts, n_el, mode="both"):
     """FP32 lane operations of the first refinement level per refined point, from
-    tier_counts taken on a sample of refined points."""
+    tier_counts taken on a sample of refined points; mode "both", "phi" or "E" (which
+    quantities the point has re-evaluated)."""
+    pair, slot = {"both": (ACC1_OPS_PAIR, ACC1_OPS_SLOT), "phi": (ACC1_OPS_PAIR_PHI, ACC1_OPS_SLOT_PHI),
+                  "E": (ACC1_OPS_PAIR, ACC1_OPS_SLOT_E)}[mode]
     per = counts["sample_points"]
     far = counts["t0"] + counts["a"] + counts["b"] + counts["c"]
-    return ACC1_OPS_ELEMENT * n_el + (ACC1_OPS_PAIR * far + ACC1_OPS_SLOT * counts["slots"]) / per
+    return ACC1_OPS_ELEMENT * n_el + (pair * far + slot * counts["slots"]) / per
 
 
 # Space-charge carrier sum (spacecharge.cu, mixed): per (target, source) pair, the two-float

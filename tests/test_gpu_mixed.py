@@ -252,11 +252,21 @@ def test_error_estimates_and_refinement(N):
     assert (dE_f <= ferr[:, 1]).all(), (dE_f / ferr[:, 1]).max()
     assert pp_vec(fE, E64) > TOL_MIXED or pp_scalar(fphi, phi64) > TOL_MIXED
     # which points were refined: exactly the flagged ones
-    flag = (ferr[:, 0] > 1e-6 * np.abs(fphi)) | (ferr[:, 1] > 1e-6 * np.linalg.norm(fE, axis=1))
+    fp = ferr[:, 0] > 1e-6 * np.abs(fphi)
+    fe = ferr[:, 1] > 1e-6 * np.linalg.norm(fE, axis=1)
+    flag = fp | fe
     assert int(flag.sum()) == nref
     changed = (phi != fphi) | (E != fE).any(axis=1)
     assert not changed[~flag].any()
     assert np.array_equal(err[~flag], ferr[~flag])
+    # a point re-evaluated for one quantity keeps the other's value and estimate, unless
+    # its level-1 estimate sent it on to level 2, which re-evaluates both
+    # (level-2 estimates, 1e-11 B, are far below a thousandth of the FP32 pass's, >= 7e-8 B)
+    l2 = (err[:, 0] < 1e-3 * ferr[:, 0]) & (err[:, 1] < 1e-3 * ferr[:, 1])
+    only_phi, only_e = fp & ~fe & ~l2, fe & ~fp & ~l2
+    assert only_phi.any() and only_e.any()
+    assert np.array_equal(E[only_phi], fE[only_phi]) and np.array_equal(err[only_phi, 1], ferr[only_phi, 1])
+    assert np.array_equal(phi[only_e], fphi[only_e]) and np.array_equal(err[only_e, 0], ferr[only_e, 0])
     # refined: the bound at every point, and covered estimates
     assert_mixed(phi, E, phi64, E64)
     assert (np.abs(phi - phi64)[flag] <= err[flag, 0] + 1e-12 * np.abs(phi64[flag])).all()
@@ -267,6 +277,7 @@ def test_error_estimates_and_refinement(N):
     # the stage report of that evaluation
     st = N.nebem_eval_stats(ctx.h)
     assert st.points == pts.shape[0] and st.refined_level1 == nref
+    assert st.refined_level1_phi_only == int((fp & ~fe).sum()) and st.refined_level1_E_only == int((fe & ~fp).sum())
     assert 0 <= st.refined_level2 <= st.refined_level1
     assert st.ms_fp32 > 0.0 and st.ms_level1 > 0.0 and st.ms_level2 >= 0.0
 

@@ -48,3 +48,19 @@ def test_refinement_counts():
     far = c["t0"] + c["a"] + c["b"] + c["c"]
     per = R.acc1_ops_per_point(c, g.n)
     assert per == R.ACC1_OPS_ELEMENT * g.n + (R.ACC1_OPS_PAIR * far + R.ACC1_OPS_SLOT * c["slots"]) / 16
+
+
+def test_refinement_ops_by_mode():
+    """A point re-evaluated for phi alone or E alone costs fewer counted operations than one
+    re-evaluated for both, and the per-mode counts differ from the full one by exactly the
+    parts each mode skips."""
+    c = {"sample_points": 4, "t0": 100, "a": 10, "b": 2, "c": 1, "near": 3, "slots": 460, "nodes": 458, "pairs": 116}
+    n_el = 50
+    both = R.acc1_ops_per_point(c, n_el)
+    phi = R.acc1_ops_per_point(c, n_el, "phi")
+    e = R.acc1_ops_per_point(c, n_el, "E")
+    far = 113
+    assert both - phi == ((R.ACC1_OPS_PAIR - R.ACC1_OPS_PAIR_PHI) * far
+                          + (R.ACC1_OPS_SLOT - R.ACC1_OPS_SLOT_PHI) * c["slots"]) / 4
+    assert both - e == (R.ACC1_OPS_SLOT - R.ACC1_OPS_SLOT_E) * c["slots"] / 4
+    assert phi < e < both
