@@ -283,7 +283,9 @@ int nebem_eval_device(nebem_ctx *ctx, const double *d_pts, int64_t n, double *d_
  * measured against the FP64 path by 1.7 times or more (a statistical estimate, not a
  * bound).  A point whose estimate exceeds mixed_point_tol times its
  * |phi| or |E| (context option, default 1e-6) is evaluated again in two-float arithmetic
- * (about 44 bits): first with the same Gauss rules and FP64 near pairs (estimate 1e-9 B),
+ * (about 44 bits) for the quantity or quantities whose estimate exceeds it (the other keeps
+ * its value and estimate): first with the same Gauss rules and FP64 near pairs (estimate
+ * 1e-9 B),
  * and where that estimate still exceeds the tolerance, with rules truncated below ~3e-12 of
  * each pair and FP64 closed forms within 6 element radii (estimate 1e-11 B).
  * nebem_eval / nebem_eval_device with NEBEM_MIXED
